@@ -1,0 +1,410 @@
+// Plain, slow CPU oracle for the weakly singular Burton-Miller (WSBM) Nystrom system.
+//
+// TEST INFRASTRUCTURE ONLY.  Nothing in the product library links, loads or calls this file;
+// only the test suite, the smoke check and the CPU-baseline leg of the benchmark do.  It
+// shares no code, header or constant table with the CUDA path.
+//
+// What it computes (paper: Matsumoto & Yokota, "Proxy-surface-based fast direct solver for
+// TE-mode scattering problems on distributed memory systems"):
+//   * Hankel values H0^(1)(z), H1^(1)(z) from the C++17 special functions
+//     std::cyl_bessel_jl / std::cyl_neumannl, evaluated in long double and rounded to double.
+//   * The 2x2 WSBM block of eq. (weakly_bm) for a node pair (Sec. II; the block form A_ij of
+//     Sec. III), with the kernels of S_k, D_k, D*_k and N_k of the 2-D Helmholtz fundamental
+//     solution G_k = (i/4) H0^(1)(k r).  The paper names these operators but does not print
+//     G; the reading (radiating H^(1), D differentiates in y, D* in x) is the one consistent
+//     with the jump terms +-I/2 of eqs. (bm) and (weakly_bm).
+//   * The one-point corrected diagonal (Sec. I/II: "only the diagonal terms are locally
+//     corrected"; zeta-corrected trapezoidal rule).  The paper prints no formula; the reading
+//     is the one-point log correction w_i*ln(w_i/2pi) applied to each log-singular kernel
+//     and the smooth limits of D and D* (curvature term).
+//   * Proxy-circle blocks used by the proxy-surface interpolative decomposition (Sec. III,
+//     "low-rank approximations are computed via the proxy-surface method").
+//
+// Floating point: compile with -ffp-contract=off so that the geometric quantities
+// (d, r, k*r, d.n) follow exactly the operation order written below.
+#include <cmath>
+#include <complex>
+#include <cstdint>
+#include <cstring>
+#include <vector>
+
+typedef std::complex<double> cplx;
+typedef long double ld;
+
+static const double PI = 3.14159265358979323846264338327950288;
+static const double EULER_GAMMA = 0.57721566490153286060651209008240243;
+static const ld PI_L = 3.14159265358979323846264338327950288L;
+
+// ---------------------------------------------------------------------------------------
+// Hankel functions of the first kind, orders 0 and 1, and the pole-free combination
+//   F1(z) = H1(z)/z + 2i/(pi z^2)
+// (the k-independent 1/r^2 pole of N_k cancels in N_k0 - N_k1; the paper notes that this
+// difference is only weakly singular, Sec. II after eq. (weakly_bm)).
+// ---------------------------------------------------------------------------------------
+struct Hank {
+  cplx h0, h1, f1;
+};
+
+static Hank hankel_eval(double z) {
+  ld zl = (ld)z;
+  ld j0 = std::cyl_bessel_jl(0.0L, zl);
+  ld j1 = std::cyl_bessel_jl(1.0L, zl);
+  ld y0 = std::cyl_neumannl(0.0L, zl);
+  ld y1 = std::cyl_neumannl(1.0L, zl);
+  Hank h;
+  h.h0 = cplx((double)j0, (double)y0);
+  h.h1 = cplx((double)j1, (double)y1);
+  ld f1re = j1 / zl;
+  ld f1im = y1 / zl + 2.0L / (PI_L * zl * zl);
+  h.f1 = cplx((double)f1re, (double)f1im);
+  return h;
+}
+
+struct Params {
+  double k0, k1, eps0, eps1;
+};
+
+// ---------------------------------------------------------------------------------------
+// Off-diagonal 2x2 WSBM block for row node i (target x), column node j (source y), with the
+// quadrature weight w_j folded in.  Eq. (weakly_bm):
+//   [ D_k1 + I/2                          , -eps1 S_k1                                  ]
+//   [ D_k0 - I/2 + alpha (N_k0 - N_k1)    , -eps0 S_k0 - alpha(eps0 D*_k0 - eps1 D*_k1) ]
+//       - alpha (eps0+eps1) I/2 on the diagonal;  alpha = i/k0 (Sec. II, after eq. (bm)).
+// Kernels (d = x - y, r = |d|):
+//   G_k   = (i/4) H0(k r)
+//   dG/dn_y = (i k/4) H1(k r) (d.n_y)/r                         (kernel of D_k)
+//   dG/dn_x = -(i k/4) H1(k r) (d.n_x)/r                        (kernel of D*_k)
+//   N_k   = (i k^2/4) [ H0(kr) c + H1(kr)/(kr) (n_x.n_y - 2c) ],  c = (d.n_x)(d.n_y)/r^2
+// ---------------------------------------------------------------------------------------
+struct Geom {
+  int64_t n;
+  const double *x, *y, *nx, *ny, *w, *kappa;
+};
+
+static void pair_block_offdiag(const Geom& g, const Params& p, int64_t i, int64_t j, cplx a[2][2]) {
+  const cplx I1(0.0, 1.0);
+  double dx = g.x[i] - g.x[j];
+  double dy = g.y[i] - g.y[j];
+  double r2 = dx * dx + dy * dy;
+  double r = std::sqrt(r2);
+  double z0 = p.k0 * r;
+  double z1 = p.k1 * r;
+  double dny = dx * g.nx[j] + dy * g.ny[j];
+  double dnx = dx * g.nx[i] + dy * g.ny[i];
+  double nn = g.nx[i] * g.nx[j] + g.ny[i] * g.ny[j];
+  double c = (dnx * dny) / r2;
+  Hank ha = hankel_eval(z0);
+  Hank hb = hankel_eval(z1);
+  cplx G0 = 0.25 * I1 * ha.h0;
+  cplx G1 = 0.25 * I1 * hb.h0;
+  cplx Dy0 = 0.25 * I1 * p.k0 * ha.h1 * (dny / r);
+  cplx Dy1 = 0.25 * I1 * p.k1 * hb.h1 * (dny / r);
+  cplx Dx0 = -0.25 * I1 * p.k0 * ha.h1 * (dnx / r);
+  cplx Dx1 = -0.25 * I1 * p.k1 * hb.h1 * (dnx / r);
+  double q0 = p.k0 * p.k0, q1 = p.k1 * p.k1;
+  cplx dN = 0.25 * I1 * ((q0 * ha.h0 - q1 * hb.h0) * c + (q0 * ha.f1 - q1 * hb.f1) * (nn - 2.0 * c));
+  cplx alpha = I1 / p.k0;
+  double wj = g.w[j];
+  a[0][0] = wj * Dy1;
+  a[0][1] = -p.eps1 * wj * G1;
+  a[1][0] = wj * (Dy0 + alpha * dN);
+  a[1][1] = wj * (-p.eps0 * G0 - alpha * (p.eps0 * Dx0 - p.eps1 * Dx1));
+}
+
+// Diagonal 2x2 block: one-point corrected trapezoidal rule.  A kernel a(x,y) ln|x-y| + b(x,y)
+// gets the diagonal weight w_i [a ln(w_i/2pi) + b(x_i,x_i)].  Applied to
+//   S_k:   a = -1/(2pi),            b = i/4 - (ln(k/2) + gamma)/(2pi)
+//   D, D*: a = 0,                   b = -kappa/(4pi)          (smooth limit, outward normal)
+//   N_k0 - N_k1: a = -(k0^2-k1^2)/(4pi),
+//                b = i(k0^2-k1^2)/8 - [k0^2(ln(k0/2)+gamma-1/2) - k1^2(ln(k1/2)+gamma-1/2)]/(4pi)
+// plus the identity terms of eq. (weakly_bm).
+static void pair_block_diag(const Geom& g, const Params& p, int64_t i, cplx a[2][2]) {
+  const cplx I1(0.0, 1.0);
+  double wi = g.w[i];
+  double kap = g.kappa[i];
+  auto S = [&](double k) {
+    return wi * (0.25 * I1 - (EULER_GAMMA + std::log(k * wi / (4.0 * PI))) / (2.0 * PI));
+  };
+  auto f = [&](double k) { return k * k * (std::log(k * wi / (4.0 * PI)) + EULER_GAMMA - 0.5); };
+  double Dd = -wi * kap / (4.0 * PI);
+  cplx dN = wi * (I1 * (p.k0 * p.k0 - p.k1 * p.k1) / 8.0 - (f(p.k0) - f(p.k1)) / (4.0 * PI));
+  cplx alpha = I1 / p.k0;
+  a[0][0] = Dd + 0.5;
+  a[0][1] = -p.eps1 * S(p.k1);
+  a[1][0] = Dd - 0.5 + alpha * dN;
+  a[1][1] = -p.eps0 * S(p.k0) - alpha * (p.eps0 - p.eps1) * Dd - alpha * (p.eps0 + p.eps1) * 0.5;
+}
+
+static void pair_block(const Geom& g, const Params& p, int64_t i, int64_t j, cplx a[2][2]) {
+  if (i == j)
+    pair_block_diag(g, p, i, a);
+  else
+    pair_block_offdiag(g, p, i, j, a);
+}
+
+// ---------------------------------------------------------------------------------------
+// Proxy-circle entries (proxy-surface method, Sec. III).  A proxy point p with outward unit
+// normal nu carries a combined-field source Phi_k(x,p) = dG_k(x,p)/dnu_p - i eta G_k(x,p),
+// eta = k (the combined field avoids interior resonances of the proxy disk).
+//
+// Row block (the equations of a box, used to pick row skeletons).  In eq. (weakly_bm) the
+// equations at a target x read, for far sources,
+//   eq1(x) = psi1(x),     eq2(x) = psi0(x) + alpha d_n psi0(x) - alpha d_n psi1(x)
+// with psi_k the k-field of the sources.  Column m (0 <= m < P) is the k1 proxy source
+// [Phi1 ; -alpha d_nx Phi1], column P+m the k0 proxy source [0 ; Phi0 + alpha d_nx Phi0].
+//
+// Column block (the unknowns of a box, used to pick column skeletons).  Far equations depend
+// on the box's unknowns only through psi1 and psi0 outside the proxy circle, which the
+// exterior Dirichlet data on the circle fixes.  Row m is psi1 at p_m, row P+m is psi0 at p_m:
+//   u_j -> w_j dG_k(p,y_j)/dn_y,   q_j -> -eps_k w_j G_k(p,y_j).
+// ---------------------------------------------------------------------------------------
+static void proxy_row_entries(const Geom& g, const Params& p, int64_t i, double px, double py,
+                              double pnx, double pny, double pw, cplx out[2][2]) {
+  const cplx I1(0.0, 1.0);
+  double dx = g.x[i] - px;
+  double dy = g.y[i] - py;
+  double r2 = dx * dx + dy * dy;
+  double r = std::sqrt(r2);
+  double dnu = dx * pnx + dy * pny;       // d . nu_p
+  double dnx = dx * g.nx[i] + dy * g.ny[i];  // d . n_x
+  double nn = g.nx[i] * pnx + g.ny[i] * pny;
+  double c = (dnx * dnu) / r2;
+  cplx alpha = I1 / p.k0;
+  cplx phi[2], dphi[2];
+  for (int s = 0; s < 2; ++s) {
+    double k = (s == 0) ? p.k1 : p.k0;
+    double z = k * r;
+    Hank h = hankel_eval(z);
+    cplx G = 0.25 * I1 * h.h0;
+    cplx dGdnu = 0.25 * I1 * k * h.h1 * (dnu / r);
+    cplx dGdnx = -0.25 * I1 * k * h.h1 * (dnx / r);
+    cplx Nk = 0.25 * I1 * k * k * (h.h0 * c + (h.h1 / z) * (nn - 2.0 * c));
+    double eta = k;
+    phi[s] = dGdnu - I1 * eta * G;
+    dphi[s] = Nk - I1 * eta * dGdnx;
+  }
+  // out[a][s]: equation a of node i, source s (0 = k1 source, 1 = k0 source)
+  out[0][0] = pw * phi[0];
+  out[1][0] = pw * (-alpha * dphi[0]);
+  out[0][1] = cplx(0.0, 0.0);
+  out[1][1] = pw * (phi[1] + alpha * dphi[1]);
+}
+
+static void proxy_col_entries(const Geom& g, const Params& p, int64_t j, double px, double py,
+                              cplx out[2][2]) {
+  const cplx I1(0.0, 1.0);
+  double dx = px - g.x[j];
+  double dy = py - g.y[j];
+  double r2 = dx * dx + dy * dy;
+  double r = std::sqrt(r2);
+  double dny = dx * g.nx[j] + dy * g.ny[j];
+  double wj = g.w[j];
+  // out[s][b]: field s (0 = psi1, 1 = psi0) from unknown b (0 = u_j, 1 = q_j)
+  for (int s = 0; s < 2; ++s) {
+    double k = (s == 0) ? p.k1 : p.k0;
+    double eps = (s == 0) ? p.eps1 : p.eps0;
+    Hank h = hankel_eval(k * r);
+    out[s][0] = wj * (0.25 * I1 * k * h.h1 * (dny / r));
+    out[s][1] = -eps * wj * (0.25 * I1 * h.h0);
+  }
+}
+
+extern "C" {
+
+// H0, H1 at n arguments; out[4t..4t+3] = Re H0, Im H0, Re H1, Im H1.
+int orc_hankel01(const double* z, int64_t n, double* out) {
+#pragma omp parallel for schedule(dynamic, 64)
+  for (int64_t t = 0; t < n; ++t) {
+    Hank h = hankel_eval(z[t]);
+    out[4 * t + 0] = h.h0.real();
+    out[4 * t + 1] = h.h0.imag();
+    out[4 * t + 2] = h.h1.real();
+    out[4 * t + 3] = h.h1.imag();
+  }
+  return 0;
+}
+
+// F1(z) = H1(z)/z + 2i/(pi z^2); out[2t], out[2t+1] = Re, Im.
+int orc_f1(const double* z, int64_t n, double* out) {
+  for (int64_t t = 0; t < n; ++t) {
+    Hank h = hankel_eval(z[t]);
+    out[2 * t] = h.f1.real();
+    out[2 * t + 1] = h.f1.imag();
+  }
+  return 0;
+}
+
+// Entries A[rows, cols] of the 2N x 2N WSBM matrix, unknowns in the paper's block order
+// [u ; q] (index r < N: u_r / first equation at node r;  r >= N: q_{r-N} / second equation).
+// out: column-major nr x nc complex128 (interleaved re, im), leading dimension nr.
+int orc_wsbm_entries(int64_t n, const double* x, const double* y, const double* nx,
+                     const double* ny, const double* w, const double* kappa, double k0,
+                     double k1, double eps0, double eps1, const int64_t* rows, int64_t nr,
+                     const int64_t* cols, int64_t nc, double* out) {
+  Geom g{n, x, y, nx, ny, w, kappa};
+  Params p{k0, k1, eps0, eps1};
+  for (int64_t t = 0; t < nr; ++t)
+    if (rows[t] < 0 || rows[t] >= 2 * n) return -1;
+  for (int64_t t = 0; t < nc; ++t)
+    if (cols[t] < 0 || cols[t] >= 2 * n) return -1;
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int64_t cc = 0; cc < nc; ++cc) {
+    int64_t j = cols[cc] % n, b = cols[cc] / n;
+    for (int64_t rr = 0; rr < nr; ++rr) {
+      int64_t i = rows[rr] % n, a = rows[rr] / n;
+      cplx blk[2][2];
+      pair_block(g, p, i, j, blk);
+      cplx v = blk[a][b];
+      out[2 * (cc * nr + rr)] = v.real();
+      out[2 * (cc * nr + rr) + 1] = v.imag();
+    }
+  }
+  return 0;
+}
+
+// The full dense 2N x 2N matrix, paper order, column-major complex128.
+int orc_wsbm_dense(int64_t n, const double* x, const double* y, const double* nx, const double* ny,
+                   const double* w, const double* kappa, double k0, double k1, double eps0,
+                   double eps1, double* out) {
+  Geom g{n, x, y, nx, ny, w, kappa};
+  Params p{k0, k1, eps0, eps1};
+  int64_t ld2 = 2 * n;
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int64_t j = 0; j < n; ++j) {
+    for (int64_t i = 0; i < n; ++i) {
+      cplx blk[2][2];
+      pair_block(g, p, i, j, blk);
+      for (int a = 0; a < 2; ++a)
+        for (int b = 0; b < 2; ++b) {
+          int64_t r = a * n + i, c = b * n + j;
+          out[2 * (c * ld2 + r)] = blk[a][b].real();
+          out[2 * (c * ld2 + r) + 1] = blk[a][b].imag();
+        }
+    }
+  }
+  return 0;
+}
+
+// Matrix-free product y = A x for the dense system (paper order), x, y complex128 of length
+// 2N, nrhs columns (column-major, leading dimension 2N).
+int orc_wsbm_matvec(int64_t n, const double* x, const double* y, const double* nx, const double* ny,
+                    const double* w, const double* kappa, double k0, double k1, double eps0,
+                    double eps1, const double* xin, int64_t nrhs, double* yout) {
+  Geom g{n, x, y, nx, ny, w, kappa};
+  Params p{k0, k1, eps0, eps1};
+  const cplx* X = reinterpret_cast<const cplx*>(xin);
+  cplx* Y = reinterpret_cast<cplx*>(yout);
+#pragma omp parallel for schedule(dynamic, 4)
+  for (int64_t i = 0; i < n; ++i) {
+    std::vector<cplx> acc(2 * nrhs, cplx(0.0, 0.0));
+    for (int64_t j = 0; j < n; ++j) {
+      cplx blk[2][2];
+      pair_block(g, p, i, j, blk);
+      for (int64_t c = 0; c < nrhs; ++c) {
+        const cplx* xc = X + c * 2 * n;
+        acc[2 * c] += blk[0][0] * xc[j] + blk[0][1] * xc[n + j];
+        acc[2 * c + 1] += blk[1][0] * xc[j] + blk[1][1] * xc[n + j];
+      }
+    }
+    for (int64_t c = 0; c < nrhs; ++c) {
+      Y[c * 2 * n + i] = acc[2 * c];
+      Y[c * 2 * n + n + i] = acc[2 * c + 1];
+    }
+  }
+  return 0;
+}
+
+// Proxy circle of a set of nodes: centre = midpoint of the bounding box, R = largest distance
+// from the centre to a node, proxy radius rho = ratio * R.  out: cx, cy, R, rho.
+int orc_proxy_circle(const double* x, const double* y, const int64_t* nodes, int64_t m,
+                     double ratio, double* out) {
+  if (m <= 0) return -1;
+  double xmin = x[nodes[0]], xmax = xmin, ymin = y[nodes[0]], ymax = ymin;
+  for (int64_t t = 1; t < m; ++t) {
+    double a = x[nodes[t]], b = y[nodes[t]];
+    if (a < xmin) xmin = a;
+    if (a > xmax) xmax = a;
+    if (b < ymin) ymin = b;
+    if (b > ymax) ymax = b;
+  }
+  double cx = 0.5 * (xmin + xmax), cy = 0.5 * (ymin + ymax);
+  double R = 0.0;
+  for (int64_t t = 0; t < m; ++t) {
+    double dx = x[nodes[t]] - cx, dy = y[nodes[t]] - cy;
+    double d = std::sqrt(dx * dx + dy * dy);
+    if (d > R) R = d;
+  }
+  out[0] = cx;
+  out[1] = cy;
+  out[2] = R;
+  out[3] = ratio * R;
+  return 0;
+}
+
+// Proxy points p_m = c + rho (cos t_m, sin t_m), t_m = 2 pi m / P, outward normals.
+static void proxy_point(double cx, double cy, double rho, int64_t P, int64_t m, double* px,
+                        double* py, double* pnx, double* pny) {
+  double t = 2.0 * PI * (double)m / (double)P;
+  double ct = std::cos(t), st = std::sin(t);
+  *pnx = ct;
+  *pny = st;
+  *px = cx + rho * ct;
+  *py = cy + rho * st;
+}
+
+// Row proxy block: rows = equation indices (paper order) of a box, columns = 2P proxy
+// sources (k1 sources first, then k0 sources), each scaled by the proxy weight 2 pi rho / P.
+// out: column-major nr x 2P complex128.
+int orc_proxy_row_block(int64_t n, const double* x, const double* y, const double* nx,
+                        const double* ny, const double* w, const double* kappa, double k0,
+                        double k1, double eps0, double eps1, const int64_t* rows, int64_t nr,
+                        double cx, double cy, double rho, int64_t P, double* out) {
+  Geom g{n, x, y, nx, ny, w, kappa};
+  Params p{k0, k1, eps0, eps1};
+  double pw = 2.0 * PI * rho / (double)P;
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int64_t m = 0; m < P; ++m) {
+    double px, py, pnx, pny;
+    proxy_point(cx, cy, rho, P, m, &px, &py, &pnx, &pny);
+    for (int64_t rr = 0; rr < nr; ++rr) {
+      int64_t i = rows[rr] % n, a = rows[rr] / n;
+      cplx e[2][2];
+      proxy_row_entries(g, p, i, px, py, pnx, pny, pw, e);
+      for (int s = 0; s < 2; ++s) {
+        int64_t cc = s * P + m;
+        out[2 * (cc * nr + rr)] = e[a][s].real();
+        out[2 * (cc * nr + rr) + 1] = e[a][s].imag();
+      }
+    }
+  }
+  return 0;
+}
+
+// Column proxy block: rows = 2P proxy evaluations (psi1 at the P points, then psi0), columns =
+// unknown indices (paper order) of a box.  out: column-major 2P x nc complex128.
+int orc_proxy_col_block(int64_t n, const double* x, const double* y, const double* nx,
+                        const double* ny, const double* w, const double* kappa, double k0,
+                        double k1, double eps0, double eps1, const int64_t* cols, int64_t nc,
+                        double cx, double cy, double rho, int64_t P, double* out) {
+  Geom g{n, x, y, nx, ny, w, kappa};
+  Params p{k0, k1, eps0, eps1};
+  int64_t ldo = 2 * P;
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int64_t cc = 0; cc < nc; ++cc) {
+    int64_t j = cols[cc] % n, b = cols[cc] / n;
+    for (int64_t m = 0; m < P; ++m) {
+      double px, py, pnx, pny;
+      proxy_point(cx, cy, rho, P, m, &px, &py, &pnx, &pny);
+      cplx e[2][2];
+      proxy_col_entries(g, p, j, px, py, e);
+      for (int s = 0; s < 2; ++s) {
+        int64_t rr = s * P + m;
+        out[2 * (cc * ldo + rr)] = e[s][b].real();
+        out[2 * (cc * ldo + rr) + 1] = e[s][b].imag();
+      }
+    }
+  }
+  return 0;
+}
+
+}  // extern "C"
