@@ -1,0 +1,195 @@
+/*
+ * wsbm_hss.h -- C ABI of the GB300 (sm_103a) entry generator and HSS direct solver for the
+ * weakly singular Burton-Miller (WSBM) boundary integral equation of 2-D TE-mode transmission
+ * scattering (Matsumoto & Yokota, "Proxy-surface-based fast direct solver for TE-mode
+ * scattering problems on distributed memory systems").
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ *  - Return value: WSBM_OK (0) on success, a negative WSBM_ERR_* code otherwise; no C++
+ *    exception crosses this boundary.  wsbm_strerror() names a code.
+ *  - Pointers documented as "device" are CUDA device pointers of the current device; they are
+ *    owned by the caller and only read (inputs) or written (outputs) during the call, in
+ *    stream order on `stream` (a cudaStream_t passed as void*; NULL = the legacy default
+ *    stream).  Calls return after enqueueing unless stated otherwise.
+ *  - Complex numbers are interleaved (re, im) pairs of doubles (complex128).
+ *  - Matrices are column-major.
+ *  - Unknown indices follow the paper's block order [u ; q] (eq. weakly_bm): for a curve of N
+ *    nodes, index r < N is u at node r (and, as a row, the first equation at node r);
+ *    index r >= N is q at node r - N (the second equation).
+ *  - Geometry: N nodes in counter-clockwise order along a closed smooth curve, outward unit
+ *    normals, trapezoidal weights w_j (= h |gamma'(t_j)| for equispaced t_j) and curvature
+ *    kappa_j (needed by the one-point corrected diagonal of D and D*).
+ */
+#ifndef WSBM_HSS_H
+#define WSBM_HSS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  WSBM_OK = 0,
+  WSBM_ERR_INVALID_ARG = -1,   /* bad size, NULL pointer, non-finite or inconsistent input */
+  WSBM_ERR_OOM = -2,           /* a device or host allocation failed                        */
+  WSBM_ERR_CUDA = -3,          /* a CUDA runtime call or kernel launch failed               */
+  WSBM_ERR_RANK_OVERFLOW = -4, /* an interpolative decomposition needed more than its cap   */
+  WSBM_ERR_TIMEOUT = -5,       /* a bounded device wait gave up                             */
+  WSBM_ERR_NOT_FACTORED = -6,  /* solve/farfield before a successful wsbm_factor            */
+  WSBM_ERR_NO_DEVICE = -7      /* no usable sm_103 device                                   */
+};
+
+enum { WSBM_FP64 = 0, WSBM_MIXED = 1 };
+
+/* Curve data, all device pointers to n doubles, caller-owned. */
+typedef struct {
+  int64_t n;
+  const double *x, *y;   /* node positions                    */
+  const double *nx, *ny; /* outward unit normals              */
+  const double *w;       /* quadrature weights                */
+  const double *kappa;   /* signed curvature (circle: 1/R)    */
+} wsbm_geom;
+
+/* Physical and solver parameters.
+ *  k0          exterior wavenumber (> 0)
+ *  refr_index  n = k1/k0 (> 0); with mu0 = mu1 = 1, eps1 = n^2 eps0 (Sec. II, k_j = omega sqrt(eps_j mu_j))
+ *  eps0, eps1  permittivities; eps1 <= 0 selects eps1 = n^2 eps0; eps0 <= 0 selects 1
+ *  leaf        target leaf size in nodes (>= 4); the tree is a perfect binary tree of depth
+ *              L = ceil(log2(n/leaf)) over contiguous node ranges (Sec. III, Fig. tree)
+ *  nproxy      proxy points on each leaf's proxy circle (>= 8; grown on upper levels)
+ *  id_tol      relative tolerance of the interpolative decompositions (0 < id_tol < 1)
+ *  precision   WSBM_FP64, or WSBM_MIXED: proxy blocks evaluated with an FP32 amplitude and an
+ *              FP64-reduced phase; every other entry, the ID and the factor stay FP64
+ *  proxy_ratio proxy radius / box radius (<= 1 selects 1.5)
+ *  max_levels  0: build and factor the whole tree.  m > 0: compress only the m lowest tree
+ *              levels and stop before the dense root (a partial build for measuring the build
+ *              phase on problems whose root system would not fit); solve then fails with
+ *              WSBM_ERR_NOT_FACTORED
+ *  root_cap    largest dense root order accepted (0 selects 40000); a factorization whose
+ *              merged skeleton system would be larger fails with WSBM_ERR_RANK_OVERFLOW
+ */
+typedef struct {
+  double k0, refr_index, eps0, eps1;
+  int32_t leaf, nproxy;
+  double id_tol;
+  int32_t precision;
+  double proxy_ratio;
+  int32_t max_levels, root_cap;
+} wsbm_params;
+
+/* Counters of a handle. */
+typedef struct {
+  int32_t levels;              /* tree depth L                                        */
+  int32_t nboxes_leaf;
+  int64_t entries_generated;   /* complex entries written by the entry kernels         */
+  int64_t pairs_evaluated;     /* node-node and node-proxy pairs evaluated             */
+  double ms_entries;           /* summed device time of the entry kernels             */
+  double ms_id;                /* interpolative decompositions                        */
+  double ms_factor;            /* LU, R D^-1 L, root                                  */
+  double ms_total_factor;      /* wsbm_factor wall time on the stream (events)        */
+  int32_t max_rank;            /* largest skeleton size                               */
+  int32_t root_size;           /* order of the dense root system                      */
+  int32_t rank_per_level[32];  /* largest skeleton size on each level (index = level) */
+  int64_t factor_bytes;        /* device memory held by the factors                   */
+  int64_t entries_proxy;       /* entries written by the proxy-block kernel            */
+  int64_t pairs_proxy;         /* node / proxy-point pairs it evaluated                */
+  double ms_proxy;             /* its summed device time                              */
+  int64_t entries_pairs;       /* entries written by the node-pair kernel              */
+  int64_t pairs_pairs;         /* node pairs it evaluated                              */
+  double ms_pairs;             /* its summed device time                              */
+  int64_t launches;            /* kernels launched by the last wsbm_factor            */
+} wsbm_stats_t;
+
+typedef struct wsbm_hss* wsbm_hss_t;
+
+/* ---------------------------------------------------------------- stateless kernels ---- */
+
+/* Hankel functions H0^(1)(z), H1^(1)(z) at n arguments z > 0 (the kernel of every layer
+ * potential of eq. weakly_bm; G_k = (i/4) H0^(1)(k r)).
+ *   z    device, n doubles
+ *   out  device, 6n doubles: per argument Re H0, Im H0, Re H1, Im H1, Re F1, Im F1 where
+ *        F1(z) = H1(z)/z + 2i/(pi z^2) (pole-free part used by N_k0 - N_k1)
+ *   precision  WSBM_FP64 or WSBM_MIXED (FP32 amplitude, FP64 phase reduction)
+ * Errors: INVALID_ARG (n < 0, NULL with n > 0), CUDA. */
+int wsbm_hankel01(const double* z, int64_t n, double* out, int32_t precision, void* stream);
+
+/* Entries A[rows, cols] of the 2N x 2N Nystrom matrix of eq. (weakly_bm) (block form A_ij of
+ * Sec. III) with the one-point corrected diagonal.
+ *   rows, cols  device int64 unknown indices in [0, 2N), paper order
+ *   out         device complex128, column-major nr x nc (leading dimension nr)
+ * Errors: INVALID_ARG (bad sizes, NULL pointers, parameters out of range), OOM, CUDA.
+ * Indices out of range are not checked on the device; they must lie in [0, 2N). */
+int wsbm_entries_raw(const wsbm_geom* g, const wsbm_params* p, const int64_t* rows, int64_t nr,
+                     const int64_t* cols, int64_t nc, void* out, void* stream);
+
+/* Proxy-circle blocks of the proxy-surface method (Sec. III) for one box, the inputs of its
+ * interpolative decompositions.  The circle has centre (cx, cy), radius rho and P equispaced
+ * points p_m = c + rho (cos 2 pi m/P, sin 2 pi m/P) with outward normals.
+ * Row block (side = 0): rows = the box equations `idx` (paper order), 2P columns: column m is
+ *   the k1 combined-field source (d/dnu - i k1) G_k1 at p_m entering [eq1 ; -alpha d/dn_x],
+ *   column P+m the k0 source entering [0 ; 1 + alpha d/dn_x]; scaled by 2 pi rho / P.
+ *   out: complex128 nidx x 2P, column-major.
+ * Column block (side = 1): 2P rows (the k1 field, then the k0 field, of the box unknowns at
+ *   the proxy points), columns = the box unknowns `idx`.  out: complex128 2P x nidx.
+ * precision WSBM_MIXED evaluates these blocks with an FP32 amplitude.
+ * Errors: INVALID_ARG, OOM, CUDA. */
+int wsbm_proxy_block(const wsbm_geom* g, const wsbm_params* p, int32_t side, const int64_t* idx,
+                     int64_t nidx, double cx, double cy, double rho, int32_t P, void* out,
+                     void* stream);
+
+/* -------------------------------------------------------------------- HSS solver ---- */
+
+/* Create a solver handle for a curve (copies nothing but the pointers' data it needs: the
+ * geometry is copied into library-owned device memory, so the caller may free g afterwards).
+ * The handle uses `stream` for all its work.  Errors: INVALID_ARG (n < 2*leaf... see leaf,
+ * non-finite geometry), OOM, CUDA, NO_DEVICE. */
+int wsbm_create(const wsbm_geom* g, const wsbm_params* p, void* stream, wsbm_hss_t* out);
+
+/* Build and factor the HSS approximation of the WSBM matrix: per tree level, leaf to root,
+ * generate the dense diagonal blocks, the proxy and near-field blocks, compute row and column
+ * interpolative decompositions (column-pivoted QR with relative tolerance id_tol), form the
+ * sibling skeleton blocks and the compressed Martinsson-Rokhlin factors; LU of the dense
+ * root.  Synchronous (returns when the factor is complete).  Errors: OOM, CUDA,
+ * RANK_OVERFLOW. */
+int wsbm_factor(wsbm_hss_t h);
+
+/* Right-hand sides of eq. (weakly_bm) for plane waves exp(i k0 (cos a, sin a).x):
+ * [0 ; -u_in - alpha du_in/dn].  angles: device, nang doubles; rhs: device complex128,
+ * 2N x nang column-major, paper order. */
+int wsbm_rhs_planewave(wsbm_hss_t h, const double* angles, int32_t nang, void* rhs);
+
+/* Solve A [u; q] = rhs with the factors.  rhs: device complex128 2N x nrhs (paper order);
+ * u, q: device complex128 N x nrhs each.  Errors: NOT_FACTORED, OOM, CUDA. */
+int wsbm_solve(wsbm_hss_t h, const void* rhs, int32_t nrhs, void* u, void* q);
+
+/* Far-field pattern of the scattered field at nang observation angles:
+ * u_inf(a) = e^{i pi/4}/sqrt(8 pi k0) sum_j w_j [-i k0 (xh.n_j) u_j - eps0 q_j] e^{-i k0 xh.x_j}.
+ * u, q: device complex128 N x nrhs; angles: device doubles; out: device complex128
+ * nang x nrhs. */
+int wsbm_farfield(wsbm_hss_t h, const void* u, const void* q, int32_t nrhs, const double* angles,
+                  int32_t nang, void* out);
+
+/* Entries of the handle's matrix (same as wsbm_entries_raw with the handle's geometry). */
+int wsbm_entries(wsbm_hss_t h, const int64_t* rows, int64_t nr, const int64_t* cols, int64_t nc,
+                 void* out);
+
+/* Proxy circle the handle uses for box `box` (0-based, left to right) on tree level `level`
+ * (0 = root, L = leaves), and the node range [first, last) of that box.
+ * out4 (host): cx, cy, R, rho; range2 (host): first, last. */
+int wsbm_box_info(wsbm_hss_t h, int32_t level, int32_t box, double* out4, int64_t* range2);
+
+/* Counters and timings (host struct). */
+int wsbm_stats(wsbm_hss_t h, wsbm_stats_t* s);
+
+/* Release every device buffer of the handle. */
+void wsbm_destroy(wsbm_hss_t h);
+
+/* Static name of an error code. */
+const char* wsbm_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* WSBM_HSS_H */

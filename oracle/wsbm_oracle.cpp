@@ -226,6 +226,7 @@ int orc_hankel01(const double* z, int64_t n, double* out) {
 
 // F1(z) = H1(z)/z + 2i/(pi z^2); out[2t], out[2t+1] = Re, Im.
 int orc_f1(const double* z, int64_t n, double* out) {
+#pragma omp parallel for schedule(dynamic, 64)
   for (int64_t t = 0; t < n; ++t) {
     Hank h = hankel_eval(z[t]);
     out[2 * t] = h.f1.real();

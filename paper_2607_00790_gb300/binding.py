@@ -1,0 +1,222 @@
+"""Thin ctypes binding of ``libwsbm_hss.so`` (declared in include/wsbm_hss.h).
+
+Argument marshalling only: every computation runs in the library's CUDA kernels.  PyTorch
+supplies device memory and the stream (the current torch stream of the tensors' device).
+The binding refuses to run when the library is missing or a tensor is not on a CUDA device.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+from .build import LIB as LIB_PATH
+
+_LIB = None
+
+WSBM_OK = 0
+WSBM_FP64 = 0
+WSBM_MIXED = 1
+ERRORS = {0: "ok", -1: "invalid argument", -2: "out of memory", -3: "CUDA error",
+          -4: "rank overflow", -5: "timeout", -6: "not factored", -7: "no device"}
+
+
+class WsbmError(RuntimeError):
+    def __init__(self, code, where):
+        super().__init__(f"{where}: {ERRORS.get(code, code)} ({code})")
+        self.code = code
+
+
+class Geom(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("x", ctypes.c_void_p), ("y", ctypes.c_void_p),
+                ("nx", ctypes.c_void_p), ("ny", ctypes.c_void_p), ("w", ctypes.c_void_p),
+                ("kappa", ctypes.c_void_p)]
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("k0", ctypes.c_double), ("refr_index", ctypes.c_double),
+                ("eps0", ctypes.c_double), ("eps1", ctypes.c_double),
+                ("leaf", ctypes.c_int32), ("nproxy", ctypes.c_int32),
+                ("id_tol", ctypes.c_double), ("precision", ctypes.c_int32),
+                ("proxy_ratio", ctypes.c_double), ("max_levels", ctypes.c_int32),
+                ("root_cap", ctypes.c_int32)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("levels", ctypes.c_int32), ("nboxes_leaf", ctypes.c_int32),
+                ("entries_generated", ctypes.c_int64), ("pairs_evaluated", ctypes.c_int64),
+                ("ms_entries", ctypes.c_double), ("ms_id", ctypes.c_double),
+                ("ms_factor", ctypes.c_double), ("ms_total_factor", ctypes.c_double),
+                ("max_rank", ctypes.c_int32), ("root_size", ctypes.c_int32),
+                ("rank_per_level", ctypes.c_int32 * 32), ("factor_bytes", ctypes.c_int64),
+                ("entries_proxy", ctypes.c_int64), ("pairs_proxy", ctypes.c_int64),
+                ("ms_proxy", ctypes.c_double), ("entries_pairs", ctypes.c_int64),
+                ("pairs_pairs", ctypes.c_int64), ("ms_pairs", ctypes.c_double),
+                ("launches", ctypes.c_int64)]
+
+    def as_dict(self):
+        d = {k: getattr(self, k) for k, _ in self._fields_ if k != "rank_per_level"}
+        d["rank_per_level"] = list(self.rank_per_level)[: self.levels + 1]
+        return d
+
+
+def lib():
+    global _LIB
+    if _LIB is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: run paper_2607_00790_gb300.build.build() first")
+        L = ctypes.CDLL(LIB_PATH)
+        vp, i64, i32, d = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_double
+        L.wsbm_hankel01.argtypes = [vp, i64, vp, i32, vp]
+        L.wsbm_entries_raw.argtypes = [ctypes.POINTER(Geom), ctypes.POINTER(Params), vp, i64, vp,
+                                       i64, vp, vp]
+        L.wsbm_proxy_block.argtypes = [ctypes.POINTER(Geom), ctypes.POINTER(Params), i32, vp, i64,
+                                       d, d, d, i32, vp, vp]
+        L.wsbm_create.argtypes = [ctypes.POINTER(Geom), ctypes.POINTER(Params), vp,
+                                  ctypes.POINTER(vp)]
+        L.wsbm_factor.argtypes = [vp]
+        L.wsbm_rhs_planewave.argtypes = [vp, vp, i32, vp]
+        L.wsbm_solve.argtypes = [vp, vp, i32, vp, vp]
+        L.wsbm_farfield.argtypes = [vp, vp, vp, i32, vp, i32, vp]
+        L.wsbm_entries.argtypes = [vp, vp, i64, vp, i64, vp]
+        L.wsbm_box_info.argtypes = [vp, i32, i32, ctypes.POINTER(d), ctypes.POINTER(i64)]
+        L.wsbm_stats.argtypes = [vp, ctypes.POINTER(Stats)]
+        L.wsbm_destroy.argtypes = [vp]
+        L.wsbm_destroy.restype = None
+        L.wsbm_strerror.argtypes = [ctypes.c_int]
+        L.wsbm_strerror.restype = ctypes.c_char_p
+        for f in ("wsbm_hankel01", "wsbm_entries_raw", "wsbm_proxy_block", "wsbm_create",
+                  "wsbm_factor", "wsbm_rhs_planewave", "wsbm_solve", "wsbm_farfield",
+                  "wsbm_entries", "wsbm_box_info", "wsbm_stats"):
+            getattr(L, f).restype = ctypes.c_int
+        _LIB = L
+    return _LIB
+
+
+def _check(rc, where):
+    if rc != WSBM_OK:
+        raise WsbmError(rc, where)
+
+
+def _dev(t, dtype):
+    if not isinstance(t, torch.Tensor) or t.device.type != "cuda":
+        raise ValueError("expected a CUDA tensor")
+    if t.dtype != dtype or not t.is_contiguous():
+        raise ValueError(f"expected a contiguous {dtype} tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(device=None):
+    return ctypes.c_void_p(torch.cuda.current_stream(device).cuda_stream)
+
+
+def make_geom(curve, device="cuda"):
+    """Device copies of a curve's arrays (x, y, nx, ny, w, kappa) and the ABI struct."""
+    t = {k: torch.as_tensor(curve[k], dtype=torch.float64).to(device).contiguous()
+         for k in ("x", "y", "nx", "ny", "w", "kappa")}
+    g = Geom(t["x"].numel(), *[t[k].data_ptr() for k in ("x", "y", "nx", "ny", "w", "kappa")])
+    return g, t
+
+
+def make_params(k0, n, eps0=1.0, eps1=0.0, leaf=64, nproxy=64, id_tol=1e-10,
+                precision=WSBM_FP64, proxy_ratio=1.5, max_levels=0, root_cap=0):
+    return Params(k0, n, eps0, eps1, leaf, nproxy, id_tol, precision, proxy_ratio, max_levels,
+                  root_cap)
+
+
+# ---------------------------------------------------------------- stateless calls ----
+def wsbm_hankel01(z, precision=WSBM_FP64):
+    out = torch.empty((z.numel(), 6), dtype=torch.float64, device=z.device)
+    _check(lib().wsbm_hankel01(_dev(z, torch.float64), z.numel(), _dev(out, torch.float64),
+                               precision, _stream(z.device)), "wsbm_hankel01")
+    return out
+
+
+def wsbm_entries_raw(geom, params, rows, cols):
+    dev = rows.device
+    out = torch.empty((cols.numel(), rows.numel()), dtype=torch.complex128, device=dev)
+    _check(lib().wsbm_entries_raw(ctypes.byref(geom), ctypes.byref(params), _dev(rows, torch.int64),
+                                  rows.numel(), _dev(cols, torch.int64), cols.numel(),
+                                  _dev(out, torch.complex128), _stream(dev)), "wsbm_entries_raw")
+    return out.T
+
+
+def wsbm_proxy_block(geom, params, side, idx, circle, P):
+    dev = idx.device
+    cx, cy, rho = circle
+    shape = (2 * P, idx.numel()) if side == 0 else (idx.numel(), 2 * P)
+    out = torch.empty(shape, dtype=torch.complex128, device=dev)
+    _check(lib().wsbm_proxy_block(ctypes.byref(geom), ctypes.byref(params), side,
+                                  _dev(idx, torch.int64), idx.numel(), cx, cy, rho, P,
+                                  _dev(out, torch.complex128), _stream(dev)), "wsbm_proxy_block")
+    return out.T
+
+
+# --------------------------------------------------------------------- HSS handle ----
+class Solver:
+    """wsbm_create / wsbm_factor / wsbm_solve / wsbm_farfield on one handle."""
+
+    def __init__(self, geom, params, device="cuda"):
+        self.device = torch.device(device)
+        self.n = geom.n
+        h = ctypes.c_void_p()
+        _check(lib().wsbm_create(ctypes.byref(geom), ctypes.byref(params), _stream(self.device),
+                                 ctypes.byref(h)), "wsbm_create")
+        self.h = h
+
+    def factor(self):
+        _check(lib().wsbm_factor(self.h), "wsbm_factor")
+
+    def rhs_planewave(self, angles):
+        out = torch.empty((angles.numel(), 2 * self.n), dtype=torch.complex128, device=self.device)
+        _check(lib().wsbm_rhs_planewave(self.h, _dev(angles, torch.float64), angles.numel(),
+                                        _dev(out, torch.complex128)), "wsbm_rhs_planewave")
+        return out.T
+
+    def solve(self, rhs):
+        rhs_c = rhs.T.contiguous() if not rhs.T.is_contiguous() else rhs.T
+        nrhs = rhs.shape[1]
+        u = torch.empty((nrhs, self.n), dtype=torch.complex128, device=self.device)
+        q = torch.empty((nrhs, self.n), dtype=torch.complex128, device=self.device)
+        _check(lib().wsbm_solve(self.h, _dev(rhs_c, torch.complex128), nrhs,
+                                _dev(u, torch.complex128), _dev(q, torch.complex128)), "wsbm_solve")
+        return u.T, q.T
+
+    def farfield(self, u, q, angles):
+        uc, qc = u.T.contiguous(), q.T.contiguous()
+        nrhs = u.shape[1]
+        out = torch.empty((nrhs, angles.numel()), dtype=torch.complex128, device=self.device)
+        _check(lib().wsbm_farfield(self.h, _dev(uc, torch.complex128), _dev(qc, torch.complex128),
+                                   nrhs, _dev(angles, torch.float64), angles.numel(),
+                                   _dev(out, torch.complex128)), "wsbm_farfield")
+        return out.T
+
+    def entries(self, rows, cols):
+        out = torch.empty((cols.numel(), rows.numel()), dtype=torch.complex128, device=self.device)
+        _check(lib().wsbm_entries(self.h, _dev(rows, torch.int64), rows.numel(),
+                                  _dev(cols, torch.int64), cols.numel(),
+                                  _dev(out, torch.complex128)), "wsbm_entries")
+        return out.T
+
+    def box_info(self, level, box):
+        out = (ctypes.c_double * 4)()
+        rng = (ctypes.c_int64 * 2)()
+        _check(lib().wsbm_box_info(self.h, level, box, out, rng), "wsbm_box_info")
+        return tuple(out), tuple(rng)
+
+    def stats(self):
+        s = Stats()
+        _check(lib().wsbm_stats(self.h, ctypes.byref(s)), "wsbm_stats")
+        return s.as_dict()
+
+    def close(self):
+        if self.h:
+            lib().wsbm_destroy(self.h)
+            self.h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

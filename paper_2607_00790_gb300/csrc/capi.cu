@@ -1,0 +1,174 @@
+// C ABI: argument checking, scratch management and launches of the stateless calls.
+#include <math.h>
+#include <string.h>
+
+#include <atomic>
+
+#include "wsbm_internal.h"
+
+static std::atomic<int64_t> g_launches{0};
+void wsbm_count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+int64_t wsbm_launch_count() { return g_launches.load(std::memory_order_relaxed); }
+
+extern "C" const char* wsbm_strerror(int code) {
+  switch (code) {
+    case WSBM_OK: return "ok";
+    case WSBM_ERR_INVALID_ARG: return "invalid argument";
+    case WSBM_ERR_OOM: return "out of memory";
+    case WSBM_ERR_CUDA: return "CUDA error";
+    case WSBM_ERR_RANK_OVERFLOW: return "interpolative decomposition rank above its cap";
+    case WSBM_ERR_TIMEOUT: return "bounded device wait timed out";
+    case WSBM_ERR_NOT_FACTORED: return "handle not factored";
+    case WSBM_ERR_NO_DEVICE: return "no usable CUDA device";
+    default: return "unknown error";
+  }
+}
+
+// Physics of eq. (weakly_bm) from the parameters: k1 = n k0 (mu0 = mu1 = 1), eps1 defaults to
+// n^2 eps0, eps0 to 1.
+int wsbm_phys_from_params(const wsbm_params* p, Phys* ph) {
+  if (!p || !ph) return WSBM_ERR_INVALID_ARG;
+  if (!(p->k0 > 0.0) || !(p->refr_index > 0.0) || !isfinite(p->k0) || !isfinite(p->refr_index))
+    return WSBM_ERR_INVALID_ARG;
+  double eps0 = p->eps0 > 0.0 ? p->eps0 : 1.0;
+  double eps1 = p->eps1 > 0.0 ? p->eps1 : p->refr_index * p->refr_index * eps0;
+  if (!isfinite(eps0) || !isfinite(eps1)) return WSBM_ERR_INVALID_ARG;
+  ph->k0 = p->k0;
+  ph->k1 = p->refr_index * p->k0;
+  ph->eps0 = eps0;
+  ph->eps1 = eps1;
+  return WSBM_OK;
+}
+
+int wsbm_geom_check(const wsbm_geom* g) {
+  if (!g || g->n < 2 || g->n > (int64_t)1 << 30) return WSBM_ERR_INVALID_ARG;
+  if (!g->x || !g->y || !g->nx || !g->ny || !g->w || !g->kappa) return WSBM_ERR_INVALID_ARG;
+  return WSBM_OK;
+}
+
+DevGeom wsbm_devgeom(const wsbm_geom* g) {
+  DevGeom d;
+  d.x = g->x;
+  d.y = g->y;
+  d.nx = g->nx;
+  d.ny = g->ny;
+  d.w = g->w;
+  d.kappa = g->kappa;
+  d.n = g->n;
+  return d;
+}
+
+#define CK(call)                                  \
+  do {                                            \
+    if ((call) != cudaSuccess) {                  \
+      rc = WSBM_ERR_CUDA;                         \
+      goto done;                                  \
+    }                                             \
+  } while (0)
+
+extern "C" int wsbm_hankel01(const double* z, int64_t n, double* out, int32_t precision,
+                             void* stream) {
+  if (n < 0 || (n > 0 && (!z || !out))) return WSBM_ERR_INVALID_ARG;
+  if (precision != WSBM_FP64 && precision != WSBM_MIXED) return WSBM_ERR_INVALID_ARG;
+  return wsbm_launch_hankel(z, n, out, precision == WSBM_MIXED, (cudaStream_t)stream);
+}
+
+extern "C" int wsbm_entries_raw(const wsbm_geom* g, const wsbm_params* p, const int64_t* rows,
+                                int64_t nr, const int64_t* cols, int64_t nc, void* out,
+                                void* stream) {
+  int rc = wsbm_geom_check(g);
+  if (rc) return rc;
+  Phys ph;
+  if ((rc = wsbm_phys_from_params(p, &ph))) return rc;
+  if (nr < 0 || nc < 0 || nr > INT32_MAX / 2 || nc > INT32_MAX / 2) return WSBM_ERR_INVALID_ARG;
+  if (nr == 0 || nc == 0) return WSBM_OK;
+  if (!rows || !cols || !out) return WSBM_ERR_INVALID_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  int32_t* buf = nullptr;
+  PairTask* dtask = nullptr;
+  size_t nint = (size_t)3 * nr + 3 * nc;
+  if (cudaMallocAsync((void**)&buf, nint * sizeof(int32_t), st) != cudaSuccess) return WSBM_ERR_OOM;
+  if (cudaMallocAsync((void**)&dtask, sizeof(PairTask), st) != cudaSuccess) {
+    cudaFreeAsync(buf, st);
+    return WSBM_ERR_OOM;
+  }
+  {
+    int32_t* rnode = buf;
+    int32_t* rpos = rnode + nr;
+    int32_t* cnode = rpos + 2 * nr;
+    int32_t* cpos = cnode + nc;
+    PairTask t;
+    memset(&t, 0, sizeof(t));
+    t.rnode = rnode;
+    t.rpos = rpos;
+    t.cnode = cnode;
+    t.cpos = cpos;
+    t.out = (double2*)out;
+    t.ld = nr;
+    t.nr = (int32_t)nr;
+    t.nc = (int32_t)nc;
+    t.trans = 0;
+    t.tile0 = 0;
+    DevGeom dg = wsbm_devgeom(g);
+    if ((rc = wsbm_launch_unknowns_to_slots(rows, nr, g->n, rnode, rpos, st))) goto done;
+    if ((rc = wsbm_launch_unknowns_to_slots(cols, nc, g->n, cnode, cpos, st))) goto done;
+    CK(cudaMemcpyAsync(dtask, &t, sizeof(t), cudaMemcpyHostToDevice, st));
+    rc = wsbm_launch_pairs(dg, ph, dtask, 1, wsbm_pair_tiles(t.nr, t.nc, 0), st);
+    // the task struct lives on this stack frame: wait for the copy before returning
+    CK(cudaStreamSynchronize(st));
+  }
+done:
+  cudaFreeAsync(dtask, st);
+  cudaFreeAsync(buf, st);
+  return rc;
+}
+
+extern "C" int wsbm_proxy_block(const wsbm_geom* g, const wsbm_params* p, int32_t side,
+                                const int64_t* idx, int64_t nidx, double cx, double cy, double rho,
+                                int32_t P, void* out, void* stream) {
+  int rc = wsbm_geom_check(g);
+  if (rc) return rc;
+  Phys ph;
+  if ((rc = wsbm_phys_from_params(p, &ph))) return rc;
+  if ((side != 0 && side != 1) || P < 1 || nidx < 0 || nidx > INT32_MAX / 2) return WSBM_ERR_INVALID_ARG;
+  if (!(rho > 0.0) || !isfinite(cx) || !isfinite(cy) || !isfinite(rho)) return WSBM_ERR_INVALID_ARG;
+  if (p->precision != WSBM_FP64 && p->precision != WSBM_MIXED) return WSBM_ERR_INVALID_ARG;
+  if (nidx == 0) return WSBM_OK;
+  if (!idx || !out) return WSBM_ERR_INVALID_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  int32_t* buf = nullptr;
+  ProxyTask* dtask = nullptr;
+  if (cudaMallocAsync((void**)&buf, (size_t)3 * nidx * sizeof(int32_t), st) != cudaSuccess)
+    return WSBM_ERR_OOM;
+  if (cudaMallocAsync((void**)&dtask, sizeof(ProxyTask), st) != cudaSuccess) {
+    cudaFreeAsync(buf, st);
+    return WSBM_ERR_OOM;
+  }
+  {
+    ProxyTask t;
+    memset(&t, 0, sizeof(t));
+    t.node = buf;
+    t.pos = buf + nidx;
+    t.out = (double2*)out;
+    t.cx = cx;
+    t.cy = cy;
+    t.rho = rho;
+    t.nn = (int32_t)nidx;
+    t.P = P;
+    t.side = side;
+    t.tr = side == 0 ? 1 : 0;  // row block: box equations are the rows of the output
+    t.ld = side == 0 ? nidx : 2 * (int64_t)P;
+    t.off = 0;
+    t.tile0 = 0;
+    DevGeom dg = wsbm_devgeom(g);
+    if ((rc = wsbm_launch_unknowns_to_slots(idx, nidx, g->n, buf, buf + nidx, st))) goto done;
+    CK(cudaMemcpyAsync(dtask, &t, sizeof(t), cudaMemcpyHostToDevice, st));
+    rc = wsbm_launch_proxy(dg, ph, dtask, 1, wsbm_proxy_tiles(t.nn, P), p->precision == WSBM_MIXED,
+                           st);
+    CK(cudaStreamSynchronize(st));
+  }
+done:
+  cudaFreeAsync(dtask, st);
+  cudaFreeAsync(buf, st);
+  return rc;
+}

@@ -1,0 +1,521 @@
+// Batched dense complex128 linear algebra for the HSS factor (Martinsson-Rokhlin solver,
+// Sec. III): blocked LU with partial pivoting, blocked triangular solves, complex GEMM and a
+// column-pivoted Householder QR for the interpolative decompositions.
+//
+// Every routine works on a batch of column-major matrices of different sizes described by
+// device arrays.  Blocked algorithms step through panels of WSBM_NB columns on the host; each
+// step launches one kernel over the whole batch (matrices that are already finished skip).
+// The O(n^3) work is in the GEMM kernel, which tiles every matrix of the batch over many CTAs.
+#include <math.h>
+
+#include "dense.h"
+
+#define GT 32  // GEMM tile (GT x GT outputs per CTA)
+#define GK 16  // GEMM k-chunk
+
+__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
+  return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ double2 cfma(double2 a, double2 b, double2 c) {  // a*b + c
+  return make_double2(fma(a.x, b.x, fma(-a.y, b.y, c.x)), fma(a.x, b.y, fma(a.y, b.x, c.y)));
+}
+__device__ __forceinline__ double2 cfms(double2 a, double2 b, double2 c) {  // c - a*b
+  return make_double2(fma(-a.x, b.x, fma(a.y, b.y, c.x)), fma(-a.x, b.y, fma(-a.y, b.x, c.y)));
+}
+__device__ __forceinline__ double2 cdiv(double2 a, double2 b) {
+  double s = 1.0 / (b.x * b.x + b.y * b.y);
+  return make_double2((a.x * b.x + a.y * b.y) * s, (a.y * b.x - a.x * b.y) * s);
+}
+__device__ __forceinline__ double cabs2(double2 a) { return a.x * a.x + a.y * a.y; }
+
+// --------------------------------------------------------------------------- GEMM ----
+// C[m x n] = alpha * A[m x k] * B[k x n] + beta * C, one GT x GT tile of C.
+__device__ void gemm_tile(int m, int n, int k, const double2* __restrict__ A, int64_t lda,
+                          const double2* __restrict__ B, int64_t ldb, double2* C, int64_t ldc,
+                          double2 alpha, double2 beta, int tm, int tn) {
+  __shared__ double2 sA[GK][GT + 1];
+  __shared__ double2 sB[GK][GT + 1];
+  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;  // 256 threads: 16 x 16, 2x2 each
+  const int i0 = tm * GT, j0 = tn * GT;
+  double2 acc[2][2];
+#pragma unroll
+  for (int a = 0; a < 2; ++a)
+#pragma unroll
+    for (int b = 0; b < 2; ++b) acc[a][b] = make_double2(0.0, 0.0);
+  for (int kk = 0; kk < k; kk += GK) {
+    __syncthreads();
+    for (int t = threadIdx.x; t < GK * GT; t += blockDim.x) {
+      int r = t % GT, c = t / GT;  // A: row r of the tile, k index c
+      int gi = i0 + r, gk = kk + c;
+      sA[c][r] = (gi < m && gk < k) ? A[gi + (int64_t)gk * lda] : make_double2(0.0, 0.0);
+      int br = t % GK, bc = t / GK;  // B: k index br, column bc
+      int gk2 = kk + br, gj = j0 + bc;
+      sB[br][bc] = (gk2 < k && gj < n) ? B[gk2 + (int64_t)gj * ldb] : make_double2(0.0, 0.0);
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int c = 0; c < GK; ++c) {
+      double2 a0 = sA[c][tx], a1 = sA[c][tx + 16];
+      double2 b0 = sB[c][ty], b1 = sB[c][ty + 16];
+      acc[0][0] = cfma(a0, b0, acc[0][0]);
+      acc[1][0] = cfma(a1, b0, acc[1][0]);
+      acc[0][1] = cfma(a0, b1, acc[0][1]);
+      acc[1][1] = cfma(a1, b1, acc[1][1]);
+    }
+  }
+  const bool beta0 = beta.x == 0.0 && beta.y == 0.0;
+#pragma unroll
+  for (int a = 0; a < 2; ++a)
+#pragma unroll
+    for (int b = 0; b < 2; ++b) {
+      int gi = i0 + tx + 16 * a, gj = j0 + ty + 16 * b;
+      if (gi < m && gj < n) {
+        double2* p = C + gi + (int64_t)gj * ldc;
+        double2 v = cmul(alpha, acc[a][b]);
+        *p = beta0 ? v : cfma(beta, *p, v);
+      }
+    }
+}
+
+__global__ void __launch_bounds__(256) k_gemm(const GemmDesc* __restrict__ d, int nbatch) {
+  const GemmDesc g = d[blockIdx.y];
+  int ntm = (g.m + GT - 1) / GT, ntn = (g.n + GT - 1) / GT;
+  for (int t = blockIdx.x; t < ntm * ntn; t += gridDim.x)
+    gemm_tile(g.m, g.n, g.k, g.A, g.lda, g.B, g.ldb, g.C, g.ldc, g.alpha, g.beta, t % ntm, t / ntm);
+}
+
+// LU trailing update at panel j0 (width jb): A22 -= A21 * A12.
+__global__ void __launch_bounds__(256) k_lu_update(const LuDesc* __restrict__ d, int j0, int jb) {
+  const LuDesc q = d[blockIdx.y];
+  int e = j0 + jb;
+  if (e >= q.n) return;
+  int m = q.n - e;
+  int nt = (m + GT - 1) / GT;
+  const double2 one = make_double2(1.0, 0.0), mone = make_double2(-1.0, 0.0);
+  int kb = min(jb, q.n - j0);
+  for (int t = blockIdx.x; t < nt * nt; t += gridDim.x)
+    gemm_tile(m, m, kb, q.A + e + (int64_t)j0 * q.lda, q.lda, q.A + j0 + (int64_t)e * q.lda, q.lda,
+              q.A + e + (int64_t)e * q.lda, q.lda, mone, one, t % nt, t / nt);
+}
+
+// ------------------------------------------------------------------- LU panel ----
+// Factor columns [j0, j0+jb) of rows [j0, n) in place with partial pivoting; row swaps are
+// applied inside the panel only (k_laswp applies them elsewhere).  One CTA per matrix.
+__global__ void __launch_bounds__(256) k_lu_panel(const LuDesc* __restrict__ d, int j0, int jb,
+                                                  int* __restrict__ info) {
+  const LuDesc q = d[blockIdx.x];
+  if (j0 >= q.n) return;
+  const int n = q.n;
+  const int je = min(j0 + jb, n);
+  double2* A = q.A;
+  const int64_t lda = q.lda;
+  __shared__ double sval[256];
+  __shared__ int sidx[256];
+  __shared__ int spiv;
+  for (int j = j0; j < je; ++j) {
+    // pivot search over rows j..n-1 of column j
+    double best = -1.0;
+    int bi = j;
+    for (int i = j + threadIdx.x; i < n; i += blockDim.x) {
+      double v = cabs2(A[i + (int64_t)j * lda]);
+      if (v > best) {
+        best = v;
+        bi = i;
+      }
+    }
+    sval[threadIdx.x] = best;
+    sidx[threadIdx.x] = bi;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+      if (threadIdx.x < s) {
+        double o = sval[threadIdx.x + s];
+        int oi = sidx[threadIdx.x + s];
+        if (o > sval[threadIdx.x] || (o == sval[threadIdx.x] && oi < sidx[threadIdx.x])) {
+          sval[threadIdx.x] = o;
+          sidx[threadIdx.x] = oi;
+        }
+      }
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+      spiv = sidx[0];
+      q.piv[j] = sidx[0];
+      if (sval[0] == 0.0 && info) info[blockIdx.x] = j + 1;  // exactly singular
+    }
+    __syncthreads();
+    const int p = spiv;
+    if (p != j) {
+      for (int c = j0 + threadIdx.x; c < je; c += blockDim.x) {
+        double2 t = A[j + (int64_t)c * lda];
+        A[j + (int64_t)c * lda] = A[p + (int64_t)c * lda];
+        A[p + (int64_t)c * lda] = t;
+      }
+    }
+    __syncthreads();
+    double2 piv = A[j + (int64_t)j * lda];
+    double2 inv = (piv.x == 0.0 && piv.y == 0.0) ? make_double2(0.0, 0.0)
+                                                   : cdiv(make_double2(1.0, 0.0), piv);
+    for (int i = j + 1 + threadIdx.x; i < n; i += blockDim.x)
+      A[i + (int64_t)j * lda] = cmul(A[i + (int64_t)j * lda], inv);
+    __syncthreads();
+    // rank-1 update of the remaining panel columns
+    for (int c = j + 1; c < je; ++c) {
+      double2 u = A[j + (int64_t)c * lda];
+      for (int i = j + 1 + threadIdx.x; i < n; i += blockDim.x)
+        A[i + (int64_t)c * lda] = cfms(A[i + (int64_t)j * lda], u, A[i + (int64_t)c * lda]);
+    }
+    __syncthreads();
+  }
+}
+
+// Apply the row interchanges of panel [j0, j0+jb) to the columns outside the panel.
+__global__ void k_laswp(const LuDesc* __restrict__ d, int j0, int jb) {
+  const LuDesc q = d[blockIdx.y];
+  if (j0 >= q.n) return;
+  const int je = min(j0 + jb, q.n);
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < q.n; c += gridDim.x * blockDim.x) {
+    if (c >= j0 && c < je) continue;
+    double2* col = q.A + (int64_t)c * q.lda;
+    for (int j = j0; j < je; ++j) {
+      int p = q.piv[j];
+      if (p != j) {
+        double2 t = col[j];
+        col[j] = col[p];
+        col[p] = t;
+      }
+    }
+  }
+}
+
+// A12 = L11^-1 A12 for the block row of panel [j0, j0+jb) (unit lower L11), columns >= j0+jb.
+__global__ void k_lu_trsm_row(const LuDesc* __restrict__ d, int j0, int jb) {
+  const LuDesc q = d[blockIdx.y];
+  const int je = min(j0 + jb, q.n);
+  if (je >= q.n) return;
+  for (int c = je + blockIdx.x * blockDim.x + threadIdx.x; c < q.n; c += gridDim.x * blockDim.x) {
+    double2* col = q.A + (int64_t)c * q.lda;
+    for (int i = j0 + 1; i < je; ++i) {
+      double2 s = col[i];
+      for (int t = j0; t < i; ++t) s = cfms(q.A[i + (int64_t)t * q.lda], col[t], s);
+      col[i] = s;
+    }
+  }
+}
+
+// ------------------------------------------------------------- triangular solves ----
+// B <- op(T)^-1 B for a diagonal block [j0, j0+jb) of T (lower unit or upper non-unit),
+// RHS columns in parallel.
+__global__ void k_trsm_diag(const TrsmDesc* __restrict__ d, int j0, int jb, int lower) {
+  const TrsmDesc q = d[blockIdx.y];
+  if (j0 >= q.n) return;
+  const int je = min(j0 + jb, q.n);
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < q.nrhs; c += gridDim.x * blockDim.x) {
+    double2* col = q.B + (int64_t)c * q.ldb;
+    if (lower) {
+      for (int i = j0 + 1; i < je; ++i) {
+        double2 s = col[i];
+        for (int t = j0; t < i; ++t) s = cfms(q.T[i + (int64_t)t * q.ldt], col[t], s);
+        col[i] = s;
+      }
+    } else {
+      for (int i = je - 1; i >= j0; --i) {
+        double2 s = col[i];
+        for (int t = i + 1; t < je; ++t) s = cfms(q.T[i + (int64_t)t * q.ldt], col[t], s);
+        col[i] = cdiv(s, q.T[i + (int64_t)i * q.ldt]);
+      }
+    }
+  }
+}
+
+// Update after a solved diagonal block: lower: B[je:n] -= T[je:n, j0:je] B[j0:je];
+// upper: B[0:j0] -= T[0:j0, j0:je] B[j0:je].
+__global__ void __launch_bounds__(256) k_trsm_update(const TrsmDesc* __restrict__ d, int j0, int jb,
+                                                     int lower) {
+  const TrsmDesc q = d[blockIdx.y];
+  if (j0 >= q.n) return;
+  const int je = min(j0 + jb, q.n);
+  int m = lower ? q.n - je : j0;
+  if (m <= 0 || q.nrhs <= 0) return;
+  int r0 = lower ? je : 0;
+  int ntm = (m + GT - 1) / GT, ntn = (q.nrhs + GT - 1) / GT;
+  const double2 one = make_double2(1.0, 0.0), mone = make_double2(-1.0, 0.0);
+  for (int t = blockIdx.x; t < ntm * ntn; t += gridDim.x)
+    gemm_tile(m, q.nrhs, je - j0, q.T + r0 + (int64_t)j0 * q.ldt, q.ldt, q.B + j0, q.ldb, q.B + r0,
+              q.ldb, mone, one, t % ntm, t / ntm);
+}
+
+// Apply the LU row interchanges to B (forward order).
+__global__ void k_apply_piv(const TrsmDesc* __restrict__ d) {
+  const TrsmDesc q = d[blockIdx.y];
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < q.nrhs; c += gridDim.x * blockDim.x) {
+    double2* col = q.B + (int64_t)c * q.ldb;
+    for (int j = 0; j < q.n; ++j) {
+      int p = q.piv[j];
+      if (p != j) {
+        double2 t = col[j];
+        col[j] = col[p];
+        col[p] = t;
+      }
+    }
+  }
+}
+
+// ------------------------------------------------- column-pivoted Householder QR ----
+// One CTA per matrix M (m x n, in place).  Step j: pivot the column of largest remaining norm
+// to position j, reflect rows j..m-1 with P = I - tau u u^H (Hermitian, tau real,
+// u = x - beta e1, beta = -(x0/|x0|)|x|), so P x = beta e1.  Mode 0 stops at the first j with
+// |beta_j| <= tol |beta_0| (rank k = j); mode 1 runs until step kt.  The state (reflected
+// matrix, exact remaining column norms, permutation) lets a later call resume.  On return
+// the R factor sits in rows 0..k-1 (diagonal included; below it, reflector data).
+__global__ void __launch_bounds__(256) k_cpqr(const QrDesc* __restrict__ d, int mode) {
+  const QrDesc q = d[blockIdx.x];
+  const int m = q.m, n = q.n;
+  double2* M = q.A;
+  const int64_t ld = q.lda;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  __shared__ double sval[256];
+  __shared__ int sidx[256];
+  __shared__ double s_tau;
+  __shared__ double2 s_beta;
+  __shared__ int s_stop;
+  const int kmax = min(m, n);
+  int j = q.state[0];  // resume point
+  if (j == 0 && threadIdx.x == 0) q.state[1] = 0;
+  // initial exact norms
+  if (j == 0) {
+    for (int c = warp; c < n; c += nw) {
+      double s = 0.0;
+      for (int i = lane; i < m; i += 32) s += cabs2(M[i + (int64_t)c * ld]);
+      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+      if (lane == 0) q.norm2[c] = s;
+    }
+    for (int c = threadIdx.x; c < n; c += blockDim.x) q.perm[c] = c;
+  }
+  __syncthreads();
+  const int kt = mode == 1 ? min(q.kt, kmax) : kmax;
+  for (; j < kt; ++j) {
+    // pivot: largest remaining norm (lowest index on ties)
+    double best = -1.0;
+    int bi = j;
+    for (int c = j + threadIdx.x; c < n; c += blockDim.x) {
+      double v = q.norm2[c];
+      if (v > best) {
+        best = v;
+        bi = c;
+      }
+    }
+    sval[threadIdx.x] = best;
+    sidx[threadIdx.x] = bi;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+      if (threadIdx.x < s) {
+        double o = sval[threadIdx.x + s];
+        int oi = sidx[threadIdx.x + s];
+        if (o > sval[threadIdx.x] || (o == sval[threadIdx.x] && oi < sidx[threadIdx.x])) {
+          sval[threadIdx.x] = o;
+          sidx[threadIdx.x] = oi;
+        }
+      }
+      __syncthreads();
+    }
+    const int p = sidx[0];
+    const double nrm = sqrt(fmax(sval[0], 0.0));
+    if (threadIdx.x == 0) {
+      int stop = 0;
+      if (j == 0) q.rdiag0[0] = nrm;
+      if (mode == 0 && (nrm <= q.tol * q.rdiag0[0] || nrm == 0.0)) stop = 1;
+      s_stop = stop;
+    }
+    __syncthreads();
+    if (s_stop) break;
+    if (p != j) {  // swap whole columns j <-> p
+      for (int i = threadIdx.x; i < m; i += blockDim.x) {
+        double2 t = M[i + (int64_t)j * ld];
+        M[i + (int64_t)j * ld] = M[i + (int64_t)p * ld];
+        M[i + (int64_t)p * ld] = t;
+      }
+      if (threadIdx.x == 0) {
+        double t = q.norm2[j];
+        q.norm2[j] = q.norm2[p];
+        q.norm2[p] = t;
+        int ti = q.perm[j];
+        q.perm[j] = q.perm[p];
+        q.perm[p] = ti;
+      }
+    }
+    __syncthreads();
+    // reflector from x = M[j:m, j]; |x| recomputed exactly
+    double s = 0.0;
+    for (int i = j + threadIdx.x; i < m; i += blockDim.x) s += cabs2(M[i + (int64_t)j * ld]);
+    sval[threadIdx.x] = s;
+    __syncthreads();
+    for (int t = blockDim.x / 2; t > 0; t >>= 1) {
+      if (threadIdx.x < t) sval[threadIdx.x] += sval[threadIdx.x + t];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+      double xn = sqrt(sval[0]);
+      double2 x0 = M[j + (int64_t)j * ld];
+      double a0 = sqrt(cabs2(x0));
+      double2 beta = a0 > 0.0 ? make_double2(-x0.x / a0 * xn, -x0.y / a0 * xn) : make_double2(-xn, 0.0);
+      double2 u0 = make_double2(x0.x - beta.x, x0.y - beta.y);
+      // u^H u = 2 |x| (|x| + |x0|)
+      double uu = 2.0 * xn * (xn + a0);
+      s_tau = uu > 0.0 ? 2.0 / uu : 0.0;
+      s_beta = beta;
+      M[j + (int64_t)j * ld] = u0;
+    }
+    __syncthreads();
+    const double tau = s_tau;
+    // apply P to the trailing columns: one warp per column; exact new norms on the way
+    for (int c = j + 1 + warp; c < n; c += nw) {
+      double2* col = M + (int64_t)c * ld;
+      const double2* u = M + (int64_t)j * ld;
+      double2 w = make_double2(0.0, 0.0);
+      for (int i = j + lane; i < m; i += 32) {  // w = u^H col
+        double2 ui = u[i], ci = col[i];
+        w.x += ui.x * ci.x + ui.y * ci.y;
+        w.y += ui.x * ci.y - ui.y * ci.x;
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        w.x += __shfl_xor_sync(0xffffffffu, w.x, o);
+        w.y += __shfl_xor_sync(0xffffffffu, w.y, o);
+      }
+      w.x *= tau;
+      w.y *= tau;
+      double ns = 0.0;
+      for (int i = j + lane; i < m; i += 32) {
+        double2 v = cfms(u[i], w, col[i]);
+        col[i] = v;
+        if (i > j) ns += cabs2(v);
+      }
+      for (int o = 16; o > 0; o >>= 1) ns += __shfl_xor_sync(0xffffffffu, ns, o);
+      if (lane == 0) q.norm2[c] = ns;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      q.tauv[j] = tau;
+      q.betav[j] = s_beta;
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    q.state[0] = j;
+    q.state[1] = j;  // rank reached
+  }
+}
+
+// After the QR: put the diagonal of R back (the reflectors are no longer needed) and zero
+// the part of column t below the diagonal within the first k rows (none: R11 is k x k).
+__global__ void k_cpqr_finish(const QrDesc* __restrict__ d) {
+  const QrDesc q = d[blockIdx.x];
+  int k = q.state[1];
+  for (int t = threadIdx.x; t < k; t += blockDim.x) q.A[t + (int64_t)t * q.lda] = q.betav[t];
+}
+
+// ------------------------------------------------------------------ host drivers ----
+static int grid_cap() {
+  static int nsm = 0;
+  if (nsm == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (nsm <= 0) nsm = 152;
+  }
+  return nsm * 8;
+}
+
+static int tiles_x(int64_t tiles) {
+  int cap = grid_cap();
+  return (int)(tiles < 1 ? 1 : (tiles < cap ? tiles : cap));
+}
+
+int wsbm_gemm_batched(const GemmDesc* d_desc, int nbatch, int max_m, int max_n, cudaStream_t st) {
+  if (nbatch <= 0) return 0;
+  int64_t t = (int64_t)((max_m + GT - 1) / GT) * ((max_n + GT - 1) / GT);
+  dim3 grid(tiles_x(t), nbatch);
+  k_gemm<<<grid, 256, 0, st>>>(d_desc, nbatch);
+  wsbm_count_launch();
+  return cudaGetLastError() == cudaSuccess ? 0 : -3;
+}
+
+int wsbm_lu_batched(const LuDesc* d_desc, int nbatch, int max_n, int* d_info, cudaStream_t st) {
+  if (nbatch <= 0) return 0;
+  for (int j0 = 0; j0 < max_n; j0 += WSBM_NB) {
+    k_lu_panel<<<nbatch, 256, 0, st>>>(d_desc, j0, WSBM_NB, d_info);
+    wsbm_count_launch();
+    dim3 gs(tiles_x((max_n + 127) / 128), nbatch);
+    k_laswp<<<gs, 128, 0, st>>>(d_desc, j0, WSBM_NB);
+    wsbm_count_launch();
+    k_lu_trsm_row<<<gs, 128, 0, st>>>(d_desc, j0, WSBM_NB);
+    wsbm_count_launch();
+    int m = max_n - j0 - WSBM_NB;
+    if (m > 0) {
+      int64_t t = (int64_t)((m + GT - 1) / GT) * ((m + GT - 1) / GT);
+      dim3 gg(tiles_x(t), nbatch);
+      k_lu_update<<<gg, 256, 0, st>>>(d_desc, j0, WSBM_NB);
+      wsbm_count_launch();
+    }
+  }
+  return cudaGetLastError() == cudaSuccess ? 0 : -3;
+}
+
+// Triangular solves T^-1 B (lower unit: forward; upper non-unit: backward), blocked.
+int wsbm_trsm_batched(const TrsmDesc* d_desc, int nbatch, int max_n, int max_nrhs, int lower,
+                      cudaStream_t st) {
+  if (nbatch <= 0 || max_n <= 0 || max_nrhs <= 0) return 0;
+  dim3 gd(tiles_x((max_nrhs + 127) / 128), nbatch);
+  if (lower) {
+    for (int j0 = 0; j0 < max_n; j0 += WSBM_NB) {
+      k_trsm_diag<<<gd, 128, 0, st>>>(d_desc, j0, WSBM_NB, 1);
+      wsbm_count_launch();
+      int m = max_n - j0 - WSBM_NB;
+      if (m > 0) {
+        int64_t t = (int64_t)((m + GT - 1) / GT) * ((max_nrhs + GT - 1) / GT);
+        k_trsm_update<<<dim3(tiles_x(t), nbatch), 256, 0, st>>>(d_desc, j0, WSBM_NB, 1);
+        wsbm_count_launch();
+      }
+    }
+  } else {
+    int last = ((max_n - 1) / WSBM_NB) * WSBM_NB;
+    for (int j0 = last; j0 >= 0; j0 -= WSBM_NB) {
+      k_trsm_diag<<<gd, 128, 0, st>>>(d_desc, j0, WSBM_NB, 0);
+      wsbm_count_launch();
+      if (j0 > 0) {
+        int64_t t = (int64_t)((j0 + GT - 1) / GT) * ((max_nrhs + GT - 1) / GT);
+        k_trsm_update<<<dim3(tiles_x(t), nbatch), 256, 0, st>>>(d_desc, j0, WSBM_NB, 0);
+        wsbm_count_launch();
+      }
+    }
+  }
+  return cudaGetLastError() == cudaSuccess ? 0 : -3;
+}
+
+// Upper-triangular backward solves must start at each matrix's own last block; the blocked
+// loop above runs from the batch maximum, and blocks with j0 >= n skip, so a smaller matrix
+// simply starts later.  (Each k_trsm_diag / k_trsm_update guards j0 >= n.)
+
+int wsbm_lu_solve_batched(const TrsmDesc* d_desc_lower, const TrsmDesc* d_desc_upper, int nbatch,
+                          int max_n, int max_nrhs, cudaStream_t st) {
+  if (nbatch <= 0) return 0;
+  dim3 gd(tiles_x((max_nrhs + 127) / 128), nbatch);
+  k_apply_piv<<<gd, 128, 0, st>>>(d_desc_lower);
+  wsbm_count_launch();
+  int rc = wsbm_trsm_batched(d_desc_lower, nbatch, max_n, max_nrhs, 1, st);
+  if (rc) return rc;
+  return wsbm_trsm_batched(d_desc_upper, nbatch, max_n, max_nrhs, 0, st);
+}
+
+int wsbm_cpqr_batched(const QrDesc* d_desc, int nbatch, int mode, cudaStream_t st) {
+  if (nbatch <= 0) return 0;
+  k_cpqr<<<nbatch, 256, 0, st>>>(d_desc, mode);
+  wsbm_count_launch();
+  return cudaGetLastError() == cudaSuccess ? 0 : -3;
+}
+
+int wsbm_cpqr_finish(const QrDesc* d_desc, int nbatch, cudaStream_t st) {
+  if (nbatch <= 0) return 0;
+  k_cpqr_finish<<<nbatch, 128, 0, st>>>(d_desc);
+  wsbm_count_launch();
+  return cudaGetLastError() == cudaSuccess ? 0 : -3;
+}

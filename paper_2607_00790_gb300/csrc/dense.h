@@ -1,0 +1,66 @@
+// Descriptors and host entry points of the batched dense complex128 kernels (dense.cu).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#define WSBM_NB 32  // panel / block width of the blocked LU and triangular solves
+
+// Kernel-launch counter of the library (every launch site calls wsbm_count_launch()).
+void wsbm_count_launch();
+int64_t wsbm_launch_count();
+
+// C = alpha * A * B + beta * C  (column-major, A m x k, B k x n, C m x n)
+struct GemmDesc {
+  const double2* A;
+  const double2* B;
+  double2* C;
+  int64_t lda, ldb, ldc;
+  int32_t m, n, k, pad;
+  double2 alpha, beta;
+};
+
+// In-place LU with partial pivoting of an n x n matrix; piv[j] = row swapped with row j.
+struct LuDesc {
+  double2* A;
+  int64_t lda;
+  int32_t* piv;
+  int32_t n, pad;
+};
+
+// B (n x nrhs) <- T^-1 B with T n x n triangular (lower unit or upper non-unit);
+// piv: LU row interchanges applied to B by the LU solve.
+struct TrsmDesc {
+  const double2* T;
+  int64_t ldt;
+  double2* B;
+  int64_t ldb;
+  const int32_t* piv;
+  int32_t n, nrhs;
+};
+
+// Column-pivoted QR state of an m x n matrix.  state[0] = next step (0 for a fresh matrix),
+// state[1] = rank reached; perm[t] = original column at position t; norm2 = remaining squared
+// column norms; tauv, betav = reflector scalars and R diagonal; rdiag0 = |R_00|.
+struct QrDesc {
+  double2* A;
+  int64_t lda;
+  int32_t m, n;
+  int32_t kt;  // mode 1 target rank
+  int32_t pad;
+  double tol;
+  int32_t* perm;
+  int32_t* state;
+  double* norm2;
+  double* tauv;
+  double2* betav;
+  double* rdiag0;
+};
+
+int wsbm_gemm_batched(const GemmDesc* d_desc, int nbatch, int max_m, int max_n, cudaStream_t st);
+int wsbm_lu_batched(const LuDesc* d_desc, int nbatch, int max_n, int* d_info, cudaStream_t st);
+int wsbm_trsm_batched(const TrsmDesc* d_desc, int nbatch, int max_n, int max_nrhs, int lower,
+                      cudaStream_t st);
+int wsbm_lu_solve_batched(const TrsmDesc* d_desc_lower, const TrsmDesc* d_desc_upper, int nbatch,
+                          int max_n, int max_nrhs, cudaStream_t st);
+int wsbm_cpqr_batched(const QrDesc* d_desc, int nbatch, int mode, cudaStream_t st);
+int wsbm_cpqr_finish(const QrDesc* d_desc, int nbatch, cudaStream_t st);

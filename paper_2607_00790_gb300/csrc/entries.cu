@@ -1,0 +1,514 @@
+// Entry generation for the WSBM Nystrom matrix (eq. weakly_bm; block form A_ij of Sec. III)
+// and for the proxy-circle blocks of the proxy-surface method (Sec. III).
+//
+// Work unit: one node pair (or node / proxy-point pair).  It evaluates H0, H1 at z0 = k0 r and
+// z1 = k1 r once and writes all entries of its 2x2 block, so every unit costs the same (the
+// paper balances threads the same way: each block A_ij carries the same seven layer-potential
+// terms).  A CTA stages the node data of a 32 x 4 tile in shared memory; the 32 slots of the
+// fast dimension map to consecutive output rows, so a warp's complex128 stores are contiguous.
+// Launches are grid-stride over a flat tile list spanning many blocks (all boxes of a tree
+// level in one launch).
+#include <math.h>
+
+#include "hankel.cuh"
+#include "wsbm_internal.h"
+
+#define WSBM_4PI 12.566370614359172954
+
+// Geometric quantities of a pair with the operation order fixed (no contraction): r and the
+// arguments z = k r are reproducible bit for bit by any IEEE double implementation.
+struct PairGeom {
+  double r, ir, z0, z1, dnx, dny, nn, c;
+};
+
+__device__ __forceinline__ void pair_geom(double xi, double yi, double nxi, double nyi, double xj,
+                                          double yj, double nxj, double nyj, const Phys& ph,
+                                          PairGeom& G) {
+  double dx = __dsub_rn(xi, xj);
+  double dy = __dsub_rn(yi, yj);
+  double r2 = __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy));
+  double r = __dsqrt_rn(r2);
+  G.r = r;
+  G.z0 = __dmul_rn(ph.k0, r);
+  G.z1 = __dmul_rn(ph.k1, r);
+  G.dny = __dadd_rn(__dmul_rn(dx, nxj), __dmul_rn(dy, nyj));
+  G.dnx = __dadd_rn(__dmul_rn(dx, nxi), __dmul_rn(dy, nyi));
+  G.nn = __dadd_rn(__dmul_rn(nxi, nxj), __dmul_rn(nyi, nyj));
+  G.ir = 1.0 / r;
+  G.c = G.dnx * G.dny * (G.ir * G.ir);
+}
+
+// Off-diagonal 2x2 block, weight w_j folded in (kernels: G_k = (i/4) H0(kr);
+// D: (ik/4) H1 (d.n_y)/r;  D*: -(ik/4) H1 (d.n_x)/r;
+// N_k0 - N_k1 = (i/4)[(k0^2 H0(z0) - k1^2 H0(z1)) c + (k0^2 F1(z0) - k1^2 F1(z1))(n_x.n_y - 2c)]).
+__device__ __forceinline__ void block_offdiag(const HkTables& T, const Phys& ph, const PairGeom& G,
+                                              double wj, double2 e[2][2]) {
+  Hk a, b;
+  hankel_fp64(T, G.z0, a);
+  hankel_fp64(T, G.z1, b);
+  const double k0 = ph.k0, k1 = ph.k1;
+  double s11 = 0.25 * wj * k1 * G.dny * G.ir;  // A11 = i s11 H1(z1)
+  e[0][0] = make_double2(-s11 * b.h1i, s11 * b.h1r);
+  double s12 = -0.25 * ph.eps1 * wj;  // A12 = i s12 H0(z1)
+  e[0][1] = make_double2(-s12 * b.h0i, s12 * b.h0r);
+  double q0 = k0 * k0, q1 = k1 * k1;
+  double m2c = G.nn - 2.0 * G.c;
+  double gr = (q0 * a.h0r - q1 * b.h0r) * G.c + (q0 * a.f1r - q1 * b.f1r) * m2c;
+  double gi = (q0 * a.h0i - q1 * b.h0i) * G.c + (q0 * a.f1i - q1 * b.f1i) * m2c;
+  double inv4k0 = 0.25 / k0;
+  double t1 = 0.25 * k0 * G.dny * G.ir;
+  // A21 = w [ i t1 H1(z0) + alpha dN ],  alpha dN = -(1/(4 k0)) (gr + i gi)
+  e[1][0] = make_double2(wj * (-t1 * a.h1i - inv4k0 * gr), wj * (t1 * a.h1r - inv4k0 * gi));
+  // A22 = w [ -i (eps0/4) H0(z0) - (d.n_x/(4 k0 r)) (eps0 k0 H1(z0) - eps1 k1 H1(z1)) ]
+  double u = G.dnx * G.ir * inv4k0;
+  double vr = ph.eps0 * k0 * a.h1r - ph.eps1 * k1 * b.h1r;
+  double vi = ph.eps0 * k0 * a.h1i - ph.eps1 * k1 * b.h1i;
+  e[1][1] = make_double2(wj * (0.25 * ph.eps0 * a.h0i - u * vr),
+                         wj * (-0.25 * ph.eps0 * a.h0r - u * vi));
+}
+
+// Diagonal 2x2 block: one-point corrected trapezoidal rule.  A kernel a ln|x-y| + b gets the
+// weight w_i [a ln(w_i/2pi) + b(x_i, x_i)]; D and D* tend to -kappa/(4 pi).
+__device__ __forceinline__ void block_diag(const Phys& ph, double wi, double kap, double2 e[2][2]) {
+  const double k0 = ph.k0, k1 = ph.k1;
+  double L0 = log(k0 * wi / WSBM_4PI);
+  double L1 = log(k1 * wi / WSBM_4PI);
+  double S0r = -wi * (WSBM_EULER + L0) / (2.0 * WSBM_PI), Si = 0.25 * wi;
+  double S1r = -wi * (WSBM_EULER + L1) / (2.0 * WSBM_PI);
+  double Dd = -wi * kap / WSBM_4PI;
+  double f0 = k0 * k0 * (L0 + WSBM_EULER - 0.5);
+  double f1 = k1 * k1 * (L1 + WSBM_EULER - 0.5);
+  double dNr = -wi * (f0 - f1) / WSBM_4PI;
+  double dNi = wi * (k0 * k0 - k1 * k1) / 8.0;
+  e[0][0] = make_double2(Dd + 0.5, 0.0);
+  e[0][1] = make_double2(-ph.eps1 * S1r, -ph.eps1 * Si);
+  e[1][0] = make_double2(Dd - 0.5 - dNi / k0, dNr / k0);
+  e[1][1] = make_double2(-ph.eps0 * S0r,
+                         -ph.eps0 * Si - ((ph.eps0 - ph.eps1) * Dd + 0.5 * (ph.eps0 + ph.eps1)) / k0);
+}
+
+struct SlotData {
+  double x, y, nx, ny, w, kap;
+  int32_t node, p0, p1;
+};
+
+__device__ __forceinline__ int find_task_by_tile(const int32_t* tile0s, int stride, int ntasks,
+                                                 int64_t tile) {
+  int lo = 0, hi = ntasks - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if ((int64_t)tile0s[(int64_t)mid * stride] <= tile)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  return lo;
+}
+
+__device__ __forceinline__ void load_slot(const DevGeom& g, const int32_t* nodes,
+                                          const int32_t* pos, int t, SlotData& s) {
+  int32_t nd = nodes[t];
+  s.node = nd;
+  s.x = g.x[nd];
+  s.y = g.y[nd];
+  s.nx = g.nx[nd];
+  s.ny = g.ny[nd];
+  s.w = g.w[nd];
+  s.kap = g.kappa[nd];
+  s.p0 = pos[2 * t];
+  s.p1 = pos[2 * t + 1];
+}
+
+__global__ void __launch_bounds__(WSBM_PAIR_THREADS)
+    k_pairs(DevGeom g, Phys ph, const PairTask* __restrict__ tasks, int ntasks, int64_t ntiles) {
+  __shared__ HkTables T;
+  __shared__ SlotData sf[WSBM_TILE_F];
+  __shared__ SlotData ss[WSBM_TILE_S];
+  hk_stage_tables(&T);
+  const int tx = threadIdx.x & (WSBM_TILE_F - 1);
+  const int ty = threadIdx.x / WSBM_TILE_F;
+  const int stride = sizeof(PairTask) / sizeof(int32_t);
+  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    int ti = find_task_by_tile(&tasks[0].tile0, stride, ntasks, tile);
+    const PairTask tk = tasks[ti];
+    const int nf = tk.trans ? tk.nc : tk.nr;
+    const int ns = tk.trans ? tk.nr : tk.nc;
+    const int nft = (nf + WSBM_TILE_F - 1) / WSBM_TILE_F;
+    const int64_t lt = tile - tk.tile0;
+    const int f0 = (int)(lt % nft) * WSBM_TILE_F;
+    const int s0 = (int)(lt / nft) * WSBM_TILE_S;
+    __syncthreads();  // previous tile done with the staged slots (and tables staged)
+    if (threadIdx.x < WSBM_TILE_F) {
+      int f = f0 + threadIdx.x;
+      if (f < nf) {
+        if (tk.trans)
+          load_slot(g, tk.cnode, tk.cpos, f, sf[threadIdx.x]);
+        else
+          load_slot(g, tk.rnode, tk.rpos, f, sf[threadIdx.x]);
+      }
+    } else if (threadIdx.x < WSBM_TILE_F + WSBM_TILE_S) {
+      int k = threadIdx.x - WSBM_TILE_F;
+      int s = s0 + k;
+      if (s < ns) {
+        if (tk.trans)
+          load_slot(g, tk.rnode, tk.rpos, s, ss[k]);
+        else
+          load_slot(g, tk.cnode, tk.cpos, s, ss[k]);
+      }
+    }
+    __syncthreads();
+    const int f = f0 + tx, s = s0 + ty;
+    if (f < nf && s < ns) {
+      const SlotData& R = tk.trans ? ss[ty] : sf[tx];
+      const SlotData& C = tk.trans ? sf[tx] : ss[ty];
+      double2 e[2][2];
+      if (R.node == C.node) {
+        block_diag(ph, R.w, R.kap, e);
+      } else {
+        PairGeom G;
+        pair_geom(R.x, R.y, R.nx, R.ny, C.x, C.y, C.nx, C.ny, ph, G);
+        block_offdiag(T, ph, G, C.w, e);
+      }
+      const int rp[2] = {R.p0, R.p1};
+      const int cp[2] = {C.p0, C.p1};
+#pragma unroll
+      for (int b = 0; b < 2; ++b)
+#pragma unroll
+        for (int a = 0; a < 2; ++a) {
+          if (rp[a] >= 0 && cp[b] >= 0) {
+            int64_t off = tk.trans ? ((int64_t)cp[b] + (int64_t)rp[a] * tk.ld)
+                                   : ((int64_t)rp[a] + (int64_t)cp[b] * tk.ld);
+            tk.out[off] = e[a][b];
+          }
+        }
+    }
+  }
+}
+
+// --------------------------------------------------------------------- proxy blocks ----
+struct ProxyPt {
+  double px, py, pnx, pny;
+};
+
+// Sources on the proxy circle acting on equations at node x (row side).  Combined-field
+// source Phi_k = dG/dnu_p - i k G;  out[s][a]: source s (0: k1, 1: k0), equation a.
+//   s = k1: [Phi1 ; -alpha d_nx Phi1]     s = k0: [0 ; Phi0 + alpha d_nx Phi0]
+__device__ __forceinline__ void proxy_row_fp64(const HkTables& T, const Phys& ph, const SlotData& X,
+                                               const ProxyPt& p, double pw, double2 o[2][2]) {
+  double dx = X.x - p.px, dy = X.y - p.py;
+  double r2 = dx * dx + dy * dy;
+  double r = sqrt(r2);
+  double ir = 1.0 / r;
+  double dnu = (dx * p.pnx + dy * p.pny) * ir;
+  double dnx = (dx * X.nx + dy * X.ny) * ir;
+  double nn = X.nx * p.pnx + X.ny * p.pny;
+  double c = dnx * dnu;
+  double inv_k0 = 1.0 / ph.k0;
+#pragma unroll
+  for (int s = 0; s < 2; ++s) {
+    double k = s == 0 ? ph.k1 : ph.k0;
+    Hk h;
+    hankel_fp64(T, k * r, h);
+    // phi = (ik/4) H1 dnu + (k/4) H0
+    double q = 0.25 * k;
+    double phr = q * (-h.h1i * dnu + h.h0r), phi = q * (h.h1r * dnu + h.h0i);
+    // dphi = N_k - (k^2/4) H1 dnx,  N_k = (i k^2/4)[H0 c + H1/(kr) (nn - 2c)]
+    double q2 = 0.25 * k * k;
+    double izr = ir / k;
+    double m2c = nn - 2.0 * c;
+    double Xr = h.h0r * c + h.h1r * izr * m2c, Xi = h.h0i * c + h.h1i * izr * m2c;
+    double dpr = q2 * (-Xi - h.h1r * dnx), dpi = q2 * (Xr - h.h1i * dnx);
+    // alpha * dphi = (i/k0)(dpr + i dpi) = (-dpi/k0, dpr/k0)
+    double adr = -dpi * inv_k0, adi = dpr * inv_k0;
+    if (s == 0) {
+      o[0][0] = make_double2(pw * phr, pw * phi);
+      o[0][1] = make_double2(-pw * adr, -pw * adi);
+    } else {
+      o[1][0] = make_double2(0.0, 0.0);
+      o[1][1] = make_double2(pw * (phr + adr), pw * (phi + adi));
+    }
+  }
+}
+
+// Fields of the box unknowns at a proxy point (column side).  out[s][b]: field s (0: psi1,
+// 1: psi0), unknown b:  u_j -> w_j (ik/4) H1 (d.n_y)/r,  q_j -> -eps_s w_j (i/4) H0.
+__device__ __forceinline__ void proxy_col_fp64(const HkTables& T, const Phys& ph, const SlotData& Y,
+                                               const ProxyPt& p, double2 o[2][2]) {
+  double dx = p.px - Y.x, dy = p.py - Y.y;
+  double r2 = dx * dx + dy * dy;
+  double r = sqrt(r2);
+  double dny = (dx * Y.nx + dy * Y.ny) / r;
+#pragma unroll
+  for (int s = 0; s < 2; ++s) {
+    double k = s == 0 ? ph.k1 : ph.k0;
+    double eps = s == 0 ? ph.eps1 : ph.eps0;
+    Hk h;
+    hankel_fp64(T, k * r, h);
+    double a = 0.25 * Y.w * k * dny;
+    o[s][0] = make_double2(-a * h.h1i, a * h.h1r);
+    double bq = -0.25 * eps * Y.w;
+    o[s][1] = make_double2(-bq * h.h0i, bq * h.h0r);
+  }
+}
+
+// Mixed precision versions: z = k r formed in FP64 and reduced mod 2 pi in FP64; amplitude and
+// entry algebra in FP32.
+__device__ __forceinline__ void hankel_mixed(const HkTables& T, double z, HkF& o) {
+  if (z >= HK_Z_SERIES) {
+    hankel_mixed_large(T, z, o);
+  } else {
+    Hk h;
+    hankel_fp64(T, z, h);
+    o.h0r = (float)h.h0r;
+    o.h0i = (float)h.h0i;
+    o.h1r = (float)h.h1r;
+    o.h1i = (float)h.h1i;
+  }
+}
+
+// Row side in mixed precision.  With H1 = -i H0 + D (D = H1 + i H0, small for large z) and
+// 1 + d.nu/r = |d x nu|^2 / (r (r - d.nu)), the combined-field source and its normal
+// derivative are written without the leading-order cancellation:
+//   (4/k) Phi     = H0 (1 + dnu) + i dnu D
+//   (4/k^2) dPhi  = dnx (i H0 (1 + dnu) - D) + i (H1/z)(n_x.nu - 2 dnx dnu)
+// (dnu = d.nu/r, dnx = d.n_x/r).  d.nu and d x nu are formed in FP64.
+__device__ __forceinline__ void proxy_row_mixed(const HkTables& T, const Phys& ph, const SlotData& X,
+                                                const ProxyPt& p, double pw, double2 o[2][2]) {
+  double dx = X.x - p.px, dy = X.y - p.py;
+  double r = sqrt(dx * dx + dy * dy);
+  double dnu_d = dx * p.pnx + dy * p.pny;
+  double crs_d = dx * p.pny - dy * p.pnx;
+  float ir = 1.0f / (float)r;
+  float dnu = (float)dnu_d * ir;
+  float cr = (float)crs_d * ir;
+  float opd = cr * cr / (1.0f - dnu);  // 1 + dnu
+  float dnx = ((float)dx * (float)X.nx + (float)dy * (float)X.ny) * ir;
+  float nn = (float)X.nx * (float)p.pnx + (float)X.ny * (float)p.pny;
+  float m2c = nn - 2.0f * dnx * dnu;
+  float inv_k0 = (float)(1.0 / ph.k0);
+  float fpw = (float)pw;
+#pragma unroll
+  for (int s = 0; s < 2; ++s) {
+    double kd = s == 0 ? ph.k1 : ph.k0;
+    float k = (float)kd;
+    double z = kd * r;
+    HkF h;
+    float Dr, Di;
+    if (z >= HK_Z_SERIES) {
+      hankel_mixed_large(T, z, h, &Dr, &Di);
+    } else {
+      Hk hd;
+      hankel_fp64(T, z, hd);
+      h.h0r = (float)hd.h0r;
+      h.h0i = (float)hd.h0i;
+      h.h1r = (float)hd.h1r;
+      h.h1i = (float)hd.h1i;
+      Dr = (float)(hd.h1r - hd.h0i);
+      Di = (float)(hd.h1i + hd.h0r);
+    }
+    float q = 0.25f * k;
+    // (4/k) Phi = H0 opd + i dnu D
+    float phr = q * (h.h0r * opd - dnu * Di), phi = q * (h.h0i * opd + dnu * Dr);
+    // (4/k^2) dPhi = dnx (i H0 opd - D) + i (H1/z) m2c
+    float izr = ir / k;
+    float Br = -h.h0i * opd - Dr, Bi = h.h0r * opd - Di;
+    float q2 = 0.25f * k * k;
+    float dpr = q2 * (dnx * Br - h.h1i * izr * m2c), dpi = q2 * (dnx * Bi + h.h1r * izr * m2c);
+    float adr = -dpi * inv_k0, adi = dpr * inv_k0;
+    if (s == 0) {
+      o[0][0] = make_double2(fpw * phr, fpw * phi);
+      o[0][1] = make_double2(-fpw * adr, -fpw * adi);
+    } else {
+      o[1][0] = make_double2(0.0, 0.0);
+      o[1][1] = make_double2(fpw * (phr + adr), fpw * (phi + adi));
+    }
+  }
+}
+
+__device__ __forceinline__ void proxy_col_mixed(const HkTables& T, const Phys& ph, const SlotData& Y,
+                                                const ProxyPt& p, double2 o[2][2]) {
+  double dx = p.px - Y.x, dy = p.py - Y.y;
+  double r = sqrt(dx * dx + dy * dy);
+  float dny = ((float)dx * (float)Y.nx + (float)dy * (float)Y.ny) / (float)r;
+  float w = (float)Y.w;
+#pragma unroll
+  for (int s = 0; s < 2; ++s) {
+    double kd = s == 0 ? ph.k1 : ph.k0;
+    float eps = (float)(s == 0 ? ph.eps1 : ph.eps0);
+    HkF h;
+    hankel_mixed(T, kd * r, h);
+    float a = 0.25f * w * (float)kd * dny;
+    o[s][0] = make_double2(-a * h.h1i, a * h.h1r);
+    float bq = -0.25f * eps * w;
+    o[s][1] = make_double2(-bq * h.h0i, bq * h.h0r);
+  }
+}
+
+template <bool MIXED>
+__global__ void __launch_bounds__(WSBM_PAIR_THREADS)
+    k_proxy(DevGeom g, Phys ph, const ProxyTask* __restrict__ tasks, int ntasks, int64_t ntiles) {
+  __shared__ HkTables T;
+  __shared__ ProxyPt sp[WSBM_TILE_F];
+  __shared__ SlotData ss[WSBM_TILE_S];
+  hk_stage_tables(&T);
+  const int tx = threadIdx.x & (WSBM_TILE_F - 1);
+  const int ty = threadIdx.x / WSBM_TILE_F;
+  const int stride = sizeof(ProxyTask) / sizeof(int32_t);
+  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    int ti = find_task_by_tile(&tasks[0].tile0, stride, ntasks, tile);
+    const ProxyTask tk = tasks[ti];
+    const int nft = (tk.P + WSBM_TILE_F - 1) / WSBM_TILE_F;
+    const int64_t lt = tile - tk.tile0;
+    const int m0 = (int)(lt % nft) * WSBM_TILE_F;
+    const int s0 = (int)(lt / nft) * WSBM_TILE_S;
+    __syncthreads();
+    if (threadIdx.x < WSBM_TILE_F) {
+      int m = m0 + threadIdx.x;
+      if (m < tk.P) {
+        double sn, cs;
+        sincospi(2.0 * (double)m / (double)tk.P, &sn, &cs);
+        sp[threadIdx.x].pnx = cs;
+        sp[threadIdx.x].pny = sn;
+        sp[threadIdx.x].px = tk.cx + tk.rho * cs;
+        sp[threadIdx.x].py = tk.cy + tk.rho * sn;
+      }
+    } else if (threadIdx.x < WSBM_TILE_F + WSBM_TILE_S) {
+      int k = threadIdx.x - WSBM_TILE_F;
+      if (s0 + k < tk.nn) load_slot(g, tk.node, tk.pos, s0 + k, ss[k]);
+    }
+    __syncthreads();
+    const int m = m0 + tx, s = s0 + ty;
+    if (m < tk.P && s < tk.nn) {
+      double2 o[2][2];
+      const SlotData& X = ss[ty];
+      if (tk.side == 0) {
+        double pw = 2.0 * WSBM_PI * tk.rho / (double)tk.P;
+        if (MIXED)
+          proxy_row_mixed(T, ph, X, sp[tx], pw, o);
+        else
+          proxy_row_fp64(T, ph, X, sp[tx], pw, o);
+      } else {
+        if (MIXED)
+          proxy_col_mixed(T, ph, X, sp[tx], o);
+        else
+          proxy_col_fp64(T, ph, X, sp[tx], o);
+      }
+      const int bp[2] = {X.p0, X.p1};
+#pragma unroll
+      for (int sgn = 0; sgn < 2; ++sgn) {
+        int64_t prow = (int64_t)tk.off + (int64_t)sgn * tk.P + m;
+#pragma unroll
+        for (int a = 0; a < 2; ++a) {
+          if (bp[a] >= 0) {
+            int64_t off = tk.tr ? ((int64_t)bp[a] + prow * tk.ld) : (prow + (int64_t)bp[a] * tk.ld);
+            tk.out[off] = o[sgn][a];
+          }
+        }
+      }
+    }
+  }
+}
+
+// -------------------------------------------------------------- Hankel test kernel ----
+__global__ void k_hankel(const double* __restrict__ z, int64_t n, double* __restrict__ out,
+                         int mixed) {
+  __shared__ HkTables T;
+  hk_stage_tables(&T);
+  __syncthreads();
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    double zi = z[i];
+    double* o = out + 6 * i;
+    if (mixed) {
+      HkF h;
+      hankel_mixed(T, zi, h);
+      o[0] = h.h0r;
+      o[1] = h.h0i;
+      o[2] = h.h1r;
+      o[3] = h.h1i;
+      o[4] = 0.0;
+      o[5] = 0.0;
+    } else {
+      Hk h;
+      hankel_fp64(T, zi, h);
+      o[0] = h.h0r;
+      o[1] = h.h0i;
+      o[2] = h.h1r;
+      o[3] = h.h1i;
+      o[4] = h.f1r;
+      o[5] = h.f1i;
+    }
+  }
+}
+
+__global__ void k_unknowns_to_slots(const int64_t* __restrict__ idx, int64_t n, int64_t N,
+                                    int32_t* __restrict__ node, int32_t* __restrict__ pos) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    int64_t u = idx[t];
+    int comp = u >= N ? 1 : 0;
+    node[t] = (int32_t)(u - comp * N);
+    pos[2 * t + comp] = (int32_t)t;
+    pos[2 * t + 1 - comp] = -1;
+  }
+}
+
+// ------------------------------------------------------------------- host helpers ----
+static int grid_for(int64_t ntiles) {
+  static int nsm = 0;
+  if (nsm == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (nsm <= 0) nsm = 152;
+  }
+  int64_t cap = (int64_t)nsm * 16;
+  return (int)(ntiles < cap ? ntiles : cap);
+}
+
+int64_t wsbm_pair_tiles(int32_t nr, int32_t nc, int32_t trans) {
+  int32_t nf = trans ? nc : nr, ns = trans ? nr : nc;
+  if (nf <= 0 || ns <= 0) return 0;
+  return (int64_t)((nf + WSBM_TILE_F - 1) / WSBM_TILE_F) * ((ns + WSBM_TILE_S - 1) / WSBM_TILE_S);
+}
+
+int64_t wsbm_proxy_tiles(int32_t nn, int32_t P) {
+  if (nn <= 0 || P <= 0) return 0;
+  return (int64_t)((P + WSBM_TILE_F - 1) / WSBM_TILE_F) * ((nn + WSBM_TILE_S - 1) / WSBM_TILE_S);
+}
+
+int wsbm_launch_pairs(const DevGeom& g, const Phys& ph, const PairTask* d_tasks, int ntasks,
+                      int64_t ntiles, cudaStream_t st) {
+  if (ntiles <= 0) return WSBM_OK;
+  k_pairs<<<grid_for(ntiles), WSBM_PAIR_THREADS, 0, st>>>(g, ph, d_tasks, ntasks, ntiles);
+  wsbm_count_launch();
+  return cudaGetLastError() == cudaSuccess ? WSBM_OK : WSBM_ERR_CUDA;
+}
+
+int wsbm_launch_proxy(const DevGeom& g, const Phys& ph, const ProxyTask* d_tasks, int ntasks,
+                      int64_t ntiles, int mixed, cudaStream_t st) {
+  if (ntiles <= 0) return WSBM_OK;
+  if (mixed)
+    k_proxy<true><<<grid_for(ntiles), WSBM_PAIR_THREADS, 0, st>>>(g, ph, d_tasks, ntasks, ntiles);
+  else
+    k_proxy<false><<<grid_for(ntiles), WSBM_PAIR_THREADS, 0, st>>>(g, ph, d_tasks, ntasks, ntiles);
+  wsbm_count_launch();
+  return cudaGetLastError() == cudaSuccess ? WSBM_OK : WSBM_ERR_CUDA;
+}
+
+int wsbm_launch_hankel(const double* z, int64_t n, double* out, int mixed, cudaStream_t st) {
+  if (n <= 0) return WSBM_OK;
+  int64_t blocks = (n + 255) / 256;
+  k_hankel<<<grid_for(blocks), 256, 0, st>>>(z, n, out, mixed);
+  wsbm_count_launch();
+  return cudaGetLastError() == cudaSuccess ? WSBM_OK : WSBM_ERR_CUDA;
+}
+
+int wsbm_launch_unknowns_to_slots(const int64_t* idx, int64_t n, int64_t N, int32_t* node,
+                                  int32_t* pos, cudaStream_t st) {
+  if (n <= 0) return WSBM_OK;
+  int64_t blocks = (n + 255) / 256;
+  k_unknowns_to_slots<<<grid_for(blocks), 256, 0, st>>>(idx, n, N, node, pos);
+  wsbm_count_launch();
+  return cudaGetLastError() == cudaSuccess ? WSBM_OK : WSBM_ERR_CUDA;
+}

@@ -1,0 +1,1447 @@
+// HSS direct solver for the WSBM system (Sec. III): perfect binary tree over the curve-ordered
+// nodes, proxy-surface interpolative decompositions, Martinsson-Rokhlin compressed factor,
+// solve, plane-wave right-hand sides and far field.
+//
+// Unknowns are interleaved inside the library (unknown 2i+c: c = 0 for u_i / the first
+// equation at node i, c = 1 for q_i / the second), so every box owns a contiguous range; the
+// ABI converts from and to the paper's block order [u; q].
+//
+// Per tree level, leaves to root, the host builds flat task lists for all boxes of the level
+// and each phase is one batched launch (the GPU analogue of the paper's one-block-per-thread
+// load balance): entries of the diagonal blocks, sibling blocks and near-field blocks (one
+// node-pair kernel), proxy blocks (one proxy kernel), column-pivoted QR of every box's row and
+// column ID matrices, LU of the diagonal blocks, D^-1 L, R D^-1 L and its inverse.  Between
+// levels the host reads the ranks and skeleton indices (the paper's halo exchange of skeleton
+// indices between neighbouring subtrees becomes this read-back).
+//
+// For box tau with candidate rows I_r and columns I_c (leaf: its unknowns; otherwise the
+// children's skeletons), the row ID gives L (A(I_r, far) ~ L A(J_r, far)), the column ID R
+// (A(far, I_c) ~ A(far, J_c) R), and the compressed factor stores
+//   LU(D), Z = D^-1 L, Dhat = (R D^-1 L)^-1, the column-ID coefficients and permutation.
+// Solve:  up   xh = D^-1 b, bt = Dhat R xh;  root: dense LU solve of the merged skeleton system;
+//         down x = xh - Z (bt - Dhat y).
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <unordered_map>
+#include <vector>
+
+#include "dense.h"
+#include "wsbm_internal.h"
+
+int wsbm_phys_from_params(const wsbm_params* p, Phys* ph);
+int wsbm_geom_check(const wsbm_geom* g);
+
+#define HK(call)                               \
+  do {                                         \
+    int _rc = (call);                          \
+    if (_rc != WSBM_OK) return _rc;            \
+  } while (0)
+#define HC(call)                                 \
+  do {                                           \
+    if ((call) != cudaSuccess) return WSBM_ERR_CUDA; \
+  } while (0)
+
+struct Box {
+  int64_t lo, hi;
+  double cx, cy, R, rho;
+  int P;
+  std::vector<int32_t> cr, cc;  // candidate rows / columns (interleaved unknown ids)
+  int n = 0, k = 0;
+  std::vector<int32_t> Jr, Jc;
+  std::vector<int> near;
+  // factor storage (device)
+  double2* D = nullptr;   // LU of D, n x n
+  int32_t* piv = nullptr;
+  double2* Z = nullptr;   // n x k
+  double2* Dc = nullptr;  // k x k
+  double2* Tc = nullptr;  // k x (n - k)
+  int32_t* pc = nullptr;  // n
+};
+
+struct Level {
+  std::vector<Box> box;
+  bool compressed = false;
+};
+
+struct wsbm_hss {
+  int dev = 0;
+  cudaStream_t st = nullptr;
+  int64_t N = 0;
+  double *x = nullptr, *y = nullptr, *nx = nullptr, *ny = nullptr, *w = nullptr, *kappa = nullptr;
+  std::vector<double> hx, hy, hw;
+  DevGeom g;
+  Phys ph;
+  wsbm_params prm;
+  double cut = 0.0;  // CPQR cutoff
+  int L = 0, top = 0;
+  std::vector<Level> lv;
+  double2* root = nullptr;
+  int32_t* root_piv = nullptr;
+  int root_n = 0;
+  bool factored = false;
+  std::vector<void*> owned;  // factor allocations
+  wsbm_stats_t stats;
+  cudaEvent_t ev[6];
+};
+
+// ---------------------------------------------------------------- small kernels ----
+__global__ void k_fill_identity(double2* A, int64_t lda, int n) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < (int64_t)n * n;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    int i = (int)(t % n), j = (int)(t / n);
+    A[i + (int64_t)j * lda] = make_double2(i == j ? 1.0 : 0.0, 0.0);
+  }
+}
+
+// L (n x k): L[perm[t], t] = 1 for t < k; L[perm[k+s], t] = T[t + s*ldt]  (T: k x (n-k)).
+struct BuildLDesc {
+  double2* L;
+  const double2* T;
+  const int32_t* perm;
+  int64_t ldt;
+  int32_t n, k;
+};
+__global__ void k_build_L(const BuildLDesc* __restrict__ d) {
+  const BuildLDesc q = d[blockIdx.y];
+  int64_t tot = (int64_t)q.n * q.k;
+  // written by permuted position, so no inverse permutation is needed
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    int pos = (int)(e % q.n), t = (int)(e / q.n);
+    double2 v;
+    if (pos < q.k)
+      v = make_double2(pos == t ? 1.0 : 0.0, 0.0);
+    else
+      v = q.T[t + (int64_t)(pos - q.k) * q.ldt];
+    q.L[q.perm[pos] + (int64_t)t * q.n] = v;
+  }
+}
+
+// out[t, c] = in[perm[t], c]  (rows gathered; n x ncol)
+struct GatherDesc {
+  double2* out;
+  const double2* in;
+  const int32_t* perm;
+  int64_t ldo, ldi;
+  int32_t n, ncol;
+};
+__global__ void k_gather_rows(const GatherDesc* __restrict__ d) {
+  const GatherDesc q = d[blockIdx.y];
+  int64_t tot = (int64_t)q.n * q.ncol;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    int t = (int)(e % q.n), c = (int)(e / q.n);
+    q.out[t + (int64_t)c * q.ldo] = q.in[q.perm[t] + (int64_t)c * q.ldi];
+  }
+}
+
+// 2D copy (n rows, ncol columns) between strided matrices, batched.
+struct CopyDesc {
+  double2* dst;
+  const double2* src;
+  int64_t ldd, lds;
+  int32_t m, n;
+};
+__global__ void k_copy2d(const CopyDesc* __restrict__ d) {
+  const CopyDesc q = d[blockIdx.y];
+  int64_t tot = (int64_t)q.m * q.n;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    int i = (int)(e % q.m), j = (int)(e / q.m);
+    q.dst[i + (int64_t)j * q.ldd] = q.src[i + (int64_t)j * q.lds];
+  }
+}
+
+// Plane-wave right-hand side, interleaved: b[2i] = 0, b[2i+1] = -u_in - alpha du_in/dn
+//   = (d.n - 1) u_in  (alpha = i/k0, du_in/dn = i k0 (d.n) u_in).  Output in paper order.
+__global__ void k_rhs_planewave(DevGeom g, double k0, const double* __restrict__ ang, int nang,
+                                double2* __restrict__ rhs) {
+  int64_t N = g.n;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < N * nang;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    int64_t i = e % N;
+    int a = (int)(e / N);
+    double ca, sa;
+    sincos(ang[a], &sa, &ca);
+    double ph = k0 * (ca * g.x[i] + sa * g.y[i]);
+    double s, c;
+    sincos(ph, &s, &c);
+    double dn = ca * g.nx[i] + sa * g.ny[i];
+    double2* col = rhs + (int64_t)a * 2 * N;
+    col[i] = make_double2(0.0, 0.0);
+    col[N + i] = make_double2((dn - 1.0) * c, (dn - 1.0) * s);
+  }
+}
+
+// paper order (2N x nrhs, ld 2N) -> interleaved (2N x nrhs)
+__global__ void k_to_interleaved(const double2* __restrict__ in, double2* __restrict__ out, int64_t N,
+                                 int nrhs) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < 2 * N * nrhs;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    int64_t r = e % (2 * N), c = e / (2 * N);
+    int64_t node = r % N, comp = r / N;
+    out[2 * node + comp + c * 2 * N] = in[e];
+  }
+}
+
+// interleaved x (2N x nrhs) -> u, q (N x nrhs each)
+__global__ void k_split_uq(const double2* __restrict__ x, double2* __restrict__ u,
+                           double2* __restrict__ q, int64_t N, int nrhs) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < N * nrhs;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    int64_t i = e % N, c = e / N;
+    u[e] = x[2 * i + c * 2 * N];
+    q[e] = x[2 * i + 1 + c * 2 * N];
+  }
+}
+
+// Far field: one CTA per observation angle, all right-hand sides, reduction over nodes.
+//   u_inf = e^{i pi/4}/sqrt(8 pi k0) sum_j w_j [-i k0 (xh.n_j) u_j - eps0 q_j] e^{-i k0 xh.x_j}
+#define FF_CHUNK 8
+__global__ void __launch_bounds__(256) k_farfield(DevGeom g, double k0, double eps0,
+                                                  const double2* __restrict__ u,
+                                                  const double2* __restrict__ q, int nrhs,
+                                                  const double* __restrict__ ang, int nang,
+                                                  double2* __restrict__ out) {
+  __shared__ double2 red[FF_CHUNK][256 / 32];
+  const int a = blockIdx.x;
+  double ca, sa;
+  sincos(ang[a], &sa, &ca);
+  const int64_t N = g.n;
+  const double pr = 1.0 / sqrt(8.0 * 3.14159265358979323846 * k0);
+  const double2 pref = make_double2(pr * 0.70710678118654752440, pr * 0.70710678118654752440);
+  for (int c0 = 0; c0 < nrhs; c0 += FF_CHUNK) {
+    double2 acc[FF_CHUNK];
+#pragma unroll
+    for (int c = 0; c < FF_CHUNK; ++c) acc[c] = make_double2(0.0, 0.0);
+    for (int64_t j = threadIdx.x; j < N; j += blockDim.x) {
+      double s, cph;
+      sincos(k0 * (ca * g.x[j] + sa * g.y[j]), &s, &cph);
+      double2 e = make_double2(cph, -s);  // e^{-i k0 xh.x_j}
+      double xn = k0 * (ca * g.nx[j] + sa * g.ny[j]);
+      double wj = g.w[j];
+#pragma unroll
+      for (int c = 0; c < FF_CHUNK; ++c) {
+        if (c0 + c < nrhs) {
+          double2 uj = u[j + (int64_t)(c0 + c) * N], qj = q[j + (int64_t)(c0 + c) * N];
+          // -i xn u - eps0 q
+          double2 t = make_double2(xn * uj.y - eps0 * qj.x, -xn * uj.x - eps0 * qj.y);
+          acc[c].x += wj * (t.x * e.x - t.y * e.y);
+          acc[c].y += wj * (t.x * e.y + t.y * e.x);
+        }
+      }
+    }
+    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+#pragma unroll
+    for (int c = 0; c < FF_CHUNK; ++c) {
+      double2 v = acc[c];
+      for (int o = 16; o > 0; o >>= 1) {
+        v.x += __shfl_xor_sync(0xffffffffu, v.x, o);
+        v.y += __shfl_xor_sync(0xffffffffu, v.y, o);
+      }
+      if (lane == 0) red[c][wp] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < FF_CHUNK && c0 + threadIdx.x < nrhs) {
+      double2 v = make_double2(0.0, 0.0);
+      for (int k = 0; k < 256 / 32; ++k) {
+        v.x += red[threadIdx.x][k].x;
+        v.y += red[threadIdx.x][k].y;
+      }
+      out[a + (int64_t)(c0 + threadIdx.x) * nang] =
+          make_double2(pref.x * v.x - pref.y * v.y, pref.x * v.y + pref.y * v.x);
+    }
+    __syncthreads();
+  }
+}
+
+// ------------------------------------------------------------------ host helpers ----
+static int gridfor(int64_t work, int per = 256) {
+  int64_t b = (work + per - 1) / per;
+  if (b < 1) b = 1;
+  if (b > 152 * 16) b = 152 * 16;
+  return (int)b;
+}
+
+template <class T>
+static int upload(wsbm_hss* h, const std::vector<T>& v, T** d, std::vector<void*>& tmp) {
+  *d = nullptr;
+  if (v.empty()) return WSBM_OK;
+  if (cudaMallocAsync((void**)d, v.size() * sizeof(T), h->st) != cudaSuccess) return WSBM_ERR_OOM;
+  tmp.push_back(*d);
+  if (cudaMemcpyAsync(*d, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, h->st) != cudaSuccess)
+    return WSBM_ERR_CUDA;
+  return WSBM_OK;
+}
+
+static int dalloc(wsbm_hss* h, size_t bytes, void** p, std::vector<void*>& list) {
+  *p = nullptr;
+  if (bytes == 0) bytes = 16;
+  if (cudaMallocAsync(p, bytes, h->st) != cudaSuccess) return WSBM_ERR_OOM;
+  list.push_back(*p);
+  return WSBM_OK;
+}
+
+static void free_list(wsbm_hss* h, std::vector<void*>& list) {
+  for (void* p : list) cudaFreeAsync(p, h->st);
+  list.clear();
+}
+
+// Slots (node, two output positions) for a list of interleaved unknowns placed at output
+// positions base + t.
+static void make_slots(const std::vector<int32_t>& U, int base, std::vector<int32_t>& nodes,
+                       std::vector<int32_t>& pos) {
+  std::unordered_map<int32_t, int32_t> at;
+  at.reserve(U.size() * 2);
+  for (size_t t = 0; t < U.size(); ++t) {
+    int32_t node = U[t] >> 1, comp = U[t] & 1;
+    auto it = at.find(node);
+    int32_t s;
+    if (it == at.end()) {
+      s = (int32_t)nodes.size();
+      at.emplace(node, s);
+      nodes.push_back(node);
+      pos.push_back(-1);
+      pos.push_back(-1);
+    } else {
+      s = it->second;
+    }
+    pos[2 * (size_t)s + comp] = base + (int32_t)t;
+  }
+}
+
+// A flat list of pair tasks for one launch; slot arrays are concatenated and uploaded once.
+struct PairBatch {
+  std::vector<PairTask> tasks;
+  std::vector<int32_t> ints;  // slot data
+  struct Ref {
+    int64_t rn, rp, cn, cp;
+  };
+  std::vector<Ref> refs;
+  int64_t tiles = 0, entries = 0, pairs = 0;
+
+  void add(const std::vector<int32_t>& rowU, int rbase, const std::vector<int32_t>& colU, int cbase,
+           double2* out, int64_t ld, int trans) {
+    if (rowU.empty() || colU.empty()) return;
+    std::vector<int32_t> rn, rp, cn, cp;
+    make_slots(rowU, rbase, rn, rp);
+    make_slots(colU, cbase, cn, cp);
+    Ref r;
+    r.rn = (int64_t)ints.size();
+    ints.insert(ints.end(), rn.begin(), rn.end());
+    r.rp = (int64_t)ints.size();
+    ints.insert(ints.end(), rp.begin(), rp.end());
+    r.cn = (int64_t)ints.size();
+    ints.insert(ints.end(), cn.begin(), cn.end());
+    r.cp = (int64_t)ints.size();
+    ints.insert(ints.end(), cp.begin(), cp.end());
+    refs.push_back(r);
+    PairTask t;
+    memset(&t, 0, sizeof(t));
+    t.out = out;
+    t.ld = ld;
+    t.nr = (int32_t)rn.size();
+    t.nc = (int32_t)cn.size();
+    t.trans = trans;
+    t.tile0 = (int32_t)tiles;
+    tiles += wsbm_pair_tiles(t.nr, t.nc, trans);
+    entries += (int64_t)rowU.size() * colU.size();
+    pairs += (int64_t)rn.size() * cn.size();
+    tasks.push_back(t);
+  }
+
+  int launch(wsbm_hss* h, std::vector<void*>& tmp) {
+    if (tasks.empty()) return WSBM_OK;
+    int32_t* dints = nullptr;
+    HK(upload(h, ints, &dints, tmp));
+    for (size_t i = 0; i < tasks.size(); ++i) {
+      tasks[i].rnode = dints + refs[i].rn;
+      tasks[i].rpos = dints + refs[i].rp;
+      tasks[i].cnode = dints + refs[i].cn;
+      tasks[i].cpos = dints + refs[i].cp;
+    }
+    PairTask* dt = nullptr;
+    HK(upload(h, tasks, &dt, tmp));
+    return wsbm_launch_pairs(h->g, h->ph, dt, (int)tasks.size(), tiles, h->st);
+  }
+};
+
+struct ProxyBatch {
+  std::vector<ProxyTask> tasks;
+  std::vector<int32_t> ints;
+  std::vector<std::pair<int64_t, int64_t>> refs;
+  int64_t tiles = 0, entries = 0, pairs = 0;
+
+  void add(const std::vector<int32_t>& U, const Box& b, int side, double2* out, int64_t ld) {
+    std::vector<int32_t> nn, pp;
+    make_slots(U, 0, nn, pp);
+    refs.push_back({(int64_t)ints.size(), (int64_t)ints.size() + (int64_t)nn.size()});
+    ints.insert(ints.end(), nn.begin(), nn.end());
+    ints.insert(ints.end(), pp.begin(), pp.end());
+    ProxyTask t;
+    memset(&t, 0, sizeof(t));
+    t.out = out;
+    t.ld = ld;
+    t.cx = b.cx;
+    t.cy = b.cy;
+    t.rho = b.rho;
+    t.nn = (int32_t)nn.size();
+    t.P = b.P;
+    t.side = side;
+    t.tr = 0;
+    t.off = 0;
+    t.tile0 = (int32_t)tiles;
+    tiles += wsbm_proxy_tiles(t.nn, t.P);
+    entries += (int64_t)U.size() * 2 * b.P;
+    pairs += (int64_t)nn.size() * b.P;
+    tasks.push_back(t);
+  }
+
+  int launch(wsbm_hss* h, std::vector<void*>& tmp) {
+    if (tasks.empty()) return WSBM_OK;
+    int32_t* dints = nullptr;
+    HK(upload(h, ints, &dints, tmp));
+    for (size_t i = 0; i < tasks.size(); ++i) {
+      tasks[i].node = dints + refs[i].first;
+      tasks[i].pos = dints + refs[i].second;
+    }
+    ProxyTask* dt = nullptr;
+    HK(upload(h, tasks, &dt, tmp));
+    return wsbm_launch_proxy(h->g, h->ph, dt, (int)tasks.size(), tiles,
+                             h->prm.precision == WSBM_MIXED, h->st);
+  }
+};
+
+static void box_circle(const wsbm_hss* h, Box& b) {
+  double xmin = h->hx[b.lo], xmax = xmin, ymin = h->hy[b.lo], ymax = ymin;
+  for (int64_t i = b.lo + 1; i < b.hi; ++i) {
+    double a = h->hx[i], c = h->hy[i];
+    if (a < xmin) xmin = a;
+    if (a > xmax) xmax = a;
+    if (c < ymin) ymin = c;
+    if (c > ymax) ymax = c;
+  }
+  b.cx = 0.5 * (xmin + xmax);
+  b.cy = 0.5 * (ymin + ymax);
+  double R = 0.0;
+  for (int64_t i = b.lo; i < b.hi; ++i) {
+    double dx = h->hx[i] - b.cx, dy = h->hy[i] - b.cy;
+    double d = sqrt(dx * dx + dy * dy);
+    if (d > R) R = d;
+  }
+  b.R = R;
+  b.rho = h->prm.proxy_ratio * R;
+  // proxy count: the leaf value, grown so the circle resolves k1 rho plus enough evanescent
+  // modes for the cutoff (modes decay like (R/rho)^m)
+  double need = 2.0 * (h->ph.k1 * b.rho + log(1.0 / h->cut) / log(h->prm.proxy_ratio));
+  int P = (int)ceil(need);
+  if (P < h->prm.nproxy) P = h->prm.nproxy;
+  P = (P + 7) / 8 * 8;
+  b.P = P;
+}
+
+static double elapsed(cudaEvent_t a, cudaEvent_t b) {
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, a, b);
+  return ms;
+}
+
+// -------------------------------------------------------------------------- create ----
+extern "C" int wsbm_create(const wsbm_geom* g, const wsbm_params* p, void* stream, wsbm_hss_t* out) {
+  if (!out) return WSBM_ERR_INVALID_ARG;
+  *out = nullptr;
+  int rc = wsbm_geom_check(g);
+  if (rc) return rc;
+  Phys ph;
+  if ((rc = wsbm_phys_from_params(p, &ph))) return rc;
+  if (p->leaf < 4 || p->nproxy < 8 || !(p->id_tol > 0.0) || !(p->id_tol < 1.0)) return WSBM_ERR_INVALID_ARG;
+  if (p->precision != WSBM_FP64 && p->precision != WSBM_MIXED) return WSBM_ERR_INVALID_ARG;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev <= 0) return WSBM_ERR_NO_DEVICE;
+  wsbm_hss* h = new wsbm_hss();
+  cudaGetDevice(&h->dev);
+  h->st = (cudaStream_t)stream;
+  h->N = g->n;
+  h->ph = ph;
+  h->prm = *p;
+  if (!(h->prm.proxy_ratio > 1.0)) h->prm.proxy_ratio = 1.5;
+  h->cut = p->id_tol / 4.0;
+  memset(&h->stats, 0, sizeof(h->stats));
+  for (int i = 0; i < 6; ++i) cudaEventCreate(&h->ev[i]);
+  size_t bytes = (size_t)h->N * sizeof(double);
+  double** dst[6] = {&h->x, &h->y, &h->nx, &h->ny, &h->w, &h->kappa};
+  const double* src[6] = {g->x, g->y, g->nx, g->ny, g->w, g->kappa};
+  for (int a = 0; a < 6; ++a) {
+    if (cudaMalloc((void**)dst[a], bytes) != cudaSuccess) {
+      wsbm_destroy(h);
+      return WSBM_ERR_OOM;
+    }
+    if (cudaMemcpyAsync(*dst[a], src[a], bytes, cudaMemcpyDeviceToDevice, h->st) != cudaSuccess) {
+      wsbm_destroy(h);
+      return WSBM_ERR_CUDA;
+    }
+  }
+  h->hx.resize(h->N);
+  h->hy.resize(h->N);
+  h->hw.resize(h->N);
+  std::vector<double> hk(h->N), hnx(h->N), hny(h->N);
+  cudaMemcpyAsync(h->hx.data(), g->x, bytes, cudaMemcpyDeviceToHost, h->st);
+  cudaMemcpyAsync(h->hy.data(), g->y, bytes, cudaMemcpyDeviceToHost, h->st);
+  cudaMemcpyAsync(h->hw.data(), g->w, bytes, cudaMemcpyDeviceToHost, h->st);
+  cudaMemcpyAsync(hnx.data(), g->nx, bytes, cudaMemcpyDeviceToHost, h->st);
+  cudaMemcpyAsync(hny.data(), g->ny, bytes, cudaMemcpyDeviceToHost, h->st);
+  cudaMemcpyAsync(hk.data(), g->kappa, bytes, cudaMemcpyDeviceToHost, h->st);
+  if (cudaStreamSynchronize(h->st) != cudaSuccess) {
+    wsbm_destroy(h);
+    return WSBM_ERR_CUDA;
+  }
+  for (int64_t i = 0; i < h->N; ++i) {
+    if (!isfinite(h->hx[i]) || !isfinite(h->hy[i]) || !isfinite(h->hw[i]) || !isfinite(hk[i]) ||
+        !isfinite(hnx[i]) || !isfinite(hny[i]) || !(h->hw[i] > 0.0)) {
+      wsbm_destroy(h);
+      return WSBM_ERR_INVALID_ARG;
+    }
+  }
+  h->g.x = h->x;
+  h->g.y = h->y;
+  h->g.nx = h->nx;
+  h->g.ny = h->ny;
+  h->g.w = h->w;
+  h->g.kappa = h->kappa;
+  h->g.n = h->N;
+  // tree: perfect binary tree over contiguous node ranges
+  int L = 0;
+  while (((h->N) >> L) > p->leaf && L < 24) ++L;
+  if (L > 0 && (h->N >> L) < 2) --L;
+  h->L = L;
+  h->lv.resize(L + 1);
+  for (int l = 0; l <= L; ++l) {
+    int nb = 1 << l;
+    h->lv[l].box.resize(nb);
+    for (int b = 0; b < nb; ++b) {
+      Box& bx = h->lv[l].box[b];
+      bx.lo = (int64_t)((__int128)b * h->N / nb);
+      bx.hi = (int64_t)((__int128)(b + 1) * h->N / nb);
+      box_circle(h, bx);
+    }
+  }
+  h->stats.levels = L;
+  h->stats.nboxes_leaf = 1 << L;
+  *out = h;
+  return WSBM_OK;
+}
+
+static void release_factors(wsbm_hss* h) {
+  free_list(h, h->owned);
+  for (auto& l : h->lv)
+    for (auto& b : l.box) {
+      b.D = b.Z = b.Dc = b.Tc = nullptr;
+      b.piv = b.pc = nullptr;
+      b.k = b.n = 0;
+      b.cr.clear();
+      b.cc.clear();
+      b.Jr.clear();
+      b.Jc.clear();
+      b.near.clear();
+    }
+  h->root = nullptr;
+  h->root_piv = nullptr;
+  h->root_n = 0;
+  h->factored = false;
+}
+
+extern "C" void wsbm_destroy(wsbm_hss_t h) {
+  if (!h) return;
+  if (h->st || true) {
+    release_factors(h);
+    cudaStreamSynchronize(h->st);
+  }
+  double* arr[6] = {h->x, h->y, h->nx, h->ny, h->w, h->kappa};
+  for (double* a : arr)
+    if (a) cudaFree(a);
+  for (int i = 0; i < 6; ++i)
+    if (h->ev[i]) cudaEventDestroy(h->ev[i]);
+  delete h;
+}
+
+// ---------------------------------------------------------------------- one level ----
+// Compress and factor every box of level l.  Candidates (cr, cc) must be set.
+static int factor_level(wsbm_hss* h, int l) {
+  Level& LV = h->lv[l];
+  const int nb = (int)LV.box.size();
+  std::vector<void*> tmp;
+  cudaStream_t st = h->st;
+  // ---- near lists: boxes with a candidate node inside the proxy circle, and curve neighbours
+  for (int b = 0; b < nb; ++b) {
+    Box& B = LV.box[b];
+    B.near.clear();
+    for (int s = 0; s < nb; ++s) {
+      if (s == b) continue;
+      bool nb_adj = (s == (b + 1) % nb) || (s == (b + nb - 1) % nb);
+      bool inside = false;
+      if (!nb_adj) {
+        const Box& S = LV.box[s];
+        for (size_t t = 0; t < S.cr.size() && !inside; ++t) {
+          int32_t node = S.cr[t] >> 1;
+          double dx = h->hx[node] - B.cx, dy = h->hy[node] - B.cy;
+          if (dx * dx + dy * dy < B.rho * B.rho) inside = true;
+        }
+        for (size_t t = 0; t < S.cc.size() && !inside; ++t) {
+          int32_t node = S.cc[t] >> 1;
+          double dx = h->hx[node] - B.cx, dy = h->hy[node] - B.cy;
+          if (dx * dx + dy * dy < B.rho * B.rho) inside = true;
+        }
+      }
+      if (nb_adj || inside) B.near.push_back(s);
+    }
+  }
+  // ---- storage: D (factor, kept), ID matrices (temporary)
+  std::vector<int64_t> mr(nb), mc(nb);
+  size_t Dtot = 0, Mtot = 0, ntot = 0;
+  int maxn = 0;
+  for (int b = 0; b < nb; ++b) {
+    Box& B = LV.box[b];
+    B.n = (int)B.cr.size();
+    int64_t nearr = 0, nearc = 0;
+    for (int s : B.near) {
+      nearc += (int64_t)LV.box[s].cc.size();
+      nearr += (int64_t)LV.box[s].cr.size();
+    }
+    mr[b] = 2 * (int64_t)B.P + nearc;
+    mc[b] = 2 * (int64_t)B.P + nearr;
+    Dtot += (size_t)B.n * B.n;
+    Mtot += (size_t)(mr[b] + mc[b]) * B.n;
+    ntot += B.n;
+    maxn = std::max(maxn, B.n);
+  }
+  double2 *Dall = nullptr, *Mall = nullptr;
+  int32_t* pivall = nullptr;
+  HK(dalloc(h, Dtot * sizeof(double2), (void**)&Dall, h->owned));
+  HK(dalloc(h, ntot * sizeof(int32_t), (void**)&pivall, h->owned));
+  HK(dalloc(h, Mtot * sizeof(double2), (void**)&Mall, tmp));
+  std::vector<double2*> Mr(nb), Mc(nb);
+  {
+    size_t o = 0, oM = 0, on = 0;
+    for (int b = 0; b < nb; ++b) {
+      Box& B = LV.box[b];
+      B.D = Dall + o;
+      B.piv = pivall + on;
+      o += (size_t)B.n * B.n;
+      on += B.n;
+      Mr[b] = Mall + oM;
+      oM += (size_t)mr[b] * B.n;
+      Mc[b] = Mall + oM;
+      oM += (size_t)mc[b] * B.n;
+    }
+  }
+  // ---- entries: diagonal blocks (leaf) or sibling blocks (upper), near blocks, proxy blocks
+  HC(cudaEventRecord(h->ev[0], st));
+  PairBatch pb;
+  std::vector<CopyDesc> copies;
+  for (int b = 0; b < nb; ++b) {
+    Box& B = LV.box[b];
+    if (l == h->L) {
+      pb.add(B.cr, 0, B.cc, 0, B.D, B.n, 0);
+    } else {
+      Box& A1 = h->lv[l + 1].box[2 * b];
+      Box& A2 = h->lv[l + 1].box[2 * b + 1];
+      int ka = A1.k, kb = A2.k;
+      pb.add(A1.Jr, 0, A2.Jc, ka, B.D, B.n, 0);
+      pb.add(A2.Jr, ka, A1.Jc, 0, B.D, B.n, 0);
+      CopyDesc c1 = {B.D, A1.Dc, B.n, ka, ka, ka};
+      CopyDesc c2 = {B.D + ka + (int64_t)ka * B.n, A2.Dc, B.n, kb, kb, kb};
+      copies.push_back(c1);
+      copies.push_back(c2);
+    }
+    // near blocks: row ID matrix (transposed: rows = near columns), column ID matrix
+    int64_t offr = 2 * (int64_t)B.P, offc = 2 * (int64_t)B.P;
+    for (int s : B.near) {
+      Box& S = LV.box[s];
+      pb.add(B.cr, 0, S.cc, (int)offr, Mr[b], mr[b], 1);
+      offr += (int64_t)S.cc.size();
+      pb.add(S.cr, (int)offc, B.cc, 0, Mc[b], mc[b], 0);
+      offc += (int64_t)S.cr.size();
+    }
+  }
+  ProxyBatch xb;
+  for (int b = 0; b < nb; ++b) {
+    Box& B = LV.box[b];
+    xb.add(B.cr, B, 0, Mr[b], mr[b]);
+    xb.add(B.cc, B, 1, Mc[b], mc[b]);
+  }
+  if (!copies.empty()) {
+    CopyDesc* dc = nullptr;
+    HK(upload(h, copies, &dc, tmp));
+    int64_t mx = 0;
+    for (auto& c : copies) mx = std::max(mx, (int64_t)c.m * c.n);
+    k_copy2d<<<dim3(gridfor(mx), (unsigned)copies.size()), 256, 0, st>>>(dc);
+    wsbm_count_launch();
+  }
+  HK(pb.launch(h, tmp));
+  HC(cudaEventRecord(h->ev[4], st));
+  HK(xb.launch(h, tmp));
+  HC(cudaEventRecord(h->ev[1], st));
+  h->stats.entries_generated += pb.entries + xb.entries;
+  h->stats.pairs_evaluated += pb.pairs + xb.pairs;
+  h->stats.entries_pairs += pb.entries;
+  h->stats.pairs_pairs += pb.pairs;
+  h->stats.entries_proxy += xb.entries;
+  h->stats.pairs_proxy += xb.pairs;
+  // ---- interpolative decompositions: CPQR of Mr (row ID) and Mc (column ID) of every box
+  std::vector<QrDesc> qd(2 * nb);
+  int32_t *perm = nullptr, *state = nullptr;
+  double *norm2 = nullptr, *tauv = nullptr, *rd0 = nullptr;
+  double2* betav = nullptr;
+  HK(dalloc(h, 2 * ntot * sizeof(int32_t), (void**)&perm, tmp));
+  HK(dalloc(h, 2 * nb * 2 * sizeof(int32_t), (void**)&state, tmp));
+  HK(dalloc(h, 2 * ntot * sizeof(double), (void**)&norm2, tmp));
+  HK(dalloc(h, 2 * ntot * sizeof(double), (void**)&tauv, tmp));
+  HK(dalloc(h, 2 * ntot * sizeof(double2), (void**)&betav, tmp));
+  HK(dalloc(h, 2 * nb * sizeof(double), (void**)&rd0, tmp));
+  HC(cudaMemsetAsync(state, 0, 2 * nb * 2 * sizeof(int32_t), st));
+  {
+    size_t on = 0;
+    for (int b = 0; b < nb; ++b)
+      for (int s = 0; s < 2; ++s) {
+        QrDesc& q = qd[2 * b + s];
+        memset(&q, 0, sizeof(q));
+        q.A = s == 0 ? Mr[b] : Mc[b];
+        q.lda = s == 0 ? mr[b] : mc[b];
+        q.m = (int32_t)q.lda;
+        q.n = LV.box[b].n;
+        q.tol = h->cut;
+        q.perm = perm + on;
+        q.norm2 = norm2 + on;
+        q.tauv = tauv + on;
+        q.betav = betav + on;
+        q.state = state + 2 * (2 * b + s);
+        q.rdiag0 = rd0 + (2 * b + s);
+        on += q.n;
+      }
+  }
+  QrDesc* dq = nullptr;
+  HK(upload(h, qd, &dq, tmp));
+  HK(wsbm_cpqr_batched(dq, 2 * nb, 0, st));
+  std::vector<int32_t> hstate(4 * nb);
+  HC(cudaMemcpyAsync(hstate.data(), state, hstate.size() * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+  HC(cudaStreamSynchronize(st));
+  std::vector<QrDesc> more;
+  for (int b = 0; b < nb; ++b) {
+    Box& B = LV.box[b];
+    int kr = hstate[4 * b + 1], kc = hstate[4 * b + 3];
+    int k = std::max(std::max(kr, kc), 1);
+    k = std::min(k, B.n);
+    B.k = k;
+    for (int s = 0; s < 2; ++s) {
+      int ks = s == 0 ? kr : kc;
+      if (ks < k) {
+        QrDesc q = qd[2 * b + s];
+        q.kt = k;
+        more.push_back(q);
+      }
+    }
+  }
+  if (!more.empty()) {
+    QrDesc* dm = nullptr;
+    HK(upload(h, more, &dm, tmp));
+    HK(wsbm_cpqr_batched(dm, (int)more.size(), 1, st));
+  }
+  HK(wsbm_cpqr_finish(dq, 2 * nb, st));
+  // T = R11^-1 R12 in place (both sides)
+  {
+    std::vector<TrsmDesc> td;
+    int mk = 0, mrhs = 0;
+    for (int b = 0; b < nb; ++b)
+      for (int s = 0; s < 2; ++s) {
+        Box& B = LV.box[b];
+        TrsmDesc t;
+        memset(&t, 0, sizeof(t));
+        t.T = qd[2 * b + s].A;
+        t.ldt = qd[2 * b + s].lda;
+        t.B = qd[2 * b + s].A + (int64_t)B.k * t.ldt;
+        t.ldb = t.ldt;
+        t.n = B.k;
+        t.nrhs = B.n - B.k;
+        mk = std::max(mk, t.n);
+        mrhs = std::max(mrhs, t.nrhs);
+        td.push_back(t);
+      }
+    TrsmDesc* dtd = nullptr;
+    HK(upload(h, td, &dtd, tmp));
+    HK(wsbm_trsm_batched(dtd, (int)td.size(), mk, mrhs, 0, st));
+  }
+  std::vector<int32_t> hperm(2 * ntot);
+  HC(cudaMemcpyAsync(hperm.data(), perm, hperm.size() * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+  HC(cudaEventRecord(h->ev[2], st));
+  // ---- factor: LU(D), Z = D^-1 L, M = R Z, Dhat = M^-1
+  size_t Ztot = 0, Ktot = 0, Ttot = 0;
+  int maxk = 0;
+  for (int b = 0; b < nb; ++b) {
+    Box& B = LV.box[b];
+    Ztot += (size_t)B.n * B.k;
+    Ktot += (size_t)B.k * B.k;
+    Ttot += (size_t)B.k * (B.n - B.k);
+    maxk = std::max(maxk, B.k);
+  }
+  double2 *Zall = nullptr, *Dcall = nullptr, *Tcall = nullptr, *Mall2 = nullptr, *Zp = nullptr;
+  int32_t *pcall = nullptr, *pivM = nullptr;
+  HK(dalloc(h, Ztot * sizeof(double2), (void**)&Zall, h->owned));
+  HK(dalloc(h, Ktot * sizeof(double2), (void**)&Dcall, h->owned));
+  HK(dalloc(h, Ttot * sizeof(double2), (void**)&Tcall, h->owned));
+  HK(dalloc(h, ntot * sizeof(int32_t), (void**)&pcall, h->owned));
+  HK(dalloc(h, Ktot * sizeof(double2), (void**)&Mall2, tmp));
+  HK(dalloc(h, Ztot * sizeof(double2), (void**)&Zp, tmp));
+  HK(dalloc(h, ntot * sizeof(int32_t), (void**)&pivM, tmp));
+  std::vector<LuDesc> luD, luM;
+  std::vector<BuildLDesc> bl;
+  std::vector<TrsmDesc> zl, zu, ml, mu;
+  std::vector<GatherDesc> gz;
+  std::vector<GemmDesc> gm;
+  std::vector<CopyDesc> tcc, pcopy;
+  {
+    size_t oz = 0, ok = 0, ot = 0, on = 0;
+    for (int b = 0; b < nb; ++b) {
+      Box& B = LV.box[b];
+      const int n = B.n, k = B.k;
+      B.Z = Zall + oz;
+      B.Dc = Dcall + ok;
+      B.Tc = Tcall + ot;
+      B.pc = pcall + on;
+      double2* M = Mall2 + ok;
+      double2* Zg = Zp + oz;
+      int32_t* pM = pivM + on;
+      oz += (size_t)n * k;
+      ok += (size_t)k * k;
+      ot += (size_t)k * (n - k);
+      on += n;
+      luD.push_back({B.D, n, B.piv, n, 0});
+      const QrDesc& qr = qd[2 * b];
+      const QrDesc& qc = qd[2 * b + 1];
+      bl.push_back({B.Z, qr.A + (int64_t)k * qr.lda, qr.perm, qr.lda, n, k});
+      TrsmDesc t;
+      memset(&t, 0, sizeof(t));
+      t.T = B.D;
+      t.ldt = n;
+      t.B = B.Z;
+      t.ldb = n;
+      t.piv = B.piv;
+      t.n = n;
+      t.nrhs = k;
+      zl.push_back(t);
+      zu.push_back(t);
+      // Zg = Z[pc, :]
+      gz.push_back({Zg, B.Z, qc.perm, n, n, n, k});
+      // M = Zg[0:k, :] + Tc Zg[k:n, :]
+      pcopy.push_back({M, Zg, k, n, k, k});
+      if (n > k) {
+        GemmDesc gd;
+        memset(&gd, 0, sizeof(gd));
+        gd.A = qc.A + (int64_t)k * qc.lda;
+        gd.lda = qc.lda;
+        gd.B = Zg + k;
+        gd.ldb = n;
+        gd.C = M;
+        gd.ldc = k;
+        gd.m = k;
+        gd.n = k;
+        gd.k = n - k;
+        gd.alpha = make_double2(1.0, 0.0);
+        gd.beta = make_double2(1.0, 0.0);
+        gm.push_back(gd);
+        tcc.push_back({B.Tc, qc.A + (int64_t)k * qc.lda, k, qc.lda, k, n - k});
+      }
+      luM.push_back({M, k, pM, k, 0});
+      TrsmDesc tm;
+      memset(&tm, 0, sizeof(tm));
+      tm.T = M;
+      tm.ldt = k;
+      tm.B = B.Dc;
+      tm.ldb = k;
+      tm.piv = pM;
+      tm.n = k;
+      tm.nrhs = k;
+      ml.push_back(tm);
+      mu.push_back(tm);
+    }
+  }
+  LuDesc *dluD = nullptr, *dluM = nullptr;
+  BuildLDesc* dbl = nullptr;
+  TrsmDesc *dzl = nullptr, *dml = nullptr;
+  GatherDesc* dgz = nullptr;
+  GemmDesc* dgm = nullptr;
+  CopyDesc *dtcc = nullptr, *dpc = nullptr;
+  HK(upload(h, luD, &dluD, tmp));
+  HK(upload(h, luM, &dluM, tmp));
+  HK(upload(h, bl, &dbl, tmp));
+  HK(upload(h, zl, &dzl, tmp));
+  HK(upload(h, ml, &dml, tmp));
+  HK(upload(h, gz, &dgz, tmp));
+  HK(upload(h, gm, &dgm, tmp));
+  HK(upload(h, tcc, &dtcc, tmp));
+  HK(upload(h, pcopy, &dpc, tmp));
+  int64_t maxnk = 0;
+  for (int b = 0; b < nb; ++b) maxnk = std::max(maxnk, (int64_t)LV.box[b].n * LV.box[b].k);
+  HK(wsbm_lu_batched(dluD, nb, maxn, nullptr, st));
+  k_build_L<<<dim3(gridfor(maxnk), nb), 256, 0, st>>>(dbl);
+  wsbm_count_launch();
+  HK(wsbm_lu_solve_batched(dzl, dzl, nb, maxn, maxk, st));
+  k_gather_rows<<<dim3(gridfor(maxnk), nb), 256, 0, st>>>(dgz);
+  wsbm_count_launch();
+  k_copy2d<<<dim3(gridfor((int64_t)maxk * maxk), nb), 256, 0, st>>>(dpc);
+  wsbm_count_launch();
+  if (!gm.empty()) HK(wsbm_gemm_batched(dgm, (int)gm.size(), maxk, maxk, st));
+  if (!tcc.empty()) { k_copy2d<<<dim3(gridfor(maxnk), (unsigned)tcc.size()), 256, 0, st>>>(dtcc); wsbm_count_launch(); }
+  HK(wsbm_lu_batched(dluM, nb, maxk, nullptr, st));
+  for (int b = 0; b < nb; ++b) {
+    Box& B = LV.box[b];
+    k_fill_identity<<<gridfor((int64_t)B.k * B.k), 256, 0, st>>>(B.Dc, B.k, B.k);
+    wsbm_count_launch();
+  }
+  HK(wsbm_lu_solve_batched(dml, dml, nb, maxk, maxk, st));
+  HC(cudaGetLastError());
+  // column permutations (kept for the solve)
+  {
+    size_t on = 0;
+    for (int b = 0; b < nb; ++b) {
+      Box& B = LV.box[b];
+      HC(cudaMemcpyAsync(B.pc, qd[2 * b + 1].perm, B.n * sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
+      on += B.n;
+    }
+  }
+  HC(cudaEventRecord(h->ev[3], st));
+  HC(cudaStreamSynchronize(st));
+  h->stats.ms_entries += elapsed(h->ev[0], h->ev[1]);
+  h->stats.ms_pairs += elapsed(h->ev[0], h->ev[4]);
+  h->stats.ms_proxy += elapsed(h->ev[4], h->ev[1]);
+  h->stats.ms_id += elapsed(h->ev[1], h->ev[2]);
+  h->stats.ms_factor += elapsed(h->ev[2], h->ev[3]);
+  // skeletons
+  {
+    size_t on = 0;
+    int rmax = 0;
+    for (int b = 0; b < nb; ++b) {
+      Box& B = LV.box[b];
+      const int32_t* pr = hperm.data() + on;
+      on += B.n;
+      const int32_t* pcp = hperm.data() + on;
+      on += B.n;
+      B.Jr.resize(B.k);
+      B.Jc.resize(B.k);
+      for (int t = 0; t < B.k; ++t) {
+        B.Jr[t] = B.cr[pr[t]];
+        B.Jc[t] = B.cc[pcp[t]];
+      }
+      rmax = std::max(rmax, B.k);
+    }
+    h->stats.rank_per_level[l] = rmax;
+    h->stats.max_rank = std::max(h->stats.max_rank, rmax);
+  }
+  LV.compressed = true;
+  free_list(h, tmp);
+  return WSBM_OK;
+}
+
+// Dense root: merge the skeletons of every box of level `top` (all of A when the tree has a
+// single box).
+static int factor_root(wsbm_hss* h) {
+  std::vector<void*> tmp;
+  cudaStream_t st = h->st;
+  std::vector<int32_t> Rr, Rc;
+  std::vector<int> off;
+  if (h->L == 0) {
+    for (int64_t u = 0; u < 2 * h->N; ++u) {
+      Rr.push_back((int32_t)u);
+      Rc.push_back((int32_t)u);
+    }
+  } else {
+    Level& T = h->lv[h->top];
+    for (auto& b : T.box) {
+      off.push_back((int)Rr.size());
+      Rr.insert(Rr.end(), b.Jr.begin(), b.Jr.end());
+      Rc.insert(Rc.end(), b.Jc.begin(), b.Jc.end());
+    }
+  }
+  const int n = (int)Rr.size();
+  h->root_n = n;
+  h->stats.root_size = n;
+  HK(dalloc(h, (size_t)n * n * sizeof(double2), (void**)&h->root, h->owned));
+  HK(dalloc(h, (size_t)n * sizeof(int32_t), (void**)&h->root_piv, h->owned));
+  HC(cudaEventRecord(h->ev[0], st));
+  PairBatch pb;
+  std::vector<CopyDesc> copies;
+  if (h->L == 0) {
+    pb.add(Rr, 0, Rc, 0, h->root, n, 0);
+  } else {
+    Level& T = h->lv[h->top];
+    int nb = (int)T.box.size();
+    for (int a = 0; a < nb; ++a) {
+      Box& A = T.box[a];
+      copies.push_back({h->root + off[a] + (int64_t)off[a] * n, A.Dc, n, A.k, A.k, A.k});
+      for (int b = 0; b < nb; ++b) {
+        if (a == b) continue;
+        pb.add(A.Jr, off[a], T.box[b].Jc, off[b], h->root, n, 0);
+      }
+    }
+  }
+  if (!copies.empty()) {
+    CopyDesc* dc = nullptr;
+    HK(upload(h, copies, &dc, tmp));
+    int64_t mx = 0;
+    for (auto& c : copies) mx = std::max(mx, (int64_t)c.m * c.n);
+    k_copy2d<<<dim3(gridfor(mx), (unsigned)copies.size()), 256, 0, st>>>(dc);
+    wsbm_count_launch();
+  }
+  HK(pb.launch(h, tmp));
+  HC(cudaEventRecord(h->ev[1], st));
+  h->stats.entries_generated += pb.entries;
+  h->stats.pairs_evaluated += pb.pairs;
+  LuDesc ld = {h->root, n, h->root_piv, n, 0};
+  std::vector<LuDesc> v(1, ld);
+  LuDesc* dl = nullptr;
+  HK(upload(h, v, &dl, tmp));
+  HK(wsbm_lu_batched(dl, 1, n, nullptr, st));
+  HC(cudaEventRecord(h->ev[2], st));
+  HC(cudaStreamSynchronize(st));
+  h->stats.ms_entries += elapsed(h->ev[0], h->ev[1]);
+  h->stats.ms_pairs += elapsed(h->ev[0], h->ev[1]);
+  h->stats.entries_pairs += pb.entries;
+  h->stats.pairs_pairs += pb.pairs;
+  h->stats.ms_factor += elapsed(h->ev[1], h->ev[2]);
+  free_list(h, tmp);
+  return WSBM_OK;
+}
+
+extern "C" int wsbm_factor(wsbm_hss_t h) {
+  if (!h) return WSBM_ERR_INVALID_ARG;
+  release_factors(h);
+  int32_t lev = h->stats.levels, nbl = h->stats.nboxes_leaf;
+  memset(&h->stats, 0, sizeof(h->stats));
+  h->stats.levels = lev;
+  h->stats.nboxes_leaf = nbl;
+  cudaEvent_t t0, t1;
+  cudaEventCreate(&t0);
+  cudaEventCreate(&t1);
+  cudaEventRecord(t0, h->st);
+  const int64_t launches0 = wsbm_launch_count();
+  int rc = WSBM_OK;
+  h->top = h->L;
+  if (h->L > 0) {
+    // leaf candidates: all unknowns of each box, interleaved
+    for (auto& b : h->lv[h->L].box) {
+      for (int64_t i = b.lo; i < b.hi; ++i) {
+        b.cr.push_back((int32_t)(2 * i));
+        b.cr.push_back((int32_t)(2 * i + 1));
+      }
+      b.cc = b.cr;
+    }
+    const int root_cap = h->prm.root_cap > 0 ? h->prm.root_cap : 40000;
+    int done = 0;
+    for (int l = h->L; l >= 1; --l) {
+      rc = factor_level(h, l);
+      if (rc) break;
+      h->top = l;
+      ++done;
+      if (l == 1) break;
+      if (h->prm.max_levels > 0 && done >= h->prm.max_levels) break;
+      // candidates of the parents
+      int64_t Scur = 0, Snext = 0;
+      int nmax = 0;
+      for (auto& b : h->lv[l].box) {
+        Scur += b.n;
+        Snext += b.k;
+      }
+      for (int p = 0; p < (1 << (l - 1)); ++p) {
+        Box& P = h->lv[l - 1].box[p];
+        Box& A = h->lv[l].box[2 * p];
+        Box& B = h->lv[l].box[2 * p + 1];
+        P.cr = A.Jr;
+        P.cr.insert(P.cr.end(), B.Jr.begin(), B.Jr.end());
+        P.cc = A.Jc;
+        P.cc.insert(P.cc.end(), B.Jc.begin(), B.Jc.end());
+        nmax = std::max(nmax, (int)P.cr.size());
+      }
+      // stop compressing when it no longer pays (high-frequency boxes keep most unknowns) and
+      // the merged system fits the root, or when the next level's boxes would be too large
+      // for one-CTA column-pivoted QR
+      if ((Snext > 0.8 * (double)Scur && Snext <= root_cap) || nmax > 3072) break;
+    }
+    if (!rc && h->prm.max_levels <= 0) {
+      int64_t S = 0;
+      for (auto& b : h->lv[h->top].box) S += b.k;
+      if (S > root_cap) rc = WSBM_ERR_RANK_OVERFLOW;
+    }
+  }
+  bool partial = h->L > 0 && h->prm.max_levels > 0;
+  if (!rc && !partial) rc = factor_root(h);
+  cudaEventRecord(t1, h->st);
+  cudaEventSynchronize(t1);
+  h->stats.ms_total_factor = elapsed(t0, t1);
+  h->stats.launches = wsbm_launch_count() - launches0;
+  cudaEventDestroy(t0);
+  cudaEventDestroy(t1);
+  if (rc) {
+    int32_t keep[32];
+    memcpy(keep, h->stats.rank_per_level, sizeof(keep));
+    release_factors(h);
+    memcpy(h->stats.rank_per_level, keep, sizeof(keep));  // kept for diagnosis
+    return rc;
+  }
+  size_t bytes = 0;
+  for (int l = h->top; l <= h->L && h->L > 0; ++l)
+    for (auto& b : h->lv[l].box)
+      bytes += ((size_t)b.n * b.n + (size_t)b.n * b.k + (size_t)b.k * b.k + (size_t)b.k * (b.n - b.k)) *
+               sizeof(double2);
+  bytes += (size_t)h->root_n * h->root_n * sizeof(double2);
+  h->stats.factor_bytes = (int64_t)bytes;
+  h->factored = !partial;
+  return WSBM_OK;
+}
+
+// ----------------------------------------------------------------------- solve ----
+extern "C" int wsbm_solve(wsbm_hss_t h, const void* rhs, int32_t nrhs, void* u, void* q) {
+  if (!h) return WSBM_ERR_INVALID_ARG;
+  if (!h->factored) return WSBM_ERR_NOT_FACTORED;
+  if (nrhs < 0 || (nrhs > 0 && (!rhs || !u || !q))) return WSBM_ERR_INVALID_ARG;
+  if (nrhs == 0) return WSBM_OK;
+  cudaStream_t st = h->st;
+  std::vector<void*> tmp;
+  const int64_t N = h->N;
+  double2* bint = nullptr;
+  HK(dalloc(h, (size_t)2 * N * nrhs * sizeof(double2), (void**)&bint, tmp));
+  k_to_interleaved<<<gridfor(2 * N * nrhs), 256, 0, st>>>((const double2*)rhs, bint, N, nrhs);
+  wsbm_count_launch();
+  if (h->L == 0) {
+    TrsmDesc t;
+    memset(&t, 0, sizeof(t));
+    t.T = h->root;
+    t.ldt = h->root_n;
+    t.B = bint;
+    t.ldb = 2 * N;
+    t.piv = h->root_piv;
+    t.n = h->root_n;
+    t.nrhs = nrhs;
+    std::vector<TrsmDesc> v(1, t);
+    TrsmDesc* dt = nullptr;
+    HK(upload(h, v, &dt, tmp));
+    HK(wsbm_lu_solve_batched(dt, dt, 1, h->root_n, nrhs, st));
+    k_split_uq<<<gridfor(N * nrhs), 256, 0, st>>>(bint, (double2*)u, (double2*)q, N, nrhs);
+    wsbm_count_launch();
+    HC(cudaStreamSynchronize(st));
+    free_list(h, tmp);
+    return WSBM_OK;
+  }
+  // per level buffers: bv (n x nrhs), xh (n x nrhs), bt (k x nrhs)
+  const int L = h->L, top = h->top;
+  std::vector<std::vector<double2*>> BV(L + 1), XH(L + 1), BT(L + 1);
+  for (int l = L; l >= top; --l) {
+    Level& LV = h->lv[l];
+    int nb = (int)LV.box.size();
+    BV[l].resize(nb);
+    XH[l].resize(nb);
+    BT[l].resize(nb);
+    size_t tn = 0, tk = 0;
+    for (auto& b : LV.box) {
+      tn += b.n;
+      tk += b.k;
+    }
+    double2 *bv = nullptr, *xh = nullptr, *bt = nullptr;
+    HK(dalloc(h, tn * nrhs * sizeof(double2), (void**)&bv, tmp));
+    HK(dalloc(h, tn * nrhs * sizeof(double2), (void**)&xh, tmp));
+    HK(dalloc(h, tk * nrhs * sizeof(double2), (void**)&bt, tmp));
+    size_t on = 0, ok = 0;
+    for (int b = 0; b < nb; ++b) {
+      BV[l][b] = bv + on * nrhs;
+      XH[l][b] = xh + on * nrhs;
+      BT[l][b] = bt + ok * nrhs;
+      on += LV.box[b].n;
+      ok += LV.box[b].k;
+    }
+  }
+  int maxn = 0, maxk = 0;
+  for (int l = top; l <= L; ++l)
+    for (auto& b : h->lv[l].box) {
+      maxn = std::max(maxn, b.n);
+      maxk = std::max(maxk, b.k);
+    }
+  // ---- upward sweep
+  for (int l = L; l >= top; --l) {
+    Level& LV = h->lv[l];
+    int nb = (int)LV.box.size();
+    // bv = leaf rows of the right-hand side, or the children's bt; then xh = bv
+    std::vector<CopyDesc> c1, c2;
+    for (int b = 0; b < nb; ++b) {
+      Box& B = LV.box[b];
+      if (l == L) {
+        c1.push_back({BV[l][b], bint + 2 * B.lo, B.n, 2 * N, B.n, nrhs});
+      } else {
+        Box& A1 = h->lv[l + 1].box[2 * b];
+        Box& A2 = h->lv[l + 1].box[2 * b + 1];
+        c1.push_back({BV[l][b], BT[l + 1][2 * b], B.n, A1.k, A1.k, nrhs});
+        c1.push_back({BV[l][b] + A1.k, BT[l + 1][2 * b + 1], B.n, A2.k, A2.k, nrhs});
+      }
+      c2.push_back({XH[l][b], BV[l][b], B.n, B.n, B.n, nrhs});
+    }
+    CopyDesc *d1 = nullptr, *d2 = nullptr;
+    HK(upload(h, c1, &d1, tmp));
+    HK(upload(h, c2, &d2, tmp));
+    k_copy2d<<<dim3(gridfor((int64_t)maxn * nrhs), (unsigned)c1.size()), 256, 0, st>>>(d1);
+    wsbm_count_launch();
+    k_copy2d<<<dim3(gridfor((int64_t)maxn * nrhs), (unsigned)c2.size()), 256, 0, st>>>(d2);
+    wsbm_count_launch();
+    // xh = D^-1 bv
+    std::vector<TrsmDesc> sd;
+    for (int b = 0; b < nb; ++b) {
+      Box& B = LV.box[b];
+      TrsmDesc t;
+      memset(&t, 0, sizeof(t));
+      t.T = B.D;
+      t.ldt = B.n;
+      t.B = XH[l][b];
+      t.ldb = B.n;
+      t.piv = B.piv;
+      t.n = B.n;
+      t.nrhs = nrhs;
+      sd.push_back(t);
+    }
+    TrsmDesc* dsd = nullptr;
+    HK(upload(h, sd, &dsd, tmp));
+    int ln = 0;
+    for (auto& b : LV.box) ln = std::max(ln, b.n);
+    HK(wsbm_lu_solve_batched(dsd, dsd, nb, ln, nrhs, st));
+    // bt = Dhat (R xh):  g = xh[pc]; r = g[0:k] + Tc g[k:n]; bt = Dhat r
+    size_t tn = 0, tk = 0;
+    for (auto& b : LV.box) {
+      tn += b.n;
+      tk += b.k;
+    }
+    double2 *g = nullptr, *r = nullptr;
+    HK(dalloc(h, tn * nrhs * sizeof(double2), (void**)&g, tmp));
+    HK(dalloc(h, tk * nrhs * sizeof(double2), (void**)&r, tmp));
+    std::vector<GatherDesc> gd;
+    std::vector<CopyDesc> rc0;
+    std::vector<GemmDesc> g1, g2;
+    size_t on = 0, ok = 0;
+    int lk = 0;
+    for (int b = 0; b < nb; ++b) {
+      Box& B = LV.box[b];
+      double2* gb = g + on * nrhs;
+      double2* rb = r + ok * nrhs;
+      on += B.n;
+      ok += B.k;
+      lk = std::max(lk, B.k);
+      gd.push_back({gb, XH[l][b], B.pc, B.n, B.n, B.n, nrhs});
+      rc0.push_back({rb, gb, B.k, B.n, B.k, nrhs});
+      if (B.n > B.k) {
+        GemmDesc a;
+        memset(&a, 0, sizeof(a));
+        a.A = B.Tc;
+        a.lda = B.k;
+        a.B = gb + B.k;
+        a.ldb = B.n;
+        a.C = rb;
+        a.ldc = B.k;
+        a.m = B.k;
+        a.n = nrhs;
+        a.k = B.n - B.k;
+        a.alpha = make_double2(1.0, 0.0);
+        a.beta = make_double2(1.0, 0.0);
+        g1.push_back(a);
+      }
+      GemmDesc c;
+      memset(&c, 0, sizeof(c));
+      c.A = B.Dc;
+      c.lda = B.k;
+      c.B = rb;
+      c.ldb = B.k;
+      c.C = BT[l][b];
+      c.ldc = B.k;
+      c.m = B.k;
+      c.n = nrhs;
+      c.k = B.k;
+      c.alpha = make_double2(1.0, 0.0);
+      c.beta = make_double2(0.0, 0.0);
+      g2.push_back(c);
+    }
+    GatherDesc* dgd = nullptr;
+    CopyDesc* drc = nullptr;
+    GemmDesc *dg1 = nullptr, *dg2 = nullptr;
+    HK(upload(h, gd, &dgd, tmp));
+    HK(upload(h, rc0, &drc, tmp));
+    HK(upload(h, g1, &dg1, tmp));
+    HK(upload(h, g2, &dg2, tmp));
+    k_gather_rows<<<dim3(gridfor((int64_t)ln * nrhs), nb), 256, 0, st>>>(dgd);
+    wsbm_count_launch();
+    k_copy2d<<<dim3(gridfor((int64_t)lk * nrhs), nb), 256, 0, st>>>(drc);
+    wsbm_count_launch();
+    if (!g1.empty()) HK(wsbm_gemm_batched(dg1, (int)g1.size(), lk, nrhs, st));
+    HK(wsbm_gemm_batched(dg2, nb, lk, nrhs, st));
+  }
+  // ---- root
+  double2* y = nullptr;
+  HK(dalloc(h, (size_t)h->root_n * nrhs * sizeof(double2), (void**)&y, tmp));
+  {
+    Level& T = h->lv[top];
+    std::vector<CopyDesc> c;
+    int off = 0;
+    for (int b = 0; b < (int)T.box.size(); ++b) {
+      c.push_back({y + off, BT[top][b], h->root_n, T.box[b].k, T.box[b].k, nrhs});
+      off += T.box[b].k;
+    }
+    CopyDesc* dc = nullptr;
+    HK(upload(h, c, &dc, tmp));
+    k_copy2d<<<dim3(gridfor((int64_t)maxk * nrhs), (unsigned)c.size()), 256, 0, st>>>(dc);
+    wsbm_count_launch();
+    TrsmDesc t;
+    memset(&t, 0, sizeof(t));
+    t.T = h->root;
+    t.ldt = h->root_n;
+    t.B = y;
+    t.ldb = h->root_n;
+    t.piv = h->root_piv;
+    t.n = h->root_n;
+    t.nrhs = nrhs;
+    std::vector<TrsmDesc> v(1, t);
+    TrsmDesc* dt = nullptr;
+    HK(upload(h, v, &dt, tmp));
+    HK(wsbm_lu_solve_batched(dt, dt, 1, h->root_n, nrhs, st));
+  }
+  // ---- downward sweep: x = xh - Z (bt - Dhat y); y of a box = its slice of the parent's x
+  std::vector<std::vector<double2*>> X(L + 1);
+  for (int l = top; l <= L; ++l) {
+    Level& LV = h->lv[l];
+    int nb = (int)LV.box.size();
+    X[l].resize(nb);
+    std::vector<GemmDesc> g1, g2;
+    size_t tk = 0;
+    for (auto& b : LV.box) tk += b.k;
+    double2* tb = nullptr;
+    HK(dalloc(h, tk * nrhs * sizeof(double2), (void**)&tb, tmp));
+    std::vector<CopyDesc> cb;
+    size_t ok = 0;
+    int lk = 0, ln = 0;
+    int yoff = 0;
+    for (int b = 0; b < nb; ++b) {
+      Box& B = LV.box[b];
+      const double2* yb;
+      int64_t ldy;
+      if (l == top) {
+        yb = y + yoff;
+        ldy = h->root_n;
+        yoff += B.k;
+      } else {
+        Box& P = h->lv[l - 1].box[b / 2];
+        yb = X[l - 1][b / 2] + ((b % 2) ? h->lv[l].box[b - 1].k : 0);
+        ldy = P.n;
+      }
+      double2* t = tb + ok * nrhs;
+      ok += B.k;
+      lk = std::max(lk, B.k);
+      ln = std::max(ln, B.n);
+      cb.push_back({t, BT[l][b], B.k, B.k, B.k, nrhs});
+      GemmDesc a;  // t = bt - Dhat y
+      memset(&a, 0, sizeof(a));
+      a.A = B.Dc;
+      a.lda = B.k;
+      a.B = yb;
+      a.ldb = ldy;
+      a.C = t;
+      a.ldc = B.k;
+      a.m = B.k;
+      a.n = nrhs;
+      a.k = B.k;
+      a.alpha = make_double2(-1.0, 0.0);
+      a.beta = make_double2(1.0, 0.0);
+      g1.push_back(a);
+      GemmDesc z;  // xh -= Z t
+      memset(&z, 0, sizeof(z));
+      z.A = B.Z;
+      z.lda = B.n;
+      z.B = t;
+      z.ldb = B.k;
+      z.C = XH[l][b];
+      z.ldc = B.n;
+      z.m = B.n;
+      z.n = nrhs;
+      z.k = B.k;
+      z.alpha = make_double2(-1.0, 0.0);
+      z.beta = make_double2(1.0, 0.0);
+      g2.push_back(z);
+      X[l][b] = XH[l][b];
+    }
+    CopyDesc* dcb = nullptr;
+    GemmDesc *dg1 = nullptr, *dg2 = nullptr;
+    HK(upload(h, cb, &dcb, tmp));
+    HK(upload(h, g1, &dg1, tmp));
+    HK(upload(h, g2, &dg2, tmp));
+    k_copy2d<<<dim3(gridfor((int64_t)lk * nrhs), nb), 256, 0, st>>>(dcb);
+    wsbm_count_launch();
+    HK(wsbm_gemm_batched(dg1, nb, lk, nrhs, st));
+    HK(wsbm_gemm_batched(dg2, nb, ln, nrhs, st));
+  }
+  // leaves: x (interleaved, per box contiguous) -> bint -> u, q
+  {
+    Level& LV = h->lv[L];
+    std::vector<CopyDesc> c;
+    for (int b = 0; b < (int)LV.box.size(); ++b) {
+      Box& B = LV.box[b];
+      c.push_back({bint + 2 * B.lo, X[L][b], 2 * N, B.n, B.n, nrhs});
+    }
+    CopyDesc* dc = nullptr;
+    HK(upload(h, c, &dc, tmp));
+    k_copy2d<<<dim3(gridfor((int64_t)maxn * nrhs), (unsigned)c.size()), 256, 0, st>>>(dc);
+    wsbm_count_launch();
+    k_split_uq<<<gridfor(N * nrhs), 256, 0, st>>>(bint, (double2*)u, (double2*)q, N, nrhs);
+    wsbm_count_launch();
+  }
+  HC(cudaGetLastError());
+  HC(cudaStreamSynchronize(st));
+  free_list(h, tmp);
+  return WSBM_OK;
+}
+
+extern "C" int wsbm_rhs_planewave(wsbm_hss_t h, const double* angles, int32_t nang, void* rhs) {
+  if (!h || nang < 0 || (nang > 0 && (!angles || !rhs))) return WSBM_ERR_INVALID_ARG;
+  if (nang == 0) return WSBM_OK;
+  k_rhs_planewave<<<gridfor(h->N * nang), 256, 0, h->st>>>(h->g, h->ph.k0, angles, nang, (double2*)rhs);
+  wsbm_count_launch();
+  return cudaGetLastError() == cudaSuccess ? WSBM_OK : WSBM_ERR_CUDA;
+}
+
+extern "C" int wsbm_farfield(wsbm_hss_t h, const void* u, const void* q, int32_t nrhs,
+                             const double* angles, int32_t nang, void* out) {
+  if (!h || nrhs < 0 || nang < 0) return WSBM_ERR_INVALID_ARG;
+  if (nrhs == 0 || nang == 0) return WSBM_OK;
+  if (!u || !q || !angles || !out) return WSBM_ERR_INVALID_ARG;
+  k_farfield<<<nang, 256, 0, h->st>>>(h->g, h->ph.k0, h->ph.eps0, (const double2*)u, (const double2*)q, nrhs, angles, nang, (double2*)out);
+  wsbm_count_launch();
+  return cudaGetLastError() == cudaSuccess ? WSBM_OK : WSBM_ERR_CUDA;
+}
+
+extern "C" int wsbm_entries(wsbm_hss_t h, const int64_t* rows, int64_t nr, const int64_t* cols,
+                            int64_t nc, void* out) {
+  if (!h) return WSBM_ERR_INVALID_ARG;
+  wsbm_geom g = {h->N, h->x, h->y, h->nx, h->ny, h->w, h->kappa};
+  return wsbm_entries_raw(&g, &h->prm, rows, nr, cols, nc, out, h->st);
+}
+
+extern "C" int wsbm_box_info(wsbm_hss_t h, int32_t level, int32_t box, double* out4, int64_t* range2) {
+  if (!h || level < 0 || level > h->L || box < 0 || box >= (1 << level) || !out4 || !range2)
+    return WSBM_ERR_INVALID_ARG;
+  const Box& b = h->lv[level].box[box];
+  out4[0] = b.cx;
+  out4[1] = b.cy;
+  out4[2] = b.R;
+  out4[3] = b.rho;
+  range2[0] = b.lo;
+  range2[1] = b.hi;
+  return WSBM_OK;
+}
+
+extern "C" int wsbm_stats(wsbm_hss_t h, wsbm_stats_t* s) {
+  if (!h || !s) return WSBM_ERR_INVALID_ARG;
+  *s = h->stats;
+  return WSBM_OK;
+}

@@ -1,0 +1,65 @@
+// Internal types shared by the CUDA translation units of the library (not part of the ABI).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/wsbm_hss.h"
+#include "dense.h"
+
+struct DevGeom {
+  const double *x, *y, *nx, *ny, *w, *kappa;
+  int64_t n;
+};
+
+struct Phys {
+  double k0, k1, eps0, eps1;
+};
+
+// One output block of node-pair entries of the WSBM matrix.  A row "slot" t names row node
+// rnode[t]; its equation a (0: first row of eq. (weakly_bm), 1: second row) goes to output
+// row rpos[2t+a] (-1: not requested).  Columns likewise with the unknowns u (b = 0), q (b = 1).
+// trans = 0: entry (row, col) is stored at out[row + col*ld]; trans = 1: at out[col + row*ld].
+struct PairTask {
+  const int32_t* rnode;
+  const int32_t* rpos;
+  const int32_t* cnode;
+  const int32_t* cpos;
+  double2* out;
+  int64_t ld;
+  int32_t nr, nc;
+  int32_t trans;
+  int32_t tile0;  // index of this task's first tile in the launch
+};
+
+// One proxy-circle block (proxy-surface method).  Box slot t names node node[t]; its
+// component a goes to box column pos[2t+a] (-1: absent).  Proxy row index = off + s*P + m,
+// s = 0 for the k1 source / field, s = 1 for k0.
+// side = 0: sources acting on the box equations;  side = 1: box unknowns' fields at p_m.
+// tr = 0: out[proxyrow + boxcol*ld];  tr = 1: out[boxcol + proxyrow*ld].
+struct ProxyTask {
+  const int32_t* node;
+  const int32_t* pos;
+  double2* out;
+  int64_t ld;
+  double cx, cy, rho;
+  int32_t nn, P;
+  int32_t side, tr;
+  int32_t off;
+  int32_t tile0;
+};
+
+// Tiles: TILE_F slots along the fast (contiguous-output) dimension x TILE_S along the other.
+#define WSBM_TILE_F 32
+#define WSBM_TILE_S 4
+#define WSBM_PAIR_THREADS 128
+
+// entries.cu
+int wsbm_launch_pairs(const DevGeom& g, const Phys& ph, const PairTask* d_tasks, int ntasks,
+                      int64_t ntiles, cudaStream_t st);
+int wsbm_launch_proxy(const DevGeom& g, const Phys& ph, const ProxyTask* d_tasks, int ntasks,
+                      int64_t ntiles, int mixed, cudaStream_t st);
+int64_t wsbm_pair_tiles(int32_t nr, int32_t nc, int32_t trans);
+int64_t wsbm_proxy_tiles(int32_t nn, int32_t P);
+int wsbm_launch_hankel(const double* z, int64_t n, double* out, int mixed, cudaStream_t st);
+int wsbm_launch_unknowns_to_slots(const int64_t* idx, int64_t n, int64_t N, int32_t* node,
+                                  int32_t* pos, cudaStream_t st);

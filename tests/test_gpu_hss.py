@@ -1,0 +1,161 @@
+"""HSS build, factor, solve and far field on the GPU against the dense oracle (densities and
+far field within 10x the ID tolerance) and against the Mie series on the disk."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2607_00790_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+def gpu_solver(curve, prm, precision=0, leaf=None, tol=None, nproxy=None):
+    from paper_2607_00790_gb300 import binding
+    g, keep = binding.make_geom(curve)
+    p = binding.make_params(prm["k0"], prm["n"], leaf=leaf or prm["leaf"],
+                            nproxy=nproxy or prm["nproxy"], id_tol=tol or prm["tol"],
+                            precision=precision)
+    s = binding.Solver(g, p)
+    s._keep = keep
+    return s
+
+
+def solve_gpu(s, angles):
+    import torch
+    ang = torch.tensor(np.asarray(angles, dtype=np.float64), device="cuda")
+    s.factor()
+    rhs = s.rhs_planewave(ang)
+    u, q = s.solve(rhs)
+    torch.cuda.synchronize()
+    return rhs.cpu().numpy(), u.cpu().numpy(), q.cpu().numpy()
+
+
+def farfield_gpu(s, u, q, angles):
+    import torch
+    uu = torch.tensor(u, device="cuda")
+    qq = torch.tensor(q, device="cuda")
+    a = torch.tensor(np.asarray(angles, dtype=np.float64), device="cuda")
+    return s.farfield(uu, qq, a).cpu().numpy()
+
+
+def dense_reference(curve, ph, angles):
+    A = oracle.wsbm_dense(curve, ph)
+    b = oracle.rhs_planewave(curve, ph, angles)
+    x = oracle.dense_solve(A, b)
+    u, q = oracle.split_uq(x)
+    return b, u, q
+
+
+def rel(a, b):
+    return np.linalg.norm(a - b) / np.linalg.norm(b)
+
+
+def test_disk_config_vs_dense_and_mie():
+    c, prm = inputs.workload("disk")
+    ph = oracle.Physics(prm["k0"], n=prm["n"])
+    s = gpu_solver(c, prm)
+    rhs, u, q = solve_gpu(s, [0.0])
+    b, ud, qd = dense_reference(c, ph, [0.0])
+    assert rel(rhs, b) < 1e-14
+    tol = prm["tol"]
+    assert rel(u, ud) < 10 * tol, rel(u, ud)
+    assert rel(q, qd) < 10 * tol, rel(q, qd)
+    ang = 2 * np.pi * np.arange(360) / 360
+    ff = farfield_gpu(s, u, q, ang)
+    ffd = oracle.farfield(c, ph, ud, qd, ang)
+    assert rel(ff, ffd) < 10 * tol, rel(ff, ffd)
+    # Mie: the HSS solution carries the O(h^3) discretisation error of the dense system
+    ue, _ = oracle.mie_boundary(1.0, ph, c["t"])
+    err = np.linalg.norm(u[:, 0].real - ue.real) / np.linalg.norm(ue.real)
+    assert abs(err - 7.74e-5) < 1e-6, err
+    st = s.stats()
+    assert st["levels"] == 2 and st["root_size"] > 0 and st["entries_generated"] > 0
+
+
+@pytest.mark.parametrize("N,leaf", [(1024, 64), (1536, 128)])
+def test_star_15_nodes_per_wavelength_vs_dense(N, leaf):
+    c = inputs.star(N)
+    prm = dict(k0=inputs.k0_for_density(c), n=1.5, leaf=leaf, nproxy=64, tol=1e-8)
+    ph = oracle.Physics(prm["k0"], n=prm["n"])
+    angles = 2 * np.pi * np.arange(8) / 8
+    s = gpu_solver(c, prm)
+    rhs, u, q = solve_gpu(s, angles)
+    b, ud, qd = dense_reference(c, ph, angles)
+    assert rel(u, ud) < 10 * prm["tol"], rel(u, ud)
+    assert rel(q, qd) < 10 * prm["tol"], rel(q, qd)
+    ang = 2 * np.pi * np.arange(360) / 360
+    ff = farfield_gpu(s, u, q, ang)
+    ffd = oracle.farfield(c, ph, ud, qd, ang)
+    assert rel(ff, ffd) < 10 * prm["tol"], rel(ff, ffd)
+
+
+def test_mixed_precision_vs_fp64_path():
+    c = inputs.star(1024)
+    prm = dict(k0=inputs.k0_for_density(c), n=1.5, leaf=64, nproxy=64, tol=1e-6)
+    ang = 2 * np.pi * np.arange(360) / 360
+    s64 = gpu_solver(c, prm, precision=0)
+    _, u64, q64 = solve_gpu(s64, [0.0, 1.0])
+    f64 = farfield_gpu(s64, u64, q64, ang)
+    smx = gpu_solver(c, prm, precision=1)
+    _, umx, qmx = solve_gpu(smx, [0.0, 1.0])
+    fmx = farfield_gpu(smx, umx, qmx, ang)
+    assert rel(fmx, f64) < 1e-5, rel(fmx, f64)
+
+
+def test_single_box_tree():
+    c = inputs.star(48)
+    prm = dict(k0=3.0, n=1.5, leaf=64, nproxy=16, tol=1e-10)
+    ph = oracle.Physics(prm["k0"], n=prm["n"])
+    s = gpu_solver(c, prm)
+    _, u, q = solve_gpu(s, [0.3])
+    _, ud, qd = dense_reference(c, ph, [0.3])
+    assert rel(u, ud) < 1e-12 and rel(q, qd) < 1e-12
+    assert s.stats()["levels"] == 0
+
+
+def test_paper_table_parameters_star():
+    c = inputs.star(1024)
+    prm = dict(k0=10.0, n=float(np.sqrt(5.0)), leaf=64, nproxy=64, tol=1e-10)
+    ph = oracle.Physics(10.0, eps0=1.0, eps1=5.0)
+    s = gpu_solver(c, prm)
+    _, u, q = solve_gpu(s, [0.0])
+    _, ud, qd = dense_reference(c, ph, [0.0])
+    assert rel(u, ud) < 1e-9 and rel(q, qd) < 1e-9
+
+
+def test_solve_before_factor_and_bad_args():
+    import torch
+    from paper_2607_00790_gb300 import binding
+    c = inputs.disk(128)
+    g, keep = binding.make_geom(c)
+    s = binding.Solver(g, binding.make_params(2 * np.pi, 1.5, leaf=32, nproxy=32, id_tol=1e-8))
+    rhs = torch.zeros((256, 1), dtype=torch.complex128, device="cuda")
+    with pytest.raises(binding.WsbmError) as e:
+        s.solve(rhs)
+    assert e.value.code == -6
+    with pytest.raises(binding.WsbmError):
+        binding.Solver(g, binding.make_params(2 * np.pi, 1.5, leaf=2))
+    bad = dict(c)
+    bad["w"] = c["w"].copy()
+    bad["w"][3] = np.nan
+    gb, kb = binding.make_geom(bad)
+    with pytest.raises(binding.WsbmError):
+        binding.Solver(gb, binding.make_params(2 * np.pi, 1.5))
+
+
+def test_box_info_matches_oracle_circle():
+    c, prm = inputs.workload("star", N=4096)
+    s = gpu_solver(c, prm)
+    for level, box in [(5, 0), (5, 17), (3, 5), (1, 1)]:
+        circ, rng = s.box_info(level, box)
+        cx, cy, rho = oracle.proxy_circle(c, np.arange(rng[0], rng[1]))
+        assert (circ[0], circ[1], circ[3]) == (cx, cy, rho)
+
+
+def test_factor_solve_deterministic():
+    c = inputs.star(768)
+    prm = dict(k0=inputs.k0_for_density(c), n=1.5, leaf=64, nproxy=64, tol=1e-8)
+    s = gpu_solver(c, prm)
+    _, u1, q1 = solve_gpu(s, [0.0])
+    _, u2, q2 = solve_gpu(s, [0.0])
+    assert np.array_equal(u1, u2) and np.array_equal(q1, q2)
