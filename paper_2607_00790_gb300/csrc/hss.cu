@@ -574,7 +574,8 @@ static int factor_level(wsbm_hss* h, int l) {
   const int nb = (int)LV.box.size();
   std::vector<void*> tmp;
   cudaStream_t st = h->st;
-  // ---- near lists: boxes with a candidate node inside the proxy circle, and curve neighbours
+  // ---- near lists: boxes with a candidate node inside the proxy circle, and curve neighbours.
+  // Only boxes whose bounding circle meets the proxy circle are scanned node by node.
   for (int b = 0; b < nb; ++b) {
     Box& B = LV.box[b];
     B.near.clear();
@@ -582,8 +583,10 @@ static int factor_level(wsbm_hss* h, int l) {
       if (s == b) continue;
       bool nb_adj = (s == (b + 1) % nb) || (s == (b + nb - 1) % nb);
       bool inside = false;
-      if (!nb_adj) {
-        const Box& S = LV.box[s];
+      const Box& S = LV.box[s];
+      double cdx = S.cx - B.cx, cdy = S.cy - B.cy;
+      double reach = B.rho + S.R;
+      if (!nb_adj && cdx * cdx + cdy * cdy < reach * reach) {
         for (size_t t = 0; t < S.cr.size() && !inside; ++t) {
           int32_t node = S.cr[t] >> 1;
           double dx = h->hx[node] - B.cx, dy = h->hy[node] - B.cy;
