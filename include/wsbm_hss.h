@@ -124,6 +124,25 @@ int wsbm_hankel01(const double* z, int64_t n, double* out, int32_t precision, vo
 int wsbm_entries_raw(const wsbm_geom* g, const wsbm_params* p, const int64_t* rows, int64_t nr,
                      const int64_t* cols, int64_t nc, void* out, void* stream);
 
+/* Largest nr + nc accepted by wsbm_entries_raw_noalloc. */
+#define WSBM_NOALLOC_MAX_INDICES 65536
+
+/* Same entries as wsbm_entries_raw, computed without allocating any device memory.  The paper
+ * has no counterpart to this call: it exists for callers that cannot allocate, for example a
+ * framework whose caching allocator already owns the GPU's memory, code that runs under a fixed
+ * device-memory budget, or a latency-critical path that must not pay for cudaMalloc/cudaFree
+ * (which can synchronise with the device).
+ * Scratch: a library-owned device array of 256 + 24 * WSBM_NOALLOC_MAX_INDICES bytes (about
+ * 1.5 MB), held by every GPU that loads the library until the process exits.  The first call on
+ * a device looks up that array's device address (cudaGetSymbolAddress, with that device
+ * current); make that first call before any stream capture.  The array is shared by every
+ * call and keeps the last call's contents: calls whose work overlaps on the GPU (different
+ * streams, or different host threads on one device) race and must be ordered by the caller.
+ * Arguments, layout and ownership as for wsbm_entries_raw; the call only enqueues work.
+ * Errors: INVALID_ARG (also when nr + nc > WSBM_NOALLOC_MAX_INDICES), CUDA, NO_DEVICE. */
+int wsbm_entries_raw_noalloc(const wsbm_geom* g, const wsbm_params* p, const int64_t* rows,
+                             int64_t nr, const int64_t* cols, int64_t nc, void* out, void* stream);
+
 /* Proxy-circle blocks of the proxy-surface method (Sec. III) for one box, the inputs of its
  * interpolative decompositions.  The circle has centre (cx, cy), radius rho and P equispaced
  * points p_m = c + rho (cos 2 pi m/P, sin 2 pi m/P) with outward normals.
