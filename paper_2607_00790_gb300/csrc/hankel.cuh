@@ -1,20 +1,23 @@
 // Device evaluation of the Hankel functions H0^(1), H1^(1) (the kernels of every layer
 // potential in eq. (weakly_bm): G_k = (i/4) H0^(1)(k r) and its normal derivatives).
 //
-// FP64 evaluator, three regimes:
-//   z <  3    ascending series in u = z^2/4 (A&S 9.1.10, 9.1.11, 9.1.13); the 1/z pole of Y1
-//             is kept apart so F1 = H1/z + 2i/(pi z^2) is formed without cancellation;
-//   3 <= z < 20   H_nu = sqrt(2/(pi z)) (P_nu + i Q_nu) e^{i(z - pi/4 - nu pi/2)} with P_nu - 1
-//             and Q_nu from piecewise polynomial fits (degree 16 on [a, 1.5a] intervals);
-//   z >= 20   the same form with P, Q from the Hankel asymptotic expansion (A&S 9.2.5-9.2.10);
-//             the number of terms falls as z grows.
-// The phase factor e^{iz} comes from sincos(z) of the exact double z, and e^{-i pi/4} is
-// applied as a constant rotation, so no rounding of z - pi/4 enters the phase (one ulp of a
-// z near 5e4 would otherwise cost ~4e-12 relative).
+// GB300 executes FP64 at 1/64 of the FP32 rate, so the evaluator is built to spend few FP64
+// instructions per argument:
+//   z < 1.5     ascending series in z^2/4 (A&S 9.1.10, 9.1.11, 9.1.13); the 1/z pole of Y1 is kept
+//               apart so F1 = H1/z + 2i/(pi z^2) is formed without cancellation;
+//   z >= 1.5    H_nu = sqrt(2/(pi z)) (P_nu + i Q_nu) e^{i(z - pi/4 - nu pi/2)};
+//               P_nu - 1, Q_nu are degree-10 polynomials in u = 1/z on seven intervals up to
+//               z = 20 (the functions are smooth in 1/z), and degree-6 polynomials in 1/z^2
+//               beyond (P_nu - 1 and z Q_nu);
+//   phase       z - pi/4 is reduced by multiples of pi/2 (Cody-Waite with a two-part pi/2 and
+//               fused multiply-adds) and sin/cos of the remainder |w| <= pi/4 come from fitted
+//               polynomials, so no rounding of z - pi/4 enters the phase.
+// The interval is chosen by comparing the high 32-bit word of z as an integer (integer pipe).
+// All coefficients are fitted by gen_hankel_coeffs.py (50-digit arithmetic) and checked there.
 //
-// Mixed evaluator (WSBM_MIXED): the phase is reduced in FP64 (z - 2 pi n, two-part constant),
-// then sin/cos of the reduced phase, the amplitude sqrt(2/(pi z)) and P, Q are FP32 (fits of
-// degree 6, three asymptotic terms).  Arguments below 3 fall back to the FP64 evaluator.
+// Mixed evaluator (WSBM_MIXED): the phase is reduced in FP64 (z - 2 pi n, two-part 2 pi), then
+// sin/cos of the remainder, sqrt(2/(pi z)) and P, Q (degree-4 fits in 1/z, degree-2 in 1/z^2)
+// are FP32.  Arguments below 1.5 fall back to the FP64 evaluator.
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -36,25 +39,35 @@ struct HkF {
 };
 
 // Coefficient tables staged in shared memory by every kernel that evaluates Hankel values
-// (divergent interval indices within a warp make constant-bank reads serialise).
+// (divergent interval indices within a warp would serialise constant-bank reads).
 struct HkTables {
-  double iv[HK_NIV][4];
+  double iv[HK_NIV][2];
   double fit[HK_NIV][4][HK_DEG + 1];
-  double asy[4][HK_NASY];
+  double asy[4][HK_DEG_T + 1];
   double ser[4][HK_NSER];
+  double sn[HK_DEG_SC + 1];
+  double cs[HK_DEG_SC + 1];
+  float ivf[HK_NIV][2];
   float fitf[HK_NIV][4][HKF_DEG + 1];
-  float asyf[4][3];
+  float asyf[4][HKF_DEG_T + 1];
 };
 
+template <class T>
+__device__ __forceinline__ void hk_copy(T* dst, const T* src, int n) {
+  for (int k = threadIdx.x; k < n; k += blockDim.x) dst[k] = src[k];
+}
+
 __device__ __forceinline__ void hk_stage_tables(HkTables* t) {
-  const double* src[4] = {&hk_iv[0][0], &hk_fit[0][0][0], &hk_asy[0][0], &hk_ser[0][0]};
-  double* dst[4] = {&t->iv[0][0], &t->fit[0][0][0], &t->asy[0][0], &t->ser[0][0]};
-  const int cnt[4] = {HK_NIV * 4, HK_NIV * 4 * (HK_DEG + 1), 4 * HK_NASY, 4 * HK_NSER};
-  for (int a = 0; a < 4; ++a)
-    for (int k = threadIdx.x; k < cnt[a]; k += blockDim.x) dst[a][k] = src[a][k];
-  for (int k = threadIdx.x; k < HK_NIV * 4 * (HKF_DEG + 1); k += blockDim.x)
-    (&t->fitf[0][0][0])[k] = (&hkf_fit[0][0][0])[k];
-  for (int k = threadIdx.x; k < 12; k += blockDim.x) t->asyf[k / 3][k % 3] = (float)hk_asy[k / 3][k % 3];
+  hk_copy(&t->iv[0][0], &hk_iv[0][0], HK_NIV * 2);
+  hk_copy(&t->fit[0][0][0], &hk_fit[0][0][0], HK_NIV * 4 * (HK_DEG + 1));
+  hk_copy(&t->asy[0][0], &hk_asy[0][0], 4 * (HK_DEG_T + 1));
+  hk_copy(&t->ser[0][0], &hk_ser[0][0], 4 * HK_NSER);
+  hk_copy(t->sn, hk_sin, HK_DEG_SC + 1);
+  hk_copy(t->cs, hk_cos, HK_DEG_SC + 1);
+  hk_copy(&t->fitf[0][0][0], &hkf_fit[0][0][0], HK_NIV * 4 * (HKF_DEG + 1));
+  hk_copy(&t->asyf[0][0], &hkf_asy[0][0], 4 * (HKF_DEG_T + 1));
+  for (int k = threadIdx.x; k < HK_NIV * 2; k += blockDim.x)
+    (&t->ivf[0][0])[k] = (float)(&hk_iv[0][0])[k];
 }
 
 template <int N>
@@ -62,12 +75,6 @@ __device__ __forceinline__ double hk_horner(const double* c, double s) {
   double r = c[N - 1];
 #pragma unroll
   for (int k = N - 2; k >= 0; --k) r = fma(r, s, c[k]);
-  return r;
-}
-
-__device__ __forceinline__ double hk_horner_n(const double* c, int n, double s) {
-  double r = c[n - 1];
-  for (int k = n - 2; k >= 0; --k) r = fma(r, s, c[k]);
   return r;
 }
 
@@ -79,11 +86,36 @@ __device__ __forceinline__ float hk_hornerf(const float* c, float s) {
   return r;
 }
 
+// Interval index for HK_Z_SERIES <= z < HK_Z_ASYM from the high word of z (integer compares:
+// the bounds have zero low words, and positive doubles order like their bit patterns).
 __device__ __forceinline__ int hk_interval(double z) {
+  const int hi = __double2hiint(z);
+  const int lim[HK_NIV - 1] = HK_IV_HI;
   int iv = 0;
 #pragma unroll
-  for (int k = 1; k < HK_NIV; ++k) iv += (z >= 0.0 + hk_iv_lo(k)) ? 1 : 0;
+  for (int k = 0; k < HK_NIV - 1; ++k) iv += (hi >= lim[k]) ? 1 : 0;
   return iv;
+}
+
+// e^{i(z - pi/4)} = E + iF.  z - pi/4 = w + k pi/2 with |w| <= pi/4: k = rint(2z/pi - 1/2),
+// w = z - (k + 1/2) pi/2 by two fused multiply-adds with a two-part pi/2, then
+// e^{i(w + k pi/2)} = i^k (cos w + i sin w).
+__device__ __forceinline__ void hk_phase(const HkTables& T, double z, double* E, double* F) {
+  const double MAGIC = 6755399441055744.0;  // 1.5 * 2^52: adding it rounds to an integer
+  double t = fma(z, HK_2_OVER_PI, -0.5);
+  double tm = __dadd_rn(t, MAGIC);
+  int q = __double2loint(tm);
+  double k = __dsub_rn(tm, MAGIC);
+  double m = k + 0.5;
+  double w = fma(-m, HK_PIO2_HI, z);
+  w = fma(-m, HK_PIO2_LO, w);
+  double v = w * w;
+  double s = fma(w * v, hk_horner<HK_DEG_SC + 1>(T.sn, v), w);
+  double c = fma(v, fma(v, hk_horner<HK_DEG_SC + 1>(T.cs, v), -0.5), 1.0);
+  double a = (q & 1) ? s : c;
+  double b = (q & 1) ? c : s;
+  *E = ((q + 1) & 2) ? -a : a;  // negative for k = 1, 2 (mod 4)
+  *F = (q & 2) ? -b : b;        // negative for k = 2, 3
 }
 
 // Small argument: ascending series.
@@ -106,23 +138,22 @@ __device__ __forceinline__ void hk_series(const HkTables& T, double z, Hk& o) {
   o.f1i = y1h * iz;
 }
 
-// P_nu, Q_nu for z >= HK_Z_SERIES.
-__device__ __forceinline__ void hk_pq(const HkTables& T, double z, double iz, double* P0,
-                                      double* Q0, double* P1, double* Q1) {
+// P_nu - 1 (pm0, pm1) and Q_nu for z >= HK_Z_SERIES, u = 1/z.
+__device__ __forceinline__ void hk_pq(const HkTables& T, double z, double u, double* pm0,
+                                      double* Q0, double* pm1, double* Q1) {
   if (z < HK_Z_ASYM) {
     int iv = hk_interval(z);
-    double s = (z - T.iv[iv][2]) * T.iv[iv][3];
-    *P0 = 1.0 + hk_horner<HK_DEG + 1>(T.fit[iv][0], s);
+    double s = (u - T.iv[iv][0]) * T.iv[iv][1];
+    *pm0 = hk_horner<HK_DEG + 1>(T.fit[iv][0], s);
     *Q0 = hk_horner<HK_DEG + 1>(T.fit[iv][1], s);
-    *P1 = 1.0 + hk_horner<HK_DEG + 1>(T.fit[iv][2], s);
+    *pm1 = hk_horner<HK_DEG + 1>(T.fit[iv][2], s);
     *Q1 = hk_horner<HK_DEG + 1>(T.fit[iv][3], s);
   } else {
-    double t = iz * iz;
-    int n = (z < 40.0) ? HK_NASY : (z < 100.0) ? 7 : (z < 1000.0) ? 5 : 3;
-    *P0 = hk_horner_n(T.asy[0], n, t);
-    *Q0 = iz * hk_horner_n(T.asy[1], n, t);
-    *P1 = hk_horner_n(T.asy[2], n, t);
-    *Q1 = iz * hk_horner_n(T.asy[3], n, t);
+    double s = (u * u - HK_T_C) * HK_T_IH;
+    *pm0 = hk_horner<HK_DEG_T + 1>(T.asy[0], s);
+    *Q0 = u * hk_horner<HK_DEG_T + 1>(T.asy[1], s);
+    *pm1 = hk_horner<HK_DEG_T + 1>(T.asy[2], s);
+    *Q1 = u * hk_horner<HK_DEG_T + 1>(T.asy[3], s);
   }
 }
 
@@ -133,21 +164,21 @@ __device__ __forceinline__ void hankel_fp64(const HkTables& T, double z, Hk& o) 
     return;
   }
   double rs = rsqrt(z);
-  double iz = rs * rs;
+  double u = rs * rs;
   double A = WSBM_SQRT_2_OVER_PI * rs;
-  double sn, cs;
-  sincos(z, &sn, &cs);
-  double E = (cs + sn) * WSBM_INV_SQRT2;  // e^{i(z - pi/4)} = E + iF
-  double F = (sn - cs) * WSBM_INV_SQRT2;
-  double P0, Q0, P1, Q1;
-  hk_pq(T, z, iz, &P0, &Q0, &P1, &Q1);
-  o.h0r = A * (P0 * E - Q0 * F);
-  o.h0i = A * (P0 * F + Q0 * E);
+  double E, F;
+  hk_phase(T, z, &E, &F);
+  double pm0, Q0, pm1, Q1;
+  hk_pq(T, z, u, &pm0, &Q0, &pm1, &Q1);
+  double P0 = fma(A, pm0, A), AQ0 = A * Q0;
+  double P1 = fma(A, pm1, A), AQ1 = A * Q1;
+  o.h0r = fma(P0, E, -AQ0 * F);
+  o.h0i = fma(P0, F, AQ0 * E);
   // e^{i(z - 3pi/4)} = -i (E + iF) = F - iE
-  o.h1r = A * (P1 * F + Q1 * E);
-  o.h1i = A * (Q1 * F - P1 * E);
-  o.f1r = o.h1r * iz;
-  o.f1i = fma(WSBM_2_OVER_PI * iz, iz, o.h1i * iz);
+  o.h1r = fma(P1, F, AQ1 * E);
+  o.h1i = fma(AQ1, F, -P1 * E);
+  o.f1r = o.h1r * u;
+  o.f1i = fma(WSBM_2_OVER_PI * u, u, o.h1i * u);
 }
 
 // Mixed: FP64 phase reduction, FP32 amplitude.  Valid for z >= HK_Z_SERIES.  Also returns
@@ -165,24 +196,24 @@ __device__ __forceinline__ void hankel_mixed_large(const HkTables& T, double z, 
   sincosf(yf, &sn, &cs);
   float zf = (float)z;
   float rs = rsqrtf(zf);
+  float u = rs * rs;
   float A = (float)WSBM_SQRT_2_OVER_PI * rs;
   float E = (cs + sn) * (float)WSBM_INV_SQRT2;
   float F = (sn - cs) * (float)WSBM_INV_SQRT2;
-  float P0, Q0, P1, Q1;
+  float P0, Q0, P1, Q1;  // P0, P1 hold P - 1 until D is formed
   if (z < HK_Z_ASYM) {
     int iv = hk_interval(z);
-    float s = (float)((z - T.iv[iv][2]) * T.iv[iv][3]);
-    P0 = hk_hornerf<HKF_DEG + 1>(T.fitf[iv][0], s);  // P0 - 1
+    float s = (u - T.ivf[iv][0]) * T.ivf[iv][1];
+    P0 = hk_hornerf<HKF_DEG + 1>(T.fitf[iv][0], s);
     Q0 = hk_hornerf<HKF_DEG + 1>(T.fitf[iv][1], s);
-    P1 = hk_hornerf<HKF_DEG + 1>(T.fitf[iv][2], s);  // P1 - 1
+    P1 = hk_hornerf<HKF_DEG + 1>(T.fitf[iv][2], s);
     Q1 = hk_hornerf<HKF_DEG + 1>(T.fitf[iv][3], s);
   } else {
-    float iz = rs * rs;
-    float t = iz * iz;
-    P0 = t * fmaf(T.asyf[0][2], t, T.asyf[0][1]);  // P0 - 1
-    Q0 = iz * fmaf(fmaf(T.asyf[1][2], t, T.asyf[1][1]), t, T.asyf[1][0]);
-    P1 = t * fmaf(T.asyf[2][2], t, T.asyf[2][1]);  // P1 - 1
-    Q1 = iz * fmaf(fmaf(T.asyf[3][2], t, T.asyf[3][1]), t, T.asyf[3][0]);
+    float s = (u * u - (float)HK_T_C) * (float)HK_T_IH;
+    P0 = hk_hornerf<HKF_DEG_T + 1>(T.asyf[0], s);
+    Q0 = u * hk_hornerf<HKF_DEG_T + 1>(T.asyf[1], s);
+    P1 = hk_hornerf<HKF_DEG_T + 1>(T.asyf[2], s);
+    Q1 = u * hk_hornerf<HKF_DEG_T + 1>(T.asyf[3], s);
   }
   if (Dr) {
     float dr = Q1 - Q0, di = P0 - P1;
