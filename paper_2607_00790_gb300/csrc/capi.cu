@@ -37,6 +37,10 @@ int wsbm_phys_from_params(const wsbm_params* p, Phys* ph) {
   ph->k1 = p->refr_index * p->k0;
   ph->eps0 = eps0;
   ph->eps1 = eps1;
+  ph->inv_k0 = 1.0 / ph->k0;
+  ph->inv_k1 = 1.0 / ph->k1;
+  ph->s01 = sqrt(ph->k0 / ph->k1);
+  ph->s10 = sqrt(ph->k1 / ph->k0);
   return WSBM_OK;
 }
 

@@ -287,7 +287,10 @@ __global__ void __launch_bounds__(256) k_cpqr(const QrDesc* __restrict__ d, int 
       double s = 0.0;
       for (int i = lane; i < m; i += 32) s += cabs2(M[i + (int64_t)c * ld]);
       for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-      if (lane == 0) q.norm2[c] = s;
+      if (lane == 0) {
+        q.norm2[c] = s;
+        q.nref[c] = s;
+      }
     }
     for (int c = threadIdx.x; c < n; c += blockDim.x) q.perm[c] = c;
   }
@@ -338,6 +341,9 @@ __global__ void __launch_bounds__(256) k_cpqr(const QrDesc* __restrict__ d, int 
         double t = q.norm2[j];
         q.norm2[j] = q.norm2[p];
         q.norm2[p] = t;
+        t = q.nref[j];
+        q.nref[j] = q.nref[p];
+        q.nref[p] = t;
         int ti = q.perm[j];
         q.perm[j] = q.perm[p];
         q.perm[p] = ti;
@@ -367,7 +373,9 @@ __global__ void __launch_bounds__(256) k_cpqr(const QrDesc* __restrict__ d, int 
     }
     __syncthreads();
     const double tau = s_tau;
-    // apply P to the trailing columns: one warp per column; exact new norms on the way
+    // apply P to the trailing columns: one warp per column.  The remaining norm is downdated by
+    // the new row-j entry and recomputed exactly once cancellation has eaten half its digits
+    // (remaining norm below 1e-8 of the last exact one).
     for (int c = j + 1 + warp; c < n; c += nw) {
       double2* col = M + (int64_t)c * ld;
       const double2* u = M + (int64_t)j * ld;
@@ -383,14 +391,24 @@ __global__ void __launch_bounds__(256) k_cpqr(const QrDesc* __restrict__ d, int 
       }
       w.x *= tau;
       w.y *= tau;
-      double ns = 0.0;
+      double rj = 0.0;
       for (int i = j + lane; i < m; i += 32) {
         double2 v = cfms(u[i], w, col[i]);
         col[i] = v;
-        if (i > j) ns += cabs2(v);
+        if (i == j) rj = cabs2(v);
       }
-      for (int o = 16; o > 0; o >>= 1) ns += __shfl_xor_sync(0xffffffffu, ns, o);
-      if (lane == 0) q.norm2[c] = ns;
+      rj = __shfl_sync(0xffffffffu, rj, 0);  // lane 0 held row j
+      double nv = q.norm2[c] - rj;
+      if (nv <= 1e-8 * q.nref[c]) {
+        double ns = 0.0;
+        for (int i = j + 1 + lane; i < m; i += 32) ns += cabs2(col[i]);
+        for (int o = 16; o > 0; o >>= 1) ns += __shfl_xor_sync(0xffffffffu, ns, o);
+        nv = ns;
+        __syncwarp();
+        if (lane == 0) q.nref[c] = ns;
+      }
+      __syncwarp();
+      if (lane == 0) q.norm2[c] = fmax(nv, 0.0);
     }
     __syncthreads();
     if (threadIdx.x == 0) {

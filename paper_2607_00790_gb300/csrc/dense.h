@@ -51,6 +51,7 @@ struct QrDesc {
   int32_t* perm;
   int32_t* state;
   double* norm2;
+  double* nref;  // remaining squared norm at its last exact computation
   double* tauv;
   double2* betav;
   double* rdiag0;

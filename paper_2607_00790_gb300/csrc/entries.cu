@@ -18,7 +18,7 @@
 // Geometric quantities of a pair with the operation order fixed (no contraction): r and the
 // arguments z = k r are reproducible bit for bit by any IEEE double implementation.
 struct PairGeom {
-  double r, ir, z0, z1, dnx, dny, nn, c;
+  double r, ir, z0, z1, dnx, dny, nn, c, rs0, rs1;
 };
 
 __device__ __forceinline__ void pair_geom(double xi, double yi, double nxi, double nyi, double xj,
@@ -34,7 +34,10 @@ __device__ __forceinline__ void pair_geom(double xi, double yi, double nxi, doub
   G.dny = __dadd_rn(__dmul_rn(dx, nxj), __dmul_rn(dy, nyj));
   G.dnx = __dadd_rn(__dmul_rn(dx, nxi), __dmul_rn(dy, nyi));
   G.nn = __dadd_rn(__dmul_rn(nxi, nxj), __dmul_rn(nyi, nyj));
-  G.ir = 1.0 / r;
+  // one reciprocal square root serves both wavenumbers and 1/r
+  G.rs0 = rsqrt(G.z0);
+  G.rs1 = G.rs0 * ph.s01;
+  G.ir = ph.k0 * (G.rs0 * G.rs0);
   G.c = G.dnx * G.dny * (G.ir * G.ir);
 }
 
@@ -44,8 +47,8 @@ __device__ __forceinline__ void pair_geom(double xi, double yi, double nxi, doub
 __device__ __forceinline__ void block_offdiag(const HkTables& T, const Phys& ph, const PairGeom& G,
                                               double wj, double2 e[2][2]) {
   Hk a, b;
-  hankel_fp64(T, G.z0, a);
-  hankel_fp64(T, G.z1, b);
+  hankel_fp64_rs<true>(T, G.z0, G.rs0, a);
+  hankel_fp64_rs<true>(T, G.z1, G.rs1, b);
   const double k0 = ph.k0, k1 = ph.k1;
   double s11 = 0.25 * wj * k1 * G.dny * G.ir;  // A11 = i s11 H1(z1)
   e[0][0] = make_double2(-s11 * b.h1i, s11 * b.h1r);
@@ -55,7 +58,7 @@ __device__ __forceinline__ void block_offdiag(const HkTables& T, const Phys& ph,
   double m2c = G.nn - 2.0 * G.c;
   double gr = (q0 * a.h0r - q1 * b.h0r) * G.c + (q0 * a.f1r - q1 * b.f1r) * m2c;
   double gi = (q0 * a.h0i - q1 * b.h0i) * G.c + (q0 * a.f1i - q1 * b.f1i) * m2c;
-  double inv4k0 = 0.25 / k0;
+  double inv4k0 = 0.25 * ph.inv_k0;
   double t1 = 0.25 * k0 * G.dny * G.ir;
   // A21 = w [ i t1 H1(z0) + alpha dN ],  alpha dN = -(1/(4 k0)) (gr + i gi)
   e[1][0] = make_double2(wj * (-t1 * a.h1i - inv4k0 * gr), wj * (t1 * a.h1r - inv4k0 * gi));
@@ -198,23 +201,29 @@ __device__ __forceinline__ void proxy_row_fp64(const HkTables& T, const Phys& ph
   double dx = X.x - p.px, dy = X.y - p.py;
   double r2 = dx * dx + dy * dy;
   double r = sqrt(r2);
-  double ir = 1.0 / r;
+  double z1 = ph.k1 * r;
+  double rs1 = rsqrt(z1);
+  double ir = ph.k1 * (rs1 * rs1);
   double dnu = (dx * p.pnx + dy * p.pny) * ir;
   double dnx = (dx * X.nx + dy * X.ny) * ir;
   double nn = X.nx * p.pnx + X.ny * p.pny;
   double c = dnx * dnu;
-  double inv_k0 = 1.0 / ph.k0;
+  double inv_k0 = ph.inv_k0;
 #pragma unroll
   for (int s = 0; s < 2; ++s) {
     double k = s == 0 ? ph.k1 : ph.k0;
+    double ik = s == 0 ? ph.inv_k1 : ph.inv_k0;
     Hk h;
-    hankel_fp64(T, k * r, h);
+    if (s == 0)
+      hankel_fp64_rs<false>(T, z1, rs1, h);
+    else
+      hankel_fp64_rs<false>(T, ph.k0 * r, rs1 * ph.s10, h);
     // phi = (ik/4) H1 dnu + (k/4) H0
     double q = 0.25 * k;
     double phr = q * (-h.h1i * dnu + h.h0r), phi = q * (h.h1r * dnu + h.h0i);
     // dphi = N_k - (k^2/4) H1 dnx,  N_k = (i k^2/4)[H0 c + H1/(kr) (nn - 2c)]
     double q2 = 0.25 * k * k;
-    double izr = ir / k;
+    double izr = ir * ik;
     double m2c = nn - 2.0 * c;
     double Xr = h.h0r * c + h.h1r * izr * m2c, Xi = h.h0i * c + h.h1i * izr * m2c;
     double dpr = q2 * (-Xi - h.h1r * dnx), dpi = q2 * (Xr - h.h1i * dnx);
@@ -237,13 +246,18 @@ __device__ __forceinline__ void proxy_col_fp64(const HkTables& T, const Phys& ph
   double dx = p.px - Y.x, dy = p.py - Y.y;
   double r2 = dx * dx + dy * dy;
   double r = sqrt(r2);
-  double dny = (dx * Y.nx + dy * Y.ny) / r;
+  double z1 = ph.k1 * r;
+  double rs1 = rsqrt(z1);
+  double dny = (dx * Y.nx + dy * Y.ny) * (ph.k1 * (rs1 * rs1));
 #pragma unroll
   for (int s = 0; s < 2; ++s) {
     double k = s == 0 ? ph.k1 : ph.k0;
     double eps = s == 0 ? ph.eps1 : ph.eps0;
     Hk h;
-    hankel_fp64(T, k * r, h);
+    if (s == 0)
+      hankel_fp64_rs<false>(T, z1, rs1, h);
+    else
+      hankel_fp64_rs<false>(T, ph.k0 * r, rs1 * ph.s10, h);
     double a = 0.25 * Y.w * k * dny;
     o[s][0] = make_double2(-a * h.h1i, a * h.h1r);
     double bq = -0.25 * eps * Y.w;

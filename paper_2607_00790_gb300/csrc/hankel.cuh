@@ -118,15 +118,14 @@ __device__ __forceinline__ void hk_phase(const HkTables& T, double z, double* E,
   *F = (q & 2) ? -b : b;        // negative for k = 2, 3
 }
 
-// Small argument: ascending series.
-__device__ __forceinline__ void hk_series(const HkTables& T, double z, Hk& o) {
+// Small argument: ascending series (u_in = 1/z).
+__device__ __forceinline__ void hk_series(const HkTables& T, double z, double iz, Hk& o) {
   double u = 0.25 * z * z;
   double j0 = hk_horner<HK_NSER>(T.ser[0], u);
   double j1 = 0.5 * z * hk_horner<HK_NSER>(T.ser[1], u);
   double s0 = hk_horner<HK_NSER>(T.ser[2], u);
   double s1 = hk_horner<HK_NSER>(T.ser[3], u);
   double L = log(0.5 * z);
-  double iz = 1.0 / z;
   double y0 = WSBM_2_OVER_PI * (fma(L + WSBM_EULER, j0, s0));
   // Y1 + 2/(pi z): pole-free part
   double y1h = WSBM_2_OVER_PI * L * j1 - (0.5 / WSBM_PI) * z * s1;
@@ -157,14 +156,15 @@ __device__ __forceinline__ void hk_pq(const HkTables& T, double z, double u, dou
   }
 }
 
-// FP64 H0, H1 and F1 = H1/z + 2i/(pi z^2) at z > 0.
-__device__ __forceinline__ void hankel_fp64(const HkTables& T, double z, Hk& o) {
+// FP64 H0, H1 and (WITH_F1) F1 = H1/z + 2i/(pi z^2) at z > 0, given rs ~ 1/sqrt(z) to a few
+// ulp (callers derive it for both wavenumbers from one reciprocal square root).
+template <bool WITH_F1 = true>
+__device__ __forceinline__ void hankel_fp64_rs(const HkTables& T, double z, double rs, Hk& o) {
+  double u = rs * rs;
   if (z < HK_Z_SERIES) {
-    hk_series(T, z, o);
+    hk_series(T, z, u, o);
     return;
   }
-  double rs = rsqrt(z);
-  double u = rs * rs;
   double A = WSBM_SQRT_2_OVER_PI * rs;
   double E, F;
   hk_phase(T, z, &E, &F);
@@ -177,8 +177,14 @@ __device__ __forceinline__ void hankel_fp64(const HkTables& T, double z, Hk& o) 
   // e^{i(z - 3pi/4)} = -i (E + iF) = F - iE
   o.h1r = fma(P1, F, AQ1 * E);
   o.h1i = fma(AQ1, F, -P1 * E);
-  o.f1r = o.h1r * u;
-  o.f1i = fma(WSBM_2_OVER_PI * u, u, o.h1i * u);
+  if (WITH_F1) {
+    o.f1r = o.h1r * u;
+    o.f1i = fma(WSBM_2_OVER_PI * u, u, o.h1i * u);
+  }
+}
+
+__device__ __forceinline__ void hankel_fp64(const HkTables& T, double z, Hk& o) {
+  hankel_fp64_rs<true>(T, z, rsqrt(z), o);
 }
 
 // Mixed: FP64 phase reduction, FP32 amplitude.  Valid for z >= HK_Z_SERIES.  Also returns
@@ -191,9 +197,13 @@ __device__ __forceinline__ void hankel_mixed_large(const HkTables& T, double z, 
   double n = rint(z * (0.5 / WSBM_PI));
   double y = fma(-n, HK_TWO_PI_HI, z);
   y = fma(-n, HK_TWO_PI_LO, y);
+  // y = yf + ylo: the FP32 rounding of the phase (up to 1.2e-7) is carried to first order
   float yf = (float)y;
-  float sn, cs;
-  sincosf(yf, &sn, &cs);
+  float ylo = (float)(y - (double)yf);
+  float sn0, cs0;
+  sincosf(yf, &sn0, &cs0);
+  float sn = fmaf(cs0, ylo, sn0);
+  float cs = fmaf(-sn0, ylo, cs0);
   float zf = (float)z;
   float rs = rsqrtf(zf);
   float u = rs * rs;

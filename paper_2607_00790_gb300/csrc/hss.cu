@@ -770,8 +770,9 @@ static int factor_level(wsbm_hss* h, int l) {
   // ---- interpolative decompositions: CPQR of Mr (row ID) and Mc (column ID) of every box
   std::vector<QrDesc> qd(2 * nb);
   int32_t *perm = nullptr, *state = nullptr;
-  double *norm2 = nullptr, *tauv = nullptr, *rd0 = nullptr;
+  double *norm2 = nullptr, *nref = nullptr, *tauv = nullptr, *rd0 = nullptr;
   double2* betav = nullptr;
+  HK(dalloc(h, 2 * ntot * sizeof(double), (void**)&nref, tmp));
   HK(dalloc(h, 2 * ntot * sizeof(int32_t), (void**)&perm, tmp));
   HK(dalloc(h, 2 * nb * 2 * sizeof(int32_t), (void**)&state, tmp));
   HK(dalloc(h, 2 * ntot * sizeof(double), (void**)&norm2, tmp));
@@ -792,6 +793,7 @@ static int factor_level(wsbm_hss* h, int l) {
         q.tol = h->cut;
         q.perm = perm + on;
         q.norm2 = norm2 + on;
+        q.nref = nref + on;
         q.tauv = tauv + on;
         q.betav = betav + on;
         q.state = state + 2 * (2 * b + s);

@@ -13,6 +13,8 @@ struct DevGeom {
 
 struct Phys {
   double k0, k1, eps0, eps1;
+  double inv_k0, inv_k1;  // 1/k0, 1/k1
+  double s01, s10;        // sqrt(k0/k1), sqrt(k1/k0): 1/sqrt(k1 r) = s01/sqrt(k0 r)
 };
 
 // One output block of node-pair entries of the WSBM matrix.  A row "slot" t names row node
