@@ -380,10 +380,10 @@ __global__ void __launch_bounds__(256) k_cpqr(const QrDesc* __restrict__ d, int 
       double2* col = M + (int64_t)c * ld;
       const double2* u = M + (int64_t)j * ld;
       double2 w = make_double2(0.0, 0.0);
-      for (int i = j + lane; i < m; i += 32) {  // w = u^H col
+      for (int i = j + lane; i < m; i += 32) {  // w = u^H col, as fused multiply-adds
         double2 ui = u[i], ci = col[i];
-        w.x += ui.x * ci.x + ui.y * ci.y;
-        w.y += ui.x * ci.y - ui.y * ci.x;
+        w.x = fma(ui.x, ci.x, fma(ui.y, ci.y, w.x));
+        w.y = fma(ui.x, ci.y, fma(-ui.y, ci.x, w.y));
       }
       for (int o = 16; o > 0; o >>= 1) {
         w.x += __shfl_xor_sync(0xffffffffu, w.x, o);

@@ -268,7 +268,7 @@ __device__ __forceinline__ void proxy_col_fp64(const HkTables& T, const Phys& ph
 // Mixed precision versions: z = k r formed in FP64 and reduced mod 2 pi in FP64; amplitude and
 // entry algebra in FP32.
 __device__ __forceinline__ void hankel_mixed(const HkTables& T, double z, HkF& o) {
-  if (z >= HK_Z_SERIES) {
+  if (__double2hiint(z) >= HK_SERIES_HI) {
     hankel_mixed_large(T, z, o);
   } else {
     Hk h;
@@ -308,7 +308,7 @@ __device__ __forceinline__ void proxy_row_mixed(const HkTables& T, const Phys& p
     double z = kd * r;
     HkF h;
     float Dr, Di;
-    if (z >= HK_Z_SERIES) {
+    if (__double2hiint(z) >= HK_SERIES_HI) {
       hankel_mixed_large(T, z, h, &Dr, &Di);
     } else {
       Hk hd;

@@ -224,6 +224,8 @@ def main():
     assert all(l == 0 for l in los), "bounds must have a zero low word"
     L.append("// high 32-bit words of the inner interval bounds (their low words are zero)")
     L.append("#define HK_IV_HI {" + ", ".join(str(h) for h in his) + "}")
+    L.append(f"#define HK_SERIES_HI {struct.unpack('<II', struct.pack('<d', BOUNDS[0]))[1]}")
+    L.append(f"#define HK_ASYM_HI {struct.unpack('<II', struct.pack('<d', BOUNDS[-1]))[1]}")
     L.append("// per interval: centre and 1/half-width in u = 1/z")
     L.append("static __device__ const double hk_iv[HK_NIV][2] = {")
     for (a, b, c, ih) in mids:

@@ -88,14 +88,14 @@ __device__ __forceinline__ float hk_hornerf(const float* c, float s) {
 
 // Interval index for HK_Z_SERIES <= z < HK_Z_ASYM from the high word of z (integer compares:
 // the bounds have zero low words, and positive doubles order like their bit patterns).
-__device__ __forceinline__ int hk_interval(double z) {
-  const int hi = __double2hiint(z);
+__device__ __forceinline__ int hk_interval_hi(int hi) {
   const int lim[HK_NIV - 1] = HK_IV_HI;
   int iv = 0;
 #pragma unroll
   for (int k = 0; k < HK_NIV - 1; ++k) iv += (hi >= lim[k]) ? 1 : 0;
   return iv;
 }
+__device__ __forceinline__ int hk_interval(double z) { return hk_interval_hi(__double2hiint(z)); }
 
 // e^{i(z - pi/4)} = E + iF.  z - pi/4 = w + k pi/2 with |w| <= pi/4: k = rint(2z/pi - 1/2),
 // w = z - (k + 1/2) pi/2 by two fused multiply-adds with a two-part pi/2, then
@@ -138,10 +138,10 @@ __device__ __forceinline__ void hk_series(const HkTables& T, double z, double iz
 }
 
 // P_nu - 1 (pm0, pm1) and Q_nu for z >= HK_Z_SERIES, u = 1/z.
-__device__ __forceinline__ void hk_pq(const HkTables& T, double z, double u, double* pm0,
+__device__ __forceinline__ void hk_pq(const HkTables& T, int zhi, double u, double* pm0,
                                       double* Q0, double* pm1, double* Q1) {
-  if (z < HK_Z_ASYM) {
-    int iv = hk_interval(z);
+  if (zhi < HK_ASYM_HI) {
+    int iv = hk_interval_hi(zhi);
     double s = (u - T.iv[iv][0]) * T.iv[iv][1];
     *pm0 = hk_horner<HK_DEG + 1>(T.fit[iv][0], s);
     *Q0 = hk_horner<HK_DEG + 1>(T.fit[iv][1], s);
@@ -161,7 +161,8 @@ __device__ __forceinline__ void hk_pq(const HkTables& T, double z, double u, dou
 template <bool WITH_F1 = true>
 __device__ __forceinline__ void hankel_fp64_rs(const HkTables& T, double z, double rs, Hk& o) {
   double u = rs * rs;
-  if (z < HK_Z_SERIES) {
+  const int zhi = __double2hiint(z);
+  if (zhi < HK_SERIES_HI) {
     hk_series(T, z, u, o);
     return;
   }
@@ -169,7 +170,7 @@ __device__ __forceinline__ void hankel_fp64_rs(const HkTables& T, double z, doub
   double E, F;
   hk_phase(T, z, &E, &F);
   double pm0, Q0, pm1, Q1;
-  hk_pq(T, z, u, &pm0, &Q0, &pm1, &Q1);
+  hk_pq(T, zhi, u, &pm0, &Q0, &pm1, &Q1);
   double P0 = fma(A, pm0, A), AQ0 = A * Q0;
   double P1 = fma(A, pm1, A), AQ1 = A * Q1;
   o.h0r = fma(P0, E, -AQ0 * F);
@@ -211,8 +212,9 @@ __device__ __forceinline__ void hankel_mixed_large(const HkTables& T, double z, 
   float E = (cs + sn) * (float)WSBM_INV_SQRT2;
   float F = (sn - cs) * (float)WSBM_INV_SQRT2;
   float P0, Q0, P1, Q1;  // P0, P1 hold P - 1 until D is formed
-  if (z < HK_Z_ASYM) {
-    int iv = hk_interval(z);
+  const int zhi = __double2hiint(z);
+  if (zhi < HK_ASYM_HI) {
+    int iv = hk_interval_hi(zhi);
     float s = (u - T.ivf[iv][0]) * T.ivf[iv][1];
     P0 = hk_hornerf<HKF_DEG + 1>(T.fitf[iv][0], s);
     Q0 = hk_hornerf<HKF_DEG + 1>(T.fitf[iv][1], s);
