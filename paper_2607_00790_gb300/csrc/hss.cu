@@ -97,6 +97,10 @@ __global__ void k_fill_identity(double2* A, int64_t lda, int n) {
   }
 }
 
+// Identity into each dst (m x n, leading dimension ldd); batched over blockIdx.y.
+struct CopyDesc;
+__global__ void k_fill_identity_batched(const CopyDesc* __restrict__ d);
+
 // L (n x k): L[perm[t], t] = 1 for t < k; L[perm[k+s], t] = T[t + s*ldt]  (T: k x (n-k)).
 struct BuildLDesc {
   double2* L;
@@ -146,6 +150,16 @@ struct CopyDesc {
   int64_t ldd, lds;
   int32_t m, n;
 };
+__global__ void k_fill_identity_batched(const CopyDesc* __restrict__ d) {
+  const CopyDesc q = d[blockIdx.y];
+  int64_t tot = (int64_t)q.m * q.n;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    int i = (int)(e % q.m), j = (int)(e / q.m);
+    q.dst[i + (int64_t)j * q.ldd] = make_double2(i == j ? 1.0 : 0.0, 0.0);
+  }
+}
+
 __global__ void k_copy2d(const CopyDesc* __restrict__ d) {
   const CopyDesc q = d[blockIdx.y];
   int64_t tot = (int64_t)q.m * q.n;
@@ -423,33 +437,6 @@ struct ProxyBatch {
   }
 };
 
-// Transposed copies dst[c + r*ldd] = src[r + c*lds] (r < m, c < n), 32 x 32 tiles via shared memory.
-struct TransDesc {
-  double2* dst;
-  const double2* src;
-  int64_t ldd, lds;
-  int32_t m, n;
-};
-__global__ void k_transpose(const TransDesc* __restrict__ d) {
-  __shared__ double2 tile[32][33];
-  const TransDesc q = d[blockIdx.y];
-  int tm = (q.m + 31) / 32, tn = (q.n + 31) / 32;
-  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 256 threads: 32 x 8
-  for (int t = blockIdx.x; t < tm * tn; t += gridDim.x) {
-    int r0 = (t % tm) * 32, c0 = (t / tm) * 32;
-    __syncthreads();
-    for (int k = ty; k < 32; k += 8) {
-      int r = r0 + tx, c = c0 + k;
-      if (r < q.m && c < q.n) tile[k][tx] = q.src[r + (int64_t)c * q.lds];
-    }
-    __syncthreads();
-    for (int k = ty; k < 32; k += 8) {
-      int c = c0 + tx, r = r0 + k;
-      if (r < q.m && c < q.n) q.dst[c + (int64_t)r * q.ldd] = tile[tx][k];
-    }
-  }
-}
-
 static void box_circle(const wsbm_hss* h, Box& b) {
   double xmin = h->hx[b.lo], xmax = xmin, ymin = h->hy[b.lo], ymax = ymin;
   for (int64_t i = b.lo + 1; i < b.hi; ++i) {
@@ -469,9 +456,9 @@ static void box_circle(const wsbm_hss* h, Box& b) {
   }
   b.R = R;
   b.rho = h->prm.proxy_ratio * R;
-  // proxy count: the leaf value, grown so the circle resolves k1 rho plus enough evanescent
-  // modes for the cutoff (modes decay like (R/rho)^m)
-  double need = 2.0 * (h->ph.k1 * b.rho + log(1.0 / h->cut) / log(h->prm.proxy_ratio));
+  // proxy count: the leaf value, grown with the circle so it carries the k1 rho propagating
+  // modes plus the evanescent ones down to the cutoff (they decay like (R/rho)^m)
+  double need = h->ph.k1 * b.rho + log(1.0 / h->cut) / log(h->prm.proxy_ratio);
   int P = (int)ceil(need);
   if (P < h->prm.nproxy) P = h->prm.nproxy;
   P = (P + 7) / 8 * 8;
@@ -610,31 +597,31 @@ static int factor_level(wsbm_hss* h, int l) {
   const int nb = (int)LV.box.size();
   std::vector<void*> tmp;
   cudaStream_t st = h->st;
-  // ---- near lists: boxes with a candidate node inside the proxy circle, and curve neighbours.
-  // Only boxes whose bounding circle meets the proxy circle are scanned node by node.
+  // ---- near candidates: the candidate rows / columns of the other boxes of this level whose
+  // nodes lie inside the proxy circle.  Everything outside the circle is represented by the
+  // proxy sources, whatever box it belongs to.  Only boxes whose bounding circle meets the
+  // proxy circle are scanned.
+  std::vector<std::vector<int32_t>> NR(nb), NC(nb);
   for (int b = 0; b < nb; ++b) {
     Box& B = LV.box[b];
     B.near.clear();
-    for (int s = 0; s < nb; ++s) {
-      if (s == b) continue;
-      bool nb_adj = (s == (b + 1) % nb) || (s == (b + nb - 1) % nb);
-      bool inside = false;
-      const Box& S = LV.box[s];
+    const double r2 = B.rho * B.rho;
+    for (int s2 = 0; s2 < nb; ++s2) {
+      if (s2 == b) continue;
+      const Box& S = LV.box[s2];
       double cdx = S.cx - B.cx, cdy = S.cy - B.cy;
       double reach = B.rho + S.R;
-      if (!nb_adj && cdx * cdx + cdy * cdy < reach * reach) {
-        for (size_t t = 0; t < S.cr.size() && !inside; ++t) {
-          int32_t node = S.cr[t] >> 1;
-          double dx = h->hx[node] - B.cx, dy = h->hy[node] - B.cy;
-          if (dx * dx + dy * dy < B.rho * B.rho) inside = true;
-        }
-        for (size_t t = 0; t < S.cc.size() && !inside; ++t) {
-          int32_t node = S.cc[t] >> 1;
-          double dx = h->hx[node] - B.cx, dy = h->hy[node] - B.cy;
-          if (dx * dx + dy * dy < B.rho * B.rho) inside = true;
-        }
+      if (cdx * cdx + cdy * cdy >= reach * reach) continue;
+      size_t nr0 = NR[b].size(), nc0 = NC[b].size();
+      for (int32_t u : S.cr) {
+        double dx = h->hx[u >> 1] - B.cx, dy = h->hy[u >> 1] - B.cy;
+        if (dx * dx + dy * dy < r2) NR[b].push_back(u);
       }
-      if (nb_adj || inside) B.near.push_back(s);
+      for (int32_t u : S.cc) {
+        double dx = h->hx[u >> 1] - B.cx, dy = h->hy[u >> 1] - B.cy;
+        if (dx * dx + dy * dy < r2) NC[b].push_back(u);
+      }
+      if (NR[b].size() > nr0 || NC[b].size() > nc0) B.near.push_back(s2);
     }
   }
   // ---- storage: D (factor, kept), ID matrices (temporary)
@@ -644,13 +631,8 @@ static int factor_level(wsbm_hss* h, int l) {
   for (int b = 0; b < nb; ++b) {
     Box& B = LV.box[b];
     B.n = (int)B.cr.size();
-    int64_t nearr = 0, nearc = 0;
-    for (int s : B.near) {
-      nearc += (int64_t)LV.box[s].cc.size();
-      nearr += (int64_t)LV.box[s].cr.size();
-    }
-    mr[b] = 2 * (int64_t)B.P + nearc;
-    mc[b] = 2 * (int64_t)B.P + nearr;
+    mr[b] = 2 * (int64_t)B.P + (int64_t)NC[b].size();
+    mc[b] = 2 * (int64_t)B.P + (int64_t)NR[b].size();
     Dtot += (size_t)B.n * B.n;
     Mtot += (size_t)(mr[b] + mc[b]) * B.n;
     ntot += B.n;
@@ -676,23 +658,9 @@ static int factor_level(wsbm_hss* h, int l) {
       oM += (size_t)mc[b] * B.n;
     }
   }
-  // ---- entries: diagonal blocks (leaf) or sibling blocks (upper), near blocks, proxy blocks.
-  // A near block A(I_b, I_s) feeds the row ID of b (stored transposed) and, when b is also
-  // near s, the column ID of s: it is generated once, into the column-ID matrix of s, and
-  // transposed into the row-ID matrix of b.
+  // ---- entries: diagonal blocks (leaf) or sibling blocks (upper), near blocks, proxy blocks
   PairBatch pb(h->slot_scratch);
   std::vector<CopyDesc> copies;
-  std::vector<TransDesc> trans;
-  std::vector<std::vector<int64_t>> offc_of(nb);  // offc_of[s][j]: row offset of near box j in Mc[s]
-  for (int s2 = 0; s2 < nb; ++s2) {
-    Box& S = LV.box[s2];
-    int64_t off = 2 * (int64_t)S.P;
-    offc_of[s2].resize(S.near.size());
-    for (size_t j = 0; j < S.near.size(); ++j) {
-      offc_of[s2][j] = off;
-      off += (int64_t)LV.box[S.near[j]].cr.size();
-    }
-  }
   for (int b = 0; b < nb; ++b) {
     Box& B = LV.box[b];
     if (l == h->L) {
@@ -708,28 +676,9 @@ static int factor_level(wsbm_hss* h, int l) {
       copies.push_back(c1);
       copies.push_back(c2);
     }
-    // column ID of b: near rows A(I_s, I_b) for every s in near(b)
-    for (size_t j = 0; j < B.near.size(); ++j) {
-      Box& S = LV.box[B.near[j]];
-      pb.add(S.cr, (int)offc_of[b][j], B.cc, 0, Mc[b], mc[b], 0);
-    }
-  }
-  for (int b = 0; b < nb; ++b) {
-    // row ID of b: near columns A(I_b, I_s), copied from Mc[s] when b is near s
-    Box& B = LV.box[b];
-    int64_t offr = 2 * (int64_t)B.P;
-    for (int s2 : B.near) {
-      Box& S = LV.box[s2];
-      auto it = std::find(S.near.begin(), S.near.end(), b);
-      if (it != S.near.end()) {
-        int64_t oc = offc_of[s2][it - S.near.begin()];
-        trans.push_back({Mr[b] + offr, Mc[s2] + oc, mr[b], mc[s2], (int32_t)B.cr.size(),
-                         (int32_t)S.cc.size()});
-      } else {
-        pb.add(B.cr, 0, S.cc, (int)offr, Mr[b], mr[b], 1);
-      }
-      offr += (int64_t)S.cc.size();
-    }
+    // row ID matrix (stored transposed: rows = near columns) and column ID matrix
+    pb.add(B.cr, 0, NC[b], 2 * B.P, Mr[b], mr[b], 1);
+    pb.add(NR[b], 2 * B.P, B.cc, 0, Mc[b], mc[b], 0);
   }
   ProxyBatch xb(h->slot_scratch);
   for (int b = 0; b < nb; ++b) {
@@ -745,8 +694,6 @@ static int factor_level(wsbm_hss* h, int l) {
     k_copy2d<<<dim3(gridfor(mx), (unsigned)copies.size()), 256, 0, st>>>(dc);
     wsbm_count_launch();
   }
-  TransDesc* dtr = nullptr;
-  HK(upload(h, trans, &dtr, tmp));
   HK(pb.prepare(h, tmp));
   HK(xb.prepare(h, tmp));
   // timed: the two entry kernels only
@@ -755,12 +702,6 @@ static int factor_level(wsbm_hss* h, int l) {
   HC(cudaEventRecord(h->ev[4], st));
   HK(xb.run(h));
   HC(cudaEventRecord(h->ev[1], st));
-  if (!trans.empty()) {
-    int64_t mx = 0;
-    for (auto& t : trans) mx = std::max(mx, (int64_t)((t.m + 31) / 32) * ((t.n + 31) / 32));
-    k_transpose<<<dim3((unsigned)std::min<int64_t>(mx, 64), (unsigned)trans.size()), 256, 0, st>>>(dtr);
-    wsbm_count_launch();
-  }
   h->stats.entries_generated += pb.entries + xb.entries;
   h->stats.pairs_evaluated += pb.pairs + xb.pairs;
   h->stats.entries_pairs += pb.entries;
@@ -974,9 +915,12 @@ static int factor_level(wsbm_hss* h, int l) {
   if (!gm.empty()) HK(wsbm_gemm_batched(dgm, (int)gm.size(), maxk, maxk, st));
   if (!tcc.empty()) { k_copy2d<<<dim3(gridfor(maxnk), (unsigned)tcc.size()), 256, 0, st>>>(dtcc); wsbm_count_launch(); }
   HK(wsbm_lu_batched(dluM, nb, maxk, nullptr, st));
-  for (int b = 0; b < nb; ++b) {
-    Box& B = LV.box[b];
-    k_fill_identity<<<gridfor((int64_t)B.k * B.k), 256, 0, st>>>(B.Dc, B.k, B.k);
+  {
+    std::vector<CopyDesc> idd;
+    for (int b = 0; b < nb; ++b) idd.push_back({LV.box[b].Dc, nullptr, LV.box[b].k, 0, LV.box[b].k, LV.box[b].k});
+    CopyDesc* didd = nullptr;
+    HK(upload(h, idd, &didd, tmp));
+    k_fill_identity_batched<<<dim3(gridfor((int64_t)maxk * maxk), nb), 256, 0, st>>>(didd);
     wsbm_count_launch();
   }
   HK(wsbm_lu_solve_batched(dml, dml, nb, maxk, maxk, st));
@@ -995,7 +939,7 @@ static int factor_level(wsbm_hss* h, int l) {
   h->stats.ms_entries += elapsed(h->ev[0], h->ev[1]);
   h->stats.ms_pairs += elapsed(h->ev[0], h->ev[4]);
   h->stats.ms_proxy += elapsed(h->ev[4], h->ev[1]);
-  h->stats.ms_id += elapsed(h->ev[1], h->ev[2]);  // includes the near-block transposes
+  h->stats.ms_id += elapsed(h->ev[1], h->ev[2]);
   h->stats.ms_factor += elapsed(h->ev[2], h->ev[3]);
   // skeletons
   {
