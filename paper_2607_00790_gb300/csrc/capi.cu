@@ -113,6 +113,7 @@ extern "C" int wsbm_entries_raw(const wsbm_geom* g, const wsbm_params* p, const 
     t.nc = (int32_t)nc;
     t.trans = 0;
     t.tile0 = 0;
+    t.fastc = 0;
     DevGeom dg = wsbm_devgeom(g);
     if ((rc = wsbm_launch_unknowns_to_slots(rows, nr, g->n, rnode, rpos, st))) goto done;
     if ((rc = wsbm_launch_unknowns_to_slots(cols, nc, g->n, cnode, cpos, st))) goto done;

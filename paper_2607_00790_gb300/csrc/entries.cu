@@ -5,7 +5,9 @@
 // z1 = k1 r once and writes all entries of its 2x2 block, so every unit costs the same (the
 // paper balances threads the same way: each block A_ij carries the same seven layer-potential
 // terms).  A CTA stages the node data of a 32 x 4 tile in shared memory; the 32 slots of the
-// fast dimension map to consecutive output rows, so a warp's complex128 stores are contiguous.
+// fast dimension normally map to consecutive output rows, so a warp's complex128 stores are
+// contiguous; for short-by-long blocks the longer list takes the fast dimension instead (the
+// kernels are FP64-bound, so fewer idle lanes beat coalesced stores).
 // Launches are grid-stride over a flat tile list spanning many blocks (all boxes of a tree
 // level in one launch).
 #include <math.h>
@@ -134,8 +136,9 @@ __global__ void __launch_bounds__(WSBM_PAIR_THREADS)
   for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     int ti = find_task_by_tile(&tasks[0].tile0, stride, ntasks, tile);
     const PairTask tk = tasks[ti];
-    const int nf = tk.trans ? tk.nc : tk.nr;
-    const int ns = tk.trans ? tk.nr : tk.nc;
+    const bool fc = tk.fastc != 0;
+    const int nf = fc ? tk.nc : tk.nr;
+    const int ns = fc ? tk.nr : tk.nc;
     const int nft = (nf + WSBM_TILE_F - 1) / WSBM_TILE_F;
     const int64_t lt = tile - tk.tile0;
     const int f0 = (int)(lt % nft) * WSBM_TILE_F;
@@ -144,7 +147,7 @@ __global__ void __launch_bounds__(WSBM_PAIR_THREADS)
     if (threadIdx.x < WSBM_TILE_F) {
       int f = f0 + threadIdx.x;
       if (f < nf) {
-        if (tk.trans)
+        if (fc)
           load_slot(g, tk.cnode, tk.cpos, f, sf[threadIdx.x]);
         else
           load_slot(g, tk.rnode, tk.rpos, f, sf[threadIdx.x]);
@@ -153,7 +156,7 @@ __global__ void __launch_bounds__(WSBM_PAIR_THREADS)
       int k = threadIdx.x - WSBM_TILE_F;
       int s = s0 + k;
       if (s < ns) {
-        if (tk.trans)
+        if (fc)
           load_slot(g, tk.rnode, tk.rpos, s, ss[k]);
         else
           load_slot(g, tk.cnode, tk.cpos, s, ss[k]);
@@ -162,8 +165,8 @@ __global__ void __launch_bounds__(WSBM_PAIR_THREADS)
     __syncthreads();
     const int f = f0 + tx, s = s0 + ty;
     if (f < nf && s < ns) {
-      const SlotData& R = tk.trans ? ss[ty] : sf[tx];
-      const SlotData& C = tk.trans ? sf[tx] : ss[ty];
+      const SlotData& R = fc ? ss[ty] : sf[tx];
+      const SlotData& C = fc ? sf[tx] : ss[ty];
       double2 e[2][2];
       if (R.node == C.node) {
         block_diag(ph, R.w, R.kap, e);
@@ -480,8 +483,8 @@ static int grid_for(int64_t ntiles) {
   return (int)(ntiles < cap ? ntiles : cap);
 }
 
-int64_t wsbm_pair_tiles(int32_t nr, int32_t nc, int32_t trans) {
-  int32_t nf = trans ? nc : nr, ns = trans ? nr : nc;
+int64_t wsbm_pair_tiles(int32_t nr, int32_t nc, int32_t fastc) {
+  int32_t nf = fastc ? nc : nr, ns = fastc ? nr : nc;
   if (nf <= 0 || ns <= 0) return 0;
   return (int64_t)((nf + WSBM_TILE_F - 1) / WSBM_TILE_F) * ((ns + WSBM_TILE_S - 1) / WSBM_TILE_S);
 }

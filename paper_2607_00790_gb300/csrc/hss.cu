@@ -361,7 +361,10 @@ struct PairBatch {
     t.nc = (int32_t)cn.size();
     t.trans = trans;
     t.tile0 = (int32_t)tiles;
-    tiles += wsbm_pair_tiles(t.nr, t.nc, trans);
+    // the longer slot list runs along the 32-wide fast dimension (fewer idle lanes); for
+    // equal lengths the one that gives contiguous stores
+    t.fastc = t.nc > t.nr ? 1 : (t.nc < t.nr ? 0 : trans);
+    tiles += wsbm_pair_tiles(t.nr, t.nc, t.fastc);
     entries += (int64_t)rowU.size() * colU.size();
     pairs += (int64_t)rn.size() * cn.size();
     tasks.push_back(t);

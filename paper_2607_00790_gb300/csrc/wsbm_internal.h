@@ -29,8 +29,10 @@ struct PairTask {
   double2* out;
   int64_t ld;
   int32_t nr, nc;
-  int32_t trans;
+  int32_t trans;  // output layout (see above)
   int32_t tile0;  // index of this task's first tile in the launch
+  int32_t fastc;  // 1: column slots run along the 32-wide fast tile dimension, 0: row slots
+  int32_t pad;
 };
 
 // One proxy-circle block (proxy-surface method).  Box slot t names node node[t]; its
@@ -60,7 +62,7 @@ int wsbm_launch_pairs(const DevGeom& g, const Phys& ph, const PairTask* d_tasks,
                       int64_t ntiles, cudaStream_t st);
 int wsbm_launch_proxy(const DevGeom& g, const Phys& ph, const ProxyTask* d_tasks, int ntasks,
                       int64_t ntiles, int mixed, cudaStream_t st);
-int64_t wsbm_pair_tiles(int32_t nr, int32_t nc, int32_t trans);
+int64_t wsbm_pair_tiles(int32_t nr, int32_t nc, int32_t fastc);
 int64_t wsbm_proxy_tiles(int32_t nn, int32_t P);
 int wsbm_launch_hankel(const double* z, int64_t n, double* out, int mixed, cudaStream_t st);
 int wsbm_launch_unknowns_to_slots(const int64_t* idx, int64_t n, int64_t N, int32_t* node,
