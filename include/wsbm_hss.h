@@ -205,6 +205,32 @@ int wsbm_stats(wsbm_hss_t h, wsbm_stats_t* s);
 /* Release every device buffer of the handle. */
 void wsbm_destroy(wsbm_hss_t h);
 
+/* ------------------------------------------------------------------ batched builds ---- */
+
+/* Batches of independent scatterers (each curve with its own physics and parameters, all
+ * sharing one stream).  wsbm_batch_factor builds and factors every curve with one launch per
+ * phase per tree level over all curves (curves of different depth are aligned at their leaves,
+ * each stops compressing by its own rule), then all dense roots in one batched LU: the paper's
+ * "same number of layer potentials per block" load balance carried across many scatterers.
+ * Results are identical to factoring each curve alone. */
+typedef struct wsbm_batch* wsbm_batch_t;
+
+/* g[0..count), p[0..count): as for wsbm_create (geometry copied).  Errors as wsbm_create. */
+int wsbm_batch_create(const wsbm_geom* g, const wsbm_params* p, int32_t count, void* stream,
+                      wsbm_batch_t* out);
+
+/* Synchronous.  Errors: OOM, CUDA, RANK_OVERFLOW (any curve). */
+int wsbm_batch_factor(wsbm_batch_t b);
+
+/* Handle of curve i (owned by the batch: use it for rhs / solve / far field / stats, do not
+ * destroy it). */
+int wsbm_batch_handle(wsbm_batch_t b, int32_t i, wsbm_hss_t* out);
+
+/* Timings of the shared launches and summed counters of the last wsbm_batch_factor. */
+int wsbm_batch_stats(wsbm_batch_t b, wsbm_stats_t* s);
+
+void wsbm_batch_destroy(wsbm_batch_t b);
+
 /* Static name of an error code. */
 const char* wsbm_strerror(int code);
 

@@ -84,11 +84,19 @@ def lib():
         L.wsbm_stats.argtypes = [vp, ctypes.POINTER(Stats)]
         L.wsbm_destroy.argtypes = [vp]
         L.wsbm_destroy.restype = None
+        L.wsbm_batch_create.argtypes = [ctypes.POINTER(Geom), ctypes.POINTER(Params), i32, vp,
+                                        ctypes.POINTER(vp)]
+        L.wsbm_batch_factor.argtypes = [vp]
+        L.wsbm_batch_handle.argtypes = [vp, i32, ctypes.POINTER(vp)]
+        L.wsbm_batch_stats.argtypes = [vp, ctypes.POINTER(Stats)]
+        L.wsbm_batch_destroy.argtypes = [vp]
+        L.wsbm_batch_destroy.restype = None
         L.wsbm_strerror.argtypes = [ctypes.c_int]
         L.wsbm_strerror.restype = ctypes.c_char_p
         for f in ("wsbm_hankel01", "wsbm_entries_raw", "wsbm_proxy_block", "wsbm_create",
                   "wsbm_factor", "wsbm_rhs_planewave", "wsbm_solve", "wsbm_farfield",
-                  "wsbm_entries", "wsbm_box_info", "wsbm_stats"):
+                  "wsbm_entries", "wsbm_box_info", "wsbm_stats", "wsbm_batch_create",
+                  "wsbm_batch_factor", "wsbm_batch_handle", "wsbm_batch_stats"):
             getattr(L, f).restype = ctypes.c_int
         _LIB = L
     return _LIB
@@ -157,9 +165,13 @@ def wsbm_proxy_block(geom, params, side, idx, circle, P):
 class Solver:
     """wsbm_create / wsbm_factor / wsbm_solve / wsbm_farfield on one handle."""
 
-    def __init__(self, geom, params, device="cuda"):
+    def __init__(self, geom, params, device="cuda", _handle=None):
         self.device = torch.device(device)
         self.n = geom.n
+        self.owned = _handle is None
+        if _handle is not None:
+            self.h = _handle
+            return
         h = ctypes.c_void_p()
         _check(lib().wsbm_create(ctypes.byref(geom), ctypes.byref(params), _stream(self.device),
                                  ctypes.byref(h)), "wsbm_create")
@@ -211,8 +223,48 @@ class Solver:
         return s.as_dict()
 
     def close(self):
-        if self.h:
+        if self.h and self.owned:
             lib().wsbm_destroy(self.h)
+        self.h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """wsbm_batch_*: many curves built and factored with shared launches per tree level."""
+
+    def __init__(self, geoms, params, device="cuda"):
+        self.device = torch.device(device)
+        n = len(geoms)
+        G = (Geom * n)(*geoms)
+        P = (Params * n)(*params)
+        h = ctypes.c_void_p()
+        _check(lib().wsbm_batch_create(G, P, n, _stream(self.device), ctypes.byref(h)),
+               "wsbm_batch_create")
+        self.h = h
+        self.sizes = [g.n for g in geoms]
+
+    def factor(self):
+        _check(lib().wsbm_batch_factor(self.h), "wsbm_batch_factor")
+
+    def solver(self, i):
+        hh = ctypes.c_void_p()
+        _check(lib().wsbm_batch_handle(self.h, i, ctypes.byref(hh)), "wsbm_batch_handle")
+        g = Geom(self.sizes[i])
+        return Solver(g, None, self.device, _handle=hh)
+
+    def stats(self):
+        s = Stats()
+        _check(lib().wsbm_batch_stats(self.h, ctypes.byref(s)), "wsbm_batch_stats")
+        return s.as_dict()
+
+    def close(self):
+        if self.h:
+            lib().wsbm_batch_destroy(self.h)
             self.h = ctypes.c_void_p()
 
     def __del__(self):

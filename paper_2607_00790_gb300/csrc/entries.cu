@@ -125,7 +125,8 @@ __device__ __forceinline__ void load_slot(const DevGeom& g, const int32_t* nodes
 }
 
 __global__ void __launch_bounds__(WSBM_PAIR_THREADS)
-    k_pairs(DevGeom g, Phys ph, const PairTask* __restrict__ tasks, int ntasks, int64_t ntiles) {
+    k_pairs(DevGeom g0, Phys ph0, const PairTask* __restrict__ tasks, int ntasks, int64_t ntiles,
+            const DevGeom* __restrict__ geos, const Phys* __restrict__ phys) {
   __shared__ HkTables T;
   __shared__ SlotData sf[WSBM_TILE_F];
   __shared__ SlotData ss[WSBM_TILE_S];
@@ -136,6 +137,8 @@ __global__ void __launch_bounds__(WSBM_PAIR_THREADS)
   for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     int ti = find_task_by_tile(&tasks[0].tile0, stride, ntasks, tile);
     const PairTask tk = tasks[ti];
+    const DevGeom g = geos ? geos[tk.inst] : g0;
+    const Phys ph = phys ? phys[tk.inst] : ph0;
     const bool fc = tk.fastc != 0;
     const int nf = fc ? tk.nc : tk.nr;
     const int ns = fc ? tk.nr : tk.nc;
@@ -363,7 +366,8 @@ __device__ __forceinline__ void proxy_col_mixed(const HkTables& T, const Phys& p
 
 template <bool MIXED>
 __global__ void __launch_bounds__(WSBM_PAIR_THREADS)
-    k_proxy(DevGeom g, Phys ph, const ProxyTask* __restrict__ tasks, int ntasks, int64_t ntiles) {
+    k_proxy(DevGeom g0, Phys ph0, const ProxyTask* __restrict__ tasks, int ntasks, int64_t ntiles,
+            const DevGeom* __restrict__ geos, const Phys* __restrict__ phys) {
   __shared__ HkTables T;
   __shared__ ProxyPt sp[WSBM_TILE_F];
   __shared__ SlotData ss[WSBM_TILE_S];
@@ -374,6 +378,8 @@ __global__ void __launch_bounds__(WSBM_PAIR_THREADS)
   for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     int ti = find_task_by_tile(&tasks[0].tile0, stride, ntasks, tile);
     const ProxyTask tk = tasks[ti];
+    const DevGeom g = geos ? geos[tk.inst] : g0;
+    const Phys ph = phys ? phys[tk.inst] : ph0;
     const int nft = (tk.P + WSBM_TILE_F - 1) / WSBM_TILE_F;
     const int64_t lt = tile - tk.tile0;
     const int m0 = (int)(lt % nft) * WSBM_TILE_F;
@@ -495,20 +501,21 @@ int64_t wsbm_proxy_tiles(int32_t nn, int32_t P) {
 }
 
 int wsbm_launch_pairs(const DevGeom& g, const Phys& ph, const PairTask* d_tasks, int ntasks,
-                      int64_t ntiles, cudaStream_t st) {
+                      int64_t ntiles, cudaStream_t st, const DevGeom* geos, const Phys* phys) {
   if (ntiles <= 0) return WSBM_OK;
-  k_pairs<<<grid_for(ntiles), WSBM_PAIR_THREADS, 0, st>>>(g, ph, d_tasks, ntasks, ntiles);
+  k_pairs<<<grid_for(ntiles), WSBM_PAIR_THREADS, 0, st>>>(g, ph, d_tasks, ntasks, ntiles, geos, phys);
   wsbm_count_launch();
   return cudaGetLastError() == cudaSuccess ? WSBM_OK : WSBM_ERR_CUDA;
 }
 
 int wsbm_launch_proxy(const DevGeom& g, const Phys& ph, const ProxyTask* d_tasks, int ntasks,
-                      int64_t ntiles, int mixed, cudaStream_t st) {
+                      int64_t ntiles, int mixed, cudaStream_t st, const DevGeom* geos,
+                      const Phys* phys) {
   if (ntiles <= 0) return WSBM_OK;
   if (mixed)
-    k_proxy<true><<<grid_for(ntiles), WSBM_PAIR_THREADS, 0, st>>>(g, ph, d_tasks, ntasks, ntiles);
+    k_proxy<true><<<grid_for(ntiles), WSBM_PAIR_THREADS, 0, st>>>(g, ph, d_tasks, ntasks, ntiles, geos, phys);
   else
-    k_proxy<false><<<grid_for(ntiles), WSBM_PAIR_THREADS, 0, st>>>(g, ph, d_tasks, ntasks, ntiles);
+    k_proxy<false><<<grid_for(ntiles), WSBM_PAIR_THREADS, 0, st>>>(g, ph, d_tasks, ntasks, ntiles, geos, phys);
   wsbm_count_launch();
   return cudaGetLastError() == cudaSuccess ? WSBM_OK : WSBM_ERR_CUDA;
 }

@@ -324,10 +324,9 @@ static void make_slots(const std::vector<int32_t>& U, int base, std::vector<int3
   for (int32_t nd : nodes) at[nd] = -1;
 }
 
-// A flat list of pair tasks for one launch; slot arrays are concatenated and uploaded once.
+// A flat list of pair tasks for one launch (possibly over several curves: `inst` selects the
+// curve's geometry and physics); slot arrays are concatenated and uploaded once.
 struct PairBatch {
-  std::vector<int32_t>& at;
-  explicit PairBatch(std::vector<int32_t>& a) : at(a) {}
   std::vector<PairTask> tasks;
   PairTask* dtasks = nullptr;
   std::vector<int32_t> ints;  // slot data
@@ -337,9 +336,10 @@ struct PairBatch {
   std::vector<Ref> refs;
   int64_t tiles = 0, entries = 0, pairs = 0;
 
-  void add(const std::vector<int32_t>& rowU, int rbase, const std::vector<int32_t>& colU, int cbase,
-           double2* out, int64_t ld, int trans) {
-    if (rowU.empty() || colU.empty()) return;
+  // entries of the block (rowU x colU) of curve `inst`; `at` is that curve's slot scratch
+  int64_t add(int inst, std::vector<int32_t>& at, const std::vector<int32_t>& rowU, int rbase,
+              const std::vector<int32_t>& colU, int cbase, double2* out, int64_t ld, int trans) {
+    if (rowU.empty() || colU.empty()) return 0;
     std::vector<int32_t> rn, rp, cn, cp;
     make_slots(rowU, rbase, rn, rp, at);
     make_slots(colU, cbase, cn, cp, at);
@@ -361,13 +361,16 @@ struct PairBatch {
     t.nc = (int32_t)cn.size();
     t.trans = trans;
     t.tile0 = (int32_t)tiles;
+    t.inst = inst;
     // the longer slot list runs along the 32-wide fast dimension (fewer idle lanes); for
     // equal lengths the one that gives contiguous stores
     t.fastc = t.nc > t.nr ? 1 : (t.nc < t.nr ? 0 : trans);
     tiles += wsbm_pair_tiles(t.nr, t.nc, t.fastc);
-    entries += (int64_t)rowU.size() * colU.size();
+    int64_t e = (int64_t)rowU.size() * colU.size();
+    entries += e;
     pairs += (int64_t)rn.size() * cn.size();
     tasks.push_back(t);
+    return e;
   }
 
   // upload slot data and task list (before any timed region)
@@ -383,22 +386,21 @@ struct PairBatch {
     }
     return upload(h, tasks, &dtasks, tmp);
   }
-  int run(wsbm_hss* h) {
+  int run(wsbm_hss* h, const DevGeom* geos, const Phys* phys) {
     if (tasks.empty()) return WSBM_OK;
-    return wsbm_launch_pairs(h->g, h->ph, dtasks, (int)tasks.size(), tiles, h->st);
+    return wsbm_launch_pairs(h->g, h->ph, dtasks, (int)tasks.size(), tiles, h->st, geos, phys);
   }
 };
 
 struct ProxyBatch {
-  std::vector<int32_t>& at;
-  explicit ProxyBatch(std::vector<int32_t>& a) : at(a) {}
   std::vector<ProxyTask> tasks;
   ProxyTask* dtasks = nullptr;
   std::vector<int32_t> ints;
   std::vector<std::pair<int64_t, int64_t>> refs;
   int64_t tiles = 0, entries = 0, pairs = 0;
 
-  void add(const std::vector<int32_t>& U, const Box& b, int side, double2* out, int64_t ld) {
+  int64_t add(int inst, std::vector<int32_t>& at, const std::vector<int32_t>& U, const Box& b,
+              int side, double2* out, int64_t ld) {
     std::vector<int32_t> nn, pp;
     make_slots(U, 0, nn, pp, at);
     refs.push_back({(int64_t)ints.size(), (int64_t)ints.size() + (int64_t)nn.size()});
@@ -417,10 +419,13 @@ struct ProxyBatch {
     t.tr = 0;
     t.off = 0;
     t.tile0 = (int32_t)tiles;
+    t.inst = inst;
     tiles += wsbm_proxy_tiles(t.nn, t.P);
-    entries += (int64_t)U.size() * 2 * b.P;
+    int64_t e = (int64_t)U.size() * 2 * b.P;
+    entries += e;
     pairs += (int64_t)nn.size() * b.P;
     tasks.push_back(t);
+    return e;
   }
 
   int prepare(wsbm_hss* h, std::vector<void*>& tmp) {
@@ -433,10 +438,9 @@ struct ProxyBatch {
     }
     return upload(h, tasks, &dtasks, tmp);
   }
-  int run(wsbm_hss* h) {
+  int run(wsbm_hss* h, int mixed, const DevGeom* geos, const Phys* phys) {
     if (tasks.empty()) return WSBM_OK;
-    return wsbm_launch_proxy(h->g, h->ph, dtasks, (int)tasks.size(), tiles,
-                             h->prm.precision == WSBM_MIXED, h->st);
+    return wsbm_launch_proxy(h->g, h->ph, dtasks, (int)tasks.size(), tiles, mixed, h->st, geos, phys);
   }
 };
 
@@ -594,174 +598,229 @@ extern "C" void wsbm_destroy(wsbm_hss_t h) {
 }
 
 // ---------------------------------------------------------------------- one level ----
-// Compress and factor every box of level l.  Candidates (cr, cc) must be set.
-static int factor_level(wsbm_hss* h, int l) {
-  Level& LV = h->lv[l];
-  const int nb = (int)LV.box.size();
+// A box of one tree level of one curve, as seen by a (possibly batched) level build.
+struct BoxRef {
+  wsbm_hss* h;
+  int inst;  // index of h in the batch (selects geometry and physics in the kernels)
+  int l, b;
+  Box& box() const { return h->lv[l].box[b]; }
+};
+
+// Per-launch device copies of the curves' geometry and physics, indexed by instance.
+struct InstArrays {
+  DevGeom* geos = nullptr;
+  Phys* phys = nullptr;
+};
+static int upload_instances(wsbm_hss* h0, const std::vector<wsbm_hss*>& hs, InstArrays* ia,
+                            std::vector<void*>& tmp) {
+  std::vector<DevGeom> g;
+  std::vector<Phys> p;
+  for (auto* h : hs) {
+    g.push_back(h->g);
+    p.push_back(h->ph);
+  }
+  HK(upload(h0, g, &ia->geos, tmp));
+  return upload(h0, p, &ia->phys, tmp);
+}
+
+// Compress and factor one tree level of each item (a curve and its level): every phase is one
+// launch over all boxes of all items (entries, proxy blocks, IDs, LU, D^-1 L, Dhat).  All
+// handles share one stream.  Candidates (cr, cc) of every box must be set.
+static int factor_levels(const std::vector<wsbm_hss*>& hs, const std::vector<int>& levels,
+                         double ms_out[4]) {
+  wsbm_hss* h0 = hs[0];
+  cudaStream_t st = h0->st;
   std::vector<void*> tmp;
-  cudaStream_t st = h->st;
-  // ---- near candidates: the candidate rows / columns of the other boxes of this level whose
-  // nodes lie inside the proxy circle.  Everything outside the circle is represented by the
-  // proxy sources, whatever box it belongs to.  Only boxes whose bounding circle meets the
+  std::vector<BoxRef> R;
+  for (size_t i = 0; i < hs.size(); ++i) {
+    if (levels[i] < 1) continue;
+    int nb = (int)hs[i]->lv[levels[i]].box.size();
+    for (int b = 0; b < nb; ++b) R.push_back({hs[i], (int)i, levels[i], b});
+  }
+  const int NB = (int)R.size();
+  if (NB == 0) return WSBM_OK;
+  InstArrays ia;
+  HK(upload_instances(h0, hs, &ia, tmp));
+  // ---- near candidates: the candidate rows / columns of the other boxes of the same level
+  // whose nodes lie inside the proxy circle.  Everything outside the circle is represented by
+  // the proxy sources, whatever box it belongs to.  Only boxes whose bounding circle meets the
   // proxy circle are scanned.
-  std::vector<std::vector<int32_t>> NR(nb), NC(nb);
-  for (int b = 0; b < nb; ++b) {
-    Box& B = LV.box[b];
+  std::vector<std::vector<int32_t>> NR(NB), NC(NB);
+  for (int r = 0; r < NB; ++r) {
+    wsbm_hss* h = R[r].h;
+    Level& LV = h->lv[R[r].l];
+    const int nb = (int)LV.box.size();
+    Box& B = R[r].box();
     B.near.clear();
     const double r2 = B.rho * B.rho;
     for (int s2 = 0; s2 < nb; ++s2) {
-      if (s2 == b) continue;
+      if (s2 == R[r].b) continue;
       const Box& S = LV.box[s2];
       double cdx = S.cx - B.cx, cdy = S.cy - B.cy;
       double reach = B.rho + S.R;
       if (cdx * cdx + cdy * cdy >= reach * reach) continue;
-      size_t nr0 = NR[b].size(), nc0 = NC[b].size();
+      size_t nr0 = NR[r].size(), nc0 = NC[r].size();
       for (int32_t u : S.cr) {
         double dx = h->hx[u >> 1] - B.cx, dy = h->hy[u >> 1] - B.cy;
-        if (dx * dx + dy * dy < r2) NR[b].push_back(u);
+        if (dx * dx + dy * dy < r2) NR[r].push_back(u);
       }
       for (int32_t u : S.cc) {
         double dx = h->hx[u >> 1] - B.cx, dy = h->hy[u >> 1] - B.cy;
-        if (dx * dx + dy * dy < r2) NC[b].push_back(u);
+        if (dx * dx + dy * dy < r2) NC[r].push_back(u);
       }
-      if (NR[b].size() > nr0 || NC[b].size() > nc0) B.near.push_back(s2);
+      if (NR[r].size() > nr0 || NC[r].size() > nc0) B.near.push_back(s2);
     }
   }
-  // ---- storage: D (factor, kept), ID matrices (temporary)
-  std::vector<int64_t> mr(nb), mc(nb);
-  size_t Dtot = 0, Mtot = 0, ntot = 0;
+  // ---- storage: D and its pivots (kept, per curve), ID matrices (temporary)
+  std::vector<int64_t> mr(NB), mc(NB);
+  std::vector<size_t> Dtot(hs.size(), 0), ntot_h(hs.size(), 0);
+  size_t Mtot = 0, ntot = 0;
   int maxn = 0;
-  for (int b = 0; b < nb; ++b) {
-    Box& B = LV.box[b];
+  for (int r = 0; r < NB; ++r) {
+    Box& B = R[r].box();
     B.n = (int)B.cr.size();
-    mr[b] = 2 * (int64_t)B.P + (int64_t)NC[b].size();
-    mc[b] = 2 * (int64_t)B.P + (int64_t)NR[b].size();
-    Dtot += (size_t)B.n * B.n;
-    Mtot += (size_t)(mr[b] + mc[b]) * B.n;
+    mr[r] = 2 * (int64_t)B.P + (int64_t)NC[r].size();
+    mc[r] = 2 * (int64_t)B.P + (int64_t)NR[r].size();
+    Dtot[R[r].inst] += (size_t)B.n * B.n;
+    ntot_h[R[r].inst] += B.n;
+    Mtot += (size_t)(mr[r] + mc[r]) * B.n;
     ntot += B.n;
     maxn = std::max(maxn, B.n);
   }
-  double2 *Dall = nullptr, *Mall = nullptr;
-  int32_t* pivall = nullptr;
-  HK(dalloc(h, Dtot * sizeof(double2), (void**)&Dall, h->owned));
-  HK(dalloc(h, ntot * sizeof(int32_t), (void**)&pivall, h->owned));
-  HK(dalloc(h, Mtot * sizeof(double2), (void**)&Mall, tmp));
-  std::vector<double2*> Mr(nb), Mc(nb);
+  std::vector<double2*> Dall(hs.size(), nullptr);
+  std::vector<int32_t*> pivall(hs.size(), nullptr);
+  for (size_t i = 0; i < hs.size(); ++i) {
+    if (!Dtot[i]) continue;
+    HK(dalloc(hs[i], Dtot[i] * sizeof(double2), (void**)&Dall[i], hs[i]->owned));
+    HK(dalloc(hs[i], ntot_h[i] * sizeof(int32_t), (void**)&pivall[i], hs[i]->owned));
+  }
+  double2* Mall = nullptr;
+  HK(dalloc(h0, Mtot * sizeof(double2), (void**)&Mall, tmp));
+  std::vector<double2*> Mr(NB), Mc(NB);
   {
-    size_t o = 0, oM = 0, on = 0;
-    for (int b = 0; b < nb; ++b) {
-      Box& B = LV.box[b];
-      B.D = Dall + o;
-      B.piv = pivall + on;
-      o += (size_t)B.n * B.n;
-      on += B.n;
-      Mr[b] = Mall + oM;
-      oM += (size_t)mr[b] * B.n;
-      Mc[b] = Mall + oM;
-      oM += (size_t)mc[b] * B.n;
+    std::vector<size_t> oD(hs.size(), 0), oN(hs.size(), 0);
+    size_t oM = 0;
+    for (int r = 0; r < NB; ++r) {
+      Box& B = R[r].box();
+      int i = R[r].inst;
+      B.D = Dall[i] + oD[i];
+      B.piv = pivall[i] + oN[i];
+      oD[i] += (size_t)B.n * B.n;
+      oN[i] += B.n;
+      Mr[r] = Mall + oM;
+      oM += (size_t)mr[r] * B.n;
+      Mc[r] = Mall + oM;
+      oM += (size_t)mc[r] * B.n;
     }
   }
   // ---- entries: diagonal blocks (leaf) or sibling blocks (upper), near blocks, proxy blocks
-  PairBatch pb(h->slot_scratch);
+  PairBatch pb;
+  ProxyBatch xb64, xbmx;  // FP64 and mixed-precision curves (one proxy launch each)
   std::vector<CopyDesc> copies;
-  for (int b = 0; b < nb; ++b) {
-    Box& B = LV.box[b];
+  std::vector<int64_t> e_pairs(hs.size(), 0), e_proxy(hs.size(), 0);
+  for (int r = 0; r < NB; ++r) {
+    wsbm_hss* h = R[r].h;
+    const int i = R[r].inst, l = R[r].l;
+    Box& B = R[r].box();
+    std::vector<int32_t>& at = h->slot_scratch;
     if (l == h->L) {
-      pb.add(B.cr, 0, B.cc, 0, B.D, B.n, 0);
+      e_pairs[i] += pb.add(i, at, B.cr, 0, B.cc, 0, B.D, B.n, 0);
     } else {
-      Box& A1 = h->lv[l + 1].box[2 * b];
-      Box& A2 = h->lv[l + 1].box[2 * b + 1];
+      Box& A1 = h->lv[l + 1].box[2 * R[r].b];
+      Box& A2 = h->lv[l + 1].box[2 * R[r].b + 1];
       int ka = A1.k, kb = A2.k;
-      pb.add(A1.Jr, 0, A2.Jc, ka, B.D, B.n, 0);
-      pb.add(A2.Jr, ka, A1.Jc, 0, B.D, B.n, 0);
-      CopyDesc c1 = {B.D, A1.Dc, B.n, ka, ka, ka};
-      CopyDesc c2 = {B.D + ka + (int64_t)ka * B.n, A2.Dc, B.n, kb, kb, kb};
-      copies.push_back(c1);
-      copies.push_back(c2);
+      e_pairs[i] += pb.add(i, at, A1.Jr, 0, A2.Jc, ka, B.D, B.n, 0);
+      e_pairs[i] += pb.add(i, at, A2.Jr, ka, A1.Jc, 0, B.D, B.n, 0);
+      copies.push_back({B.D, A1.Dc, B.n, ka, ka, ka});
+      copies.push_back({B.D + ka + (int64_t)ka * B.n, A2.Dc, B.n, kb, kb, kb});
     }
     // row ID matrix (stored transposed: rows = near columns) and column ID matrix
-    pb.add(B.cr, 0, NC[b], 2 * B.P, Mr[b], mr[b], 1);
-    pb.add(NR[b], 2 * B.P, B.cc, 0, Mc[b], mc[b], 0);
-  }
-  ProxyBatch xb(h->slot_scratch);
-  for (int b = 0; b < nb; ++b) {
-    Box& B = LV.box[b];
-    xb.add(B.cr, B, 0, Mr[b], mr[b]);
-    xb.add(B.cc, B, 1, Mc[b], mc[b]);
+    e_pairs[i] += pb.add(i, at, B.cr, 0, NC[r], 2 * B.P, Mr[r], mr[r], 1);
+    e_pairs[i] += pb.add(i, at, NR[r], 2 * B.P, B.cc, 0, Mc[r], mc[r], 0);
+    ProxyBatch& xb = h->prm.precision == WSBM_MIXED ? xbmx : xb64;
+    e_proxy[i] += xb.add(i, at, B.cr, B, 0, Mr[r], mr[r]);
+    e_proxy[i] += xb.add(i, at, B.cc, B, 1, Mc[r], mc[r]);
   }
   if (!copies.empty()) {
     CopyDesc* dc = nullptr;
-    HK(upload(h, copies, &dc, tmp));
+    HK(upload(h0, copies, &dc, tmp));
     int64_t mx = 0;
     for (auto& c : copies) mx = std::max(mx, (int64_t)c.m * c.n);
     k_copy2d<<<dim3(gridfor(mx), (unsigned)copies.size()), 256, 0, st>>>(dc);
     wsbm_count_launch();
   }
-  HK(pb.prepare(h, tmp));
-  HK(xb.prepare(h, tmp));
-  // timed: the two entry kernels only
-  HC(cudaEventRecord(h->ev[0], st));
-  HK(pb.run(h));
-  HC(cudaEventRecord(h->ev[4], st));
-  HK(xb.run(h));
-  HC(cudaEventRecord(h->ev[1], st));
-  h->stats.entries_generated += pb.entries + xb.entries;
-  h->stats.pairs_evaluated += pb.pairs + xb.pairs;
-  h->stats.entries_pairs += pb.entries;
-  h->stats.pairs_pairs += pb.pairs;
-  h->stats.entries_proxy += xb.entries;
-  h->stats.pairs_proxy += xb.pairs;
+  HK(pb.prepare(h0, tmp));
+  HK(xb64.prepare(h0, tmp));
+  HK(xbmx.prepare(h0, tmp));
+  // timed: the entry kernels only
+  HC(cudaEventRecord(h0->ev[0], st));
+  HK(pb.run(h0, ia.geos, ia.phys));
+  HC(cudaEventRecord(h0->ev[4], st));
+  HK(xb64.run(h0, 0, ia.geos, ia.phys));
+  HK(xbmx.run(h0, 1, ia.geos, ia.phys));
+  HC(cudaEventRecord(h0->ev[1], st));
+  for (size_t i = 0; i < hs.size(); ++i) {
+    hs[i]->stats.entries_generated += e_pairs[i] + e_proxy[i];
+    hs[i]->stats.entries_pairs += e_pairs[i];
+    hs[i]->stats.entries_proxy += e_proxy[i];
+  }
+  // pair counts are kept per launch; a single curve owns them all
+  if (hs.size() == 1) {
+    h0->stats.pairs_evaluated += pb.pairs + xb64.pairs + xbmx.pairs;
+    h0->stats.pairs_pairs += pb.pairs;
+    h0->stats.pairs_proxy += xb64.pairs + xbmx.pairs;
+  }
   // ---- interpolative decompositions: CPQR of Mr (row ID) and Mc (column ID) of every box
-  std::vector<QrDesc> qd(2 * nb);
+  std::vector<QrDesc> qd(2 * NB);
   int32_t *perm = nullptr, *state = nullptr;
   double *norm2 = nullptr, *nref = nullptr, *tauv = nullptr, *rd0 = nullptr;
   double2* betav = nullptr;
-  HK(dalloc(h, 2 * ntot * sizeof(double), (void**)&nref, tmp));
-  HK(dalloc(h, 2 * ntot * sizeof(int32_t), (void**)&perm, tmp));
-  HK(dalloc(h, 2 * nb * 2 * sizeof(int32_t), (void**)&state, tmp));
-  HK(dalloc(h, 2 * ntot * sizeof(double), (void**)&norm2, tmp));
-  HK(dalloc(h, 2 * ntot * sizeof(double), (void**)&tauv, tmp));
-  HK(dalloc(h, 2 * ntot * sizeof(double2), (void**)&betav, tmp));
-  HK(dalloc(h, 2 * nb * sizeof(double), (void**)&rd0, tmp));
-  HC(cudaMemsetAsync(state, 0, 2 * nb * 2 * sizeof(int32_t), st));
+  HK(dalloc(h0, 2 * ntot * sizeof(double), (void**)&nref, tmp));
+  HK(dalloc(h0, 2 * ntot * sizeof(int32_t), (void**)&perm, tmp));
+  HK(dalloc(h0, 2 * NB * 2 * sizeof(int32_t), (void**)&state, tmp));
+  HK(dalloc(h0, 2 * ntot * sizeof(double), (void**)&norm2, tmp));
+  HK(dalloc(h0, 2 * ntot * sizeof(double), (void**)&tauv, tmp));
+  HK(dalloc(h0, 2 * ntot * sizeof(double2), (void**)&betav, tmp));
+  HK(dalloc(h0, 2 * NB * sizeof(double), (void**)&rd0, tmp));
+  HC(cudaMemsetAsync(state, 0, 2 * NB * 2 * sizeof(int32_t), st));
   {
     size_t on = 0;
-    for (int b = 0; b < nb; ++b)
+    for (int r = 0; r < NB; ++r)
       for (int s = 0; s < 2; ++s) {
-        QrDesc& q = qd[2 * b + s];
+        QrDesc& q = qd[2 * r + s];
         memset(&q, 0, sizeof(q));
-        q.A = s == 0 ? Mr[b] : Mc[b];
-        q.lda = s == 0 ? mr[b] : mc[b];
+        q.A = s == 0 ? Mr[r] : Mc[r];
+        q.lda = s == 0 ? mr[r] : mc[r];
         q.m = (int32_t)q.lda;
-        q.n = LV.box[b].n;
-        q.tol = h->cut;
+        q.n = R[r].box().n;
+        q.tol = R[r].h->cut;
         q.perm = perm + on;
         q.norm2 = norm2 + on;
         q.nref = nref + on;
         q.tauv = tauv + on;
         q.betav = betav + on;
-        q.state = state + 2 * (2 * b + s);
-        q.rdiag0 = rd0 + (2 * b + s);
+        q.state = state + 2 * (2 * r + s);
+        q.rdiag0 = rd0 + (2 * r + s);
         on += q.n;
       }
   }
   QrDesc* dq = nullptr;
-  HK(upload(h, qd, &dq, tmp));
-  HK(wsbm_cpqr_batched(dq, 2 * nb, 0, st));
-  std::vector<int32_t> hstate(4 * nb);
+  HK(upload(h0, qd, &dq, tmp));
+  HK(wsbm_cpqr_batched(dq, 2 * NB, 0, st));
+  std::vector<int32_t> hstate(4 * NB);
   HC(cudaMemcpyAsync(hstate.data(), state, hstate.size() * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
   HC(cudaStreamSynchronize(st));
   std::vector<QrDesc> more;
-  for (int b = 0; b < nb; ++b) {
-    Box& B = LV.box[b];
-    int kr = hstate[4 * b + 1], kc = hstate[4 * b + 3];
+  for (int r = 0; r < NB; ++r) {
+    Box& B = R[r].box();
+    int kr = hstate[4 * r + 1], kc = hstate[4 * r + 3];
     int k = std::max(std::max(kr, kc), 1);
     k = std::min(k, B.n);
     B.k = k;
     for (int s = 0; s < 2; ++s) {
       int ks = s == 0 ? kr : kc;
       if (ks < k) {
-        QrDesc q = qd[2 * b + s];
+        QrDesc q = qd[2 * r + s];
         q.kt = k;
         more.push_back(q);
       }
@@ -769,22 +828,22 @@ static int factor_level(wsbm_hss* h, int l) {
   }
   if (!more.empty()) {
     QrDesc* dm = nullptr;
-    HK(upload(h, more, &dm, tmp));
+    HK(upload(h0, more, &dm, tmp));
     HK(wsbm_cpqr_batched(dm, (int)more.size(), 1, st));
   }
-  HK(wsbm_cpqr_finish(dq, 2 * nb, st));
+  HK(wsbm_cpqr_finish(dq, 2 * NB, st));
   // T = R11^-1 R12 in place (both sides)
   {
     std::vector<TrsmDesc> td;
     int mk = 0, mrhs = 0;
-    for (int b = 0; b < nb; ++b)
+    for (int r = 0; r < NB; ++r)
       for (int s = 0; s < 2; ++s) {
-        Box& B = LV.box[b];
+        Box& B = R[r].box();
         TrsmDesc t;
         memset(&t, 0, sizeof(t));
-        t.T = qd[2 * b + s].A;
-        t.ldt = qd[2 * b + s].lda;
-        t.B = qd[2 * b + s].A + (int64_t)B.k * t.ldt;
+        t.T = qd[2 * r + s].A;
+        t.ldt = qd[2 * r + s].lda;
+        t.B = qd[2 * r + s].A + (int64_t)B.k * t.ldt;
         t.ldb = t.ldt;
         t.n = B.k;
         t.nrhs = B.n - B.k;
@@ -793,56 +852,70 @@ static int factor_level(wsbm_hss* h, int l) {
         td.push_back(t);
       }
     TrsmDesc* dtd = nullptr;
-    HK(upload(h, td, &dtd, tmp));
+    HK(upload(h0, td, &dtd, tmp));
     HK(wsbm_trsm_batched(dtd, (int)td.size(), mk, mrhs, 0, st));
   }
   std::vector<int32_t> hperm(2 * ntot);
   HC(cudaMemcpyAsync(hperm.data(), perm, hperm.size() * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
-  HC(cudaEventRecord(h->ev[2], st));
+  HC(cudaEventRecord(h0->ev[2], st));
   // ---- factor: LU(D), Z = D^-1 L, M = R Z, Dhat = M^-1
-  size_t Ztot = 0, Ktot = 0, Ttot = 0;
+  std::vector<size_t> Ztot(hs.size(), 0), Ktot(hs.size(), 0), Ttot(hs.size(), 0);
+  size_t Zsum = 0, Ksum = 0;
   int maxk = 0;
-  for (int b = 0; b < nb; ++b) {
-    Box& B = LV.box[b];
-    Ztot += (size_t)B.n * B.k;
-    Ktot += (size_t)B.k * B.k;
-    Ttot += (size_t)B.k * (B.n - B.k);
+  for (int r = 0; r < NB; ++r) {
+    Box& B = R[r].box();
+    int i = R[r].inst;
+    Ztot[i] += (size_t)B.n * B.k;
+    Ktot[i] += (size_t)B.k * B.k;
+    Ttot[i] += (size_t)B.k * (B.n - B.k);
+    Zsum += (size_t)B.n * B.k;
+    Ksum += (size_t)B.k * B.k;
     maxk = std::max(maxk, B.k);
   }
-  double2 *Zall = nullptr, *Dcall = nullptr, *Tcall = nullptr, *Mall2 = nullptr, *Zp = nullptr;
-  int32_t *pcall = nullptr, *pivM = nullptr;
-  HK(dalloc(h, Ztot * sizeof(double2), (void**)&Zall, h->owned));
-  HK(dalloc(h, Ktot * sizeof(double2), (void**)&Dcall, h->owned));
-  HK(dalloc(h, Ttot * sizeof(double2), (void**)&Tcall, h->owned));
-  HK(dalloc(h, ntot * sizeof(int32_t), (void**)&pcall, h->owned));
-  HK(dalloc(h, Ktot * sizeof(double2), (void**)&Mall2, tmp));
-  HK(dalloc(h, Ztot * sizeof(double2), (void**)&Zp, tmp));
-  HK(dalloc(h, ntot * sizeof(int32_t), (void**)&pivM, tmp));
+  std::vector<double2*> Zall(hs.size(), nullptr), Dcall(hs.size(), nullptr), Tcall(hs.size(), nullptr);
+  std::vector<int32_t*> pcall(hs.size(), nullptr);
+  for (size_t i = 0; i < hs.size(); ++i) {
+    if (!ntot_h[i]) continue;
+    HK(dalloc(hs[i], Ztot[i] * sizeof(double2), (void**)&Zall[i], hs[i]->owned));
+    HK(dalloc(hs[i], Ktot[i] * sizeof(double2), (void**)&Dcall[i], hs[i]->owned));
+    HK(dalloc(hs[i], Ttot[i] * sizeof(double2), (void**)&Tcall[i], hs[i]->owned));
+    HK(dalloc(hs[i], ntot_h[i] * sizeof(int32_t), (void**)&pcall[i], hs[i]->owned));
+  }
+  double2 *Mall2 = nullptr, *Zp = nullptr;
+  int32_t* pivM = nullptr;
+  HK(dalloc(h0, Ksum * sizeof(double2), (void**)&Mall2, tmp));
+  HK(dalloc(h0, Zsum * sizeof(double2), (void**)&Zp, tmp));
+  HK(dalloc(h0, ntot * sizeof(int32_t), (void**)&pivM, tmp));
   std::vector<LuDesc> luD, luM;
   std::vector<BuildLDesc> bl;
-  std::vector<TrsmDesc> zl, zu, ml, mu;
+  std::vector<TrsmDesc> zl, ml;
   std::vector<GatherDesc> gz;
   std::vector<GemmDesc> gm;
-  std::vector<CopyDesc> tcc, pcopy;
+  std::vector<CopyDesc> tcc, pcopy, idd;
   {
-    size_t oz = 0, ok = 0, ot = 0, on = 0;
-    for (int b = 0; b < nb; ++b) {
-      Box& B = LV.box[b];
+    std::vector<size_t> oz(hs.size(), 0), ok(hs.size(), 0), ot(hs.size(), 0), on(hs.size(), 0);
+    size_t gz_o = 0, gk_o = 0, gn_o = 0;
+    for (int r = 0; r < NB; ++r) {
+      Box& B = R[r].box();
+      const int i = R[r].inst;
       const int n = B.n, k = B.k;
-      B.Z = Zall + oz;
-      B.Dc = Dcall + ok;
-      B.Tc = Tcall + ot;
-      B.pc = pcall + on;
-      double2* M = Mall2 + ok;
-      double2* Zg = Zp + oz;
-      int32_t* pM = pivM + on;
-      oz += (size_t)n * k;
-      ok += (size_t)k * k;
-      ot += (size_t)k * (n - k);
-      on += n;
+      B.Z = Zall[i] + oz[i];
+      B.Dc = Dcall[i] + ok[i];
+      B.Tc = Tcall[i] + ot[i];
+      B.pc = pcall[i] + on[i];
+      oz[i] += (size_t)n * k;
+      ok[i] += (size_t)k * k;
+      ot[i] += (size_t)k * (n - k);
+      on[i] += n;
+      double2* M = Mall2 + gk_o;
+      double2* Zg = Zp + gz_o;
+      int32_t* pM = pivM + gn_o;
+      gz_o += (size_t)n * k;
+      gk_o += (size_t)k * k;
+      gn_o += n;
       luD.push_back({B.D, n, B.piv, n, 0});
-      const QrDesc& qr = qd[2 * b];
-      const QrDesc& qc = qd[2 * b + 1];
+      const QrDesc& qr = qd[2 * r];
+      const QrDesc& qc = qd[2 * r + 1];
       bl.push_back({B.Z, qr.A + (int64_t)k * qr.lda, qr.perm, qr.lda, n, k});
       TrsmDesc t;
       memset(&t, 0, sizeof(t));
@@ -854,10 +927,8 @@ static int factor_level(wsbm_hss* h, int l) {
       t.n = n;
       t.nrhs = k;
       zl.push_back(t);
-      zu.push_back(t);
-      // Zg = Z[pc, :]
+      // Zg = Z[pc, :];  M = Zg[0:k, :] + Tc Zg[k:n, :]
       gz.push_back({Zg, B.Z, qc.perm, n, n, n, k});
-      // M = Zg[0:k, :] + Tc Zg[k:n, :]
       pcopy.push_back({M, Zg, k, n, k, k});
       if (n > k) {
         GemmDesc gd;
@@ -887,7 +958,7 @@ static int factor_level(wsbm_hss* h, int l) {
       tm.n = k;
       tm.nrhs = k;
       ml.push_back(tm);
-      mu.push_back(tm);
+      idd.push_back({B.Dc, nullptr, k, 0, k, k});
     }
   }
   LuDesc *dluD = nullptr, *dluM = nullptr;
@@ -895,61 +966,53 @@ static int factor_level(wsbm_hss* h, int l) {
   TrsmDesc *dzl = nullptr, *dml = nullptr;
   GatherDesc* dgz = nullptr;
   GemmDesc* dgm = nullptr;
-  CopyDesc *dtcc = nullptr, *dpc = nullptr;
-  HK(upload(h, luD, &dluD, tmp));
-  HK(upload(h, luM, &dluM, tmp));
-  HK(upload(h, bl, &dbl, tmp));
-  HK(upload(h, zl, &dzl, tmp));
-  HK(upload(h, ml, &dml, tmp));
-  HK(upload(h, gz, &dgz, tmp));
-  HK(upload(h, gm, &dgm, tmp));
-  HK(upload(h, tcc, &dtcc, tmp));
-  HK(upload(h, pcopy, &dpc, tmp));
+  CopyDesc *dtcc = nullptr, *dpc = nullptr, *didd = nullptr;
+  HK(upload(h0, luD, &dluD, tmp));
+  HK(upload(h0, luM, &dluM, tmp));
+  HK(upload(h0, bl, &dbl, tmp));
+  HK(upload(h0, zl, &dzl, tmp));
+  HK(upload(h0, ml, &dml, tmp));
+  HK(upload(h0, gz, &dgz, tmp));
+  HK(upload(h0, gm, &dgm, tmp));
+  HK(upload(h0, tcc, &dtcc, tmp));
+  HK(upload(h0, pcopy, &dpc, tmp));
+  HK(upload(h0, idd, &didd, tmp));
   int64_t maxnk = 0;
-  for (int b = 0; b < nb; ++b) maxnk = std::max(maxnk, (int64_t)LV.box[b].n * LV.box[b].k);
-  HK(wsbm_lu_batched(dluD, nb, maxn, nullptr, st));
-  k_build_L<<<dim3(gridfor(maxnk), nb), 256, 0, st>>>(dbl);
+  for (int r = 0; r < NB; ++r) maxnk = std::max(maxnk, (int64_t)R[r].box().n * R[r].box().k);
+  HK(wsbm_lu_batched(dluD, NB, maxn, nullptr, st));
+  k_build_L<<<dim3(gridfor(maxnk), NB), 256, 0, st>>>(dbl);
   wsbm_count_launch();
-  HK(wsbm_lu_solve_batched(dzl, dzl, nb, maxn, maxk, st));
-  k_gather_rows<<<dim3(gridfor(maxnk), nb), 256, 0, st>>>(dgz);
+  HK(wsbm_lu_solve_batched(dzl, dzl, NB, maxn, maxk, st));
+  k_gather_rows<<<dim3(gridfor(maxnk), NB), 256, 0, st>>>(dgz);
   wsbm_count_launch();
-  k_copy2d<<<dim3(gridfor((int64_t)maxk * maxk), nb), 256, 0, st>>>(dpc);
+  k_copy2d<<<dim3(gridfor((int64_t)maxk * maxk), NB), 256, 0, st>>>(dpc);
   wsbm_count_launch();
   if (!gm.empty()) HK(wsbm_gemm_batched(dgm, (int)gm.size(), maxk, maxk, st));
-  if (!tcc.empty()) { k_copy2d<<<dim3(gridfor(maxnk), (unsigned)tcc.size()), 256, 0, st>>>(dtcc); wsbm_count_launch(); }
-  HK(wsbm_lu_batched(dluM, nb, maxk, nullptr, st));
-  {
-    std::vector<CopyDesc> idd;
-    for (int b = 0; b < nb; ++b) idd.push_back({LV.box[b].Dc, nullptr, LV.box[b].k, 0, LV.box[b].k, LV.box[b].k});
-    CopyDesc* didd = nullptr;
-    HK(upload(h, idd, &didd, tmp));
-    k_fill_identity_batched<<<dim3(gridfor((int64_t)maxk * maxk), nb), 256, 0, st>>>(didd);
+  if (!tcc.empty()) {
+    k_copy2d<<<dim3(gridfor(maxnk), (unsigned)tcc.size()), 256, 0, st>>>(dtcc);
     wsbm_count_launch();
   }
-  HK(wsbm_lu_solve_batched(dml, dml, nb, maxk, maxk, st));
+  HK(wsbm_lu_batched(dluM, NB, maxk, nullptr, st));
+  k_fill_identity_batched<<<dim3(gridfor((int64_t)maxk * maxk), NB), 256, 0, st>>>(didd);
+  wsbm_count_launch();
+  HK(wsbm_lu_solve_batched(dml, dml, NB, maxk, maxk, st));
   HC(cudaGetLastError());
   // column permutations (kept for the solve)
-  {
-    size_t on = 0;
-    for (int b = 0; b < nb; ++b) {
-      Box& B = LV.box[b];
-      HC(cudaMemcpyAsync(B.pc, qd[2 * b + 1].perm, B.n * sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
-      on += B.n;
-    }
+  for (int r = 0; r < NB; ++r) {
+    Box& B = R[r].box();
+    HC(cudaMemcpyAsync(B.pc, qd[2 * r + 1].perm, B.n * sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
   }
-  HC(cudaEventRecord(h->ev[3], st));
+  HC(cudaEventRecord(h0->ev[3], st));
   HC(cudaStreamSynchronize(st));
-  h->stats.ms_entries += elapsed(h->ev[0], h->ev[1]);
-  h->stats.ms_pairs += elapsed(h->ev[0], h->ev[4]);
-  h->stats.ms_proxy += elapsed(h->ev[4], h->ev[1]);
-  h->stats.ms_id += elapsed(h->ev[1], h->ev[2]);
-  h->stats.ms_factor += elapsed(h->ev[2], h->ev[3]);
+  ms_out[0] = elapsed(h0->ev[0], h0->ev[1]);
+  ms_out[1] = elapsed(h0->ev[0], h0->ev[4]);
+  ms_out[2] = elapsed(h0->ev[1], h0->ev[2]);
+  ms_out[3] = elapsed(h0->ev[2], h0->ev[3]);
   // skeletons
   {
     size_t on = 0;
-    int rmax = 0;
-    for (int b = 0; b < nb; ++b) {
-      Box& B = LV.box[b];
+    for (int r = 0; r < NB; ++r) {
+      Box& B = R[r].box();
       const int32_t* pr = hperm.data() + on;
       on += B.n;
       const int32_t* pcp = hperm.data() + on;
@@ -960,171 +1023,300 @@ static int factor_level(wsbm_hss* h, int l) {
         B.Jr[t] = B.cr[pr[t]];
         B.Jc[t] = B.cc[pcp[t]];
       }
-      rmax = std::max(rmax, B.k);
+      wsbm_hss* h = R[r].h;
+      h->stats.rank_per_level[R[r].l] = std::max(h->stats.rank_per_level[R[r].l], B.k);
+      h->stats.max_rank = std::max(h->stats.max_rank, B.k);
     }
-    h->stats.rank_per_level[l] = rmax;
-    h->stats.max_rank = std::max(h->stats.max_rank, rmax);
   }
-  LV.compressed = true;
-  free_list(h, tmp);
+  for (size_t i = 0; i < hs.size(); ++i)
+    if (levels[i] >= 1) hs[i]->lv[levels[i]].compressed = true;
+  free_list(h0, tmp);
   return WSBM_OK;
 }
 
-// Dense root: merge the skeletons of every box of level `top` (all of A when the tree has a
-// single box).
-static int factor_root(wsbm_hss* h) {
+// Dense roots: for each curve, merge the skeletons of every box of its top level (all of A when
+// its tree has a single box); entries in one launch, LU in one batched call.
+static int factor_roots(const std::vector<wsbm_hss*>& hs, double ms_out[2]) {
+  wsbm_hss* h0 = hs[0];
+  cudaStream_t st = h0->st;
   std::vector<void*> tmp;
-  cudaStream_t st = h->st;
-  std::vector<int32_t> Rr, Rc;
-  std::vector<int> off;
-  if (h->L == 0) {
-    for (int64_t u = 0; u < 2 * h->N; ++u) {
-      Rr.push_back((int32_t)u);
-      Rc.push_back((int32_t)u);
-    }
-  } else {
-    Level& T = h->lv[h->top];
-    for (auto& b : T.box) {
-      off.push_back((int)Rr.size());
-      Rr.insert(Rr.end(), b.Jr.begin(), b.Jr.end());
-      Rc.insert(Rc.end(), b.Jc.begin(), b.Jc.end());
-    }
-  }
-  const int n = (int)Rr.size();
-  h->root_n = n;
-  h->stats.root_size = n;
-  HK(dalloc(h, (size_t)n * n * sizeof(double2), (void**)&h->root, h->owned));
-  HK(dalloc(h, (size_t)n * sizeof(int32_t), (void**)&h->root_piv, h->owned));
-  PairBatch pb(h->slot_scratch);
+  InstArrays ia;
+  HK(upload_instances(h0, hs, &ia, tmp));
+  PairBatch pb;
   std::vector<CopyDesc> copies;
-  if (h->L == 0) {
-    pb.add(Rr, 0, Rc, 0, h->root, n, 0);
-  } else {
-    Level& T = h->lv[h->top];
-    int nb = (int)T.box.size();
-    for (int a = 0; a < nb; ++a) {
-      Box& A = T.box[a];
-      copies.push_back({h->root + off[a] + (int64_t)off[a] * n, A.Dc, n, A.k, A.k, A.k});
-      for (int b = 0; b < nb; ++b) {
-        if (a == b) continue;
-        pb.add(A.Jr, off[a], T.box[b].Jc, off[b], h->root, n, 0);
+  std::vector<LuDesc> lus;
+  std::vector<int64_t> e_pairs(hs.size(), 0);
+  int maxn = 0;
+  for (size_t i = 0; i < hs.size(); ++i) {
+    wsbm_hss* h = hs[i];
+    std::vector<int32_t> Rr, Rc;
+    std::vector<int> off;
+    if (h->L == 0) {
+      for (int64_t u = 0; u < 2 * h->N; ++u) {
+        Rr.push_back((int32_t)u);
+        Rc.push_back((int32_t)u);
+      }
+    } else {
+      for (auto& b : h->lv[h->top].box) {
+        off.push_back((int)Rr.size());
+        Rr.insert(Rr.end(), b.Jr.begin(), b.Jr.end());
+        Rc.insert(Rc.end(), b.Jc.begin(), b.Jc.end());
       }
     }
+    const int n = (int)Rr.size();
+    h->root_n = n;
+    h->stats.root_size = n;
+    maxn = std::max(maxn, n);
+    HK(dalloc(h, (size_t)n * n * sizeof(double2), (void**)&h->root, h->owned));
+    HK(dalloc(h, (size_t)n * sizeof(int32_t), (void**)&h->root_piv, h->owned));
+    if (h->L == 0) {
+      e_pairs[i] += pb.add((int)i, h->slot_scratch, Rr, 0, Rc, 0, h->root, n, 0);
+    } else {
+      Level& T = h->lv[h->top];
+      int nb = (int)T.box.size();
+      for (int a = 0; a < nb; ++a) {
+        Box& A = T.box[a];
+        copies.push_back({h->root + off[a] + (int64_t)off[a] * n, A.Dc, n, A.k, A.k, A.k});
+        for (int b = 0; b < nb; ++b) {
+          if (a == b) continue;
+          e_pairs[i] += pb.add((int)i, h->slot_scratch, A.Jr, off[a], T.box[b].Jc, off[b], h->root, n, 0);
+        }
+      }
+    }
+    lus.push_back({h->root, n, h->root_piv, n, 0});
   }
   if (!copies.empty()) {
     CopyDesc* dc = nullptr;
-    HK(upload(h, copies, &dc, tmp));
+    HK(upload(h0, copies, &dc, tmp));
     int64_t mx = 0;
     for (auto& c : copies) mx = std::max(mx, (int64_t)c.m * c.n);
     k_copy2d<<<dim3(gridfor(mx), (unsigned)copies.size()), 256, 0, st>>>(dc);
     wsbm_count_launch();
   }
-  HK(pb.prepare(h, tmp));
-  HC(cudaEventRecord(h->ev[0], st));
-  HK(pb.run(h));
-  HC(cudaEventRecord(h->ev[1], st));
-  h->stats.entries_generated += pb.entries;
-  h->stats.pairs_evaluated += pb.pairs;
-  LuDesc ld = {h->root, n, h->root_piv, n, 0};
-  std::vector<LuDesc> v(1, ld);
+  HK(pb.prepare(h0, tmp));
   LuDesc* dl = nullptr;
-  HK(upload(h, v, &dl, tmp));
-  HK(wsbm_lu_batched(dl, 1, n, nullptr, st));
-  HC(cudaEventRecord(h->ev[2], st));
+  HK(upload(h0, lus, &dl, tmp));
+  HC(cudaEventRecord(h0->ev[0], st));
+  HK(pb.run(h0, ia.geos, ia.phys));
+  HC(cudaEventRecord(h0->ev[1], st));
+  for (size_t i = 0; i < hs.size(); ++i) {
+    hs[i]->stats.entries_generated += e_pairs[i];
+    hs[i]->stats.entries_pairs += e_pairs[i];
+  }
+  if (hs.size() == 1) {
+    h0->stats.pairs_evaluated += pb.pairs;
+    h0->stats.pairs_pairs += pb.pairs;
+  }
+  HK(wsbm_lu_batched(dl, (int)lus.size(), maxn, nullptr, st));
+  HC(cudaEventRecord(h0->ev[2], st));
   HC(cudaStreamSynchronize(st));
-  h->stats.ms_entries += elapsed(h->ev[0], h->ev[1]);
-  h->stats.ms_pairs += elapsed(h->ev[0], h->ev[1]);
-  h->stats.entries_pairs += pb.entries;
-  h->stats.pairs_pairs += pb.pairs;
-  h->stats.ms_factor += elapsed(h->ev[1], h->ev[2]);
-  free_list(h, tmp);
+  ms_out[0] = elapsed(h0->ev[0], h0->ev[1]);
+  ms_out[1] = elapsed(h0->ev[1], h0->ev[2]);
+  free_list(h0, tmp);
   return WSBM_OK;
+}
+
+// Build and factor every handle of `hs` (sharing one stream): level by level from the leaves,
+// each round batching the current level of every curve that is still compressing (curves of
+// different depth are aligned at their leaves), then all dense roots at once.
+// bstats (optional) receives the timings of the shared launches.
+static int factor_all(const std::vector<wsbm_hss*>& hs, wsbm_stats_t* bstats) {
+  wsbm_hss* h0 = hs[0];
+  cudaEvent_t t0, t1;
+  cudaEventCreate(&t0);
+  cudaEventCreate(&t1);
+  cudaEventRecord(t0, h0->st);
+  const int64_t launches0 = wsbm_launch_count();
+  double ms[4] = {0, 0, 0, 0};  // entries, pair kernel, IDs, factor
+  std::vector<int> level(hs.size(), 0), done(hs.size(), 0);
+  std::vector<char> partial(hs.size(), 0);
+  int rc = WSBM_OK;
+  for (size_t i = 0; i < hs.size(); ++i) {
+    wsbm_hss* h = hs[i];
+    release_factors(h);
+    int32_t lev = h->stats.levels, nbl = h->stats.nboxes_leaf;
+    memset(&h->stats, 0, sizeof(h->stats));
+    h->stats.levels = lev;
+    h->stats.nboxes_leaf = nbl;
+    h->top = h->L;
+    level[i] = h->L;  // 0: nothing to compress
+    partial[i] = h->L > 0 && h->prm.max_levels > 0;
+    if (h->L > 0) {
+      for (auto& b : h->lv[h->L].box) {
+        for (int64_t n = b.lo; n < b.hi; ++n) {
+          b.cr.push_back((int32_t)(2 * n));
+          b.cr.push_back((int32_t)(2 * n + 1));
+        }
+        b.cc = b.cr;
+      }
+    }
+  }
+  for (;;) {
+    bool any = false;
+    for (int l : level) any = any || l >= 1;
+    if (!any) break;
+    double m4[4];
+    rc = factor_levels(hs, level, m4);
+    if (rc) break;
+    for (int a = 0; a < 4; ++a) ms[a] += m4[a];
+    for (size_t i = 0; i < hs.size(); ++i) {
+      if (level[i] < 1) continue;
+      wsbm_hss* h = hs[i];
+      const int l = level[i];
+      h->top = l;
+      ++done[i];
+      int next = 0;
+      if (l > 1 && !(h->prm.max_levels > 0 && done[i] >= h->prm.max_levels)) {
+        const int root_cap = h->prm.root_cap > 0 ? h->prm.root_cap : 40000;
+        int64_t Scur = 0, Snext = 0;
+        int nmax = 0;
+        for (auto& b : h->lv[l].box) {
+          Scur += b.n;
+          Snext += b.k;
+        }
+        for (int p = 0; p < (1 << (l - 1)); ++p) {
+          Box& P = h->lv[l - 1].box[p];
+          Box& A = h->lv[l].box[2 * p];
+          Box& B = h->lv[l].box[2 * p + 1];
+          P.cr = A.Jr;
+          P.cr.insert(P.cr.end(), B.Jr.begin(), B.Jr.end());
+          P.cc = A.Jc;
+          P.cc.insert(P.cc.end(), B.Jc.begin(), B.Jc.end());
+          nmax = std::max(nmax, (int)P.cr.size());
+        }
+        // stop compressing when it no longer pays (high-frequency boxes keep most unknowns)
+        // and the merged system fits the root, or when the next level's boxes would be too
+        // large for one-CTA column-pivoted QR
+        bool stop = (Snext > 0.8 * (double)Scur && Snext <= root_cap) || nmax > 3072;
+        if (!stop) next = l - 1;
+      }
+      level[i] = next;
+    }
+  }
+  std::vector<wsbm_hss*> roots;
+  if (!rc) {
+    for (size_t i = 0; i < hs.size(); ++i) {
+      wsbm_hss* h = hs[i];
+      if (h->L > 0 && !partial[i]) {
+        const int root_cap = h->prm.root_cap > 0 ? h->prm.root_cap : 40000;
+        int64_t S = 0;
+        for (auto& b : h->lv[h->top].box) S += b.k;
+        if (S > root_cap) rc = WSBM_ERR_RANK_OVERFLOW;
+      }
+      if (!partial[i]) roots.push_back(h);
+    }
+  }
+  double mr2[2] = {0, 0};
+  if (!rc && !roots.empty()) rc = factor_roots(roots, mr2);
+  cudaEventRecord(t1, h0->st);
+  cudaEventSynchronize(t1);
+  const double total = elapsed(t0, t1);
+  const int64_t launches = wsbm_launch_count() - launches0;
+  cudaEventDestroy(t0);
+  cudaEventDestroy(t1);
+  for (size_t i = 0; i < hs.size(); ++i) {
+    wsbm_hss* h = hs[i];
+    if (rc) {
+      int32_t keep[32];
+      memcpy(keep, h->stats.rank_per_level, sizeof(keep));
+      release_factors(h);
+      memcpy(h->stats.rank_per_level, keep, sizeof(keep));  // kept for diagnosis
+      continue;
+    }
+    // a single curve owns the shared launches; in a batch they are reported by the batch
+    if (hs.size() == 1) {
+      h->stats.ms_entries = ms[0] + mr2[0];
+      h->stats.ms_pairs = ms[1] + mr2[0];
+      h->stats.ms_proxy = ms[0] - ms[1];
+      h->stats.ms_id = ms[2];
+      h->stats.ms_factor = ms[3] + mr2[1];
+      h->stats.ms_total_factor = total;
+      h->stats.launches = launches;
+    }
+    size_t bytes = 0;
+    for (int l = h->top; l <= h->L && h->L > 0; ++l)
+      for (auto& b : h->lv[l].box)
+        bytes += ((size_t)b.n * b.n + (size_t)b.n * b.k + (size_t)b.k * b.k + (size_t)b.k * (b.n - b.k)) *
+                 sizeof(double2);
+    bytes += (size_t)h->root_n * h->root_n * sizeof(double2);
+    h->stats.factor_bytes = (int64_t)bytes;
+    h->factored = !partial[i];
+  }
+  if (bstats) {
+    memset(bstats, 0, sizeof(*bstats));
+    for (auto* h : hs) {
+      bstats->entries_generated += h->stats.entries_generated;
+      bstats->entries_pairs += h->stats.entries_pairs;
+      bstats->entries_proxy += h->stats.entries_proxy;
+      bstats->max_rank = std::max(bstats->max_rank, h->stats.max_rank);
+      bstats->root_size = std::max(bstats->root_size, h->stats.root_size);
+      bstats->factor_bytes += h->stats.factor_bytes;
+      bstats->levels = std::max(bstats->levels, h->stats.levels);
+      bstats->nboxes_leaf += h->stats.nboxes_leaf;
+    }
+    bstats->ms_entries = ms[0] + mr2[0];
+    bstats->ms_pairs = ms[1] + mr2[0];
+    bstats->ms_proxy = ms[0] - ms[1];
+    bstats->ms_id = ms[2];
+    bstats->ms_factor = ms[3] + mr2[1];
+    bstats->ms_total_factor = total;
+    bstats->launches = launches;
+  }
+  return rc;
 }
 
 extern "C" int wsbm_factor(wsbm_hss_t h) {
   if (!h) return WSBM_ERR_INVALID_ARG;
-  release_factors(h);
-  int32_t lev = h->stats.levels, nbl = h->stats.nboxes_leaf;
-  memset(&h->stats, 0, sizeof(h->stats));
-  h->stats.levels = lev;
-  h->stats.nboxes_leaf = nbl;
-  cudaEvent_t t0, t1;
-  cudaEventCreate(&t0);
-  cudaEventCreate(&t1);
-  cudaEventRecord(t0, h->st);
-  const int64_t launches0 = wsbm_launch_count();
-  int rc = WSBM_OK;
-  h->top = h->L;
-  if (h->L > 0) {
-    // leaf candidates: all unknowns of each box, interleaved
-    for (auto& b : h->lv[h->L].box) {
-      for (int64_t i = b.lo; i < b.hi; ++i) {
-        b.cr.push_back((int32_t)(2 * i));
-        b.cr.push_back((int32_t)(2 * i + 1));
-      }
-      b.cc = b.cr;
+  std::vector<wsbm_hss*> hs(1, h);
+  return factor_all(hs, nullptr);
+}
+
+// ------------------------------------------------------------------------ batches ----
+struct wsbm_batch {
+  std::vector<wsbm_hss*> hs;
+  wsbm_stats_t stats;
+};
+
+extern "C" int wsbm_batch_create(const wsbm_geom* g, const wsbm_params* p, int32_t count,
+                                 void* stream, wsbm_batch_t* out) {
+  if (!out || !g || !p || count < 1) return WSBM_ERR_INVALID_ARG;
+  *out = nullptr;
+  wsbm_batch* b = new wsbm_batch();
+  memset(&b->stats, 0, sizeof(b->stats));
+  for (int i = 0; i < count; ++i) {
+    wsbm_hss_t h = nullptr;
+    int rc = wsbm_create(&g[i], &p[i], stream, &h);
+    if (rc) {
+      wsbm_batch_destroy(b);
+      return rc;
     }
-    const int root_cap = h->prm.root_cap > 0 ? h->prm.root_cap : 40000;
-    int done = 0;
-    for (int l = h->L; l >= 1; --l) {
-      rc = factor_level(h, l);
-      if (rc) break;
-      h->top = l;
-      ++done;
-      if (l == 1) break;
-      if (h->prm.max_levels > 0 && done >= h->prm.max_levels) break;
-      // candidates of the parents
-      int64_t Scur = 0, Snext = 0;
-      int nmax = 0;
-      for (auto& b : h->lv[l].box) {
-        Scur += b.n;
-        Snext += b.k;
-      }
-      for (int p = 0; p < (1 << (l - 1)); ++p) {
-        Box& P = h->lv[l - 1].box[p];
-        Box& A = h->lv[l].box[2 * p];
-        Box& B = h->lv[l].box[2 * p + 1];
-        P.cr = A.Jr;
-        P.cr.insert(P.cr.end(), B.Jr.begin(), B.Jr.end());
-        P.cc = A.Jc;
-        P.cc.insert(P.cc.end(), B.Jc.begin(), B.Jc.end());
-        nmax = std::max(nmax, (int)P.cr.size());
-      }
-      // stop compressing when it no longer pays (high-frequency boxes keep most unknowns) and
-      // the merged system fits the root, or when the next level's boxes would be too large
-      // for one-CTA column-pivoted QR
-      if ((Snext > 0.8 * (double)Scur && Snext <= root_cap) || nmax > 3072) break;
-    }
-    if (!rc && h->prm.max_levels <= 0) {
-      int64_t S = 0;
-      for (auto& b : h->lv[h->top].box) S += b.k;
-      if (S > root_cap) rc = WSBM_ERR_RANK_OVERFLOW;
-    }
+    b->hs.push_back(h);
   }
-  bool partial = h->L > 0 && h->prm.max_levels > 0;
-  if (!rc && !partial) rc = factor_root(h);
-  cudaEventRecord(t1, h->st);
-  cudaEventSynchronize(t1);
-  h->stats.ms_total_factor = elapsed(t0, t1);
-  h->stats.launches = wsbm_launch_count() - launches0;
-  cudaEventDestroy(t0);
-  cudaEventDestroy(t1);
-  if (rc) {
-    int32_t keep[32];
-    memcpy(keep, h->stats.rank_per_level, sizeof(keep));
-    release_factors(h);
-    memcpy(h->stats.rank_per_level, keep, sizeof(keep));  // kept for diagnosis
-    return rc;
-  }
-  size_t bytes = 0;
-  for (int l = h->top; l <= h->L && h->L > 0; ++l)
-    for (auto& b : h->lv[l].box)
-      bytes += ((size_t)b.n * b.n + (size_t)b.n * b.k + (size_t)b.k * b.k + (size_t)b.k * (b.n - b.k)) *
-               sizeof(double2);
-  bytes += (size_t)h->root_n * h->root_n * sizeof(double2);
-  h->stats.factor_bytes = (int64_t)bytes;
-  h->factored = !partial;
+  *out = b;
   return WSBM_OK;
+}
+
+extern "C" int wsbm_batch_factor(wsbm_batch_t b) {
+  if (!b || b->hs.empty()) return WSBM_ERR_INVALID_ARG;
+  return factor_all(b->hs, &b->stats);
+}
+
+extern "C" int wsbm_batch_handle(wsbm_batch_t b, int32_t i, wsbm_hss_t* out) {
+  if (!b || !out || i < 0 || i >= (int32_t)b->hs.size()) return WSBM_ERR_INVALID_ARG;
+  *out = b->hs[i];
+  return WSBM_OK;
+}
+
+extern "C" int wsbm_batch_stats(wsbm_batch_t b, wsbm_stats_t* s) {
+  if (!b || !s) return WSBM_ERR_INVALID_ARG;
+  *s = b->stats;
+  return WSBM_OK;
+}
+
+extern "C" void wsbm_batch_destroy(wsbm_batch_t b) {
+  if (!b) return;
+  for (auto* h : b->hs) wsbm_destroy(h);
+  delete b;
 }
 
 // ----------------------------------------------------------------------- solve ----

@@ -32,7 +32,7 @@ struct PairTask {
   int32_t trans;  // output layout (see above)
   int32_t tile0;  // index of this task's first tile in the launch
   int32_t fastc;  // 1: column slots run along the 32-wide fast tile dimension, 0: row slots
-  int32_t pad;
+  int32_t inst;   // instance (curve) of a batched launch; 0 otherwise
 };
 
 // One proxy-circle block (proxy-surface method).  Box slot t names node node[t]; its
@@ -50,6 +50,8 @@ struct ProxyTask {
   int32_t side, tr;
   int32_t off;
   int32_t tile0;
+  int32_t inst;  // instance (curve) of a batched launch; 0 otherwise
+  int32_t pad;
 };
 
 // Tiles: TILE_F slots along the fast (contiguous-output) dimension x TILE_S along the other.
@@ -58,10 +60,14 @@ struct ProxyTask {
 #define WSBM_PAIR_THREADS 128
 
 // entries.cu
+// Launch the entry kernels.  geos / phys: optional device arrays indexed by the tasks' `inst`
+// (batched launches over several curves); when NULL every task uses g / ph.
 int wsbm_launch_pairs(const DevGeom& g, const Phys& ph, const PairTask* d_tasks, int ntasks,
-                      int64_t ntiles, cudaStream_t st);
+                      int64_t ntiles, cudaStream_t st, const DevGeom* geos = nullptr,
+                      const Phys* phys = nullptr);
 int wsbm_launch_proxy(const DevGeom& g, const Phys& ph, const ProxyTask* d_tasks, int ntasks,
-                      int64_t ntiles, int mixed, cudaStream_t st);
+                      int64_t ntiles, int mixed, cudaStream_t st, const DevGeom* geos = nullptr,
+                      const Phys* phys = nullptr);
 int64_t wsbm_pair_tiles(int32_t nr, int32_t nc, int32_t fastc);
 int64_t wsbm_proxy_tiles(int32_t nn, int32_t P);
 int wsbm_launch_hankel(const double* z, int64_t n, double* out, int mixed, cudaStream_t st);
