@@ -8,11 +8,9 @@ which defines the real functions P_nu, Q_nu exactly (P -> 1, Q -> 0 as z -> infi
   DEG in s = (u - c)/h, u = 1/z (c, h: centre and half-width of the interval in u), obtained by
   interpolation at Chebyshev points in 50-digit arithmetic (mpmath).  In u the functions are far
   smoother than in z (degree 10 instead of 16 for the same accuracy).
-* z >= Z_ASYM: P_nu - 1 and z Q_nu as polynomials of the same degree DEG in s = (t - c)/h,
-  t = 1/z^2 on [0, 1/Z_ASYM^2], interpolated the same way (their values at t = 0 follow the
-  Hankel asymptotic expansion, A&S 9.2.5-9.2.10: P -> 1, z Q -> (4 nu^2 - 1)/8).  This row is
-  stored as one more interval, so the device evaluates every z >= Z_SERIES with the same
-  branch-free code (no divergence between regimes inside a warp).
+* z >= Z_ASYM: P_nu - 1 and z Q_nu as polynomials of degree DEG_T in s = (t - c)/h, t = 1/z^2 on
+  [0, 1/Z_ASYM^2], interpolated the same way (their values at t = 0 follow the Hankel asymptotic
+  expansion, A&S 9.2.5-9.2.10: P -> 1, z Q -> (4 nu^2 - 1)/8).
 * z < Z_SERIES: ascending series (A&S 9.1.10, 9.1.11, 9.1.13 with psi(k+1) = H_k - gamma) in
   u = z^2/4:
     J0 = sum (-u)^k/(k!)^2,          J1 = (z/2) sum (-u)^k/(k!(k+1)!),
@@ -37,16 +35,16 @@ import numpy as np
 mp.mp.dps = 50
 
 # interval bounds in z: dyadic values, so the device can compare the high word of z as an integer
-BOUNDS = [1.5, 2.0, 3.0, 4.0, 5.5, 8.0, 10.0]
+BOUNDS = [1.5, 2.0, 3.0, 4.0, 5.5, 8.0, 12.0, 20.0]
 Z_SERIES = BOUNDS[0]
 Z_ASYM = BOUNDS[-1]
 DEG = 10
-DEG_T = DEG
+DEG_T = 6
 N_SERIES = 12
 DEG_SC = 6
 VMAX = 0.66   # (pi/4 + slack)^2
 DEG_F = 4
-DEG_TF = DEG_F
+DEG_TF = 2
 TWO_PI_HEAD_BITS = 33   # 2 pi head for the mixed evaluator: n * head is exact for n < 2^20
 
 
@@ -144,7 +142,7 @@ def sincos_tables():
 
 # ---------------------------------------------------------------- device emulation ----
 def pq_eval64(z, mids, fits, asy, tc, tih):
-    if z < Z_ASYM:  # intervals in u (the device picks the row by the high word of z)
+    if z < Z_ASYM:
         iv = sum(1 for b in BOUNDS[1:-1] if z >= b)
         a, b, c, ih = mids[iv]
         s = (1.0 / z - float(c)) * float(ih)
@@ -216,33 +214,37 @@ def main():
     nv = len(mids)
     L = ["// Generated by gen_hankel_coeffs.py -- do not edit.",
          f"// max abs error (emulated): P,Q FP64 {errs[0]:.2e}, FP32 {errs[1]:.2e}; sin {errs[2]:.2e}, cos {errs[3]:.2e}",
-         f"#define HK_Z_SERIES {Z_SERIES!r}", f"#define HK_Z_ASYM {Z_ASYM!r}",
-         f"#define HK_NIV {nv + 1}  // intervals in 1/z plus the row in 1/z^2",
-         f"#define HK_DEG {DEG}", f"#define HK_NSER {N_SERIES}",
-         f"#define HK_DEG_SC {DEG_SC}", f"#define HKF_DEG {DEG_F}", ""]
+         f"#define HK_Z_SERIES {Z_SERIES!r}", f"#define HK_Z_ASYM {Z_ASYM!r}", f"#define HK_NIV {nv}",
+         f"#define HK_DEG {DEG}", f"#define HK_DEG_T {DEG_T}", f"#define HK_NSER {N_SERIES}",
+         f"#define HK_DEG_SC {DEG_SC}", f"#define HKF_DEG {DEG_F}", f"#define HKF_DEG_T {DEG_TF}", ""]
     # interval i covers [BOUNDS[i], BOUNDS[i+1]); high 32-bit words of the inner bounds
     import struct
-    his = [struct.unpack("<II", struct.pack("<d", b))[1] for b in BOUNDS[1:-1]]  # + Z_ASYM below
+    his = [struct.unpack("<II", struct.pack("<d", b))[1] for b in BOUNDS[1:-1]]
     los = [struct.unpack("<II", struct.pack("<d", b))[0] for b in BOUNDS]
     assert all(l == 0 for l in los), "bounds must have a zero low word"
     L.append("// high 32-bit words of the inner interval bounds (their low words are zero)")
-    L.append("#define HK_IV_HI {" + ", ".join(str(h) for h in his + [struct.unpack("<II", struct.pack("<d", Z_ASYM))[1]]) + "}")
+    L.append("#define HK_IV_HI {" + ", ".join(str(h) for h in his) + "}")
     L.append(f"#define HK_SERIES_HI {struct.unpack('<II', struct.pack('<d', BOUNDS[0]))[1]}")
     L.append(f"#define HK_ASYM_HI {struct.unpack('<II', struct.pack('<d', BOUNDS[-1]))[1]}")
-    L.append("// rows 0..HK_NIV-2: centre and 1/half-width in u = 1/z of the intervals;")
-    L.append("// row HK_NIV-1: centre and 1/half-width in t = 1/z^2 of [0, 1/HK_Z_ASYM^2]")
+    L.append("// per interval: centre and 1/half-width in u = 1/z")
     L.append("static __device__ const double hk_iv[HK_NIV][2] = {")
     for (a, b, c, ih) in mids:
         L.append(f"  {{{fmt(c)}, {fmt(ih)}}},  // z in [{a}, {b})")
-    L.append(f"  {{{fmt(tc)}, {fmt(tih)}}},  // z >= {Z_ASYM}")
     L.append("};")
-    L.append("// fits[row][fn][k]: fn = P0-1, Q0, P1-1, Q1 (last row: P0-1, z Q0, P1-1, z Q1)")
+    L.append("// fits[iv][fn][k], fn = P0-1, Q0, P1-1, Q1")
     L.append("static __device__ const double hk_fit[HK_NIV][4][HK_DEG + 1] = {")
-    for row in fits + [asy]:
+    for row in fits:
         L.append("  {")
         for cf in row:
             L.append("    {" + ", ".join(fmt(v) for v in cf) + "},")
         L.append("  },")
+    L.append("};")
+    L.append(f"#define HK_T_C {fmt(tc)}")
+    L.append(f"#define HK_T_IH {fmt(tih)}")
+    L.append("// z >= HK_Z_ASYM, in t = 1/z^2: fn = P0-1, z Q0, P1-1, z Q1")
+    L.append("static __device__ const double hk_asy[4][HK_DEG_T + 1] = {")
+    for cf in asy:
+        L.append("  {" + ", ".join(fmt(v) for v in cf) + "},")
     L.append("};")
     j0, j1, y0, y1 = series_coeffs()
     L.append("static __device__ const double hk_ser[4][HK_NSER] = {")
@@ -258,11 +260,15 @@ def main():
     L.append(f"#define HK_PIO2_LO {fmt(half_pi - c1)}")
     L.append(f"#define HK_2_OVER_PI {fmt(2 / mp.pi)}")
     L.append("static __device__ const float hkf_fit[HK_NIV][4][HKF_DEG + 1] = {")
-    for row in fitsf + [asyf]:
+    for row in fitsf:
         L.append("  {")
         for cf in row:
             L.append("    {" + ", ".join(fmt(v) + "f" for v in cf) + "},")
         L.append("  },")
+    L.append("};")
+    L.append("static __device__ const float hkf_asy[4][HKF_DEG_T + 1] = {")
+    for cf in asyf:
+        L.append("  {" + ", ".join(fmt(v) + "f" for v in cf) + "},")
     L.append("};")
     two_pi = 2 * mp.pi
     e = int(mp.floor(mp.log(two_pi, 2)))

@@ -6,11 +6,9 @@
 //   z < 1.5     ascending series in z^2/4 (A&S 9.1.10, 9.1.11, 9.1.13); the 1/z pole of Y1 is kept
 //               apart so F1 = H1/z + 2i/(pi z^2) is formed without cancellation;
 //   z >= 1.5    H_nu = sqrt(2/(pi z)) (P_nu + i Q_nu) e^{i(z - pi/4 - nu pi/2)};
-//               P_nu - 1, Q_nu are degree-10 polynomials in u = 1/z on six intervals up to
-//               z = 10 (the functions are smooth in 1/z), and P_nu - 1, z Q_nu degree-10
-//               polynomials in 1/z^2 beyond.  All regimes run the same instructions (the
-//               table row, the variable and a final factor are selected per lane), so lanes of
-//               a warp in different regimes do not diverge;
+//               P_nu - 1, Q_nu are degree-10 polynomials in u = 1/z on seven intervals up to
+//               z = 20 (the functions are smooth in 1/z), and degree-6 polynomials in 1/z^2
+//               beyond (P_nu - 1 and z Q_nu);
 //   phase       z - pi/4 is reduced by multiples of pi/2 (Cody-Waite with a two-part pi/2 and
 //               fused multiply-adds) and sin/cos of the remainder |w| <= pi/4 come from fitted
 //               polynomials, so no rounding of z - pi/4 enters the phase.
@@ -18,8 +16,8 @@
 // All coefficients are fitted by gen_hankel_coeffs.py (50-digit arithmetic) and checked there.
 //
 // Mixed evaluator (WSBM_MIXED): the phase is reduced in FP64 (z - 2 pi n, two-part 2 pi), then
-// sin/cos of the remainder, sqrt(2/(pi z)) and P, Q (degree-4 fits in 1/z and in 1/z^2) are
-// FP32.  Arguments below 1.5 fall back to the FP64 evaluator.
+// sin/cos of the remainder, sqrt(2/(pi z)) and P, Q (degree-4 fits in 1/z, degree-2 in 1/z^2)
+// are FP32.  Arguments below 1.5 fall back to the FP64 evaluator.
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -45,11 +43,13 @@ struct HkF {
 struct HkTables {
   double iv[HK_NIV][2];
   double fit[HK_NIV][4][HK_DEG + 1];
+  double asy[4][HK_DEG_T + 1];
   double ser[4][HK_NSER];
   double sn[HK_DEG_SC + 1];
   double cs[HK_DEG_SC + 1];
   float ivf[HK_NIV][2];
   float fitf[HK_NIV][4][HKF_DEG + 1];
+  float asyf[4][HKF_DEG_T + 1];
 };
 
 template <class T>
@@ -60,10 +60,12 @@ __device__ __forceinline__ void hk_copy(T* dst, const T* src, int n) {
 __device__ __forceinline__ void hk_stage_tables(HkTables* t) {
   hk_copy(&t->iv[0][0], &hk_iv[0][0], HK_NIV * 2);
   hk_copy(&t->fit[0][0][0], &hk_fit[0][0][0], HK_NIV * 4 * (HK_DEG + 1));
+  hk_copy(&t->asy[0][0], &hk_asy[0][0], 4 * (HK_DEG_T + 1));
   hk_copy(&t->ser[0][0], &hk_ser[0][0], 4 * HK_NSER);
   hk_copy(t->sn, hk_sin, HK_DEG_SC + 1);
   hk_copy(t->cs, hk_cos, HK_DEG_SC + 1);
   hk_copy(&t->fitf[0][0][0], &hkf_fit[0][0][0], HK_NIV * 4 * (HKF_DEG + 1));
+  hk_copy(&t->asyf[0][0], &hkf_asy[0][0], 4 * (HKF_DEG_T + 1));
   for (int k = threadIdx.x; k < HK_NIV * 2; k += blockDim.x)
     (&t->ivf[0][0])[k] = (float)(&hk_iv[0][0])[k];
 }
@@ -84,8 +86,8 @@ __device__ __forceinline__ float hk_hornerf(const float* c, float s) {
   return r;
 }
 
-// Table row for z >= HK_Z_SERIES from the high word of z (integer compares: the bounds have zero
-// low words, and positive doubles order like their bit patterns); HK_NIV - 1 for z >= HK_Z_ASYM.
+// Interval index for HK_Z_SERIES <= z < HK_Z_ASYM from the high word of z (integer compares:
+// the bounds have zero low words, and positive doubles order like their bit patterns).
 __device__ __forceinline__ int hk_interval_hi(int hi) {
   const int lim[HK_NIV - 1] = HK_IV_HI;
   int iv = 0;
@@ -135,20 +137,23 @@ __device__ __forceinline__ void hk_series(const HkTables& T, double z, double iz
   o.f1i = y1h * iz;
 }
 
-// P_nu - 1 (pm0, pm1) and Q_nu for z >= HK_Z_SERIES, u = 1/z, without branches: rows below
-// HK_Z_ASYM are polynomials in u, the last row a polynomial in u^2 that gives z Q_nu.
+// P_nu - 1 (pm0, pm1) and Q_nu for z >= HK_Z_SERIES, u = 1/z.
 __device__ __forceinline__ void hk_pq(const HkTables& T, int zhi, double u, double* pm0,
                                       double* Q0, double* pm1, double* Q1) {
-  const int iv = hk_interval_hi(zhi);
-  const bool asym = iv == HK_NIV - 1;
-  const double uu = u * u;
-  const double a = asym ? uu : u;
-  const double s = (a - T.iv[iv][0]) * T.iv[iv][1];
-  const double qf = asym ? u : 1.0;
-  *pm0 = hk_horner<HK_DEG + 1>(T.fit[iv][0], s);
-  *Q0 = qf * hk_horner<HK_DEG + 1>(T.fit[iv][1], s);
-  *pm1 = hk_horner<HK_DEG + 1>(T.fit[iv][2], s);
-  *Q1 = qf * hk_horner<HK_DEG + 1>(T.fit[iv][3], s);
+  if (zhi < HK_ASYM_HI) {
+    int iv = hk_interval_hi(zhi);
+    double s = (u - T.iv[iv][0]) * T.iv[iv][1];
+    *pm0 = hk_horner<HK_DEG + 1>(T.fit[iv][0], s);
+    *Q0 = hk_horner<HK_DEG + 1>(T.fit[iv][1], s);
+    *pm1 = hk_horner<HK_DEG + 1>(T.fit[iv][2], s);
+    *Q1 = hk_horner<HK_DEG + 1>(T.fit[iv][3], s);
+  } else {
+    double s = (u * u - HK_T_C) * HK_T_IH;
+    *pm0 = hk_horner<HK_DEG_T + 1>(T.asy[0], s);
+    *Q0 = u * hk_horner<HK_DEG_T + 1>(T.asy[1], s);
+    *pm1 = hk_horner<HK_DEG_T + 1>(T.asy[2], s);
+    *Q1 = u * hk_horner<HK_DEG_T + 1>(T.asy[3], s);
+  }
 }
 
 // FP64 H0, H1 and (WITH_F1) F1 = H1/z + 2i/(pi z^2) at z > 0, given rs ~ 1/sqrt(z) to a few
@@ -207,16 +212,20 @@ __device__ __forceinline__ void hankel_mixed_large(const HkTables& T, double z, 
   float E = (cs + sn) * (float)WSBM_INV_SQRT2;
   float F = (sn - cs) * (float)WSBM_INV_SQRT2;
   float P0, Q0, P1, Q1;  // P0, P1 hold P - 1 until D is formed
-  {
-    const int iv = hk_interval_hi(__double2hiint(z));
-    const bool asym = iv == HK_NIV - 1;
-    const float a = asym ? u * u : u;
-    const float s = (a - T.ivf[iv][0]) * T.ivf[iv][1];
-    const float qf = asym ? u : 1.0f;
+  const int zhi = __double2hiint(z);
+  if (zhi < HK_ASYM_HI) {
+    int iv = hk_interval_hi(zhi);
+    float s = (u - T.ivf[iv][0]) * T.ivf[iv][1];
     P0 = hk_hornerf<HKF_DEG + 1>(T.fitf[iv][0], s);
-    Q0 = qf * hk_hornerf<HKF_DEG + 1>(T.fitf[iv][1], s);
+    Q0 = hk_hornerf<HKF_DEG + 1>(T.fitf[iv][1], s);
     P1 = hk_hornerf<HKF_DEG + 1>(T.fitf[iv][2], s);
-    Q1 = qf * hk_hornerf<HKF_DEG + 1>(T.fitf[iv][3], s);
+    Q1 = hk_hornerf<HKF_DEG + 1>(T.fitf[iv][3], s);
+  } else {
+    float s = (u * u - (float)HK_T_C) * (float)HK_T_IH;
+    P0 = hk_hornerf<HKF_DEG_T + 1>(T.asyf[0], s);
+    Q0 = u * hk_hornerf<HKF_DEG_T + 1>(T.asyf[1], s);
+    P1 = hk_hornerf<HKF_DEG_T + 1>(T.asyf[2], s);
+    Q1 = u * hk_hornerf<HKF_DEG_T + 1>(T.asyf[3], s);
   }
   if (Dr) {
     float dr = Q1 - Q0, di = P0 - P1;

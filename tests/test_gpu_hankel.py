@@ -7,7 +7,7 @@ import oracle
 pytestmark = pytest.mark.gpu
 
 # Break points of the device evaluator (series / fitted intervals / asymptotic term counts).
-BREAKS = [1.5, 2.0, 3.0, 4.0, 5.5, 8.0, 10.0, 20.0, 100.0, 1000.0]
+BREAKS = [1.5, 2.0, 3.0, 4.0, 5.5, 8.0, 12.0, 20.0, 100.0, 1000.0]
 
 
 def sample_z(seed=0):
