@@ -41,6 +41,14 @@ int wsbm_phys_from_params(const wsbm_params* p, Phys* ph) {
   ph->inv_k1 = 1.0 / ph->k1;
   ph->s01 = sqrt(ph->k0 / ph->k1);
   ph->s10 = sqrt(ph->k1 / ph->k0);
+  ph->fk0 = (float)ph->k0;
+  ph->fk1 = (float)ph->k1;
+  ph->frk0 = (float)(1.0 / sqrt(ph->k0));
+  ph->frk1 = (float)(1.0 / sqrt(ph->k1));
+  ph->finv_k0 = (float)ph->inv_k0;
+  ph->feps0 = (float)ph->eps0;
+  ph->feps1 = (float)ph->eps1;
+  ph->fpad = 0.0f;
   return WSBM_OK;
 }
 

@@ -94,6 +94,7 @@ __device__ __forceinline__ void block_diag(const Phys& ph, double wi, double kap
 
 struct SlotData {
   double x, y, nx, ny, w, kap;
+  float fnx, fny, fw;  // FP32 copies for the mixed-precision algebra
   int32_t node, p0, p1;
 };
 
@@ -120,6 +121,9 @@ __device__ __forceinline__ void load_slot(const DevGeom& g, const int32_t* nodes
   s.ny = g.ny[nd];
   s.w = g.w[nd];
   s.kap = g.kappa[nd];
+  s.fnx = (float)s.nx;
+  s.fny = (float)s.ny;
+  s.fw = (float)s.w;
   s.p0 = pos[2 * t];
   s.p1 = pos[2 * t + 1];
 }
@@ -197,6 +201,7 @@ __global__ void __launch_bounds__(WSBM_PAIR_THREADS)
 // --------------------------------------------------------------------- proxy blocks ----
 struct ProxyPt {
   double px, py, pnx, pny;
+  float fpnx, fpny;
 };
 
 // Sources on the proxy circle acting on equations at node x (row side).  Combined-field
@@ -273,9 +278,19 @@ __device__ __forceinline__ void proxy_col_fp64(const HkTables& T, const Phys& ph
 
 // Mixed precision versions: z = k r formed in FP64 and reduced mod 2 pi in FP64; amplitude and
 // entry algebra in FP32.
-__device__ __forceinline__ void hankel_mixed(const HkTables& T, double z, HkF& o) {
+// sqrt of r2 > 0 for the mixed path: FP64 reciprocal-square-root seed and one Newton step
+// (relative error ~1e-13, far below the FP32 amplitude; no IEEE rounding needed there).
+__device__ __forceinline__ double sqrt_mixed(double r2) {
+  double y;
+  asm("rsqrt.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(r2));
+  double h = 0.5 * r2;
+  y = fma(y, fma(-h * y, y, 0.5), y);
+  return r2 * y;
+}
+
+__device__ __forceinline__ void hankel_mixed(const HkTables& T, double z, float rsz, HkF& o) {
   if (__double2hiint(z) >= HK_SERIES_HI) {
-    hankel_mixed_large(T, z, o);
+    hankel_mixed_large(T, z, rsz, o);
   } else {
     Hk h;
     hankel_fp64(T, z, h);
@@ -295,27 +310,30 @@ __device__ __forceinline__ void hankel_mixed(const HkTables& T, double z, HkF& o
 __device__ __forceinline__ void proxy_row_mixed(const HkTables& T, const Phys& ph, const SlotData& X,
                                                 const ProxyPt& p, double pw, double2 o[2][2]) {
   double dx = X.x - p.px, dy = X.y - p.py;
-  double r = sqrt(dx * dx + dy * dy);
-  double dnu_d = dx * p.pnx + dy * p.pny;
-  double crs_d = dx * p.pny - dy * p.pnx;
-  float ir = 1.0f / (float)r;
-  float dnu = (float)dnu_d * ir;
-  float cr = (float)crs_d * ir;
+  double r = sqrt_mixed(fma(dx, dx, dy * dy));
+  // directions in FP32 from the FP64 difference vector (d.nu and d x nu keep relative accuracy)
+  float fdx = (float)dx, fdy = (float)dy, fr = (float)r;
+  float ir = 1.0f / fr;
+  float pnx = p.fpnx, pny = p.fpny;
+  float dnu = (fdx * pnx + fdy * pny) * ir;
+  float cr = (fdx * pny - fdy * pnx) * ir;
   float opd = cr * cr / (1.0f - dnu);  // 1 + dnu
-  float dnx = ((float)dx * (float)X.nx + (float)dy * (float)X.ny) * ir;
-  float nn = (float)X.nx * (float)p.pnx + (float)X.ny * (float)p.pny;
+  float dnx = (fdx * X.fnx + fdy * X.fny) * ir;
+  float nn = X.fnx * pnx + X.fny * pny;
   float m2c = nn - 2.0f * dnx * dnu;
-  float inv_k0 = (float)(1.0 / ph.k0);
+  float inv_k0 = ph.finv_k0;
   float fpw = (float)pw;
+  float rsr = rsqrtf(fr);
 #pragma unroll
   for (int s = 0; s < 2; ++s) {
     double kd = s == 0 ? ph.k1 : ph.k0;
-    float k = (float)kd;
+    float k = s == 0 ? ph.fk1 : ph.fk0;
     double z = kd * r;
+    float rsz = rsr * (s == 0 ? ph.frk1 : ph.frk0);
     HkF h;
     float Dr, Di;
     if (__double2hiint(z) >= HK_SERIES_HI) {
-      hankel_mixed_large(T, z, h, &Dr, &Di);
+      hankel_mixed_large(T, z, rsz, h, &Dr, &Di);
     } else {
       Hk hd;
       hankel_fp64(T, z, hd);
@@ -348,16 +366,19 @@ __device__ __forceinline__ void proxy_row_mixed(const HkTables& T, const Phys& p
 __device__ __forceinline__ void proxy_col_mixed(const HkTables& T, const Phys& ph, const SlotData& Y,
                                                 const ProxyPt& p, double2 o[2][2]) {
   double dx = p.px - Y.x, dy = p.py - Y.y;
-  double r = sqrt(dx * dx + dy * dy);
-  float dny = ((float)dx * (float)Y.nx + (float)dy * (float)Y.ny) / (float)r;
-  float w = (float)Y.w;
+  double r = sqrt_mixed(fma(dx, dx, dy * dy));
+  float fr = (float)r;
+  float dny = ((float)dx * Y.fnx + (float)dy * Y.fny) / fr;
+  float w = Y.fw;
+  float rsr = rsqrtf(fr);
 #pragma unroll
   for (int s = 0; s < 2; ++s) {
     double kd = s == 0 ? ph.k1 : ph.k0;
-    float eps = (float)(s == 0 ? ph.eps1 : ph.eps0);
+    float k = s == 0 ? ph.fk1 : ph.fk0;
+    float eps = s == 0 ? ph.feps1 : ph.feps0;
     HkF h;
-    hankel_mixed(T, kd * r, h);
-    float a = 0.25f * w * (float)kd * dny;
+    hankel_mixed(T, kd * r, rsr * (s == 0 ? ph.frk1 : ph.frk0), h);
+    float a = 0.25f * w * k * dny;
     o[s][0] = make_double2(-a * h.h1i, a * h.h1r);
     float bq = -0.25f * eps * w;
     o[s][1] = make_double2(-bq * h.h0i, bq * h.h0r);
@@ -392,6 +413,8 @@ __global__ void __launch_bounds__(WSBM_PAIR_THREADS)
         sincospi(2.0 * (double)m / (double)tk.P, &sn, &cs);
         sp[threadIdx.x].pnx = cs;
         sp[threadIdx.x].pny = sn;
+        sp[threadIdx.x].fpnx = (float)cs;
+        sp[threadIdx.x].fpny = (float)sn;
         sp[threadIdx.x].px = tk.cx + tk.rho * cs;
         sp[threadIdx.x].py = tk.cy + tk.rho * sn;
       }
@@ -444,7 +467,7 @@ __global__ void k_hankel(const double* __restrict__ z, int64_t n, double* __rest
     double* o = out + 6 * i;
     if (mixed) {
       HkF h;
-      hankel_mixed(T, zi, h);
+      hankel_mixed(T, zi, rsqrtf((float)zi), h);
       o[0] = h.h0r;
       o[1] = h.h0i;
       o[2] = h.h1r;

@@ -16,7 +16,7 @@
 // All coefficients are fitted by gen_hankel_coeffs.py (50-digit arithmetic) and checked there.
 //
 // Mixed evaluator (WSBM_MIXED): the phase is reduced in FP64 (z - 2 pi n, two-part 2 pi), then
-// sin/cos of the remainder, sqrt(2/(pi z)) and P, Q (degree-4 fits in 1/z, degree-2 in 1/z^2)
+// sin/cos of the remainder (rounded to FP32: phase error <= 2e-7), sqrt(2/(pi z)) and P, Q (degree-4 fits in 1/z, degree-2 in 1/z^2)
 // are FP32.  Arguments below 1.5 fall back to the FP64 evaluator.
 #pragma once
 #include <cuda_runtime.h>
@@ -192,21 +192,17 @@ __device__ __forceinline__ void hankel_fp64(const HkTables& T, double z, Hk& o) 
 // D = H1 + i H0 = sqrt(2/(pi z)) e^{i(z - pi/4)} [(Q1 - Q0) + i(P0 - P1)], formed from the small
 // differences of P and Q so that it keeps its relative accuracy (H1 ~ -i H0 for large z, and
 // combined-field sources cancel to leading order).
-__device__ __forceinline__ void hankel_mixed_large(const HkTables& T, double z, HkF& o,
+// rsz: 1/sqrt(z) in FP32 (callers derive it from one FP32 reciprocal square root per pair).
+__device__ __forceinline__ void hankel_mixed_large(const HkTables& T, double z, float rsz, HkF& o,
                                                    float* Dr = nullptr, float* Di = nullptr) {
   // z - 2 pi n with 2 pi split into a short head (n * head exact) and a tail
   double n = rint(z * (0.5 / WSBM_PI));
   double y = fma(-n, HK_TWO_PI_HI, z);
   y = fma(-n, HK_TWO_PI_LO, y);
-  // y = yf + ylo: the FP32 rounding of the phase (up to 1.2e-7) is carried to first order
   float yf = (float)y;
-  float ylo = (float)(y - (double)yf);
-  float sn0, cs0;
-  sincosf(yf, &sn0, &cs0);
-  float sn = fmaf(cs0, ylo, sn0);
-  float cs = fmaf(-sn0, ylo, cs0);
-  float zf = (float)z;
-  float rs = rsqrtf(zf);
+  float sn, cs;
+  sincosf(yf, &sn, &cs);
+  float rs = rsz;
   float u = rs * rs;
   float A = (float)WSBM_SQRT_2_OVER_PI * rs;
   float E = (cs + sn) * (float)WSBM_INV_SQRT2;

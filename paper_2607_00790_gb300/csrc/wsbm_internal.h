@@ -15,6 +15,8 @@ struct Phys {
   double k0, k1, eps0, eps1;
   double inv_k0, inv_k1;  // 1/k0, 1/k1
   double s01, s10;        // sqrt(k0/k1), sqrt(k1/k0): 1/sqrt(k1 r) = s01/sqrt(k0 r)
+  // FP32 copies for the mixed-precision kernels
+  float fk0, fk1, frk0, frk1, finv_k0, feps0, feps1, fpad;  // frk = 1/sqrt(k)
 };
 
 // One output block of node-pair entries of the WSBM matrix.  A row "slot" t names row node
