@@ -391,13 +391,9 @@ __global__ void __launch_bounds__(256) k_cpqr(const QrDesc* __restrict__ d, int 
       }
       w.x *= tau;
       w.y *= tau;
-      double rj = 0.0;
-      for (int i = j + lane; i < m; i += 32) {
-        double2 v = cfms(u[i], w, col[i]);
-        col[i] = v;
-        if (i == j) rj = cabs2(v);
-      }
-      rj = __shfl_sync(0xffffffffu, rj, 0);  // lane 0 held row j
+      for (int i = j + lane; i < m; i += 32) col[i] = cfms(u[i], w, col[i]);
+      __syncwarp();
+      const double rj = cabs2(col[j]);  // the new row-j entry (written by lane 0)
       double nv = q.norm2[c] - rj;
       if (nv <= 1e-8 * q.nref[c]) {
         double ns = 0.0;
