@@ -199,6 +199,13 @@ int wsbm_entries(wsbm_hss_t h, const int64_t* rows, int64_t nr, const int64_t* c
  * out4 (host): cx, cy, R, rho; range2 (host): first, last. */
 int wsbm_box_info(wsbm_hss_t h, int32_t level, int32_t box, double* out4, int64_t* range2);
 
+/* Skeletons of box `box` on level `level` after wsbm_factor (also after a partial build):
+ * k (host) receives the skeleton size; jr, jc (host, capacity cap each) receive the row and
+ * column skeleton indices in the paper's unknown order.  Errors: INVALID_ARG (level not
+ * compressed, cap < k). */
+int wsbm_box_skeletons(wsbm_hss_t h, int32_t level, int32_t box, int64_t* jr, int64_t* jc,
+                       int32_t cap, int32_t* k);
+
 /* Counters and timings (host struct). */
 int wsbm_stats(wsbm_hss_t h, wsbm_stats_t* s);
 

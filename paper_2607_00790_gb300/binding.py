@@ -82,6 +82,8 @@ def lib():
         L.wsbm_entries.argtypes = [vp, vp, i64, vp, i64, vp]
         L.wsbm_box_info.argtypes = [vp, i32, i32, ctypes.POINTER(d), ctypes.POINTER(i64)]
         L.wsbm_stats.argtypes = [vp, ctypes.POINTER(Stats)]
+        L.wsbm_box_skeletons.argtypes = [vp, i32, i32, vp, vp, i32, ctypes.POINTER(i32)]
+        L.wsbm_box_skeletons.restype = ctypes.c_int
         L.wsbm_destroy.argtypes = [vp]
         L.wsbm_destroy.restype = None
         L.wsbm_batch_create.argtypes = [ctypes.POINTER(Geom), ctypes.POINTER(Params), i32, vp,
@@ -221,6 +223,17 @@ class Solver:
         s = Stats()
         _check(lib().wsbm_stats(self.h, ctypes.byref(s)), "wsbm_stats")
         return s.as_dict()
+
+    def skeletons(self, level, box, cap=4096):
+        """Row and column skeleton indices (paper order) of a compressed box."""
+        import numpy as np
+        jr = np.empty(cap, dtype=np.int64)
+        jc = np.empty(cap, dtype=np.int64)
+        k = ctypes.c_int32()
+        _check(lib().wsbm_box_skeletons(self.h, level, box, ctypes.c_void_p(jr.ctypes.data),
+                                        ctypes.c_void_p(jc.ctypes.data), cap, ctypes.byref(k)),
+               "wsbm_box_skeletons")
+        return jr[: k.value].copy(), jc[: k.value].copy()
 
     def close(self):
         if self.h and self.owned:

@@ -566,6 +566,7 @@ extern "C" int wsbm_create(const wsbm_geom* g, const wsbm_params* p, void* strea
 
 static void release_factors(wsbm_hss* h) {
   free_list(h, h->owned);
+  for (auto& l : h->lv) l.compressed = false;
   for (auto& l : h->lv)
     for (auto& b : l.box) {
       b.D = b.Z = b.Dc = b.Tc = nullptr;
@@ -1656,6 +1657,23 @@ extern "C" int wsbm_box_info(wsbm_hss_t h, int32_t level, int32_t box, double* o
   out4[3] = b.rho;
   range2[0] = b.lo;
   range2[1] = b.hi;
+  return WSBM_OK;
+}
+
+extern "C" int wsbm_box_skeletons(wsbm_hss_t h, int32_t level, int32_t box, int64_t* jr,
+                                  int64_t* jc, int32_t cap, int32_t* k) {
+  if (!h || !k || level < 1 || level > h->L || box < 0 || box >= (1 << level))
+    return WSBM_ERR_INVALID_ARG;
+  const Level& LV = h->lv[level];
+  if (!LV.compressed) return WSBM_ERR_INVALID_ARG;
+  const Box& b = LV.box[box];
+  *k = b.k;
+  if (cap < b.k || !jr || !jc) return WSBM_ERR_INVALID_ARG;
+  // interleaved 2i + c  ->  paper order c N + i
+  for (int t = 0; t < b.k; ++t) {
+    jr[t] = (int64_t)(b.Jr[t] & 1) * h->N + (b.Jr[t] >> 1);
+    jc[t] = (int64_t)(b.Jc[t] & 1) * h->N + (b.Jc[t] >> 1);
+  }
   return WSBM_OK;
 }
 

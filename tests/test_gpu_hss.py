@@ -159,3 +159,39 @@ def test_factor_solve_deterministic():
     _, u1, q1 = solve_gpu(s, [0.0])
     _, u2, q2 = solve_gpu(s, [0.0])
     assert np.array_equal(u1, u2) and np.array_equal(q1, q2)
+
+
+def test_full_size_leaf_skeletons_span_far_field():
+    """At the bench size (N = 2^18, 15 nodes per wavelength, leaf-level build): the row
+    skeleton of a box must reproduce the box's far-field rows, and the column skeleton its
+    far-field columns, to the ID tolerance; far entries are sampled from the oracle."""
+    from paper_2607_00790_gb300 import binding
+    c, prm = inputs.workload("mixed")  # star, N = 262144, 15 nodes per wavelength
+    N = c["x"].size
+    tol = 1e-8
+    g, keep = binding.make_geom(c)
+    p = binding.make_params(prm["k0"], prm["n"], leaf=128, nproxy=128, id_tol=tol, max_levels=1)
+    s = binding.Solver(g, p)
+    s._keep = keep
+    s.factor()
+    ph = oracle.Physics(prm["k0"], n=prm["n"])
+    L = s.stats()["levels"]
+    rng = np.random.default_rng(31)
+    for box in (3, 1000):
+        circ, (lo, hi) = s.box_info(L, box)
+        nodes = np.arange(lo, hi)
+        unk = np.concatenate([nodes, nodes + N])
+        jr, jc = s.skeletons(L, box)
+        assert 0 < jr.size < unk.size
+        d = np.hypot(c["x"] - circ[0], c["y"] - circ[1])
+        far_nodes = rng.choice(np.nonzero(d > circ[3])[0], 600, replace=False)
+        far = np.concatenate([far_nodes, far_nodes + N])
+        for rows_side in (True, False):
+            A = oracle.wsbm_entries(c, ph, unk, far) if rows_side else oracle.wsbm_entries(c, ph, far, unk).T
+            sk = jr if rows_side else jc
+            pos = np.searchsorted(unk, sk)
+            Q, _ = np.linalg.qr(A[pos].T)           # span of the skeleton rows
+            R = A.T - Q @ (Q.conj().T @ A.T)
+            rel = np.linalg.norm(R) / np.linalg.norm(A)
+            assert rel < 10 * tol, (box, rows_side, rel)
+    s.close()
