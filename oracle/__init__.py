@@ -13,6 +13,9 @@ Two parts (paper: Matsumoto & Yokota, TE-mode transmission, Secs. II-IV):
 * O-phys: the Mie series for a disk (Sec. IV: "the analytical solution ... can be
   explicitly calculated"), which fixes the discretisation and the paper's O(h^3) claim.
 
+* Shape gradients (``gradient.py``): the dense adjoint of a far-field intensity misfit,
+  with matrix derivatives from a dual-number evaluation of the same blocks.
+
 Every public function states the passage it follows.  Nothing here is tuned for speed.
 """
 from __future__ import annotations
@@ -50,9 +53,10 @@ def _lib():
         lib.orc_proxy_circle.argtypes = [_pd, _pd, _pi64, _i64, _d, _pd]
         lib.orc_proxy_row_block.argtypes = geo + [_pi64, _i64, _d, _d, _d, _i64, _pd]
         lib.orc_proxy_col_block.argtypes = geo + [_pi64, _i64, _d, _d, _d, _i64, _pd]
+        lib.orc_wsbm_bilinear_tangent.argtypes = geo + [_pd, _pd, _i64, _pd, _pd, _pd, _pd]
         for f in (lib.orc_hankel01, lib.orc_f1, lib.orc_wsbm_entries, lib.orc_wsbm_dense,
                   lib.orc_wsbm_matvec, lib.orc_proxy_circle, lib.orc_proxy_row_block,
-                  lib.orc_proxy_col_block):
+                  lib.orc_proxy_col_block, lib.orc_wsbm_bilinear_tangent):
             f.restype = ctypes.c_int
         _LIB = lib
     return _LIB
@@ -324,3 +328,27 @@ def circle_eigenvalues(k, R, m):
     D = 1j * np.pi * k * R / 4 * (Jp * H + J * Hp)
     N = 1j * np.pi * k * k * R / 2 * Jp * Hp
     return S, D, N
+
+
+# ------------------------------------------------------- derivatives (shape gradient) ----
+def wsbm_bilinear_tangent(curve, phys, lam, xv, tan, tk1, teps1):
+    """Directional derivatives d/ds (lam^T A x) of the Nystrom matrix of eq. (weakly_bm) with
+    the one-point corrected diagonal, by forward-mode (dual-number) evaluation of the same
+    block definitions.  lam, xv: (2N,) complex, paper order; tan: (ntan, 6, N) tangents of
+    (x, y, nx, ny, w, kappa); tk1, teps1: (ntan,) tangents of k1 and eps1.  Returns (ntan,)."""
+    g = _geo(curve)
+    n = g[0].size
+    tan = _c64(np.asarray(tan, dtype=np.float64).reshape(-1, 6, n))
+    ntan = tan.shape[0]
+    tk1 = _c64(np.broadcast_to(np.asarray(tk1, dtype=np.float64), (ntan,)))
+    teps1 = _c64(np.broadcast_to(np.asarray(teps1, dtype=np.float64), (ntan,)))
+    lam = np.ascontiguousarray(lam, dtype=np.complex128).view(np.float64)
+    xv = np.ascontiguousarray(xv, dtype=np.complex128).view(np.float64)
+    out = np.empty(2 * ntan)
+    _lib().orc_wsbm_bilinear_tangent(n, *[_p(a) for a in g], *phys.args(), _p(lam), _p(xv),
+                                     ntan, _p(tan), _p(tk1), _p(teps1), _p(out))
+    return out.view(np.complex128)
+
+
+from .gradient import (farfield_matrix, farfield_tangent, fourier_tangents,  # noqa: E402
+                       rhs_tangent, shape_loss_dense, shape_loss_grad_dense)

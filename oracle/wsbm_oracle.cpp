@@ -18,7 +18,10 @@
 //     is the one-point log correction w_i*ln(w_i/2pi) applied to each log-singular kernel
 //     and the smooth limits of D and D* (curvature term).
 //   * Proxy-circle blocks used by the proxy-surface interpolative decomposition (Sec. III,
-//     "low-rank approximations are computed via the proxy-surface method").
+//     proxy-surface low-rank approximation).
+//   * Directional derivatives of lam^T A x along tangents of the node data, k1 and eps1, by
+//     evaluating the same block definitions in dual-number arithmetic (forward mode).  The
+//     paper does not differentiate its solver; this serves the shape-gradient tests.
 //
 // Floating point: compile with -ffp-contract=off so that the geometric quantities
 // (d, r, k*r, d.n) follow exactly the operation order written below.
@@ -207,6 +210,121 @@ static void proxy_col_entries(const Geom& g, const Params& p, int64_t j, double 
     out[s][0] = wj * (0.25 * I1 * k * h.h1 * (dny / r));
     out[s][1] = -eps * wj * (0.25 * I1 * h.h0);
   }
+}
+
+// ---------------------------------------------------------------------------------------
+// Forward-mode derivatives (shape and refractive-index gradients).  A dual number carries a
+// value and its derivative along one tangent direction of the inputs (node positions,
+// normals, weights, curvatures, k1, eps1).  The blocks below are the blocks above evaluated
+// in dual arithmetic, so their derivative parts are the exact directional derivatives of
+// the same definitions.  Hankel derivatives: H0' = -H1, H1' = H0 - H1/z, and for
+// F1 = H1/z + 2i/(pi z^2):  F1' = (H0 - 2 F1)/z.
+// ---------------------------------------------------------------------------------------
+struct rd {
+  double v, t;
+};
+struct cd {
+  cplx v, t;
+};
+static inline rd R(double v) { return rd{v, 0.0}; }
+static inline rd operator+(rd a, rd b) { return rd{a.v + b.v, a.t + b.t}; }
+static inline rd operator-(rd a, rd b) { return rd{a.v - b.v, a.t - b.t}; }
+static inline rd operator*(rd a, rd b) { return rd{a.v * b.v, a.t * b.v + a.v * b.t}; }
+static inline rd operator*(double s, rd a) { return rd{s * a.v, s * a.t}; }
+static inline rd operator/(rd a, rd b) { return rd{a.v / b.v, (a.t * b.v - a.v * b.t) / (b.v * b.v)}; }
+static inline rd operator/(rd a, double s) { return rd{a.v / s, a.t / s}; }
+static inline rd dsqrt(rd a) {
+  double q = std::sqrt(a.v);
+  return rd{q, a.t / (2.0 * q)};
+}
+static inline rd dlog(rd a) { return rd{std::log(a.v), a.t / a.v}; }
+static inline cd C(cplx v) { return cd{v, cplx(0.0, 0.0)}; }
+static inline cd operator+(cd a, cd b) { return cd{a.v + b.v, a.t + b.t}; }
+static inline cd operator-(cd a, cd b) { return cd{a.v - b.v, a.t - b.t}; }
+static inline cd operator-(cd a) { return cd{-a.v, -a.t}; }
+static inline cd operator*(cd a, cd b) { return cd{a.v * b.v, a.t * b.v + a.v * b.t}; }
+static inline cd operator*(cd a, rd b) { return cd{a.v * b.v, a.t * b.v + a.v * b.t}; }
+static inline cd operator*(rd b, cd a) { return a * b; }
+static inline cd operator*(cplx s, cd a) { return cd{s * a.v, s * a.t}; }
+static inline cd operator*(double s, cd a) { return cd{s * a.v, s * a.t}; }
+static inline cd operator/(cd a, double s) { return cd{a.v / s, a.t / s}; }
+static inline cd operator+(cd a, rd b) { return cd{a.v + b.v, a.t + b.t}; }
+static inline cd operator-(cd a, rd b) { return cd{a.v - b.v, a.t - b.t}; }
+static inline cd operator+(rd b, cd a) { return a + b; }
+
+struct HankD {
+  cd h0, h1, f1;
+};
+static HankD hankel_dual(const Hank& h, rd z) {
+  HankD o;
+  o.h0 = cd{h.h0, -h.h1 * z.t};
+  o.h1 = cd{h.h1, (h.h0 - h.h1 / z.v) * z.t};
+  o.f1 = cd{h.f1, (h.h0 - 2.0 * h.f1) / z.v * z.t};
+  return o;
+}
+
+struct GeomT {  // node arrays and one tangent direction of them
+  const double *x, *y, *nx, *ny, *w, *kappa;
+  const double *tx, *ty, *tnx, *tny, *tw, *tkappa;
+};
+struct ParamsT {
+  double k0;
+  rd k1;
+  double eps0;
+  rd eps1;
+};
+
+static void pair_block_offdiag_dual(const GeomT& g, const ParamsT& p, int64_t i, int64_t j,
+                                    const Hank& ha, const Hank& hb, cd a[2][2]) {
+  const cplx I1(0.0, 1.0);
+  rd dx = rd{g.x[i], g.tx[i]} - rd{g.x[j], g.tx[j]};
+  rd dy = rd{g.y[i], g.ty[i]} - rd{g.y[j], g.ty[j]};
+  rd nxi{g.nx[i], g.tnx[i]}, nyi{g.ny[i], g.tny[i]}, nxj{g.nx[j], g.tnx[j]}, nyj{g.ny[j], g.tny[j]};
+  rd r2 = dx * dx + dy * dy;
+  rd r = dsqrt(r2);
+  rd z0 = p.k0 * r;
+  rd z1 = p.k1 * r;
+  rd dny = dx * nxj + dy * nyj;
+  rd dnx = dx * nxi + dy * nyi;
+  rd nn = nxi * nxj + nyi * nyj;
+  rd c = (dnx * dny) / r2;
+  HankD A = hankel_dual(ha, z0);
+  HankD B = hankel_dual(hb, z1);
+  cd G0 = (0.25 * I1) * A.h0;
+  cd G1 = (0.25 * I1) * B.h0;
+  cd Dy0 = (0.25 * I1 * p.k0) * (A.h1 * (dny / r));
+  cd Dy1 = (0.25 * I1) * (p.k1 * (B.h1 * (dny / r)));
+  cd Dx0 = (-0.25 * I1 * p.k0) * (A.h1 * (dnx / r));
+  cd Dx1 = (-0.25 * I1) * (p.k1 * (B.h1 * (dnx / r)));
+  double q0 = p.k0 * p.k0;
+  rd q1 = p.k1 * p.k1;
+  rd m2c = nn - 2.0 * c;
+  cd dN = (0.25 * I1) * ((q0 * A.h0 - q1 * B.h0) * c + (q0 * A.f1 - q1 * B.f1) * m2c);
+  cplx alpha = I1 / p.k0;
+  rd wj{g.w[j], g.tw[j]};
+  a[0][0] = wj * Dy1;
+  a[0][1] = -(p.eps1 * (wj * G1));
+  a[1][0] = wj * (Dy0 + alpha * dN);
+  a[1][1] = wj * ((-p.eps0) * G0 - alpha * (p.eps0 * Dx0 - p.eps1 * Dx1));
+}
+
+static void pair_block_diag_dual(const GeomT& g, const ParamsT& p, int64_t i, cd a[2][2]) {
+  const cplx I1(0.0, 1.0);
+  rd wi{g.w[i], g.tw[i]};
+  rd kap{g.kappa[i], g.tkappa[i]};
+  auto S = [&](rd k) {
+    return wi * (C(0.25 * I1) - (R(EULER_GAMMA) + dlog(k * wi / (4.0 * PI))) / (2.0 * PI));
+  };
+  auto f = [&](rd k) { return k * k * (dlog(k * wi / (4.0 * PI)) + R(EULER_GAMMA - 0.5)); };
+  rd k0 = R(p.k0);
+  rd Dd = -1.0 * (wi * kap) / (4.0 * PI);
+  cd dN = wi * (C(I1 / 8.0) * (k0 * k0 - p.k1 * p.k1) - C(cplx(1.0, 0.0)) * ((f(k0) - f(p.k1)) / (4.0 * PI)));
+  cplx alpha = I1 / p.k0;
+  a[0][0] = C(cplx(0.5, 0.0)) + Dd;
+  a[0][1] = -(p.eps1 * S(p.k1));
+  a[1][0] = C(cplx(-0.5, 0.0)) + Dd + alpha * dN;
+  a[1][1] = (-p.eps0) * S(k0) - alpha * (C(cplx(1.0, 0.0)) * ((R(p.eps0) - p.eps1) * Dd)) -
+            alpha * (C(cplx(0.5, 0.0)) * (R(p.eps0) + p.eps1));
 }
 
 extern "C" {
@@ -404,6 +522,58 @@ int orc_proxy_col_block(int64_t n, const double* x, const double* y, const doubl
         out[2 * (cc * ldo + rr) + 1] = e[s][b].imag();
       }
     }
+  }
+  return 0;
+}
+
+
+// Directional derivatives of the bilinear form lam^T A x along ntan tangent directions of the
+// inputs: out[t] = sum_{r,c} lam_r (dA_rc / ds_t) x_c (complex), paper order for lam (equation
+// index) and x (unknown index), both complex128 of length 2N.  tan: ntan x 6 x N doubles, the
+// tangent of (x, y, nx, ny, w, kappa); tk1, teps1: ntan tangents of k1 and eps1.
+int orc_wsbm_bilinear_tangent(int64_t n, const double* x, const double* y, const double* nx,
+                              const double* ny, const double* w, const double* kappa, double k0,
+                              double k1, double eps0, double eps1, const double* lam,
+                              const double* xv, int64_t ntan, const double* tan,
+                              const double* tk1, const double* teps1, double* out) {
+  const cplx* L = reinterpret_cast<const cplx*>(lam);
+  const cplx* X = reinterpret_cast<const cplx*>(xv);
+  std::vector<cplx> acc((size_t)ntan, cplx(0.0, 0.0));
+#pragma omp parallel
+  {
+    std::vector<cplx> mine((size_t)ntan, cplx(0.0, 0.0));
+#pragma omp for schedule(dynamic, 1)
+    for (int64_t i = 0; i < n; ++i) {
+      for (int64_t j = 0; j < n; ++j) {
+        Hank ha{}, hb{};
+        if (i != j) {
+          double dx = x[i] - x[j], dy = y[i] - y[j];
+          double r = std::sqrt(dx * dx + dy * dy);
+          ha = hankel_eval(k0 * r);
+          hb = hankel_eval(k1 * r);
+        }
+        for (int64_t t = 0; t < ntan; ++t) {
+          const double* tv = tan + t * 6 * n;
+          GeomT g{x, y, nx, ny, w, kappa, tv, tv + n, tv + 2 * n, tv + 3 * n, tv + 4 * n, tv + 5 * n};
+          ParamsT p{k0, rd{k1, tk1[t]}, eps0, rd{eps1, teps1[t]}};
+          cd blk[2][2];
+          if (i == j)
+            pair_block_diag_dual(g, p, i, blk);
+          else
+            pair_block_offdiag_dual(g, p, i, j, ha, hb, blk);
+          cplx s(0.0, 0.0);
+          for (int a = 0; a < 2; ++a)
+            for (int b = 0; b < 2; ++b) s += L[a * n + i] * blk[a][b].t * X[b * n + j];
+          mine[t] += s;
+        }
+      }
+    }
+#pragma omp critical
+    for (int64_t t = 0; t < ntan; ++t) acc[t] += mine[t];
+  }
+  for (int64_t t = 0; t < ntan; ++t) {
+    out[2 * t] = acc[t].real();
+    out[2 * t + 1] = acc[t].imag();
   }
   return 0;
 }
