@@ -183,6 +183,13 @@ int wsbm_rhs_planewave(wsbm_hss_t h, const double* angles, int32_t nang, void* r
  * u, q: device complex128 N x nrhs each.  Errors: NOT_FACTORED, OOM, CUDA. */
 int wsbm_solve(wsbm_hss_t h, const void* rhs, int32_t nrhs, void* u, void* q);
 
+/* Transposed solve A^T lam = rhs with the same factors (the adjoint solve of a gradient).
+ * rhs: device complex128 2N x nrhs indexed like the unknowns [u; q] (paper order); lam1, lam2:
+ * device complex128 N x nrhs each, the multipliers of the first and second equations.
+ * The paper has no counterpart (it does not differentiate its solver).  Errors: as
+ * wsbm_solve. */
+int wsbm_solve_transposed(wsbm_hss_t h, const void* rhs, int32_t nrhs, void* lam1, void* lam2);
+
 /* Far-field pattern of the scattered field at nang observation angles:
  * u_inf(a) = e^{i pi/4}/sqrt(8 pi k0) sum_j w_j [-i k0 (xh.n_j) u_j - eps0 q_j] e^{-i k0 xh.x_j}.
  * u, q: device complex128 N x nrhs; angles: device doubles; out: device complex128
@@ -237,6 +244,46 @@ int wsbm_batch_handle(wsbm_batch_t b, int32_t i, wsbm_hss_t* out);
 int wsbm_batch_stats(wsbm_batch_t b, wsbm_stats_t* s);
 
 void wsbm_batch_destroy(wsbm_batch_t b);
+
+/* ---------------------------------------------------------------- gradients ----
+ * Reverse-mode building blocks of shape and refractive-index gradients of a far-field loss
+ * (no counterpart in the paper, which does not differentiate its solver).  With the solution x
+ * of A x = b and multipliers lam of A^T lam = v:
+ *   dL/ds = Re(conj(gF) . dF/ds) + Re(lam^T db/ds) - Re(lam^T (dA/ds) x)
+ * for every input s.  Node gradients are device doubles laid out as six N-blocks
+ * [x | y | nx | ny | w | kappa]; outputs are overwritten; all calls are asynchronous on
+ * `stream` (a cudaStream_t, NULL = default stream).  Errors: INVALID_ARG, OOM, CUDA. */
+
+/* grad = Re(lam^T (dA/ds) x) for every node input s of the Nystrom matrix of eq. (weakly_bm)
+ * (dense: every node pair, O(N^2) work), gphys[0] = Re(lam^T (dA/dk1) x),
+ * gphys[1] = Re(lam^T (dA/deps1) x).  lam, x: device complex128 2N (paper order: lam by
+ * equation, x by unknown).  Scratch: about 6 N x (2 .. 8 waves of CTAs) doubles from
+ * cudaMallocAsync on `stream`. */
+int wsbm_entries_vjp(const wsbm_geom* g, const wsbm_params* p, const void* lam, const void* x,
+                     double* grad, double* gphys, void* stream);
+
+/* grad = Re(sum_a lam_a^T db_a/ds) for plane-wave right-hand sides at nang angles (device
+ * doubles); lam: device complex128 2N x nang (paper order).  Only x, y, nx, ny are nonzero. */
+int wsbm_rhs_planewave_vjp(const wsbm_geom* g, const wsbm_params* p, const double* angles,
+                           int32_t nang, const void* lam, double* grad, void* stream);
+
+/* For far fields F = C [u; q] (the formula of wsbm_farfield) and gF = dL/dRe F + i dL/dIm F
+ * (device complex128 nang x nrhs): v = C^T conj(gF) (device complex128 2N x nrhs, paper order)
+ * and grad = Re(sum conj(gF) dF/ds) at fixed u, q (device complex128 N x nrhs each). */
+int wsbm_farfield_vjp(const wsbm_geom* g, const wsbm_params* p, const void* u, const void* q,
+                      int32_t nrhs, const double* angles, int32_t nang, const void* gF, void* v,
+                      double* grad, void* stream);
+
+/* Nodes of the curve r(t) = 1 + sum_{j=1..M} a_j cos(jt) + b_j sin(jt), gamma = r (cos t, sin t),
+ * at t_i = 2 pi i / N: positions, outward unit normals, trapezoidal weights (2 pi/N)|gamma'|
+ * and curvature.  a, b: device M doubles; outputs: device N doubles each. */
+int wsbm_curve_fourier(int32_t M, int64_t N, const double* a, const double* b, double* x,
+                       double* y, double* nx, double* ny, double* w, double* kappa, void* stream);
+
+/* gcoef (device, 2M doubles: a_1..a_M, b_1..b_M) = the coefficient gradient of a loss whose
+ * node gradient (six N-blocks as above) is grad. */
+int wsbm_curve_fourier_vjp(int32_t M, int64_t N, const double* a, const double* b,
+                           const double* grad, double* gcoef, void* stream);
 
 /* Static name of an error code. */
 const char* wsbm_strerror(int code);

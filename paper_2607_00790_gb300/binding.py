@@ -93,6 +93,16 @@ def lib():
         L.wsbm_batch_stats.argtypes = [vp, ctypes.POINTER(Stats)]
         L.wsbm_batch_destroy.argtypes = [vp]
         L.wsbm_batch_destroy.restype = None
+        G, P = ctypes.POINTER(Geom), ctypes.POINTER(Params)
+        L.wsbm_solve_transposed.argtypes = [vp, vp, i32, vp, vp]
+        L.wsbm_entries_vjp.argtypes = [G, P, vp, vp, vp, vp, vp]
+        L.wsbm_rhs_planewave_vjp.argtypes = [G, P, vp, i32, vp, vp, vp]
+        L.wsbm_farfield_vjp.argtypes = [G, P, vp, vp, i32, vp, i32, vp, vp, vp, vp]
+        L.wsbm_curve_fourier.argtypes = [i32, i64, vp, vp, vp, vp, vp, vp, vp, vp, vp]
+        L.wsbm_curve_fourier_vjp.argtypes = [i32, i64, vp, vp, vp, vp, vp]
+        for f in ("wsbm_solve_transposed", "wsbm_entries_vjp", "wsbm_rhs_planewave_vjp",
+                  "wsbm_farfield_vjp", "wsbm_curve_fourier", "wsbm_curve_fourier_vjp"):
+            getattr(L, f).restype = ctypes.c_int
         L.wsbm_strerror.argtypes = [ctypes.c_int]
         L.wsbm_strerror.restype = ctypes.c_char_p
         for f in ("wsbm_hankel01", "wsbm_entries_raw", "wsbm_proxy_block", "wsbm_create",
@@ -163,6 +173,78 @@ def wsbm_proxy_block(geom, params, side, idx, circle, P):
     return out.T
 
 
+# ------------------------------------------------------------------- gradients ----
+def entries_vjp(geom, params, lam, x):
+    """(Re(lam^T dA/ds x) for the six node arrays as a (6, N) tensor, [d/dk1, d/deps1]);
+    lam, x: complex128 vectors of length 2N (paper order)."""
+    dev = lam.device
+    N = geom.n
+    grad = torch.empty((6, N), dtype=torch.float64, device=dev)
+    gphys = torch.empty(2, dtype=torch.float64, device=dev)
+    _check(lib().wsbm_entries_vjp(ctypes.byref(geom), ctypes.byref(params),
+                                  _dev(lam, torch.complex128), _dev(x, torch.complex128),
+                                  _dev(grad, torch.float64), _dev(gphys, torch.float64),
+                                  _stream(dev)), "wsbm_entries_vjp")
+    return grad, gphys
+
+
+def rhs_planewave_vjp(geom, params, angles, lam):
+    """Re(sum_a lam_a^T db_a/ds) as (6, N); lam: 2N x nang complex128."""
+    dev = lam.device
+    lc = lam.T.contiguous()
+    grad = torch.empty((6, geom.n), dtype=torch.float64, device=dev)
+    _check(lib().wsbm_rhs_planewave_vjp(ctypes.byref(geom), ctypes.byref(params),
+                                        _dev(angles, torch.float64), angles.numel(),
+                                        _dev(lc, torch.complex128), _dev(grad, torch.float64),
+                                        _stream(dev)), "wsbm_rhs_planewave_vjp")
+    return grad
+
+
+def farfield_vjp(geom, params, u, q, angles, gF):
+    """(v = C^T conj(gF) as 2N x nrhs, explicit node gradient (6, N)); u, q: N x nrhs,
+    gF: nang x nrhs (complex128)."""
+    dev = u.device
+    nrhs = u.shape[1]
+    uc, qc, gc = u.T.contiguous(), q.T.contiguous(), gF.T.contiguous()
+    v = torch.empty((nrhs, 2 * geom.n), dtype=torch.complex128, device=dev)
+    grad = torch.empty((6, geom.n), dtype=torch.float64, device=dev)
+    _check(lib().wsbm_farfield_vjp(ctypes.byref(geom), ctypes.byref(params),
+                                   _dev(uc, torch.complex128), _dev(qc, torch.complex128), nrhs,
+                                   _dev(angles, torch.float64), angles.numel(),
+                                   _dev(gc, torch.complex128), _dev(v, torch.complex128),
+                                   _dev(grad, torch.float64), _stream(dev)), "wsbm_farfield_vjp")
+    return v.T, grad
+
+
+def curve_fourier(a, b, N):
+    """Node arrays (x, y, nx, ny, w, kappa) of r(t) = 1 + sum a_j cos jt + b_j sin jt."""
+    dev = a.device
+    out = torch.empty((6, N), dtype=torch.float64, device=dev)
+    ptrs = [ctypes.c_void_p(out[k].data_ptr()) for k in range(6)]
+    _check(lib().wsbm_curve_fourier(a.numel(), N, _dev(a, torch.float64), _dev(b, torch.float64),
+                                    *ptrs, _stream(dev)), "wsbm_curve_fourier")
+    return out
+
+
+def curve_fourier_vjp(a, b, N, grad):
+    """Coefficient gradient (a_1..a_M, b_1..b_M) from a (6, N) node gradient."""
+    dev = a.device
+    out = torch.empty(2 * a.numel(), dtype=torch.float64, device=dev)
+    g = grad.contiguous()
+    _check(lib().wsbm_curve_fourier_vjp(a.numel(), N, _dev(a, torch.float64),
+                                        _dev(b, torch.float64), _dev(g, torch.float64),
+                                        _dev(out, torch.float64), _stream(dev)),
+           "wsbm_curve_fourier_vjp")
+    return out
+
+
+def geom_from_tensors(x, y, nx, ny, w, kappa):
+    ts = [t.contiguous() for t in (x, y, nx, ny, w, kappa)]
+    for t in ts:
+        _dev(t, torch.float64)
+    return Geom(ts[0].numel(), *[t.data_ptr() for t in ts]), ts
+
+
 # --------------------------------------------------------------------- HSS handle ----
 class Solver:
     """wsbm_create / wsbm_factor / wsbm_solve / wsbm_farfield on one handle."""
@@ -196,6 +278,18 @@ class Solver:
         _check(lib().wsbm_solve(self.h, _dev(rhs_c, torch.complex128), nrhs,
                                 _dev(u, torch.complex128), _dev(q, torch.complex128)), "wsbm_solve")
         return u.T, q.T
+
+    def solve_transposed(self, v):
+        """A^T lam = v (v: 2N x nrhs indexed like the unknowns); returns the multipliers of
+        the first and second equations, N x nrhs each."""
+        vc = v.T.contiguous()
+        nrhs = v.shape[1]
+        l1 = torch.empty((nrhs, self.n), dtype=torch.complex128, device=self.device)
+        l2 = torch.empty((nrhs, self.n), dtype=torch.complex128, device=self.device)
+        _check(lib().wsbm_solve_transposed(self.h, _dev(vc, torch.complex128), nrhs,
+                                           _dev(l1, torch.complex128), _dev(l2, torch.complex128)),
+               "wsbm_solve_transposed")
+        return l1.T, l2.T
 
     def farfield(self, u, q, angles):
         uc, qc = u.T.contiguous(), q.T.contiguous()

@@ -30,6 +30,7 @@ __device__ __forceinline__ double cabs2(double2 a) { return a.x * a.x + a.y * a.
 
 // --------------------------------------------------------------------------- GEMM ----
 // C[m x n] = alpha * A[m x k] * B[k x n] + beta * C, one GT x GT tile of C.
+template <bool TA>
 __device__ void gemm_tile(int m, int n, int k, const double2* __restrict__ A, int64_t lda,
                           const double2* __restrict__ B, int64_t ldb, double2* C, int64_t ldc,
                           double2 alpha, double2 beta, int tm, int tn) {
@@ -47,7 +48,8 @@ __device__ void gemm_tile(int m, int n, int k, const double2* __restrict__ A, in
     for (int t = threadIdx.x; t < GK * GT; t += blockDim.x) {
       int r = t % GT, c = t / GT;  // A: row r of the tile, k index c
       int gi = i0 + r, gk = kk + c;
-      sA[c][r] = (gi < m && gk < k) ? A[gi + (int64_t)gk * lda] : make_double2(0.0, 0.0);
+      sA[c][r] = (gi < m && gk < k) ? A[TA ? gk + (int64_t)gi * lda : gi + (int64_t)gk * lda]
+                                    : make_double2(0.0, 0.0);
       int br = t % GK, bc = t / GK;  // B: k index br, column bc
       int gk2 = kk + br, gj = j0 + bc;
       sB[br][bc] = (gk2 < k && gj < n) ? B[gk2 + (int64_t)gj * ldb] : make_double2(0.0, 0.0);
@@ -80,8 +82,12 @@ __device__ void gemm_tile(int m, int n, int k, const double2* __restrict__ A, in
 __global__ void __launch_bounds__(256) k_gemm(const GemmDesc* __restrict__ d, int nbatch) {
   const GemmDesc g = d[blockIdx.y];
   int ntm = (g.m + GT - 1) / GT, ntn = (g.n + GT - 1) / GT;
-  for (int t = blockIdx.x; t < ntm * ntn; t += gridDim.x)
-    gemm_tile(g.m, g.n, g.k, g.A, g.lda, g.B, g.ldb, g.C, g.ldc, g.alpha, g.beta, t % ntm, t / ntm);
+  for (int t = blockIdx.x; t < ntm * ntn; t += gridDim.x) {
+    if (g.ta)
+      gemm_tile<true>(g.m, g.n, g.k, g.A, g.lda, g.B, g.ldb, g.C, g.ldc, g.alpha, g.beta, t % ntm, t / ntm);
+    else
+      gemm_tile<false>(g.m, g.n, g.k, g.A, g.lda, g.B, g.ldb, g.C, g.ldc, g.alpha, g.beta, t % ntm, t / ntm);
+  }
 }
 
 // LU trailing update at panel j0 (width jb): A22 -= A21 * A12.
@@ -94,7 +100,7 @@ __global__ void __launch_bounds__(256) k_lu_update(const LuDesc* __restrict__ d,
   const double2 one = make_double2(1.0, 0.0), mone = make_double2(-1.0, 0.0);
   int kb = min(jb, q.n - j0);
   for (int t = blockIdx.x; t < nt * nt; t += gridDim.x)
-    gemm_tile(m, m, kb, q.A + e + (int64_t)j0 * q.lda, q.lda, q.A + j0 + (int64_t)e * q.lda, q.lda,
+    gemm_tile<false>(m, m, kb, q.A + e + (int64_t)j0 * q.lda, q.lda, q.A + j0 + (int64_t)e * q.lda, q.lda,
               q.A + e + (int64_t)e * q.lda, q.lda, mone, one, t % nt, t / nt);
 }
 
@@ -205,23 +211,25 @@ __global__ void k_lu_trsm_row(const LuDesc* __restrict__ d, int j0, int jb) {
 // ------------------------------------------------------------- triangular solves ----
 // B <- op(T)^-1 B for a diagonal block [j0, j0+jb) of T (lower unit or upper non-unit),
 // RHS columns in parallel.
-__global__ void k_trsm_diag(const TrsmDesc* __restrict__ d, int j0, int jb, int lower) {
+__global__ void k_trsm_diag(const TrsmDesc* __restrict__ d, int j0, int jb, int fwd) {
   const TrsmDesc q = d[blockIdx.y];
   if (j0 >= q.n) return;
   const int je = min(j0 + jb, q.n);
+  const bool unit = (fwd != 0) != (q.trans != 0);  // L and L^T have a unit diagonal
+  const int64_t si = q.trans ? q.ldt : 1, st = q.trans ? 1 : q.ldt;  // op(T)(i,t) = T[i*si + t*st]
   for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < q.nrhs; c += gridDim.x * blockDim.x) {
     double2* col = q.B + (int64_t)c * q.ldb;
-    if (lower) {
-      for (int i = j0 + 1; i < je; ++i) {
+    if (fwd) {
+      for (int i = j0; i < je; ++i) {
         double2 s = col[i];
-        for (int t = j0; t < i; ++t) s = cfms(q.T[i + (int64_t)t * q.ldt], col[t], s);
-        col[i] = s;
+        for (int t = j0; t < i; ++t) s = cfms(q.T[i * si + t * st], col[t], s);
+        col[i] = unit ? s : cdiv(s, q.T[i * si + i * st]);
       }
     } else {
       for (int i = je - 1; i >= j0; --i) {
         double2 s = col[i];
-        for (int t = i + 1; t < je; ++t) s = cfms(q.T[i + (int64_t)t * q.ldt], col[t], s);
-        col[i] = cdiv(s, q.T[i + (int64_t)i * q.ldt]);
+        for (int t = i + 1; t < je; ++t) s = cfms(q.T[i * si + t * st], col[t], s);
+        col[i] = unit ? s : cdiv(s, q.T[i * si + i * st]);
       }
     }
   }
@@ -239,9 +247,14 @@ __global__ void __launch_bounds__(256) k_trsm_update(const TrsmDesc* __restrict_
   int r0 = lower ? je : 0;
   int ntm = (m + GT - 1) / GT, ntn = (q.nrhs + GT - 1) / GT;
   const double2 one = make_double2(1.0, 0.0), mone = make_double2(-1.0, 0.0);
-  for (int t = blockIdx.x; t < ntm * ntn; t += gridDim.x)
-    gemm_tile(m, q.nrhs, je - j0, q.T + r0 + (int64_t)j0 * q.ldt, q.ldt, q.B + j0, q.ldb, q.B + r0,
-              q.ldb, mone, one, t % ntm, t / ntm);
+  for (int t = blockIdx.x; t < ntm * ntn; t += gridDim.x) {
+    if (q.trans)  // op(T)[r0.., j0..je) = (T[j0..je, r0..])^T
+      gemm_tile<true>(m, q.nrhs, je - j0, q.T + j0 + (int64_t)r0 * q.ldt, q.ldt, q.B + j0, q.ldb,
+                      q.B + r0, q.ldb, mone, one, t % ntm, t / ntm);
+    else
+      gemm_tile<false>(m, q.nrhs, je - j0, q.T + r0 + (int64_t)j0 * q.ldt, q.ldt, q.B + j0, q.ldb,
+                       q.B + r0, q.ldb, mone, one, t % ntm, t / ntm);
+  }
 }
 
 // Apply the LU row interchanges to B (forward order).
@@ -250,6 +263,22 @@ __global__ void k_apply_piv(const TrsmDesc* __restrict__ d) {
   for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < q.nrhs; c += gridDim.x * blockDim.x) {
     double2* col = q.B + (int64_t)c * q.ldb;
     for (int j = 0; j < q.n; ++j) {
+      int p = q.piv[j];
+      if (p != j) {
+        double2 t = col[j];
+        col[j] = col[p];
+        col[p] = t;
+      }
+    }
+  }
+}
+
+// Undo the LU row interchanges (reverse order): B <- P^T B.
+__global__ void k_apply_piv_inv(const TrsmDesc* __restrict__ d) {
+  const TrsmDesc q = d[blockIdx.y];
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < q.nrhs; c += gridDim.x * blockDim.x) {
+    double2* col = q.B + (int64_t)c * q.ldb;
+    for (int j = q.n - 1; j >= 0; --j) {
       int p = q.piv[j];
       if (p != j) {
         double2 t = col[j];
@@ -530,6 +559,19 @@ int wsbm_cpqr_batched(const QrDesc* d_desc, int nbatch, int mode, cudaStream_t s
 int wsbm_cpqr_finish(const QrDesc* d_desc, int nbatch, cudaStream_t st) {
   if (nbatch <= 0) return 0;
   k_cpqr_finish<<<nbatch, 128, 0, st>>>(d_desc);
+  wsbm_count_launch();
+  return cudaGetLastError() == cudaSuccess ? 0 : -3;
+}
+
+int wsbm_lu_solve_t_batched(const TrsmDesc* d_desc, int nbatch, int max_n, int max_nrhs,
+                            cudaStream_t st) {
+  if (nbatch <= 0) return 0;
+  int rc = wsbm_trsm_batched(d_desc, nbatch, max_n, max_nrhs, 1, st);  // U^T, forward
+  if (rc) return rc;
+  rc = wsbm_trsm_batched(d_desc, nbatch, max_n, max_nrhs, 0, st);  // L^T, backward
+  if (rc) return rc;
+  dim3 gd(tiles_x((max_nrhs + 127) / 128), nbatch);
+  k_apply_piv_inv<<<gd, 128, 0, st>>>(d_desc);
   wsbm_count_launch();
   return cudaGetLastError() == cudaSuccess ? 0 : -3;
 }

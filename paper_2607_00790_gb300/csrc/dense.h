@@ -9,13 +9,14 @@
 void wsbm_count_launch();
 int64_t wsbm_launch_count();
 
-// C = alpha * A * B + beta * C  (column-major, A m x k, B k x n, C m x n)
+// C = alpha * op(A) * B + beta * C  (column-major, op(A) m x k, B k x n, C m x n);
+// op(A) = A (ta = 0, A stored m x k) or A^T (ta = 1, A stored k x m).
 struct GemmDesc {
   const double2* A;
   const double2* B;
   double2* C;
   int64_t lda, ldb, ldc;
-  int32_t m, n, k, pad;
+  int32_t m, n, k, ta;
   double2 alpha, beta;
 };
 
@@ -27,8 +28,9 @@ struct LuDesc {
   int32_t n, pad;
 };
 
-// B (n x nrhs) <- T^-1 B with T n x n triangular (lower unit or upper non-unit);
-// piv: LU row interchanges applied to B by the LU solve.
+// B (n x nrhs) <- op(T)^-1 B with T n x n holding an LU factor (unit lower L below the
+// diagonal, non-unit upper U on and above it); piv: the LU row interchanges.  trans = 0 solves
+// with L (forward) and U (backward); trans = 1 with U^T (forward) and L^T (backward).
 struct TrsmDesc {
   const double2* T;
   int64_t ldt;
@@ -36,6 +38,7 @@ struct TrsmDesc {
   int64_t ldb;
   const int32_t* piv;
   int32_t n, nrhs;
+  int32_t trans, pad;
 };
 
 // Column-pivoted QR state of an m x n matrix.  state[0] = next step (0 for a fresh matrix),
@@ -63,5 +66,9 @@ int wsbm_trsm_batched(const TrsmDesc* d_desc, int nbatch, int max_n, int max_nrh
                       cudaStream_t st);
 int wsbm_lu_solve_batched(const TrsmDesc* d_desc_lower, const TrsmDesc* d_desc_upper, int nbatch,
                           int max_n, int max_nrhs, cudaStream_t st);
+// B <- D^-T B for LU-factored D (descriptors with trans = 1): U^T, then L^T, then the row
+// interchanges undone in reverse order.
+int wsbm_lu_solve_t_batched(const TrsmDesc* d_desc, int nbatch, int max_n, int max_nrhs,
+                            cudaStream_t st);
 int wsbm_cpqr_batched(const QrDesc* d_desc, int nbatch, int mode, cudaStream_t st);
 int wsbm_cpqr_finish(const QrDesc* d_desc, int nbatch, cudaStream_t st);

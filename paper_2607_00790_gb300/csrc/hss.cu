@@ -143,6 +143,20 @@ __global__ void k_gather_rows(const GatherDesc* __restrict__ d) {
   }
 }
 
+// out[perm[t], c] -= in[t, c]: applies R^T = Pi^T [I; Tc^T] after its dense part (the
+// column-ID permutation is a bijection, so no two threads touch the same row).
+__global__ void k_scatter_sub_rows(const GatherDesc* __restrict__ d) {
+  const GatherDesc q = d[blockIdx.y];
+  int64_t tot = (int64_t)q.n * q.ncol;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    int t = (int)(e % q.n), c = (int)(e / q.n);
+    double2* o = q.out + q.perm[t] + (int64_t)c * q.ldo;
+    double2 v = q.in[t + (int64_t)c * q.ldi];
+    *o = make_double2(o->x - v.x, o->y - v.y);
+  }
+}
+
 // 2D copy (n rows, ncol columns) between strided matrices, batched.
 struct CopyDesc {
   double2* dst;
@@ -1614,6 +1628,241 @@ extern "C" int wsbm_solve(wsbm_hss_t h, const void* rhs, int32_t nrhs, void* u, 
     k_copy2d<<<dim3(gridfor((int64_t)maxn * nrhs), (unsigned)c.size()), 256, 0, st>>>(dc);
     wsbm_count_launch();
     k_split_uq<<<gridfor(N * nrhs), 256, 0, st>>>(bint, (double2*)u, (double2*)q, N, nrhs);
+    wsbm_count_launch();
+  }
+  HC(cudaGetLastError());
+  HC(cudaStreamSynchronize(st));
+  free_list(h, tmp);
+  return WSBM_OK;
+}
+
+// Transposed solve A^T lam = v with the same factors.  For A ~ D + L A~ R (per level) the
+// transpose has the same form with L <-> R^T, so with Z = D^-1 L and Dhat = (R D^-1 L)^-1:
+//   up    s = Z^T v (= L^T D^-T v),  bt = Dhat^T s;   root: transposed LU solve;
+//   down  lam = D^-T (v - R^T (bt - Dhat^T y)),  R^T = Pi^T [I; Tc^T].
+static GemmDesc gemm_t(const double2* A, int64_t lda, const double2* B, int64_t ldb, double2* C,
+                       int64_t ldc, int m, int n, int k, double alpha, double beta) {
+  GemmDesc g;
+  memset(&g, 0, sizeof(g));
+  g.A = A;
+  g.lda = lda;
+  g.B = B;
+  g.ldb = ldb;
+  g.C = C;
+  g.ldc = ldc;
+  g.m = m;
+  g.n = n;
+  g.k = k;
+  g.ta = 1;
+  g.alpha = make_double2(alpha, 0.0);
+  g.beta = make_double2(beta, 0.0);
+  return g;
+}
+
+static TrsmDesc lu_t(const double2* T, int64_t ldt, double2* B, int64_t ldb, const int32_t* piv,
+                     int n, int nrhs) {
+  TrsmDesc t;
+  memset(&t, 0, sizeof(t));
+  t.T = T;
+  t.ldt = ldt;
+  t.B = B;
+  t.ldb = ldb;
+  t.piv = piv;
+  t.n = n;
+  t.nrhs = nrhs;
+  t.trans = 1;
+  return t;
+}
+
+extern "C" int wsbm_solve_transposed(wsbm_hss_t h, const void* rhs, int32_t nrhs, void* lam1,
+                                     void* lam2) {
+  if (!h) return WSBM_ERR_INVALID_ARG;
+  if (!h->factored) return WSBM_ERR_NOT_FACTORED;
+  if (nrhs < 0 || (nrhs > 0 && (!rhs || !lam1 || !lam2))) return WSBM_ERR_INVALID_ARG;
+  if (nrhs == 0) return WSBM_OK;
+  cudaStream_t st = h->st;
+  std::vector<void*> tmp;
+  const int64_t N = h->N;
+  double2* bint = nullptr;
+  HK(dalloc(h, (size_t)2 * N * nrhs * sizeof(double2), (void**)&bint, tmp));
+  k_to_interleaved<<<gridfor(2 * N * nrhs), 256, 0, st>>>((const double2*)rhs, bint, N, nrhs);
+  wsbm_count_launch();
+  if (h->L == 0) {
+    std::vector<TrsmDesc> v(1, lu_t(h->root, h->root_n, bint, 2 * N, h->root_piv, h->root_n, nrhs));
+    TrsmDesc* dt = nullptr;
+    HK(upload(h, v, &dt, tmp));
+    HK(wsbm_lu_solve_t_batched(dt, 1, h->root_n, nrhs, st));
+    k_split_uq<<<gridfor(N * nrhs), 256, 0, st>>>(bint, (double2*)lam1, (double2*)lam2, N, nrhs);
+    wsbm_count_launch();
+    HC(cudaStreamSynchronize(st));
+    free_list(h, tmp);
+    return WSBM_OK;
+  }
+  const int L = h->L, top = h->top;
+  std::vector<std::vector<double2*>> V(L + 1), BT(L + 1);
+  int maxn = 0, maxk = 0;
+  for (int l = L; l >= top; --l) {
+    Level& LV = h->lv[l];
+    int nb = (int)LV.box.size();
+    V[l].resize(nb);
+    BT[l].resize(nb);
+    size_t tn = 0, tk = 0;
+    for (auto& b : LV.box) {
+      tn += b.n;
+      tk += b.k;
+      maxn = std::max(maxn, b.n);
+      maxk = std::max(maxk, b.k);
+    }
+    double2 *v = nullptr, *bt = nullptr;
+    HK(dalloc(h, tn * nrhs * sizeof(double2), (void**)&v, tmp));
+    HK(dalloc(h, tk * nrhs * sizeof(double2), (void**)&bt, tmp));
+    size_t on = 0, ok = 0;
+    for (int b = 0; b < nb; ++b) {
+      V[l][b] = v + on * nrhs;
+      BT[l][b] = bt + ok * nrhs;
+      on += LV.box[b].n;
+      ok += LV.box[b].k;
+    }
+  }
+  // ---- upward sweep: v = leaf rows or the children's bt;  s = Z^T v;  bt = Dhat^T s
+  for (int l = L; l >= top; --l) {
+    Level& LV = h->lv[l];
+    int nb = (int)LV.box.size();
+    std::vector<CopyDesc> c1;
+    std::vector<GemmDesc> g1, g2;
+    size_t tk = 0;
+    int lk = 0;
+    for (auto& b : LV.box) {
+      tk += b.k;
+      lk = std::max(lk, b.k);
+    }
+    double2* sbuf = nullptr;
+    HK(dalloc(h, tk * nrhs * sizeof(double2), (void**)&sbuf, tmp));
+    size_t ok = 0;
+    for (int b = 0; b < nb; ++b) {
+      Box& B = LV.box[b];
+      if (l == L) {
+        c1.push_back({V[l][b], bint + 2 * B.lo, B.n, 2 * N, B.n, nrhs});
+      } else {
+        Box& A1 = h->lv[l + 1].box[2 * b];
+        Box& A2 = h->lv[l + 1].box[2 * b + 1];
+        c1.push_back({V[l][b], BT[l + 1][2 * b], B.n, A1.k, A1.k, nrhs});
+        c1.push_back({V[l][b] + A1.k, BT[l + 1][2 * b + 1], B.n, A2.k, A2.k, nrhs});
+      }
+      double2* sb = sbuf + ok * nrhs;
+      ok += B.k;
+      g1.push_back(gemm_t(B.Z, B.n, V[l][b], B.n, sb, B.k, B.k, nrhs, B.n, 1.0, 0.0));
+      g2.push_back(gemm_t(B.Dc, B.k, sb, B.k, BT[l][b], B.k, B.k, nrhs, B.k, 1.0, 0.0));
+    }
+    CopyDesc* d1 = nullptr;
+    GemmDesc *dg1 = nullptr, *dg2 = nullptr;
+    HK(upload(h, c1, &d1, tmp));
+    HK(upload(h, g1, &dg1, tmp));
+    HK(upload(h, g2, &dg2, tmp));
+    k_copy2d<<<dim3(gridfor((int64_t)maxn * nrhs), (unsigned)c1.size()), 256, 0, st>>>(d1);
+    wsbm_count_launch();
+    HK(wsbm_gemm_batched(dg1, nb, lk, nrhs, st));
+    HK(wsbm_gemm_batched(dg2, nb, lk, nrhs, st));
+  }
+  // ---- root: transposed LU solve of the merged skeleton system
+  double2* y = nullptr;
+  HK(dalloc(h, (size_t)h->root_n * nrhs * sizeof(double2), (void**)&y, tmp));
+  {
+    Level& T = h->lv[top];
+    std::vector<CopyDesc> c;
+    int off = 0;
+    for (int b = 0; b < (int)T.box.size(); ++b) {
+      c.push_back({y + off, BT[top][b], h->root_n, T.box[b].k, T.box[b].k, nrhs});
+      off += T.box[b].k;
+    }
+    CopyDesc* dc = nullptr;
+    HK(upload(h, c, &dc, tmp));
+    k_copy2d<<<dim3(gridfor((int64_t)maxk * nrhs), (unsigned)c.size()), 256, 0, st>>>(dc);
+    wsbm_count_launch();
+    std::vector<TrsmDesc> v(1, lu_t(h->root, h->root_n, y, h->root_n, h->root_piv, h->root_n, nrhs));
+    TrsmDesc* dt = nullptr;
+    HK(upload(h, v, &dt, tmp));
+    HK(wsbm_lu_solve_t_batched(dt, 1, h->root_n, nrhs, st));
+  }
+  // ---- downward sweep: t = bt - Dhat^T y;  v -= R^T t;  lam = D^-T v  (in place in V)
+  for (int l = top; l <= L; ++l) {
+    Level& LV = h->lv[l];
+    int nb = (int)LV.box.size();
+    size_t tk = 0, tn = 0;
+    int lk = 0, ln = 0, lr = 0;
+    for (auto& b : LV.box) {
+      tk += b.k;
+      tn += b.n;
+      lk = std::max(lk, b.k);
+      ln = std::max(ln, b.n);
+      lr = std::max(lr, b.n - b.k);
+    }
+    double2 *tb = nullptr, *ub = nullptr;
+    HK(dalloc(h, tk * nrhs * sizeof(double2), (void**)&tb, tmp));
+    HK(dalloc(h, tn * nrhs * sizeof(double2), (void**)&ub, tmp));
+    std::vector<CopyDesc> cb, cu;
+    std::vector<GemmDesc> g1, g2;
+    std::vector<GatherDesc> sc;
+    std::vector<TrsmDesc> sd;
+    size_t ok = 0, on = 0;
+    int yoff = 0;
+    for (int b = 0; b < nb; ++b) {
+      Box& B = LV.box[b];
+      const double2* yb;
+      int64_t ldy;
+      if (l == top) {
+        yb = y + yoff;
+        ldy = h->root_n;
+        yoff += B.k;
+      } else {
+        Box& P = h->lv[l - 1].box[b / 2];
+        yb = V[l - 1][b / 2] + ((b % 2) ? h->lv[l].box[b - 1].k : 0);
+        ldy = P.n;
+      }
+      double2* t = tb + ok * nrhs;
+      double2* u = ub + on * nrhs;
+      ok += B.k;
+      on += B.n;
+      cb.push_back({t, BT[l][b], B.k, B.k, B.k, nrhs});
+      g1.push_back(gemm_t(B.Dc, B.k, yb, ldy, t, B.k, B.k, nrhs, B.k, -1.0, 1.0));
+      cu.push_back({u, t, B.n, B.k, B.k, nrhs});
+      if (B.n > B.k)
+        g2.push_back(gemm_t(B.Tc, B.k, t, B.k, u + B.k, B.n, B.n - B.k, nrhs, B.k, 1.0, 0.0));
+      sc.push_back({V[l][b], u, B.pc, B.n, B.n, B.n, nrhs});
+      sd.push_back(lu_t(B.D, B.n, V[l][b], B.n, B.piv, B.n, nrhs));
+    }
+    CopyDesc *dcb = nullptr, *dcu = nullptr;
+    GemmDesc *dg1 = nullptr, *dg2 = nullptr;
+    GatherDesc* dsc = nullptr;
+    TrsmDesc* dsd = nullptr;
+    HK(upload(h, cb, &dcb, tmp));
+    HK(upload(h, cu, &dcu, tmp));
+    HK(upload(h, g1, &dg1, tmp));
+    HK(upload(h, g2, &dg2, tmp));
+    HK(upload(h, sc, &dsc, tmp));
+    HK(upload(h, sd, &dsd, tmp));
+    k_copy2d<<<dim3(gridfor((int64_t)lk * nrhs), nb), 256, 0, st>>>(dcb);
+    wsbm_count_launch();
+    HK(wsbm_gemm_batched(dg1, nb, lk, nrhs, st));
+    k_copy2d<<<dim3(gridfor((int64_t)lk * nrhs), nb), 256, 0, st>>>(dcu);
+    wsbm_count_launch();
+    if (!g2.empty()) HK(wsbm_gemm_batched(dg2, (int)g2.size(), lr, nrhs, st));
+    k_scatter_sub_rows<<<dim3(gridfor((int64_t)ln * nrhs), nb), 256, 0, st>>>(dsc);
+    wsbm_count_launch();
+    HK(wsbm_lu_solve_t_batched(dsd, nb, ln, nrhs, st));
+  }
+  {
+    Level& LV = h->lv[L];
+    std::vector<CopyDesc> c;
+    for (int b = 0; b < (int)LV.box.size(); ++b) {
+      Box& B = LV.box[b];
+      c.push_back({bint + 2 * B.lo, V[L][b], 2 * N, B.n, B.n, nrhs});
+    }
+    CopyDesc* dc = nullptr;
+    HK(upload(h, c, &dc, tmp));
+    k_copy2d<<<dim3(gridfor((int64_t)maxn * nrhs), (unsigned)c.size()), 256, 0, st>>>(dc);
+    wsbm_count_launch();
+    k_split_uq<<<gridfor(N * nrhs), 256, 0, st>>>(bint, (double2*)lam1, (double2*)lam2, N, nrhs);
     wsbm_count_launch();
   }
   HC(cudaGetLastError());
