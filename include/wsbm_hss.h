@@ -245,6 +245,15 @@ int wsbm_batch_stats(wsbm_batch_t b, wsbm_stats_t* s);
 
 void wsbm_batch_destroy(wsbm_batch_t b);
 
+/* Matrix-free product y = A x (trans = 0) or y = A^T x (trans = 1) with the full Nystrom
+ * matrix of eq. (weakly_bm) (every node pair, O(N^2) work, nothing stored): residuals and
+ * iterative refinement of HSS and adjoint solutions.  x, y: device complex128 2N x nrhs in
+ * paper order (for trans = 0, x by unknown and y by equation; the reverse for trans = 1).
+ * Scratch: 2N x (eight waves of CTAs / ceil(N/128)) complex128 from cudaMallocAsync on
+ * `stream`.  Asynchronous.  Errors: INVALID_ARG, OOM, CUDA. */
+int wsbm_matvec(const wsbm_geom* g, const wsbm_params* p, int32_t trans, const void* x,
+                int32_t nrhs, void* y, void* stream);
+
 /* ---------------------------------------------------------------- gradients ----
  * Reverse-mode building blocks of shape and refractive-index gradients of a far-field loss
  * (no counterpart in the paper, which does not differentiate its solver).  With the solution x

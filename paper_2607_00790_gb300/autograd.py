@@ -46,7 +46,8 @@ def fourier_curve(a, b, N):
 
 class FarField(torch.autograd.Function):
     @staticmethod
-    def forward(ctx, x, y, nx, ny, w, kappa, n, k0, inc, obs, leaf, nproxy, tol, precision):
+    def forward(ctx, x, y, nx, ny, w, kappa, n, k0, inc, obs, leaf, nproxy, tol, precision,
+                refine):
         geom, keep = binding.geom_from_tensors(x.detach(), y.detach(), nx.detach(), ny.detach(),
                                                w.detach(), kappa.detach())
         nval = float(n.detach())
@@ -56,8 +57,11 @@ class FarField(torch.autograd.Function):
         s.factor()
         rhs = s.rhs_planewave(inc)
         u, q = s.solve(rhs)
+        if refine:
+            u, q, _ = s.refine(geom, params, rhs, u, q, iters=refine)
         F = s.farfield(u, q, obs)
         ctx.solver = s
+        ctx.refine = refine
         ctx.geom, ctx.params, ctx.keep = geom, params, keep
         ctx.k0, ctx.n = k0, nval
         ctx.save_for_backward(u, q, inc, obs)
@@ -69,6 +73,8 @@ class FarField(torch.autograd.Function):
         geom, params, s = ctx.geom, ctx.params, ctx.solver
         v, g_ff = binding.farfield_vjp(geom, params, u, q, obs, gF.contiguous())
         l1, l2 = s.solve_transposed(v)
+        if ctx.refine:
+            l1, l2, _ = s.refine(geom, params, v, l1, l2, iters=ctx.refine, trans=True)
         lam = torch.cat([l1, l2], dim=0)
         g_rhs = binding.rhs_planewave_vjp(geom, params, inc, lam)
         sol = torch.cat([u, q], dim=0)
@@ -83,12 +89,14 @@ class FarField(torch.autograd.Function):
         s.close()
         ctx.solver = None
         return (g[0], g[1], g[2], g[3], g[4], g[5], gn.reshape(()), None, None, None, None,
-                None, None, None)
+                None, None, None, None)
 
 
-def farfield(curve, n, k0, inc, obs, leaf=64, nproxy=64, tol=1e-10, precision=0):
+def farfield(curve, n, k0, inc, obs, leaf=64, nproxy=64, tol=1e-10, precision=0, refine=0):
     """Far field (nobs x ninc) of the node arrays `curve` = (x, y, nx, ny, w, kappa) with
-    refractive index n (a 0-d tensor), differentiable in the node arrays and n."""
+    refractive index n (a 0-d tensor), differentiable in the node arrays and n.  refine > 0
+    adds that many refinement steps against the dense matrix-free product to the solution and
+    to the adjoint multipliers (HSS factor as preconditioner; O(N^2) per step)."""
     x, y, nx, ny, w, kappa = curve
     return FarField.apply(x, y, nx, ny, w, kappa, n, float(k0), inc, obs, int(leaf), int(nproxy),
-                          float(tol), int(precision))
+                          float(tol), int(precision), int(refine))

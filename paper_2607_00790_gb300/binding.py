@@ -95,6 +95,8 @@ def lib():
         L.wsbm_batch_destroy.restype = None
         G, P = ctypes.POINTER(Geom), ctypes.POINTER(Params)
         L.wsbm_solve_transposed.argtypes = [vp, vp, i32, vp, vp]
+        L.wsbm_matvec.argtypes = [G, P, i32, vp, i32, vp, vp]
+        L.wsbm_matvec.restype = ctypes.c_int
         L.wsbm_entries_vjp.argtypes = [G, P, vp, vp, vp, vp, vp]
         L.wsbm_rhs_planewave_vjp.argtypes = [G, P, vp, i32, vp, vp, vp]
         L.wsbm_farfield_vjp.argtypes = [G, P, vp, vp, i32, vp, i32, vp, vp, vp, vp]
@@ -171,6 +173,20 @@ def wsbm_proxy_block(geom, params, side, idx, circle, P):
                                   _dev(idx, torch.int64), idx.numel(), cx, cy, rho, P,
                                   _dev(out, torch.complex128), _stream(dev)), "wsbm_proxy_block")
     return out.T
+
+
+def wsbm_matvec(geom, params, x, trans=False):
+    """y = A x, or A^T x with trans (dense, matrix-free); x: 2N x nrhs (or 2N) complex128,
+    paper order."""
+    dev = x.device
+    one = x.dim() == 1
+    xm = x.reshape(x.shape[0], -1)
+    xc = xm.T.contiguous()
+    y = torch.empty_like(xc)
+    _check(lib().wsbm_matvec(ctypes.byref(geom), ctypes.byref(params), int(bool(trans)),
+                             _dev(xc, torch.complex128), xc.shape[0], _dev(y, torch.complex128),
+                             _stream(dev)), "wsbm_matvec")
+    return y[0] if one else y.T
 
 
 # ------------------------------------------------------------------- gradients ----
@@ -290,6 +306,22 @@ class Solver:
                                            _dev(l1, torch.complex128), _dev(l2, torch.complex128)),
                "wsbm_solve_transposed")
         return l1.T, l2.T
+
+    def refine(self, geom, params, rhs, u, q, iters=3, trans=False):
+        """Iterative refinement with the dense matrix-free product: r = b - A x, x += HSS^-1 r
+        (with trans: the adjoint system A^T lam = b, lam = (u, q) the multipliers of the two
+        equations).  Returns (u, q, relative residual before each step and after the last)."""
+        x = torch.cat([u, q], dim=0)
+        res = []
+        bn = torch.linalg.norm(rhs).item()
+        for it in range(iters + 1):
+            r = rhs - wsbm_matvec(geom, params, x, trans=trans)
+            res.append(torch.linalg.norm(r).item() / bn)
+            if it == iters:
+                break
+            du, dq = self.solve_transposed(r) if trans else self.solve(r)
+            x = x + torch.cat([du, dq], dim=0)
+        return x[: self.n], x[self.n:], res
 
     def farfield(self, u, q, angles):
         uc, qc = u.T.contiguous(), q.T.contiguous()

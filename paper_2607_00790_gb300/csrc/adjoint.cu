@@ -207,7 +207,10 @@ __global__ void __launch_bounds__(VJP_THREADS)
     __syncthreads();
     if (!valid) continue;
     const int nj = (int)min((int64_t)VJP_THREADS, j1 - jc);
+#pragma unroll 1
     for (int jj = 0; jj < nj; ++jj) {
+      // keep the Hankel tables in shared memory: no hoisting of their loads out of the loop
+      asm volatile("" ::: "memory");
       if (jc + jj == i) continue;
       const VjpSlot& s = sj[jj];
       const double dx = xi - s.x, dy = yi - s.y;
