@@ -12,85 +12,7 @@
 // level in one launch).
 #include <math.h>
 
-#include "hankel.cuh"
-#include "wsbm_internal.h"
-
-#define WSBM_4PI 12.566370614359172954
-
-// Geometric quantities of a pair with the operation order fixed (no contraction): r and the
-// arguments z = k r are reproducible bit for bit by any IEEE double implementation.
-struct PairGeom {
-  double r, ir, z0, z1, dnx, dny, nn, c, rs0, rs1;
-};
-
-__device__ __forceinline__ void pair_geom(double xi, double yi, double nxi, double nyi, double xj,
-                                          double yj, double nxj, double nyj, const Phys& ph,
-                                          PairGeom& G) {
-  double dx = __dsub_rn(xi, xj);
-  double dy = __dsub_rn(yi, yj);
-  double r2 = __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy));
-  double r = __dsqrt_rn(r2);
-  G.r = r;
-  G.z0 = __dmul_rn(ph.k0, r);
-  G.z1 = __dmul_rn(ph.k1, r);
-  G.dny = __dadd_rn(__dmul_rn(dx, nxj), __dmul_rn(dy, nyj));
-  G.dnx = __dadd_rn(__dmul_rn(dx, nxi), __dmul_rn(dy, nyi));
-  G.nn = __dadd_rn(__dmul_rn(nxi, nxj), __dmul_rn(nyi, nyj));
-  // one reciprocal square root serves both wavenumbers and 1/r
-  G.rs0 = rsqrt(G.z0);
-  G.rs1 = G.rs0 * ph.s01;
-  G.ir = ph.k0 * (G.rs0 * G.rs0);
-  G.c = G.dnx * G.dny * (G.ir * G.ir);
-}
-
-// Off-diagonal 2x2 block, weight w_j folded in (kernels: G_k = (i/4) H0(kr);
-// D: (ik/4) H1 (d.n_y)/r;  D*: -(ik/4) H1 (d.n_x)/r;
-// N_k0 - N_k1 = (i/4)[(k0^2 H0(z0) - k1^2 H0(z1)) c + (k0^2 F1(z0) - k1^2 F1(z1))(n_x.n_y - 2c)]).
-__device__ __forceinline__ void block_offdiag(const HkTables& T, const Phys& ph, const PairGeom& G,
-                                              double wj, double2 e[2][2]) {
-  Hk a, b;
-  hankel_fp64_rs<true>(T, G.z0, G.rs0, a);
-  hankel_fp64_rs<true>(T, G.z1, G.rs1, b);
-  const double k0 = ph.k0, k1 = ph.k1;
-  double s11 = 0.25 * wj * k1 * G.dny * G.ir;  // A11 = i s11 H1(z1)
-  e[0][0] = make_double2(-s11 * b.h1i, s11 * b.h1r);
-  double s12 = -0.25 * ph.eps1 * wj;  // A12 = i s12 H0(z1)
-  e[0][1] = make_double2(-s12 * b.h0i, s12 * b.h0r);
-  double q0 = k0 * k0, q1 = k1 * k1;
-  double m2c = G.nn - 2.0 * G.c;
-  double gr = (q0 * a.h0r - q1 * b.h0r) * G.c + (q0 * a.f1r - q1 * b.f1r) * m2c;
-  double gi = (q0 * a.h0i - q1 * b.h0i) * G.c + (q0 * a.f1i - q1 * b.f1i) * m2c;
-  double inv4k0 = 0.25 * ph.inv_k0;
-  double t1 = 0.25 * k0 * G.dny * G.ir;
-  // A21 = w [ i t1 H1(z0) + alpha dN ],  alpha dN = -(1/(4 k0)) (gr + i gi)
-  e[1][0] = make_double2(wj * (-t1 * a.h1i - inv4k0 * gr), wj * (t1 * a.h1r - inv4k0 * gi));
-  // A22 = w [ -i (eps0/4) H0(z0) - (d.n_x/(4 k0 r)) (eps0 k0 H1(z0) - eps1 k1 H1(z1)) ]
-  double u = G.dnx * G.ir * inv4k0;
-  double vr = ph.eps0 * k0 * a.h1r - ph.eps1 * k1 * b.h1r;
-  double vi = ph.eps0 * k0 * a.h1i - ph.eps1 * k1 * b.h1i;
-  e[1][1] = make_double2(wj * (0.25 * ph.eps0 * a.h0i - u * vr),
-                         wj * (-0.25 * ph.eps0 * a.h0r - u * vi));
-}
-
-// Diagonal 2x2 block: one-point corrected trapezoidal rule.  A kernel a ln|x-y| + b gets the
-// weight w_i [a ln(w_i/2pi) + b(x_i, x_i)]; D and D* tend to -kappa/(4 pi).
-__device__ __forceinline__ void block_diag(const Phys& ph, double wi, double kap, double2 e[2][2]) {
-  const double k0 = ph.k0, k1 = ph.k1;
-  double L0 = log(k0 * wi / WSBM_4PI);
-  double L1 = log(k1 * wi / WSBM_4PI);
-  double S0r = -wi * (WSBM_EULER + L0) / (2.0 * WSBM_PI), Si = 0.25 * wi;
-  double S1r = -wi * (WSBM_EULER + L1) / (2.0 * WSBM_PI);
-  double Dd = -wi * kap / WSBM_4PI;
-  double f0 = k0 * k0 * (L0 + WSBM_EULER - 0.5);
-  double f1 = k1 * k1 * (L1 + WSBM_EULER - 0.5);
-  double dNr = -wi * (f0 - f1) / WSBM_4PI;
-  double dNi = wi * (k0 * k0 - k1 * k1) / 8.0;
-  e[0][0] = make_double2(Dd + 0.5, 0.0);
-  e[0][1] = make_double2(-ph.eps1 * S1r, -ph.eps1 * Si);
-  e[1][0] = make_double2(Dd - 0.5 - dNi / k0, dNr / k0);
-  e[1][1] = make_double2(-ph.eps0 * S0r,
-                         -ph.eps0 * Si - ((ph.eps0 - ph.eps1) * Dd + 0.5 * (ph.eps0 + ph.eps1)) / k0);
-}
+#include "entry_blocks.cuh"
 
 struct SlotData {
   double x, y, nx, ny, w, kap;
@@ -499,105 +421,6 @@ __global__ void k_unknowns_to_slots(const int64_t* __restrict__ idx, int64_t n, 
   }
 }
 
-// Matrix-free product y = A x (TRANS: y = A^T x) over every node pair (dense, O(N^2) pair
-// evaluations; used for residuals and iterative refinement of HSS and adjoint solutions).
-// Thread = output node i; CTA row blockIdx.y covers the other nodes [j0, j1); per-split
-// partial sums, reduced in a fixed order by k_matvec_reduce.  Vectors in paper order.
-#define MV_THREADS 128
-struct MvSlot {
-  double x, y, nx, ny, w, kap;
-  double2 u, q;
-};
-
-template <bool TRANS>
-__global__ void __launch_bounds__(MV_THREADS)
-    k_matvec(DevGeom g, Phys ph, const double2* __restrict__ xin, int64_t jspan,
-             double2* __restrict__ part) {
-  __shared__ HkTables T;
-  __shared__ MvSlot sj[MV_THREADS];
-  hk_stage_tables(&T);
-  const int64_t N = g.n;
-  const int64_t i = (int64_t)blockIdx.x * MV_THREADS + threadIdx.x;
-  const int64_t j0 = (int64_t)blockIdx.y * jspan;
-  const int64_t j1 = min(N, j0 + jspan);
-  const bool valid = i < N;
-  double xi = 0, yi = 0, nxi = 0, nyi = 0, wi = 0, ki = 0;
-  if (valid) {
-    xi = g.x[i];
-    yi = g.y[i];
-    nxi = g.nx[i];
-    nyi = g.ny[i];
-    wi = g.w[i];
-    ki = g.kappa[i];
-  }
-  double2 a0 = make_double2(0.0, 0.0), a1 = make_double2(0.0, 0.0);
-  for (int64_t jc = j0; jc < j1; jc += MV_THREADS) {
-    __syncthreads();
-    {
-      int64_t j = jc + threadIdx.x;
-      if (j < j1) {
-        MvSlot& s = sj[threadIdx.x];
-        s.x = g.x[j];
-        s.y = g.y[j];
-        s.nx = g.nx[j];
-        s.ny = g.ny[j];
-        s.w = g.w[j];
-        s.kap = g.kappa[j];
-        s.u = xin[j];
-        s.q = xin[N + j];
-      }
-    }
-    __syncthreads();
-    if (!valid) continue;
-    const int nj = (int)min((int64_t)MV_THREADS, j1 - jc);
-#pragma unroll 1
-    for (int jj = 0; jj < nj; ++jj) {
-      // keep the Hankel tables in shared memory: no hoisting of their loads out of the loop
-      asm volatile("" ::: "memory");
-      const MvSlot& s = sj[jj];
-      double2 e[2][2];
-      if (jc + jj == i) {
-        block_diag(ph, wi, ki, e);
-      } else if (!TRANS) {  // block (i, j): row node i, column node j
-        PairGeom G;
-        pair_geom(xi, yi, nxi, nyi, s.x, s.y, s.nx, s.ny, ph, G);
-        block_offdiag(T, ph, G, s.w, e);
-      } else {  // block (j, i), applied transposed
-        PairGeom G;
-        pair_geom(s.x, s.y, s.nx, s.ny, xi, yi, nxi, nyi, ph, G);
-        block_offdiag(T, ph, G, wi, e);
-      }
-      if (TRANS) {
-        double2 t = e[0][1];
-        e[0][1] = e[1][0];
-        e[1][0] = t;
-      }
-      a0.x += e[0][0].x * s.u.x - e[0][0].y * s.u.y + e[0][1].x * s.q.x - e[0][1].y * s.q.y;
-      a0.y += e[0][0].x * s.u.y + e[0][0].y * s.u.x + e[0][1].x * s.q.y + e[0][1].y * s.q.x;
-      a1.x += e[1][0].x * s.u.x - e[1][0].y * s.u.y + e[1][1].x * s.q.x - e[1][1].y * s.q.y;
-      a1.y += e[1][0].x * s.u.y + e[1][0].y * s.u.x + e[1][1].x * s.q.y + e[1][1].y * s.q.x;
-    }
-  }
-  if (valid) {
-    part[(int64_t)blockIdx.y * 2 * N + i] = a0;
-    part[(int64_t)blockIdx.y * 2 * N + N + i] = a1;
-  }
-}
-
-__global__ void k_matvec_reduce(int64_t N, int nsplit, const double2* __restrict__ part,
-                                double2* __restrict__ y) {
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < 2 * N;
-       e += (int64_t)gridDim.x * blockDim.x) {
-    double2 s = make_double2(0.0, 0.0);
-    for (int t = 0; t < nsplit; ++t) {
-      double2 v = part[(int64_t)t * 2 * N + e];
-      s.x += v.x;
-      s.y += v.y;
-    }
-    y[e] = s;
-  }
-}
-
 // ------------------------------------------------------------------- host helpers ----
 static int grid_for(int64_t ntiles) {
   static int nsm = 0;
@@ -657,52 +480,4 @@ int wsbm_launch_unknowns_to_slots(const int64_t* idx, int64_t n, int64_t N, int3
   k_unknowns_to_slots<<<grid_for(blocks), 256, 0, st>>>(idx, n, N, node, pos);
   wsbm_count_launch();
   return cudaGetLastError() == cudaSuccess ? WSBM_OK : WSBM_ERR_CUDA;
-}
-
-int wsbm_phys_from_params(const wsbm_params* p, Phys* ph);
-int wsbm_geom_check(const wsbm_geom* g);
-DevGeom wsbm_devgeom(const wsbm_geom* g);
-
-extern "C" int wsbm_matvec(const wsbm_geom* g, const wsbm_params* p, int32_t trans, const void* x,
-                           int32_t nrhs, void* y, void* stream) {
-  int rc = wsbm_geom_check(g);
-  if (rc) return rc;
-  Phys ph;
-  if ((rc = wsbm_phys_from_params(p, &ph))) return rc;
-  if ((trans != 0 && trans != 1) || nrhs < 0 || (nrhs > 0 && (!x || !y))) return WSBM_ERR_INVALID_ARG;
-  if (nrhs == 0) return WSBM_OK;
-  cudaStream_t st = (cudaStream_t)stream;
-  const int64_t N = g->n;
-  const int64_t nti = (N + MV_THREADS - 1) / MV_THREADS;
-  int dev = 0, nsm = 152, per_sm = 1;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_matvec<false>, MV_THREADS, 0) != cudaSuccess ||
-      per_sm < 1)
-    per_sm = 1;
-  int64_t want = (int64_t)nsm * per_sm * 8;  // about eight waves
-  int64_t nsplit = (want + nti - 1) / nti;
-  if (nsplit < 1) nsplit = 1;
-  if (nsplit > nti) nsplit = nti;
-  const int64_t jspan = (N + nsplit - 1) / nsplit;
-  nsplit = (N + jspan - 1) / jspan;
-  double2* part = nullptr;
-  if (cudaMallocAsync((void**)&part, (size_t)nsplit * 2 * N * sizeof(double2), st) != cudaSuccess)
-    return WSBM_ERR_OOM;
-  DevGeom dg = wsbm_devgeom(g);
-  for (int c = 0; c < nrhs && rc == WSBM_OK; ++c) {
-    const double2* xc = (const double2*)x + (int64_t)c * 2 * N;
-    if (trans)
-      k_matvec<true><<<dim3((unsigned)nti, (unsigned)nsplit), MV_THREADS, 0, st>>>(dg, ph, xc, jspan, part);
-    else
-      k_matvec<false><<<dim3((unsigned)nti, (unsigned)nsplit), MV_THREADS, 0, st>>>(dg, ph, xc, jspan, part);
-    wsbm_count_launch();
-    int64_t blocks = (2 * N + 255) / 256;
-    k_matvec_reduce<<<grid_for(blocks), 256, 0, st>>>(N, (int)nsplit, part,
-                                                     (double2*)y + (int64_t)c * 2 * N);
-    wsbm_count_launch();
-    if (cudaGetLastError() != cudaSuccess) rc = WSBM_ERR_CUDA;
-  }
-  cudaFreeAsync(part, st);
-  return rc;
 }

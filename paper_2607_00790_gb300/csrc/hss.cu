@@ -819,8 +819,13 @@ static int factor_levels(const std::vector<wsbm_hss*>& hs, const std::vector<int
         on += q.n;
       }
   }
+  // launch order: largest matrices first, so that the last wave holds the short ones
+  std::vector<QrDesc> qs(qd);
+  std::stable_sort(qs.begin(), qs.end(), [](const QrDesc& x, const QrDesc& y) {
+    return (int64_t)x.m * x.n > (int64_t)y.m * y.n;
+  });
   QrDesc* dq = nullptr;
-  HK(upload(h0, qd, &dq, tmp));
+  HK(upload(h0, qs, &dq, tmp));
   HK(wsbm_cpqr_batched(dq, 2 * NB, 0, st));
   std::vector<int32_t> hstate(4 * NB);
   HC(cudaMemcpyAsync(hstate.data(), state, hstate.size() * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
