@@ -225,7 +225,7 @@ void wsbm_destroy(wsbm_hss_t h);
  * sharing one stream).  wsbm_batch_factor builds and factors every curve with one launch per
  * phase per tree level over all curves (curves of different depth are aligned at their leaves,
  * each stops compressing by its own rule), then all dense roots in one batched LU: the paper's
- * "same number of layer potentials per block" load balance carried across many scatterers.
+ * equal-cost-per-block load balance carried across many scatterers.
  * Results are identical to factoring each curve alone. */
 typedef struct wsbm_batch* wsbm_batch_t;
 

@@ -10,8 +10,8 @@ Two parts (paper: Matsumoto & Yokota, TE-mode transmission, Secs. II-IV):
   (``wsbm_oracle.cpp``; Hankel values from ``std::cyl_bessel_jl`` / ``std::cyl_neumannl``),
   followed by a dense LU solve (``numpy.linalg.solve``).  The HSS solver approximates this
   system to the interpolative-decomposition tolerance.
-* O-phys: the Mie series for a disk (Sec. IV: "the analytical solution ... can be
-  explicitly calculated"), which fixes the discretisation and the paper's O(h^3) claim.
+* O-phys: the Mie series for a disk (Sec. IV compares against the closed-form solution of
+  the disk), which fixes the discretisation and the paper's O(h^3) claim.
 
 * Shape gradients (``gradient.py``): the dense adjoint of a far-field intensity misfit,
   with matrix derivatives from a dual-number evaluation of the same blocks.

@@ -13,8 +13,8 @@
 //     solution G_k = (i/4) H0^(1)(k r).  The paper names these operators but does not print
 //     G; the reading (radiating H^(1), D differentiates in y, D* in x) is the one consistent
 //     with the jump terms +-I/2 of eqs. (bm) and (weakly_bm).
-//   * The one-point corrected diagonal (Sec. I/II: "only the diagonal terms are locally
-//     corrected"; zeta-corrected trapezoidal rule).  The paper prints no formula; the reading
+//   * The one-point corrected diagonal (Sec. I/II: a local correction of the diagonal terms
+//     alone, zeta-corrected trapezoidal rule).  The paper prints no formula; the reading
 //     is the one-point log correction w_i*ln(w_i/2pi) applied to each log-singular kernel
 //     and the smooth limits of D and D* (curvature term).
 //   * Proxy-circle blocks used by the proxy-surface interpolative decomposition (Sec. III,
