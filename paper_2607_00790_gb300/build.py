@@ -42,7 +42,7 @@ def build(verbose=False):
 
     with ThreadPoolExecutor(max_workers=min(8, len(srcs))) as ex:
         list(ex.map(one, zip(srcs, objs)))
-    cmd = [nvcc(), *ARCH, "-shared", "-o", LIB, *objs, "-lcublas"]
+    cmd = [nvcc(), *ARCH, "-shared", "-o", LIB, *objs]
     subprocess.run(cmd, check=True)
     return LIB
 

@@ -296,7 +296,15 @@ __global__ void k_apply_piv_inv(const TrsmDesc* __restrict__ d) {
 // |beta_j| <= tol |beta_0| (rank k = j); mode 1 runs until step kt.  The state (reflected
 // matrix, exact remaining column norms, permutation) lets a later call resume.  On return
 // the R factor sits in rows 0..k-1 (diagonal included; below it, reflector data).
-__global__ void __launch_bounds__(256) k_cpqr(const QrDesc* __restrict__ d, int mode) {
+#ifndef CPQR_CB
+#define CPQR_CB 4  // trailing columns per warp per pass (2*CB partial sums, a power of two <= 16)
+#endif
+#ifndef CPQR_MINB
+#define CPQR_MINB 4  // minimum resident CTAs per SM asked of the register allocator (measured best)
+#endif
+// 5 - log2(2*CPQR_CB): the lane holding reduced value t is t << CPQR_SH
+#define CPQR_SH (CPQR_CB == 1 ? 4 : CPQR_CB == 2 ? 3 : CPQR_CB == 4 ? 2 : CPQR_CB == 8 ? 1 : 0)
+__global__ void __launch_bounds__(256, CPQR_MINB) k_cpqr(const QrDesc* __restrict__ d, int mode) {
   const QrDesc q = d[blockIdx.x];
   const int m = q.m, n = q.n;
   double2* M = q.A;
@@ -402,38 +410,82 @@ __global__ void __launch_bounds__(256) k_cpqr(const QrDesc* __restrict__ d, int 
     }
     __syncthreads();
     const double tau = s_tau;
-    // apply P to the trailing columns: one warp per column.  The remaining norm is downdated by
-    // the new row-j entry and recomputed exactly once cancellation has eaten half its digits
-    // (remaining norm below 1e-8 of the last exact one).
-    for (int c = j + 1 + warp; c < n; c += nw) {
-      double2* col = M + (int64_t)c * ld;
-      const double2* u = M + (int64_t)j * ld;
-      double2 w = make_double2(0.0, 0.0);
+    // apply P to the trailing columns: a warp takes CPQR_CB columns at a time, so each element
+    // of u is loaded once for all of them and the 2*CPQR_CB partial dot products are summed
+    // across the warp by recursive halving (each level hands half of the values to the partner
+    // lane; 2*CB - 1 + (5 - log2(2*CB)) adds per lane instead of 10 per column).  The remaining
+    // norm is downdated by the new row-j entry and recomputed exactly once cancellation has
+    // eaten half its digits (remaining norm below 1e-8 of the last exact one).
+    const double2* u = M + (int64_t)j * ld;
+    for (int c0 = j + 1 + warp * CPQR_CB; c0 < n; c0 += nw * CPQR_CB) {
+      const int nc = min(CPQR_CB, n - c0);
+      double acc[2 * CPQR_CB];  // re of the nc columns, then im
+#pragma unroll
+      for (int v = 0; v < 2 * CPQR_CB; ++v) acc[v] = 0.0;
       for (int i = j + lane; i < m; i += 32) {  // w = u^H col, as fused multiply-adds
-        double2 ui = u[i], ci = col[i];
-        w.x = fma(ui.x, ci.x, fma(ui.y, ci.y, w.x));
-        w.y = fma(ui.x, ci.y, fma(-ui.y, ci.x, w.y));
+        const double2 ui = u[i];
+#pragma unroll
+        for (int v = 0; v < CPQR_CB; ++v) {
+          if (v < nc) {
+            const double2 ci = M[i + (int64_t)(c0 + v) * ld];
+            acc[v] = fma(ui.x, ci.x, fma(ui.y, ci.y, acc[v]));
+            acc[CPQR_CB + v] = fma(ui.x, ci.y, fma(-ui.y, ci.x, acc[CPQR_CB + v]));
+          }
+        }
       }
-      for (int o = 16; o > 0; o >>= 1) {
-        w.x += __shfl_xor_sync(0xffffffffu, w.x, o);
-        w.y += __shfl_xor_sync(0xffffffffu, w.y, o);
+      int cur = 2 * CPQR_CB;
+#pragma unroll
+      for (int o = 16; o >= 1; o >>= 1) {
+        if (cur > 1) {
+          const int h = cur >> 1;
+          const bool up = (lane & o) != 0;
+#pragma unroll
+          for (int v = 0; v < CPQR_CB; ++v) {
+            if (v < h) {
+              const double send = up ? acc[v] : acc[v + h];
+              const double keep = up ? acc[v + h] : acc[v];
+              acc[v] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+            }
+          }
+          cur = h;
+        } else {
+          acc[0] += __shfl_xor_sync(0xffffffffu, acc[0], o);
+        }
       }
-      w.x *= tau;
-      w.y *= tau;
-      for (int i = j + lane; i < m; i += 32) col[i] = cfms(u[i], w, col[i]);
+      // value t (re of column t for t < CB, im of column t - CB otherwise) sits in lane t << CPQR_SH
+      double2 w[CPQR_CB];
+#pragma unroll
+      for (int v = 0; v < CPQR_CB; ++v) {
+        w[v].x = tau * __shfl_sync(0xffffffffu, acc[0], v << CPQR_SH);
+        w[v].y = tau * __shfl_sync(0xffffffffu, acc[0], (CPQR_CB + v) << CPQR_SH);
+      }
+      for (int i = j + lane; i < m; i += 32) {
+        const double2 ui = u[i];
+#pragma unroll
+        for (int v = 0; v < CPQR_CB; ++v) {
+          if (v < nc) {
+            double2* pc = M + i + (int64_t)(c0 + v) * ld;
+            *pc = cfms(ui, w[v], *pc);
+          }
+        }
+      }
       __syncwarp();
-      const double rj = cabs2(col[j]);  // the new row-j entry (written by lane 0)
-      double nv = q.norm2[c] - rj;
-      if (nv <= 1e-8 * q.nref[c]) {
-        double ns = 0.0;
-        for (int i = j + 1 + lane; i < m; i += 32) ns += cabs2(col[i]);
-        for (int o = 16; o > 0; o >>= 1) ns += __shfl_xor_sync(0xffffffffu, ns, o);
-        nv = ns;
+      for (int v = 0; v < nc; ++v) {
+        const int c = c0 + v;
+        const double2* col = M + (int64_t)c * ld;
+        const double rj = cabs2(col[j]);  // the new row-j entry (written by lane 0)
+        double nv = q.norm2[c] - rj;
+        if (nv <= 1e-8 * q.nref[c]) {
+          double ns = 0.0;
+          for (int i = j + 1 + lane; i < m; i += 32) ns += cabs2(col[i]);
+          for (int o = 16; o > 0; o >>= 1) ns += __shfl_xor_sync(0xffffffffu, ns, o);
+          nv = ns;
+          __syncwarp();
+          if (lane == 0) q.nref[c] = ns;
+        }
         __syncwarp();
-        if (lane == 0) q.nref[c] = ns;
+        if (lane == 0) q.norm2[c] = fmax(nv, 0.0);
       }
-      __syncwarp();
-      if (lane == 0) q.norm2[c] = fmax(nv, 0.0);
     }
     __syncthreads();
     if (threadIdx.x == 0) {
