@@ -54,6 +54,9 @@ def _lib():
         lib.orc_proxy_row_block.argtypes = geo + [_pi64, _i64, _d, _d, _d, _i64, _pd]
         lib.orc_proxy_col_block.argtypes = geo + [_pi64, _i64, _d, _d, _d, _i64, _pd]
         lib.orc_wsbm_bilinear_tangent.argtypes = geo + [_pd, _pd, _i64, _pd, _pd, _pd, _pd]
+        lib.orc_field.argtypes = geo + [_pd, _pd, _i64, _pd, _pd, _i64, _pd,
+                                        ctypes.POINTER(ctypes.c_int32)]
+        lib.orc_field.restype = ctypes.c_int
         for f in (lib.orc_hankel01, lib.orc_f1, lib.orc_wsbm_entries, lib.orc_wsbm_dense,
                   lib.orc_wsbm_matvec, lib.orc_proxy_circle, lib.orc_proxy_row_block,
                   lib.orc_proxy_col_block, lib.orc_wsbm_bilinear_tangent):
@@ -267,6 +270,27 @@ def farfield(curve, phys, u, q, angles):
     return out
 
 
+def field(curve, phys, u, q, tx, ty):
+    """Field at points off the curve from the densities (integral representations; Sec. II
+    notes the domain solution follows from u and q): scattered field D_k0[u] - eps0 S_k0[q] at
+    exterior points, total field eps1 S_k1[q] - D_k1[u] at interior points (side by the
+    crossing-number test).  u, q: (N,) or (N, nrhs).  Returns (values (nt, nrhs), inside)."""
+    g = _geo(curve)
+    n = g[0].size
+    U = np.asarray(u, dtype=np.complex128).reshape(n, -1)
+    Q = np.asarray(q, dtype=np.complex128).reshape(n, -1)
+    nrhs = U.shape[1]
+    uu = np.ascontiguousarray(U.T).view(np.float64).ravel()
+    qq = np.ascontiguousarray(Q.T).view(np.float64).ravel()
+    tx = _c64(np.atleast_1d(tx))
+    ty = _c64(np.atleast_1d(ty))
+    out = np.empty(2 * tx.size * nrhs)
+    inside = np.empty(tx.size, dtype=np.int32)
+    _lib().orc_field(n, *[_p(a) for a in g], *phys.args(), _p(uu), _p(qq), nrhs, _p(tx), _p(ty),
+                     tx.size, _p(out), inside.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)))
+    return out.view(np.complex128).reshape(nrhs, tx.size).T, inside.astype(bool)
+
+
 # -------------------------------------------------------------------------------- Mie ----
 def mie_disk(R, phys, theta_inc=0.0, mmax=None):
     """Mie-series coefficients for TE transmission by a disk of radius R centred at 0.
@@ -304,6 +328,20 @@ def mie_boundary(R, phys, theta, theta_inc=0.0):
     u = e @ (b * jv(m, phys.k1 * R))
     q = (phys.k1 / phys.eps1) * (e @ (b * jvp(m, phys.k1 * R)))
     return u, q
+
+
+def mie_field(R, phys, px, py, theta_inc=0.0):
+    """Exact field of the disk at points: scattered sum a_m H_m(k0 r) e^{im(t - t_inc)} outside,
+    total sum b_m J_m(k1 r) e^{im(t - t_inc)} inside (the split returned by ``field``)."""
+    from scipy.special import hankel1, jv
+
+    m, a, b = mie_disk(R, phys, theta_inc)
+    px, py = np.atleast_1d(px), np.atleast_1d(py)
+    r, t = np.hypot(px, py), np.arctan2(py, px)
+    e = np.exp(1j * np.outer(t - theta_inc, m))
+    out = np.where(r > R, np.sum(e * a * hankel1(m, phys.k0 * r[:, None]), axis=1),
+                   np.sum(e * b * jv(m, phys.k1 * r[:, None]), axis=1))
+    return out
 
 
 def mie_farfield(R, phys, angles, theta_inc=0.0):

@@ -578,4 +578,55 @@ int orc_wsbm_bilinear_tangent(int64_t n, const double* x, const double* y, const
   return 0;
 }
 
+
+// Field off the curve from the boundary densities by the integral representations (the paper
+// notes that u and q on the curve give the solution in the domains through them):
+//   exterior x:  u_sc(x) = D_k0[u](x) - eps0 S_k0[q](x)   (scattered part; total = u_in + u_sc)
+//   interior x:  u(x)    = eps1 S_k1[q](x) - D_k1[u](x)
+// with S_k[f](x) = sum_j w_j G_k(x, y_j) f_j, D_k[f](x) = sum_j w_j dG_k(x, y_j)/dn_y f_j.
+// The side of x is decided by the crossing-number test of the closed polygon through the nodes.
+// u, q: N x nrhs complex128 (column-major); out: nt x nrhs complex128; inside: nt int32.
+int orc_field(int64_t n, const double* x, const double* y, const double* nx, const double* ny,
+              const double* w, const double* kappa, double k0, double k1, double eps0,
+              double eps1, const double* u, const double* q, int64_t nrhs, const double* tx,
+              const double* ty, int64_t nt, double* out, int32_t* inside) {
+  (void)kappa;
+  const cplx* U = reinterpret_cast<const cplx*>(u);
+  const cplx* Q = reinterpret_cast<const cplx*>(q);
+  cplx* O = reinterpret_cast<cplx*>(out);
+  const cplx I1(0.0, 1.0);
+#pragma omp parallel for schedule(dynamic, 4)
+  for (int64_t t = 0; t < nt; ++t) {
+    // crossing number of the ray from (tx, ty) towards +x
+    int cross = 0;
+    for (int64_t j = 0; j < n; ++j) {
+      int64_t k = (j + 1) % n;
+      bool a = y[j] > ty[t], b = y[k] > ty[t];
+      if (a != b) {
+        double xc = x[j] + (ty[t] - y[j]) * (x[k] - x[j]) / (y[k] - y[j]);
+        if (xc > tx[t]) cross ^= 1;
+      }
+    }
+    inside[t] = cross;
+    const double k = cross ? k1 : k0;
+    for (int64_t c = 0; c < nrhs; ++c) {
+      cplx acc(0.0, 0.0);
+      for (int64_t j = 0; j < n; ++j) {
+        double dx = tx[t] - x[j], dy = ty[t] - y[j];
+        double r = std::sqrt(dx * dx + dy * dy);
+        Hank h = hankel_eval(k * r);
+        cplx G = 0.25 * I1 * h.h0;
+        cplx Dy = 0.25 * I1 * k * h.h1 * ((dx * nx[j] + dy * ny[j]) / r);
+        cplx uj = U[c * n + j], qj = Q[c * n + j];
+        if (cross)
+          acc += w[j] * (eps1 * G * qj - Dy * uj);
+        else
+          acc += w[j] * (Dy * uj - eps0 * G * qj);
+      }
+      O[c * nt + t] = acc;
+    }
+  }
+  return 0;
+}
+
 }  // extern "C"
