@@ -254,6 +254,18 @@ void wsbm_batch_destroy(wsbm_batch_t b);
 int wsbm_matvec(const wsbm_geom* g, const wsbm_params* p, int32_t trans, const void* x,
                 int32_t nrhs, void* y, void* stream);
 
+/* Field at nt points off the curve from densities u, q (device complex128 N x nrhs), by the
+ * integral representations (Sec. II: the domain solution follows from the boundary values):
+ * exterior points get the scattered field D_k0[u] - eps0 S_k0[q] (add the incident wave for
+ * the total field), interior points the total field eps1 S_k1[q] - D_k1[u].  tx, ty: device
+ * doubles; out: device complex128 nt x nrhs; inside: device int8 nt, 1 for interior points
+ * (Gauss test of the Laplace double layer).  The trapezoidal sums are accurate a few node
+ * spacings away from the curve; no near-singular quadrature is applied.  Scratch from
+ * cudaMallocAsync on `stream`; asynchronous.  Errors: INVALID_ARG, OOM, CUDA. */
+int wsbm_field(const wsbm_geom* g, const wsbm_params* p, const void* u, const void* q,
+               int32_t nrhs, const double* tx, const double* ty, int64_t nt, void* out,
+               int8_t* inside, void* stream);
+
 /* ---------------------------------------------------------------- gradients ----
  * Reverse-mode building blocks of shape and refractive-index gradients of a far-field loss
  * (no counterpart in the paper, which does not differentiate its solver).  With the solution x

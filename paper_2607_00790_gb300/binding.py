@@ -97,6 +97,8 @@ def lib():
         L.wsbm_solve_transposed.argtypes = [vp, vp, i32, vp, vp]
         L.wsbm_matvec.argtypes = [G, P, i32, vp, i32, vp, vp]
         L.wsbm_matvec.restype = ctypes.c_int
+        L.wsbm_field.argtypes = [G, P, vp, vp, i32, vp, vp, i64, vp, vp, vp]
+        L.wsbm_field.restype = ctypes.c_int
         L.wsbm_entries_vjp.argtypes = [G, P, vp, vp, vp, vp, vp]
         L.wsbm_rhs_planewave_vjp.argtypes = [G, P, vp, i32, vp, vp, vp]
         L.wsbm_farfield_vjp.argtypes = [G, P, vp, vp, i32, vp, i32, vp, vp, vp, vp]
@@ -187,6 +189,22 @@ def wsbm_matvec(geom, params, x, trans=False):
                              _dev(xc, torch.complex128), xc.shape[0], _dev(y, torch.complex128),
                              _stream(dev)), "wsbm_matvec")
     return y[0] if one else y.T
+
+
+def field(geom, params, u, q, tx, ty):
+    """Field at points (tx, ty) off the curve from densities u, q (N x nrhs complex128):
+    scattered field outside, total field inside.  Returns (values nt x nrhs, inside bool)."""
+    dev = u.device
+    uc, qc = u.T.contiguous(), q.T.contiguous()
+    nrhs = uc.shape[0]
+    nt = tx.numel()
+    out = torch.empty((nrhs, nt), dtype=torch.complex128, device=dev)
+    inside = torch.empty(nt, dtype=torch.int8, device=dev)
+    _check(lib().wsbm_field(ctypes.byref(geom), ctypes.byref(params), _dev(uc, torch.complex128),
+                            _dev(qc, torch.complex128), nrhs, _dev(tx, torch.float64),
+                            _dev(ty, torch.float64), nt, _dev(out, torch.complex128),
+                            _dev(inside, torch.int8), _stream(dev)), "wsbm_field")
+    return out.T, inside.bool()
 
 
 # ------------------------------------------------------------------- gradients ----
