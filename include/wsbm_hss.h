@@ -41,7 +41,7 @@ enum {
   WSBM_ERR_NO_DEVICE = -7      /* no usable sm_103 device                                   */
 };
 
-enum { WSBM_FP64 = 0, WSBM_MIXED = 1 };
+enum { WSBM_FP64 = 0, WSBM_MIXED = 1, WSBM_MIXED_FINE = 2 };
 
 /* Curve data, all device pointers to n doubles, caller-owned. */
 typedef struct {
@@ -60,8 +60,10 @@ typedef struct {
  *              L = ceil(log2(n/leaf)) over contiguous node ranges (Sec. III, Fig. tree)
  *  nproxy      proxy points on each leaf's proxy circle (>= 8; grown on upper levels)
  *  id_tol      relative tolerance of the interpolative decompositions (0 < id_tol < 1)
- *  precision   WSBM_FP64, or WSBM_MIXED: proxy blocks evaluated with an FP32 amplitude and an
- *              FP64-reduced phase; every other entry, the ID and the factor stay FP64
+ *  precision   WSBM_FP64; WSBM_MIXED: proxy blocks evaluated with an FP32 amplitude and phase
+ *              factor after an FP64 phase reduction (entries to ~1e-7); WSBM_MIXED_FINE: proxy
+ *              blocks with only the amplitude corrections P - 1, Q of the Hankel functions in
+ *              FP32 (entries to ~2e-8).  Every other entry, the ID and the factor stay FP64
  *  proxy_ratio proxy radius / box radius (<= 1 selects 1.5)
  *  max_levels  0: build and factor the whole tree.  m > 0: compress only the m lowest tree
  *              levels and stop before the dense root (a partial build for measuring the build
@@ -111,7 +113,8 @@ typedef struct wsbm_hss* wsbm_hss_t;
  *   z    device, n doubles
  *   out  device, 6n doubles: per argument Re H0, Im H0, Re H1, Im H1, Re F1, Im F1 where
  *        F1(z) = H1(z)/z + 2i/(pi z^2) (pole-free part used by N_k0 - N_k1)
- *   precision  WSBM_FP64 or WSBM_MIXED (FP32 amplitude, FP64 phase reduction)
+ *   precision  WSBM_FP64, WSBM_MIXED (FP32 amplitude and phase factor after an FP64 phase
+ *              reduction; F1 not computed, zeros) or WSBM_MIXED_FINE (FP32 P - 1 and Q only)
  * Errors: INVALID_ARG (n < 0, NULL with n > 0), CUDA. */
 int wsbm_hankel01(const double* z, int64_t n, double* out, int32_t precision, void* stream);
 
@@ -152,7 +155,7 @@ int wsbm_entries_raw_noalloc(const wsbm_geom* g, const wsbm_params* p, const int
  *   out: complex128 nidx x 2P, column-major.
  * Column block (side = 1): 2P rows (the k1 field, then the k0 field, of the box unknowns at
  *   the proxy points), columns = the box unknowns `idx`.  out: complex128 2P x nidx.
- * precision WSBM_MIXED evaluates these blocks with an FP32 amplitude.
+ * precision WSBM_MIXED / WSBM_MIXED_FINE evaluate these blocks as described for wsbm_params.
  * Errors: INVALID_ARG, OOM, CUDA. */
 int wsbm_proxy_block(const wsbm_geom* g, const wsbm_params* p, int32_t side, const int64_t* idx,
                      int64_t nidx, double cx, double cy, double rho, int32_t P, void* out,

@@ -18,6 +18,7 @@ _LIB = None
 WSBM_OK = 0
 WSBM_FP64 = 0
 WSBM_MIXED = 1
+WSBM_MIXED_FINE = 2
 ERRORS = {0: "ok", -1: "invalid argument", -2: "out of memory", -3: "CUDA error",
           -4: "rank overflow", -5: "timeout", -6: "not factored", -7: "no device"}
 

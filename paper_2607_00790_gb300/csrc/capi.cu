@@ -81,8 +81,9 @@ DevGeom wsbm_devgeom(const wsbm_geom* g) {
 extern "C" int wsbm_hankel01(const double* z, int64_t n, double* out, int32_t precision,
                              void* stream) {
   if (n < 0 || (n > 0 && (!z || !out))) return WSBM_ERR_INVALID_ARG;
-  if (precision != WSBM_FP64 && precision != WSBM_MIXED) return WSBM_ERR_INVALID_ARG;
-  return wsbm_launch_hankel(z, n, out, precision == WSBM_MIXED, (cudaStream_t)stream);
+  if (precision != WSBM_FP64 && precision != WSBM_MIXED && precision != WSBM_MIXED_FINE)
+    return WSBM_ERR_INVALID_ARG;
+  return wsbm_launch_hankel(z, n, out, precision, (cudaStream_t)stream);
 }
 
 extern "C" int wsbm_entries_raw(const wsbm_geom* g, const wsbm_params* p, const int64_t* rows,
@@ -145,7 +146,8 @@ extern "C" int wsbm_proxy_block(const wsbm_geom* g, const wsbm_params* p, int32_
   if ((rc = wsbm_phys_from_params(p, &ph))) return rc;
   if ((side != 0 && side != 1) || P < 1 || nidx < 0 || nidx > INT32_MAX / 2) return WSBM_ERR_INVALID_ARG;
   if (!(rho > 0.0) || !isfinite(cx) || !isfinite(cy) || !isfinite(rho)) return WSBM_ERR_INVALID_ARG;
-  if (p->precision != WSBM_FP64 && p->precision != WSBM_MIXED) return WSBM_ERR_INVALID_ARG;
+  if (p->precision != WSBM_FP64 && p->precision != WSBM_MIXED && p->precision != WSBM_MIXED_FINE)
+    return WSBM_ERR_INVALID_ARG;
   if (nidx == 0) return WSBM_OK;
   if (!idx || !out) return WSBM_ERR_INVALID_ARG;
   cudaStream_t st = (cudaStream_t)stream;
@@ -176,7 +178,7 @@ extern "C" int wsbm_proxy_block(const wsbm_geom* g, const wsbm_params* p, int32_
     DevGeom dg = wsbm_devgeom(g);
     if ((rc = wsbm_launch_unknowns_to_slots(idx, nidx, g->n, buf, buf + nidx, st))) goto done;
     CK(cudaMemcpyAsync(dtask, &t, sizeof(t), cudaMemcpyHostToDevice, st));
-    rc = wsbm_launch_proxy(dg, ph, dtask, 1, wsbm_proxy_tiles(t.nn, P), p->precision == WSBM_MIXED,
+    rc = wsbm_launch_proxy(dg, ph, dtask, 1, wsbm_proxy_tiles(t.nn, P), p->precision,
                            st);
     CK(cudaStreamSynchronize(st));
   }

@@ -129,6 +129,7 @@ struct ProxyPt {
 // Sources on the proxy circle acting on equations at node x (row side).  Combined-field
 // source Phi_k = dG/dnu_p - i k G;  out[s][a]: source s (0: k1, 1: k0), equation a.
 //   s = k1: [Phi1 ; -alpha d_nx Phi1]     s = k0: [0 ; Phi0 + alpha d_nx Phi0]
+template <bool PQ32>
 __device__ __forceinline__ void proxy_row_fp64(const HkTables& T, const Phys& ph, const SlotData& X,
                                                const ProxyPt& p, double pw, double2 o[2][2]) {
   double dx = X.x - p.px, dy = X.y - p.py;
@@ -148,9 +149,9 @@ __device__ __forceinline__ void proxy_row_fp64(const HkTables& T, const Phys& ph
     double ik = s == 0 ? ph.inv_k1 : ph.inv_k0;
     Hk h;
     if (s == 0)
-      hankel_fp64_rs<false>(T, z1, rs1, h);
+      hankel_fp64_rs<false, PQ32>(T, z1, rs1, h);
     else
-      hankel_fp64_rs<false>(T, ph.k0 * r, rs1 * ph.s10, h);
+      hankel_fp64_rs<false, PQ32>(T, ph.k0 * r, rs1 * ph.s10, h);
     // phi = (ik/4) H1 dnu + (k/4) H0
     double q = 0.25 * k;
     double phr = q * (-h.h1i * dnu + h.h0r), phi = q * (h.h1r * dnu + h.h0i);
@@ -174,6 +175,7 @@ __device__ __forceinline__ void proxy_row_fp64(const HkTables& T, const Phys& ph
 
 // Fields of the box unknowns at a proxy point (column side).  out[s][b]: field s (0: psi1,
 // 1: psi0), unknown b:  u_j -> w_j (ik/4) H1 (d.n_y)/r,  q_j -> -eps_s w_j (i/4) H0.
+template <bool PQ32>
 __device__ __forceinline__ void proxy_col_fp64(const HkTables& T, const Phys& ph, const SlotData& Y,
                                                const ProxyPt& p, double2 o[2][2]) {
   double dx = p.px - Y.x, dy = p.py - Y.y;
@@ -188,9 +190,9 @@ __device__ __forceinline__ void proxy_col_fp64(const HkTables& T, const Phys& ph
     double eps = s == 0 ? ph.eps1 : ph.eps0;
     Hk h;
     if (s == 0)
-      hankel_fp64_rs<false>(T, z1, rs1, h);
+      hankel_fp64_rs<false, PQ32>(T, z1, rs1, h);
     else
-      hankel_fp64_rs<false>(T, ph.k0 * r, rs1 * ph.s10, h);
+      hankel_fp64_rs<false, PQ32>(T, ph.k0 * r, rs1 * ph.s10, h);
     double a = 0.25 * Y.w * k * dny;
     o[s][0] = make_double2(-a * h.h1i, a * h.h1r);
     double bq = -0.25 * eps * Y.w;
@@ -307,7 +309,8 @@ __device__ __forceinline__ void proxy_col_mixed(const HkTables& T, const Phys& p
   }
 }
 
-template <bool MIXED>
+// MODE: WSBM_FP64, WSBM_MIXED or WSBM_MIXED_FINE
+template <int MODE>
 __global__ void __launch_bounds__(WSBM_PAIR_THREADS)
     k_proxy(DevGeom g0, Phys ph0, const ProxyTask* __restrict__ tasks, int ntasks, int64_t ntiles,
             const DevGeom* __restrict__ geos, const Phys* __restrict__ phys) {
@@ -351,15 +354,15 @@ __global__ void __launch_bounds__(WSBM_PAIR_THREADS)
       const SlotData& X = ss[ty];
       if (tk.side == 0) {
         double pw = 2.0 * WSBM_PI * tk.rho / (double)tk.P;
-        if (MIXED)
+        if (MODE == WSBM_MIXED)
           proxy_row_mixed(T, ph, X, sp[tx], pw, o);
         else
-          proxy_row_fp64(T, ph, X, sp[tx], pw, o);
+          proxy_row_fp64<MODE == WSBM_MIXED_FINE>(T, ph, X, sp[tx], pw, o);
       } else {
-        if (MIXED)
+        if (MODE == WSBM_MIXED)
           proxy_col_mixed(T, ph, X, sp[tx], o);
         else
-          proxy_col_fp64(T, ph, X, sp[tx], o);
+          proxy_col_fp64<MODE == WSBM_MIXED_FINE>(T, ph, X, sp[tx], o);
       }
       const int bp[2] = {X.p0, X.p1};
 #pragma unroll
@@ -387,7 +390,16 @@ __global__ void k_hankel(const double* __restrict__ z, int64_t n, double* __rest
        i += (int64_t)gridDim.x * blockDim.x) {
     double zi = z[i];
     double* o = out + 6 * i;
-    if (mixed) {
+    if (mixed == WSBM_MIXED_FINE) {
+      Hk h;
+      hankel_fp64_rs<true, true>(T, zi, rsqrt(zi), h);
+      o[0] = h.h0r;
+      o[1] = h.h0i;
+      o[2] = h.h1r;
+      o[3] = h.h1i;
+      o[4] = h.f1r;
+      o[5] = h.f1i;
+    } else if (mixed) {
       HkF h;
       hankel_mixed(T, zi, rsqrtf((float)zi), h);
       o[0] = h.h0r;
@@ -457,10 +469,12 @@ int wsbm_launch_proxy(const DevGeom& g, const Phys& ph, const ProxyTask* d_tasks
                       int64_t ntiles, int mixed, cudaStream_t st, const DevGeom* geos,
                       const Phys* phys) {
   if (ntiles <= 0) return WSBM_OK;
-  if (mixed)
-    k_proxy<true><<<grid_for(ntiles), WSBM_PAIR_THREADS, 0, st>>>(g, ph, d_tasks, ntasks, ntiles, geos, phys);
+  if (mixed == WSBM_MIXED)
+    k_proxy<WSBM_MIXED><<<grid_for(ntiles), WSBM_PAIR_THREADS, 0, st>>>(g, ph, d_tasks, ntasks, ntiles, geos, phys);
+  else if (mixed == WSBM_MIXED_FINE)
+    k_proxy<WSBM_MIXED_FINE><<<grid_for(ntiles), WSBM_PAIR_THREADS, 0, st>>>(g, ph, d_tasks, ntasks, ntiles, geos, phys);
   else
-    k_proxy<false><<<grid_for(ntiles), WSBM_PAIR_THREADS, 0, st>>>(g, ph, d_tasks, ntasks, ntiles, geos, phys);
+    k_proxy<WSBM_FP64><<<grid_for(ntiles), WSBM_PAIR_THREADS, 0, st>>>(g, ph, d_tasks, ntasks, ntiles, geos, phys);
   wsbm_count_launch();
   return cudaGetLastError() == cudaSuccess ? WSBM_OK : WSBM_ERR_CUDA;
 }

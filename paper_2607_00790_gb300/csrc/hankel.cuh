@@ -16,8 +16,10 @@
 // All coefficients are fitted by gen_hankel_coeffs.py (50-digit arithmetic) and checked there.
 //
 // Mixed evaluator (WSBM_MIXED): the phase is reduced in FP64 (z - 2 pi n, two-part 2 pi), then
-// sin/cos of the remainder (rounded to FP32: phase error <= 2e-7), sqrt(2/(pi z)) and P, Q (degree-4 fits in 1/z, degree-2 in 1/z^2)
-// are FP32.  Arguments below 1.5 fall back to the FP64 evaluator.
+// sin/cos of the remainder (rounded to FP32: phase error <= 2e-7), sqrt(2/(pi z)) and P, Q
+// (degree-4 fits in 1/z, degree-2 in 1/z^2) are FP32.  Arguments below 1.5 fall back to the FP64
+// evaluator.  Amplitude-only mixed evaluator (WSBM_MIXED_FINE): the FP64 evaluator with only
+// P - 1 and Q from the FP32 tables (relative error of H ~ 2e-8).
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -156,9 +158,38 @@ __device__ __forceinline__ void hk_pq(const HkTables& T, int zhi, double u, doub
   }
 }
 
+// P_nu - 1 and Q_nu from the FP32 tables (amplitude-only mixed precision, WSBM_MIXED_FINE):
+// the values are small corrections (|P - 1| ~ 1/(8z)^2, |Q| ~ 1/(8z)), so FP32 rounding of them
+// and the 2e-8 absolute error of the FP32 fits set the relative error of H; the phase factor
+// and everything after stay FP64.
+__device__ __forceinline__ void hk_pq_f32(const HkTables& T, int zhi, double u, double* pm0,
+                                          double* Q0, double* pm1, double* Q1) {
+  const float uf = (float)u;
+  float a, b, c, d;
+  if (zhi < HK_ASYM_HI) {
+    int iv = hk_interval_hi(zhi);
+    float s = (uf - T.ivf[iv][0]) * T.ivf[iv][1];
+    a = hk_hornerf<HKF_DEG + 1>(T.fitf[iv][0], s);
+    b = hk_hornerf<HKF_DEG + 1>(T.fitf[iv][1], s);
+    c = hk_hornerf<HKF_DEG + 1>(T.fitf[iv][2], s);
+    d = hk_hornerf<HKF_DEG + 1>(T.fitf[iv][3], s);
+  } else {
+    float s = (uf * uf - (float)HK_T_C) * (float)HK_T_IH;
+    a = hk_hornerf<HKF_DEG_T + 1>(T.asyf[0], s);
+    b = uf * hk_hornerf<HKF_DEG_T + 1>(T.asyf[1], s);
+    c = hk_hornerf<HKF_DEG_T + 1>(T.asyf[2], s);
+    d = uf * hk_hornerf<HKF_DEG_T + 1>(T.asyf[3], s);
+  }
+  *pm0 = (double)a;
+  *Q0 = (double)b;
+  *pm1 = (double)c;
+  *Q1 = (double)d;
+}
+
 // FP64 H0, H1 and (WITH_F1) F1 = H1/z + 2i/(pi z^2) at z > 0, given rs ~ 1/sqrt(z) to a few
-// ulp (callers derive it for both wavenumbers from one reciprocal square root).
-template <bool WITH_F1 = true>
+// ulp (callers derive it for both wavenumbers from one reciprocal square root).  PQ32: the
+// amplitude corrections P - 1, Q come from the FP32 tables (hk_pq_f32) for z >= 1.5.
+template <bool WITH_F1 = true, bool PQ32 = false>
 __device__ __forceinline__ void hankel_fp64_rs(const HkTables& T, double z, double rs, Hk& o) {
   double u = rs * rs;
   const int zhi = __double2hiint(z);
@@ -170,7 +201,10 @@ __device__ __forceinline__ void hankel_fp64_rs(const HkTables& T, double z, doub
   double E, F;
   hk_phase(T, z, &E, &F);
   double pm0, Q0, pm1, Q1;
-  hk_pq(T, zhi, u, &pm0, &Q0, &pm1, &Q1);
+  if (PQ32)
+    hk_pq_f32(T, zhi, u, &pm0, &Q0, &pm1, &Q1);
+  else
+    hk_pq(T, zhi, u, &pm0, &Q0, &pm1, &Q1);
   double P0 = fma(A, pm0, A), AQ0 = A * Q0;
   double P1 = fma(A, pm1, A), AQ1 = A * Q1;
   o.h0r = fma(P0, E, -AQ0 * F);

@@ -501,7 +501,8 @@ extern "C" int wsbm_create(const wsbm_geom* g, const wsbm_params* p, void* strea
   Phys ph;
   if ((rc = wsbm_phys_from_params(p, &ph))) return rc;
   if (p->leaf < 4 || p->nproxy < 8 || !(p->id_tol > 0.0) || !(p->id_tol < 1.0)) return WSBM_ERR_INVALID_ARG;
-  if (p->precision != WSBM_FP64 && p->precision != WSBM_MIXED) return WSBM_ERR_INVALID_ARG;
+  if (p->precision != WSBM_FP64 && p->precision != WSBM_MIXED && p->precision != WSBM_MIXED_FINE)
+    return WSBM_ERR_INVALID_ARG;
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev <= 0) return WSBM_ERR_NO_DEVICE;
   wsbm_hss* h = new wsbm_hss();
@@ -730,7 +731,7 @@ static int factor_levels(const std::vector<wsbm_hss*>& hs, const std::vector<int
   }
   // ---- entries: diagonal blocks (leaf) or sibling blocks (upper), near blocks, proxy blocks
   PairBatch pb;
-  ProxyBatch xb64, xbmx;  // FP64 and mixed-precision curves (one proxy launch each)
+  ProxyBatch xbp[3];  // per precision mode of the curves (one proxy launch each)
   std::vector<CopyDesc> copies;
   std::vector<int64_t> e_pairs(hs.size(), 0), e_proxy(hs.size(), 0);
   for (int r = 0; r < NB; ++r) {
@@ -752,7 +753,7 @@ static int factor_levels(const std::vector<wsbm_hss*>& hs, const std::vector<int
     // row ID matrix (stored transposed: rows = near columns) and column ID matrix
     e_pairs[i] += pb.add(i, at, B.cr, 0, NC[r], 2 * B.P, Mr[r], mr[r], 1);
     e_pairs[i] += pb.add(i, at, NR[r], 2 * B.P, B.cc, 0, Mc[r], mc[r], 0);
-    ProxyBatch& xb = h->prm.precision == WSBM_MIXED ? xbmx : xb64;
+    ProxyBatch& xb = xbp[h->prm.precision];
     e_proxy[i] += xb.add(i, at, B.cr, B, 0, Mr[r], mr[r]);
     e_proxy[i] += xb.add(i, at, B.cc, B, 1, Mc[r], mc[r]);
   }
@@ -765,14 +766,12 @@ static int factor_levels(const std::vector<wsbm_hss*>& hs, const std::vector<int
     wsbm_count_launch();
   }
   HK(pb.prepare(h0, tmp));
-  HK(xb64.prepare(h0, tmp));
-  HK(xbmx.prepare(h0, tmp));
+  for (auto& xb : xbp) HK(xb.prepare(h0, tmp));
   // timed: the entry kernels only
   HC(cudaEventRecord(h0->ev[0], st));
   HK(pb.run(h0, ia.geos, ia.phys));
   HC(cudaEventRecord(h0->ev[4], st));
-  HK(xb64.run(h0, 0, ia.geos, ia.phys));
-  HK(xbmx.run(h0, 1, ia.geos, ia.phys));
+  for (int m = 0; m < 3; ++m) HK(xbp[m].run(h0, m, ia.geos, ia.phys));
   HC(cudaEventRecord(h0->ev[1], st));
   for (size_t i = 0; i < hs.size(); ++i) {
     hs[i]->stats.entries_generated += e_pairs[i] + e_proxy[i];
@@ -781,9 +780,9 @@ static int factor_levels(const std::vector<wsbm_hss*>& hs, const std::vector<int
   }
   // pair counts are kept per launch; a single curve owns them all
   if (hs.size() == 1) {
-    h0->stats.pairs_evaluated += pb.pairs + xb64.pairs + xbmx.pairs;
+    h0->stats.pairs_evaluated += pb.pairs + xbp[0].pairs + xbp[1].pairs + xbp[2].pairs;
     h0->stats.pairs_pairs += pb.pairs;
-    h0->stats.pairs_proxy += xb64.pairs + xbmx.pairs;
+    h0->stats.pairs_proxy += xbp[0].pairs + xbp[1].pairs + xbp[2].pairs;
   }
   // ---- interpolative decompositions: CPQR of Mr (row ID) and Mc (column ID) of every box
   std::vector<QrDesc> qd(2 * NB);

@@ -148,3 +148,6 @@ def test_proxy_blocks_match_oracle(N, lo, hi, P):
         mixed = gpu_proxy(c, ph, side, box, circ, P, precision=1)
         rel = np.linalg.norm(mixed - ref) / np.linalg.norm(ref)
         assert rel < 1e-6, (side, rel)
+        fine = gpu_proxy(c, ph, side, box, circ, P, precision=2)
+        rel = np.linalg.norm(fine - ref) / np.linalg.norm(ref)
+        assert rel < 5e-8, (side, rel)

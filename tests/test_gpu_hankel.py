@@ -50,6 +50,22 @@ def test_mixed_hankel_within_fp32_bound():
     assert e.max() < 1e-6, (z[np.argmax(e)], e.max())
 
 
+def test_mixed_fine_hankel_within_fp32_table_bound():
+    """Amplitude-only mixed evaluation: FP32 P - 1, Q (fits to 2.1e-8 absolute), everything else
+    FP64; the series region (z < 1.5) is the FP64 evaluator unchanged."""
+    from paper_2607_00790_gb300 import binding
+    z = sample_z(3)
+    h0, h1, f1 = device_hankel(z, binding.WSBM_MIXED_FINE)
+    r0, r1 = oracle.hankel01(z)
+    e = np.maximum(np.abs(h0 - r0) / np.abs(r0), np.abs(h1 - r1) / np.abs(r1))
+    big = z >= 1.5
+    assert e[big].max() < 5e-8, (z[big][np.argmax(e[big])], e[big].max())
+    assert e[~big].max() < 3e-15
+    rf = oracle.f1(z)
+    ef = np.abs(f1 - rf) / np.abs(rf)
+    assert ef[big].max() < 2e-7 and ef[~big].max() < 3e-15
+
+
 def test_hankel_empty_and_deterministic():
     import torch
     from paper_2607_00790_gb300 import binding

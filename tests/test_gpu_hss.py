@@ -102,6 +102,21 @@ def test_mixed_precision_vs_fp64_path():
     assert rel(fmx, f64) < 1e-5, rel(fmx, f64)
 
 
+def test_mixed_fine_reaches_fp64_accuracy_at_tight_tolerance():
+    """Amplitude-only mixed precision at ID tol 1e-7: far field within 10x tol of the dense
+    oracle (the FP32 noise of WSBM_MIXED, ~1e-7, would not allow it)."""
+    c = inputs.star(1536)
+    prm = dict(k0=inputs.k0_for_density(c), n=1.5, leaf=64, nproxy=64, tol=1e-7)
+    ph = oracle.Physics(prm["k0"], n=prm["n"])
+    ang = 2 * np.pi * np.arange(360) / 360
+    s = gpu_solver(c, prm, precision=2)
+    _, u, q = solve_gpu(s, [0.0, 1.0])
+    ff = farfield_gpu(s, u, q, ang)
+    _, ud, qd = dense_reference(c, ph, [0.0, 1.0])
+    ffd = oracle.farfield(c, ph, ud, qd, ang)
+    assert rel(ff, ffd) < 10 * prm["tol"], rel(ff, ffd)
+
+
 def test_single_box_tree():
     c = inputs.star(48)
     prm = dict(k0=3.0, n=1.5, leaf=64, nproxy=16, tol=1e-10)
