@@ -183,7 +183,9 @@ int wsbm_factor(wsbm_hss_t h);
 int wsbm_rhs_planewave(wsbm_hss_t h, const double* angles, int32_t nang, void* rhs);
 
 /* Solve A [u; q] = rhs with the factors.  rhs: device complex128 2N x nrhs (paper order);
- * u, q: device complex128 N x nrhs each.  Errors: NOT_FACTORED, OOM, CUDA. */
+ * u, q: device complex128 N x nrhs each.  The first call with a given nrhs builds a solve plan
+ * (work buffers, descriptors) and captures its launches into a CUDA graph; later calls with the
+ * same nrhs replay it.  Synchronous.  Errors: NOT_FACTORED, OOM, CUDA. */
 int wsbm_solve(wsbm_hss_t h, const void* rhs, int32_t nrhs, void* u, void* q);
 
 /* Transposed solve A^T lam = rhs with the same factors (the adjoint solve of a gradient).
@@ -242,6 +244,17 @@ int wsbm_batch_factor(wsbm_batch_t b);
 /* Handle of curve i (owned by the batch: use it for rhs / solve / far field / stats, do not
  * destroy it). */
 int wsbm_batch_handle(wsbm_batch_t b, int32_t i, wsbm_hss_t* out);
+
+/* Solve every curve of a factored batch: rhs[i] (device complex128 2N_i x nrhs, paper order),
+ * u[i], q[i] (device complex128 N_i x nrhs); rhs, u, q are host arrays of `count` device
+ * pointers.  All curves go through one solve plan: each phase of a tree step is one launch over
+ * the boxes of every curve (levels aligned at the leaves), the roots are one batched LU solve,
+ * and the whole launch sequence is captured into a CUDA graph on the first call with a given
+ * nrhs and replayed by later calls (wsbm_solve uses the same plan machinery for one curve).
+ * The plan's buffers and descriptors stay allocated until the next factorization, a call with
+ * another nrhs, or destruction.  Synchronous.  Errors: NOT_FACTORED, INVALID_ARG, OOM, CUDA. */
+int wsbm_batch_solve(wsbm_batch_t b, const void* const* rhs, int32_t nrhs, void* const* u,
+                     void* const* q);
 
 /* Timings of the shared launches and summed counters of the last wsbm_batch_factor. */
 int wsbm_batch_stats(wsbm_batch_t b, wsbm_stats_t* s);

@@ -92,6 +92,9 @@ def lib():
         L.wsbm_batch_factor.argtypes = [vp]
         L.wsbm_batch_handle.argtypes = [vp, i32, ctypes.POINTER(vp)]
         L.wsbm_batch_stats.argtypes = [vp, ctypes.POINTER(Stats)]
+        L.wsbm_batch_solve.argtypes = [vp, ctypes.POINTER(vp), i32, ctypes.POINTER(vp),
+                                       ctypes.POINTER(vp)]
+        L.wsbm_batch_solve.restype = ctypes.c_int
         L.wsbm_batch_destroy.argtypes = [vp]
         L.wsbm_batch_destroy.restype = None
         G, P = ctypes.POINTER(Geom), ctypes.POINTER(Params)
@@ -419,6 +422,17 @@ class Batch:
         s = Stats()
         _check(lib().wsbm_batch_stats(self.h, ctypes.byref(s)), "wsbm_batch_stats")
         return s.as_dict()
+
+    def solve(self, rhs_list):
+        """Solve every curve at once; rhs_list[i]: 2N_i x nrhs complex128.  Returns [(u, q)]."""
+        n = len(self.sizes)
+        nrhs = rhs_list[0].shape[1]
+        rc = [r.T.contiguous() for r in rhs_list]
+        us = [torch.empty((nrhs, N), dtype=torch.complex128, device=self.device) for N in self.sizes]
+        qs = [torch.empty((nrhs, N), dtype=torch.complex128, device=self.device) for N in self.sizes]
+        arr = lambda ts: (ctypes.c_void_p * n)(*[t.data_ptr() for t in ts])
+        _check(lib().wsbm_batch_solve(self.h, arr(rc), nrhs, arr(us), arr(qs)), "wsbm_batch_solve")
+        return [(u.T, q.T) for u, q in zip(us, qs)]
 
     def close(self):
         if self.h:

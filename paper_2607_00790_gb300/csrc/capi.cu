@@ -8,6 +8,7 @@
 
 static std::atomic<int64_t> g_launches{0};
 void wsbm_count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+void wsbm_count_launches(int64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 int64_t wsbm_launch_count() { return g_launches.load(std::memory_order_relaxed); }
 
 extern "C" const char* wsbm_strerror(int code) {

@@ -7,6 +7,7 @@
 
 // Kernel-launch counter of the library (every launch site calls wsbm_count_launch()).
 void wsbm_count_launch();
+void wsbm_count_launches(int64_t n);  // launches replayed from a captured CUDA graph
 int64_t wsbm_launch_count();
 
 // C = alpha * op(A) * B + beta * C  (column-major, op(A) m x k, B k x n, C m x n);

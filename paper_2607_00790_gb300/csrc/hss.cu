@@ -25,6 +25,8 @@
 #include <string.h>
 
 #include <algorithm>
+#include <functional>
+#include <memory>
 #include <unordered_map>
 #include <vector>
 
@@ -86,6 +88,7 @@ struct wsbm_hss {
   std::vector<void*> owned;  // factor allocations
   wsbm_stats_t stats;
   cudaEvent_t ev[6];
+  std::shared_ptr<struct SolvePlan> plan;  // solve plan of the last nrhs (see wsbm_solve)
 };
 
 // ---------------------------------------------------------------- small kernels ----
@@ -580,6 +583,7 @@ extern "C" int wsbm_create(const wsbm_geom* g, const wsbm_params* p, void* strea
 }
 
 static void release_factors(wsbm_hss* h) {
+  h->plan.reset();  // a solve plan refers to the factors
   free_list(h, h->owned);
   for (auto& l : h->lv) l.compressed = false;
   for (auto& l : h->lv)
@@ -601,10 +605,8 @@ static void release_factors(wsbm_hss* h) {
 
 extern "C" void wsbm_destroy(wsbm_hss_t h) {
   if (!h) return;
-  if (h->st || true) {
-    release_factors(h);
-    cudaStreamSynchronize(h->st);
-  }
+  release_factors(h);
+  cudaStreamSynchronize(h->st);
   double* arr[6] = {h->x, h->y, h->nx, h->ny, h->w, h->kappa};
   for (double* a : arr)
     if (a) cudaFree(a);
@@ -1294,6 +1296,7 @@ extern "C" int wsbm_factor(wsbm_hss_t h) {
 struct wsbm_batch {
   std::vector<wsbm_hss*> hs;
   wsbm_stats_t stats;
+  std::shared_ptr<struct SolvePlan> plan;
 };
 
 extern "C" int wsbm_batch_create(const wsbm_geom* g, const wsbm_params* p, int32_t count,
@@ -1317,6 +1320,7 @@ extern "C" int wsbm_batch_create(const wsbm_geom* g, const wsbm_params* p, int32
 
 extern "C" int wsbm_batch_factor(wsbm_batch_t b) {
   if (!b || b->hs.empty()) return WSBM_ERR_INVALID_ARG;
+  b->plan.reset();
   return factor_all(b->hs, &b->stats);
 }
 
@@ -1334,310 +1338,461 @@ extern "C" int wsbm_batch_stats(wsbm_batch_t b, wsbm_stats_t* s) {
 
 extern "C" void wsbm_batch_destroy(wsbm_batch_t b) {
   if (!b) return;
+  b->plan.reset();
   for (auto* h : b->hs) wsbm_destroy(h);
   delete b;
 }
 
 // ----------------------------------------------------------------------- solve ----
+// Batched layout conversions (one CTA row per handle).
+struct ConvDesc {
+  const double2* in;
+  double2 *out, *out2;
+  int64_t N;
+};
+__global__ void k_to_interleaved_batched(const ConvDesc* __restrict__ d, int nrhs) {
+  const ConvDesc c = d[blockIdx.y];
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < 2 * c.N * nrhs;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    int64_t r = e % (2 * c.N), col = e / (2 * c.N);
+    int64_t node = r % c.N, comp = r / c.N;
+    c.out[2 * node + comp + col * 2 * c.N] = c.in[e];
+  }
+}
+__global__ void k_split_uq_batched(const ConvDesc* __restrict__ d, int nrhs) {
+  const ConvDesc c = d[blockIdx.y];
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < c.N * nrhs;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    int64_t i = e % c.N, col = e / c.N;
+    c.out[e] = c.in[2 * i + col * 2 * c.N];
+    c.out2[e] = c.in[2 * i + 1 + col * 2 * c.N];
+  }
+}
+
+// A solve plan: for a set of factored handles (one stream) and a number of right-hand sides,
+// every work buffer and descriptor array of the Martinsson-Rokhlin solve is allocated and
+// uploaded once, and the launches are recorded as a list of operations:
+//   up sweep    xh = D^-1 b, g = xh[pc], r = g[0:k] + Tc g[k:n], bt = Dhat r
+//   roots       dense LU solves of the merged skeleton systems (one batched launch)
+//   down sweep  x = xh - Z (bt - Dhat y)
+// Tree levels of different handles are aligned at their leaves (as in the batched factor), so
+// each phase of a tree step is one launch over every box of every handle.  On its first run the
+// list is captured into a CUDA graph; later runs replay the graph.  Right-hand sides enter and
+// solutions leave through the plan's own buffers (rin, uo, qo).
+struct SolvePlan {
+  std::vector<wsbm_hss*> hs;
+  int nrhs = 0;
+  cudaStream_t st = nullptr;  // the handles' stream (buffers are allocated in its order)
+  cudaStream_t cs = nullptr;  // the plan's own stream: capture and replay (a graph cannot be
+                              // captured on the legacy default stream)
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  std::vector<void*> mem;
+  std::vector<double2*> rin, uo, qo;
+  std::vector<std::function<int(cudaStream_t)>> ops;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  int64_t launches = 0;
+  bool graph_ok = true;
+  ~SolvePlan() {
+    if (cs) cudaStreamSynchronize(cs);
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    for (void* p : mem) cudaFreeAsync(p, st);
+    cudaStreamSynchronize(st);
+    if (ev_in) cudaEventDestroy(ev_in);
+    if (ev_out) cudaEventDestroy(ev_out);
+    if (cs) cudaStreamDestroy(cs);
+  }
+};
+
+template <class T>
+static int plan_upload(SolvePlan& P, const std::vector<T>& v, T** d) {
+  *d = nullptr;
+  if (v.empty()) return WSBM_OK;
+  if (cudaMallocAsync((void**)d, v.size() * sizeof(T), P.st) != cudaSuccess) return WSBM_ERR_OOM;
+  P.mem.push_back(*d);
+  if (cudaMemcpyAsync(*d, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, P.st) != cudaSuccess)
+    return WSBM_ERR_CUDA;
+  return WSBM_OK;
+}
+static int plan_alloc(SolvePlan& P, size_t bytes, double2** p) {
+  *p = nullptr;
+  if (cudaMallocAsync((void**)p, bytes ? bytes : 16, P.st) != cudaSuccess) return WSBM_ERR_OOM;
+  P.mem.push_back(*p);
+  return WSBM_OK;
+}
+
+static int plan_copies(SolvePlan& P, const std::vector<CopyDesc>& c) {
+  if (c.empty()) return WSBM_OK;
+  CopyDesc* d = nullptr;
+  HK(plan_upload(P, c, &d));
+  int64_t mx = 0;
+  for (auto& x : c) mx = std::max(mx, (int64_t)x.m * x.n);
+  const unsigned nb = (unsigned)c.size();
+  P.ops.push_back([d, mx, nb](cudaStream_t st) {
+    k_copy2d<<<dim3(gridfor(mx), nb), 256, 0, st>>>(d);
+    wsbm_count_launch();
+    return WSBM_OK;
+  });
+  return WSBM_OK;
+}
+static int plan_gemms(SolvePlan& P, const std::vector<GemmDesc>& g) {
+  if (g.empty()) return WSBM_OK;
+  GemmDesc* d = nullptr;
+  HK(plan_upload(P, g, &d));
+  int mm = 0, mn = 0;
+  for (auto& x : g) {
+    mm = std::max(mm, x.m);
+    mn = std::max(mn, x.n);
+  }
+  const int nb = (int)g.size();
+  P.ops.push_back([d, nb, mm, mn](cudaStream_t st) { return wsbm_gemm_batched(d, nb, mm, mn, st); });
+  return WSBM_OK;
+}
+static int plan_lu_solves(SolvePlan& P, const std::vector<TrsmDesc>& t) {
+  if (t.empty()) return WSBM_OK;
+  TrsmDesc* d = nullptr;
+  HK(plan_upload(P, t, &d));
+  int mn = 0, mr = 0;
+  for (auto& x : t) {
+    mn = std::max(mn, x.n);
+    mr = std::max(mr, x.nrhs);
+  }
+  const int nb = (int)t.size();
+  P.ops.push_back([d, nb, mn, mr](cudaStream_t st) { return wsbm_lu_solve_batched(d, d, nb, mn, mr, st); });
+  return WSBM_OK;
+}
+static int plan_gathers(SolvePlan& P, const std::vector<GatherDesc>& g) {
+  if (g.empty()) return WSBM_OK;
+  GatherDesc* d = nullptr;
+  HK(plan_upload(P, g, &d));
+  int64_t mx = 0;
+  for (auto& x : g) mx = std::max(mx, (int64_t)x.n * x.ncol);
+  const unsigned nb = (unsigned)g.size();
+  P.ops.push_back([d, mx, nb](cudaStream_t st) {
+    k_gather_rows<<<dim3(gridfor(mx), nb), 256, 0, st>>>(d);
+    wsbm_count_launch();
+    return WSBM_OK;
+  });
+  return WSBM_OK;
+}
+static TrsmDesc lu_desc(const double2* T, int64_t ldt, double2* B, int64_t ldb, const int32_t* piv,
+                        int n, int nrhs) {
+  TrsmDesc t;
+  memset(&t, 0, sizeof(t));
+  t.T = T;
+  t.ldt = ldt;
+  t.B = B;
+  t.ldb = ldb;
+  t.piv = piv;
+  t.n = n;
+  t.nrhs = nrhs;
+  return t;
+}
+static GemmDesc gemm_n(const double2* A, int64_t lda, const double2* B, int64_t ldb, double2* C,
+                       int64_t ldc, int m, int n, int k, double alpha, double beta) {
+  GemmDesc g;
+  memset(&g, 0, sizeof(g));
+  g.A = A;
+  g.lda = lda;
+  g.B = B;
+  g.ldb = ldb;
+  g.C = C;
+  g.ldc = ldc;
+  g.m = m;
+  g.n = n;
+  g.k = k;
+  g.alpha = make_double2(alpha, 0.0);
+  g.beta = make_double2(beta, 0.0);
+  return g;
+}
+
+static int plan_build(SolvePlan& P) {
+  const int nrhs = P.nrhs;
+  const size_t NH = P.hs.size();
+  P.rin.resize(NH);
+  P.uo.resize(NH);
+  P.qo.resize(NH);
+  std::vector<double2*> bint(NH);
+  // per handle, per level: xh (n x nrhs), g (n x nrhs), bt (k x nrhs), r / t (k x nrhs)
+  std::vector<std::vector<std::vector<double2*>>> XH(NH), G(NH), BT(NH), RT(NH);
+  std::vector<double2*> Y(NH, nullptr);
+  int T = 0;
+  for (size_t i = 0; i < NH; ++i) {
+    wsbm_hss* h = P.hs[i];
+    const int64_t N = h->N;
+    HK(plan_alloc(P, (size_t)2 * N * nrhs * sizeof(double2), &P.rin[i]));
+    HK(plan_alloc(P, (size_t)N * nrhs * sizeof(double2), &P.uo[i]));
+    HK(plan_alloc(P, (size_t)N * nrhs * sizeof(double2), &P.qo[i]));
+    HK(plan_alloc(P, (size_t)2 * N * nrhs * sizeof(double2), &bint[i]));
+    if (h->L == 0) continue;
+    T = std::max(T, h->L - h->top + 1);
+    XH[i].resize(h->L + 1);
+    G[i].resize(h->L + 1);
+    BT[i].resize(h->L + 1);
+    RT[i].resize(h->L + 1);
+    for (int l = h->L; l >= h->top; --l) {
+      Level& LV = h->lv[l];
+      size_t tn = 0, tk = 0;
+      for (auto& b : LV.box) {
+        tn += b.n;
+        tk += b.k;
+      }
+      double2 *xh, *g, *bt, *rt;
+      HK(plan_alloc(P, tn * nrhs * sizeof(double2), &xh));
+      HK(plan_alloc(P, tn * nrhs * sizeof(double2), &g));
+      HK(plan_alloc(P, tk * nrhs * sizeof(double2), &bt));
+      HK(plan_alloc(P, tk * nrhs * sizeof(double2), &rt));
+      size_t on = 0, ok = 0;
+      for (auto& b : LV.box) {
+        XH[i][l].push_back(xh + on * nrhs);
+        G[i][l].push_back(g + on * nrhs);
+        BT[i][l].push_back(bt + ok * nrhs);
+        RT[i][l].push_back(rt + ok * nrhs);
+        on += b.n;
+        ok += b.k;
+      }
+    }
+    HK(plan_alloc(P, (size_t)h->root_n * nrhs * sizeof(double2), &Y[i]));
+  }
+  // paper order -> interleaved
+  {
+    std::vector<ConvDesc> cv;
+    int64_t mx = 0;
+    for (size_t i = 0; i < NH; ++i) {
+      cv.push_back({P.rin[i], bint[i], nullptr, P.hs[i]->N});
+      mx = std::max(mx, 2 * P.hs[i]->N * nrhs);
+    }
+    ConvDesc* d = nullptr;
+    HK(plan_upload(P, cv, &d));
+    const unsigned nb = (unsigned)cv.size();
+    P.ops.push_back([d, mx, nb, nrhs](cudaStream_t st) {
+      k_to_interleaved_batched<<<dim3(gridfor(mx), nb), 256, 0, st>>>(d, nrhs);
+      wsbm_count_launch();
+      return WSBM_OK;
+    });
+  }
+  // ---- up sweep, tree step t = 0 at the leaves of every handle
+  for (int t = 0; t < T; ++t) {
+    std::vector<CopyDesc> c1, rc0;
+    std::vector<TrsmDesc> sd;
+    std::vector<GatherDesc> gd;
+    std::vector<GemmDesc> g1, g2;
+    for (size_t i = 0; i < NH; ++i) {
+      wsbm_hss* h = P.hs[i];
+      if (h->L == 0) continue;
+      const int l = h->L - t;
+      if (l < h->top) continue;
+      Level& LV = h->lv[l];
+      for (int b = 0; b < (int)LV.box.size(); ++b) {
+        Box& B = LV.box[b];
+        double2* xh = XH[i][l][b];
+        if (l == h->L) {
+          c1.push_back({xh, bint[i] + 2 * B.lo, B.n, 2 * h->N, B.n, nrhs});
+        } else {
+          Box& A1 = h->lv[l + 1].box[2 * b];
+          Box& A2 = h->lv[l + 1].box[2 * b + 1];
+          c1.push_back({xh, BT[i][l + 1][2 * b], B.n, A1.k, A1.k, nrhs});
+          c1.push_back({xh + A1.k, BT[i][l + 1][2 * b + 1], B.n, A2.k, A2.k, nrhs});
+        }
+        sd.push_back(lu_desc(B.D, B.n, xh, B.n, B.piv, B.n, nrhs));
+        double2* gb = G[i][l][b];
+        double2* rb = RT[i][l][b];
+        gd.push_back({gb, xh, B.pc, B.n, B.n, B.n, nrhs});
+        rc0.push_back({rb, gb, B.k, B.n, B.k, nrhs});
+        if (B.n > B.k) g1.push_back(gemm_n(B.Tc, B.k, gb + B.k, B.n, rb, B.k, B.k, nrhs, B.n - B.k, 1.0, 1.0));
+        g2.push_back(gemm_n(B.Dc, B.k, rb, B.k, BT[i][l][b], B.k, B.k, nrhs, B.k, 1.0, 0.0));
+      }
+    }
+    HK(plan_copies(P, c1));
+    HK(plan_lu_solves(P, sd));
+    HK(plan_gathers(P, gd));
+    HK(plan_copies(P, rc0));
+    HK(plan_gemms(P, g1));
+    HK(plan_gemms(P, g2));
+  }
+  // ---- roots
+  {
+    std::vector<CopyDesc> c;
+    std::vector<TrsmDesc> rs;
+    for (size_t i = 0; i < NH; ++i) {
+      wsbm_hss* h = P.hs[i];
+      if (h->L == 0) {
+        rs.push_back(lu_desc(h->root, h->root_n, bint[i], 2 * h->N, h->root_piv, h->root_n, nrhs));
+        continue;
+      }
+      Level& TL = h->lv[h->top];
+      int off = 0;
+      for (int b = 0; b < (int)TL.box.size(); ++b) {
+        c.push_back({Y[i] + off, BT[i][h->top][b], h->root_n, TL.box[b].k, TL.box[b].k, nrhs});
+        off += TL.box[b].k;
+      }
+      rs.push_back(lu_desc(h->root, h->root_n, Y[i], h->root_n, h->root_piv, h->root_n, nrhs));
+    }
+    HK(plan_copies(P, c));
+    HK(plan_lu_solves(P, rs));
+  }
+  // ---- down sweep: t = bt - Dhat y (in RT), xh -= Z t; y of a box = its slice of the parent's x
+  for (int t = T - 1; t >= 0; --t) {
+    std::vector<CopyDesc> cb;
+    std::vector<GemmDesc> g1, g2;
+    for (size_t i = 0; i < NH; ++i) {
+      wsbm_hss* h = P.hs[i];
+      if (h->L == 0) continue;
+      const int l = h->L - t;
+      if (l < h->top) continue;
+      Level& LV = h->lv[l];
+      int yoff = 0;
+      for (int b = 0; b < (int)LV.box.size(); ++b) {
+        Box& B = LV.box[b];
+        const double2* yb;
+        int64_t ldy;
+        if (l == h->top) {
+          yb = Y[i] + yoff;
+          ldy = h->root_n;
+          yoff += B.k;
+        } else {
+          Box& Pb = h->lv[l - 1].box[b / 2];
+          yb = XH[i][l - 1][b / 2] + ((b % 2) ? LV.box[b - 1].k : 0);
+          ldy = Pb.n;
+        }
+        double2* tt = RT[i][l][b];
+        cb.push_back({tt, BT[i][l][b], B.k, B.k, B.k, nrhs});
+        g1.push_back(gemm_n(B.Dc, B.k, yb, ldy, tt, B.k, B.k, nrhs, B.k, -1.0, 1.0));
+        g2.push_back(gemm_n(B.Z, B.n, tt, B.k, XH[i][l][b], B.n, B.n, nrhs, B.k, -1.0, 1.0));
+      }
+    }
+    HK(plan_copies(P, cb));
+    HK(plan_gemms(P, g1));
+    HK(plan_gemms(P, g2));
+  }
+  // ---- leaves back to the interleaved vector, then u, q
+  {
+    std::vector<CopyDesc> c;
+    std::vector<ConvDesc> cv;
+    int64_t mx = 0;
+    for (size_t i = 0; i < NH; ++i) {
+      wsbm_hss* h = P.hs[i];
+      if (h->L > 0) {
+        Level& LV = h->lv[h->L];
+        for (int b = 0; b < (int)LV.box.size(); ++b)
+          c.push_back({bint[i] + 2 * LV.box[b].lo, XH[i][h->L][b], 2 * h->N, LV.box[b].n, LV.box[b].n, nrhs});
+      }
+      cv.push_back({bint[i], P.uo[i], P.qo[i], h->N});
+      mx = std::max(mx, h->N * nrhs);
+    }
+    HK(plan_copies(P, c));
+    ConvDesc* d = nullptr;
+    HK(plan_upload(P, cv, &d));
+    const unsigned nb = (unsigned)cv.size();
+    P.ops.push_back([d, mx, nb, nrhs](cudaStream_t st) {
+      k_split_uq_batched<<<dim3(gridfor(mx), nb), 256, 0, st>>>(d, nrhs);
+      wsbm_count_launch();
+      return WSBM_OK;
+    });
+  }
+  return cudaGetLastError() == cudaSuccess ? WSBM_OK : WSBM_ERR_CUDA;
+}
+
+static int plan_exec(SolvePlan& P) {
+  cudaStream_t st = P.cs;
+  if (P.graph_ok && !P.exec) {
+    const int64_t c0 = wsbm_launch_count();
+    bool ok = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+    int rc = WSBM_OK;
+    if (ok)
+      for (auto& op : P.ops)
+        if ((rc = op(st)) != WSBM_OK) break;
+    cudaGraph_t g = nullptr;
+    if (ok) ok = cudaStreamEndCapture(st, &g) == cudaSuccess && rc == WSBM_OK && g != nullptr;
+    if (ok) ok = cudaGraphInstantiate(&P.exec, g, 0) == cudaSuccess;
+    P.launches = wsbm_launch_count() - c0;
+    if (ok) {
+      P.graph = g;
+    } else {
+      if (g) cudaGraphDestroy(g);
+      P.exec = nullptr;
+      P.graph_ok = false;
+      cudaGetLastError();  // clear a capture error; run the operations directly instead
+    }
+    wsbm_count_launches(-P.launches);  // counted again when they run
+  }
+  if (P.exec) {
+    HC(cudaGraphLaunch(P.exec, st));
+    wsbm_count_launches(P.launches);
+    return WSBM_OK;
+  }
+  for (auto& op : P.ops) HK(op(st));
+  return cudaGetLastError() == cudaSuccess ? WSBM_OK : WSBM_ERR_CUDA;
+}
+
+// Run the plan on its own stream, ordered after everything already queued on the handles'
+// stream and before anything queued there later: capture its operations into a CUDA graph on
+// the first run, replay the graph after (or run the operations directly if capture failed).
+static int plan_run(SolvePlan& P) {
+  HC(cudaEventRecord(P.ev_in, P.st));
+  HC(cudaStreamWaitEvent(P.cs, P.ev_in, 0));
+  HK(plan_exec(P));
+  HC(cudaEventRecord(P.ev_out, P.cs));
+  HC(cudaStreamWaitEvent(P.st, P.ev_out, 0));
+  return WSBM_OK;
+}
+
+static int plan_get(std::shared_ptr<SolvePlan>& slot, const std::vector<wsbm_hss*>& hs, int nrhs) {
+  if (slot && slot->nrhs == nrhs && slot->hs == hs) return WSBM_OK;
+  slot.reset();
+  auto P = std::make_shared<SolvePlan>();
+  P->hs = hs;
+  P->nrhs = nrhs;
+  P->st = hs[0]->st;
+  if (cudaStreamCreateWithFlags(&P->cs, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&P->ev_in, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&P->ev_out, cudaEventDisableTiming) != cudaSuccess)
+    return WSBM_ERR_CUDA;
+  int rc = plan_build(*P);
+  if (rc != WSBM_OK) return rc;
+  slot = P;
+  return WSBM_OK;
+}
+
+// Solves of several handles (paper-order right-hand sides in, u and q out) with one plan.
+static int solve_set(std::shared_ptr<SolvePlan>& slot, const std::vector<wsbm_hss*>& hs,
+                     const void* const* rhs, int32_t nrhs, void* const* u, void* const* q) {
+  HK(plan_get(slot, hs, nrhs));
+  SolvePlan& P = *slot;
+  cudaStream_t st = P.st;
+  for (size_t i = 0; i < hs.size(); ++i)
+    HC(cudaMemcpyAsync(P.rin[i], rhs[i], (size_t)2 * hs[i]->N * nrhs * sizeof(double2),
+                       cudaMemcpyDeviceToDevice, st));
+  HK(plan_run(P));
+  for (size_t i = 0; i < hs.size(); ++i) {
+    const size_t bytes = (size_t)hs[i]->N * nrhs * sizeof(double2);
+    HC(cudaMemcpyAsync(u[i], P.uo[i], bytes, cudaMemcpyDeviceToDevice, st));
+    HC(cudaMemcpyAsync(q[i], P.qo[i], bytes, cudaMemcpyDeviceToDevice, st));
+  }
+  HC(cudaStreamSynchronize(st));
+  return WSBM_OK;
+}
+
 extern "C" int wsbm_solve(wsbm_hss_t h, const void* rhs, int32_t nrhs, void* u, void* q) {
   if (!h) return WSBM_ERR_INVALID_ARG;
   if (!h->factored) return WSBM_ERR_NOT_FACTORED;
   if (nrhs < 0 || (nrhs > 0 && (!rhs || !u || !q))) return WSBM_ERR_INVALID_ARG;
   if (nrhs == 0) return WSBM_OK;
-  cudaStream_t st = h->st;
-  std::vector<void*> tmp;
-  const int64_t N = h->N;
-  double2* bint = nullptr;
-  HK(dalloc(h, (size_t)2 * N * nrhs * sizeof(double2), (void**)&bint, tmp));
-  k_to_interleaved<<<gridfor(2 * N * nrhs), 256, 0, st>>>((const double2*)rhs, bint, N, nrhs);
-  wsbm_count_launch();
-  if (h->L == 0) {
-    TrsmDesc t;
-    memset(&t, 0, sizeof(t));
-    t.T = h->root;
-    t.ldt = h->root_n;
-    t.B = bint;
-    t.ldb = 2 * N;
-    t.piv = h->root_piv;
-    t.n = h->root_n;
-    t.nrhs = nrhs;
-    std::vector<TrsmDesc> v(1, t);
-    TrsmDesc* dt = nullptr;
-    HK(upload(h, v, &dt, tmp));
-    HK(wsbm_lu_solve_batched(dt, dt, 1, h->root_n, nrhs, st));
-    k_split_uq<<<gridfor(N * nrhs), 256, 0, st>>>(bint, (double2*)u, (double2*)q, N, nrhs);
-    wsbm_count_launch();
-    HC(cudaStreamSynchronize(st));
-    free_list(h, tmp);
-    return WSBM_OK;
-  }
-  // per level buffers: bv (n x nrhs), xh (n x nrhs), bt (k x nrhs)
-  const int L = h->L, top = h->top;
-  std::vector<std::vector<double2*>> BV(L + 1), XH(L + 1), BT(L + 1);
-  for (int l = L; l >= top; --l) {
-    Level& LV = h->lv[l];
-    int nb = (int)LV.box.size();
-    BV[l].resize(nb);
-    XH[l].resize(nb);
-    BT[l].resize(nb);
-    size_t tn = 0, tk = 0;
-    for (auto& b : LV.box) {
-      tn += b.n;
-      tk += b.k;
-    }
-    double2 *bv = nullptr, *xh = nullptr, *bt = nullptr;
-    HK(dalloc(h, tn * nrhs * sizeof(double2), (void**)&bv, tmp));
-    HK(dalloc(h, tn * nrhs * sizeof(double2), (void**)&xh, tmp));
-    HK(dalloc(h, tk * nrhs * sizeof(double2), (void**)&bt, tmp));
-    size_t on = 0, ok = 0;
-    for (int b = 0; b < nb; ++b) {
-      BV[l][b] = bv + on * nrhs;
-      XH[l][b] = xh + on * nrhs;
-      BT[l][b] = bt + ok * nrhs;
-      on += LV.box[b].n;
-      ok += LV.box[b].k;
-    }
-  }
-  int maxn = 0, maxk = 0;
-  for (int l = top; l <= L; ++l)
-    for (auto& b : h->lv[l].box) {
-      maxn = std::max(maxn, b.n);
-      maxk = std::max(maxk, b.k);
-    }
-  // ---- upward sweep
-  for (int l = L; l >= top; --l) {
-    Level& LV = h->lv[l];
-    int nb = (int)LV.box.size();
-    // bv = leaf rows of the right-hand side, or the children's bt; then xh = bv
-    std::vector<CopyDesc> c1, c2;
-    for (int b = 0; b < nb; ++b) {
-      Box& B = LV.box[b];
-      if (l == L) {
-        c1.push_back({BV[l][b], bint + 2 * B.lo, B.n, 2 * N, B.n, nrhs});
-      } else {
-        Box& A1 = h->lv[l + 1].box[2 * b];
-        Box& A2 = h->lv[l + 1].box[2 * b + 1];
-        c1.push_back({BV[l][b], BT[l + 1][2 * b], B.n, A1.k, A1.k, nrhs});
-        c1.push_back({BV[l][b] + A1.k, BT[l + 1][2 * b + 1], B.n, A2.k, A2.k, nrhs});
-      }
-      c2.push_back({XH[l][b], BV[l][b], B.n, B.n, B.n, nrhs});
-    }
-    CopyDesc *d1 = nullptr, *d2 = nullptr;
-    HK(upload(h, c1, &d1, tmp));
-    HK(upload(h, c2, &d2, tmp));
-    k_copy2d<<<dim3(gridfor((int64_t)maxn * nrhs), (unsigned)c1.size()), 256, 0, st>>>(d1);
-    wsbm_count_launch();
-    k_copy2d<<<dim3(gridfor((int64_t)maxn * nrhs), (unsigned)c2.size()), 256, 0, st>>>(d2);
-    wsbm_count_launch();
-    // xh = D^-1 bv
-    std::vector<TrsmDesc> sd;
-    for (int b = 0; b < nb; ++b) {
-      Box& B = LV.box[b];
-      TrsmDesc t;
-      memset(&t, 0, sizeof(t));
-      t.T = B.D;
-      t.ldt = B.n;
-      t.B = XH[l][b];
-      t.ldb = B.n;
-      t.piv = B.piv;
-      t.n = B.n;
-      t.nrhs = nrhs;
-      sd.push_back(t);
-    }
-    TrsmDesc* dsd = nullptr;
-    HK(upload(h, sd, &dsd, tmp));
-    int ln = 0;
-    for (auto& b : LV.box) ln = std::max(ln, b.n);
-    HK(wsbm_lu_solve_batched(dsd, dsd, nb, ln, nrhs, st));
-    // bt = Dhat (R xh):  g = xh[pc]; r = g[0:k] + Tc g[k:n]; bt = Dhat r
-    size_t tn = 0, tk = 0;
-    for (auto& b : LV.box) {
-      tn += b.n;
-      tk += b.k;
-    }
-    double2 *g = nullptr, *r = nullptr;
-    HK(dalloc(h, tn * nrhs * sizeof(double2), (void**)&g, tmp));
-    HK(dalloc(h, tk * nrhs * sizeof(double2), (void**)&r, tmp));
-    std::vector<GatherDesc> gd;
-    std::vector<CopyDesc> rc0;
-    std::vector<GemmDesc> g1, g2;
-    size_t on = 0, ok = 0;
-    int lk = 0;
-    for (int b = 0; b < nb; ++b) {
-      Box& B = LV.box[b];
-      double2* gb = g + on * nrhs;
-      double2* rb = r + ok * nrhs;
-      on += B.n;
-      ok += B.k;
-      lk = std::max(lk, B.k);
-      gd.push_back({gb, XH[l][b], B.pc, B.n, B.n, B.n, nrhs});
-      rc0.push_back({rb, gb, B.k, B.n, B.k, nrhs});
-      if (B.n > B.k) {
-        GemmDesc a;
-        memset(&a, 0, sizeof(a));
-        a.A = B.Tc;
-        a.lda = B.k;
-        a.B = gb + B.k;
-        a.ldb = B.n;
-        a.C = rb;
-        a.ldc = B.k;
-        a.m = B.k;
-        a.n = nrhs;
-        a.k = B.n - B.k;
-        a.alpha = make_double2(1.0, 0.0);
-        a.beta = make_double2(1.0, 0.0);
-        g1.push_back(a);
-      }
-      GemmDesc c;
-      memset(&c, 0, sizeof(c));
-      c.A = B.Dc;
-      c.lda = B.k;
-      c.B = rb;
-      c.ldb = B.k;
-      c.C = BT[l][b];
-      c.ldc = B.k;
-      c.m = B.k;
-      c.n = nrhs;
-      c.k = B.k;
-      c.alpha = make_double2(1.0, 0.0);
-      c.beta = make_double2(0.0, 0.0);
-      g2.push_back(c);
-    }
-    GatherDesc* dgd = nullptr;
-    CopyDesc* drc = nullptr;
-    GemmDesc *dg1 = nullptr, *dg2 = nullptr;
-    HK(upload(h, gd, &dgd, tmp));
-    HK(upload(h, rc0, &drc, tmp));
-    HK(upload(h, g1, &dg1, tmp));
-    HK(upload(h, g2, &dg2, tmp));
-    k_gather_rows<<<dim3(gridfor((int64_t)ln * nrhs), nb), 256, 0, st>>>(dgd);
-    wsbm_count_launch();
-    k_copy2d<<<dim3(gridfor((int64_t)lk * nrhs), nb), 256, 0, st>>>(drc);
-    wsbm_count_launch();
-    if (!g1.empty()) HK(wsbm_gemm_batched(dg1, (int)g1.size(), lk, nrhs, st));
-    HK(wsbm_gemm_batched(dg2, nb, lk, nrhs, st));
-  }
-  // ---- root
-  double2* y = nullptr;
-  HK(dalloc(h, (size_t)h->root_n * nrhs * sizeof(double2), (void**)&y, tmp));
-  {
-    Level& T = h->lv[top];
-    std::vector<CopyDesc> c;
-    int off = 0;
-    for (int b = 0; b < (int)T.box.size(); ++b) {
-      c.push_back({y + off, BT[top][b], h->root_n, T.box[b].k, T.box[b].k, nrhs});
-      off += T.box[b].k;
-    }
-    CopyDesc* dc = nullptr;
-    HK(upload(h, c, &dc, tmp));
-    k_copy2d<<<dim3(gridfor((int64_t)maxk * nrhs), (unsigned)c.size()), 256, 0, st>>>(dc);
-    wsbm_count_launch();
-    TrsmDesc t;
-    memset(&t, 0, sizeof(t));
-    t.T = h->root;
-    t.ldt = h->root_n;
-    t.B = y;
-    t.ldb = h->root_n;
-    t.piv = h->root_piv;
-    t.n = h->root_n;
-    t.nrhs = nrhs;
-    std::vector<TrsmDesc> v(1, t);
-    TrsmDesc* dt = nullptr;
-    HK(upload(h, v, &dt, tmp));
-    HK(wsbm_lu_solve_batched(dt, dt, 1, h->root_n, nrhs, st));
-  }
-  // ---- downward sweep: x = xh - Z (bt - Dhat y); y of a box = its slice of the parent's x
-  std::vector<std::vector<double2*>> X(L + 1);
-  for (int l = top; l <= L; ++l) {
-    Level& LV = h->lv[l];
-    int nb = (int)LV.box.size();
-    X[l].resize(nb);
-    std::vector<GemmDesc> g1, g2;
-    size_t tk = 0;
-    for (auto& b : LV.box) tk += b.k;
-    double2* tb = nullptr;
-    HK(dalloc(h, tk * nrhs * sizeof(double2), (void**)&tb, tmp));
-    std::vector<CopyDesc> cb;
-    size_t ok = 0;
-    int lk = 0, ln = 0;
-    int yoff = 0;
-    for (int b = 0; b < nb; ++b) {
-      Box& B = LV.box[b];
-      const double2* yb;
-      int64_t ldy;
-      if (l == top) {
-        yb = y + yoff;
-        ldy = h->root_n;
-        yoff += B.k;
-      } else {
-        Box& P = h->lv[l - 1].box[b / 2];
-        yb = X[l - 1][b / 2] + ((b % 2) ? h->lv[l].box[b - 1].k : 0);
-        ldy = P.n;
-      }
-      double2* t = tb + ok * nrhs;
-      ok += B.k;
-      lk = std::max(lk, B.k);
-      ln = std::max(ln, B.n);
-      cb.push_back({t, BT[l][b], B.k, B.k, B.k, nrhs});
-      GemmDesc a;  // t = bt - Dhat y
-      memset(&a, 0, sizeof(a));
-      a.A = B.Dc;
-      a.lda = B.k;
-      a.B = yb;
-      a.ldb = ldy;
-      a.C = t;
-      a.ldc = B.k;
-      a.m = B.k;
-      a.n = nrhs;
-      a.k = B.k;
-      a.alpha = make_double2(-1.0, 0.0);
-      a.beta = make_double2(1.0, 0.0);
-      g1.push_back(a);
-      GemmDesc z;  // xh -= Z t
-      memset(&z, 0, sizeof(z));
-      z.A = B.Z;
-      z.lda = B.n;
-      z.B = t;
-      z.ldb = B.k;
-      z.C = XH[l][b];
-      z.ldc = B.n;
-      z.m = B.n;
-      z.n = nrhs;
-      z.k = B.k;
-      z.alpha = make_double2(-1.0, 0.0);
-      z.beta = make_double2(1.0, 0.0);
-      g2.push_back(z);
-      X[l][b] = XH[l][b];
-    }
-    CopyDesc* dcb = nullptr;
-    GemmDesc *dg1 = nullptr, *dg2 = nullptr;
-    HK(upload(h, cb, &dcb, tmp));
-    HK(upload(h, g1, &dg1, tmp));
-    HK(upload(h, g2, &dg2, tmp));
-    k_copy2d<<<dim3(gridfor((int64_t)lk * nrhs), nb), 256, 0, st>>>(dcb);
-    wsbm_count_launch();
-    HK(wsbm_gemm_batched(dg1, nb, lk, nrhs, st));
-    HK(wsbm_gemm_batched(dg2, nb, ln, nrhs, st));
-  }
-  // leaves: x (interleaved, per box contiguous) -> bint -> u, q
-  {
-    Level& LV = h->lv[L];
-    std::vector<CopyDesc> c;
-    for (int b = 0; b < (int)LV.box.size(); ++b) {
-      Box& B = LV.box[b];
-      c.push_back({bint + 2 * B.lo, X[L][b], 2 * N, B.n, B.n, nrhs});
-    }
-    CopyDesc* dc = nullptr;
-    HK(upload(h, c, &dc, tmp));
-    k_copy2d<<<dim3(gridfor((int64_t)maxn * nrhs), (unsigned)c.size()), 256, 0, st>>>(dc);
-    wsbm_count_launch();
-    k_split_uq<<<gridfor(N * nrhs), 256, 0, st>>>(bint, (double2*)u, (double2*)q, N, nrhs);
-    wsbm_count_launch();
-  }
-  HC(cudaGetLastError());
-  HC(cudaStreamSynchronize(st));
-  free_list(h, tmp);
-  return WSBM_OK;
+  std::vector<wsbm_hss*> hs(1, h);
+  return solve_set(h->plan, hs, &rhs, nrhs, &u, &q);
+}
+
+extern "C" int wsbm_batch_solve(wsbm_batch_t b, const void* const* rhs, int32_t nrhs,
+                                void* const* u, void* const* q) {
+  if (!b || b->hs.empty()) return WSBM_ERR_INVALID_ARG;
+  for (auto* h : b->hs)
+    if (!h->factored) return WSBM_ERR_NOT_FACTORED;
+  if (nrhs < 0 || (nrhs > 0 && (!rhs || !u || !q))) return WSBM_ERR_INVALID_ARG;
+  if (nrhs == 0) return WSBM_OK;
+  for (size_t i = 0; i < b->hs.size(); ++i)
+    if (!rhs[i] || !u[i] || !q[i]) return WSBM_ERR_INVALID_ARG;
+  return solve_set(b->plan, b->hs, rhs, nrhs, u, q);
 }
 
 // Transposed solve A^T lam = v with the same factors.  For A ~ D + L A~ R (per level) the

@@ -68,3 +68,24 @@ def test_batch_equals_individual_and_dense():
     ffd = oracle.farfield(c, ph, ud, qd, obs)
     assert np.linalg.norm(ff - ffd) / np.linalg.norm(ffd) < 10 * d["tol"]
     b.close()
+
+
+def test_batch_solve_equals_individual_solves_and_replays():
+    """wsbm_batch_solve (one plan, shared launches per tree step, captured CUDA graph) gives
+    exactly the per-curve solves, also on a second call (graph replay) with new right-hand
+    sides; curves of different depth, including a root-only one, are mixed."""
+    import torch
+    from paper_2607_00790_gb300 import binding
+    ms = members()
+    geoms = [binding.make_geom(c) for c, _ in ms]
+    b = binding.Batch([g for g, _ in geoms], [params(binding, d) for _, d in ms])
+    b.factor()
+    rng = np.random.default_rng(5)
+    for call in range(2):
+        rhs = [torch.as_tensor(rng.normal(size=(2 * g.n, 3)) + 1j * rng.normal(size=(2 * g.n, 3)),
+                               device="cuda") for g, _ in geoms]
+        got = b.solve(rhs)
+        for i in range(len(ms)):
+            u, q = b.solver(i).solve(rhs[i])
+            assert torch.equal(got[i][0], u) and torch.equal(got[i][1], q), (call, i)
+    b.close()
