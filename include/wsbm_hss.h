@@ -102,6 +102,8 @@ typedef struct {
   int64_t pairs_pairs;         /* node pairs it evaluated                              */
   double ms_pairs;             /* its summed device time                              */
   int64_t launches;            /* kernels launched by the last wsbm_factor            */
+  double ms_cpqr;              /* summed device time of the column-pivoted QR launches */
+  int64_t cpqr_matrices;       /* ID matrices they factored                           */
 } wsbm_stats_t;
 
 typedef struct wsbm_hss* wsbm_hss_t;

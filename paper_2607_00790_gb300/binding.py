@@ -54,7 +54,8 @@ class Stats(ctypes.Structure):
                 ("entries_proxy", ctypes.c_int64), ("pairs_proxy", ctypes.c_int64),
                 ("ms_proxy", ctypes.c_double), ("entries_pairs", ctypes.c_int64),
                 ("pairs_pairs", ctypes.c_int64), ("ms_pairs", ctypes.c_double),
-                ("launches", ctypes.c_int64)]
+                ("launches", ctypes.c_int64), ("ms_cpqr", ctypes.c_double),
+                ("cpqr_matrices", ctypes.c_int64)]
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_ if k != "rank_per_level"}

@@ -87,7 +87,7 @@ struct wsbm_hss {
   bool factored = false;
   std::vector<void*> owned;  // factor allocations
   wsbm_stats_t stats;
-  cudaEvent_t ev[6];
+  cudaEvent_t ev[8];
   std::shared_ptr<struct SolvePlan> plan;  // solve plan of the last nrhs (see wsbm_solve)
 };
 
@@ -517,7 +517,7 @@ extern "C" int wsbm_create(const wsbm_geom* g, const wsbm_params* p, void* strea
   if (!(h->prm.proxy_ratio > 1.0)) h->prm.proxy_ratio = 1.5;
   h->cut = p->id_tol / 4.0;
   memset(&h->stats, 0, sizeof(h->stats));
-  for (int i = 0; i < 6; ++i) cudaEventCreate(&h->ev[i]);
+  for (int i = 0; i < 8; ++i) cudaEventCreate(&h->ev[i]);
   size_t bytes = (size_t)h->N * sizeof(double);
   double** dst[6] = {&h->x, &h->y, &h->nx, &h->ny, &h->w, &h->kappa};
   const double* src[6] = {g->x, g->y, g->nx, g->ny, g->w, g->kappa};
@@ -610,7 +610,7 @@ extern "C" void wsbm_destroy(wsbm_hss_t h) {
   double* arr[6] = {h->x, h->y, h->nx, h->ny, h->w, h->kappa};
   for (double* a : arr)
     if (a) cudaFree(a);
-  for (int i = 0; i < 6; ++i)
+  for (int i = 0; i < 8; ++i)
     if (h->ev[i]) cudaEventDestroy(h->ev[i]);
   delete h;
 }
@@ -645,7 +645,7 @@ static int upload_instances(wsbm_hss* h0, const std::vector<wsbm_hss*>& hs, Inst
 // launch over all boxes of all items (entries, proxy blocks, IDs, LU, D^-1 L, Dhat).  All
 // handles share one stream.  Candidates (cr, cc) of every box must be set.
 static int factor_levels(const std::vector<wsbm_hss*>& hs, const std::vector<int>& levels,
-                         double ms_out[4]) {
+                         double ms_out[5], int64_t* cpqr_mats) {
   wsbm_hss* h0 = hs[0];
   cudaStream_t st = h0->st;
   std::vector<void*> tmp;
@@ -827,7 +827,10 @@ static int factor_levels(const std::vector<wsbm_hss*>& hs, const std::vector<int
   });
   QrDesc* dq = nullptr;
   HK(upload(h0, qs, &dq, tmp));
+  HC(cudaEventRecord(h0->ev[5], st));
   HK(wsbm_cpqr_batched(dq, 2 * NB, 0, st));
+  HC(cudaEventRecord(h0->ev[6], st));
+  *cpqr_mats = 2 * (int64_t)NB;
   std::vector<int32_t> hstate(4 * NB);
   HC(cudaMemcpyAsync(hstate.data(), state, hstate.size() * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
   HC(cudaStreamSynchronize(st));
@@ -1029,6 +1032,7 @@ static int factor_levels(const std::vector<wsbm_hss*>& hs, const std::vector<int
   ms_out[1] = elapsed(h0->ev[0], h0->ev[4]);
   ms_out[2] = elapsed(h0->ev[1], h0->ev[2]);
   ms_out[3] = elapsed(h0->ev[2], h0->ev[3]);
+  ms_out[4] = elapsed(h0->ev[5], h0->ev[6]);
   // skeletons
   {
     size_t on = 0;
@@ -1148,7 +1152,8 @@ static int factor_all(const std::vector<wsbm_hss*>& hs, wsbm_stats_t* bstats) {
   cudaEventCreate(&t1);
   cudaEventRecord(t0, h0->st);
   const int64_t launches0 = wsbm_launch_count();
-  double ms[4] = {0, 0, 0, 0};  // entries, pair kernel, IDs, factor
+  double ms[5] = {0, 0, 0, 0, 0};  // entries, pair kernel, IDs, factor, CPQR
+  int64_t cpqr_mats = 0;
   std::vector<int> level(hs.size(), 0), done(hs.size(), 0);
   std::vector<char> partial(hs.size(), 0);
   int rc = WSBM_OK;
@@ -1176,10 +1181,12 @@ static int factor_all(const std::vector<wsbm_hss*>& hs, wsbm_stats_t* bstats) {
     bool any = false;
     for (int l : level) any = any || l >= 1;
     if (!any) break;
-    double m4[4];
-    rc = factor_levels(hs, level, m4);
+    double m4[5];
+    int64_t nq = 0;
+    rc = factor_levels(hs, level, m4, &nq);
     if (rc) break;
-    for (int a = 0; a < 4; ++a) ms[a] += m4[a];
+    for (int a = 0; a < 5; ++a) ms[a] += m4[a];
+    cpqr_mats += nq;
     for (size_t i = 0; i < hs.size(); ++i) {
       if (level[i] < 1) continue;
       wsbm_hss* h = hs[i];
@@ -1253,6 +1260,8 @@ static int factor_all(const std::vector<wsbm_hss*>& hs, wsbm_stats_t* bstats) {
       h->stats.ms_factor = ms[3] + mr2[1];
       h->stats.ms_total_factor = total;
       h->stats.launches = launches;
+      h->stats.ms_cpqr = ms[4];
+      h->stats.cpqr_matrices = cpqr_mats;
     }
     size_t bytes = 0;
     for (int l = h->top; l <= h->L && h->L > 0; ++l)
@@ -1282,6 +1291,8 @@ static int factor_all(const std::vector<wsbm_hss*>& hs, wsbm_stats_t* bstats) {
     bstats->ms_factor = ms[3] + mr2[1];
     bstats->ms_total_factor = total;
     bstats->launches = launches;
+    bstats->ms_cpqr = ms[4];
+    bstats->cpqr_matrices = cpqr_mats;
   }
   return rc;
 }
