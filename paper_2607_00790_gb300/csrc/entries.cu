@@ -56,6 +56,9 @@ __global__ void __launch_bounds__(WSBM_PAIR_THREADS)
   __shared__ HkTables T;
   __shared__ SlotData sf[WSBM_TILE_F];
   __shared__ SlotData ss[WSBM_TILE_S];
+  __shared__ int s_cnt[WSBM_PAIR_THREADS / 32][3];
+  __shared__ int16_t s_list[WSBM_PAIR_THREADS];
+  __shared__ int s_ntot;
   hk_stage_tables(&T);
   const int tx = threadIdx.x & (WSBM_TILE_F - 1);
   const int ty = threadIdx.x / WSBM_TILE_F;
@@ -92,10 +95,59 @@ __global__ void __launch_bounds__(WSBM_PAIR_THREADS)
       }
     }
     __syncthreads();
-    const int f = f0 + tx, s = s0 + ty;
-    if (f < nf && s < ns) {
-      const SlotData& R = fc ? ss[ty] : sf[tx];
-      const SlotData& C = fc ? sf[tx] : ss[ty];
+    // Group the tile's pairs by evaluation path before evaluating them: far pairs (both
+    // Hankel arguments on the large-argument branch), near pairs (at least one ascending
+    // series) and diagonal pairs (one-point correction).  Threads then take pairs from the
+    // grouped list, so a warp mixes paths only at a group boundary instead of wherever the
+    // diagonal band crosses the tile.  (The grouping only orders work; any pair may be
+    // evaluated by any thread.)
+    int cls = 3;  // 3: outside the task
+    {
+      const int f = f0 + tx, s = s0 + ty;
+      if (f < nf && s < ns) {
+        const SlotData& R = fc ? ss[ty] : sf[tx];
+        const SlotData& C = fc ? sf[tx] : ss[ty];
+        if (R.node == C.node) {
+          cls = 2;
+        } else {
+          // near: min(k0, k1) r < HK_Z_SERIES, compared on r^2 (no square root)
+          const double dx = R.x - C.x, dy = R.y - C.y;
+          const double rz = HK_Z_SERIES / fmin(ph.k0, ph.k1);
+          cls = fma(dx, dx, dy * dy) < rz * rz ? 1 : 0;
+        }
+      }
+    }
+    {
+      const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+      const unsigned lt = (1u << lane) - 1u;
+      unsigned bal[3];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        bal[c] = __ballot_sync(0xffffffffu, cls == c);
+        if (lane == 0) s_cnt[warp][c] = __popc(bal[c]);
+      }
+      __syncthreads();
+      int base = 0, pos = -1;
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        int before = 0, total = 0;
+#pragma unroll
+        for (int w = 0; w < WSBM_PAIR_THREADS / 32; ++w) {
+          total += s_cnt[w][c];
+          if (w < warp) before += s_cnt[w][c];
+        }
+        if (cls == c) pos = base + before + __popc(bal[c] & lt);
+        base += total;
+      }
+      if (pos >= 0) s_list[pos] = (int16_t)threadIdx.x;
+      if (threadIdx.x == 0) s_ntot = base;
+    }
+    __syncthreads();
+    if ((int)threadIdx.x < s_ntot) {
+      const int me = s_list[threadIdx.x];
+      const int mx = me & (WSBM_TILE_F - 1), my = me / WSBM_TILE_F;
+      const SlotData& R = fc ? ss[my] : sf[mx];
+      const SlotData& C = fc ? sf[mx] : ss[my];
       double2 e[2][2];
       if (R.node == C.node) {
         block_diag(ph, R.w, R.kap, e);
