@@ -112,7 +112,7 @@ __global__ void __launch_bounds__(WSBM_PAIR_THREADS)
         } else {
           // near: min(k0, k1) r < HK_Z_SERIES, compared on r^2 (no square root)
           const double dx = R.x - C.x, dy = R.y - C.y;
-          const double rz = HK_Z_SERIES / fmin(ph.k0, ph.k1);
+          const double rz = HK_Z_SERIES * fmax(ph.inv_k0, ph.inv_k1);
           cls = fma(dx, dx, dy * dy) < rz * rz ? 1 : 0;
         }
       }
