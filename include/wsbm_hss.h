@@ -71,7 +71,12 @@ typedef struct {
  *              WSBM_ERR_NOT_FACTORED
  *  root_cap    largest dense root order accepted (0 selects 40000); a factorization whose
  *              merged skeleton system would be larger fails with WSBM_ERR_RANK_OVERFLOW
+ *  id_method   WSBM_ID_SKETCH (0): leaf-level IDs from the column-pivoted QR of a tensor-core
+ *              sketch Omega M of the ID matrix (l = 16 ceil((n/2 + 32)/16) rows, used when M has
+ *              at least 1.5 l rows; a side whose rank comes within 16 of l is redone on M);
+ *              WSBM_ID_FULL (1): column-pivoted QR of the full ID matrices everywhere
  */
+enum { WSBM_ID_SKETCH = 0, WSBM_ID_FULL = 1 };
 typedef struct {
   double k0, refr_index, eps0, eps1;
   int32_t leaf, nproxy;
@@ -79,6 +84,7 @@ typedef struct {
   int32_t precision;
   double proxy_ratio;
   int32_t max_levels, root_cap;
+  int32_t id_method, pad;
 } wsbm_params;
 
 /* Counters of a handle. */
@@ -102,8 +108,12 @@ typedef struct {
   int64_t pairs_pairs;         /* node pairs it evaluated                              */
   double ms_pairs;             /* its summed device time                              */
   int64_t launches;            /* kernels launched by the last wsbm_factor            */
-  double ms_cpqr;              /* summed device time of the column-pivoted QR launches */
-  int64_t cpqr_matrices;       /* ID matrices they factored                           */
+  double ms_cpqr;              /* device time of the first column-pivoted QR launch   */
+  int64_t cpqr_matrices;       /* ID matrices it factored (sketches or full matrices) */
+  double cpqr_flops;           /* its algorithmic FP64 flops: 16 per element per step */
+  int64_t sketch_matrices;     /* ID matrices replaced by their sketch                */
+  int64_t sketch_fallbacks;    /* sketched sides redone on the full matrix            */
+  double ms_sketch;            /* device time of the sketch launches                  */
 } wsbm_stats_t;
 
 typedef struct wsbm_hss* wsbm_hss_t;
@@ -283,6 +293,17 @@ int wsbm_matvec(const wsbm_geom* g, const wsbm_params* p, int32_t trans, const v
 int wsbm_field(const wsbm_geom* g, const wsbm_params* p, const void* u, const void* q,
                int32_t nrhs, const double* tx, const double* ty, int64_t nt, void* out,
                int8_t* inside, void* stream);
+
+/* Randomized row sketch Y = Omega A on the tensor cores: A device complex128 m x n (column-
+ * major, lda >= m), Omega the l x m Rademacher matrix with entries +-1 (bit 0 of a counter-based
+ * hash of (row, column, seed)), Y device complex128 l x n (ldy >= l).  Products are formed
+ * exactly from 8-bit slices of the power-of-two scaled columns of A (BF16 mma with FP32
+ * accumulation), so Y carries a relative error of about 2^-41 of its column scale.  The HSS
+ * build uses it for the interpolative decompositions of the leaf level (no counterpart in the
+ * paper, which does not say how its IDs are computed).  l: multiple of 16 in [16, 256];
+ * m <= 65536.  Synchronous.  Errors: INVALID_ARG, OOM, CUDA. */
+int wsbm_sketch(const void* A, int64_t lda, int32_t m, int32_t n, int32_t l, void* Y, int64_t ldy,
+                uint32_t seed, void* stream);
 
 /* ---------------------------------------------------------------- gradients ----
  * Reverse-mode building blocks of shape and refractive-index gradients of a far-field loss

@@ -41,7 +41,7 @@ class Params(ctypes.Structure):
                 ("leaf", ctypes.c_int32), ("nproxy", ctypes.c_int32),
                 ("id_tol", ctypes.c_double), ("precision", ctypes.c_int32),
                 ("proxy_ratio", ctypes.c_double), ("max_levels", ctypes.c_int32),
-                ("root_cap", ctypes.c_int32)]
+                ("root_cap", ctypes.c_int32), ("id_method", ctypes.c_int32), ("pad", ctypes.c_int32)]
 
 
 class Stats(ctypes.Structure):
@@ -55,7 +55,9 @@ class Stats(ctypes.Structure):
                 ("ms_proxy", ctypes.c_double), ("entries_pairs", ctypes.c_int64),
                 ("pairs_pairs", ctypes.c_int64), ("ms_pairs", ctypes.c_double),
                 ("launches", ctypes.c_int64), ("ms_cpqr", ctypes.c_double),
-                ("cpqr_matrices", ctypes.c_int64)]
+                ("cpqr_matrices", ctypes.c_int64), ("cpqr_flops", ctypes.c_double),
+                ("sketch_matrices", ctypes.c_int64), ("sketch_fallbacks", ctypes.c_int64),
+                ("ms_sketch", ctypes.c_double)]
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_ if k != "rank_per_level"}
@@ -103,6 +105,8 @@ def lib():
         L.wsbm_matvec.argtypes = [G, P, i32, vp, i32, vp, vp]
         L.wsbm_matvec.restype = ctypes.c_int
         L.wsbm_field.argtypes = [G, P, vp, vp, i32, vp, vp, i64, vp, vp, vp]
+        L.wsbm_sketch.argtypes = [vp, i64, i32, i32, i32, vp, i64, ctypes.c_uint32, vp]
+        L.wsbm_sketch.restype = ctypes.c_int
         L.wsbm_field.restype = ctypes.c_int
         L.wsbm_entries_vjp.argtypes = [G, P, vp, vp, vp, vp, vp]
         L.wsbm_rhs_planewave_vjp.argtypes = [G, P, vp, i32, vp, vp, vp]
@@ -148,10 +152,15 @@ def make_geom(curve, device="cuda"):
     return g, t
 
 
+WSBM_ID_SKETCH = 0
+WSBM_ID_FULL = 1
+
+
 def make_params(k0, n, eps0=1.0, eps1=0.0, leaf=64, nproxy=64, id_tol=1e-10,
-                precision=WSBM_FP64, proxy_ratio=1.5, max_levels=0, root_cap=0):
+                precision=WSBM_FP64, proxy_ratio=1.5, max_levels=0, root_cap=0,
+                id_method=WSBM_ID_SKETCH):
     return Params(k0, n, eps0, eps1, leaf, nproxy, id_tol, precision, proxy_ratio, max_levels,
-                  root_cap)
+                  root_cap, id_method, 0)
 
 
 # ---------------------------------------------------------------- stateless calls ----
@@ -194,6 +203,17 @@ def wsbm_matvec(geom, params, x, trans=False):
                              _dev(xc, torch.complex128), xc.shape[0], _dev(y, torch.complex128),
                              _stream(dev)), "wsbm_matvec")
     return y[0] if one else y.T
+
+
+def wsbm_sketch(A, l, seed=0):
+    """Y = Omega A (l x n) for a complex128 matrix A (m x n), Omega Rademacher +-1."""
+    dev = A.device
+    Ac = A.T.contiguous()  # column-major storage of A
+    m, n = A.shape
+    Y = torch.empty((n, l), dtype=torch.complex128, device=dev)
+    _check(lib().wsbm_sketch(_dev(Ac, torch.complex128), m, m, n, l, _dev(Y, torch.complex128), l,
+                             seed, _stream(dev)), "wsbm_sketch")
+    return Y.T
 
 
 def field(geom, params, u, q, tx, ty):

@@ -506,6 +506,7 @@ extern "C" int wsbm_create(const wsbm_geom* g, const wsbm_params* p, void* strea
   if (p->leaf < 4 || p->nproxy < 8 || !(p->id_tol > 0.0) || !(p->id_tol < 1.0)) return WSBM_ERR_INVALID_ARG;
   if (p->precision != WSBM_FP64 && p->precision != WSBM_MIXED && p->precision != WSBM_MIXED_FINE)
     return WSBM_ERR_INVALID_ARG;
+  if (p->id_method != WSBM_ID_SKETCH && p->id_method != WSBM_ID_FULL) return WSBM_ERR_INVALID_ARG;
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev <= 0) return WSBM_ERR_NO_DEVICE;
   wsbm_hss* h = new wsbm_hss();
@@ -645,7 +646,8 @@ static int upload_instances(wsbm_hss* h0, const std::vector<wsbm_hss*>& hs, Inst
 // launch over all boxes of all items (entries, proxy blocks, IDs, LU, D^-1 L, Dhat).  All
 // handles share one stream.  Candidates (cr, cc) of every box must be set.
 static int factor_levels(const std::vector<wsbm_hss*>& hs, const std::vector<int>& levels,
-                         double ms_out[5], int64_t* cpqr_mats) {
+                         double ms_out[5], int64_t* cpqr_mats, double* cpqr_flops,
+                         int64_t sketch_out[2], double* sketch_ms) {
   wsbm_hss* h0 = hs[0];
   cudaStream_t st = h0->st;
   std::vector<void*> tmp;
@@ -786,7 +788,59 @@ static int factor_levels(const std::vector<wsbm_hss*>& hs, const std::vector<int
     h0->stats.pairs_pairs += pb.pairs;
     h0->stats.pairs_proxy += xbp[0].pairs + xbp[1].pairs + xbp[2].pairs;
   }
+  // ---- randomized sketches of the leaf-level ID matrices (tensor cores): Y = Omega M with
+  // l = 16 ceil((n/2 + 32)/16) rows, where M has at least 1.5 l rows
+  std::vector<int> lsk(2 * NB, 0);
+  std::vector<double2*> Ysk(2 * NB, nullptr);
+  {
+    size_t Ytot = 0;
+    int maxl = 0, maxnn = 0;
+    for (int r = 0; r < NB; ++r) {
+      wsbm_hss* h = R[r].h;
+      Box& B = R[r].box();
+      if (h->prm.id_method != WSBM_ID_SKETCH || R[r].l != h->L || B.n < 64) continue;
+      const int l = 16 * ((B.n / 2 + 32 + 15) / 16);
+      for (int s2 = 0; s2 < 2; ++s2) {
+        const int64_t m = s2 == 0 ? mr[r] : mc[r];
+        if (l > 256 || m < (3 * (int64_t)l) / 2 || m > 65536) continue;
+        lsk[2 * r + s2] = l;
+        Ytot += (size_t)l * B.n;
+        maxl = std::max(maxl, l);
+        maxnn = std::max(maxnn, B.n);
+      }
+    }
+    if (Ytot) {
+      double2* Yall = nullptr;
+      HK(dalloc(h0, Ytot * sizeof(double2), (void**)&Yall, tmp));
+      const size_t dsz = wsbm_sketch_desc_size();
+      std::vector<unsigned char> sd;
+      size_t oY = 0;
+      int nsk = 0;
+      for (int r = 0; r < NB; ++r)
+        for (int s2 = 0; s2 < 2; ++s2) {
+          const int l = lsk[2 * r + s2];
+          if (!l) continue;
+          Box& B = R[r].box();
+          Ysk[2 * r + s2] = Yall + oY;
+          oY += (size_t)l * B.n;
+          sd.resize(sd.size() + dsz);
+          const int64_t m = s2 == 0 ? mr[r] : mc[r];
+          wsbm_sketch_desc_fill(sd.data() + (size_t)nsk * dsz, s2 == 0 ? Mr[r] : Mc[r], m,
+                                Ysk[2 * r + s2], l, (int32_t)m, B.n, l);
+          ++nsk;
+        }
+      unsigned char* dsd = nullptr;
+      HK(upload(h0, sd, &dsd, tmp));
+      HC(cudaEventRecord(h0->ev[5], st));
+      HK(wsbm_sketch_batched(dsd, nsk, maxnn, maxl, 0x5eed1234u, st));
+      HC(cudaEventRecord(h0->ev[7], st));
+      sketch_out[0] += nsk;
+      HC(cudaEventSynchronize(h0->ev[7]));
+      sketch_ms[0] += elapsed(h0->ev[5], h0->ev[7]);
+    }
+  }
   // ---- interpolative decompositions: CPQR of Mr (row ID) and Mc (column ID) of every box
+  // (or of their sketches)
   std::vector<QrDesc> qd(2 * NB);
   int32_t *perm = nullptr, *state = nullptr;
   double *norm2 = nullptr, *nref = nullptr, *tauv = nullptr, *rd0 = nullptr;
@@ -805,8 +859,13 @@ static int factor_levels(const std::vector<wsbm_hss*>& hs, const std::vector<int
       for (int s = 0; s < 2; ++s) {
         QrDesc& q = qd[2 * r + s];
         memset(&q, 0, sizeof(q));
-        q.A = s == 0 ? Mr[r] : Mc[r];
-        q.lda = s == 0 ? mr[r] : mc[r];
+        if (lsk[2 * r + s]) {
+          q.A = Ysk[2 * r + s];
+          q.lda = lsk[2 * r + s];
+        } else {
+          q.A = s == 0 ? Mr[r] : Mc[r];
+          q.lda = s == 0 ? mr[r] : mc[r];
+        }
         q.m = (int32_t)q.lda;
         q.n = R[r].box().n;
         q.tol = R[r].h->cut;
@@ -834,6 +893,50 @@ static int factor_levels(const std::vector<wsbm_hss*>& hs, const std::vector<int
   std::vector<int32_t> hstate(4 * NB);
   HC(cudaMemcpyAsync(hstate.data(), state, hstate.size() * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
   HC(cudaStreamSynchronize(st));
+  // algorithmic flops of that launch: 16 per element per reflection step (complex dot and
+  // update of the trailing columns) plus the initial column norms
+  for (int r = 0; r < NB; ++r)
+    for (int s = 0; s < 2; ++s) {
+      const QrDesc& q = qd[2 * r + s];
+      const int k = hstate[4 * r + 2 * s + 1];
+      double f = 4.0 * q.m * q.n;
+      for (int j = 0; j < k; ++j) f += 16.0 * (double)(q.m - j) * (double)(q.n - j - 1);
+      cpqr_flops[0] += f;
+    }
+  // a sketched side must leave room for the rank of both sides (the row and column IDs share
+  // k): redo it on the full matrix when its rank, or the box's rank, comes within 16 of l
+  for (int pass = 0; pass < 2; ++pass) {
+    std::vector<QrDesc> redo;
+    std::vector<int> which;
+    for (int r = 0; r < NB; ++r) {
+      const int k = std::max(hstate[4 * r + 1], hstate[4 * r + 3]);
+      for (int s = 0; s < 2; ++s) {
+        const int l = lsk[2 * r + s];
+        if (!l || k + 16 <= l) continue;
+        QrDesc& q = qd[2 * r + s];
+        q.A = s == 0 ? Mr[r] : Mc[r];
+        q.lda = s == 0 ? mr[r] : mc[r];
+        q.m = (int32_t)q.lda;
+        lsk[2 * r + s] = 0;
+        redo.push_back(q);
+        which.push_back(2 * r + s);
+      }
+    }
+    if (redo.empty()) break;
+    sketch_out[1] += (int64_t)redo.size();
+    for (int w : which)  // restart these QRs from step 0 (the others keep their resume state)
+      HC(cudaMemsetAsync(state + 2 * w, 0, 2 * sizeof(int32_t), st));
+    QrDesc* dr = nullptr;
+    HK(upload(h0, redo, &dr, tmp));
+    HK(wsbm_cpqr_batched(dr, (int)redo.size(), 0, st));
+    std::vector<int32_t> hs2(4 * NB);
+    HC(cudaMemcpyAsync(hs2.data(), state, hs2.size() * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    HC(cudaStreamSynchronize(st));
+    for (int w : which) {
+      hstate[2 * w] = hs2[2 * w];
+      hstate[2 * w + 1] = hs2[2 * w + 1];
+    }
+  }
   std::vector<QrDesc> more;
   for (int r = 0; r < NB; ++r) {
     Box& B = R[r].box();
@@ -855,7 +958,11 @@ static int factor_levels(const std::vector<wsbm_hss*>& hs, const std::vector<int
     HK(upload(h0, more, &dm, tmp));
     HK(wsbm_cpqr_batched(dm, (int)more.size(), 1, st));
   }
-  HK(wsbm_cpqr_finish(dq, 2 * NB, st));
+  {
+    QrDesc* dfin = nullptr;  // the final descriptors (sketched sides may have been redone on M)
+    HK(upload(h0, qd, &dfin, tmp));
+    HK(wsbm_cpqr_finish(dfin, 2 * NB, st));
+  }
   // T = R11^-1 R12 in place (both sides)
   {
     std::vector<TrsmDesc> td;
@@ -1154,6 +1261,8 @@ static int factor_all(const std::vector<wsbm_hss*>& hs, wsbm_stats_t* bstats) {
   const int64_t launches0 = wsbm_launch_count();
   double ms[5] = {0, 0, 0, 0, 0};  // entries, pair kernel, IDs, factor, CPQR
   int64_t cpqr_mats = 0;
+  double cpqr_flops = 0.0, ms_sketch = 0.0;
+  int64_t sketch_cnt[2] = {0, 0};  // sketched ID matrices, redone on the full matrix
   std::vector<int> level(hs.size(), 0), done(hs.size(), 0);
   std::vector<char> partial(hs.size(), 0);
   int rc = WSBM_OK;
@@ -1183,7 +1292,7 @@ static int factor_all(const std::vector<wsbm_hss*>& hs, wsbm_stats_t* bstats) {
     if (!any) break;
     double m4[5];
     int64_t nq = 0;
-    rc = factor_levels(hs, level, m4, &nq);
+    rc = factor_levels(hs, level, m4, &nq, &cpqr_flops, sketch_cnt, &ms_sketch);
     if (rc) break;
     for (int a = 0; a < 5; ++a) ms[a] += m4[a];
     cpqr_mats += nq;
@@ -1262,6 +1371,10 @@ static int factor_all(const std::vector<wsbm_hss*>& hs, wsbm_stats_t* bstats) {
       h->stats.launches = launches;
       h->stats.ms_cpqr = ms[4];
       h->stats.cpqr_matrices = cpqr_mats;
+      h->stats.cpqr_flops = cpqr_flops;
+      h->stats.sketch_matrices = sketch_cnt[0];
+      h->stats.sketch_fallbacks = sketch_cnt[1];
+      h->stats.ms_sketch = ms_sketch;
     }
     size_t bytes = 0;
     for (int l = h->top; l <= h->L && h->L > 0; ++l)
@@ -1293,6 +1406,10 @@ static int factor_all(const std::vector<wsbm_hss*>& hs, wsbm_stats_t* bstats) {
     bstats->launches = launches;
     bstats->ms_cpqr = ms[4];
     bstats->cpqr_matrices = cpqr_mats;
+    bstats->cpqr_flops = cpqr_flops;
+    bstats->sketch_matrices = sketch_cnt[0];
+    bstats->sketch_fallbacks = sketch_cnt[1];
+    bstats->ms_sketch = ms_sketch;
   }
   return rc;
 }
