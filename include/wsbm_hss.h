@@ -300,7 +300,7 @@ int wsbm_field(const wsbm_geom* g, const wsbm_params* p, const void* u, const vo
  * exactly from 8-bit slices of the power-of-two scaled columns of A (BF16 mma with FP32
  * accumulation), so Y carries a relative error of about 2^-41 of its column scale.  The HSS
  * build uses it for the interpolative decompositions of the leaf level (no counterpart in the
- * paper, which does not say how its IDs are computed).  l: multiple of 16 in [16, 256];
+ * paper, which does not say how its IDs are computed).  l: multiple of 16 in [16, 192];
  * m <= 65536.  Synchronous.  Errors: INVALID_ARG, OOM, CUDA. */
 int wsbm_sketch(const void* A, int64_t lda, int32_t m, int32_t n, int32_t l, void* Y, int64_t ldy,
                 uint32_t seed, void* stream);

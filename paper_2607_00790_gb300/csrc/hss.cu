@@ -802,7 +802,7 @@ static int factor_levels(const std::vector<wsbm_hss*>& hs, const std::vector<int
       const int l = 16 * ((B.n / 2 + 32 + 15) / 16);
       for (int s2 = 0; s2 < 2; ++s2) {
         const int64_t m = s2 == 0 ? mr[r] : mc[r];
-        if (l > 256 || m < (3 * (int64_t)l) / 2 || m > 65536) continue;
+        if (l > 192 || m < (3 * (int64_t)l) / 2 || m > 65536) continue;
         lsk[2 * r + s2] = l;
         Ytot += (size_t)l * B.n;
         maxl = std::max(maxl, l);

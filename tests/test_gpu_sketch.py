@@ -21,7 +21,7 @@ def omega(l, m, seed):
     return np.where(h & np.uint64(1), -1.0, 1.0)
 
 
-@pytest.mark.parametrize("m,n,l,seed", [(382, 256, 160, 0), (37, 13, 16, 7), (1000, 9, 48, 3),
+@pytest.mark.parametrize("m,n,l,seed", [(382, 256, 160, 0), (37, 13, 16, 7), (1000, 9, 48, 3), (500, 40, 192, 9),
                                         (16, 8, 16, 1)])
 def test_sketch_matches_numpy(m, n, l, seed):
     import torch
