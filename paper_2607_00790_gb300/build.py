@@ -17,7 +17,7 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # host code: no FMA contraction, so host-side geometry (proxy circles) rounds the same on
 # x86 and Arm hosts
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
-              "-Xcompiler", "-ffp-contract=off", "--expt-relaxed-constexpr"]
+              "-Xcompiler", "-ffp-contract=off", "-Xcompiler", "-fopenmp", "--expt-relaxed-constexpr"]
 
 
 def nvcc():
@@ -42,7 +42,7 @@ def build(verbose=False):
 
     with ThreadPoolExecutor(max_workers=min(8, len(srcs))) as ex:
         list(ex.map(one, zip(srcs, objs)))
-    cmd = [nvcc(), *ARCH, "-shared", "-o", LIB, *objs]
+    cmd = [nvcc(), *ARCH, "-shared", "-o", LIB, *objs, "-lgomp"]
     subprocess.run(cmd, check=True)
     return LIB
 

@@ -324,6 +324,18 @@ static void free_list(wsbm_hss* h, std::vector<void*>& list) {
 
 // Slots (node, two output positions) for a list of interleaved unknowns placed at output
 // positions base + t.  `at` is a per-node scratch array holding -1 on entry and on exit.
+// Per-thread node scratch for make_slots in parallel host loops (holds -1 between uses).
+static std::vector<int32_t>& thread_slot_scratch(int64_t n) {
+  static thread_local std::vector<int32_t> at;
+  if ((int64_t)at.size() < n) at.assign((size_t)n, -1);
+  return at;
+}
+
+// Slots of one unknown list (node ids and the positions of their two components).
+struct Slots {
+  std::vector<int32_t> nodes, pos;
+};
+
 static void make_slots(const std::vector<int32_t>& U, int base, std::vector<int32_t>& nodes,
                        std::vector<int32_t>& pos, std::vector<int32_t>& at) {
   for (size_t t = 0; t < U.size(); ++t) {
@@ -357,9 +369,17 @@ struct PairBatch {
   int64_t add(int inst, std::vector<int32_t>& at, const std::vector<int32_t>& rowU, int rbase,
               const std::vector<int32_t>& colU, int cbase, double2* out, int64_t ld, int trans) {
     if (rowU.empty() || colU.empty()) return 0;
-    std::vector<int32_t> rn, rp, cn, cp;
-    make_slots(rowU, rbase, rn, rp, at);
-    make_slots(colU, cbase, cn, cp, at);
+    Slots R, C;
+    make_slots(rowU, rbase, R.nodes, R.pos, at);
+    make_slots(colU, cbase, C.nodes, C.pos, at);
+    return add_slots(inst, R, C, (int64_t)rowU.size() * colU.size(), out, ld, trans);
+  }
+
+  // the same with the slots already made (entries = |rowU| |colU|)
+  int64_t add_slots(int inst, const Slots& R, const Slots& C, int64_t e, double2* out, int64_t ld,
+                    int trans) {
+    if (e == 0) return 0;
+    const std::vector<int32_t>&rn = R.nodes, &rp = R.pos, &cn = C.nodes, &cp = C.pos;
     Ref r;
     r.rn = (int64_t)ints.size();
     ints.insert(ints.end(), rn.begin(), rn.end());
@@ -383,7 +403,6 @@ struct PairBatch {
     // equal lengths the one that gives contiguous stores
     t.fastc = t.nc > t.nr ? 1 : (t.nc < t.nr ? 0 : trans);
     tiles += wsbm_pair_tiles(t.nr, t.nc, t.fastc);
-    int64_t e = (int64_t)rowU.size() * colU.size();
     entries += e;
     pairs += (int64_t)rn.size() * cn.size();
     tasks.push_back(t);
@@ -418,8 +437,14 @@ struct ProxyBatch {
 
   int64_t add(int inst, std::vector<int32_t>& at, const std::vector<int32_t>& U, const Box& b,
               int side, double2* out, int64_t ld) {
-    std::vector<int32_t> nn, pp;
-    make_slots(U, 0, nn, pp, at);
+    Slots S;
+    make_slots(U, 0, S.nodes, S.pos, at);
+    return add_slots(inst, S, (int64_t)U.size(), b, side, out, ld);
+  }
+
+  int64_t add_slots(int inst, const Slots& S, int64_t nU, const Box& b, int side, double2* out,
+                    int64_t ld) {
+    const std::vector<int32_t>&nn = S.nodes, &pp = S.pos;
     refs.push_back({(int64_t)ints.size(), (int64_t)ints.size() + (int64_t)nn.size()});
     ints.insert(ints.end(), nn.begin(), nn.end());
     ints.insert(ints.end(), pp.begin(), pp.end());
@@ -438,7 +463,7 @@ struct ProxyBatch {
     t.tile0 = (int32_t)tiles;
     t.inst = inst;
     tiles += wsbm_proxy_tiles(t.nn, t.P);
-    int64_t e = (int64_t)U.size() * 2 * b.P;
+    int64_t e = nU * 2 * b.P;
     entries += e;
     pairs += (int64_t)nn.size() * b.P;
     tasks.push_back(t);
@@ -666,6 +691,7 @@ static int factor_levels(const std::vector<wsbm_hss*>& hs, const std::vector<int
   // the proxy sources, whatever box it belongs to.  Only boxes whose bounding circle meets the
   // proxy circle are scanned.
   std::vector<std::vector<int32_t>> NR(NB), NC(NB);
+#pragma omp parallel for schedule(dynamic, 16)
   for (int r = 0; r < NB; ++r) {
     wsbm_hss* h = R[r].h;
     Level& LV = h->lv[R[r].l];
@@ -738,28 +764,54 @@ static int factor_levels(const std::vector<wsbm_hss*>& hs, const std::vector<int
   ProxyBatch xbp[3];  // per precision mode of the curves (one proxy launch each)
   std::vector<CopyDesc> copies;
   std::vector<int64_t> e_pairs(hs.size(), 0), e_proxy(hs.size(), 0);
+  // slots of every box's lists in parallel (per-thread scratch), then the batches in box order
+  // (the task order, and so every result, is that of a serial build)
+  struct BoxSlots {
+    Slots cr, cc, nc, nr, s1r, s1c, s2r, s2c;
+  };
+  std::vector<BoxSlots> bs(NB);
+#pragma omp parallel for schedule(dynamic, 16)
+  for (int r = 0; r < NB; ++r) {
+    wsbm_hss* h = R[r].h;
+    const int l = R[r].l;
+    Box& B = R[r].box();
+    std::vector<int32_t>& at = thread_slot_scratch(h->N);
+    BoxSlots& S = bs[r];
+    make_slots(B.cr, 0, S.cr.nodes, S.cr.pos, at);
+    make_slots(B.cc, 0, S.cc.nodes, S.cc.pos, at);
+    make_slots(NC[r], 2 * B.P, S.nc.nodes, S.nc.pos, at);
+    make_slots(NR[r], 2 * B.P, S.nr.nodes, S.nr.pos, at);
+    if (l != h->L) {
+      Box& A1 = h->lv[l + 1].box[2 * R[r].b];
+      Box& A2 = h->lv[l + 1].box[2 * R[r].b + 1];
+      make_slots(A1.Jr, 0, S.s1r.nodes, S.s1r.pos, at);
+      make_slots(A2.Jc, A1.k, S.s1c.nodes, S.s1c.pos, at);
+      make_slots(A2.Jr, A1.k, S.s2r.nodes, S.s2r.pos, at);
+      make_slots(A1.Jc, 0, S.s2c.nodes, S.s2c.pos, at);
+    }
+  }
   for (int r = 0; r < NB; ++r) {
     wsbm_hss* h = R[r].h;
     const int i = R[r].inst, l = R[r].l;
     Box& B = R[r].box();
-    std::vector<int32_t>& at = h->slot_scratch;
+    const BoxSlots& S = bs[r];
     if (l == h->L) {
-      e_pairs[i] += pb.add(i, at, B.cr, 0, B.cc, 0, B.D, B.n, 0);
+      e_pairs[i] += pb.add_slots(i, S.cr, S.cc, (int64_t)B.cr.size() * B.cc.size(), B.D, B.n, 0);
     } else {
       Box& A1 = h->lv[l + 1].box[2 * R[r].b];
       Box& A2 = h->lv[l + 1].box[2 * R[r].b + 1];
       int ka = A1.k, kb = A2.k;
-      e_pairs[i] += pb.add(i, at, A1.Jr, 0, A2.Jc, ka, B.D, B.n, 0);
-      e_pairs[i] += pb.add(i, at, A2.Jr, ka, A1.Jc, 0, B.D, B.n, 0);
+      e_pairs[i] += pb.add_slots(i, S.s1r, S.s1c, (int64_t)A1.Jr.size() * A2.Jc.size(), B.D, B.n, 0);
+      e_pairs[i] += pb.add_slots(i, S.s2r, S.s2c, (int64_t)A2.Jr.size() * A1.Jc.size(), B.D, B.n, 0);
       copies.push_back({B.D, A1.Dc, B.n, ka, ka, ka});
       copies.push_back({B.D + ka + (int64_t)ka * B.n, A2.Dc, B.n, kb, kb, kb});
     }
     // row ID matrix (stored transposed: rows = near columns) and column ID matrix
-    e_pairs[i] += pb.add(i, at, B.cr, 0, NC[r], 2 * B.P, Mr[r], mr[r], 1);
-    e_pairs[i] += pb.add(i, at, NR[r], 2 * B.P, B.cc, 0, Mc[r], mc[r], 0);
+    e_pairs[i] += pb.add_slots(i, S.cr, S.nc, (int64_t)B.cr.size() * NC[r].size(), Mr[r], mr[r], 1);
+    e_pairs[i] += pb.add_slots(i, S.nr, S.cc, (int64_t)NR[r].size() * B.cc.size(), Mc[r], mc[r], 0);
     ProxyBatch& xb = xbp[h->prm.precision];
-    e_proxy[i] += xb.add(i, at, B.cr, B, 0, Mr[r], mr[r]);
-    e_proxy[i] += xb.add(i, at, B.cc, B, 1, Mc[r], mc[r]);
+    e_proxy[i] += xb.add_slots(i, S.cr, (int64_t)B.cr.size(), B, 0, Mr[r], mr[r]);
+    e_proxy[i] += xb.add_slots(i, S.cc, (int64_t)B.cc.size(), B, 1, Mc[r], mc[r]);
   }
   if (!copies.empty()) {
     CopyDesc* dc = nullptr;
