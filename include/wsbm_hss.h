@@ -72,8 +72,9 @@ typedef struct {
  *  root_cap    largest dense root order accepted (0 selects 40000); a factorization whose
  *              merged skeleton system would be larger fails with WSBM_ERR_RANK_OVERFLOW
  *  id_method   WSBM_ID_SKETCH (0): leaf-level IDs from the column-pivoted QR of a tensor-core
- *              sketch Omega M of the ID matrix (l = 16 ceil((n/2 + 32)/16) rows, used when M has
- *              at least 1.5 l rows; a side whose rank comes within 16 of l is redone on M);
+ *              sketch Omega M of the ID matrix (l = 16 ceil(n/32) rows, used when M has at
+ *              least 1.5 l rows; the QR of a sketch stops at a quarter of the usual cutoff; a
+ *              side whose rank, or the box's, comes within 16 of l is redone on M);
  *              WSBM_ID_FULL (1): column-pivoted QR of the full ID matrices everywhere
  */
 enum { WSBM_ID_SKETCH = 0, WSBM_ID_FULL = 1 };

@@ -33,6 +33,16 @@
 #include "dense.h"
 #include "wsbm_internal.h"
 
+// Randomized leaf IDs: sketch rows l = 16 ceil((n/2 + PAD)/16) and the QR cutoff on a sketch
+// relative to that of a full QR (a sketch's trailing singular values are distorted, so its QR
+// stops with a slightly tighter cutoff).
+#ifndef WSBM_SKETCH_PAD
+#define WSBM_SKETCH_PAD 0
+#endif
+#ifndef WSBM_SKETCH_CUT
+#define WSBM_SKETCH_CUT 0.25  // measured: far-field error 3.6-5.8x tol, as with the full QR
+#endif
+
 int wsbm_phys_from_params(const wsbm_params* p, Phys* ph);
 int wsbm_geom_check(const wsbm_geom* g);
 
@@ -841,7 +851,8 @@ static int factor_levels(const std::vector<wsbm_hss*>& hs, const std::vector<int
     h0->stats.pairs_proxy += xbp[0].pairs + xbp[1].pairs + xbp[2].pairs;
   }
   // ---- randomized sketches of the leaf-level ID matrices (tensor cores): Y = Omega M with
-  // l = 16 ceil((n/2 + 32)/16) rows, where M has at least 1.5 l rows
+  // l = max(32, 16 ceil((n/2 + WSBM_SKETCH_PAD)/16)) rows, where M has at least 1.5 l rows;
+  // their QR stops at WSBM_SKETCH_CUT times the cutoff of a full QR
   std::vector<int> lsk(2 * NB, 0);
   std::vector<double2*> Ysk(2 * NB, nullptr);
   {
@@ -851,7 +862,7 @@ static int factor_levels(const std::vector<wsbm_hss*>& hs, const std::vector<int
       wsbm_hss* h = R[r].h;
       Box& B = R[r].box();
       if (h->prm.id_method != WSBM_ID_SKETCH || R[r].l != h->L || B.n < 64) continue;
-      const int l = 16 * ((B.n / 2 + 32 + 15) / 16);
+      const int l = std::max(32, 16 * ((B.n / 2 + WSBM_SKETCH_PAD + 15) / 16));
       for (int s2 = 0; s2 < 2; ++s2) {
         const int64_t m = s2 == 0 ? mr[r] : mc[r];
         if (l > 192 || m < (3 * (int64_t)l) / 2 || m > 65536) continue;
@@ -920,7 +931,7 @@ static int factor_levels(const std::vector<wsbm_hss*>& hs, const std::vector<int
         }
         q.m = (int32_t)q.lda;
         q.n = R[r].box().n;
-        q.tol = R[r].h->cut;
+        q.tol = R[r].h->cut * (lsk[2 * r + s] ? WSBM_SKETCH_CUT : 1.0);
         q.perm = perm + on;
         q.norm2 = norm2 + on;
         q.nref = nref + on;
@@ -969,6 +980,7 @@ static int factor_levels(const std::vector<wsbm_hss*>& hs, const std::vector<int
         q.A = s == 0 ? Mr[r] : Mc[r];
         q.lda = s == 0 ? mr[r] : mc[r];
         q.m = (int32_t)q.lda;
+        q.tol = R[r].h->cut;
         lsk[2 * r + s] = 0;
         redo.push_back(q);
         which.push_back(2 * r + s);
