@@ -304,7 +304,16 @@ __global__ void k_apply_piv_inv(const TrsmDesc* __restrict__ d) {
 #endif
 // 5 - log2(2*CPQR_CB): the lane holding reduced value t is t << CPQR_SH
 #define CPQR_SH (CPQR_CB == 1 ? 4 : CPQR_CB == 2 ? 3 : CPQR_CB == 4 ? 2 : CPQR_CB == 8 ? 1 : 0)
+// TPC (thread per column): each thread updates whole trailing columns against the reflector
+// staged in shared memory (no warp reductions; the strided column loads stay in L1, and on
+// GB300 a warp-wide DFMA takes 16 clocks, which hides them).  Used when the reflector fits the
+// shared memory budget (m <= CPQR_TPC_MAXM).
+#ifndef CPQR_TPC_MAXM
+#define CPQR_TPC_MAXM 2048
+#endif
+template <bool TPC>
 __global__ void __launch_bounds__(256, CPQR_MINB) k_cpqr(const QrDesc* __restrict__ d, int mode) {
+  extern __shared__ double2 su[];  // TPC: the reflector u = M[j:m, j]
   const QrDesc q = d[blockIdx.x];
   const int m = q.m, n = q.n;
   double2* M = q.A;
@@ -410,6 +419,47 @@ __global__ void __launch_bounds__(256, CPQR_MINB) k_cpqr(const QrDesc* __restric
     }
     __syncthreads();
     const double tau = s_tau;
+    if (TPC) {
+      const int mm = m - j;
+      for (int i = threadIdx.x; i < mm; i += blockDim.x) su[i] = M[j + i + (int64_t)j * ld];
+      __syncthreads();
+      for (int c = j + 1 + threadIdx.x; c < n; c += blockDim.x) {
+        double2* col = M + (int64_t)c * ld + j;
+        double wr0 = 0.0, wi0 = 0.0, wr1 = 0.0, wi1 = 0.0;  // w = u^H col, two chains
+        int i = 0;
+        for (; i + 1 < mm; i += 2) {
+          const double2 u0 = su[i], c0 = col[i], u1 = su[i + 1], c1 = col[i + 1];
+          wr0 = fma(u0.x, c0.x, fma(u0.y, c0.y, wr0));
+          wi0 = fma(u0.x, c0.y, fma(-u0.y, c0.x, wi0));
+          wr1 = fma(u1.x, c1.x, fma(u1.y, c1.y, wr1));
+          wi1 = fma(u1.x, c1.y, fma(-u1.y, c1.x, wi1));
+        }
+        if (i < mm) {
+          const double2 u0 = su[i], c0 = col[i];
+          wr0 = fma(u0.x, c0.x, fma(u0.y, c0.y, wr0));
+          wi0 = fma(u0.x, c0.y, fma(-u0.y, c0.x, wi0));
+        }
+        const double2 w = make_double2(tau * (wr0 + wr1), tau * (wi0 + wi1));
+        for (i = 0; i < mm; ++i) col[i] = cfms(su[i], w, col[i]);
+        // remaining norm: downdate by the new row-j entry, recompute once cancellation has
+        // eaten half its digits
+        double nv = q.norm2[c] - cabs2(col[0]);
+        if (nv <= 1e-8 * q.nref[c]) {
+          double ns = 0.0;
+          for (i = 1; i < mm; ++i) ns += cabs2(col[i]);
+          nv = ns;
+          q.nref[c] = ns;
+        }
+        q.norm2[c] = fmax(nv, 0.0);
+      }
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        q.tauv[j] = tau;
+        q.betav[j] = s_beta;
+      }
+      __syncthreads();
+      continue;
+    }
     // apply P to the trailing columns: a warp takes CPQR_CB columns at a time, so each element
     // of u is loaded once for all of them and the 2*CPQR_CB partial dot products are summed
     // across the warp by recursive halving (each level hands half of the values to the partner
@@ -601,9 +651,12 @@ int wsbm_lu_solve_batched(const TrsmDesc* d_desc_lower, const TrsmDesc* d_desc_u
   return wsbm_trsm_batched(d_desc_upper, nbatch, max_n, max_nrhs, 0, st);
 }
 
-int wsbm_cpqr_batched(const QrDesc* d_desc, int nbatch, int mode, cudaStream_t st) {
+int wsbm_cpqr_batched(const QrDesc* d_desc, int nbatch, int mode, int max_m, cudaStream_t st) {
   if (nbatch <= 0) return 0;
-  k_cpqr<<<nbatch, 256, 0, st>>>(d_desc, mode);
+  if (max_m <= CPQR_TPC_MAXM)
+    k_cpqr<true><<<nbatch, 256, (size_t)max_m * sizeof(double2), st>>>(d_desc, mode);
+  else
+    k_cpqr<false><<<nbatch, 256, 0, st>>>(d_desc, mode);
   wsbm_count_launch();
   return cudaGetLastError() == cudaSuccess ? 0 : -3;
 }

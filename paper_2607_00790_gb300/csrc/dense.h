@@ -71,5 +71,6 @@ int wsbm_lu_solve_batched(const TrsmDesc* d_desc_lower, const TrsmDesc* d_desc_u
 // interchanges undone in reverse order.
 int wsbm_lu_solve_t_batched(const TrsmDesc* d_desc, int nbatch, int max_n, int max_nrhs,
                             cudaStream_t st);
-int wsbm_cpqr_batched(const QrDesc* d_desc, int nbatch, int mode, cudaStream_t st);
+// max_m: the largest m of the batch (selects the thread-per-column kernel when it fits)
+int wsbm_cpqr_batched(const QrDesc* d_desc, int nbatch, int mode, int max_m, cudaStream_t st);
 int wsbm_cpqr_finish(const QrDesc* d_desc, int nbatch, cudaStream_t st);

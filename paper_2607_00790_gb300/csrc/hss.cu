@@ -950,7 +950,9 @@ static int factor_levels(const std::vector<wsbm_hss*>& hs, const std::vector<int
   QrDesc* dq = nullptr;
   HK(upload(h0, qs, &dq, tmp));
   HC(cudaEventRecord(h0->ev[5], st));
-  HK(wsbm_cpqr_batched(dq, 2 * NB, 0, st));
+  int qmax_m = 0;
+  for (auto& q : qd) qmax_m = std::max(qmax_m, q.m);
+  HK(wsbm_cpqr_batched(dq, 2 * NB, 0, qmax_m, st));
   HC(cudaEventRecord(h0->ev[6], st));
   *cpqr_mats = 2 * (int64_t)NB;
   std::vector<int32_t> hstate(4 * NB);
@@ -992,7 +994,9 @@ static int factor_levels(const std::vector<wsbm_hss*>& hs, const std::vector<int
       HC(cudaMemsetAsync(state + 2 * w, 0, 2 * sizeof(int32_t), st));
     QrDesc* dr = nullptr;
     HK(upload(h0, redo, &dr, tmp));
-    HK(wsbm_cpqr_batched(dr, (int)redo.size(), 0, st));
+    int rmax = 0;
+    for (auto& q : redo) rmax = std::max(rmax, q.m);
+    HK(wsbm_cpqr_batched(dr, (int)redo.size(), 0, rmax, st));
     std::vector<int32_t> hs2(4 * NB);
     HC(cudaMemcpyAsync(hs2.data(), state, hs2.size() * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
     HC(cudaStreamSynchronize(st));
@@ -1020,7 +1024,9 @@ static int factor_levels(const std::vector<wsbm_hss*>& hs, const std::vector<int
   if (!more.empty()) {
     QrDesc* dm = nullptr;
     HK(upload(h0, more, &dm, tmp));
-    HK(wsbm_cpqr_batched(dm, (int)more.size(), 1, st));
+    int mmax = 0;
+    for (auto& q : more) mmax = std::max(mmax, q.m);
+    HK(wsbm_cpqr_batched(dm, (int)more.size(), 1, mmax, st));
   }
   {
     QrDesc* dfin = nullptr;  // the final descriptors (sketched sides may have been redone on M)
