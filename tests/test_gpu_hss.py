@@ -9,12 +9,12 @@ from paper_2607_00790_gb300 import inputs
 pytestmark = pytest.mark.gpu
 
 
-def gpu_solver(curve, prm, precision=0, leaf=None, tol=None, nproxy=None):
+def gpu_solver(curve, prm, precision=0, leaf=None, tol=None, nproxy=None, id_method=0):
     from paper_2607_00790_gb300 import binding
     g, keep = binding.make_geom(curve)
     p = binding.make_params(prm["k0"], prm["n"], leaf=leaf or prm["leaf"],
                             nproxy=nproxy or prm["nproxy"], id_tol=tol or prm["tol"],
-                            precision=precision)
+                            precision=precision, id_method=id_method)
     s = binding.Solver(g, p)
     s._keep = keep
     return s
@@ -115,6 +115,40 @@ def test_mixed_fine_reaches_fp64_accuracy_at_tight_tolerance():
     _, ud, qd = dense_reference(c, ph, [0.0, 1.0])
     ffd = oracle.farfield(c, ph, ud, qd, ang)
     assert rel(ff, ffd) < 10 * prm["tol"], rel(ff, ffd)
+
+
+@pytest.mark.parametrize("id_method", [0, 1])
+def test_id_methods_match_dense(id_method):
+    """Randomized leaf IDs (sketch, default) and the full column-pivoted QR everywhere: both
+    within 10x the ID tolerance of the dense oracle; the sketch is used only by the first."""
+    c = inputs.star(1536)
+    prm = dict(k0=inputs.k0_for_density(c), n=1.5, leaf=128, nproxy=128, tol=1e-8)
+    ph = oracle.Physics(prm["k0"], n=prm["n"])
+    ang = 2 * np.pi * np.arange(90) / 90
+    s = gpu_solver(c, prm, id_method=id_method)
+    _, u, q = solve_gpu(s, [0.0, 2.5])
+    st = s.stats()
+    assert (st["sketch_matrices"] > 0) == (id_method == 0)
+    _, ud, qd = dense_reference(c, ph, [0.0, 2.5])
+    assert rel(u, ud) < 10 * prm["tol"] and rel(q, qd) < 10 * prm["tol"], (rel(u, ud), rel(q, qd))
+    ff = farfield_gpu(s, u, q, ang)
+    assert rel(ff, oracle.farfield(c, ph, ud, qd, ang)) < 10 * prm["tol"]
+    s.close()
+
+
+def test_sketch_fallback_keeps_accuracy():
+    """Leaf boxes of 64 nodes at tol 1e-10: the ranks come within 16 rows of the 64-row sketches,
+    so those sides are redone on the full ID matrices; the result stays within 10x tol."""
+    c = inputs.star(2048)
+    prm = dict(k0=inputs.k0_for_density(c), n=1.5, leaf=64, nproxy=64, tol=1e-10)
+    ph = oracle.Physics(prm["k0"], n=prm["n"])
+    s = gpu_solver(c, prm)
+    _, u, q = solve_gpu(s, [0.7])
+    st = s.stats()
+    assert st["sketch_matrices"] > 0 and st["sketch_fallbacks"] > 0, st
+    _, ud, qd = dense_reference(c, ph, [0.7])
+    assert rel(u, ud) < 10 * prm["tol"] and rel(q, qd) < 10 * prm["tol"], (rel(u, ud), rel(q, qd))
+    s.close()
 
 
 def test_single_box_tree():
