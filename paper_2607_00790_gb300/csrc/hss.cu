@@ -27,6 +27,7 @@
 #include <algorithm>
 #include <functional>
 #include <memory>
+#include <mutex>
 #include <unordered_map>
 #include <vector>
 
@@ -308,13 +309,75 @@ static int gridfor(int64_t work, int per = 256) {
   return (int)b;
 }
 
+// Pinned staging for host <-> device copies, one buffer per stream: copies from pageable memory
+// are staged by the driver at a few GB/s.  The buffer is handed out bump-allocated and reset
+// only at the start of a call that ends with its stream synchronized (the build of one tree
+// level, the roots, a transposed solve, a create), so nothing staged earlier is still being
+// copied; a reset grows it to the previous call's peak.  When it is full, copies fall back to
+// pageable memory.
+struct PinPool {
+  unsigned char* p = nullptr;
+  size_t cap = 0, off = 0, peak = 0;
+  int users = 0;  // handles created on this stream; the buffer is freed with the last one
+};
+static std::mutex g_pin_mu;
+static std::unordered_map<cudaStream_t, PinPool> g_pin;
+
+static void pin_acquire(cudaStream_t st) {
+  std::lock_guard<std::mutex> lk(g_pin_mu);
+  ++g_pin[st].users;
+}
+
+static void pin_release(cudaStream_t st) {
+  std::lock_guard<std::mutex> lk(g_pin_mu);
+  auto it = g_pin.find(st);
+  if (it == g_pin.end() || --it->second.users > 0) return;
+  if (it->second.p) cudaFreeHost(it->second.p);
+  g_pin.erase(it);
+}
+
+static void pin_reset(cudaStream_t st) {
+  // a call that returned early on an error may have left copies queued; an idle stream returns
+  // at once
+  cudaStreamSynchronize(st);
+  std::lock_guard<std::mutex> lk(g_pin_mu);
+  PinPool& P = g_pin[st];
+  if (P.peak > P.cap) {
+    if (P.p) cudaFreeHost(P.p);
+    P.p = nullptr;
+    P.cap = 0;
+    const size_t want = P.peak + P.peak / 4;
+    if (cudaMallocHost((void**)&P.p, want) == cudaSuccess) P.cap = want;
+    else cudaGetLastError();
+  }
+  P.off = 0;
+  P.peak = 0;
+}
+
+static void* pin_take(cudaStream_t st, size_t bytes) {
+  std::lock_guard<std::mutex> lk(g_pin_mu);
+  PinPool& P = g_pin[st];
+  // the offset also advances past requests that did not fit, so the peak is what the whole
+  // call needed
+  const size_t a = (P.off + 255) & ~(size_t)255;
+  P.off = a + bytes;
+  P.peak = std::max(P.peak, P.off);
+  return (P.p && P.off <= P.cap) ? P.p + a : nullptr;
+}
+
 template <class T>
 static int upload(wsbm_hss* h, const std::vector<T>& v, T** d, std::vector<void*>& tmp) {
   *d = nullptr;
   if (v.empty()) return WSBM_OK;
-  if (cudaMallocAsync((void**)d, v.size() * sizeof(T), h->st) != cudaSuccess) return WSBM_ERR_OOM;
+  const size_t bytes = v.size() * sizeof(T);
+  if (cudaMallocAsync((void**)d, bytes, h->st) != cudaSuccess) return WSBM_ERR_OOM;
   tmp.push_back(*d);
-  if (cudaMemcpyAsync(*d, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, h->st) != cudaSuccess)
+  const void* src = v.data();
+  if (void* stage = pin_take(h->st, bytes)) {
+    memcpy(stage, v.data(), bytes);
+    src = stage;
+  }
+  if (cudaMemcpyAsync(*d, src, bytes, cudaMemcpyHostToDevice, h->st) != cudaSuccess)
     return WSBM_ERR_CUDA;
   return WSBM_OK;
 }
@@ -547,6 +610,7 @@ extern "C" int wsbm_create(const wsbm_geom* g, const wsbm_params* p, void* strea
   wsbm_hss* h = new wsbm_hss();
   cudaGetDevice(&h->dev);
   h->st = (cudaStream_t)stream;
+  pin_acquire(h->st);
   h->N = g->n;
   h->ph = ph;
   h->prm = *p;
@@ -572,15 +636,24 @@ extern "C" int wsbm_create(const wsbm_geom* g, const wsbm_params* p, void* strea
   h->slot_scratch.assign(h->N, -1);
   h->hw.resize(h->N);
   std::vector<double> hk(h->N), hnx(h->N), hny(h->N);
-  cudaMemcpyAsync(h->hx.data(), g->x, bytes, cudaMemcpyDeviceToHost, h->st);
-  cudaMemcpyAsync(h->hy.data(), g->y, bytes, cudaMemcpyDeviceToHost, h->st);
-  cudaMemcpyAsync(h->hw.data(), g->w, bytes, cudaMemcpyDeviceToHost, h->st);
-  cudaMemcpyAsync(hnx.data(), g->nx, bytes, cudaMemcpyDeviceToHost, h->st);
-  cudaMemcpyAsync(hny.data(), g->ny, bytes, cudaMemcpyDeviceToHost, h->st);
-  cudaMemcpyAsync(hk.data(), g->kappa, bytes, cudaMemcpyDeviceToHost, h->st);
-  if (cudaStreamSynchronize(h->st) != cudaSuccess) {
-    wsbm_destroy(h);
-    return WSBM_ERR_CUDA;
+  {
+    // read the geometry back through the stream's pinned staging buffer when it is large enough
+    // (create ends with the stream synchronized, like the calls that reset the buffer)
+    pin_reset(h->st);
+    std::vector<double>* dsth[6] = {&h->hx, &h->hy, &h->hw, &hnx, &hny, &hk};
+    const double* srch[6] = {g->x, g->y, g->w, g->nx, g->ny, g->kappa};
+    void* stage[6];
+    for (int a = 0; a < 6; ++a) {
+      stage[a] = pin_take(h->st, bytes);
+      cudaMemcpyAsync(stage[a] ? stage[a] : (void*)dsth[a]->data(), srch[a], bytes,
+                      cudaMemcpyDeviceToHost, h->st);
+    }
+    if (cudaStreamSynchronize(h->st) != cudaSuccess) {
+      wsbm_destroy(h);
+      return WSBM_ERR_CUDA;
+    }
+    for (int a = 0; a < 6; ++a)
+      if (stage[a]) memcpy(dsth[a]->data(), stage[a], bytes);
   }
   for (int64_t i = 0; i < h->N; ++i) {
     if (!isfinite(h->hx[i]) || !isfinite(h->hy[i]) || !isfinite(h->hw[i]) || !isfinite(hk[i]) ||
@@ -643,6 +716,7 @@ extern "C" void wsbm_destroy(wsbm_hss_t h) {
   if (!h) return;
   release_factors(h);
   cudaStreamSynchronize(h->st);
+  pin_release(h->st);
   double* arr[6] = {h->x, h->y, h->nx, h->ny, h->w, h->kappa};
   for (double* a : arr)
     if (a) cudaFree(a);
@@ -685,6 +759,7 @@ static int factor_levels(const std::vector<wsbm_hss*>& hs, const std::vector<int
                          int64_t sketch_out[2], double* sketch_ms) {
   wsbm_hss* h0 = hs[0];
   cudaStream_t st = h0->st;
+  pin_reset(st);  // the previous level ended with the stream synchronized
   std::vector<void*> tmp;
   std::vector<BoxRef> R;
   for (size_t i = 0; i < hs.size(); ++i) {
@@ -1241,6 +1316,7 @@ static int factor_levels(const std::vector<wsbm_hss*>& hs, const std::vector<int
 static int factor_roots(const std::vector<wsbm_hss*>& hs, double ms_out[2]) {
   wsbm_hss* h0 = hs[0];
   cudaStream_t st = h0->st;
+  pin_reset(st);  // the levels ended with the stream synchronized
   std::vector<void*> tmp;
   InstArrays ia;
   HK(upload_instances(h0, hs, &ia, tmp));
@@ -2038,6 +2114,7 @@ extern "C" int wsbm_solve_transposed(wsbm_hss_t h, const void* rhs, int32_t nrhs
   if (nrhs < 0 || (nrhs > 0 && (!rhs || !lam1 || !lam2))) return WSBM_ERR_INVALID_ARG;
   if (nrhs == 0) return WSBM_OK;
   cudaStream_t st = h->st;
+  pin_reset(st);
   std::vector<void*> tmp;
   const int64_t N = h->N;
   double2* bint = nullptr;
