@@ -39,15 +39,31 @@ KERNEL_COUNTS = {
     "k_pairs": {"fp64_flops_per_pair": 377.3, "dram_bytes_per_pair": 64.4},
     # DRAM traffic of the column-pivoted QR per ID matrix of this workload, keyed by the dense.cu
     # hash and the matrix rows it was measured on (None: not measured for the current shape)
-    "k_cpqr": {"src_sha": "6aa68f8f50ddf6d1", "rows": 128, "dram_bytes_per_matrix": 6.27e7},
+    "k_cpqr": {"src_sha": "845cb05fd193638d", "rows": 128, "dram_bytes_per_matrix": 6.27e7},
 }
 # FP64 peak from the unit counts: 152 SMs x 4 FP64 flops/clk/SM (2 DFMA) x 2.07 GHz.
 FP64_PEAK_TFLOPS = 152 * 4 * 2.07e9 / 1e12
 
 
-def cpqr_src_sha():
+def _dense_section(begin, end):
     with open(os.path.join(ROOT, "paper_2607_00790_gb300", "csrc", "dense.cu"), "rb") as fh:
-        return hashlib.sha256(fh.read()).hexdigest()[:16]
+        src = fh.read()
+    a = src.index(begin.encode())
+    return src[a:src.index(end.encode(), a)]
+
+
+def cpqr_src_sha():
+    """Hash of the column-pivoted QR kernel's source section of dense.cu."""
+    sec = _dense_section("// ------------------------------------------------- column-pivoted Householder QR ----",
+                         "// ------------------------------------------------------------------ host drivers ----")
+    return hashlib.sha256(sec).hexdigest()[:16]
+
+
+def lu_src_sha():
+    """Hash of the fused LU + solve kernel's source section of dense.cu."""
+    sec = _dense_section("// --------------------------------------------------------- fused LU + solve ----",
+                         "// ------------------------------------------------- column-pivoted Householder QR ----")
+    return hashlib.sha256(sec).hexdigest()[:16]
 
 
 def kernel_src_sha():
@@ -224,6 +240,23 @@ def run_ours(args, ws, rank, local):
               "peak_note": "FP64 pipe: 152 SMs x 2 DFMA/clk x 2.07 GHz (unit counts); a DFMA "
                            "microbenchmark reached 1.013 TFLOP/s",
               "counts_fresh": qfresh}
+    # the fused LU + solve launches of the factor (box LU with D^-1 L, and Dhat = M^-1)
+    kl = KERNEL_COUNTS.get("k_lu_solve_fused", {})
+    lfresh = kl.get("src_sha") == lu_src_sha()
+    roof_l = None
+    if s0["ms_lu"] > 0:
+        l_ach = s0["lu_flops"] / (s0["ms_lu"] * 1e-3) / 1e12
+        roof_l = {"bound": "alu", "achieved": l_ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                  "frac": l_ach / FP64_PEAK_TFLOPS,
+                  "traffic": (kl["dram_bytes_per_matrix"] * s0["lu_matrices"])
+                             if (lfresh and kl.get("dram_bytes_per_matrix")) else None,
+                  "kernel": "k_lu_solve_fused", "matrices_per_step": s0["lu_matrices"],
+                  "launches_per_step": 2, "flops_per_step": s0["lu_flops"], "ms_per_step": s0["ms_lu"],
+                  "peak_note": roof_q["peak_note"], "counts_fresh": lfresh}
+    # the headline roofline is the kernel with the larger device time per step
+    roof_main, roof_other = roof_q, roof_l
+    if roof_l is not None and s0["ms_lu"] > s0["ms_cpqr"]:
+        roof_main, roof_other = roof_l, roof_q
     # roofline of the dominant entry kernel (the metric's entries/s)
     dom = "k_proxy" if s0["ms_proxy"] >= s0["ms_pairs"] else "k_pairs"
     pairs = s0["pairs_proxy"] if dom == "k_proxy" else s0["pairs_pairs"]
@@ -244,7 +277,9 @@ def run_ours(args, ws, rank, local):
            "warmup": args.warmup, "ms_per_step": ms_region_max / args.steps,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
            "data": "synthetic", "config": {k: cfg[k] for k in ("workload", "N", "k0", "n", "leaf", "nproxy", "tol", "l2")},
-           "gpu_launches": launches, "clocks": clk, "roofline": roof_q, "roofline_entry_kernel": roof,
+           "gpu_launches": launches, "clocks": clk, "roofline": roof_main,
+           "roofline_" + ("lu" if roof_other is roof_l else "cpqr") + "_kernel": roof_other,
+           "roofline_entry_kernel": roof,
            "step": {"entries_per_step": entries / args.steps,
                     "build_factor_s_leaf_level": ms_region / args.steps / 1e3,
                     "ms_entries": ms_kern / args.steps,
@@ -252,7 +287,8 @@ def run_ours(args, ws, rank, local):
                     "ms_factor": sum(s["ms_factor"] for s in stats) / args.steps,
                     "leaf_rank_max": s0["rank_per_level"][-1] if s0["rank_per_level"] else None,
                     "sketched_id_matrices": s0["sketch_matrices"],
-                    "sketch_fallbacks": s0["sketch_fallbacks"], "ms_sketch": s0["ms_sketch"]}}
+                    "sketch_fallbacks": s0["sketch_fallbacks"], "ms_sketch": s0["ms_sketch"],
+                    "ms_cpqr": s0["ms_cpqr"], "ms_lu_fused": s0["ms_lu"]}}
     out["e2e"] = run_e2e(args, curve, cfg, dev, params)
     if ws == 1:
         out["cpu_baseline"] = run_cpu_baseline(curve, cfg, budget_s=12.0)

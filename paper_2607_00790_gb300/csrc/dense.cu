@@ -289,6 +289,248 @@ __global__ void k_apply_piv_inv(const TrsmDesc* __restrict__ d) {
   }
 }
 
+// --------------------------------------------------------- fused LU + solve ----
+// One CTA per matrix on a row-major working copy S of [A | B], so that a row of the trailing
+// matrix is one coalesced access per warp.  Blocked right-looking LU with panels of LUS_B
+// columns: the panel (rows j0..n-1) is staged in shared memory and factored by one warp with
+// partial pivoting; then every thread takes one column c >= j0 + LUS_B at a time, applies the
+// panel's row interchanges, solves the unit-lower L11 for its LUS_B rows of U12 and updates its
+// trailing column with the rank-LUS_B product L21 U12 (one load and store per LUS_B complex
+// FMAs).  Columns left of the panel only take the interchanges.  Back substitution with U on
+// the B columns runs in the same blocks from the bottom, the U block column staged in shared
+// memory.  Pivot choice: largest max(|re|, |im|) (integer compare of the bit patterns), first
+// row on ties.
+#define LUS_T 256
+#define LUS_B 8
+
+__device__ __forceinline__ unsigned long long lus_key(double2 v) {
+  const unsigned long long m = 0x7fffffffffffffffull;
+  const unsigned long long a = (unsigned long long)__double_as_longlong(v.x) & m;
+  const unsigned long long b = (unsigned long long)__double_as_longlong(v.y) & m;
+  return a > b ? a : b;
+}
+
+__device__ __forceinline__ double2* lus_col(const LuSolveDesc& q, int c) {
+  return c < q.n ? q.A + (int64_t)c * q.lda : q.B + (int64_t)(c - q.n) * q.ldb;
+}
+
+// column-major [A | B] <-> row-major S through a 32 x 33 shared tile (8 warps, 4 rows each)
+__device__ void lus_transpose(const LuSolveDesc& q, double2* S, int64_t ldr, double2* tile,
+                              bool to_rows) {
+  const int n = q.n, nc = q.n + q.nrhs;
+  const int ntr = (n + 31) / 32, ntc = (nc + 31) / 32;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (int t = 0; t < ntr * ntc; ++t) {
+    const int r0 = (t % ntr) * 32, c0 = (t / ntr) * 32;
+#pragma unroll
+    for (int s = 0; s < 4; ++s) {
+      const int a = w + 8 * s;
+      if (to_rows) {
+        const int c = c0 + a, r = r0 + lane;
+        if (r < n && c < nc) tile[a * 33 + lane] = lus_col(q, c)[r];
+      } else {
+        const int r = r0 + a, c = c0 + lane;
+        if (r < n && c < nc) tile[lane * 33 + a] = S[(int64_t)r * ldr + c];
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int s = 0; s < 4; ++s) {
+      const int a = w + 8 * s;
+      if (to_rows) {
+        const int r = r0 + a, c = c0 + lane;
+        if (r < n && c < nc) S[(int64_t)r * ldr + c] = tile[lane * 33 + a];
+      } else {
+        const int c = c0 + a, r = r0 + lane;
+        if (r < n && c < nc) lus_col(q, c)[r] = tile[a * 33 + lane];
+      }
+    }
+    __syncthreads();
+  }
+}
+
+__global__ void __launch_bounds__(LUS_T) k_lu_solve_fused(const LuSolveDesc* __restrict__ d) {
+  const LuSolveDesc q = d[blockIdx.x];
+  const int n = q.n, nr = q.nrhs, nc = n + nr;
+  if (n <= 0) return;
+  const int64_t ldr = ((int64_t)nc + 7) & ~(int64_t)7;  // = wsbm_lu_solve_ldr(n, nrhs)
+  double2* __restrict__ S = q.S;
+  extern __shared__ double2 lus_sm[];
+  double2* sinv = lus_sm;    // n pivot reciprocals
+  double2* sp = lus_sm + n;  // panel / U block: LUS_B columns of stride m + 1; transpose tile
+  __shared__ int spiv[LUS_B];
+  const int tid = threadIdx.x, lane = tid & 31;
+
+  lus_transpose(q, S, ldr, sp, true);
+  for (int j0 = 0; j0 < n; j0 += LUS_B) {
+    const int bb = min(LUS_B, n - j0), m = n - j0, ld = m + 1;
+    __syncthreads();  // trailing updates of the previous panel done
+    for (int e = tid; e < m * bb; e += LUS_T) {
+      const int r = e / bb, t = e - r * bb;
+      sp[t * ld + r] = S[(int64_t)(j0 + r) * ldr + j0 + t];
+    }
+    __syncthreads();
+    if (tid < 32) {  // panel factorization, one warp
+      for (int jj = 0; jj < bb; ++jj) {
+        double2* col = sp + jj * ld;
+        unsigned long long best = 0;
+        int bi = 0x7fffffff;
+        for (int r = jj + lane; r < m; r += 32) {
+          const unsigned long long k = lus_key(col[r]);
+          if (k > best || bi == 0x7fffffff) {
+            best = k;
+            bi = r;
+          }
+        }
+#pragma unroll
+        for (int o = 16; o; o >>= 1) {
+          const unsigned long long ob = __shfl_xor_sync(0xffffffffu, best, o);
+          const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+          if (ob > best || (ob == best && oi < bi)) {
+            best = ob;
+            bi = oi;
+          }
+        }
+        const int p = bi;
+        if (p != jj && lane < bb) {
+          double2* a = sp + lane * ld;
+          const double2 x = a[jj];
+          a[jj] = a[p];
+          a[p] = x;
+        }
+        __syncwarp();
+        const double2 pv = col[jj];
+        const double2 inv =
+            (pv.x == 0.0 && pv.y == 0.0) ? make_double2(0.0, 0.0) : cdiv(make_double2(1.0, 0.0), pv);
+        if (lane == 0) {
+          spiv[jj] = j0 + p;
+          q.piv[j0 + jj] = j0 + p;
+          sinv[j0 + jj] = inv;
+        }
+        for (int r = jj + 1 + lane; r < m; r += 32) col[r] = cmul(col[r], inv);
+        __syncwarp();
+        for (int t = jj + 1; t < bb; ++t) {
+          double2* ct = sp + t * ld;
+          const double2 u = ct[jj];
+          for (int r = jj + 1 + lane; r < m; r += 32) ct[r] = cfms(col[r], u, ct[r]);
+        }
+        __syncwarp();
+      }
+    }
+    __syncthreads();
+    for (int e = tid; e < m * bb; e += LUS_T) {
+      const int r = e / bb, t = e - r * bb;
+      S[(int64_t)(j0 + r) * ldr + j0 + t] = sp[t * ld + r];
+    }
+    for (int c = tid; c < j0; c += LUS_T)  // columns of L: interchanges only
+      for (int jj = 0; jj < bb; ++jj) {
+        const int p = spiv[jj];
+        if (p != j0 + jj) {
+          double2* a = S + (int64_t)(j0 + jj) * ldr + c;
+          double2* b = S + (int64_t)p * ldr + c;
+          const double2 x = *a;
+          *a = *b;
+          *b = x;
+        }
+      }
+    for (int c = j0 + bb + tid; c < nc; c += LUS_T) {
+      double2 u[LUS_B];
+#pragma unroll
+      for (int jj = 0; jj < LUS_B; ++jj)
+        if (jj < bb) {
+          const int p = spiv[jj];
+          double2* a = S + (int64_t)(j0 + jj) * ldr + c;
+          if (p != j0 + jj) {
+            double2* b = S + (int64_t)p * ldr + c;
+            const double2 x = *a;
+            *a = *b;
+            *b = x;
+          }
+        }
+#pragma unroll
+      for (int t = 0; t < LUS_B; ++t)
+        if (t < bb) {
+          double2 v = S[(int64_t)(j0 + t) * ldr + c];
+#pragma unroll
+          for (int s2 = 0; s2 < t; ++s2) v = cfms(sp[s2 * ld + t], u[s2], v);
+          u[t] = v;
+          S[(int64_t)(j0 + t) * ldr + c] = v;
+        }
+      int r = bb;
+      for (; r + 1 < m; r += 2) {
+        double2* e0 = S + (int64_t)(j0 + r) * ldr + c;
+        double2* e1 = e0 + ldr;
+        double2 a0 = *e0, a1 = *e1;
+#pragma unroll
+        for (int t = 0; t < LUS_B; ++t)
+          if (t < bb) {
+            a0 = cfms(sp[t * ld + r], u[t], a0);
+            a1 = cfms(sp[t * ld + r + 1], u[t], a1);
+          }
+        *e0 = a0;
+        *e1 = a1;
+      }
+      if (r < m) {
+        double2* e0 = S + (int64_t)(j0 + r) * ldr + c;
+        double2 a0 = *e0;
+#pragma unroll
+        for (int t = 0; t < LUS_B; ++t)
+          if (t < bb) a0 = cfms(sp[t * ld + r], u[t], a0);
+        *e0 = a0;
+      }
+    }
+  }
+  // back substitution U X = Y on the B columns, block rows from the bottom
+  for (int j0 = ((n - 1) / LUS_B) * LUS_B; j0 >= 0; j0 -= LUS_B) {
+    const int bb = min(LUS_B, n - j0), m = j0 + bb, ld = m + 1;
+    __syncthreads();
+    for (int e = tid; e < m * bb; e += LUS_T) {
+      const int r = e / bb, t = e - r * bb;
+      sp[t * ld + r] = S[(int64_t)r * ldr + j0 + t];
+    }
+    __syncthreads();
+    for (int c = n + tid; c < nc; c += LUS_T) {
+      double2 x[LUS_B];
+#pragma unroll
+      for (int t = 0; t < LUS_B; ++t) x[t] = t < bb ? S[(int64_t)(j0 + t) * ldr + c] : make_double2(0.0, 0.0);
+#pragma unroll
+      for (int t = LUS_B - 1; t >= 0; --t)
+        if (t < bb) {
+          x[t] = cmul(x[t], sinv[j0 + t]);
+#pragma unroll
+          for (int s2 = 0; s2 < t; ++s2) x[s2] = cfms(sp[t * ld + j0 + s2], x[t], x[s2]);
+        }
+#pragma unroll
+      for (int t = 0; t < LUS_B; ++t)
+        if (t < bb) S[(int64_t)(j0 + t) * ldr + c] = x[t];
+      int i = 0;
+      for (; i + 1 < j0; i += 2) {
+        double2* e0 = S + (int64_t)i * ldr + c;
+        double2* e1 = e0 + ldr;
+        double2 a0 = *e0, a1 = *e1;
+#pragma unroll
+        for (int t = 0; t < LUS_B; ++t)
+          if (t < bb) {
+            a0 = cfms(sp[t * ld + i], x[t], a0);
+            a1 = cfms(sp[t * ld + i + 1], x[t], a1);
+          }
+        *e0 = a0;
+        *e1 = a1;
+      }
+      if (i < j0) {
+        double2* e0 = S + (int64_t)i * ldr + c;
+        double2 a0 = *e0;
+#pragma unroll
+        for (int t = 0; t < LUS_B; ++t)
+          if (t < bb) a0 = cfms(sp[t * ld + i], x[t], a0);
+        *e0 = a0;
+      }
+    }
+  }
+  __syncthreads();
+  lus_transpose(q, S, ldr, sp, false);
+}
+
 // ------------------------------------------------- column-pivoted Householder QR ----
 // One CTA per matrix M (m x n, in place).  Step j: pivot the column of largest remaining norm
 // to position j, reflect rows j..m-1 with P = I - tau u u^H (Hermitian, tau real,
@@ -649,6 +891,26 @@ int wsbm_lu_solve_batched(const TrsmDesc* d_desc_lower, const TrsmDesc* d_desc_u
   int rc = wsbm_trsm_batched(d_desc_lower, nbatch, max_n, max_nrhs, 1, st);
   if (rc) return rc;
   return wsbm_trsm_batched(d_desc_upper, nbatch, max_n, max_nrhs, 0, st);
+}
+
+int64_t wsbm_lu_solve_ldr(int n, int nrhs) { return ((int64_t)n + nrhs + 7) & ~(int64_t)7; }
+
+int wsbm_lu_solve_fused_batched(const LuSolveDesc* d_desc, int nbatch, int max_n, int max_nc,
+                                cudaStream_t st) {
+  if (nbatch <= 0) return 0;
+  if (max_n > WSBM_LUS_MAXN || max_n > max_nc) return -1;
+  const size_t tile = 32 * 33, panel = (size_t)(max_n + 1) * LUS_B;
+  const size_t sm = ((size_t)max_n + (panel > tile ? panel : tile)) * sizeof(double2);
+  static size_t set = 0;
+  if (sm > 48 * 1024 && sm > set) {
+    if (cudaFuncSetAttribute(k_lu_solve_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) !=
+        cudaSuccess)
+      return -3;
+    set = sm;
+  }
+  k_lu_solve_fused<<<nbatch, LUS_T, sm, st>>>(d_desc);
+  wsbm_count_launch();
+  return cudaGetLastError() == cudaSuccess ? 0 : -3;
 }
 
 int wsbm_cpqr_batched(const QrDesc* d_desc, int nbatch, int mode, int max_m, cudaStream_t st) {

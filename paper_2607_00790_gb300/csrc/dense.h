@@ -61,6 +61,24 @@ struct QrDesc {
   double* rdiag0;
 };
 
+// Fused LU with partial pivoting and solve of [A | B]: A (n x n, column-major, in place) <- its
+// LU factor (the LuDesc layout, piv[j] = row swapped with row j), B (n x nrhs) <- A^-1 B.
+// S: scratch of n x wsbm_lu_solve_ldr(n, nrhs) elements (the row-major working copy).
+struct LuSolveDesc {
+  double2* A;
+  int64_t lda;
+  int32_t* piv;
+  double2* B;
+  int64_t ldb;
+  double2* S;
+  int32_t n, nrhs;
+};
+#define WSBM_LUS_MAXN 1024  // largest n of the fused kernel (its panel sits in shared memory)
+int64_t wsbm_lu_solve_ldr(int n, int nrhs);
+// Returns -1 (nothing launched) when max_n exceeds WSBM_LUS_MAXN.
+int wsbm_lu_solve_fused_batched(const LuSolveDesc* d_desc, int nbatch, int max_n, int max_nc,
+                                cudaStream_t st);
+
 int wsbm_gemm_batched(const GemmDesc* d_desc, int nbatch, int max_m, int max_n, cudaStream_t st);
 int wsbm_lu_batched(const LuDesc* d_desc, int nbatch, int max_n, int* d_info, cudaStream_t st);
 int wsbm_trsm_batched(const TrsmDesc* d_desc, int nbatch, int max_n, int max_nrhs, int lower,

@@ -98,7 +98,7 @@ struct wsbm_hss {
   bool factored = false;
   std::vector<void*> owned;  // factor allocations
   wsbm_stats_t stats;
-  cudaEvent_t ev[8];
+  cudaEvent_t ev[12];
   std::shared_ptr<struct SolvePlan> plan;  // solve plan of the last nrhs (see wsbm_solve)
 };
 
@@ -186,6 +186,18 @@ __global__ void k_fill_identity_batched(const CopyDesc* __restrict__ d) {
     int i = (int)(e % q.m), j = (int)(e / q.m);
     q.dst[i + (int64_t)j * q.ldd] = make_double2(i == j ? 1.0 : 0.0, 0.0);
   }
+}
+
+// int32 vector copies, one descriptor per block row of the grid
+struct CopyIntDesc {
+  int32_t* dst;
+  const int32_t* src;
+  int64_t n;
+};
+__global__ void k_copy_int(const CopyIntDesc* __restrict__ d) {
+  const CopyIntDesc q = d[blockIdx.y];
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < q.n; e += (int64_t)gridDim.x * blockDim.x)
+    q.dst[e] = q.src[e];
 }
 
 __global__ void k_copy2d(const CopyDesc* __restrict__ d) {
@@ -617,7 +629,7 @@ extern "C" int wsbm_create(const wsbm_geom* g, const wsbm_params* p, void* strea
   if (!(h->prm.proxy_ratio > 1.0)) h->prm.proxy_ratio = 1.5;
   h->cut = p->id_tol / 4.0;
   memset(&h->stats, 0, sizeof(h->stats));
-  for (int i = 0; i < 8; ++i) cudaEventCreate(&h->ev[i]);
+  for (int i = 0; i < 12; ++i) cudaEventCreate(&h->ev[i]);
   size_t bytes = (size_t)h->N * sizeof(double);
   double** dst[6] = {&h->x, &h->y, &h->nx, &h->ny, &h->w, &h->kappa};
   const double* src[6] = {g->x, g->y, g->nx, g->ny, g->w, g->kappa};
@@ -720,7 +732,7 @@ extern "C" void wsbm_destroy(wsbm_hss_t h) {
   double* arr[6] = {h->x, h->y, h->nx, h->ny, h->w, h->kappa};
   for (double* a : arr)
     if (a) cudaFree(a);
-  for (int i = 0; i < 8; ++i)
+  for (int i = 0; i < 12; ++i)
     if (h->ev[i]) cudaEventDestroy(h->ev[i]);
   delete h;
 }
@@ -754,9 +766,17 @@ static int upload_instances(wsbm_hss* h0, const std::vector<wsbm_hss*>& hs, Inst
 // Compress and factor one tree level of each item (a curve and its level): every phase is one
 // launch over all boxes of all items (entries, proxy blocks, IDs, LU, D^-1 L, Dhat).  All
 // handles share one stream.  Candidates (cr, cc) of every box must be set.
+// Algorithmic flops of the fused LU + solve of an n x n matrix with nrhs right-hand sides:
+// multipliers (one complex multiply, 6 flops) and trailing updates (one complex FMA, 8 flops) of
+// the LU, the forward and backward substitutions, and the pivot scalings of the back solve.
+static double lu_solve_flops(double n, double nrhs) {
+  const double a = n * (n - 1) / 2, b = (n - 1) * n * (2 * n - 1) / 6;
+  return 6 * a + 8 * b + 16 * a * nrhs + 6 * n * nrhs;
+}
+
 static int factor_levels(const std::vector<wsbm_hss*>& hs, const std::vector<int>& levels,
                          double ms_out[5], int64_t* cpqr_mats, double* cpqr_flops,
-                         int64_t sketch_out[2], double* sketch_ms) {
+                         int64_t sketch_out[2], double* sketch_ms, double lu_out[3]) {
   wsbm_hss* h0 = hs[0];
   cudaStream_t st = h0->st;
   pin_reset(st);  // the previous level ended with the stream synchronized
@@ -1131,8 +1151,12 @@ static int factor_levels(const std::vector<wsbm_hss*>& hs, const std::vector<int
     HK(upload(h0, td, &dtd, tmp));
     HK(wsbm_trsm_batched(dtd, (int)td.size(), mk, mrhs, 0, st));
   }
+  // the permutations are read on the host after the final synchronization of this call; a
+  // pageable read-back here would hold the host until the queue drains
   std::vector<int32_t> hperm(2 * ntot);
-  HC(cudaMemcpyAsync(hperm.data(), perm, hperm.size() * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+  void* perm_stage = pin_take(st, hperm.size() * sizeof(int32_t));
+  HC(cudaMemcpyAsync(perm_stage ? perm_stage : (void*)hperm.data(), perm, hperm.size() * sizeof(int32_t),
+                     cudaMemcpyDeviceToHost, st));
   HC(cudaEventRecord(h0->ev[2], st));
   // ---- factor: LU(D), Z = D^-1 L, M = R Z, Dhat = M^-1
   std::vector<size_t> Ztot(hs.size(), 0), Ktot(hs.size(), 0), Ttot(hs.size(), 0);
@@ -1255,10 +1279,40 @@ static int factor_levels(const std::vector<wsbm_hss*>& hs, const std::vector<int
   HK(upload(h0, idd, &didd, tmp));
   int64_t maxnk = 0;
   for (int r = 0; r < NB; ++r) maxnk = std::max(maxnk, (int64_t)R[r].box().n * R[r].box().k);
-  HK(wsbm_lu_batched(dluD, NB, maxn, nullptr, st));
+  // LU(D) with Z = D^-1 L, and LU(M) with Dhat = M^-1, in the fused kernel when [D | L] fits it
+  // (one scratch serves both launches), else blocked LU and triangular solves
+  LuSolveDesc *dfz = nullptr, *dfm = nullptr;
+  if (maxn <= WSBM_LUS_MAXN) {
+    size_t sz = 0, sm = 0;
+    for (int r = 0; r < NB; ++r) {
+      const Box& B = R[r].box();
+      sz += (size_t)B.n * wsbm_lu_solve_ldr(B.n, B.k);
+      sm += (size_t)B.k * wsbm_lu_solve_ldr(B.k, B.k);
+    }
+    double2* Sc = nullptr;
+    HK(dalloc(h0, std::max(sz, sm) * sizeof(double2), (void**)&Sc, tmp));
+    std::vector<LuSolveDesc> fz(NB), fm(NB);
+    size_t oz = 0, om = 0;
+    for (int r = 0; r < NB; ++r) {
+      const Box& B = R[r].box();
+      fz[r] = {B.D, B.n, B.piv, B.Z, B.n, Sc + oz, B.n, B.k};
+      fm[r] = {luM[r].A, B.k, luM[r].piv, B.Dc, B.k, Sc + om, B.k, B.k};
+      oz += (size_t)B.n * wsbm_lu_solve_ldr(B.n, B.k);
+      om += (size_t)B.k * wsbm_lu_solve_ldr(B.k, B.k);
+    }
+    HK(upload(h0, fz, &dfz, tmp));
+    HK(upload(h0, fm, &dfm, tmp));
+  }
   k_build_L<<<dim3(gridfor(maxnk), NB), 256, 0, st>>>(dbl);
   wsbm_count_launch();
-  HK(wsbm_lu_solve_batched(dzl, dzl, NB, maxn, maxk, st));
+  if (dfz) {
+    HC(cudaEventRecord(h0->ev[8], st));
+    HK(wsbm_lu_solve_fused_batched(dfz, NB, maxn, maxn + maxk, st));
+    HC(cudaEventRecord(h0->ev[9], st));
+  } else {
+    HK(wsbm_lu_batched(dluD, NB, maxn, nullptr, st));
+    HK(wsbm_lu_solve_batched(dzl, dzl, NB, maxn, maxk, st));
+  }
   k_gather_rows<<<dim3(gridfor(maxnk), NB), 256, 0, st>>>(dgz);
   wsbm_count_launch();
   k_copy2d<<<dim3(gridfor((int64_t)maxk * maxk), NB), 256, 0, st>>>(dpc);
@@ -1268,18 +1322,44 @@ static int factor_levels(const std::vector<wsbm_hss*>& hs, const std::vector<int
     k_copy2d<<<dim3(gridfor(maxnk), (unsigned)tcc.size()), 256, 0, st>>>(dtcc);
     wsbm_count_launch();
   }
-  HK(wsbm_lu_batched(dluM, NB, maxk, nullptr, st));
   k_fill_identity_batched<<<dim3(gridfor((int64_t)maxk * maxk), NB), 256, 0, st>>>(didd);
   wsbm_count_launch();
-  HK(wsbm_lu_solve_batched(dml, dml, NB, maxk, maxk, st));
+  if (dfm) {
+    HC(cudaEventRecord(h0->ev[10], st));
+    HK(wsbm_lu_solve_fused_batched(dfm, NB, maxk, 2 * maxk, st));
+    HC(cudaEventRecord(h0->ev[11], st));
+  } else {
+    HK(wsbm_lu_batched(dluM, NB, maxk, nullptr, st));
+    HK(wsbm_lu_solve_batched(dml, dml, NB, maxk, maxk, st));
+  }
   HC(cudaGetLastError());
-  // column permutations (kept for the solve)
-  for (int r = 0; r < NB; ++r) {
-    Box& B = R[r].box();
-    HC(cudaMemcpyAsync(B.pc, qd[2 * r + 1].perm, B.n * sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
+  // column permutations (kept for the solve): one launch copies them out of the QR state
+  {
+    std::vector<CopyIntDesc> pcd(NB);
+    int64_t maxpn = 1;
+    size_t on = 0;
+    for (int r = 0; r < NB; ++r) {
+      const Box& B = R[r].box();
+      pcd[r] = {B.pc, perm + on + B.n, B.n};  // column side of box r
+      on += 2 * (size_t)B.n;
+      maxpn = std::max(maxpn, (int64_t)B.n);
+    }
+    CopyIntDesc* dpcd = nullptr;
+    HK(upload(h0, pcd, &dpcd, tmp));
+    k_copy_int<<<dim3(gridfor(maxpn), NB), 256, 0, st>>>(dpcd);
+    wsbm_count_launch();
   }
   HC(cudaEventRecord(h0->ev[3], st));
   HC(cudaStreamSynchronize(st));
+  if (perm_stage) memcpy(hperm.data(), perm_stage, hperm.size() * sizeof(int32_t));
+  if (dfz && dfm) {  // device time, flops and matrices of the two fused LU + solve launches
+    lu_out[0] += elapsed(h0->ev[8], h0->ev[9]) + elapsed(h0->ev[10], h0->ev[11]);
+    for (int r = 0; r < NB; ++r) {
+      const Box& B = R[r].box();
+      lu_out[1] += lu_solve_flops(B.n, B.k) + lu_solve_flops(B.k, B.k);
+    }
+    lu_out[2] += 2.0 * NB;
+  }
   ms_out[0] = elapsed(h0->ev[0], h0->ev[1]);
   ms_out[1] = elapsed(h0->ev[0], h0->ev[4]);
   ms_out[2] = elapsed(h0->ev[1], h0->ev[2]);
@@ -1408,6 +1488,7 @@ static int factor_all(const std::vector<wsbm_hss*>& hs, wsbm_stats_t* bstats) {
   double ms[5] = {0, 0, 0, 0, 0};  // entries, pair kernel, IDs, factor, CPQR
   int64_t cpqr_mats = 0;
   double cpqr_flops = 0.0, ms_sketch = 0.0;
+  double lu_acc[3] = {0.0, 0.0, 0.0};  // fused LU + solve: device ms, flops, matrices
   int64_t sketch_cnt[2] = {0, 0};  // sketched ID matrices, redone on the full matrix
   std::vector<int> level(hs.size(), 0), done(hs.size(), 0);
   std::vector<char> partial(hs.size(), 0);
@@ -1438,7 +1519,7 @@ static int factor_all(const std::vector<wsbm_hss*>& hs, wsbm_stats_t* bstats) {
     if (!any) break;
     double m4[5];
     int64_t nq = 0;
-    rc = factor_levels(hs, level, m4, &nq, &cpqr_flops, sketch_cnt, &ms_sketch);
+    rc = factor_levels(hs, level, m4, &nq, &cpqr_flops, sketch_cnt, &ms_sketch, lu_acc);
     if (rc) break;
     for (int a = 0; a < 5; ++a) ms[a] += m4[a];
     cpqr_mats += nq;
@@ -1521,6 +1602,9 @@ static int factor_all(const std::vector<wsbm_hss*>& hs, wsbm_stats_t* bstats) {
       h->stats.sketch_matrices = sketch_cnt[0];
       h->stats.sketch_fallbacks = sketch_cnt[1];
       h->stats.ms_sketch = ms_sketch;
+      h->stats.ms_lu = lu_acc[0];
+      h->stats.lu_flops = lu_acc[1];
+      h->stats.lu_matrices = (int64_t)lu_acc[2];
     }
     size_t bytes = 0;
     for (int l = h->top; l <= h->L && h->L > 0; ++l)
@@ -1556,6 +1640,9 @@ static int factor_all(const std::vector<wsbm_hss*>& hs, wsbm_stats_t* bstats) {
     bstats->sketch_matrices = sketch_cnt[0];
     bstats->sketch_fallbacks = sketch_cnt[1];
     bstats->ms_sketch = ms_sketch;
+    bstats->ms_lu = lu_acc[0];
+    bstats->lu_flops = lu_acc[1];
+    bstats->lu_matrices = (int64_t)lu_acc[2];
   }
   return rc;
 }
