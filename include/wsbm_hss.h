@@ -353,6 +353,12 @@ int wsbm_curve_fourier_vjp(int32_t M, int64_t N, const double* a, const double* 
 /* Static name of an error code. */
 const char* wsbm_strerror(int code);
 
+/* The work space of wsbm_factor, wsbm_batch_factor and the transposed solve comes from a
+ * memory pool per device that keeps up to a quarter of the device memory (at most 48 GB)
+ * mapped between calls, so that repeated builds do not map it again.  This call returns every
+ * cached, unused byte of those pools to the device.  WSBM_OK or WSBM_ERR_CUDA. */
+int wsbm_trim_memory(void);
+
 #ifdef __cplusplus
 }
 #endif

@@ -119,6 +119,8 @@ def lib():
             getattr(L, f).restype = ctypes.c_int
         L.wsbm_strerror.argtypes = [ctypes.c_int]
         L.wsbm_strerror.restype = ctypes.c_char_p
+        L.wsbm_trim_memory.argtypes = []
+        L.wsbm_trim_memory.restype = ctypes.c_int
         for f in ("wsbm_hankel01", "wsbm_entries_raw", "wsbm_proxy_block", "wsbm_create",
                   "wsbm_factor", "wsbm_rhs_planewave", "wsbm_solve", "wsbm_farfield",
                   "wsbm_entries", "wsbm_box_info", "wsbm_stats", "wsbm_batch_create",
@@ -143,6 +145,11 @@ def _dev(t, dtype):
 
 def _stream(device=None):
     return ctypes.c_void_p(torch.cuda.current_stream(device).cuda_stream)
+
+
+def trim_memory():
+    """Return the library's cached work-space memory to the device."""
+    _check(lib().wsbm_trim_memory(), "wsbm_trim_memory")
 
 
 def make_geom(curve, device="cuda"):

@@ -3,6 +3,7 @@
 #include <string.h>
 
 #include <atomic>
+#include <mutex>
 
 #include "wsbm_internal.h"
 
@@ -10,6 +11,50 @@ static std::atomic<int64_t> g_launches{0};
 void wsbm_count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 void wsbm_count_launches(int64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 int64_t wsbm_launch_count() { return g_launches.load(std::memory_order_relaxed); }
+
+// One memory pool per device for the work space of the factor and solve.  The default pool
+// unmaps freed memory at every synchronization, so each tree level would map its gigabytes of
+// ID matrices again; this pool keeps up to a quarter of the device memory (at most 48 GB)
+// mapped between calls.  wsbm_trim_memory() hands the cached part back.
+static std::mutex g_pool_mu;
+static cudaMemPool_t g_pool[64];
+
+static cudaMemPool_t lib_pool(int dev) {
+  if (dev < 0 || dev >= 64) return nullptr;
+  std::lock_guard<std::mutex> lk(g_pool_mu);
+  if (!g_pool[dev]) {
+    cudaMemPoolProps props;
+    memset(&props, 0, sizeof(props));
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    cudaMemPool_t pool = nullptr;
+    if (cudaMemPoolCreate(&pool, &props) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    cudaDeviceProp prop;
+    uint64_t thr = 0;
+    if (cudaGetDeviceProperties(&prop, dev) == cudaSuccess) thr = prop.totalGlobalMem / 4;
+    if (thr > (48ull << 30)) thr = 48ull << 30;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    g_pool[dev] = pool;
+  }
+  return g_pool[dev];
+}
+
+cudaError_t wsbm_malloc_async(void** p, size_t bytes, int dev, cudaStream_t st) {
+  cudaMemPool_t pool = lib_pool(dev);
+  if (!pool) return cudaMallocAsync(p, bytes, st);
+  return cudaMallocFromPoolAsync(p, bytes, pool, st);
+}
+
+extern "C" int wsbm_trim_memory(void) {
+  std::lock_guard<std::mutex> lk(g_pool_mu);
+  for (int d = 0; d < 64; ++d)
+    if (g_pool[d] && cudaMemPoolTrimTo(g_pool[d], 0) != cudaSuccess) return WSBM_ERR_CUDA;
+  return WSBM_OK;
+}
 
 extern "C" const char* wsbm_strerror(int code) {
   switch (code) {

@@ -9,6 +9,8 @@
 void wsbm_count_launch();
 void wsbm_count_launches(int64_t n);  // launches replayed from a captured CUDA graph
 int64_t wsbm_launch_count();
+// Stream-ordered allocation from the library's memory pool of device dev (see capi.cu).
+cudaError_t wsbm_malloc_async(void** p, size_t bytes, int dev, cudaStream_t st);
 
 // C = alpha * op(A) * B + beta * C  (column-major, op(A) m x k, B k x n, C m x n);
 // op(A) = A (ta = 0, A stored m x k) or A^T (ta = 1, A stored k x m).

@@ -151,6 +151,24 @@ def test_sketch_fallback_keeps_accuracy():
     s.close()
 
 
+def test_leaf_boxes_beyond_fused_lu_limit():
+    """Two leaf boxes of 520 nodes (1040 unknowns, above the fused LU + solve kernel's 1024)
+    take the blocked LU and triangular solves; the result stays within 10x tol of the dense
+    oracle, and the memory pool can be trimmed after."""
+    from paper_2607_00790_gb300 import binding
+    c = inputs.star(1040)
+    prm = dict(k0=inputs.k0_for_density(c), n=1.5, leaf=520, nproxy=64, tol=1e-8)
+    ph = oracle.Physics(prm["k0"], n=prm["n"])
+    s = gpu_solver(c, prm)
+    _, u, q = solve_gpu(s, [0.3])
+    st = s.stats()
+    assert st["levels"] >= 1 and st["rank_per_level"][st["levels"]] > 0 and st["lu_matrices"] == 0, st
+    _, ud, qd = dense_reference(c, ph, [0.3])
+    assert rel(u, ud) < 10 * prm["tol"] and rel(q, qd) < 10 * prm["tol"], (rel(u, ud), rel(q, qd))
+    s.close()
+    binding.trim_memory()
+
+
 def test_single_box_tree():
     c = inputs.star(48)
     prm = dict(k0=3.0, n=1.5, leaf=64, nproxy=16, tol=1e-10)
