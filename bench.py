@@ -37,9 +37,13 @@ KERNEL_COUNTS = {
     "src_sha": "0b66cd3acb2ca2d7",
     "k_proxy": {"fp64_flops_per_pair": 333.1, "dram_bytes_per_pair": 63.5},
     "k_pairs": {"fp64_flops_per_pair": 377.3, "dram_bytes_per_pair": 64.4},
-    # DRAM traffic of the column-pivoted QR per ID matrix of this workload, keyed by the dense.cu
-    # hash and the matrix rows it was measured on (None: not measured for the current shape)
+    # DRAM traffic of the column-pivoted QR per ID matrix of this workload, keyed by the hash of
+    # its dense.cu section and the matrix rows it was measured on
     "k_cpqr": {"src_sha": "845cb05fd193638d", "rows": 128, "dram_bytes_per_matrix": 6.27e7},
+    # DRAM traffic of the two fused LU + solve launches of a leaf level (box LU with D^-1 L of
+    # 256 unknowns, and Dhat), per factored matrix: 25.71 GB over the 1024 matrices of the
+    # 512 leaf boxes of the same star at N = 65536 (boxes of the same size and ranks)
+    "k_lu_solve_fused": {"src_sha": "f6983435ab7b8259", "dram_bytes_per_matrix": 25.711e9 / 1024},
 }
 # FP64 peak from the unit counts: 152 SMs x 4 FP64 flops/clk/SM (2 DFMA) x 2.07 GHz.
 FP64_PEAK_TFLOPS = 152 * 4 * 2.07e9 / 1e12
