@@ -57,6 +57,10 @@ def _lib():
         lib.orc_field.argtypes = geo + [_pd, _pd, _i64, _pd, _pd, _i64, _pd,
                                         ctypes.POINTER(ctypes.c_int32)]
         lib.orc_field.restype = ctypes.c_int
+        lib.orc_form_dense.argtypes = geo + [ctypes.c_int32, _pd]
+        lib.orc_form_dense.restype = ctypes.c_int
+        lib.orc_layer_ops.argtypes = geo[:9] + [_pd]
+        lib.orc_layer_ops.restype = ctypes.c_int
         for f in (lib.orc_hankel01, lib.orc_f1, lib.orc_wsbm_entries, lib.orc_wsbm_dense,
                   lib.orc_wsbm_matvec, lib.orc_proxy_circle, lib.orc_proxy_row_block,
                   lib.orc_proxy_col_block, lib.orc_wsbm_bilinear_tangent):
@@ -237,6 +241,53 @@ def rhs_planewave(curve, phys, angles):
         duin = 1j * phys.k0 * (dx * nx + dy * ny) * uin
         b[n:, a] = -uin - phys.alpha * duin
     return b
+
+
+# --------------------------------------------- the comparison formulations (eqs. bm, pmchwt) ----
+FORM_WSBM, FORM_BM, FORM_PMCHWT = 0, 1, 2
+
+
+def form_dense(curve, phys, form):
+    """Dense 2N x 2N matrix, unknowns [u ; q]: form 0 eq. (weakly_bm), 1 eq. (bm), 2 eq.
+    (pmchwt) with its columns in the order (u, q).  N_k alone (forms 1, 2) takes the one-point
+    correction -pi/(6 w_i) of its 1/r^2 part plus the log correction; its O(1) diagonal term
+    is left out, so both converge at first order (Sec. II, after eq. (bm))."""
+    g = _geo(curve)
+    n = g[0].size
+    out = np.empty(2 * (2 * n) * (2 * n))
+    rc = _lib().orc_form_dense(n, *[_p(a) for a in g], *phys.args(), int(form), _p(out))
+    if rc:
+        raise ValueError(f"form {form}")
+    return out.view(np.complex128).reshape(2 * n, 2 * n).T
+
+
+def form_rhs(curve, phys, angles, form):
+    """Right-hand sides for plane waves: forms 0 and 1 [0 ; -u_in - alpha du_in/dn] (eqs.
+    weakly_bm, bm), form 2 [-u_in ; -eps0^-1 du_in/dn] (eq. pmchwt)."""
+    if form in (FORM_WSBM, FORM_BM):
+        return rhs_planewave(curve, phys, angles)
+    angles = np.atleast_1d(np.asarray(angles, dtype=np.float64))
+    x, y, nx, ny = (np.asarray(curve[k]) for k in ("x", "y", "nx", "ny"))
+    n = x.size
+    b = np.zeros((2 * n, angles.size), dtype=np.complex128)
+    for a, th in enumerate(angles):
+        dx, dy = np.cos(th), np.sin(th)
+        uin = np.exp(1j * phys.k0 * (dx * x + dy * y))
+        b[:n, a] = -uin
+        b[n:, a] = -(1j * phys.k0 * (dx * nx + dy * ny) * uin) / phys.eps0
+    return b
+
+
+def layer_ops(curve, k0, k1):
+    """The discretized S, D, D*, N at k0 and k1 (one-point corrected diagonals, weights folded
+    in) as a dict of N x N complex matrices: S0, S1, D0, D1, Ds0, Ds1, N0, N1."""
+    g = _geo(curve)
+    n = g[0].size
+    out = np.empty(2 * 8 * n * n)
+    _lib().orc_layer_ops(n, *[_p(a) for a in g], float(k0), float(k1), _p(out))
+    m = out.view(np.complex128).reshape(8, n, n)
+    names = ("S0", "S1", "D0", "D1", "Ds0", "Ds1", "N0", "N1")
+    return {nm: m[t].T.copy() for t, nm in enumerate(names)}
 
 
 def dense_solve(A, b):

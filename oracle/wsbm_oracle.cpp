@@ -19,6 +19,8 @@
 //     and the smooth limits of D and D* (curvature term).
 //   * Proxy-circle blocks used by the proxy-surface interpolative decomposition (Sec. III,
 //     proxy-surface low-rank approximation).
+//   * The standard Burton-Miller (eq. bm) and PMCHWT (eq. pmchwt) matrices, with a one-point
+//     correction of the hypersingular N_k (first-order accurate, as the paper reports).
 //   * Directional derivatives of lam^T A x along tangents of the node data, k1 and eps1, by
 //     evaluating the same block definitions in dual-number arithmetic (forward mode).  The
 //     paper does not differentiate its solver; this serves the shape-gradient tests.
@@ -121,14 +123,21 @@ static void pair_block_offdiag(const Geom& g, const Params& p, int64_t i, int64_
 //   N_k0 - N_k1: a = -(k0^2-k1^2)/(4pi),
 //                b = i(k0^2-k1^2)/8 - [k0^2(ln(k0/2)+gamma-1/2) - k1^2(ln(k1/2)+gamma-1/2)]/(4pi)
 // plus the identity terms of eq. (weakly_bm).
+// corrected diagonal of S_k, and the k-dependent log and smooth parts of N_k (times 4 pi / w_i)
+static cplx s_diag(double k, double wi) {
+  const cplx I1(0.0, 1.0);
+  return wi * (0.25 * I1 - (EULER_GAMMA + std::log(k * wi / (4.0 * PI))) / (2.0 * PI));
+}
+static double n_log_part(double k, double wi) {
+  return k * k * (std::log(k * wi / (4.0 * PI)) + EULER_GAMMA - 0.5);
+}
+
 static void pair_block_diag(const Geom& g, const Params& p, int64_t i, cplx a[2][2]) {
   const cplx I1(0.0, 1.0);
   double wi = g.w[i];
   double kap = g.kappa[i];
-  auto S = [&](double k) {
-    return wi * (0.25 * I1 - (EULER_GAMMA + std::log(k * wi / (4.0 * PI))) / (2.0 * PI));
-  };
-  auto f = [&](double k) { return k * k * (std::log(k * wi / (4.0 * PI)) + EULER_GAMMA - 0.5); };
+  auto S = [&](double k) { return s_diag(k, wi); };
+  auto f = [&](double k) { return n_log_part(k, wi); };
   double Dd = -wi * kap / (4.0 * PI);
   cplx dN = wi * (I1 * (p.k0 * p.k0 - p.k1 * p.k1) / 8.0 - (f(p.k0) - f(p.k1)) / (4.0 * PI));
   cplx alpha = I1 / p.k0;
@@ -143,6 +152,93 @@ static void pair_block(const Geom& g, const Params& p, int64_t i, int64_t j, cpl
     pair_block_diag(g, p, i, a);
   else
     pair_block_offdiag(g, p, i, j, a);
+}
+
+// ---------------------------------------------------------------------------------------
+// The two formulations the paper sets against eq. (weakly_bm) (Sec. II): the PMCHWT equation
+// (eq. pmchwt) and the standard Burton-Miller equation (eq. bm).  Both contain N_k alone, whose
+// kernel is hypersingular: near the diagonal, in the curve parameter t with trapezoidal step h
+// and speed |x'|,  N_k(x(s), x(t)) |x'(t)| = 1/(2 pi |x'| (t-s)^2) + O(1/(t-s))
+// - (k^2/4pi) |x'| ln|t-s| + O(1).  One-point correction of the diagonal (reading of the
+// zeta-corrected rule for the hypersingular operator; the paper does not print it):
+//   * the 1/(t-s)^2 part: the punctured sum h sum_{j!=0} g(jh)/(jh)^2 exceeds the finite-part
+//     integral by 2 zeta(2) g(0)/h, so the diagonal weight is -(pi^2/3h) / (2 pi |x'|)
+//     = -pi / (6 w_i)  (w_i = h |x'_i|);
+//   * the log part: the weight w_i [a ln(w_i/2pi) + b] as for S_k, with a = -k^2/(4pi) and
+//     b = i k^2/8 - k^2 (ln(k/2) + gamma - 1/2)/(4pi) (the k-dependent smooth limit);
+//   * the O(1) term of the expansion (a curvature term of the Laplace hypersingular kernel)
+//     is not corrected: it leaves an O(h) error, the first-order convergence the paper
+//     reports for both formulations.
+// In N_k0 - N_k1 the -pi/(6 w_i) weights cancel and the rest reproduces the diagonal of
+// eq. (weakly_bm) above.
+// ---------------------------------------------------------------------------------------
+struct Ops {
+  cplx S[2], D[2], Dx[2], N[2];  // index 0: k0, 1: k1; quadrature weight w_j folded in
+};
+
+static void pair_ops_offdiag(const Geom& g, const Params& p, int64_t i, int64_t j, Ops& o) {
+  const cplx I1(0.0, 1.0);
+  double dx = g.x[i] - g.x[j];
+  double dy = g.y[i] - g.y[j];
+  double r2 = dx * dx + dy * dy;
+  double r = std::sqrt(r2);
+  double dny = dx * g.nx[j] + dy * g.ny[j];
+  double dnx = dx * g.nx[i] + dy * g.ny[i];
+  double nn = g.nx[i] * g.nx[j] + g.ny[i] * g.ny[j];
+  double c = (dnx * dny) / r2;
+  double wj = g.w[j];
+  const double ks[2] = {p.k0, p.k1};
+  for (int t = 0; t < 2; ++t) {
+    const double k = ks[t];
+    Hank h = hankel_eval(k * r);
+    o.S[t] = wj * 0.25 * I1 * h.h0;
+    o.D[t] = wj * 0.25 * I1 * k * h.h1 * (dny / r);
+    o.Dx[t] = -wj * 0.25 * I1 * k * h.h1 * (dnx / r);
+    // N_k = (i k^2/4) [H0 c + H1/(kr) (nn - 2c)]
+    o.N[t] = wj * 0.25 * I1 * k * k * (h.h0 * c + h.h1 / (k * r) * (nn - 2.0 * c));
+  }
+}
+
+static void pair_ops_diag(const Geom& g, const Params& p, int64_t i, Ops& o) {
+  const cplx I1(0.0, 1.0);
+  double wi = g.w[i];
+  double kap = g.kappa[i];
+  const double ks[2] = {p.k0, p.k1};
+  for (int t = 0; t < 2; ++t) {
+    const double k = ks[t];
+    o.S[t] = s_diag(k, wi);
+    o.D[t] = -wi * kap / (4.0 * PI);
+    o.Dx[t] = o.D[t];
+    o.N[t] = wi * (I1 * k * k / 8.0 - n_log_part(k, wi) / (4.0 * PI)) - PI / (6.0 * wi);
+  }
+}
+
+// 2x2 block of a formulation, unknowns (u, q) in this order for all three:
+//   form 1, eq. (bm):     [ D_k1 + I/2,          -eps1 S_k1                  ]
+//                          [ D_k0 - I/2 + a N_k0, -eps0 (S_k0 + a (D*_k0 + I/2)) ]
+//   form 2, eq. (pmchwt), its columns in the order (u, q):
+//                          [ D_k0 + D_k1,              -(eps0 S_k0 + eps1 S_k1) ]
+//                          [ N_k0/eps0 + N_k1/eps1,    -(D*_k0 + D*_k1)          ]
+static void form_block(const Geom& g, const Params& p, int form, int64_t i, int64_t j, cplx a[2][2]) {
+  const cplx I1(0.0, 1.0);
+  Ops o;
+  if (i == j)
+    pair_ops_diag(g, p, i, o);
+  else
+    pair_ops_offdiag(g, p, i, j, o);
+  const double id = (i == j) ? 0.5 : 0.0;
+  const cplx alpha = I1 / p.k0;
+  if (form == 1) {
+    a[0][0] = o.D[1] + id;
+    a[0][1] = -p.eps1 * o.S[1];
+    a[1][0] = o.D[0] - id + alpha * o.N[0];
+    a[1][1] = -p.eps0 * (o.S[0] + alpha * (o.Dx[0] + id));
+  } else {
+    a[0][0] = o.D[0] + o.D[1];
+    a[0][1] = -(p.eps0 * o.S[0] + p.eps1 * o.S[1]);
+    a[1][0] = o.N[0] / p.eps0 + o.N[1] / p.eps1;
+    a[1][1] = -(o.Dx[0] + o.Dx[1]);
+  }
 }
 
 // ---------------------------------------------------------------------------------------
@@ -401,6 +497,59 @@ int orc_wsbm_dense(int64_t n, const double* x, const double* y, const double* nx
         }
     }
   }
+  return 0;
+}
+
+// Dense 2N x 2N matrix of form 1 (eq. bm) or 2 (eq. pmchwt, columns (u, q)), paper order
+// [u ; q] columns and [eq1 ; eq2] rows as orc_wsbm_dense; form 0 is eq. (weakly_bm).
+int orc_form_dense(int64_t n, const double* x, const double* y, const double* nx, const double* ny,
+                   const double* w, const double* kappa, double k0, double k1, double eps0,
+                   double eps1, int32_t form, double* out) {
+  if (form < 0 || form > 2) return -1;
+  Geom g{n, x, y, nx, ny, w, kappa};
+  Params p{k0, k1, eps0, eps1};
+  int64_t ld2 = 2 * n;
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int64_t j = 0; j < n; ++j) {
+    for (int64_t i = 0; i < n; ++i) {
+      cplx blk[2][2];
+      if (form == 0)
+        pair_block(g, p, i, j, blk);
+      else
+        form_block(g, p, form, i, j, blk);
+      for (int a = 0; a < 2; ++a)
+        for (int b = 0; b < 2; ++b) {
+          int64_t r = a * n + i, c = b * n + j;
+          out[2 * (c * ld2 + r)] = blk[a][b].real();
+          out[2 * (c * ld2 + r) + 1] = blk[a][b].imag();
+        }
+    }
+  }
+  return 0;
+}
+
+// The four layer operators at k0 and k1 as dense N x N matrices (one-point corrected
+// diagonal as above, weights folded in): out = [S0, S1, D0, D1, D*0, D*1, N0, N1], each N x N
+// column-major complex128.
+int orc_layer_ops(int64_t n, const double* x, const double* y, const double* nx, const double* ny,
+                  const double* w, const double* kappa, double k0, double k1, double* out) {
+  Geom g{n, x, y, nx, ny, w, kappa};
+  Params p{k0, k1, 1.0, 1.0};
+  const int64_t nn = n * n;
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int64_t j = 0; j < n; ++j)
+    for (int64_t i = 0; i < n; ++i) {
+      Ops o;
+      if (i == j)
+        pair_ops_diag(g, p, i, o);
+      else
+        pair_ops_offdiag(g, p, i, j, o);
+      const cplx v[8] = {o.S[0], o.S[1], o.D[0], o.D[1], o.Dx[0], o.Dx[1], o.N[0], o.N[1]};
+      for (int t = 0; t < 8; ++t) {
+        out[2 * (t * nn + j * n + i)] = v[t].real();
+        out[2 * (t * nn + j * n + i) + 1] = v[t].imag();
+      }
+    }
   return 0;
 }
 

@@ -1,0 +1,97 @@
+"""Oracle of the two comparison formulations of Sec. II, the PMCHWT equation (eq. pmchwt) and
+the standard Burton-Miller equation (eq. bm), against what the paper and the mathematics fix:
+
+* on the disk, WSBM converges at third order and BM and PMCHWT at first order to the Mie series
+  (the paper's convergence comparison, Sec. IV: WSBM O(h^3), PMCHWT and BM O(h));
+* the discretized hypersingular operator N_k has the circle eigenvalues (i pi k^2 R/2) J_m' H_m'
+  (separation of variables) up to O(h). Dropping its one-point correction, a mistake planted
+  here in the assembled matrix on the CPU, leaves an O(1) error;
+* eq. (weakly_bm) is eq. (bm) minus alpha times the interior Neumann trace equation: the
+  assembled matrices satisfy that identity entry by entry, which ties every k-dependent part
+  of the N_k diagonal to the already pinned WSBM diagonal.
+"""
+import numpy as np
+import pytest
+from scipy.special import h1vp, jvp
+
+import oracle
+from paper_2607_00790_gb300 import inputs
+
+
+def _disk_errors(form, Ns=(64, 128, 256, 512)):
+    out = []
+    for N in Ns:
+        c, prm = inputs.workload("disk", N=N)
+        ph = oracle.Physics(prm["k0"], n=prm["n"])
+        x = oracle.dense_solve(oracle.form_dense(c, ph, form), oracle.form_rhs(c, ph, [0.0], form))
+        th = np.arctan2(np.asarray(c["y"]), np.asarray(c["x"]))
+        ue, qe = oracle.mie_boundary(1.0, ph, th)
+        u, q = x[:N, 0], x[N:, 0]
+        out.append((np.linalg.norm(u.real - ue.real) / np.linalg.norm(ue.real),
+                    np.linalg.norm(q - qe) / np.linalg.norm(qe)))
+    return np.array(out)
+
+
+def test_convergence_orders_on_the_disk():
+    e_w = _disk_errors(oracle.FORM_WSBM)
+    e_b = _disk_errors(oracle.FORM_BM)
+    e_p = _disk_errors(oracle.FORM_PMCHWT)
+    s_w = np.log2(e_w[:-1, 0] / e_w[1:, 0])
+    s_b = np.log2(e_b[:-1, 0] / e_b[1:, 0])
+    s_p = np.log2(e_p[:-1, 0] / e_p[1:, 0])
+    assert np.all(np.abs(s_w - 3.0) < 0.1), s_w
+    # first order, approached from below for BM (the O(h) term dominates from N = 128 on)
+    assert np.all(np.abs(s_b[1:] - 1.0) < 0.15) and np.all(np.abs(s_p - 1.0) < 0.15), (s_b, s_p)
+    # q converges at the same orders
+    assert np.all(np.log2(e_b[1:-1, 1] / e_b[2:, 1]) > 0.85)
+    assert np.all(np.log2(e_p[1:-1, 1] / e_p[2:, 1]) > 0.85)
+    # at every N the weakly singular formulation is the most accurate
+    assert np.all(e_w[:, 0] < e_b[:, 0]) and np.all(e_w[:, 0] < e_p[:, 0])
+
+
+@pytest.mark.parametrize("m", [0, 1, 3])
+def test_hypersingular_circle_eigenvalues_first_order(m):
+    errs = []
+    for N in (256, 512, 1024):
+        c, prm = inputs.workload("disk", N=N)
+        k = prm["k0"]
+        ops = oracle.layer_ops(c, k, 1.5 * k)
+        th = np.arctan2(np.asarray(c["y"]), np.asarray(c["x"]))
+        v = np.exp(1j * m * th)
+        lam = (1j * np.pi * k * k / 2) * jvp(m, k) * h1vp(m, k)
+        errs.append(np.linalg.norm(ops["N0"] @ v - lam * v) / np.linalg.norm(lam * v))
+        if N == 256:
+            w = np.asarray(c["w"])
+            dropped = ops["N0"] + np.diag(np.pi / (6 * w))
+            assert np.linalg.norm(dropped @ v - lam * v) / np.linalg.norm(lam * v) > 1.0
+    ratio = np.array(errs[:-1]) / np.array(errs[1:])
+    assert np.all(np.abs(ratio - 2.0) < 0.2), ratio
+    assert errs[-1] < 2e-3, errs
+
+
+def test_wsbm_is_bm_minus_alpha_interior_neumann():
+    n = 96
+    c = inputs.star(n)  # a curve with varying curvature and speed
+    ph = oracle.Physics(float(inputs.k0_for_density(c)), n=1.5)
+    A0 = oracle.form_dense(c, ph, oracle.FORM_WSBM)
+    A1 = oracle.form_dense(c, ph, oracle.FORM_BM)
+    ops = oracle.layer_ops(c, ph.k0, ph.k1)
+    eye = np.eye(n)
+    R = A1[n:].copy()
+    R[:, :n] -= ph.alpha * ops["N1"]
+    R[:, n:] -= ph.alpha * (-ph.eps1 * (ops["Ds1"] - eye / 2))
+    assert np.abs(R - A0[n:]).max() <= 1e-13 * np.abs(A0[n:]).max()
+    assert np.abs(A1[:n] - A0[:n]).max() <= 1e-15 * np.abs(A0[:n]).max()
+
+
+def test_pmchwt_blocks_from_the_layer_operators():
+    """Eq. (pmchwt) assembled here from the discretized operators: the sums of the exterior
+    and interior Dirichlet and Neumann trace equations, columns (u, q)."""
+    n = 80
+    c = inputs.star(n)
+    ph = oracle.Physics(float(inputs.k0_for_density(c)), n=1.5)
+    A = oracle.form_dense(c, ph, oracle.FORM_PMCHWT)
+    o = oracle.layer_ops(c, ph.k0, ph.k1)
+    B = np.block([[o["D0"] + o["D1"], -(ph.eps0 * o["S0"] + ph.eps1 * o["S1"])],
+                  [o["N0"] / ph.eps0 + o["N1"] / ph.eps1, -(o["Ds0"] + o["Ds1"])]])
+    assert np.abs(A - B).max() <= 1e-14 * np.abs(B).max()
