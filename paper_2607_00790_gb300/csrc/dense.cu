@@ -8,6 +8,8 @@
 // The O(n^3) work is in the GEMM kernel, which tiles every matrix of the batch over many CTAs.
 #include <math.h>
 
+#include <algorithm>
+
 #include "dense.h"
 
 #define GT 32  // GEMM tile (GT x GT outputs per CTA)
@@ -817,8 +819,18 @@ static int tiles_x(int64_t tiles) {
   return (int)(tiles < 1 ? 1 : (tiles < cap ? tiles : cap));
 }
 
+// The batched kernels below index their descriptor by blockIdx.y; a batch of more than
+// LAUNCH_MAX_Y matrices runs as consecutive chunks (the matrices are independent).
+#define LAUNCH_MAX_Y 65535
+
 int wsbm_gemm_batched(const GemmDesc* d_desc, int nbatch, int max_m, int max_n, cudaStream_t st) {
   if (nbatch <= 0) return 0;
+  if (nbatch > LAUNCH_MAX_Y) {
+    for (int c = 0; c < nbatch; c += LAUNCH_MAX_Y)
+      if (int rc = wsbm_gemm_batched(d_desc + c, std::min(LAUNCH_MAX_Y, nbatch - c), max_m, max_n, st))
+        return rc;
+    return 0;
+  }
   int64_t t = (int64_t)((max_m + GT - 1) / GT) * ((max_n + GT - 1) / GT);
   dim3 grid(tiles_x(t), nbatch);
   k_gemm<<<grid, 256, 0, st>>>(d_desc, nbatch);
@@ -828,6 +840,13 @@ int wsbm_gemm_batched(const GemmDesc* d_desc, int nbatch, int max_m, int max_n, 
 
 int wsbm_lu_batched(const LuDesc* d_desc, int nbatch, int max_n, int* d_info, cudaStream_t st) {
   if (nbatch <= 0) return 0;
+  if (nbatch > LAUNCH_MAX_Y) {
+    for (int c = 0; c < nbatch; c += LAUNCH_MAX_Y)
+      if (int rc = wsbm_lu_batched(d_desc + c, std::min(LAUNCH_MAX_Y, nbatch - c), max_n,
+                                   d_info ? d_info + c : nullptr, st))
+        return rc;
+    return 0;
+  }
   for (int j0 = 0; j0 < max_n; j0 += WSBM_NB) {
     k_lu_panel<<<nbatch, 256, 0, st>>>(d_desc, j0, WSBM_NB, d_info);
     wsbm_count_launch();
@@ -851,6 +870,13 @@ int wsbm_lu_batched(const LuDesc* d_desc, int nbatch, int max_n, int* d_info, cu
 int wsbm_trsm_batched(const TrsmDesc* d_desc, int nbatch, int max_n, int max_nrhs, int lower,
                       cudaStream_t st) {
   if (nbatch <= 0 || max_n <= 0 || max_nrhs <= 0) return 0;
+  if (nbatch > LAUNCH_MAX_Y) {
+    for (int c = 0; c < nbatch; c += LAUNCH_MAX_Y)
+      if (int rc = wsbm_trsm_batched(d_desc + c, std::min(LAUNCH_MAX_Y, nbatch - c), max_n, max_nrhs,
+                                     lower, st))
+        return rc;
+    return 0;
+  }
   dim3 gd(tiles_x((max_nrhs + 127) / 128), nbatch);
   if (lower) {
     for (int j0 = 0; j0 < max_n; j0 += WSBM_NB) {
@@ -885,6 +911,13 @@ int wsbm_trsm_batched(const TrsmDesc* d_desc, int nbatch, int max_n, int max_nrh
 int wsbm_lu_solve_batched(const TrsmDesc* d_desc_lower, const TrsmDesc* d_desc_upper, int nbatch,
                           int max_n, int max_nrhs, cudaStream_t st) {
   if (nbatch <= 0) return 0;
+  if (nbatch > LAUNCH_MAX_Y) {
+    for (int c = 0; c < nbatch; c += LAUNCH_MAX_Y)
+      if (int rc = wsbm_lu_solve_batched(d_desc_lower + c, d_desc_upper + c,
+                                         std::min(LAUNCH_MAX_Y, nbatch - c), max_n, max_nrhs, st))
+        return rc;
+    return 0;
+  }
   dim3 gd(tiles_x((max_nrhs + 127) / 128), nbatch);
   k_apply_piv<<<gd, 128, 0, st>>>(d_desc_lower);
   wsbm_count_launch();
@@ -933,6 +966,13 @@ int wsbm_cpqr_finish(const QrDesc* d_desc, int nbatch, cudaStream_t st) {
 int wsbm_lu_solve_t_batched(const TrsmDesc* d_desc, int nbatch, int max_n, int max_nrhs,
                             cudaStream_t st) {
   if (nbatch <= 0) return 0;
+  if (nbatch > LAUNCH_MAX_Y) {
+    for (int c = 0; c < nbatch; c += LAUNCH_MAX_Y)
+      if (int rc = wsbm_lu_solve_t_batched(d_desc + c, std::min(LAUNCH_MAX_Y, nbatch - c), max_n,
+                                           max_nrhs, st))
+        return rc;
+    return 0;
+  }
   int rc = wsbm_trsm_batched(d_desc, nbatch, max_n, max_nrhs, 1, st);  // U^T, forward
   if (rc) return rc;
   rc = wsbm_trsm_batched(d_desc, nbatch, max_n, max_nrhs, 0, st);  // L^T, backward

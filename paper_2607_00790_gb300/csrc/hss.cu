@@ -314,6 +314,18 @@ __global__ void __launch_bounds__(256) k_farfield(DevGeom g, double k0, double e
 }
 
 // ------------------------------------------------------------------ host helpers ----
+// Launch a kernel whose blockIdx.y indexes a descriptor array d[0..n), in chunks of at most
+// 65535 descriptors (the grid's y limit), 256 threads a block.
+template <class D, class... KA, class... A>
+static void launch_y(void (*kern)(const D*, KA...), unsigned gx, int64_t n, const D* d,
+                     cudaStream_t st, A... args) {
+  for (int64_t y0 = 0; y0 < n; y0 += 65535) {
+    const unsigned gy = (unsigned)std::min<int64_t>(65535, n - y0);
+    kern<<<dim3(gx, gy), 256, 0, st>>>(d + y0, args...);
+    wsbm_count_launch();
+  }
+}
+
 static int gridfor(int64_t work, int per = 256) {
   int64_t b = (work + per - 1) / per;
   if (b < 1) b = 1;
@@ -923,8 +935,7 @@ static int factor_levels(const std::vector<wsbm_hss*>& hs, const std::vector<int
     HK(upload(h0, copies, &dc, tmp));
     int64_t mx = 0;
     for (auto& c : copies) mx = std::max(mx, (int64_t)c.m * c.n);
-    k_copy2d<<<dim3(gridfor(mx), (unsigned)copies.size()), 256, 0, st>>>(dc);
-    wsbm_count_launch();
+    launch_y(k_copy2d, gridfor(mx), (int64_t)copies.size(), dc, st);
   }
   HK(pb.prepare(h0, tmp));
   for (auto& xb : xbp) HK(xb.prepare(h0, tmp));
@@ -1304,8 +1315,7 @@ static int factor_levels(const std::vector<wsbm_hss*>& hs, const std::vector<int
     HK(upload(h0, fz, &dfz, tmp));
     HK(upload(h0, fm, &dfm, tmp));
   }
-  k_build_L<<<dim3(gridfor(maxnk), NB), 256, 0, st>>>(dbl);
-  wsbm_count_launch();
+  launch_y(k_build_L, gridfor(maxnk), NB, dbl, st);
   if (dfz) {
     HC(cudaEventRecord(h0->ev[8], st));
     HK(wsbm_lu_solve_fused_batched(dfz, NB, maxn, maxn + maxk, st));
@@ -1314,17 +1324,13 @@ static int factor_levels(const std::vector<wsbm_hss*>& hs, const std::vector<int
     HK(wsbm_lu_batched(dluD, NB, maxn, nullptr, st));
     HK(wsbm_lu_solve_batched(dzl, dzl, NB, maxn, maxk, st));
   }
-  k_gather_rows<<<dim3(gridfor(maxnk), NB), 256, 0, st>>>(dgz);
-  wsbm_count_launch();
-  k_copy2d<<<dim3(gridfor((int64_t)maxk * maxk), NB), 256, 0, st>>>(dpc);
-  wsbm_count_launch();
+  launch_y(k_gather_rows, gridfor(maxnk), NB, dgz, st);
+  launch_y(k_copy2d, gridfor((int64_t)maxk * maxk), NB, dpc, st);
   if (!gm.empty()) HK(wsbm_gemm_batched(dgm, (int)gm.size(), maxk, maxk, st));
   if (!tcc.empty()) {
-    k_copy2d<<<dim3(gridfor(maxnk), (unsigned)tcc.size()), 256, 0, st>>>(dtcc);
-    wsbm_count_launch();
+    launch_y(k_copy2d, gridfor(maxnk), (int64_t)tcc.size(), dtcc, st);
   }
-  k_fill_identity_batched<<<dim3(gridfor((int64_t)maxk * maxk), NB), 256, 0, st>>>(didd);
-  wsbm_count_launch();
+  launch_y(k_fill_identity_batched, gridfor((int64_t)maxk * maxk), NB, didd, st);
   if (dfm) {
     HC(cudaEventRecord(h0->ev[10], st));
     HK(wsbm_lu_solve_fused_batched(dfm, NB, maxk, 2 * maxk, st));
@@ -1347,8 +1353,7 @@ static int factor_levels(const std::vector<wsbm_hss*>& hs, const std::vector<int
     }
     CopyIntDesc* dpcd = nullptr;
     HK(upload(h0, pcd, &dpcd, tmp));
-    k_copy_int<<<dim3(gridfor(maxpn), NB), 256, 0, st>>>(dpcd);
-    wsbm_count_launch();
+    launch_y(k_copy_int, gridfor(maxpn), NB, dpcd, st);
   }
   HC(cudaEventRecord(h0->ev[3], st));
   HC(cudaStreamSynchronize(st));
@@ -1449,8 +1454,7 @@ static int factor_roots(const std::vector<wsbm_hss*>& hs, double ms_out[2]) {
     HK(upload(h0, copies, &dc, tmp));
     int64_t mx = 0;
     for (auto& c : copies) mx = std::max(mx, (int64_t)c.m * c.n);
-    k_copy2d<<<dim3(gridfor(mx), (unsigned)copies.size()), 256, 0, st>>>(dc);
-    wsbm_count_launch();
+    launch_y(k_copy2d, gridfor(mx), (int64_t)copies.size(), dc, st);
   }
   HK(pb.prepare(h0, tmp));
   LuDesc* dl = nullptr;
@@ -1792,8 +1796,7 @@ static int plan_copies(SolvePlan& P, const std::vector<CopyDesc>& c) {
   for (auto& x : c) mx = std::max(mx, (int64_t)x.m * x.n);
   const unsigned nb = (unsigned)c.size();
   P.ops.push_back([d, mx, nb](cudaStream_t st) {
-    k_copy2d<<<dim3(gridfor(mx), nb), 256, 0, st>>>(d);
-    wsbm_count_launch();
+    launch_y(k_copy2d, gridfor(mx), nb, d, st);
     return WSBM_OK;
   });
   return WSBM_OK;
@@ -1832,8 +1835,7 @@ static int plan_gathers(SolvePlan& P, const std::vector<GatherDesc>& g) {
   for (auto& x : g) mx = std::max(mx, (int64_t)x.n * x.ncol);
   const unsigned nb = (unsigned)g.size();
   P.ops.push_back([d, mx, nb](cudaStream_t st) {
-    k_gather_rows<<<dim3(gridfor(mx), nb), 256, 0, st>>>(d);
-    wsbm_count_launch();
+    launch_y(k_gather_rows, gridfor(mx), nb, d, st);
     return WSBM_OK;
   });
   return WSBM_OK;
@@ -1929,8 +1931,7 @@ static int plan_build(SolvePlan& P) {
     HK(plan_upload(P, cv, &d));
     const unsigned nb = (unsigned)cv.size();
     P.ops.push_back([d, mx, nb, nrhs](cudaStream_t st) {
-      k_to_interleaved_batched<<<dim3(gridfor(mx), nb), 256, 0, st>>>(d, nrhs);
-      wsbm_count_launch();
+      launch_y(k_to_interleaved_batched, gridfor(mx), nb, d, st, nrhs);
       return WSBM_OK;
     });
   }
@@ -2048,8 +2049,7 @@ static int plan_build(SolvePlan& P) {
     HK(plan_upload(P, cv, &d));
     const unsigned nb = (unsigned)cv.size();
     P.ops.push_back([d, mx, nb, nrhs](cudaStream_t st) {
-      k_split_uq_batched<<<dim3(gridfor(mx), nb), 256, 0, st>>>(d, nrhs);
-      wsbm_count_launch();
+      launch_y(k_split_uq_batched, gridfor(mx), nb, d, st, nrhs);
       return WSBM_OK;
     });
   }
@@ -2281,8 +2281,7 @@ extern "C" int wsbm_solve_transposed(wsbm_hss_t h, const void* rhs, int32_t nrhs
     HK(upload(h, c1, &d1, tmp));
     HK(upload(h, g1, &dg1, tmp));
     HK(upload(h, g2, &dg2, tmp));
-    k_copy2d<<<dim3(gridfor((int64_t)maxn * nrhs), (unsigned)c1.size()), 256, 0, st>>>(d1);
-    wsbm_count_launch();
+    launch_y(k_copy2d, gridfor((int64_t)maxn * nrhs), (int64_t)c1.size(), d1, st);
     HK(wsbm_gemm_batched(dg1, nb, lk, nrhs, st));
     HK(wsbm_gemm_batched(dg2, nb, lk, nrhs, st));
   }
@@ -2299,8 +2298,7 @@ extern "C" int wsbm_solve_transposed(wsbm_hss_t h, const void* rhs, int32_t nrhs
     }
     CopyDesc* dc = nullptr;
     HK(upload(h, c, &dc, tmp));
-    k_copy2d<<<dim3(gridfor((int64_t)maxk * nrhs), (unsigned)c.size()), 256, 0, st>>>(dc);
-    wsbm_count_launch();
+    launch_y(k_copy2d, gridfor((int64_t)maxk * nrhs), (int64_t)c.size(), dc, st);
     std::vector<TrsmDesc> v(1, lu_t(h->root, h->root_n, y, h->root_n, h->root_piv, h->root_n, nrhs));
     TrsmDesc* dt = nullptr;
     HK(upload(h, v, &dt, tmp));
@@ -2363,14 +2361,11 @@ extern "C" int wsbm_solve_transposed(wsbm_hss_t h, const void* rhs, int32_t nrhs
     HK(upload(h, g2, &dg2, tmp));
     HK(upload(h, sc, &dsc, tmp));
     HK(upload(h, sd, &dsd, tmp));
-    k_copy2d<<<dim3(gridfor((int64_t)lk * nrhs), nb), 256, 0, st>>>(dcb);
-    wsbm_count_launch();
+    launch_y(k_copy2d, gridfor((int64_t)lk * nrhs), nb, dcb, st);
     HK(wsbm_gemm_batched(dg1, nb, lk, nrhs, st));
-    k_copy2d<<<dim3(gridfor((int64_t)lk * nrhs), nb), 256, 0, st>>>(dcu);
-    wsbm_count_launch();
+    launch_y(k_copy2d, gridfor((int64_t)lk * nrhs), nb, dcu, st);
     if (!g2.empty()) HK(wsbm_gemm_batched(dg2, (int)g2.size(), lr, nrhs, st));
-    k_scatter_sub_rows<<<dim3(gridfor((int64_t)ln * nrhs), nb), 256, 0, st>>>(dsc);
-    wsbm_count_launch();
+    launch_y(k_scatter_sub_rows, gridfor((int64_t)ln * nrhs), nb, dsc, st);
     HK(wsbm_lu_solve_t_batched(dsd, nb, ln, nrhs, st));
   }
   {
@@ -2382,8 +2377,7 @@ extern "C" int wsbm_solve_transposed(wsbm_hss_t h, const void* rhs, int32_t nrhs
     }
     CopyDesc* dc = nullptr;
     HK(upload(h, c, &dc, tmp));
-    k_copy2d<<<dim3(gridfor((int64_t)maxn * nrhs), (unsigned)c.size()), 256, 0, st>>>(dc);
-    wsbm_count_launch();
+    launch_y(k_copy2d, gridfor((int64_t)maxn * nrhs), (int64_t)c.size(), dc, st);
     k_split_uq<<<gridfor(N * nrhs), 256, 0, st>>>(bint, (double2*)lam1, (double2*)lam2, N, nrhs);
     wsbm_count_launch();
   }

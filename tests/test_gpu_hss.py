@@ -262,3 +262,43 @@ def test_full_size_leaf_skeletons_span_far_field():
             rel = np.linalg.norm(R) / np.linalg.norm(A)
             assert rel < 10 * tol, (box, rows_side, rel)
     s.close()
+
+
+def test_leaf_level_of_65536_boxes():
+    """A tree level of 65536 boxes (N = 2^20, leaf 16): every batched launch over the boxes of a
+    level runs in chunks of at most 65535 along the grid's y dimension. The skeletons of a box
+    in the first chunk and of the last box (the second chunk) must reproduce their far-field
+    rows and columns to the ID tolerance (far entries from the oracle)."""
+    from paper_2607_00790_gb300 import binding
+    N = 1 << 20
+    c = inputs.star(N)
+    k0 = float(inputs.k0_for_density(c)) / 4.0  # 60 nodes per wavelength: small box ranks
+    tol = 1e-6
+    g, keep = binding.make_geom(c)
+    p = binding.make_params(k0, 1.5, leaf=16, nproxy=32, id_tol=tol, max_levels=1)
+    s = binding.Solver(g, p)
+    s._keep = keep
+    s.factor()
+    st = s.stats()
+    L = st["levels"]
+    assert st["nboxes_leaf"] == 65536, st["nboxes_leaf"]
+    ph = oracle.Physics(k0, n=1.5)
+    rng = np.random.default_rng(7)
+    for box in (3, 65535):
+        circ, (lo, hi) = s.box_info(L, box)
+        nodes = np.arange(lo, hi)
+        unk = np.concatenate([nodes, nodes + N])
+        jr, jc = s.skeletons(L, box)
+        assert 0 < jr.size < unk.size
+        d = np.hypot(c["x"] - circ[0], c["y"] - circ[1])
+        far_nodes = rng.choice(np.nonzero(d > circ[3])[0], 400, replace=False)
+        far = np.concatenate([far_nodes, far_nodes + N])
+        for rows_side in (True, False):
+            A = oracle.wsbm_entries(c, ph, unk, far) if rows_side else oracle.wsbm_entries(c, ph, far, unk).T
+            sk = jr if rows_side else jc
+            pos = np.searchsorted(unk, sk)
+            Q, _ = np.linalg.qr(A[pos].T)
+            R = A.T - Q @ (Q.conj().T @ A.T)
+            rel = np.linalg.norm(R) / np.linalg.norm(A)
+            assert rel < 10 * tol, (box, rows_side, rel)
+    s.close()
