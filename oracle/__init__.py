@@ -61,6 +61,8 @@ def _lib():
         lib.orc_form_dense.restype = ctypes.c_int
         lib.orc_layer_ops.argtypes = geo[:9] + [_pd]
         lib.orc_layer_ops.restype = ctypes.c_int
+        lib.orc_proxy_row_block_form.argtypes = geo + [ctypes.c_int32, _pi64, _i64, _d, _d, _d, _i64, _pd]
+        lib.orc_proxy_row_block_form.restype = ctypes.c_int
         for f in (lib.orc_hankel01, lib.orc_f1, lib.orc_wsbm_entries, lib.orc_wsbm_dense,
                   lib.orc_wsbm_matvec, lib.orc_proxy_circle, lib.orc_proxy_row_block,
                   lib.orc_proxy_col_block, lib.orc_wsbm_bilinear_tangent):
@@ -212,6 +214,21 @@ def proxy_row_block(curve, phys, rows, circle, P):
     cx, cy, rho = circle
     _lib().orc_proxy_row_block(n, *[_p(a) for a in g], *phys.args(), _pi(rows), rows.size,
                                cx, cy, rho, int(P), _p(out))
+    return out.view(np.complex128).reshape(2 * P, rows.size).T
+
+
+def proxy_row_block_form(curve, phys, rows, circle, P, form):
+    """Proxy row block of form 0 (eq. weakly_bm), 1 (eq. bm) or 2 (eq. pmchwt): box equations x
+    2P combined-field proxy sources (k1 sources, then k0 sources)."""
+    g = _geo(curve)
+    n = g[0].size
+    rows = np.ascontiguousarray(rows, dtype=np.int64)
+    out = np.empty(2 * rows.size * 2 * P)
+    cx, cy, rho = circle
+    rc = _lib().orc_proxy_row_block_form(n, *[_p(a) for a in g], *phys.args(), int(form), _pi(rows),
+                                         rows.size, cx, cy, rho, int(P), _p(out))
+    if rc:
+        raise ValueError(f"form {form}")
     return out.view(np.complex128).reshape(2 * P, rows.size).T
 
 

@@ -258,7 +258,7 @@ static void form_block(const Geom& g, const Params& p, int form, int64_t i, int6
 //   u_j -> w_j dG_k(p,y_j)/dn_y,   q_j -> -eps_k w_j G_k(p,y_j).
 // ---------------------------------------------------------------------------------------
 static void proxy_row_entries(const Geom& g, const Params& p, int64_t i, double px, double py,
-                              double pnx, double pny, double pw, cplx out[2][2]) {
+                              double pnx, double pny, double pw, cplx out[2][2], int form = 0) {
   const cplx I1(0.0, 1.0);
   double dx = g.x[i] - px;
   double dy = g.y[i] - py;
@@ -283,6 +283,20 @@ static void proxy_row_entries(const Geom& g, const Params& p, int64_t i, double 
     dphi[s] = Nk - I1 * eta * dGdnx;
   }
   // out[a][s]: equation a of node i, source s (0 = k1 source, 1 = k0 source)
+  if (form == 1) {  // eq. (bm): eq1 = psi1, eq2 = psi0 + alpha d_n psi0
+    out[0][0] = pw * phi[0];
+    out[1][0] = cplx(0.0, 0.0);
+    out[0][1] = cplx(0.0, 0.0);
+    out[1][1] = pw * (phi[1] + alpha * dphi[1]);
+    return;
+  }
+  if (form == 2) {  // eq. (pmchwt): eq1 = psi0 + psi1, eq2 = d_n psi0 / eps0 + d_n psi1 / eps1
+    out[0][0] = pw * phi[0];
+    out[1][0] = pw * dphi[0] / p.eps1;
+    out[0][1] = pw * phi[1];
+    out[1][1] = pw * dphi[1] / p.eps0;
+    return;
+  }
   out[0][0] = pw * phi[0];
   out[1][0] = pw * (-alpha * dphi[0]);
   out[0][1] = cplx(0.0, 0.0);
@@ -623,6 +637,35 @@ static void proxy_point(double cx, double cy, double rho, int64_t P, int64_t m, 
 // Row proxy block: rows = equation indices (paper order) of a box, columns = 2P proxy
 // sources (k1 sources first, then k0 sources), each scaled by the proxy weight 2 pi rho / P.
 // out: column-major nr x 2P complex128.
+// The same for the equations of form 1 (eq. bm) or 2 (eq. pmchwt); form 0 is the block above.
+// The column block is the same for all three: their far interactions depend on a box's
+// unknowns only through the k0 and k1 potentials psi0, psi1.
+int orc_proxy_row_block_form(int64_t n, const double* x, const double* y, const double* nx,
+                             const double* ny, const double* w, const double* kappa, double k0,
+                             double k1, double eps0, double eps1, int32_t form, const int64_t* rows,
+                             int64_t nr, double cx, double cy, double rho, int64_t P, double* out) {
+  if (form < 0 || form > 2) return -1;
+  Geom g{n, x, y, nx, ny, w, kappa};
+  Params p{k0, k1, eps0, eps1};
+  double pw = 2.0 * PI * rho / (double)P;
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int64_t m = 0; m < P; ++m) {
+    double px, py, pnx, pny;
+    proxy_point(cx, cy, rho, P, m, &px, &py, &pnx, &pny);
+    for (int64_t rr = 0; rr < nr; ++rr) {
+      int64_t i = rows[rr] % n, a = rows[rr] / n;
+      cplx e[2][2];
+      proxy_row_entries(g, p, i, px, py, pnx, pny, pw, e, form);
+      for (int s = 0; s < 2; ++s) {
+        int64_t cc = s * P + m;
+        out[2 * (cc * nr + rr)] = e[a][s].real();
+        out[2 * (cc * nr + rr) + 1] = e[a][s].imag();
+      }
+    }
+  }
+  return 0;
+}
+
 int orc_proxy_row_block(int64_t n, const double* x, const double* y, const double* nx,
                         const double* ny, const double* w, const double* kappa, double k0,
                         double k1, double eps0, double eps1, const int64_t* rows, int64_t nr,

@@ -95,3 +95,43 @@ def test_pmchwt_blocks_from_the_layer_operators():
     B = np.block([[o["D0"] + o["D1"], -(ph.eps0 * o["S0"] + ph.eps1 * o["S1"])],
                   [o["N0"] / ph.eps0 + o["N1"] / ph.eps1, -(o["Ds0"] + o["Ds1"])]])
     assert np.abs(A - B).max() <= 1e-14 * np.abs(B).max()
+
+
+def _form_entries(A, rows, cols):
+    return A[np.ix_(rows, cols)]
+
+
+@pytest.mark.parametrize("form", [1, 2])
+def test_form_proxy_blocks_span_far_interactions(form):
+    """Proxy-surface compression (Sec. III) carries over to eqs. (bm) and (pmchwt): the far
+    columns of a box's equations lie in the range of the form's proxy row block, and the far
+    rows of the box's unknowns in the row space of the (shared) proxy column block. Form 0 of
+    the same export equals the WSBM row block. The blocks are numerically rank deficient (about
+    135 of 256 at 1e-12), so the span is a real constraint; it is the property the
+    interpolative decomposition needs. (It does not single out one row block: restricted to the
+    box's nodes, the k1 proxy fields also span the k0 fields, so even the WSBM block spans
+    these far fields.)"""
+    N, lo, hi, P = 1024, 128, 256, 200
+    c = inputs.star(N)
+    ph = oracle.Physics(inputs.k0_for_density(c, 15.0), n=1.5)
+    nodes = np.arange(lo, hi)
+    circ = oracle.proxy_circle(c, nodes)
+    d = np.hypot(c["x"] - circ[0], c["y"] - circ[1])
+    far = np.array([j for j in range(N) if (j < lo or j >= hi) and d[j] > circ[2]])
+    box = np.concatenate([nodes, nodes + N])
+    farU = np.concatenate([far, far + N])
+    A = oracle.form_dense(c, ph, form)
+
+    def resid(B, Y):
+        U, s, _ = np.linalg.svd(B, full_matrices=False)
+        U = U[:, s > 1e-12 * s[0]]
+        return np.linalg.norm(Y - U @ (U.conj().T @ Y)) / np.linalg.norm(Y)
+
+    Prow = oracle.proxy_row_block_form(c, ph, box, circ, P, form)
+    Pcol = oracle.proxy_col_block(c, ph, box, circ, P)
+    assert resid(Prow, _form_entries(A, box, farU)) < 1e-9
+    assert resid(Pcol.conj().T, _form_entries(A, farU, box).conj().T) < 1e-9
+    assert np.array_equal(oracle.proxy_row_block_form(c, ph, box, circ, P, 0),
+                          oracle.proxy_row_block(c, ph, box, circ, P))
+    sv = np.linalg.svd(Prow, compute_uv=False)
+    assert np.sum(sv > 1e-12 * sv[0]) < 0.6 * box.size
