@@ -24,6 +24,7 @@
 #ifndef WSBM_HSS_H
 #define WSBM_HSS_H
 
+#include <stddef.h>
 #include <stdint.h>
 
 #ifdef __cplusplus
@@ -122,6 +123,21 @@ typedef struct {
 } wsbm_stats_t;
 
 typedef struct wsbm_hss* wsbm_hss_t;
+
+/* Device memory of the factors and of the build's and transposed solve's work space.
+ * alloc(bytes, stream, ctx): device memory of at least `bytes` bytes usable in stream order on
+ * `stream` (the handle's stream), or NULL (the call then fails with WSBM_ERR_OOM).
+ * release(ptr, stream, ctx): returns a block in stream order: work queued on `stream` before
+ * the call may still read or write it.  Both are called from the calling host thread only.
+ * The default is a library memory pool per device (see wsbm_trim_memory); a framework's
+ * caching allocator can be plugged in instead, so that it supplies the memory. */
+typedef void* (*wsbm_alloc_fn)(size_t bytes, void* stream, void* ctx);
+typedef void (*wsbm_free_fn)(void* ptr, void* stream, void* ctx);
+
+/* Allocator of the handles created after this call (a handle keeps the one it was created
+ * with, for all its allocations and releases).  alloc = release = NULL restores the library
+ * pool.  Errors: INVALID_ARG when exactly one of the two is NULL.  No device is touched. */
+int wsbm_set_allocator(wsbm_alloc_fn alloc, wsbm_free_fn release, void* ctx);
 
 /* ---------------------------------------------------------------- stateless kernels ---- */
 

@@ -121,6 +121,8 @@ def lib():
         L.wsbm_strerror.restype = ctypes.c_char_p
         L.wsbm_trim_memory.argtypes = []
         L.wsbm_trim_memory.restype = ctypes.c_int
+        L.wsbm_set_allocator.argtypes = [_ALLOC_FN, _FREE_FN, ctypes.c_void_p]
+        L.wsbm_set_allocator.restype = ctypes.c_int
         for f in ("wsbm_hankel01", "wsbm_entries_raw", "wsbm_proxy_block", "wsbm_create",
                   "wsbm_factor", "wsbm_rhs_planewave", "wsbm_solve", "wsbm_farfield",
                   "wsbm_entries", "wsbm_box_info", "wsbm_stats", "wsbm_batch_create",
@@ -150,6 +152,36 @@ def _stream(device=None):
 def trim_memory():
     """Return the library's cached work-space memory to the device."""
     _check(lib().wsbm_trim_memory(), "wsbm_trim_memory")
+
+
+_ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+_FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p)
+_TORCH_CB = None  # created once and never released: handles keep calling them until destroyed
+
+
+def _torch_alloc(nbytes, stream, ctx):
+    import torch
+    try:
+        return torch.cuda.caching_allocator_alloc(int(nbytes), stream=int(stream or 0))
+    except Exception:  # out of memory: the library reports WSBM_ERR_OOM
+        return None
+
+
+def _torch_free(ptr, stream, ctx):
+    import torch
+    torch.cuda.caching_allocator_delete(int(ptr))
+
+
+def use_torch_allocator(enable=True):
+    """Let PyTorch's caching allocator supply the factors and work space of the handles created
+    from now on (enable=False: the library's own pool again)."""
+    global _TORCH_CB
+    if enable:
+        if _TORCH_CB is None:
+            _TORCH_CB = (_ALLOC_FN(_torch_alloc), _FREE_FN(_torch_free))
+        _check(lib().wsbm_set_allocator(_TORCH_CB[0], _TORCH_CB[1], None), "wsbm_set_allocator")
+    else:
+        _check(lib().wsbm_set_allocator(_ALLOC_FN(), _FREE_FN(), None), "wsbm_set_allocator")
 
 
 def make_geom(curve, device="cuda"):

@@ -82,6 +82,10 @@ struct Level {
 struct wsbm_hss {
   int dev = 0;
   cudaStream_t st = nullptr;
+  // allocator of the factors and work space, fixed at creation (null: the library's pool)
+  wsbm_alloc_fn ualloc = nullptr;
+  wsbm_free_fn ufree = nullptr;
+  void* uctx = nullptr;
   int64_t N = 0;
   double *x = nullptr, *y = nullptr, *nx = nullptr, *ny = nullptr, *w = nullptr, *kappa = nullptr;
   std::vector<double> hx, hy, hw;
@@ -389,12 +393,37 @@ static void* pin_take(cudaStream_t st, size_t bytes) {
   return (P.p && P.off <= P.cap) ? P.p + a : nullptr;
 }
 
+// Caller-supplied allocator (wsbm_set_allocator): captured by each handle at creation.
+static std::mutex g_alloc_mu;
+static wsbm_alloc_fn g_ualloc = nullptr;
+static wsbm_free_fn g_ufree = nullptr;
+static void* g_uctx = nullptr;
+
+extern "C" int wsbm_set_allocator(wsbm_alloc_fn alloc, wsbm_free_fn release, void* ctx) {
+  if ((alloc == nullptr) != (release == nullptr)) return WSBM_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lk(g_alloc_mu);
+  g_ualloc = alloc;
+  g_ufree = release;
+  g_uctx = alloc ? ctx : nullptr;
+  return WSBM_OK;
+}
+
+// device memory of a handle, stream ordered on its stream
+static int halloc(wsbm_hss* h, size_t bytes, void** p) {
+  *p = nullptr;
+  if (h->ualloc) {
+    *p = h->ualloc(bytes, (void*)h->st, h->uctx);
+    return *p ? WSBM_OK : WSBM_ERR_OOM;
+  }
+  return wsbm_malloc_async(p, bytes, h->dev, h->st) == cudaSuccess ? WSBM_OK : WSBM_ERR_OOM;
+}
+
 template <class T>
 static int upload(wsbm_hss* h, const std::vector<T>& v, T** d, std::vector<void*>& tmp) {
   *d = nullptr;
   if (v.empty()) return WSBM_OK;
   const size_t bytes = v.size() * sizeof(T);
-  if (wsbm_malloc_async((void**)d, bytes, h->dev, h->st) != cudaSuccess) return WSBM_ERR_OOM;
+  HK(halloc(h, bytes, (void**)d));
   tmp.push_back(*d);
   const void* src = v.data();
   if (void* stage = pin_take(h->st, bytes)) {
@@ -407,17 +436,30 @@ static int upload(wsbm_hss* h, const std::vector<T>& v, T** d, std::vector<void*
 }
 
 static int dalloc(wsbm_hss* h, size_t bytes, void** p, std::vector<void*>& list) {
-  *p = nullptr;
   if (bytes == 0) bytes = 16;
-  if (wsbm_malloc_async(p, bytes, h->dev, h->st) != cudaSuccess) return WSBM_ERR_OOM;
+  HK(halloc(h, bytes, p));
   list.push_back(*p);
   return WSBM_OK;
 }
 
 static void free_list(wsbm_hss* h, std::vector<void*>& list) {
-  for (void* p : list) cudaFreeAsync(p, h->st);
+  for (void* p : list) {
+    if (h->ufree)
+      h->ufree(p, (void*)h->st, h->uctx);
+    else
+      cudaFreeAsync(p, h->st);
+  }
   list.clear();
 }
+
+// Work space of one call: released in stream order when the call returns, also on an early
+// error return (free_list empties the list, so an explicit release before is harmless).
+struct TmpMem {
+  wsbm_hss* h;
+  std::vector<void*> v;
+  explicit TmpMem(wsbm_hss* hh) : h(hh) {}
+  ~TmpMem() { free_list(h, v); }
+};
 
 // Slots (node, two output positions) for a list of interleaved unknowns placed at output
 // positions base + t.  `at` is a per-node scratch array holding -1 on entry and on exit.
@@ -634,6 +676,12 @@ extern "C" int wsbm_create(const wsbm_geom* g, const wsbm_params* p, void* strea
   wsbm_hss* h = new wsbm_hss();
   cudaGetDevice(&h->dev);
   h->st = (cudaStream_t)stream;
+  {
+    std::lock_guard<std::mutex> lk(g_alloc_mu);
+    h->ualloc = g_ualloc;
+    h->ufree = g_ufree;
+    h->uctx = g_uctx;
+  }
   pin_acquire(h->st);
   h->N = g->n;
   h->ph = ph;
@@ -792,7 +840,8 @@ static int factor_levels(const std::vector<wsbm_hss*>& hs, const std::vector<int
   wsbm_hss* h0 = hs[0];
   cudaStream_t st = h0->st;
   pin_reset(st);  // the previous level ended with the stream synchronized
-  std::vector<void*> tmp;
+  TmpMem tmpm(h0);
+  std::vector<void*>& tmp = tmpm.v;
   std::vector<BoxRef> R;
   for (size_t i = 0; i < hs.size(); ++i) {
     if (levels[i] < 1) continue;
@@ -1403,7 +1452,8 @@ static int factor_roots(const std::vector<wsbm_hss*>& hs, double ms_out[2]) {
   wsbm_hss* h0 = hs[0];
   cudaStream_t st = h0->st;
   pin_reset(st);  // the levels ended with the stream synchronized
-  std::vector<void*> tmp;
+  TmpMem tmpm(h0);
+  std::vector<void*>& tmp = tmpm.v;
   InstArrays ia;
   HK(upload_instances(h0, hs, &ia, tmp));
   PairBatch pb;
@@ -2203,7 +2253,8 @@ extern "C" int wsbm_solve_transposed(wsbm_hss_t h, const void* rhs, int32_t nrhs
   if (nrhs == 0) return WSBM_OK;
   cudaStream_t st = h->st;
   pin_reset(st);
-  std::vector<void*> tmp;
+  TmpMem tmpm(h);
+  std::vector<void*>& tmp = tmpm.v;
   const int64_t N = h->N;
   double2* bint = nullptr;
   HK(dalloc(h, (size_t)2 * N * nrhs * sizeof(double2), (void**)&bint, tmp));

@@ -35,6 +35,18 @@ def test_library_exports_every_declared_symbol():
     assert lib.wsbm_strerror(-4) == b"interpolative decomposition rank above its cap"
 
 
+def test_set_allocator_arguments():
+    """wsbm_set_allocator touches no device: both callbacks or neither."""
+    from paper_2607_00790_gb300 import binding
+    L = binding.lib()
+    none_a, none_f = binding._ALLOC_FN(), binding._FREE_FN()
+    one = binding._ALLOC_FN(lambda n, s, c: None)
+    assert L.wsbm_set_allocator(one, none_f, None) == -1  # WSBM_ERR_INVALID_ARG
+    binding.use_torch_allocator(True)
+    binding.use_torch_allocator(False)
+    assert L.wsbm_set_allocator(none_a, none_f, None) == 0
+
+
 LAYOUT_C = r"""
 #include <stddef.h>
 #include <stdio.h>

@@ -302,3 +302,38 @@ def test_leaf_level_of_65536_boxes():
             rel = np.linalg.norm(R) / np.linalg.norm(A)
             assert rel < 10 * tol, (box, rows_side, rel)
     s.close()
+
+
+def test_torch_allocator_supplies_the_factors():
+    """With PyTorch's caching allocator plugged in (wsbm_set_allocator), the factors and the
+    build's work space come from PyTorch: the memory it reports grows by at least the factor
+    bytes, the solution is unchanged, and closing the handle returns the factors to it."""
+    import torch
+    from paper_2607_00790_gb300 import binding
+    c, prm = inputs.workload("disk")
+    ph = oracle.Physics(prm["k0"], n=prm["n"])
+    g, keep = binding.make_geom(c)
+    p = binding.make_params(prm["k0"], prm["n"], leaf=prm["leaf"], nproxy=prm["nproxy"],
+                            id_tol=prm["tol"])
+    binding.use_torch_allocator(True)
+    try:
+        torch.cuda.synchronize()
+        m0 = torch.cuda.memory_allocated()
+        s = binding.Solver(g, p)
+        s.factor()
+        torch.cuda.synchronize()
+        m1 = torch.cuda.memory_allocated()
+        fb = s.stats()["factor_bytes"]
+        assert fb > 0 and m1 - m0 >= fb, (m0, m1, fb)
+        ang = torch.tensor([0.0], dtype=torch.float64, device="cuda")
+        u, q = s.solve(s.rhs_planewave(ang))
+        _, ud, qd = dense_reference(c, ph, [0.0])
+        assert rel(u.cpu().numpy(), ud) < 10 * prm["tol"]
+        del u, q
+        torch.cuda.synchronize()
+        m2 = torch.cuda.memory_allocated()
+        s.close()
+        torch.cuda.synchronize()
+        assert m2 - torch.cuda.memory_allocated() >= fb
+    finally:
+        binding.use_torch_allocator(False)
