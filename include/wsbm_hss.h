@@ -77,8 +77,16 @@ typedef struct {
  *              least 1.5 l rows; the QR of a sketch stops at a quarter of the usual cutoff; a
  *              side whose rank, or the box's, comes within 16 of l is redone on M);
  *              WSBM_ID_FULL (1): column-pivoted QR of the full ID matrices everywhere
+ *  formulation WSBM_FORM_WSBM (0): eq. (weakly_bm), third order; WSBM_FORM_BM (1): the
+ *              standard Burton-Miller equation, eq. (bm); WSBM_FORM_PMCHWT (2): eq. (pmchwt),
+ *              unknowns still (u, q), right-hand side [-u_in ; -eps0^-1 du_in/dn].  Forms 1 and
+ *              2 hold the hypersingular N_k, whose one-point correction leaves them first order
+ *              (the paper's comparison, Sec. II); they need precision WSBM_FP64 and are
+ *              refused (INVALID_ARG) by the matrix-free product, the no-allocation entries and
+ *              the gradient calls, which implement eq. (weakly_bm) only
  */
 enum { WSBM_ID_SKETCH = 0, WSBM_ID_FULL = 1 };
+enum { WSBM_FORM_WSBM = 0, WSBM_FORM_BM = 1, WSBM_FORM_PMCHWT = 2 };
 typedef struct {
   double k0, refr_index, eps0, eps1;
   int32_t leaf, nproxy;
@@ -86,7 +94,7 @@ typedef struct {
   int32_t precision;
   double proxy_ratio;
   int32_t max_levels, root_cap;
-  int32_t id_method, pad;
+  int32_t id_method, formulation;
 } wsbm_params;
 
 /* Counters of a handle. */

@@ -41,7 +41,7 @@ class Params(ctypes.Structure):
                 ("leaf", ctypes.c_int32), ("nproxy", ctypes.c_int32),
                 ("id_tol", ctypes.c_double), ("precision", ctypes.c_int32),
                 ("proxy_ratio", ctypes.c_double), ("max_levels", ctypes.c_int32),
-                ("root_cap", ctypes.c_int32), ("id_method", ctypes.c_int32), ("pad", ctypes.c_int32)]
+                ("root_cap", ctypes.c_int32), ("id_method", ctypes.c_int32), ("formulation", ctypes.c_int32)]
 
 
 class Stats(ctypes.Structure):
@@ -196,11 +196,14 @@ WSBM_ID_SKETCH = 0
 WSBM_ID_FULL = 1
 
 
+WSBM_FORM_WSBM, WSBM_FORM_BM, WSBM_FORM_PMCHWT = 0, 1, 2
+
+
 def make_params(k0, n, eps0=1.0, eps1=0.0, leaf=64, nproxy=64, id_tol=1e-10,
                 precision=WSBM_FP64, proxy_ratio=1.5, max_levels=0, root_cap=0,
-                id_method=WSBM_ID_SKETCH):
+                id_method=WSBM_ID_SKETCH, formulation=WSBM_FORM_WSBM):
     return Params(k0, n, eps0, eps1, leaf, nproxy, id_tol, precision, proxy_ratio, max_levels,
-                  root_cap, id_method, 0)
+                  root_cap, id_method, formulation)
 
 
 # ---------------------------------------------------------------- stateless calls ----

@@ -512,6 +512,7 @@ extern "C" int wsbm_entries_vjp(const wsbm_geom* g, const wsbm_params* p, const 
   if (rc) return rc;
   Phys ph;
   if ((rc = wsbm_phys_from_params(p, &ph))) return rc;
+  if (p->formulation != WSBM_FORM_WSBM) return WSBM_ERR_INVALID_ARG;  // eq. (weakly_bm) only
   if (!lam || !x || !grad || !gphys) return WSBM_ERR_INVALID_ARG;
   cudaStream_t st = (cudaStream_t)stream;
   const int64_t N = g->n;
@@ -557,6 +558,7 @@ extern "C" int wsbm_rhs_planewave_vjp(const wsbm_geom* g, const wsbm_params* p,
   if (rc) return rc;
   if (!p || !(p->k0 > 0.0) || nang < 0 || !grad || (nang > 0 && (!angles || !lam)))
     return WSBM_ERR_INVALID_ARG;
+  if (p->formulation != WSBM_FORM_WSBM) return WSBM_ERR_INVALID_ARG;  // eq. (weakly_bm) only
   cudaStream_t st = (cudaStream_t)stream;
   k_rhs_planewave_vjp<<<grid_for(g->n, 256), 256, 0, st>>>(wsbm_devgeom(g), p->k0, angles, nang,
                                                            (const double2*)lam, grad);
@@ -571,6 +573,7 @@ extern "C" int wsbm_farfield_vjp(const wsbm_geom* g, const wsbm_params* p, const
   if (rc) return rc;
   Phys ph;
   if ((rc = wsbm_phys_from_params(p, &ph))) return rc;
+  if (p->formulation != WSBM_FORM_WSBM) return WSBM_ERR_INVALID_ARG;  // eq. (weakly_bm) only
   if (nrhs < 1 || nang < 0 || !u || !q || !v || !grad || (nang > 0 && (!angles || !gF)))
     return WSBM_ERR_INVALID_ARG;
   cudaStream_t st = (cudaStream_t)stream;

@@ -79,6 +79,7 @@ int wsbm_phys_from_params(const wsbm_params* p, Phys* ph) {
   double eps0 = p->eps0 > 0.0 ? p->eps0 : 1.0;
   double eps1 = p->eps1 > 0.0 ? p->eps1 : p->refr_index * p->refr_index * eps0;
   if (!isfinite(eps0) || !isfinite(eps1)) return WSBM_ERR_INVALID_ARG;
+  if (p->formulation < WSBM_FORM_WSBM || p->formulation > WSBM_FORM_PMCHWT) return WSBM_ERR_INVALID_ARG;
   ph->k0 = p->k0;
   ph->k1 = p->refr_index * p->k0;
   ph->eps0 = eps0;
@@ -173,7 +174,10 @@ extern "C" int wsbm_entries_raw(const wsbm_geom* g, const wsbm_params* p, const 
     if ((rc = wsbm_launch_unknowns_to_slots(rows, nr, g->n, rnode, rpos, st))) goto done;
     if ((rc = wsbm_launch_unknowns_to_slots(cols, nc, g->n, cnode, cpos, st))) goto done;
     CK(cudaMemcpyAsync(dtask, &t, sizeof(t), cudaMemcpyHostToDevice, st));
-    rc = wsbm_launch_pairs(dg, ph, dtask, 1, wsbm_pair_tiles(t.nr, t.nc, 0), st);
+    if (p->formulation == WSBM_FORM_WSBM)
+      rc = wsbm_launch_pairs(dg, ph, dtask, 1, wsbm_pair_tiles(t.nr, t.nc, 0), st);
+    else
+      rc = wsbm_launch_pairs_form(p->formulation, dg, ph, dtask, 1, wsbm_pair_tiles(t.nr, t.nc, 0), st);
     // the task struct lives on this stack frame: wait for the copy before returning
     CK(cudaStreamSynchronize(st));
   }
@@ -193,6 +197,9 @@ extern "C" int wsbm_proxy_block(const wsbm_geom* g, const wsbm_params* p, int32_
   if ((side != 0 && side != 1) || P < 1 || nidx < 0 || nidx > INT32_MAX / 2) return WSBM_ERR_INVALID_ARG;
   if (!(rho > 0.0) || !isfinite(cx) || !isfinite(cy) || !isfinite(rho)) return WSBM_ERR_INVALID_ARG;
   if (p->precision != WSBM_FP64 && p->precision != WSBM_MIXED && p->precision != WSBM_MIXED_FINE)
+    return WSBM_ERR_INVALID_ARG;
+  // the comparison formulations have FP64 row blocks only (the column block is shared)
+  if (p->formulation != WSBM_FORM_WSBM && side == 0 && p->precision != WSBM_FP64)
     return WSBM_ERR_INVALID_ARG;
   if (nidx == 0) return WSBM_OK;
   if (!idx || !out) return WSBM_ERR_INVALID_ARG;
@@ -224,8 +231,10 @@ extern "C" int wsbm_proxy_block(const wsbm_geom* g, const wsbm_params* p, int32_
     DevGeom dg = wsbm_devgeom(g);
     if ((rc = wsbm_launch_unknowns_to_slots(idx, nidx, g->n, buf, buf + nidx, st))) goto done;
     CK(cudaMemcpyAsync(dtask, &t, sizeof(t), cudaMemcpyHostToDevice, st));
-    rc = wsbm_launch_proxy(dg, ph, dtask, 1, wsbm_proxy_tiles(t.nn, P), p->precision,
-                           st);
+    if (side == 0 && p->formulation != WSBM_FORM_WSBM)
+      rc = wsbm_launch_proxy_rows_form(p->formulation, dg, ph, dtask, 1, wsbm_proxy_tiles(t.nn, P), st);
+    else
+      rc = wsbm_launch_proxy(dg, ph, dtask, 1, wsbm_proxy_tiles(t.nn, P), p->precision, st);
     CK(cudaStreamSynchronize(st));
   }
 done:

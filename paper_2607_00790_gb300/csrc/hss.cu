@@ -216,8 +216,9 @@ __global__ void k_copy2d(const CopyDesc* __restrict__ d) {
 
 // Plane-wave right-hand side, interleaved: b[2i] = 0, b[2i+1] = -u_in - alpha du_in/dn
 //   = (d.n - 1) u_in  (alpha = i/k0, du_in/dn = i k0 (d.n) u_in).  Output in paper order.
+// form 2 (eq. pmchwt): b = [-u_in ; -eps0^-1 du_in/dn] = [-u_in ; -(i k0 d.n / eps0) u_in].
 __global__ void k_rhs_planewave(DevGeom g, double k0, const double* __restrict__ ang, int nang,
-                                double2* __restrict__ rhs) {
+                                double2* __restrict__ rhs, int form, double eps0) {
   int64_t N = g.n;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < N * nang;
        e += (int64_t)gridDim.x * blockDim.x) {
@@ -230,8 +231,14 @@ __global__ void k_rhs_planewave(DevGeom g, double k0, const double* __restrict__
     sincos(ph, &s, &c);
     double dn = ca * g.nx[i] + sa * g.ny[i];
     double2* col = rhs + (int64_t)a * 2 * N;
-    col[i] = make_double2(0.0, 0.0);
-    col[N + i] = make_double2((dn - 1.0) * c, (dn - 1.0) * s);
+    if (form == WSBM_FORM_PMCHWT) {
+      const double t = k0 * dn / eps0;
+      col[i] = make_double2(-c, -s);
+      col[N + i] = make_double2(t * s, -t * c);
+    } else {
+      col[i] = make_double2(0.0, 0.0);
+      col[N + i] = make_double2((dn - 1.0) * c, (dn - 1.0) * s);
+    }
   }
 }
 
@@ -561,8 +568,12 @@ struct PairBatch {
     }
     return upload(h, tasks, &dtasks, tmp);
   }
+  // the formulation is the same for every curve of a launch (checked at batch creation)
   int run(wsbm_hss* h, const DevGeom* geos, const Phys* phys) {
     if (tasks.empty()) return WSBM_OK;
+    if (h->prm.formulation != WSBM_FORM_WSBM)
+      return wsbm_launch_pairs_form(h->prm.formulation, h->g, h->ph, dtasks, (int)tasks.size(), tiles,
+                                    h->st, geos, phys);
     return wsbm_launch_pairs(h->g, h->ph, dtasks, (int)tasks.size(), tiles, h->st, geos, phys);
   }
 };
@@ -671,6 +682,7 @@ extern "C" int wsbm_create(const wsbm_geom* g, const wsbm_params* p, void* strea
   if (p->precision != WSBM_FP64 && p->precision != WSBM_MIXED && p->precision != WSBM_MIXED_FINE)
     return WSBM_ERR_INVALID_ARG;
   if (p->id_method != WSBM_ID_SKETCH && p->id_method != WSBM_ID_FULL) return WSBM_ERR_INVALID_ARG;
+  if (p->formulation != WSBM_FORM_WSBM && p->precision != WSBM_FP64) return WSBM_ERR_INVALID_ARG;
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev <= 0) return WSBM_ERR_NO_DEVICE;
   wsbm_hss* h = new wsbm_hss();
@@ -928,6 +940,7 @@ static int factor_levels(const std::vector<wsbm_hss*>& hs, const std::vector<int
   // ---- entries: diagonal blocks (leaf) or sibling blocks (upper), near blocks, proxy blocks
   PairBatch pb;
   ProxyBatch xbp[3];  // per precision mode of the curves (one proxy launch each)
+  ProxyBatch xbf;     // row blocks of the comparison formulations (eqs. bm, pmchwt), FP64
   std::vector<CopyDesc> copies;
   std::vector<int64_t> e_pairs(hs.size(), 0), e_proxy(hs.size(), 0);
   // slots of every box's lists in parallel (per-thread scratch), then the batches in box order
@@ -976,7 +989,8 @@ static int factor_levels(const std::vector<wsbm_hss*>& hs, const std::vector<int
     e_pairs[i] += pb.add_slots(i, S.cr, S.nc, (int64_t)B.cr.size() * NC[r].size(), Mr[r], mr[r], 1);
     e_pairs[i] += pb.add_slots(i, S.nr, S.cc, (int64_t)NR[r].size() * B.cc.size(), Mc[r], mc[r], 0);
     ProxyBatch& xb = xbp[h->prm.precision];
-    e_proxy[i] += xb.add_slots(i, S.cr, (int64_t)B.cr.size(), B, 0, Mr[r], mr[r]);
+    ProxyBatch& xr = h->prm.formulation != WSBM_FORM_WSBM ? xbf : xb;
+    e_proxy[i] += xr.add_slots(i, S.cr, (int64_t)B.cr.size(), B, 0, Mr[r], mr[r]);
     e_proxy[i] += xb.add_slots(i, S.cc, (int64_t)B.cc.size(), B, 1, Mc[r], mc[r]);
   }
   if (!copies.empty()) {
@@ -988,11 +1002,15 @@ static int factor_levels(const std::vector<wsbm_hss*>& hs, const std::vector<int
   }
   HK(pb.prepare(h0, tmp));
   for (auto& xb : xbp) HK(xb.prepare(h0, tmp));
+  HK(xbf.prepare(h0, tmp));
   // timed: the entry kernels only
   HC(cudaEventRecord(h0->ev[0], st));
   HK(pb.run(h0, ia.geos, ia.phys));
   HC(cudaEventRecord(h0->ev[4], st));
   for (int m = 0; m < 3; ++m) HK(xbp[m].run(h0, m, ia.geos, ia.phys));
+  if (!xbf.tasks.empty())
+    HK(wsbm_launch_proxy_rows_form(h0->prm.formulation, h0->g, h0->ph, xbf.dtasks, (int)xbf.tasks.size(),
+                                   xbf.tiles, st, ia.geos, ia.phys));
   HC(cudaEventRecord(h0->ev[1], st));
   for (size_t i = 0; i < hs.size(); ++i) {
     hs[i]->stats.entries_generated += e_pairs[i] + e_proxy[i];
@@ -1001,9 +1019,9 @@ static int factor_levels(const std::vector<wsbm_hss*>& hs, const std::vector<int
   }
   // pair counts are kept per launch; a single curve owns them all
   if (hs.size() == 1) {
-    h0->stats.pairs_evaluated += pb.pairs + xbp[0].pairs + xbp[1].pairs + xbp[2].pairs;
+    h0->stats.pairs_evaluated += pb.pairs + xbp[0].pairs + xbp[1].pairs + xbp[2].pairs + xbf.pairs;
     h0->stats.pairs_pairs += pb.pairs;
-    h0->stats.pairs_proxy += xbp[0].pairs + xbp[1].pairs + xbp[2].pairs;
+    h0->stats.pairs_proxy += xbp[0].pairs + xbp[1].pairs + xbp[2].pairs + xbf.pairs;
   }
   // ---- randomized sketches of the leaf-level ID matrices (tensor cores): Y = Omega M with
   // l = max(32, 16 ceil((n/2 + WSBM_SKETCH_PAD)/16)) rows, where M has at least 1.5 l rows;
@@ -1719,6 +1737,8 @@ extern "C" int wsbm_batch_create(const wsbm_geom* g, const wsbm_params* p, int32
                                  void* stream, wsbm_batch_t* out) {
   if (!out || !g || !p || count < 1) return WSBM_ERR_INVALID_ARG;
   *out = nullptr;
+  for (int i = 1; i < count; ++i)  // one launch per phase serves every curve: one formulation
+    if (p[i].formulation != p[0].formulation) return WSBM_ERR_INVALID_ARG;
   wsbm_batch* b = new wsbm_batch();
   memset(&b->stats, 0, sizeof(b->stats));
   for (int i = 0; i < count; ++i) {
@@ -2441,7 +2461,8 @@ extern "C" int wsbm_solve_transposed(wsbm_hss_t h, const void* rhs, int32_t nrhs
 extern "C" int wsbm_rhs_planewave(wsbm_hss_t h, const double* angles, int32_t nang, void* rhs) {
   if (!h || nang < 0 || (nang > 0 && (!angles || !rhs))) return WSBM_ERR_INVALID_ARG;
   if (nang == 0) return WSBM_OK;
-  k_rhs_planewave<<<gridfor(h->N * nang), 256, 0, h->st>>>(h->g, h->ph.k0, angles, nang, (double2*)rhs);
+  k_rhs_planewave<<<gridfor(h->N * nang), 256, 0, h->st>>>(h->g, h->ph.k0, angles, nang, (double2*)rhs,
+                                                         h->prm.formulation, h->ph.eps0);
   wsbm_count_launch();
   return cudaGetLastError() == cudaSuccess ? WSBM_OK : WSBM_ERR_CUDA;
 }

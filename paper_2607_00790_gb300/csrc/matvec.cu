@@ -117,6 +117,7 @@ extern "C" int wsbm_matvec(const wsbm_geom* g, const wsbm_params* p, int32_t tra
   if (rc) return rc;
   Phys ph;
   if ((rc = wsbm_phys_from_params(p, &ph))) return rc;
+  if (p->formulation != WSBM_FORM_WSBM) return WSBM_ERR_INVALID_ARG;  // eq. (weakly_bm) only
   if ((trans != 0 && trans != 1) || nrhs < 0 || (nrhs > 0 && (!x || !y))) return WSBM_ERR_INVALID_ARG;
   if (nrhs == 0) return WSBM_OK;
   cudaStream_t st = (cudaStream_t)stream;

@@ -51,6 +51,7 @@ extern "C" int wsbm_entries_raw_noalloc(const wsbm_geom* g, const wsbm_params* p
   if (rc) return rc;
   Phys ph;
   if ((rc = wsbm_phys_from_params(p, &ph))) return rc;
+  if (p->formulation != WSBM_FORM_WSBM) return WSBM_ERR_INVALID_ARG;  // eq. (weakly_bm) only
   if (nr < 0 || nc < 0 || nr + nc > WSBM_NOALLOC_MAX_INDICES) return WSBM_ERR_INVALID_ARG;
   if (nr == 0 || nc == 0) return WSBM_OK;
   if (!rows || !cols || !out) return WSBM_ERR_INVALID_ARG;

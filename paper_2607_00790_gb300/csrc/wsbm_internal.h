@@ -70,6 +70,14 @@ int wsbm_launch_pairs(const DevGeom& g, const Phys& ph, const PairTask* d_tasks,
 int wsbm_launch_proxy(const DevGeom& g, const Phys& ph, const ProxyTask* d_tasks, int ntasks,
                       int64_t ntiles, int mixed, cudaStream_t st, const DevGeom* geos = nullptr,
                       const Phys* phys = nullptr);
+// forms.cu: the same tasks for the comparison formulations (form 1: eq. bm, 2: eq. pmchwt);
+// the proxy launch takes row-side tasks only (the column side is formulation independent).
+int wsbm_launch_pairs_form(int form, const DevGeom& g, const Phys& ph, const PairTask* d_tasks,
+                           int ntasks, int64_t ntiles, cudaStream_t st, const DevGeom* geos = nullptr,
+                           const Phys* phys = nullptr);
+int wsbm_launch_proxy_rows_form(int form, const DevGeom& g, const Phys& ph, const ProxyTask* d_tasks,
+                                int ntasks, int64_t ntiles, cudaStream_t st,
+                                const DevGeom* geos = nullptr, const Phys* phys = nullptr);
 int64_t wsbm_pair_tiles(int32_t nr, int32_t nc, int32_t fastc);
 int64_t wsbm_proxy_tiles(int32_t nn, int32_t P);
 int wsbm_launch_hankel(const double* z, int64_t n, double* out, int mixed, cudaStream_t st);

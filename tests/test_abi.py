@@ -56,7 +56,8 @@ int main(void) {
   printf("wsbm_geom %zu\nwsbm_params %zu\nwsbm_stats_t %zu\n", sizeof(wsbm_geom),
          sizeof(wsbm_params), sizeof(wsbm_stats_t));
   F(wsbm_params, id_tol) F(wsbm_params, precision) F(wsbm_params, proxy_ratio)
-  F(wsbm_params, max_levels) F(wsbm_params, root_cap)
+  F(wsbm_params, max_levels) F(wsbm_params, root_cap) F(wsbm_params, id_method)
+  F(wsbm_params, formulation)
   F(wsbm_stats_t, ms_entries) F(wsbm_stats_t, max_rank) F(wsbm_stats_t, rank_per_level)
   F(wsbm_stats_t, factor_bytes) F(wsbm_stats_t, ms_proxy) F(wsbm_stats_t, launches)
   return 0;
