@@ -94,7 +94,8 @@ def test_hss_solve_vs_dense(form):
     rhs = s.rhs_planewave(ang)
     u, q = s.solve(rhs)
     b = oracle.form_rhs(c, ph, angles, form)
-    assert np.abs(rhs.cpu().numpy() - b).max() <= 1e-14 * np.abs(b).max()
+    # the phase k0 d.x reaches about 62: one-ulp differences of the plane wave are about 1e-14
+    assert np.linalg.norm(rhs.cpu().numpy() - b) <= 1e-12 * np.linalg.norm(b)
     x = oracle.dense_solve(oracle.form_dense(c, ph, form), b)
     ud, qd = x[:N], x[N:]
     rel = lambda a, r: np.linalg.norm(a - r) / np.linalg.norm(r)  # noqa: E731
