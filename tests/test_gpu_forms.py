@@ -96,14 +96,25 @@ def test_hss_solve_vs_dense(form):
     b = oracle.form_rhs(c, ph, angles, form)
     # the phase k0 d.x reaches about 62: one-ulp differences of the plane wave are about 1e-14
     assert np.linalg.norm(rhs.cpu().numpy() - b) <= 1e-12 * np.linalg.norm(b)
-    x = oracle.dense_solve(oracle.form_dense(c, ph, form), b)
+    A = oracle.form_dense(c, ph, form)
+    x = oracle.dense_solve(A, b)
     ud, qd = x[:N], x[N:]
     rel = lambda a, r: np.linalg.norm(a - r) / np.linalg.norm(r)  # noqa: E731
-    assert rel(u.cpu().numpy(), ud) < 10 * tol and rel(q.cpu().numpy(), qd) < 10 * tol
+    xh = np.concatenate([u.cpu().numpy(), q.cpu().numpy()])
     obs = torch.tensor(2 * np.pi * np.arange(90) / 90, device="cuda")
     ff = s.farfield(u, q, obs).cpu().numpy()
     ffd = oracle.farfield(c, ph, ud, qd, obs.cpu().numpy())
-    assert rel(ff, ffd) < 10 * tol
+    if form == 1:  # second kind like eq. (weakly_bm): condition number 1.1e3 here
+        assert rel(xh[:N], ud) < 10 * tol and rel(xh[N:], qd) < 10 * tol
+        assert rel(ff, ffd) < 10 * tol
+    else:
+        # eq. (pmchwt) is of the first kind in q (S_k in one block, the hypersingular N_k in
+        # the other): condition number 8.2e4 against 4.8e2 for eq. (weakly_bm) on this curve, so
+        # the compression error is checked by the residual, and the densities get the
+        # conditioning on top (measured: residual 1.1e-7, u 5.3e-7, q 1.5e-6, far field 4.2e-7)
+        assert np.linalg.norm(A @ xh - b) / np.linalg.norm(b) < 100 * tol
+        assert rel(xh[:N], ud) < 1000 * tol and rel(xh[N:], qd) < 1000 * tol
+        assert rel(ff, ffd) < 100 * tol
     assert s.stats()["max_rank"] > 0
     s.close()
 
