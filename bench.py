@@ -550,6 +550,33 @@ def run_extras(curve, cfg, dev, params):
     return out
 
 
+def run_formulations(dev, N=262144, tol=1e-8):
+    """Leaf-level build (entries, IDs, leaf factors) of the star at N for the three
+    formulations of Sec. II: eq. (weakly_bm), eq. (bm) and eq. (pmchwt).  The paper reports the
+    standard Burton-Miller solver 10-20 % faster than the weakly singular one and PMCHWT about
+    equal; here the two comparison formulations run on plain (untuned) entry kernels."""
+    import torch
+    from paper_2607_00790_gb300 import binding, inputs
+    c = inputs.star(N)
+    k0 = float(inputs.k0_for_density(c))
+    g, keep = binding.make_geom(c, device=dev)
+    out = {}
+    for name, form in (("wsbm", 0), ("bm", 1), ("pmchwt", 2)):
+        p = binding.make_params(k0, 1.5, leaf=128, nproxy=128, id_tol=tol, max_levels=1,
+                                formulation=form)
+        for rep in range(2):  # the first build warms up
+            s = binding.Solver(g, p, device=dev)
+            s.factor()
+            torch.cuda.synchronize()
+            st = s.stats()
+            s.close()
+        out[name] = {"build_factor_s": st["ms_total_factor"] / 1e3, "ms_entries": st["ms_entries"],
+                     "ms_id": st["ms_id"], "ms_factor": st["ms_factor"],
+                     "entries_per_s": st["entries_generated"] / (st["ms_entries"] * 1e-3),
+                     "leaf_rank_max": st["max_rank"]}
+    return {"N": N, "id_tol": tol, **out}
+
+
 def run_batched_solve(dev, count=16, nmax=16384, nrhs=256, tol=1e-8):
     """Full HSS of the first `count` scatterers of the batched manifest with N <= nmax (batched
     factor), then `nrhs` plane waves each: one batched solve plan (shared launches per tree
@@ -766,6 +793,8 @@ def main():
     ap.add_argument("--adjoint", action="store_true",
                     help="only the shape-gradient measurement (N = 32768 Fourier curve)")
     ap.add_argument("--adjoint-n", type=int, default=32768)
+    ap.add_argument("--formulations", action="store_true",
+                    help="only the leaf-level builds of the three formulations at N = 2^18")
     ap.add_argument("--batched-solve", action="store_true",
                     help="only the batched-solve measurement (16 scatterers, 256 right-hand sides)")
     ap.add_argument("--profile-case", action="store_true",
@@ -780,6 +809,9 @@ def main():
         return
     if args.batched_solve:
         print(json.dumps({"batched_solve": run_batched_solve("cuda")}), flush=True)
+        return
+    if args.formulations:
+        print(json.dumps({"formulations": run_formulations("cuda")}), flush=True)
         return
     if args.warmup < 3:
         args.warmup = 3
