@@ -934,12 +934,16 @@ int wsbm_lu_solve_fused_batched(const LuSolveDesc* d_desc, int nbatch, int max_n
   if (max_n > WSBM_LUS_MAXN || max_n > max_nc) return -1;
   const size_t tile = 32 * 33, panel = (size_t)(max_n + 1) * LUS_B;
   const size_t sm = ((size_t)max_n + (panel > tile ? panel : tile)) * sizeof(double2);
-  static size_t set = 0;
-  if (sm > 48 * 1024 && sm > set) {
+  // the opt-in above 48 KB is a per-device attribute of the kernel
+  static size_t set[64];
+  int dev = 0;
+  cudaGetDevice(&dev);
+  size_t* done = (dev >= 0 && dev < 64) ? &set[dev] : nullptr;
+  if (sm > 48 * 1024 && (!done || sm > *done)) {
     if (cudaFuncSetAttribute(k_lu_solve_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) !=
         cudaSuccess)
       return -3;
-    set = sm;
+    if (done) *done = sm;
   }
   k_lu_solve_fused<<<nbatch, LUS_T, sm, st>>>(d_desc);
   wsbm_count_launch();
