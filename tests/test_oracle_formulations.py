@@ -135,3 +135,22 @@ def test_form_proxy_blocks_span_far_interactions(form):
                           oracle.proxy_row_block(c, ph, box, circ, P))
     sv = np.linalg.svd(Prow, compute_uv=False)
     assert np.sum(sv > 1e-12 * sv[0]) < 0.6 * box.size
+
+
+def test_far_field_orders_on_the_disk():
+    """The same comparison in the far field (360 angles) against the Mie far field: third order
+    for eq. (weakly_bm), first order for eqs. (bm) and (pmchwt)."""
+    ang = 2 * np.pi * np.arange(360) / 360
+    slopes = {}
+    for form in (oracle.FORM_WSBM, oracle.FORM_BM, oracle.FORM_PMCHWT):
+        errs = []
+        for N in (128, 256, 512):
+            c, prm = inputs.workload("disk", N=N)
+            ph = oracle.Physics(prm["k0"], n=prm["n"])
+            x = oracle.dense_solve(oracle.form_dense(c, ph, form), oracle.form_rhs(c, ph, [0.0], form))
+            ff = oracle.farfield(c, ph, x[:N], x[N:], ang)[:, 0]
+            ref = oracle.mie_farfield(1.0, ph, ang)
+            errs.append(np.linalg.norm(ff - ref) / np.linalg.norm(ref))
+        slopes[form] = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
+    assert np.all(np.abs(slopes[0] - 3.0) < 0.15), slopes
+    assert np.all(np.abs(slopes[1][-1:] - 1.0) < 0.2) and np.all(np.abs(slopes[2] - 1.0) < 0.2), slopes
