@@ -2,7 +2,8 @@
  * wsbm_hss.h -- C ABI of the GB300 (sm_103a) entry generator and HSS direct solver for the
  * weakly singular Burton-Miller (WSBM) boundary integral equation of 2-D TE-mode transmission
  * scattering (Matsumoto & Yokota, "Proxy-surface-based fast direct solver for TE-mode
- * scattering problems on distributed memory systems").
+ * scattering problems on distributed memory systems"), and of the standard Burton-Miller and
+ * PMCHWT equations the paper compares it with (wsbm_params.formulation).
  *
  * Conventions shared by every call
  * --------------------------------
