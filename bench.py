@@ -297,7 +297,11 @@ def run_ours(args, ws, rank, local):
     if ws == 1:
         out["cpu_baseline"] = run_cpu_baseline(curve, cfg, budget_s=12.0)
     if not args.no_extras:
-        out["extras"] = run_extras(curve, cfg, dev, params)
+        # the extras are context for the line above: a failure there must not cost the line
+        try:
+            out["extras"] = run_extras(curve, cfg, dev, params)
+        except Exception as exc:  # noqa: BLE001
+            out["extras"] = {"error": f"{type(exc).__name__}: {exc}"[:300]}
     return out
 
 
