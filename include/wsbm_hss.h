@@ -61,7 +61,10 @@ typedef struct {
  *  leaf        target leaf size in nodes (>= 4); the tree is a perfect binary tree of depth
  *              L = ceil(log2(n/leaf)) over contiguous node ranges (Sec. III, Fig. tree)
  *  nproxy      proxy points on each leaf's proxy circle (>= 8; grown on upper levels)
- *  id_tol      relative tolerance of the interpolative decompositions (0 < id_tol < 1)
+ *  id_tol      accuracy target of the HSS solution (0 < id_tol < 1): the column-pivoted QRs of
+ *              the interpolative decompositions stop at |R_kk| <= id_tol / (4 sqrt(2^L)) |R_00|
+ *              (L the tree depth: the errors of the 2^L leaf boxes add up in the solution), which
+ *              keeps densities and far field within a few id_tol of the dense solution
  *  precision   WSBM_FP64; WSBM_MIXED: proxy blocks evaluated with an FP32 amplitude and phase
  *              factor after an FP64 phase reduction (entries to ~1e-7); WSBM_MIXED_FINE: proxy
  *              blocks with only the amplitude corrections P - 1, Q of the Hankel functions in
@@ -133,7 +136,10 @@ typedef struct {
 
 typedef struct wsbm_hss* wsbm_hss_t;
 
-/* Device memory of the factors and of the build's and transposed solve's work space.
+/* Device memory of the library: a handle's geometry copy, factors, work space and solve plans,
+ * and the work space of the stateless calls (wsbm_entries_raw, wsbm_proxy_block, wsbm_matvec,
+ * wsbm_field, wsbm_sketch, wsbm_entries_vjp).  No call allocates device memory any other way
+ * (wsbm_entries_raw_noalloc allocates none).
  * alloc(bytes, stream, ctx): device memory of at least `bytes` bytes usable in stream order on
  * `stream` (the handle's stream), or NULL (the call then fails with WSBM_ERR_OOM).
  * release(ptr, stream, ctx): returns a block in stream order: work queued on `stream` before
@@ -144,7 +150,8 @@ typedef void* (*wsbm_alloc_fn)(size_t bytes, void* stream, void* ctx);
 typedef void (*wsbm_free_fn)(void* ptr, void* stream, void* ctx);
 
 /* Allocator of the handles created after this call (a handle keeps the one it was created
- * with, for all its allocations and releases).  alloc = release = NULL restores the library
+ * with, for all its allocations and releases) and of the stateless calls made after it (each
+ * call takes and returns its work space through the allocator current at its start).  alloc = release = NULL restores the library
  * pool.  Errors: INVALID_ARG when exactly one of the two is NULL.  No device is touched. */
 int wsbm_set_allocator(wsbm_alloc_fn alloc, wsbm_free_fn release, void* ctx);
 
@@ -237,6 +244,23 @@ int wsbm_solve(wsbm_hss_t h, const void* rhs, int32_t nrhs, void* u, void* q);
  * wsbm_solve. */
 int wsbm_solve_transposed(wsbm_hss_t h, const void* rhs, int32_t nrhs, void* lam1, void* lam2);
 
+/* Iterative refinement of a solution against the dense Nystrom matrix of eq. (weakly_bm):
+ * r = rhs - A x, x += HSS^-1 r (trans = 0; x = [u; q]), or, for the adjoint system
+ * A^T lam = rhs, r = rhs - A^T lam, lam += HSS^-T r (trans = 1; u, q then hold the multipliers
+ * lam1, lam2 of the first and second equations).  The products are the matrix-free ones of
+ * wsbm_matvec (every node pair, O(N^2) work each), the corrections come from the handle's
+ * factors (wsbm_solve / wsbm_solve_transposed), so each step gains about the accuracy of the
+ * HSS solve.  The paper has no counterpart (its solutions are the HSS ones).
+ *   rhs   device complex128 2N x nrhs (paper order, as for wsbm_solve)
+ *   u, q  device complex128 N x nrhs each: the solution on entry, the refined one on exit
+ *   iters refinement steps (>= 0)
+ *   res   host, iters + 1 doubles, or NULL: |r| / |rhs| (Frobenius over all right-hand sides)
+ *         before each step and after the last
+ * Work space from the handle's allocator.  Synchronous.  Errors: INVALID_ARG (also for the
+ * formulations other than eq. weakly_bm), NOT_FACTORED, OOM, CUDA. */
+int wsbm_refine(wsbm_hss_t h, int32_t trans, const void* rhs, int32_t nrhs, void* u, void* q,
+                int32_t iters, double* res);
+
 /* Far-field pattern of the scattered field at nang observation angles:
  * u_inf(a) = e^{i pi/4}/sqrt(8 pi k0) sum_j w_j [-i k0 (xh.n_j) u_j - eps0 q_j] e^{-i k0 xh.x_j}.
  * u, q: device complex128 N x nrhs; angles: device doubles; out: device complex128
@@ -307,8 +331,8 @@ void wsbm_batch_destroy(wsbm_batch_t b);
  * matrix of eq. (weakly_bm) (every node pair, O(N^2) work, nothing stored): residuals and
  * iterative refinement of HSS and adjoint solutions.  x, y: device complex128 2N x nrhs in
  * paper order (for trans = 0, x by unknown and y by equation; the reverse for trans = 1).
- * Scratch: 2N x (eight waves of CTAs / ceil(N/128)) complex128 from cudaMallocAsync on
- * `stream`.  Asynchronous.  Errors: INVALID_ARG, OOM, CUDA. */
+ * Scratch: 2N x (eight waves of CTAs / ceil(N/128)) complex128 from the library's allocator
+ * (wsbm_set_allocator) on `stream`.  Asynchronous.  Errors: INVALID_ARG, OOM, CUDA. */
 int wsbm_matvec(const wsbm_geom* g, const wsbm_params* p, int32_t trans, const void* x,
                 int32_t nrhs, void* y, void* stream);
 
@@ -318,8 +342,8 @@ int wsbm_matvec(const wsbm_geom* g, const wsbm_params* p, int32_t trans, const v
  * the total field), interior points the total field eps1 S_k1[q] - D_k1[u].  tx, ty: device
  * doubles; out: device complex128 nt x nrhs; inside: device int8 nt, 1 for interior points
  * (Gauss test of the Laplace double layer).  The trapezoidal sums are accurate a few node
- * spacings away from the curve; no near-singular quadrature is applied.  Scratch from
- * cudaMallocAsync on `stream`; asynchronous.  Errors: INVALID_ARG, OOM, CUDA. */
+ * spacings away from the curve; no near-singular quadrature is applied.  Scratch from the
+ * library's allocator (wsbm_set_allocator) on `stream`; asynchronous.  Errors: INVALID_ARG, OOM, CUDA. */
 int wsbm_field(const wsbm_geom* g, const wsbm_params* p, const void* u, const void* q,
                int32_t nrhs, const double* tx, const double* ty, int64_t nt, void* out,
                int8_t* inside, void* stream);
@@ -335,6 +359,32 @@ int wsbm_field(const wsbm_geom* g, const wsbm_params* p, const void* u, const vo
 int wsbm_sketch(const void* A, int64_t lda, int32_t m, int32_t n, int32_t l, void* Y, int64_t ldy,
                 uint32_t seed, void* stream);
 
+/* Complex GEMM C = beta C + alpha A B on the tensor cores, the dense contraction of the
+ * blocked LU factorizations of large boxes and of the dense root (the paper factors with FP64
+ * CPU arithmetic; GB300's FP64 pipe runs at 1/64 of its FP32 rate and far below its tensor
+ * cores).  Rows of A and columns of B are scaled by powers of two and cut into seven exact
+ * 8-bit digits; BF16 tensor-core products of the digits accumulate exactly in FP32 and are
+ * recombined in 64-bit integers, so each entry of A B carries an error below about
+ * 2^-55 * 2k * max_l |A_il| * max_l |B_lj| (the order of an FP64 product).
+ *   A  device complex128 m x k (lda >= m); B: k x n (ldb >= k); C: m x n (ldc >= m); all
+ *      column-major; alpha, beta: host, 2 doubles (re, im) each
+ *   1 <= k <= 32768
+ * Work space (7 (m + 2n) 2k BF16 values, rounded up) from the library's allocator.
+ * Synchronous.  Errors: INVALID_ARG, OOM, CUDA, TIMEOUT (a bounded wait inside the kernel ran
+ * out; the result is then incomplete). */
+int wsbm_zgemm(int32_t m, int32_t n, int32_t k, const double* alpha, const void* A, int64_t lda,
+               const void* B, int64_t ldb, const double* beta, void* C, int64_t ldc, void* stream);
+
+/* LU factorization with partial pivoting of one dense complex matrix (the dense root of the
+ * Martinsson-Rokhlin factor, Sec. III, at the sizes of full builds): right-looking, panels of
+ * 128 columns factored on the whole GPU, trailing updates through the tensor-core product of
+ * wsbm_zgemm.  A: device complex128 n x n (lda >= n), overwritten by L (unit lower, below the
+ * diagonal) and U; piv: device int32 n, piv[j] = the row swapped with row j at step j.  The
+ * pivot is the row of largest max(|Re|, |Im|) to within 2^-20 (first row on ties).  A zero
+ * pivot leaves a zero multiplier column (no error).  Work space (about 10.8 KB per row) from
+ * the library's allocator.  Synchronous.  Errors: INVALID_ARG, OOM, CUDA, TIMEOUT. */
+int wsbm_lu_dense(void* A, int64_t lda, int32_t n, int32_t* piv, void* stream);
+
 /* ---------------------------------------------------------------- gradients ----
  * Reverse-mode building blocks of shape and refractive-index gradients of a far-field loss
  * (no counterpart in the paper, which does not differentiate its solver).  With the solution x
@@ -347,8 +397,8 @@ int wsbm_sketch(const void* A, int64_t lda, int32_t m, int32_t n, int32_t l, voi
 /* grad = Re(lam^T (dA/ds) x) for every node input s of the Nystrom matrix of eq. (weakly_bm)
  * (dense: every node pair, O(N^2) work), gphys[0] = Re(lam^T (dA/dk1) x),
  * gphys[1] = Re(lam^T (dA/deps1) x).  lam, x: device complex128 2N (paper order: lam by
- * equation, x by unknown).  Scratch: about 6 N x (2 .. 8 waves of CTAs) doubles from
- * cudaMallocAsync on `stream`. */
+ * equation, x by unknown).  Scratch: about 6 N x (2 .. 8 waves of CTAs) doubles from the
+ * library's allocator (wsbm_set_allocator) on `stream`. */
 int wsbm_entries_vjp(const wsbm_geom* g, const wsbm_params* p, const void* lam, const void* x,
                      double* grad, double* gphys, void* stream);
 

@@ -103,6 +103,13 @@ def lib():
         L.wsbm_batch_destroy.restype = None
         G, P = ctypes.POINTER(Geom), ctypes.POINTER(Params)
         L.wsbm_solve_transposed.argtypes = [vp, vp, i32, vp, vp]
+        L.wsbm_refine.argtypes = [vp, i32, vp, i32, vp, vp, i32, ctypes.POINTER(d)]
+        L.wsbm_zgemm.argtypes = [i32, i32, i32, ctypes.POINTER(d), vp, i64, vp, i64,
+                                 ctypes.POINTER(d), vp, i64, vp]
+        L.wsbm_zgemm.restype = ctypes.c_int
+        L.wsbm_lu_dense.argtypes = [vp, i64, i32, vp, vp]
+        L.wsbm_lu_dense.restype = ctypes.c_int
+        L.wsbm_refine.restype = ctypes.c_int
         L.wsbm_matvec.argtypes = [G, P, i32, vp, i32, vp, vp]
         L.wsbm_matvec.restype = ctypes.c_int
         L.wsbm_field.argtypes = [G, P, vp, vp, i32, vp, vp, i64, vp, vp, vp]
@@ -246,6 +253,32 @@ def wsbm_matvec(geom, params, x, trans=False):
                              _dev(xc, torch.complex128), xc.shape[0], _dev(y, torch.complex128),
                              _stream(dev)), "wsbm_matvec")
     return y[0] if one else y.T
+
+
+def wsbm_zgemm(A, B, C=None, alpha=1.0, beta=0.0):
+    """C = beta C + alpha A B (complex128 device tensors) on the tensor cores (exact digits)."""
+    m, k = A.shape
+    n = B.shape[1]
+    Af = A.T.contiguous()  # column-major storage: the transpose's rows
+    Bf = B.T.contiguous()
+    Cf = (C.T.contiguous() if C is not None
+          else torch.zeros((n, m), dtype=torch.complex128, device=A.device))
+    al = (ctypes.c_double * 2)(complex(alpha).real, complex(alpha).imag)
+    be = (ctypes.c_double * 2)(complex(beta).real, complex(beta).imag)
+    _check(lib().wsbm_zgemm(m, n, k, al, _dev(Af, torch.complex128), m, _dev(Bf, torch.complex128), k,
+                            be, _dev(Cf, torch.complex128), m, _stream(A.device)), "wsbm_zgemm")
+    return Cf.T
+
+
+def wsbm_lu_dense(A):
+    """LU with partial pivoting of a square complex128 device matrix: returns (LU, piv) with LU
+    column-major-equivalent (L unit lower, U upper) as a torch tensor and piv (int32)."""
+    n = A.shape[0]
+    Af = A.T.contiguous()
+    piv = torch.empty(n, dtype=torch.int32, device=A.device)
+    _check(lib().wsbm_lu_dense(_dev(Af, torch.complex128), n, n, _dev(piv, torch.int32),
+                               _stream(A.device)), "wsbm_lu_dense")
+    return Af.T, piv
 
 
 def wsbm_sketch(A, l, seed=0):
@@ -394,20 +427,19 @@ class Solver:
         return l1.T, l2.T
 
     def refine(self, geom, params, rhs, u, q, iters=3, trans=False):
-        """Iterative refinement with the dense matrix-free product: r = b - A x, x += HSS^-1 r
-        (with trans: the adjoint system A^T lam = b, lam = (u, q) the multipliers of the two
-        equations).  Returns (u, q, relative residual before each step and after the last)."""
-        x = torch.cat([u, q], dim=0)
-        res = []
-        bn = torch.linalg.norm(rhs).item()
-        for it in range(iters + 1):
-            r = rhs - wsbm_matvec(geom, params, x, trans=trans)
-            res.append(torch.linalg.norm(r).item() / bn)
-            if it == iters:
-                break
-            du, dq = self.solve_transposed(r) if trans else self.solve(r)
-            x = x + torch.cat([du, dq], dim=0)
-        return x[: self.n], x[self.n:], res
+        """wsbm_refine: iterative refinement against the dense matrix-free product (with trans:
+        the adjoint system A^T lam = b, lam = (u, q) the multipliers of the two equations).
+        geom and params are the handle's (kept for the callers' convenience).  Returns
+        (u, q, relative residual before each step and after the last)."""
+        rc_ = rhs.T.contiguous()
+        nrhs = rhs.shape[1]
+        uc = u.T.contiguous()
+        qc = q.T.contiguous()
+        res = (ctypes.c_double * (iters + 1))()
+        _check(lib().wsbm_refine(self.h, 1 if trans else 0, _dev(rc_, torch.complex128), nrhs,
+                                 _dev(uc, torch.complex128), _dev(qc, torch.complex128), iters, res),
+               "wsbm_refine")
+        return uc.T, qc.T, list(res)
 
     def farfield(self, u, q, angles):
         uc, qc = u.T.contiguous(), q.T.contiguous()

@@ -496,7 +496,8 @@ __global__ void k_curve_fourier_vjp(int M, int64_t N, const double* __restrict__
 int grid_for(int64_t work, int per) {
   int64_t b = (work + per - 1) / per;
   if (b < 1) b = 1;
-  if (b > 152 * 16) b = 152 * 16;
+  const int64_t cap = (int64_t)wsbm_sm_count() * 16;
+  if (b > cap) b = cap;
   return (int)b;
 }
 
@@ -517,9 +518,7 @@ extern "C" int wsbm_entries_vjp(const wsbm_geom* g, const wsbm_params* p, const 
   cudaStream_t st = (cudaStream_t)stream;
   const int64_t N = g->n;
   const int64_t nti = (N + VJP_THREADS - 1) / VJP_THREADS;
-  int dev = 0, nsm = 152, per_sm = 1;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  int nsm = wsbm_sm_count(), per_sm = 1;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_entries_vjp, VJP_THREADS, 0) !=
           cudaSuccess ||
       per_sm < 1)
@@ -531,14 +530,11 @@ extern "C" int wsbm_entries_vjp(const wsbm_geom* g, const wsbm_params* p, const 
   const int64_t jspan = (N + nsplit - 1) / nsplit;
   nsplit = (N + jspan - 1) / jspan;
   const int64_t nblk = nti * nsplit;
+  WsbmScratch scr(st);
   double* part = nullptr;
   double* pphys = nullptr;
-  if (cudaMallocAsync((void**)&part, (size_t)nsplit * 6 * N * sizeof(double), st) != cudaSuccess)
-    return WSBM_ERR_OOM;
-  if (cudaMallocAsync((void**)&pphys, (size_t)nblk * 2 * sizeof(double), st) != cudaSuccess) {
-    cudaFreeAsync(part, st);
-    return WSBM_ERR_OOM;
-  }
+  if ((rc = scr.get((size_t)nsplit * 6 * N * sizeof(double), (void**)&part))) return rc;
+  if ((rc = scr.get((size_t)nblk * 2 * sizeof(double), (void**)&pphys))) return rc;
   DevGeom dg = wsbm_devgeom(g);
   k_entries_vjp<<<dim3((unsigned)nti, (unsigned)nsplit), VJP_THREADS, 0, st>>>(
       dg, ph, (const double2*)lam, (const double2*)x, jspan, part, pphys);
@@ -546,8 +542,6 @@ extern "C" int wsbm_entries_vjp(const wsbm_geom* g, const wsbm_params* p, const 
   k_vjp_reduce<<<grid_for(6 * N, 256), 256, 0, st>>>(N, (int)nsplit, part, nblk, pphys, grad, gphys);
   wsbm_count_launch();
   rc = cudaGetLastError() == cudaSuccess ? WSBM_OK : WSBM_ERR_CUDA;
-  cudaFreeAsync(pphys, st);
-  cudaFreeAsync(part, st);
   return rc;
 }
 

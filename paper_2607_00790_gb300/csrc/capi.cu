@@ -3,7 +3,9 @@
 #include <string.h>
 
 #include <atomic>
+#include <map>
 #include <mutex>
+#include <utility>
 
 #include "wsbm_internal.h"
 
@@ -47,6 +49,79 @@ cudaError_t wsbm_malloc_async(void** p, size_t bytes, int dev, cudaStream_t st) 
   cudaMemPool_t pool = lib_pool(dev);
   if (!pool) return cudaMallocAsync(p, bytes, st);
   return cudaMallocFromPoolAsync(p, bytes, pool, st);
+}
+
+// Caller-supplied allocator (wsbm_set_allocator).
+static std::mutex g_alloc_mu;
+static WsbmAllocator g_alloc;
+
+extern "C" int wsbm_set_allocator(wsbm_alloc_fn alloc, wsbm_free_fn release, void* ctx) {
+  if ((alloc == nullptr) != (release == nullptr)) return WSBM_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lk(g_alloc_mu);
+  g_alloc.alloc = alloc;
+  g_alloc.release = release;
+  g_alloc.ctx = alloc ? ctx : nullptr;
+  return WSBM_OK;
+}
+
+WsbmAllocator wsbm_current_allocator() {
+  std::lock_guard<std::mutex> lk(g_alloc_mu);
+  return g_alloc;
+}
+
+int wsbm_dev_alloc(const WsbmAllocator& a, size_t bytes, cudaStream_t st, void** p) {
+  *p = nullptr;
+  if (bytes == 0) bytes = 16;
+  if (a.alloc) {
+    *p = a.alloc(bytes, (void*)st, a.ctx);
+    return *p ? WSBM_OK : WSBM_ERR_OOM;
+  }
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return WSBM_ERR_CUDA;
+  if (wsbm_malloc_async(p, bytes, dev, st) != cudaSuccess) {
+    cudaGetLastError();
+    *p = nullptr;
+    return WSBM_ERR_OOM;
+  }
+  return WSBM_OK;
+}
+
+void wsbm_dev_free(const WsbmAllocator& a, void* p, cudaStream_t st) {
+  if (!p) return;
+  if (a.alloc)
+    a.release(p, (void*)st, a.ctx);
+  else
+    cudaFreeAsync(p, st);
+}
+
+// SM count and shared-memory opt-ins, per device.
+static std::mutex g_dev_mu;
+static int g_nsm[64];
+static std::map<std::pair<int, const void*>, size_t> g_optin;
+
+int wsbm_sm_count() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 152;
+  std::lock_guard<std::mutex> lk(g_dev_mu);
+  if (g_nsm[dev] <= 0) {
+    int n = 0;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 152;
+    g_nsm[dev] = n;
+  }
+  return g_nsm[dev];
+}
+
+cudaError_t wsbm_smem_optin(const void* kernel, size_t bytes) {
+  if (bytes <= 48 * 1024) return cudaSuccess;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lk(g_dev_mu);
+  size_t& done = g_optin[std::make_pair(dev, kernel)];
+  if (bytes <= done) return cudaSuccess;
+  e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e == cudaSuccess) done = bytes;
+  return e;
 }
 
 extern "C" int wsbm_trim_memory(void) {
@@ -144,14 +219,12 @@ extern "C" int wsbm_entries_raw(const wsbm_geom* g, const wsbm_params* p, const 
   if (nr == 0 || nc == 0) return WSBM_OK;
   if (!rows || !cols || !out) return WSBM_ERR_INVALID_ARG;
   cudaStream_t st = (cudaStream_t)stream;
+  WsbmScratch scr(st);
   int32_t* buf = nullptr;
   PairTask* dtask = nullptr;
   size_t nint = (size_t)3 * nr + 3 * nc;
-  if (cudaMallocAsync((void**)&buf, nint * sizeof(int32_t), st) != cudaSuccess) return WSBM_ERR_OOM;
-  if (cudaMallocAsync((void**)&dtask, sizeof(PairTask), st) != cudaSuccess) {
-    cudaFreeAsync(buf, st);
-    return WSBM_ERR_OOM;
-  }
+  if ((rc = scr.get(nint * sizeof(int32_t), (void**)&buf))) return rc;
+  if ((rc = scr.get(sizeof(PairTask), (void**)&dtask))) return rc;
   {
     int32_t* rnode = buf;
     int32_t* rpos = rnode + nr;
@@ -182,8 +255,6 @@ extern "C" int wsbm_entries_raw(const wsbm_geom* g, const wsbm_params* p, const 
     CK(cudaStreamSynchronize(st));
   }
 done:
-  cudaFreeAsync(dtask, st);
-  cudaFreeAsync(buf, st);
   return rc;
 }
 
@@ -204,14 +275,11 @@ extern "C" int wsbm_proxy_block(const wsbm_geom* g, const wsbm_params* p, int32_
   if (nidx == 0) return WSBM_OK;
   if (!idx || !out) return WSBM_ERR_INVALID_ARG;
   cudaStream_t st = (cudaStream_t)stream;
+  WsbmScratch scr(st);
   int32_t* buf = nullptr;
   ProxyTask* dtask = nullptr;
-  if (cudaMallocAsync((void**)&buf, (size_t)3 * nidx * sizeof(int32_t), st) != cudaSuccess)
-    return WSBM_ERR_OOM;
-  if (cudaMallocAsync((void**)&dtask, sizeof(ProxyTask), st) != cudaSuccess) {
-    cudaFreeAsync(buf, st);
-    return WSBM_ERR_OOM;
-  }
+  if ((rc = scr.get((size_t)3 * nidx * sizeof(int32_t), (void**)&buf))) return rc;
+  if ((rc = scr.get(sizeof(ProxyTask), (void**)&dtask))) return rc;
   {
     ProxyTask t;
     memset(&t, 0, sizeof(t));
@@ -238,7 +306,39 @@ extern "C" int wsbm_proxy_block(const wsbm_geom* g, const wsbm_params* p, int32_
     CK(cudaStreamSynchronize(st));
   }
 done:
-  cudaFreeAsync(dtask, st);
-  cudaFreeAsync(buf, st);
   return rc;
+}
+
+extern "C" int wsbm_zgemm(int32_t m, int32_t n, int32_t k, const double* alpha, const void* A, int64_t lda,
+                          const void* B, int64_t ldb, const double* beta, void* C, int64_t ldc,
+                          void* stream) {
+  if (m < 0 || n < 0 || k < 1 || k > 32768 || !alpha || !beta) return WSBM_ERR_INVALID_ARG;
+  if (m == 0 || n == 0) return WSBM_OK;
+  if (!A || !B || !C || lda < m || ldb < k || ldc < m) return WSBM_ERR_INVALID_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  WsbmScratch scr(st);
+  void* ws = nullptr;
+  int rc = scr.get(wsbm_zgemm_tc_ws_bytes(m, n, k), &ws);
+  if (rc) return rc;
+  rc = wsbm_zgemm_tc(m, n, k, make_double2(alpha[0], alpha[1]), (const double2*)A, lda, (const double2*)B, ldb,
+                     make_double2(beta[0], beta[1]), (double2*)C, ldc, ws, st);
+  if (rc == -1) return WSBM_ERR_INVALID_ARG;
+  if (rc) return WSBM_ERR_CUDA;
+  rc = wsbm_zgemm_tc_status(st);
+  return rc == 0 ? WSBM_OK : (rc == -5 ? WSBM_ERR_TIMEOUT : WSBM_ERR_CUDA);
+}
+
+extern "C" int wsbm_lu_dense(void* A, int64_t lda, int32_t n, int32_t* piv, void* stream) {
+  if (n < 0 || (n > 0 && (!A || !piv || lda < n))) return WSBM_ERR_INVALID_ARG;
+  if (n == 0) return WSBM_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  WsbmScratch scr(st);
+  void* ws = nullptr;
+  int rc = scr.get(wsbm_lu_big_ws_bytes(n), &ws);
+  if (rc) return rc;
+  rc = wsbm_lu_big((double2*)A, lda, n, piv, nullptr, ws, st);
+  if (rc == -1) return WSBM_ERR_INVALID_ARG;
+  if (rc) return WSBM_ERR_CUDA;
+  rc = wsbm_zgemm_tc_status(st);
+  return rc == 0 ? WSBM_OK : (rc == -5 ? WSBM_ERR_TIMEOUT : WSBM_ERR_CUDA);
 }

@@ -803,16 +803,7 @@ __global__ void k_cpqr_finish(const QrDesc* __restrict__ d) {
 }
 
 // ------------------------------------------------------------------ host drivers ----
-static int grid_cap() {
-  static int nsm = 0;
-  if (nsm == 0) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    if (nsm <= 0) nsm = 152;
-  }
-  return nsm * 8;
-}
+static int grid_cap() { return wsbm_sm_count() * 8; }
 
 static int tiles_x(int64_t tiles) {
   int cap = grid_cap();
@@ -935,16 +926,7 @@ int wsbm_lu_solve_fused_batched(const LuSolveDesc* d_desc, int nbatch, int max_n
   const size_t tile = 32 * 33, panel = (size_t)(max_n + 1) * LUS_B;
   const size_t sm = ((size_t)max_n + (panel > tile ? panel : tile)) * sizeof(double2);
   // the opt-in above 48 KB is a per-device attribute of the kernel
-  static size_t set[64];
-  int dev = 0;
-  cudaGetDevice(&dev);
-  size_t* done = (dev >= 0 && dev < 64) ? &set[dev] : nullptr;
-  if (sm > 48 * 1024 && (!done || sm > *done)) {
-    if (cudaFuncSetAttribute(k_lu_solve_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) !=
-        cudaSuccess)
-      return -3;
-    if (done) *done = sm;
-  }
+  if (wsbm_smem_optin((const void*)k_lu_solve_fused, sm) != cudaSuccess) return -3;
   k_lu_solve_fused<<<nbatch, LUS_T, sm, st>>>(d_desc);
   wsbm_count_launch();
   return cudaGetLastError() == cudaSuccess ? 0 : -3;
@@ -984,5 +966,242 @@ int wsbm_lu_solve_t_batched(const TrsmDesc* d_desc, int nbatch, int max_n, int m
   dim3 gd(tiles_x((max_nrhs + 127) / 128), nbatch);
   k_apply_piv_inv<<<gd, 128, 0, st>>>(d_desc);
   wsbm_count_launch();
+  return cudaGetLastError() == cudaSuccess ? 0 : -3;
+}
+
+// ------------------------------------------------------------- LU of one large matrix ----
+// Right-looking blocked LU with partial pivoting for a single large matrix (the dense root of
+// a full build): outer panels of LUB_NB columns.  Each panel is factored recursively (halves,
+// down to blocks of LUB_WB columns done column by column), with every column operation spread
+// over the whole GPU: the pivot search is one launch whose CTAs combine their candidates with
+// atomicMax on a 64-bit key, the row swap one small launch, the scaling and rank-1 update of
+// the block (with the search of the next column fused in) one launch.  The panel's row swaps
+// are applied to the other columns (k_laswp), U12 = L11^-1 A12 (k_lu_trsm_row) and the trailing
+// update A22 -= L21 U12 runs on the tensor cores (wsbm_zgemm_tc).  Factors and piv as for
+// wsbm_lu_batched.  Pivot: the row of largest max(|re|, |im|) compared on the upper 32 bits of
+// its bit pattern (within 2^-20 of the largest), first row on ties.
+#define LUB_NB 128  // outer panel width
+#define LUB_WB 8    // column-by-column block width
+
+__device__ __forceinline__ unsigned long long lub_key(double2 v, int row) {
+  const unsigned long long m = 0x7fffffffffffffffull;
+  const unsigned long long a = (unsigned long long)__double_as_longlong(v.x) & m;
+  const unsigned long long b = (unsigned long long)__double_as_longlong(v.y) & m;
+  const unsigned long long hi = (a > b ? a : b) >> 32;
+  return (hi << 32) | (unsigned long long)(0xFFFFFFFFu - (unsigned)row);
+}
+
+__device__ __forceinline__ void lub_block_max(unsigned long long best, unsigned long long* key) {
+  __shared__ unsigned long long red[32];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long x = __shfl_xor_sync(0xFFFFFFFFu, best, o);
+    best = x > best ? x : best;
+  }
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = best;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    best = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0ull;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const unsigned long long x = __shfl_xor_sync(0xFFFFFFFFu, best, o);
+      best = x > best ? x : best;
+    }
+    if (threadIdx.x == 0 && best) atomicMax(key, best);
+  }
+}
+
+// key = max over rows [c, n) of column c (the key must be 0 on entry).
+__global__ void __launch_bounds__(256) k_lub_search(const double2* __restrict__ A, int64_t lda, int n, int c,
+                                                   unsigned long long* __restrict__ key) {
+  unsigned long long best = 0;
+  const double2* col = A + (int64_t)c * lda;
+  for (int i = c + blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const unsigned long long k = lub_key(col[i], i);
+    best = k > best ? k : best;
+  }
+  lub_block_max(best, key);
+}
+
+// Pivot of column c from its key: piv[c] = p, swap rows c and p over the panel columns
+// [cs, ce), store 1/pivot; clear the key of column c + 1.
+__global__ void k_lub_swap(double2* __restrict__ A, int64_t lda, int c, int cs, int ce,
+                           const unsigned long long* __restrict__ key, int* __restrict__ piv,
+                           double2* __restrict__ inv, unsigned long long* __restrict__ key_next,
+                           int* __restrict__ info) {
+  const unsigned long long k = key[0];
+  const int p = k ? (int)(0xFFFFFFFFu - (unsigned)(k & 0xFFFFFFFFull)) : c;
+  __shared__ double2 spv;
+  if (threadIdx.x == 0) spv = A[p + (int64_t)c * lda];  // the value that lands on the diagonal
+  __syncthreads();
+  if (p != c) {
+    for (int cc = cs + threadIdx.x; cc < ce; cc += blockDim.x) {
+      double2* col = A + (int64_t)cc * lda;
+      const double2 t = col[c];
+      col[c] = col[p];
+      col[p] = t;
+    }
+  }
+  if (threadIdx.x == 0) {
+    const double2 pv = spv;
+    piv[c] = p;
+    key_next[0] = 0ull;
+    inv[0] = (pv.x == 0.0 && pv.y == 0.0) ? make_double2(0.0, 0.0) : cdiv(make_double2(1.0, 0.0), pv);
+    if (pv.x == 0.0 && pv.y == 0.0 && info) info[0] = c + 1;
+  }
+}
+
+// Rows (c, n): l = A[i,c] / pivot, A[i,c] = l, A[i,cc] -= l A[c,cc] for cc in (c, ce);
+// then, when c + 1 < ce, the candidates of column c + 1 into key_next.
+__global__ void __launch_bounds__(256) k_lub_update(double2* __restrict__ A, int64_t lda, int n, int c, int ce,
+                                                   const double2* __restrict__ inv,
+                                                   unsigned long long* __restrict__ key_next) {
+  const double2 iv = inv[0];
+  double2 u[LUB_WB];
+  const int w = ce - c - 1;
+#pragma unroll
+  for (int t = 0; t < LUB_WB - 1; ++t) u[t] = t < w ? A[c + (int64_t)(c + 1 + t) * lda] : make_double2(0.0, 0.0);
+  unsigned long long best = 0;
+  for (int i = c + 1 + blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    double2* a = A + i + (int64_t)c * lda;
+    const double2 l = cmul(*a, iv);
+    *a = l;
+#pragma unroll
+    for (int t = 0; t < LUB_WB - 1; ++t) {
+      if (t < w) {
+        double2* b = a + (int64_t)(1 + t) * lda;
+        const double2 v = cfms(l, u[t], *b);
+        *b = v;
+        if (t == 0) {
+          const unsigned long long k = lub_key(v, i);
+          best = k > best ? k : best;
+        }
+      }
+    }
+  }
+  if (w > 0) lub_block_max(best, key_next);
+}
+
+// B[r0 : r0+nb, cols] <- L^-1 B with L = the unit lower triangle of A[r0 : r0+nb, r0 : r0+nb];
+// one thread per column of [c0, c1).
+__global__ void k_lub_trsm(double2* __restrict__ A, int64_t lda, int r0, int nb, int c0, int c1) {
+  const int c = c0 + blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= c1) return;
+  double2* col = A + (int64_t)c * lda;
+  for (int i = r0 + 1; i < r0 + nb; ++i) {
+    double2 s = col[i];
+    for (int t = r0; t < i; ++t) s = cfms(A[i + (int64_t)t * lda], col[t], s);
+    col[i] = s;
+  }
+}
+
+// C[m x nc] -= A[m x k] B[k x nc] (the updates inside a panel), FP64 tiles.
+__global__ void __launch_bounds__(256) k_lub_gemm(int m, int nc, int k, const double2* __restrict__ A,
+                                                  int64_t lda, const double2* __restrict__ B, int64_t ldb,
+                                                  double2* C, int64_t ldc) {
+  const int ntm = (m + GT - 1) / GT, ntn = (nc + GT - 1) / GT;
+  const double2 one = make_double2(1.0, 0.0), mone = make_double2(-1.0, 0.0);
+  for (int t = blockIdx.x; t < ntm * ntn; t += gridDim.x)
+    gemm_tile<false>(m, nc, k, A, lda, B, ldb, C, ldc, mone, one, t % ntm, t / ntm);
+}
+
+namespace {
+struct LubCtx {
+  double2* A;
+  int64_t lda;
+  int n;
+  int* piv;
+  unsigned long long* key;  // n + 1 keys
+  double2* inv;
+  int* info;
+  cudaStream_t st;
+  int cs, ce;  // current outer panel
+};
+
+int lub_grid(int64_t rows) {
+  const int64_t b = (rows + 255) / 256, cap = (int64_t)wsbm_sm_count() * 4;
+  return (int)(b < 1 ? 1 : (b < cap ? b : cap));
+}
+
+// factor columns [c0, c1) of rows [c0, n); row swaps across the whole outer panel
+void lub_rec(const LubCtx& x, int c0, int c1) {
+  const int w = c1 - c0;
+  if (w <= LUB_WB) {
+    k_lub_search<<<lub_grid(x.n - c0), 256, 0, x.st>>>(x.A, x.lda, x.n, c0, x.key + c0);
+    wsbm_count_launch();
+    for (int c = c0; c < c1; ++c) {
+      k_lub_swap<<<1, 128, 0, x.st>>>(x.A, x.lda, c, x.cs, x.ce, x.key + c, x.piv, x.inv, x.key + c + 1, x.info);
+      k_lub_update<<<lub_grid(x.n - c - 1), 256, 0, x.st>>>(x.A, x.lda, x.n, c, c1, x.inv, x.key + c + 1);
+      wsbm_count_launches(2);
+    }
+    return;
+  }
+  const int mid = c0 + ((w / 2 + LUB_WB - 1) / LUB_WB) * LUB_WB;
+  lub_rec(x, c0, mid);
+  // A[c0:mid, mid:c1] = L11^-1 A[c0:mid, mid:c1];  A[mid:n, mid:c1] -= A[mid:n, c0:mid] A[c0:mid, mid:c1]
+  k_lub_trsm<<<(c1 - mid + 63) / 64, 64, 0, x.st>>>(x.A, x.lda, c0, mid - c0, mid, c1);
+  const int m = x.n - mid;
+  const int64_t tiles = (int64_t)((m + GT - 1) / GT) * ((c1 - mid + GT - 1) / GT);
+  k_lub_gemm<<<tiles_x(tiles), 256, 0, x.st>>>(m, c1 - mid, mid - c0, x.A + mid + (int64_t)c0 * x.lda, x.lda,
+                                             x.A + c0 + (int64_t)mid * x.lda, x.lda,
+                                             x.A + mid + (int64_t)mid * x.lda, x.lda);
+  wsbm_count_launches(2);
+  // the key of column mid is set by the first search of the right half
+  lub_rec(x, mid, c1);
+}
+}  // namespace
+
+size_t wsbm_lu_big_ws_bytes(int n) {
+  size_t b = wsbm_zgemm_tc_ws_bytes(n, n, LUB_NB);
+  b = (b + 255) & ~(size_t)255;
+  b += ((size_t)n + 8) * sizeof(unsigned long long) + 256 + sizeof(LuDesc) + 256;
+  return b;
+}
+
+int wsbm_lu_big(double2* A, int64_t lda, int n, int* piv, int* d_info, void* ws, cudaStream_t st) {
+  if (n <= 0) return 0;
+  if (!A || !piv || !ws || lda < n || ((uintptr_t)ws & 255)) return -1;
+  size_t off = (wsbm_zgemm_tc_ws_bytes(n, n, LUB_NB) + 255) & ~(size_t)255;
+  unsigned long long* key = (unsigned long long*)((char*)ws + off);
+  off += ((size_t)n + 8) * sizeof(unsigned long long);
+  off = (off + 255) & ~(size_t)255;
+  double2* inv = (double2*)((char*)ws + off);
+  LuDesc* dd = (LuDesc*)((char*)ws + off + 256);
+  LuDesc h;
+  h.A = A;
+  h.lda = lda;
+  h.piv = piv;
+  h.n = n;
+  h.pad = 0;
+  if (cudaMemcpyAsync(dd, &h, sizeof(h), cudaMemcpyHostToDevice, st) != cudaSuccess) return -3;
+  if (cudaMemsetAsync(key, 0, ((size_t)n + 8) * sizeof(unsigned long long), st) != cudaSuccess) return -3;
+  LubCtx x;
+  x.A = A;
+  x.lda = lda;
+  x.n = n;
+  x.piv = piv;
+  x.key = key;
+  x.inv = inv;
+  x.info = d_info;
+  x.st = st;
+  const double2 mone = make_double2(-1.0, 0.0), one = make_double2(1.0, 0.0);
+  for (int j0 = 0; j0 < n; j0 += LUB_NB) {
+    const int jb = std::min(LUB_NB, n - j0), je = j0 + jb;
+    x.cs = j0;
+    x.ce = je;
+    lub_rec(x, j0, je);
+    dim3 gs(tiles_x((n + 127) / 128), 1);
+    k_laswp<<<gs, 128, 0, st>>>(dd, j0, jb);
+    wsbm_count_launch();
+    if (je < n) {
+      k_lu_trsm_row<<<gs, 128, 0, st>>>(dd, j0, jb);
+      wsbm_count_launch();
+      const int m = n - je;
+      int rc = wsbm_zgemm_tc(m, m, jb, mone, A + je + (int64_t)j0 * lda, lda, A + j0 + (int64_t)je * lda, lda,
+                             one, A + je + (int64_t)je * lda, lda, ws, st);
+      if (rc) return rc;
+    }
+  }
+  // (the tensor-core kernel's timeout flag is read by the caller through wsbm_zgemm_tc_status)
   return cudaGetLastError() == cudaSuccess ? 0 : -3;
 }

@@ -11,6 +11,22 @@ void wsbm_count_launches(int64_t n);  // launches replayed from a captured CUDA 
 int64_t wsbm_launch_count();
 // Stream-ordered allocation from the library's memory pool of device dev (see capi.cu).
 cudaError_t wsbm_malloc_async(void** p, size_t bytes, int dev, cudaStream_t st);
+// Number of SMs of the current device (cached per device, thread safe).
+int wsbm_sm_count();
+// Opt a kernel in to `bytes` of dynamic shared memory on the current device (remembered per
+// device and kernel, thread safe).  Returns cudaSuccess or the error of the attribute call.
+cudaError_t wsbm_smem_optin(const void* kernel, size_t bytes);
+
+// tc_gemm.cu: C (m x n) = beta C + alpha A (m x k) B (k x n), complex128 column-major, on the
+// tensor cores from exact 8-bit digit planes (FP64-level accuracy).  ws: 256-byte aligned
+// device work space of wsbm_zgemm_tc_ws_bytes(m, n, k) bytes.  1 <= k <= 32768.  Returns 0,
+// -1 (bad arguments) or -3 (launch / tensor-map error); enqueues only.
+int wsbm_zgemm_tc(int m, int n, int k, double2 alpha, const double2* A, int64_t lda, const double2* B,
+                  int64_t ldb, double2 beta, double2* C, int64_t ldc, void* ws, cudaStream_t st);
+size_t wsbm_zgemm_tc_ws_bytes(int m, int n, int k);
+// Synchronizes the stream and returns -5 (and clears the flag) if a bounded wait of the GEMM
+// kernel ran out since the last call, else 0 (-3 on a CUDA error).
+int wsbm_zgemm_tc_status(cudaStream_t st);
 
 // C = alpha * op(A) * B + beta * C  (column-major, op(A) m x k, B k x n, C m x n);
 // op(A) = A (ta = 0, A stored m x k) or A^T (ta = 1, A stored k x m).
@@ -83,6 +99,12 @@ int wsbm_lu_solve_fused_batched(const LuSolveDesc* d_desc, int nbatch, int max_n
 
 int wsbm_gemm_batched(const GemmDesc* d_desc, int nbatch, int max_m, int max_n, cudaStream_t st);
 int wsbm_lu_batched(const LuDesc* d_desc, int nbatch, int max_n, int* d_info, cudaStream_t st);
+// LU with partial pivoting of one large n x n matrix (same factor layout and piv as
+// wsbm_lu_batched), trailing updates on the tensor cores.  ws: 256-byte aligned device work
+// space of wsbm_lu_big_ws_bytes(n) bytes; d_info (device int, may be NULL) receives j + 1 when
+// pivot j is exactly zero.  Enqueues only; returns 0, -1 or -3.
+int wsbm_lu_big(double2* A, int64_t lda, int n, int* piv, int* d_info, void* ws, cudaStream_t st);
+size_t wsbm_lu_big_ws_bytes(int n);
 int wsbm_trsm_batched(const TrsmDesc* d_desc, int nbatch, int max_n, int max_nrhs, int lower,
                       cudaStream_t st);
 int wsbm_lu_solve_batched(const TrsmDesc* d_desc_lower, const TrsmDesc* d_desc_upper, int nbatch,

@@ -487,14 +487,7 @@ __global__ void k_unknowns_to_slots(const int64_t* __restrict__ idx, int64_t n, 
 
 // ------------------------------------------------------------------- host helpers ----
 static int grid_for(int64_t ntiles) {
-  static int nsm = 0;
-  if (nsm == 0) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    if (nsm <= 0) nsm = 152;
-  }
-  int64_t cap = (int64_t)nsm * 16;
+  const int64_t cap = (int64_t)wsbm_sm_count() * 16;
   return (int)(ntiles < cap ? ntiles : cap);
 }
 

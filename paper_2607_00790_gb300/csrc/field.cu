@@ -146,7 +146,7 @@ __global__ void k_field_reduce(int64_t nt, int nsplit, int nrhs, int c0,
 }
 
 int grid_cap(int64_t blocks) {
-  int64_t cap = 152 * 16;
+  const int64_t cap = (int64_t)wsbm_sm_count() * 16;
   return (int)(blocks < 1 ? 1 : (blocks < cap ? blocks : cap));
 }
 
@@ -169,9 +169,7 @@ extern "C" int wsbm_field(const wsbm_geom* g, const wsbm_params* p, const void* 
   cudaStream_t st = (cudaStream_t)stream;
   const int64_t N = g->n;
   const int64_t nti = (nt + FLD_THREADS - 1) / FLD_THREADS;
-  int dev = 0, nsm = 152, per_sm = 1;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  int nsm = wsbm_sm_count(), per_sm = 1;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_field, FLD_THREADS, 0) != cudaSuccess ||
       per_sm < 1)
     per_sm = 1;
@@ -179,9 +177,9 @@ extern "C" int wsbm_field(const wsbm_geom* g, const wsbm_params* p, const void* 
   int64_t nsplit = std::max<int64_t>(1, std::min<int64_t>((want + nti - 1) / nti, (N + 127) / 128));
   const int64_t jspan = (N + nsplit - 1) / nsplit;
   nsplit = (N + jspan - 1) / jspan;
+  WsbmScratch scr(st);
   double2* part = nullptr;
-  if (cudaMallocAsync((void**)&part, (size_t)nsplit * nt * FLD_RHS * sizeof(double2), st) != cudaSuccess)
-    return WSBM_ERR_OOM;
+  if ((rc = scr.get((size_t)nsplit * nt * FLD_RHS * sizeof(double2), (void**)&part))) return rc;
   DevGeom dg = wsbm_devgeom(g);
   k_field_side<<<(unsigned)nti, FLD_THREADS, 0, st>>>(dg, tx, ty, nt, inside);
   wsbm_count_launch();
@@ -194,6 +192,5 @@ extern "C" int wsbm_field(const wsbm_geom* g, const wsbm_params* p, const void* 
     wsbm_count_launch();
   }
   rc = cudaGetLastError() == cudaSuccess ? WSBM_OK : WSBM_ERR_CUDA;
-  cudaFreeAsync(part, st);
   return rc;
 }

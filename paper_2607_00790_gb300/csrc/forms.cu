@@ -283,14 +283,7 @@ __global__ void __launch_bounds__(WSBM_PAIR_THREADS)
 }
 
 int form_grid(int64_t ntiles) {
-  static int nsm = 0;
-  if (nsm == 0) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    if (nsm <= 0) nsm = 152;
-  }
-  const int64_t cap = (int64_t)nsm * 16;
+  const int64_t cap = (int64_t)wsbm_sm_count() * 16;
   return (int)(ntiles < cap ? ntiles : cap);
 }
 

@@ -82,10 +82,9 @@ struct Level {
 struct wsbm_hss {
   int dev = 0;
   cudaStream_t st = nullptr;
-  // allocator of the factors and work space, fixed at creation (null: the library's pool)
-  wsbm_alloc_fn ualloc = nullptr;
-  wsbm_free_fn ufree = nullptr;
-  void* uctx = nullptr;
+  // allocator of the geometry copy, factors and work space, fixed at creation (null
+  // callbacks: the library's pool)
+  WsbmAllocator alloc;
   int64_t N = 0;
   double *x = nullptr, *y = nullptr, *nx = nullptr, *ny = nullptr, *w = nullptr, *kappa = nullptr;
   std::vector<double> hx, hy, hw;
@@ -100,7 +99,9 @@ struct wsbm_hss {
   int32_t* root_piv = nullptr;
   int root_n = 0;
   bool factored = false;
+  uint64_t generation = 0;   // bumped whenever the factors are released (see plan_get)
   std::vector<void*> owned;  // factor allocations
+  std::vector<void*> geo;    // the geometry copy
   wsbm_stats_t stats;
   cudaEvent_t ev[14];
   std::shared_ptr<struct SolvePlan> plan;  // solve plan of the last nrhs (see wsbm_solve)
@@ -400,29 +401,10 @@ static void* pin_take(cudaStream_t st, size_t bytes) {
   return (P.p && P.off <= P.cap) ? P.p + a : nullptr;
 }
 
-// Caller-supplied allocator (wsbm_set_allocator): captured by each handle at creation.
-static std::mutex g_alloc_mu;
-static wsbm_alloc_fn g_ualloc = nullptr;
-static wsbm_free_fn g_ufree = nullptr;
-static void* g_uctx = nullptr;
-
-extern "C" int wsbm_set_allocator(wsbm_alloc_fn alloc, wsbm_free_fn release, void* ctx) {
-  if ((alloc == nullptr) != (release == nullptr)) return WSBM_ERR_INVALID_ARG;
-  std::lock_guard<std::mutex> lk(g_alloc_mu);
-  g_ualloc = alloc;
-  g_ufree = release;
-  g_uctx = alloc ? ctx : nullptr;
-  return WSBM_OK;
-}
-
-// device memory of a handle, stream ordered on its stream
+// device memory of a handle, stream ordered on its stream, from the allocator the handle
+// captured at creation
 static int halloc(wsbm_hss* h, size_t bytes, void** p) {
-  *p = nullptr;
-  if (h->ualloc) {
-    *p = h->ualloc(bytes, (void*)h->st, h->uctx);
-    return *p ? WSBM_OK : WSBM_ERR_OOM;
-  }
-  return wsbm_malloc_async(p, bytes, h->dev, h->st) == cudaSuccess ? WSBM_OK : WSBM_ERR_OOM;
+  return wsbm_dev_alloc(h->alloc, bytes, h->st, p);
 }
 
 template <class T>
@@ -450,12 +432,7 @@ static int dalloc(wsbm_hss* h, size_t bytes, void** p, std::vector<void*>& list)
 }
 
 static void free_list(wsbm_hss* h, std::vector<void*>& list) {
-  for (void* p : list) {
-    if (h->ufree)
-      h->ufree(p, (void*)h->st, h->uctx);
-    else
-      cudaFreeAsync(p, h->st);
-  }
+  for (void* p : list) wsbm_dev_free(h->alloc, p, h->st);
   list.clear();
 }
 
@@ -688,25 +665,19 @@ extern "C" int wsbm_create(const wsbm_geom* g, const wsbm_params* p, void* strea
   wsbm_hss* h = new wsbm_hss();
   cudaGetDevice(&h->dev);
   h->st = (cudaStream_t)stream;
-  {
-    std::lock_guard<std::mutex> lk(g_alloc_mu);
-    h->ualloc = g_ualloc;
-    h->ufree = g_ufree;
-    h->uctx = g_uctx;
-  }
+  h->alloc = wsbm_current_allocator();
   pin_acquire(h->st);
   h->N = g->n;
   h->ph = ph;
   h->prm = *p;
   if (!(h->prm.proxy_ratio > 1.0)) h->prm.proxy_ratio = 1.5;
-  h->cut = p->id_tol / 4.0;
   memset(&h->stats, 0, sizeof(h->stats));
   for (int i = 0; i < 14; ++i) cudaEventCreate(&h->ev[i]);
   size_t bytes = (size_t)h->N * sizeof(double);
   double** dst[6] = {&h->x, &h->y, &h->nx, &h->ny, &h->w, &h->kappa};
   const double* src[6] = {g->x, g->y, g->nx, g->ny, g->w, g->kappa};
   for (int a = 0; a < 6; ++a) {
-    if (cudaMalloc((void**)dst[a], bytes) != cudaSuccess) {
+    if (dalloc(h, bytes, (void**)dst[a], h->geo) != WSBM_OK) {
       wsbm_destroy(h);
       return WSBM_ERR_OOM;
     }
@@ -758,6 +729,11 @@ extern "C" int wsbm_create(const wsbm_geom* g, const wsbm_params* p, void* strea
   while (((h->N) >> L) > p->leaf && L < 24) ++L;
   if (L > 0 && (h->N >> L) < 2) --L;
   h->L = L;
+  // CPQR cutoff: the errors of the 2^L leaf-box IDs (and of the levels above) add up in the
+  // solution roughly incoherently, so the cutoff shrinks with the square root of the number of
+  // leaf boxes; the factor 4 keeps densities and far field within a few id_tol of the dense
+  // solution on 15-node-per-wavelength curves up to N = 32768
+  h->cut = p->id_tol / (4.0 * sqrt((double)((int64_t)1 << L)));
   h->lv.resize(L + 1);
   for (int l = 0; l <= L; ++l) {
     int nb = 1 << l;
@@ -777,6 +753,7 @@ extern "C" int wsbm_create(const wsbm_geom* g, const wsbm_params* p, void* strea
 
 static void release_factors(wsbm_hss* h) {
   h->plan.reset();  // a solve plan refers to the factors
+  ++h->generation;  // and so does any batch plan that includes this handle
   free_list(h, h->owned);
   for (auto& l : h->lv) l.compressed = false;
   for (auto& l : h->lv)
@@ -799,11 +776,9 @@ static void release_factors(wsbm_hss* h) {
 extern "C" void wsbm_destroy(wsbm_hss_t h) {
   if (!h) return;
   release_factors(h);
+  free_list(h, h->geo);
   cudaStreamSynchronize(h->st);
   pin_release(h->st);
-  double* arr[6] = {h->x, h->y, h->nx, h->ny, h->w, h->kappa};
-  for (double* a : arr)
-    if (a) cudaFree(a);
   for (int i = 0; i < 14; ++i)
     if (h->ev[i]) cudaEventDestroy(h->ev[i]);
   delete h;
@@ -1817,6 +1792,8 @@ __global__ void k_split_uq_batched(const ConvDesc* __restrict__ d, int nrhs) {
 // solutions leave through the plan's own buffers (rin, uo, qo).
 struct SolvePlan {
   std::vector<wsbm_hss*> hs;
+  std::vector<uint64_t> gen;  // factor generation of each handle when the plan was built
+  WsbmAllocator alloc;        // the first handle's allocator (buffers and descriptors)
   int nrhs = 0;
   cudaStream_t st = nullptr;  // the handles' stream (buffers are allocated in its order)
   cudaStream_t cs = nullptr;  // the plan's own stream: capture and replay (a graph cannot be
@@ -1833,7 +1810,7 @@ struct SolvePlan {
     if (cs) cudaStreamSynchronize(cs);
     if (exec) cudaGraphExecDestroy(exec);
     if (graph) cudaGraphDestroy(graph);
-    for (void* p : mem) cudaFreeAsync(p, st);
+    for (void* p : mem) wsbm_dev_free(alloc, p, st);
     cudaStreamSynchronize(st);
     if (ev_in) cudaEventDestroy(ev_in);
     if (ev_out) cudaEventDestroy(ev_out);
@@ -1845,15 +1822,14 @@ template <class T>
 static int plan_upload(SolvePlan& P, const std::vector<T>& v, T** d) {
   *d = nullptr;
   if (v.empty()) return WSBM_OK;
-  if (cudaMallocAsync((void**)d, v.size() * sizeof(T), P.st) != cudaSuccess) return WSBM_ERR_OOM;
+  HK(wsbm_dev_alloc(P.alloc, v.size() * sizeof(T), P.st, (void**)d));
   P.mem.push_back(*d);
   if (cudaMemcpyAsync(*d, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, P.st) != cudaSuccess)
     return WSBM_ERR_CUDA;
   return WSBM_OK;
 }
 static int plan_alloc(SolvePlan& P, size_t bytes, double2** p) {
-  *p = nullptr;
-  if (cudaMallocAsync((void**)p, bytes ? bytes : 16, P.st) != cudaSuccess) return WSBM_ERR_OOM;
+  HK(wsbm_dev_alloc(P.alloc, bytes, P.st, (void**)p));
   P.mem.push_back(*p);
   return WSBM_OK;
 }
@@ -2170,11 +2146,18 @@ static int plan_run(SolvePlan& P) {
   return WSBM_OK;
 }
 
+// A plan holds device pointers into its handles' factors, so it is reused only while every
+// handle still has the factors it was built from (a member of a batch may have been
+// re-factored on its own since).
 static int plan_get(std::shared_ptr<SolvePlan>& slot, const std::vector<wsbm_hss*>& hs, int nrhs) {
-  if (slot && slot->nrhs == nrhs && slot->hs == hs) return WSBM_OK;
+  std::vector<uint64_t> gen(hs.size());
+  for (size_t i = 0; i < hs.size(); ++i) gen[i] = hs[i]->generation;
+  if (slot && slot->nrhs == nrhs && slot->hs == hs && slot->gen == gen) return WSBM_OK;
   slot.reset();
   auto P = std::make_shared<SolvePlan>();
   P->hs = hs;
+  P->gen = gen;
+  P->alloc = hs[0]->alloc;
   P->nrhs = nrhs;
   P->st = hs[0]->st;
   if (cudaStreamCreateWithFlags(&P->cs, cudaStreamNonBlocking) != cudaSuccess ||
@@ -2517,5 +2500,121 @@ extern "C" int wsbm_box_skeletons(wsbm_hss_t h, int32_t level, int32_t box, int6
 extern "C" int wsbm_stats(wsbm_hss_t h, wsbm_stats_t* s) {
   if (!h || !s) return WSBM_ERR_INVALID_ARG;
   *s = h->stats;
+  return WSBM_OK;
+}
+
+// ----------------------------------------------------------------- refinement ----
+// Iterative refinement with the dense matrix-free product: r = b - A x, x += HSS^-1 r.
+// x is kept in paper order [u; q] (one column of 2N per right-hand side).
+
+// r = b - y, with per-block partial sums of |b|^2 and |r|^2 (blocks of one column each).
+__global__ void __launch_bounds__(256) k_residual(const double2* __restrict__ b,
+                                                  const double2* __restrict__ y,
+                                                  double2* __restrict__ r, int64_t len,
+                                                  double* __restrict__ part) {
+  const int c = blockIdx.y;
+  const double2* bc = b + (int64_t)c * len;
+  const double2* yc = y + (int64_t)c * len;
+  double2* rc = r + (int64_t)c * len;
+  double sb = 0.0, sr = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < len;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    double2 bv = bc[i], yv = yc[i];
+    double2 rv = make_double2(bv.x - yv.x, bv.y - yv.y);
+    rc[i] = rv;
+    sb += bv.x * bv.x + bv.y * bv.y;
+    sr += rv.x * rv.x + rv.y * rv.y;
+  }
+  __shared__ double s1[256], s2[256];
+  s1[threadIdx.x] = sb;
+  s2[threadIdx.x] = sr;
+  __syncthreads();
+  for (int s = 128; s > 0; s >>= 1) {
+    if (threadIdx.x < s) {
+      s1[threadIdx.x] += s1[threadIdx.x + s];
+      s2[threadIdx.x] += s2[threadIdx.x + s];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    part[2 * ((int64_t)c * gridDim.x + blockIdx.x)] = s1[0];
+    part[2 * ((int64_t)c * gridDim.x + blockIdx.x) + 1] = s2[0];
+  }
+}
+
+// x[:, c] = [u[:, c]; q[:, c]] (mode 0), or u += x[0:N], q += x[N:2N] (mode 1).
+__global__ void k_uq_pack(double2* __restrict__ x, double2* __restrict__ u, double2* __restrict__ q,
+                          int64_t N, int nrhs, int mode) {
+  const int64_t tot = 2 * N * nrhs;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t c = e / (2 * N), i = e % (2 * N);
+    double2* d = i < N ? u + c * N + i : q + c * N + (i - N);
+    if (mode == 0) {
+      x[e] = *d;
+    } else {
+      double2 v = *d, a = x[e];
+      *d = make_double2(v.x + a.x, v.y + a.y);
+    }
+  }
+}
+
+extern "C" int wsbm_refine(wsbm_hss_t h, int32_t trans, const void* rhs, int32_t nrhs, void* u,
+                           void* q, int32_t iters, double* res) {
+  if (!h || (trans != 0 && trans != 1) || nrhs < 0 || iters < 0) return WSBM_ERR_INVALID_ARG;
+  if (!h->factored) return WSBM_ERR_NOT_FACTORED;
+  if (h->prm.formulation != WSBM_FORM_WSBM) return WSBM_ERR_INVALID_ARG;  // matvec: eq. (weakly_bm)
+  if (nrhs == 0) return WSBM_OK;
+  if (!rhs || !u || !q) return WSBM_ERR_INVALID_ARG;
+  cudaStream_t st = h->st;
+  TmpMem tmpm(h);
+  std::vector<void*>& tmp = tmpm.v;
+  const int64_t N = h->N, len = 2 * N;
+  double2 *x = nullptr, *y = nullptr, *r = nullptr, *du = nullptr, *dq = nullptr;
+  double* part = nullptr;
+  const int gx = 64;
+  HK(dalloc(h, (size_t)len * nrhs * sizeof(double2), (void**)&x, tmp));
+  HK(dalloc(h, (size_t)len * nrhs * sizeof(double2), (void**)&y, tmp));
+  HK(dalloc(h, (size_t)len * nrhs * sizeof(double2), (void**)&r, tmp));
+  HK(dalloc(h, (size_t)N * nrhs * sizeof(double2), (void**)&du, tmp));
+  HK(dalloc(h, (size_t)N * nrhs * sizeof(double2), (void**)&dq, tmp));
+  HK(dalloc(h, (size_t)2 * gx * nrhs * sizeof(double), (void**)&part, tmp));
+  wsbm_geom g;
+  g.n = N;
+  g.x = h->x;
+  g.y = h->y;
+  g.nx = h->nx;
+  g.ny = h->ny;
+  g.w = h->w;
+  g.kappa = h->kappa;
+  std::vector<double> hp((size_t)2 * gx * nrhs);
+  for (int it = 0; it <= iters; ++it) {
+    k_uq_pack<<<gridfor(len * nrhs), 256, 0, st>>>(x, (double2*)u, (double2*)q, N, nrhs, 0);
+    wsbm_count_launch();
+    HK(wsbm_matvec(&g, &h->prm, trans, x, nrhs, y, (void*)st));
+    k_residual<<<dim3(gx, nrhs), 256, 0, st>>>((const double2*)rhs, y, r, len, part);
+    wsbm_count_launch();
+    HC(cudaGetLastError());
+    if (res) {
+      HC(cudaMemcpyAsync(hp.data(), part, hp.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+      HC(cudaStreamSynchronize(st));
+      double sb = 0.0, sr = 0.0;
+      for (size_t i = 0; i < hp.size(); i += 2) {
+        sb += hp[i];
+        sr += hp[i + 1];
+      }
+      res[it] = sb > 0.0 ? sqrt(sr / sb) : sqrt(sr);
+    }
+    if (it == iters) break;
+    HK(trans ? wsbm_solve_transposed(h, r, nrhs, du, dq) : wsbm_solve(h, r, nrhs, du, dq));
+    // x = [du; dq] then u += du, q += dq
+    HC(cudaMemcpy2DAsync(r, len * sizeof(double2), du, N * sizeof(double2), N * sizeof(double2), nrhs,
+                         cudaMemcpyDeviceToDevice, st));
+    HC(cudaMemcpy2DAsync(r + N, len * sizeof(double2), dq, N * sizeof(double2), N * sizeof(double2),
+                         nrhs, cudaMemcpyDeviceToDevice, st));
+    k_uq_pack<<<gridfor(len * nrhs), 256, 0, st>>>(r, (double2*)u, (double2*)q, N, nrhs, 1);
+    wsbm_count_launch();
+  }
+  HC(cudaStreamSynchronize(st));
   return WSBM_OK;
 }

@@ -103,7 +103,7 @@ __global__ void k_matvec_reduce(int64_t N, int nsplit, const double2* __restrict
 }
 
 static int grid_for(int64_t blocks) {
-  int64_t cap = 152 * 16;
+  const int64_t cap = (int64_t)wsbm_sm_count() * 16;
   return (int)(blocks < 1 ? 1 : (blocks < cap ? blocks : cap));
 }
 
@@ -123,9 +123,7 @@ extern "C" int wsbm_matvec(const wsbm_geom* g, const wsbm_params* p, int32_t tra
   cudaStream_t st = (cudaStream_t)stream;
   const int64_t N = g->n;
   const int64_t nti = (N + MV_THREADS - 1) / MV_THREADS;
-  int dev = 0, nsm = 152, per_sm = 1;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  int nsm = wsbm_sm_count(), per_sm = 1;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_matvec<false>, MV_THREADS, 0) != cudaSuccess ||
       per_sm < 1)
     per_sm = 1;
@@ -135,9 +133,9 @@ extern "C" int wsbm_matvec(const wsbm_geom* g, const wsbm_params* p, int32_t tra
   if (nsplit > nti) nsplit = nti;
   const int64_t jspan = (N + nsplit - 1) / nsplit;
   nsplit = (N + jspan - 1) / jspan;
+  WsbmScratch scr(st);
   double2* part = nullptr;
-  if (cudaMallocAsync((void**)&part, (size_t)nsplit * 2 * N * sizeof(double2), st) != cudaSuccess)
-    return WSBM_ERR_OOM;
+  if ((rc = scr.get((size_t)nsplit * 2 * N * sizeof(double2), (void**)&part))) return rc;
   DevGeom dg = wsbm_devgeom(g);
   for (int c = 0; c < nrhs && rc == WSBM_OK; ++c) {
     const double2* xc = (const double2*)x + (int64_t)c * 2 * N;
@@ -152,6 +150,5 @@ extern "C" int wsbm_matvec(const wsbm_geom* g, const wsbm_params* p, int32_t tra
     wsbm_count_launch();
     if (cudaGetLastError() != cudaSuccess) rc = WSBM_ERR_CUDA;
   }
-  cudaFreeAsync(part, st);
   return rc;
 }

@@ -227,12 +227,12 @@ extern "C" int wsbm_sketch(const void* A, int64_t lda, int32_t m, int32_t n, int
   cudaStream_t st = (cudaStream_t)stream;
   SketchDesc h;
   wsbm_sketch_desc_fill(&h, A, lda, Y, ldy, m, n, l);
+  WsbmScratch scr(st);
   SketchDesc* d = nullptr;
-  if (cudaMallocAsync((void**)&d, sizeof(h), st) != cudaSuccess) return WSBM_ERR_OOM;
-  int rc = WSBM_OK;
+  int rc = scr.get(sizeof(h), (void**)&d);
+  if (rc) return rc;
   if (cudaMemcpyAsync(d, &h, sizeof(h), cudaMemcpyHostToDevice, st) != cudaSuccess) rc = WSBM_ERR_CUDA;
   if (!rc) rc = wsbm_sketch_batched(d, 1, n, l, seed, st);
   if (!rc && cudaStreamSynchronize(st) != cudaSuccess) rc = WSBM_ERR_CUDA;  // h is on this frame
-  cudaFreeAsync(d, st);
   return rc;
 }

@@ -1,0 +1,608 @@
+// Complex128 GEMM on the tensor cores with exact split precision (tcgen05 + TMA + TMEM).
+//
+//   C (m x n) = beta C + alpha A (m x k) B (k x n),   complex128, column-major.
+//
+// GB300 runs FP64 at 2 DFMA/clk/SM against 4096 BF16 multiply-adds/clk/SM on the tensor
+// cores, so the dense contractions of the factorization (trailing updates of the blocked LU of
+// large boxes and of the dense root) are formed from exact 8-bit pieces:
+//
+//  1. Scaling.  Row i of A gets a power of two 2^e_i with |Re A_il|, |Im A_il| < 2^(e_i - 1);
+//     column j of B likewise 2^f_j.  The scaled values x (|x| < 1/2) are written as the 56-bit
+//     integer X = x 2^56 (rounded when x has bits below 2^-56), and X as seven balanced base-256
+//     digits d_0..d_6 in [-128, 128] (x = sum_t d_t 2^-8(t+1)), each exact in BF16.
+//  2. Real form of the complex product.  Row i of A becomes the real row (Re A_i0, Im A_i0,
+//     Re A_i1, Im A_i1, ...); column j of C becomes two real columns: 2j = Re C_j with B entries
+//     (Re B_lj, -Im B_lj), 2j+1 = Im C_j with (Im B_lj, Re B_lj).  K_real = 2k.
+//  3. Digit products on the tensor cores.  For every digit diagonal d = t + u <= 7 the FP32
+//     accumulator acc_d (in TMEM) collects sum A_t B_u over a chunk of 128 real K values: every
+//     product is an integer of magnitude <= 2^14 and a chunk adds at most 7 * 128 of them, so
+//     the FP32 sums are exact integers below 2^24.  Pairs with t + u >= 8 are left out: their
+//     weight is below 2^-63 of the leading term.
+//  4. Recombination without FP64 arithmetic.  After each chunk the accumulators are drained
+//     into a fixed-point sum of 2^-64 resolution: a 64-bit integer T of unit 2^-48 (digit
+//     diagonals 0..4 and the high part of 5) and a 16-bit fraction F of unit 2^-64 (the rest of
+//     5, diagonal 6, and diagonal 7 rounded), whose carries move into T after every chunk
+//     (integer and FP32 pipes only).  At the end of the K loop,
+//     C_ij = beta C_ij + alpha (T + F 2^-16) 2^(e_i + f_j - 48).
+//
+// Error: the rounding of X to 56 bits (relative to the row or column maximum) and the pairs
+// left out keep each entry of A B within about 2^-53 * 2k * max|A_i.| * max|B_.j| of the exact
+// product, the bound of an FP64 product.
+//
+// Kernel: one CTA per SM, persistent over 128 x 64 (real) output tiles.  Warp 0 issues the TMA
+// loads of the 14 digit planes of a 32-wide K block (a 2-stage ring in shared memory, 64-byte
+// swizzled rows), warp 1 allocates TMEM (8 accumulators x 64 columns) and issues the MMAs
+// (one thread), warps 2-9 drain the accumulators (two threads per TMEM lane = output row, each
+// with 32 of the 64 columns) and write C.  Every wait on a barrier is bounded in time; a wait that runs out sets an error
+// flag read by the host, and all roles then leave their loops.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <mutex>
+
+#include "dense.h"
+
+#define TC_BM 128                       // output rows per tile (= TMEM lanes)
+#define TC_BN 64                        // real output columns per tile (32 complex)
+#define TC_BK 32                        // real K values per pipeline stage (64-byte rows)
+#define TC_S 7                          // digits per operand
+#define TC_ND 8                         // digit diagonals kept (t + u <= 7)
+#define TC_STAGES 2
+#define TC_KC 128                       // real K values per exact accumulation chunk
+#define TC_A_TILE (TC_BM * TC_BK * 2)   // bytes of one A digit plane tile (8 KB)
+#define TC_B_TILE (TC_BN * TC_BK * 2)   // bytes of one B digit plane tile (4 KB)
+#define TC_STAGE_BYTES (TC_S * (TC_A_TILE + TC_B_TILE))
+#define TC_FRAC_BYTES (TC_BN * TC_BM * 4)  // fraction words F of a tile (int32, column-major)
+#define TC_SMEM (TC_STAGES * TC_STAGE_BYTES + TC_FRAC_BYTES + 256 + 1024)
+#define TC_THREADS 320                  // producer, MMA, 8 epilogue warps
+#define TC_EPI 256                      // epilogue threads (two per TMEM lane)
+#define TC_TMEM_COLS 512
+#define TC_WAIT_NS 2000000000ull        // bound of every barrier wait (2 s)
+
+static_assert(TC_STAGE_BYTES % 1024 == 0, "stage alignment");
+static_assert(TC_KC % TC_BK == 0, "chunk of whole stages");
+
+static __device__ int g_tc_error;  // set when a bounded wait ran out
+
+// ----------------------------------------------------------------- PTX helpers ----
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ uint64_t globaltimer() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count));
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Wait for the phase of parity `parity` of barrier `bar`, at most TC_WAIT_NS.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = globaltimer();
+  for (uint32_t it = 1;; ++it) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if ((it & 255) == 0) {
+      if (*(volatile int*)&g_tc_error) return false;
+      if (globaltimer() - t0 > TC_WAIT_NS) {
+        atomicExch(&g_tc_error, 1);
+        return false;
+      }
+    }
+  }
+}
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map, uint32_t bar, int c0,
+                                            int c1, int c2) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5}], [%2];" ::"r"(dst),
+      "l"((uint64_t)map), "r"(bar), "r"(c0), "r"(c1), "r"(c2)
+      : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// Shared-memory operand descriptor: K-major tile of 64-byte rows with the 64-byte swizzle
+// (atoms of 8 rows x 64 bytes, 512 bytes apart), descriptor version 1.
+__device__ __forceinline__ uint64_t sdesc_sw64(uint32_t addr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((addr >> 4) & 0x3FFF);      // start address
+  d |= (uint64_t)1 << 16;                     // leading byte offset (unused for this layout)
+  d |= (uint64_t)(512 >> 4) << 32;            // stride byte offset: 8-row groups
+  d |= (uint64_t)1 << 46;                     // version
+  d |= (uint64_t)4 << 61;                     // layout: 64-byte swizzle
+  return d;
+}
+// Instruction descriptor: BF16 x BF16 -> FP32, both operands K-major, M = 128, N = TC_BN.
+__host__ __device__ constexpr uint32_t tc_idesc() {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TC_BN >> 3) << 17) | ((uint32_t)(TC_BM >> 4) << 24);
+}
+__device__ __forceinline__ void tc_mma(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t accum) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "l"(a), "l"(b), "r"(tc_idesc()), "r"(accum));
+}
+__device__ __forceinline__ void tc_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+               : "memory");
+}
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float* v) {
+  uint32_t r[8];
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+               : "r"(taddr));
+#pragma unroll
+  for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
+}
+__device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// --------------------------------------------------------------- digit planes ----
+// Exponent e with |v| < 2^(e-1) for every |Re|, |Im| of the row/column maximum `mx` (as raw
+// bits of a non-negative double); 0 for an all-zero row.
+__device__ __forceinline__ int scale_exp(uint64_t mxbits) {
+  if (mxbits == 0) return 0;
+  const int E = (int)(mxbits >> 52);
+  return (E > 0 ? E : 1) - 1021;
+}
+__device__ __forceinline__ uint64_t abs_bits(double v) {
+  return (uint64_t)__double_as_longlong(v) & 0x7FFFFFFFFFFFFFFFull;
+}
+// The seven balanced base-256 digits of X = v 2^(56 - e) (|v| < 2^(e-1)), most significant first.
+__device__ __forceinline__ void digits7(double v, int e, int* d) {
+  const uint64_t b = (uint64_t)__double_as_longlong(v);
+  const int E = (int)((b >> 52) & 0x7FF);
+  uint64_t mant = b & 0xFFFFFFFFFFFFFull;
+  if (E) mant |= 1ull << 52;
+  const int sh = (E > 0 ? E : 1) - 1075 + 56 - e;
+  int64_t X;
+  if (mant == 0 || sh <= -64) {
+    X = 0;
+  } else if (sh >= 0) {
+    X = (int64_t)(mant << sh);  // sh <= 2: |X| < 2^55
+  } else {
+    X = (int64_t)((mant + (1ull << (-sh - 1))) >> (-sh));  // round half up
+  }
+  if (b >> 63) X = -X;
+#pragma unroll
+  for (int t = TC_S - 1; t >= 1; --t) {
+    const int dt = (int)((X + 128) & 255) - 128;
+    d[t] = dt;
+    X = (X - dt) >> 8;
+  }
+  d[0] = (int)X;
+}
+
+// Row exponents of A (m x k): one thread per row (coalesced along the column).
+__global__ void k_tc_row_exp(const double2* __restrict__ A, int64_t lda, int m, int k, int* __restrict__ rexp) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= m) return;
+  uint64_t mx = 0;
+  for (int l = 0; l < k; ++l) {
+    const double2 v = A[i + (int64_t)l * lda];
+    mx = max(mx, max(abs_bits(v.x), abs_bits(v.y)));
+  }
+  rexp[i] = scale_exp(mx);
+}
+
+// Digit planes of A: PA[t][i][2l + c] (c = 0: Re, 1: Im), rows of Ka BF16 values (zero beyond 2k).
+// Block: 32 rows x 32 complex columns, staged through shared memory so that both the reads
+// (along a column) and the writes (along a row) are contiguous.
+__global__ void __launch_bounds__(256) k_tc_split_a(const double2* __restrict__ A, int64_t lda, int m, int k,
+                                                    const int* __restrict__ rexp, __nv_bfloat16* __restrict__ PA,
+                                                    int64_t Ka) {
+  __shared__ __nv_bfloat16 s[TC_S][32][64 + 2];
+  const int i0 = blockIdx.x * 32, l0 = blockIdx.y * 32;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8
+  for (int ll = ty; ll < 32; ll += 8) {
+    const int i = i0 + tx, l = l0 + ll;
+    int dr[TC_S], di[TC_S];
+    if (i < m && l < k) {
+      const double2 v = A[i + (int64_t)l * lda];
+      const int e = rexp[i];
+      digits7(v.x, e, dr);
+      digits7(v.y, e, di);
+    } else {
+#pragma unroll
+      for (int t = 0; t < TC_S; ++t) dr[t] = di[t] = 0;
+    }
+#pragma unroll
+    for (int t = 0; t < TC_S; ++t) {
+      s[t][tx][2 * ll] = __float2bfloat16_rn((float)dr[t]);
+      s[t][tx][2 * ll + 1] = __float2bfloat16_rn((float)di[t]);
+    }
+  }
+  __syncthreads();
+  // write: for each plane and row, 64 consecutive BF16 values (columns 2 l0 .. 2 l0 + 63)
+  const int64_t plane = (int64_t)m * Ka;
+  for (int w = threadIdx.x; w < TC_S * 32 * 32; w += blockDim.x) {
+    const int t = w / (32 * 32), r = (w / 32) % 32, c2 = w % 32;  // c2: pair of BF16 values
+    const int i = i0 + r, kk = 2 * l0 + 2 * c2;
+    if (i >= m || kk >= Ka) continue;
+    __nv_bfloat162 p;
+    p.x = s[t][r][2 * c2];
+    p.y = s[t][r][2 * c2 + 1];
+    *reinterpret_cast<__nv_bfloat162*>(PA + t * plane + (int64_t)i * Ka + kk) = p;
+  }
+}
+
+// Column exponents of B (k x n): one warp per column.
+__global__ void k_tc_col_exp(const double2* __restrict__ B, int64_t ldb, int k, int n, int* __restrict__ cexp) {
+  const int j = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32, lane = threadIdx.x & 31;
+  if (j >= n) return;
+  uint64_t mx = 0;
+  for (int l = lane; l < k; l += 32) {
+    const double2 v = B[l + (int64_t)j * ldb];
+    mx = max(mx, max(abs_bits(v.x), abs_bits(v.y)));
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long other = __shfl_xor_sync(0xFFFFFFFFu, (unsigned long long)mx, o);
+    mx = max(mx, (uint64_t)other);
+  }
+  if (lane == 0) cexp[j] = scale_exp(mx);
+}
+
+// Digit planes of the real form of B: PB[u][2j][2l] = Re B_lj, PB[u][2j][2l+1] = -Im B_lj,
+// PB[u][2j+1][2l] = Im B_lj, PB[u][2j+1][2l+1] = Re B_lj (digits of; zero beyond 2k).
+// One thread per (l, j): reads along the column, writes along the rows.
+__global__ void __launch_bounds__(256) k_tc_split_b(const double2* __restrict__ B, int64_t ldb, int k, int n,
+                                                    const int* __restrict__ cexp, __nv_bfloat16* __restrict__ PB,
+                                                    int64_t Ka) {
+  const int j = blockIdx.x;
+  const int64_t plane = (int64_t)2 * n * Ka;
+  const int e = cexp[j];
+  for (int l = blockIdx.y * blockDim.x + threadIdx.x; 2 * l < Ka; l += gridDim.y * blockDim.x) {
+    int dr[TC_S], di[TC_S];
+    if (l < k) {
+      const double2 v = B[l + (int64_t)j * ldb];
+      digits7(v.x, e, dr);
+      digits7(v.y, e, di);
+    } else {
+#pragma unroll
+      for (int t = 0; t < TC_S; ++t) dr[t] = di[t] = 0;
+    }
+#pragma unroll
+    for (int u = 0; u < TC_S; ++u) {
+      __nv_bfloat162 re, im;
+      re.x = __float2bfloat16_rn((float)dr[u]);
+      re.y = __float2bfloat16_rn((float)-di[u]);
+      im.x = __float2bfloat16_rn((float)di[u]);
+      im.y = __float2bfloat16_rn((float)dr[u]);
+      __nv_bfloat16* row = PB + u * plane + (int64_t)(2 * j) * Ka + 2 * l;
+      *reinterpret_cast<__nv_bfloat162*>(row) = re;
+      *reinterpret_cast<__nv_bfloat162*>(row + Ka) = im;
+    }
+  }
+}
+
+// ------------------------------------------------------------------ the GEMM ----
+struct TcArgs {
+  int m, n, k;          // complex sizes
+  int tiles_m, tiles_n; // 128-row and 64-real-column tiles
+  int nkb;              // K blocks of TC_BK real values
+  double2 alpha, beta;
+  double2* C;
+  int64_t ldc;
+  const int* rexp;
+  const int* cexp;
+};
+
+// Tile t -> (tm, tn): groups of 8 row tiles, so that the CTAs running at the same time share
+// their A and B digit planes in L2.
+__device__ __forceinline__ void tile_coords(const TcArgs& a, int t, int& tm, int& tn) {
+  const int G = 8;
+  const int per_group = G * a.tiles_n;
+  const int g = t / per_group, r = t % per_group;
+  const int gm = min(G, a.tiles_m - g * G);
+  tm = g * G + r % gm;
+  tn = r / gm;
+}
+
+__global__ void __launch_bounds__(TC_THREADS, 1)
+    k_zgemm_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, const TcArgs a) {
+  extern __shared__ unsigned char smem_raw[];
+  const uint32_t raw = smem_u32(smem_raw);
+  const uint32_t base = (raw + 1023u) & ~1023u;
+  unsigned char* gbase = smem_raw + (base - raw);
+  int* frac = reinterpret_cast<int*>(gbase + TC_STAGES * TC_STAGE_BYTES);  // F[col][row]
+  const uint32_t bars = base + TC_STAGES * TC_STAGE_BYTES + TC_FRAC_BYTES;  // full[S], empty[S], tfull, tempty
+  const uint32_t full0 = bars, empty0 = bars + 8 * TC_STAGES, tfull = bars + 16 * TC_STAGES,
+                 tempty = tfull + 8;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(gbase + TC_STAGES * TC_STAGE_BYTES + TC_FRAC_BYTES + 128);
+  const int warp = threadIdx.x / 32, lane = threadIdx.x & 31;
+  const int ntiles = a.tiles_m * a.tiles_n;
+  const int nchunk_kb = TC_KC / TC_BK;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < TC_STAGES; ++s) {
+      mbar_init(full0 + 8 * s, 1);
+      mbar_init(empty0 + 8 * s, 1);
+    }
+    mbar_init(tfull, 1);
+    mbar_init(tempty, TC_EPI);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(TC_TMEM_COLS));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0) {
+    // ---------------------------------------------------------------- TMA producer
+    if (lane == 0) {
+      uint32_t it = 0;
+      bool ok = true;
+      for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+        int tm, tn;
+        tile_coords(a, t, tm, tn);
+        for (int kb = 0; kb < a.nkb && ok; ++kb, ++it) {
+          const uint32_t s = it % TC_STAGES, ph = (it / TC_STAGES) & 1;
+          if (!(ok = mbar_wait(empty0 + 8 * s, ph ^ 1))) break;
+          const uint32_t full = full0 + 8 * s;
+          mbar_expect_tx(full, TC_STAGE_BYTES);
+          const uint32_t sa = base + s * TC_STAGE_BYTES, sb = sa + TC_S * TC_A_TILE;
+#pragma unroll
+          for (int p = 0; p < TC_S; ++p) {
+            tma_load_3d(sa + p * TC_A_TILE, &mapA, full, kb * TC_BK, tm * TC_BM, p);
+            tma_load_3d(sb + p * TC_B_TILE, &mapB, full, kb * TC_BK, tn * TC_BN, p);
+          }
+        }
+      }
+      // every load issued must have landed before the CTA can leave: wait (bounded) for the
+      // last fill of each stage (no later phase of that barrier exists)
+      for (uint32_t s = 0; s < TC_STAGES; ++s) {
+        if (it <= s) continue;
+        const uint32_t last = s + ((it - 1 - s) / TC_STAGES) * TC_STAGES;
+        mbar_wait(full0 + 8 * s, (last / TC_STAGES) & 1);
+      }
+    }
+  } else if (warp == 1) {
+    // ---------------------------------------------------------------- MMA issuer
+    if (lane == 0) {
+      uint32_t it = 0, chunk = 0;
+      bool ok = true;
+      for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+        for (int kb0 = 0; kb0 < a.nkb && ok; kb0 += nchunk_kb, ++chunk) {
+          if (!(ok = mbar_wait(tempty, (chunk & 1) ^ 1))) break;
+          tc_fence_after();
+          const int kb1 = min(a.nkb, kb0 + nchunk_kb);
+          for (int kb = kb0; kb < kb1; ++kb, ++it) {
+            const uint32_t s = it % TC_STAGES, ph = (it / TC_STAGES) & 1;
+            if (!(ok = mbar_wait(full0 + 8 * s, ph))) break;
+            tc_fence_after();
+            const uint32_t sa = base + s * TC_STAGE_BYTES, sb = sa + TC_S * TC_A_TILE;
+#pragma unroll
+            for (int d = 0; d < TC_ND; ++d) {
+              const int t0 = d > TC_S - 1 ? d - (TC_S - 1) : 0;
+#pragma unroll
+              for (int tt = t0; tt <= d && tt < TC_S; ++tt) {
+                const uint64_t da = sdesc_sw64(sa + tt * TC_A_TILE);
+                const uint64_t db = sdesc_sw64(sb + (d - tt) * TC_B_TILE);
+#pragma unroll
+                for (int kk = 0; kk < TC_BK / 16; ++kk) {
+                  const uint32_t acc = (kb > kb0 || tt > t0 || kk > 0) ? 1u : 0u;
+                  // K step of 16 BF16 values = 32 bytes = 2 units of the start address
+                  tc_mma(tmem + d * TC_BN, da + 2 * kk, db + 2 * kk, acc);
+                }
+              }
+            }
+            tc_commit(empty0 + 8 * s);  // the stage is free once these MMAs have read it
+          }
+          if (ok) tc_commit(tfull);  // the chunk's accumulators are complete
+        }
+      }
+    }
+  } else {
+    // ---------------------------------------------------------------- epilogue (warps 2-9)
+    const int q = warp & 3;              // TMEM lane quadrant of this warp
+    const int half = (warp - 2) / 4;     // which 32 of the tile's 64 real columns
+    const int row = q * 32 + lane;       // output row within the tile
+    const uint32_t tq = tmem + ((uint32_t)(q * 32) << 16) + half * (TC_BN / 2);
+    uint32_t chunk = 0;
+    bool ok = true;
+    for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+      int tm, tn;
+      tile_coords(a, t, tm, tn);
+      long long T[TC_BN / 2];
+#pragma unroll
+      for (int c = 0; c < TC_BN / 2; ++c) {
+        T[c] = 0;
+        frac[(half * (TC_BN / 2) + c) * TC_BM + row] = 0;
+      }
+      for (int kb0 = 0; kb0 < a.nkb; kb0 += nchunk_kb, ++chunk) {
+        if (!(ok = mbar_wait(tfull, chunk & 1))) break;
+        tc_fence_after();
+#pragma unroll
+        for (int g = 0; g < TC_BN / 16; ++g) {
+          // diagonals in pairs, converted as they arrive (fewer live registers)
+          float v0[8], v1[8];
+          int p1[8], p2[8], p3[8], f5[8];
+          tmem_ld8(tq + 0 * TC_BN + g * 8, v0);
+          tmem_ld8(tq + 1 * TC_BN + g * 8, v1);
+          tmem_ld_wait();
+#pragma unroll
+          for (int c = 0; c < 8; ++c) p1[c] = __float2int_rn(v0[c]) * 256 + __float2int_rn(v1[c]);
+          tmem_ld8(tq + 2 * TC_BN + g * 8, v0);
+          tmem_ld8(tq + 3 * TC_BN + g * 8, v1);
+          tmem_ld_wait();
+#pragma unroll
+          for (int c = 0; c < 8; ++c) p2[c] = __float2int_rn(v0[c]) * 256 + __float2int_rn(v1[c]);
+          tmem_ld8(tq + 4 * TC_BN + g * 8, v0);
+          tmem_ld8(tq + 5 * TC_BN + g * 8, v1);
+          tmem_ld_wait();
+#pragma unroll
+          for (int c = 0; c < 8; ++c) {
+            const int i5 = __float2int_rn(v1[c]);
+            p3[c] = __float2int_rn(v0[c]) + (i5 >> 8);  // unit 2^-48
+            f5[c] = (i5 & 255) << 8;                     // unit 2^-64
+          }
+          tmem_ld8(tq + 6 * TC_BN + g * 8, v0);
+          tmem_ld8(tq + 7 * TC_BN + g * 8, v1);
+          tmem_ld_wait();
+#pragma unroll
+          for (int c = 0; c < 8; ++c) {
+            const int col = half * (TC_BN / 2) + g * 8 + c;
+            int* fp = frac + col * TC_BM + row;
+            const int fn = *fp + f5[c] + __float2int_rn(v0[c]) + __float2int_rn(v1[c] * (1.0f / 256.0f));
+            *fp = fn & 0xFFFF;
+            T[g * 8 + c] += ((long long)p1[c] << 24) + ((long long)p2[c] << 8) + (long long)p3[c] + (fn >> 16);
+          }
+        }
+        tc_fence_before();
+        mbar_arrive(tempty);
+      }
+      if (!ok) break;
+      // C = beta C + alpha T 2^(e_i + f_j - 48)
+      const int i = tm * TC_BM + row;
+      if (i < a.m) {
+        const int ei = a.rexp[i];
+#pragma unroll
+        for (int c = 0; c < TC_BN / 4; ++c) {
+          const int j = tn * (TC_BN / 2) + half * (TC_BN / 4) + c;
+          if (j >= a.n) continue;
+          const double sc = ldexp(1.0, ei + a.cexp[j] - 48);
+          const int* fp = frac + (half * (TC_BN / 2) + 2 * c) * TC_BM + row;
+          const double xr = fma((double)fp[0], 1.0 / 65536.0, (double)T[2 * c]) * sc;
+          const double xi = fma((double)fp[TC_BM], 1.0 / 65536.0, (double)T[2 * c + 1]) * sc;
+          double2* p = a.C + i + (int64_t)j * a.ldc;
+          double2 r = make_double2(a.alpha.x * xr - a.alpha.y * xi, a.alpha.x * xi + a.alpha.y * xr);
+          if (a.beta.x != 0.0 || a.beta.y != 0.0) {
+            const double2 o = *p;
+            r.x += a.beta.x * o.x - a.beta.y * o.y;
+            r.y += a.beta.x * o.y + a.beta.y * o.x;
+          }
+          *p = r;
+        }
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_TMEM_COLS));
+  }
+}
+
+// -------------------------------------------------------------------- host side ----
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn encode_fn() {
+  static std::once_flag once;
+  static EncodeTiledFn fn = nullptr;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (EncodeTiledFn)p;
+  });
+  return fn;
+}
+
+static int64_t tc_ka(int k) { return ((int64_t)2 * k + TC_BK - 1) / TC_BK * TC_BK; }
+
+size_t wsbm_zgemm_tc_ws_bytes(int m, int n, int k) {
+  const int64_t Ka = tc_ka(k);
+  size_t b = (size_t)TC_S * ((size_t)m + 2 * (size_t)n) * Ka * 2;  // digit planes
+  b = (b + 255) & ~(size_t)255;
+  b += ((size_t)m + n) * sizeof(int) + 256;  // exponents
+  return b;
+}
+
+// 3-D map over the digit planes [TC_S][rows][Ka] with boxes of TC_BK x box_rows x 1.
+static int make_map(CUtensorMap* map, void* planes, int64_t rows, int64_t Ka, int box_rows) {
+  EncodeTiledFn enc = encode_fn();
+  if (!enc) return -3;
+  cuuint64_t dims[3] = {(cuuint64_t)Ka, (cuuint64_t)rows, (cuuint64_t)TC_S};
+  cuuint64_t strides[2] = {(cuuint64_t)Ka * 2, (cuuint64_t)rows * Ka * 2};
+  cuuint32_t box[3] = {TC_BK, (cuuint32_t)box_rows, 1};
+  cuuint32_t es[3] = {1, 1, 1};
+  CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, planes, dims, strides, box, es,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? 0 : -3;
+}
+
+int wsbm_zgemm_tc(int m, int n, int k, double2 alpha, const double2* A, int64_t lda, const double2* B,
+                  int64_t ldb, double2 beta, double2* C, int64_t ldc, void* ws, cudaStream_t st) {
+  if (m < 0 || n < 0 || k < 0) return -1;
+  if (m == 0 || n == 0) return 0;
+  if (k < 1 || k > 32768) return -1;  // the 64-bit recombination is sized for K_real <= 65536
+  if (!A || !B || !C || !ws || lda < m || ldb < k || ldc < m) return -1;
+  if (((uintptr_t)ws & 255) != 0) return -1;
+  const int64_t Ka = tc_ka(k);
+  __nv_bfloat16* PA = (__nv_bfloat16*)ws;
+  __nv_bfloat16* PB = PA + (size_t)TC_S * m * Ka;
+  size_t off = ((size_t)TC_S * ((size_t)m + 2 * (size_t)n) * Ka * 2 + 255) & ~(size_t)255;
+  int* rexp = (int*)((char*)ws + off);
+  int* cexp = rexp + m;
+  // digit planes (k = 0: all-zero planes, C = beta C)
+  k_tc_row_exp<<<(m + 127) / 128, 128, 0, st>>>(A, lda, m, k, rexp);
+  k_tc_split_a<<<dim3((m + 31) / 32, (unsigned)((Ka / 2 + 31) / 32)), 256, 0, st>>>(A, lda, m, k, rexp, PA, Ka);
+  k_tc_col_exp<<<(n + 7) / 8, 256, 0, st>>>(B, ldb, k, n, cexp);
+  k_tc_split_b<<<dim3(n, (unsigned)((Ka / 2 + 255) / 256)), 256, 0, st>>>(B, ldb, k, n, cexp, PB, Ka);
+  wsbm_count_launches(4);
+  CUtensorMap ma, mb;
+  if (make_map(&ma, PA, m, Ka, TC_BM) || make_map(&mb, PB, 2 * (int64_t)n, Ka, TC_BN)) return -3;
+  TcArgs a;
+  a.m = m;
+  a.n = n;
+  a.k = k;
+  a.tiles_m = (m + TC_BM - 1) / TC_BM;
+  a.tiles_n = (2 * n + TC_BN - 1) / TC_BN;
+  a.nkb = (int)(Ka / TC_BK);
+  a.alpha = alpha;
+  a.beta = beta;
+  a.C = C;
+  a.ldc = ldc;
+  a.rexp = rexp;
+  a.cexp = cexp;
+  if (wsbm_smem_optin((const void*)k_zgemm_tc, TC_SMEM) != cudaSuccess) return -3;
+  const int ntiles = a.tiles_m * a.tiles_n;
+  const int grid = ntiles < wsbm_sm_count() ? ntiles : wsbm_sm_count();
+  k_zgemm_tc<<<grid, TC_THREADS, TC_SMEM, st>>>(ma, mb, a);
+  wsbm_count_launch();
+  return cudaGetLastError() == cudaSuccess ? 0 : -3;
+}
+
+// Error flag of the bounded waits: returns it and clears it (synchronizes the stream).
+int wsbm_zgemm_tc_status(cudaStream_t st) {
+  if (cudaStreamSynchronize(st) != cudaSuccess) return -3;
+  int v = 0;
+  if (cudaMemcpyFromSymbol(&v, g_tc_error, sizeof(int)) != cudaSuccess) return -3;
+  if (v) {
+    const int zero = 0;
+    cudaMemcpyToSymbol(g_tc_error, &zero, sizeof(int));
+    return -5;
+  }
+  return 0;
+}

@@ -3,6 +3,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 #include "../../include/wsbm_hss.h"
 #include "dense.h"
 
@@ -90,3 +92,33 @@ int wsbm_sketch_batched(const void* d_desc, int ndesc, int max_n, int max_l, uin
 size_t wsbm_sketch_desc_size();
 void wsbm_sketch_desc_fill(void* slot, const void* A, int64_t lda, void* Y, int64_t ldy, int32_t m,
                            int32_t n, int32_t l);
+
+// capi.cu: device memory of the library.  Every allocation goes through the allocator set by
+// wsbm_set_allocator (a handle captures it at creation; the stateless calls read it at each
+// call), else through the library's memory pool of the current device.  Both are stream
+// ordered on the call's stream.
+struct WsbmAllocator {
+  wsbm_alloc_fn alloc = nullptr;
+  wsbm_free_fn release = nullptr;
+  void* ctx = nullptr;
+};
+WsbmAllocator wsbm_current_allocator();
+int wsbm_dev_alloc(const WsbmAllocator& a, size_t bytes, cudaStream_t st, void** p);
+void wsbm_dev_free(const WsbmAllocator& a, void* p, cudaStream_t st);
+
+// Work space of one stateless call, released in stream order when it goes out of scope (also
+// on an early error return).
+struct WsbmScratch {
+  WsbmAllocator a;
+  cudaStream_t st;
+  std::vector<void*> v;
+  explicit WsbmScratch(cudaStream_t s) : a(wsbm_current_allocator()), st(s) {}
+  ~WsbmScratch() {
+    for (void* p : v) wsbm_dev_free(a, p, st);
+  }
+  int get(size_t bytes, void** p) {
+    int rc = wsbm_dev_alloc(a, bytes, st, p);
+    if (rc == WSBM_OK) v.push_back(*p);
+    return rc;
+  }
+};

@@ -89,3 +89,27 @@ def test_batch_solve_equals_individual_solves_and_replays():
             u, q = b.solver(i).solve(rhs[i])
             assert torch.equal(got[i][0], u) and torch.equal(got[i][1], q), (call, i)
     b.close()
+
+
+def test_batch_solve_after_member_refactor():
+    """Re-factoring one member of a batch on its own (wsbm_factor on the handle the batch hands
+    out) releases the factors that the batch's cached solve plan points into; the next batch
+    solve must build a new plan and still equal the per-curve solves."""
+    import torch
+    from paper_2607_00790_gb300 import binding
+    ms = members()[:3]
+    geoms = [binding.make_geom(c) for c, _ in ms]
+    b = binding.Batch([g for g, _ in geoms], [params(binding, d) for _, d in ms])
+    b.factor()
+    rng = np.random.default_rng(9)
+    rhs = [torch.as_tensor(rng.normal(size=(2 * g.n, 2)) + 1j * rng.normal(size=(2 * g.n, 2)),
+                           device="cuda") for g, _ in geoms]
+    first = b.solve(rhs)
+    b.solver(1).factor()
+    torch.cuda.synchronize()
+    again = b.solve(rhs)
+    for i in range(len(ms)):
+        u, q = b.solver(i).solve(rhs[i])
+        assert torch.equal(again[i][0], u) and torch.equal(again[i][1], q), i
+        assert torch.equal(again[i][0], first[i][0]), i
+    b.close()

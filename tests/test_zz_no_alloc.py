@@ -66,3 +66,27 @@ def test_noalloc_rejects_oversized_request():
     one = torch.zeros(1, dtype=torch.int64, device="cuda")
     rc, _ = noalloc_entries(g, p, big, one)
     assert rc == -1
+
+
+def test_noalloc_at_the_scratch_limit():
+    """nr + nc equal to WSBM_NOALLOC_MAX_INDICES (65536), split unevenly (65000 rows, 536
+    columns), fills the scratch array to its end: the row and column slot lists must not overlap
+    and must match wsbm_entries_raw; one index more is refused with INVALID_ARG."""
+    import torch
+    from paper_2607_00790_gb300 import binding
+    c = inputs.star(40000)
+    ph = oracle.Physics(inputs.k0_for_density(c), n=1.5)
+    g, keep = binding.make_geom(c)
+    p = binding.make_params(ph.k0, 1.5)
+    rng = np.random.default_rng(23)
+    rows = torch.tensor(rng.choice(80000, 65000, replace=False), device="cuda")
+    cols = torch.tensor(rng.choice(80000, 536, replace=False), device="cuda")
+    for _ in range(2):
+        rc, got = noalloc_entries(g, p, rows, cols)
+        assert rc == 0
+        ref = binding.wsbm_entries_raw(g, p, rows, cols)
+        torch.cuda.synchronize()
+        assert torch.linalg.norm(got - ref).item() <= TOL * torch.linalg.norm(ref).item()
+        assert (got - ref).abs().max().item() <= TOL * ref.abs().max().item()
+    rc, _ = noalloc_entries(g, p, rows, torch.cat([cols, cols[:1]]))
+    assert rc == -1
