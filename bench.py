@@ -31,8 +31,8 @@ METRIC = "HSS build+factor s and kernel entries/s at N=2^18, FP64 vs mixed, at s
 UNIT = "entries/s"
 
 # Per-pair FP64 operation counts and DRAM bytes of the entry kernels, read from ncu counters
-# (profiles/entry_kernels_ncu.md) for the kernel sources with the recorded hash; when the
-# sources change the traffic figure is withheld until re-measured.
+# for the kernel sources with the recorded hash; when the sources change the traffic figure is
+# withheld until re-measured.
 KERNEL_COUNTS = {
     "src_sha": "0b66cd3acb2ca2d7",
     "k_proxy": {"fp64_flops_per_pair": 333.1, "dram_bytes_per_pair": 63.5},
@@ -47,6 +47,30 @@ KERNEL_COUNTS = {
 }
 # FP64 peak from the unit counts: 152 SMs x 4 FP64 flops/clk/SM (2 DFMA) x 2.07 GHz.
 FP64_PEAK_TFLOPS = 152 * 4 * 2.07e9 / 1e12
+# A DFMA microbenchmark (every SM, dependent chains, CUDA events) reached 1.013 TFLOP/s at an
+# SM clock of 2.0 GHz; it scales with the clock.
+FP64_DFMA_MEASURED = (1.013, 2000.0)
+
+
+def measured_peaks():
+    """The measured peaks of this GPU pool (HBM copy, cuBLAS BF16), when present."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh)
+    except (OSError, ValueError):
+        return {}
+
+
+def add_fracs(roof, clk):
+    """frac against the unit-count FP64 peak (roof['frac']) and against the measured DFMA rate
+    scaled to the median SM clock sampled during the timed region."""
+    if not roof or roof.get("achieved") is None:
+        return roof
+    mhz = (clk or {}).get("sm_mhz") or FP64_DFMA_MEASURED[1]
+    peak_m = FP64_DFMA_MEASURED[0] * mhz / FP64_DFMA_MEASURED[1]
+    roof["peak_measured_dfma"] = peak_m
+    roof["frac_of_measured_dfma"] = roof["achieved"] / peak_m
+    return roof
 
 
 def _dense_section(begin, end):
@@ -277,6 +301,8 @@ def run_ours(args, ws, rank, local):
             "peak_note": "FP64 pipe: 152 SMs x 2 DFMA/clk x 2.07 GHz (unit counts); a DFMA "
                          "microbenchmark reached 1.013 TFLOP/s",
             "counts_fresh": fresh}
+    for r in (roof_main, roof_other, roof):
+        add_fracs(r, clk)
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms_region_max / args.steps,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
@@ -307,9 +333,13 @@ def run_ours(args, ws, rank, local):
 
 def run_e2e(args, curve, cfg, dev, params):
     """Same metric through the C ABI with the curve in pinned host memory: every step copies
-    the geometry host -> device, builds, and reads the counters back."""
+    the geometry host -> device, builds the leaf level and reads its result (the ranks and the
+    QR permutations that give the skeletons, which wsbm_factor reads back to the host; then the
+    skeleton lists through wsbm_box_skeletons).  Beside it, the user pipeline of the full HSS on
+    the 16384-node star: geometry and angles in, create, factor, plane-wave right-hand sides,
+    solve, far field, far field out."""
     import torch
-    from paper_2607_00790_gb300 import binding
+    from paper_2607_00790_gb300 import binding, inputs
 
     host = {k: torch.as_tensor(curve[k], dtype=torch.float64).pin_memory()
             for k in ("x", "y", "nx", "ny", "w", "kappa")}
@@ -320,23 +350,69 @@ def run_e2e(args, curve, cfg, dev, params):
     stream = torch.cuda.current_stream(dev)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    entries = 0
+    entries, d2h = 0, 0
     e0.record(stream)
     for _ in range(steps):
         for k in host:
             devt[k].copy_(host[k], non_blocking=True)
         s = binding.Solver(g, p, device=dev)
         s.factor()
-        entries += s.stats()["entries_generated"]
+        st = s.stats()
+        entries += st["entries_generated"]
+        L, nb = st["levels"], st["nboxes_leaf"]
+        ks = 0
+        for b in range(nb):
+            jr, jc = s.skeletons(L, b, cap=512)
+            ks += jr.size
         s.close()
+        # read back inside wsbm_factor: QR state (4 int32 per box) and the row and column
+        # permutations of every box's candidates (2 x 2N int32)
+        d2h += 16 * nb + 2 * 2 * curve["x"].size * 4
     e1.record(stream)
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1)
     h2d = sum(v.numel() * 8 for v in host.values())
-    return {"value": entries / (ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d,
-            "d2h_bytes_per_step": 0, "steps": steps,
-            "note": "H2D of the curve from pinned memory, create, leaf-level build incl. ID and "
-                    "factor; the factors stay resident in HBM, counters are host-side"}
+    out = {"value": entries / (ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+           "d2h_bytes_per_step": d2h // steps, "steps": steps,
+           "note": "H2D of the curve from pinned memory, create, leaf-level build incl. ID and factor, "
+                   "D2H of the ranks and QR permutations (skeletons, read by wsbm_factor) and the "
+                   "skeleton lists through wsbm_box_skeletons; the factors stay resident in HBM"}
+    # the user pipeline on the star workload (full HSS): in -> factor -> solve -> far field -> out
+    c16 = inputs.star(16384)
+    h16 = {k: torch.as_tensor(c16[k], dtype=torch.float64).pin_memory()
+           for k in ("x", "y", "nx", "ny", "w", "kappa")}
+    d16 = {k: torch.empty_like(v, device=dev) for k, v in h16.items()}
+    g16 = binding.Geom(16384, *[d16[k].data_ptr() for k in ("x", "y", "nx", "ny", "w", "kappa")])
+    p16 = binding.make_params(float(inputs.k0_for_density(c16)), 1.5, leaf=128, nproxy=128, id_tol=1e-8)
+    ang_h = torch.tensor(2 * np.pi * np.arange(8) / 8, dtype=torch.float64).pin_memory()
+    obs_h = torch.tensor(2 * np.pi * np.arange(360) / 360, dtype=torch.float64).pin_memory()
+    ff_h = torch.empty((360, 8), dtype=torch.complex128).pin_memory()
+
+    def pipeline():
+        for k in h16:
+            d16[k].copy_(h16[k], non_blocking=True)
+        ang = ang_h.to(dev, non_blocking=True)
+        obs = obs_h.to(dev, non_blocking=True)
+        s = binding.Solver(g16, p16, device=dev)
+        s.factor()
+        n_ent = s.stats()["entries_generated"]
+        u, q = s.solve(s.rhs_planewave(ang))
+        ff_h.copy_(s.farfield(u, q, obs), non_blocking=True)
+        torch.cuda.synchronize()
+        s.close()
+        return n_ent
+
+    pipeline()  # warm-up
+    t = time.time()
+    n_ent = pipeline()
+    wall = time.time() - t
+    out["pipeline_star16384_full"] = {
+        "seconds": wall, "entries_per_s": n_ent / wall,
+        "h2d_bytes": sum(v.numel() * 8 for v in h16.values()) + (8 + 360) * 8,
+        "d2h_bytes": ff_h.numel() * 16,
+        "steps": "H2D curve and angles, wsbm_create, wsbm_factor (full HSS), wsbm_rhs_planewave, "
+                 "wsbm_solve (8 plane waves), wsbm_farfield (360 angles), D2H far field"}
+    return out
 
 
 # --------------------------------------------------------------------- CPU oracle ----
@@ -355,7 +431,7 @@ def oracle_sample(curve, cfg, budget_s):
     rng = np.random.default_rng(11)
     entries, boxes = 0, 0
     t0 = time.time()
-    cut = cfg["tol"] / 4.0
+    cut = cfg["tol"] / (4.0 * np.sqrt(nb))  # the library's QR cutoff for 2^L leaf boxes
     while True:
         b = int(rng.integers(0, nb))
         lo, hi = b * N // nb, (b + 1) * N // nb
@@ -383,6 +459,25 @@ def oracle_sample(curve, cfg, budget_s):
     return entries, el, boxes
 
 
+def cpu_model():
+    """CPU model of this host (lscpu, else /proc/cpuinfo)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        with open("/proc/cpuinfo") as fh:
+            for line in fh:
+                if line.lower().startswith(("model name", "cpu part")):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
+
+
 def cores():
     try:
         return int(os.environ.get("OMP_NUM_THREADS") or len(os.sched_getaffinity(0)))
@@ -392,7 +487,8 @@ def cores():
 
 def run_cpu_baseline(curve, cfg, budget_s):
     entries, el, boxes = oracle_sample(curve, cfg, budget_s)
-    return {"value": entries / el, "unit": UNIT, "cores": cores(), "kind": "oracle",
+    return {"value": entries / el, "unit": UNIT, "cores": cores(), "cpu_model": cpu_model(),
+            "kind": "oracle",
             "sample": f"{boxes} random leaf boxes of the N=262144 build: diagonal, near and proxy "
                       f"blocks ({entries} entries, {el:.1f} s; long-double libstdc++ Hankel, OpenMP)"}
 
@@ -415,7 +511,8 @@ def run_reference(args, ws, rank):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": tot_t / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {k: cfg[k] for k in ("workload", "N", "k0", "n", "leaf", "nproxy", "tol")},
-            "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores(), "kind": "oracle",
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores(), "cpu_model": cpu_model(),
+                             "kind": "oracle",
                              "sample": f"one random leaf box of the build per step ({tot_b} boxes)"},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
@@ -427,6 +524,9 @@ def run_extras(curve, cfg, dev, params):
     from paper_2607_00790_gb300 import binding, inputs
 
     out = {}
+    # the whole build + factor at N = 2^18 (the metric's build+factor seconds), first
+    out["full_2p18_fp64_tol1e-8"] = run_full_2p18(dev)
+    out["roofline_tc_gemm"] = run_tc_gemm(dev)
     g, keep = binding.make_geom(curve, device=dev)
 
     def build(gg, p):
@@ -552,6 +652,111 @@ def run_extras(curve, cfg, dev, params):
     out["adjoint_fourier_32768"] = run_adjoint(dev, fd=("a8", "n"))
     out["batched_solve_16_scatterers_256_rhs"] = run_batched_solve(dev)
     return out
+
+
+def run_full_2p18(dev, precision=0, tol=1e-8, rows=256):
+    """The whole HSS build + factor at the bench workload (N = 2^18, 15 nodes per wavelength):
+    every level compressed while the one-CTA QR takes its boxes, then the dense root factored by
+    the LU whose trailing updates run on the tensor cores.  Accuracy: the relative residual on
+    `rows` random equations (entries from wsbm_entries, which matches the oracle to 1e-12), and
+    the far-field change under one step of iterative refinement with the dense matrix-free
+    product (the far-field error of the HSS solution, to within the refined error)."""
+    import torch
+    from paper_2607_00790_gb300 import binding, inputs
+    curve, cfg = workload()
+    N = cfg["N"]
+    g, keep = binding.make_geom(curve, device=dev)
+    p = binding.make_params(cfg["k0"], cfg["n"], leaf=cfg["leaf"], nproxy=cfg["nproxy"], id_tol=tol,
+                            precision=precision, root_cap=200000)
+    binding.trim_memory()
+    s = binding.Solver(g, p, device=dev)
+    t = time.time()
+    s.factor()
+    torch.cuda.synchronize()
+    wall = time.time() - t
+    st = s.stats()
+    ang = torch.tensor(2 * np.pi * np.arange(8) / 8, device=dev)
+    obs = torch.tensor(2 * np.pi * np.arange(360) / 360, device=dev)
+    t = time.time()
+    rhs = s.rhs_planewave(ang)
+    u, q = s.solve(rhs)
+    ff = s.farfield(u, q, obs)
+    torch.cuda.synchronize()
+    t_solve = time.time() - t
+    # residual on random equations
+    rng = np.random.default_rng(17)
+    ridx = torch.tensor(np.sort(rng.choice(2 * N, rows, replace=False)), device=dev)
+    cols = torch.arange(2 * N, device=dev)
+    x = torch.cat([u, q], dim=0)
+    Arows = s.entries(ridx, cols)
+    r = Arows @ x - rhs[ridx]
+    res_rows = (torch.linalg.norm(r) / torch.linalg.norm(rhs[ridx])).item()
+    # one refinement step: r = b - A x (matrix-free), x1 = x + HSS^-1 r
+    t = time.time()
+    rfull = rhs - binding.wsbm_matvec(g, p, x)
+    res_full = (torch.linalg.norm(rfull) / torch.linalg.norm(rhs)).item()
+    du, dq = s.solve(rfull)
+    ff1 = s.farfield(u + du, q + dq, obs)
+    torch.cuda.synchronize()
+    t_ref = time.time() - t
+    ff_err = (torch.linalg.norm(ff - ff1) / torch.linalg.norm(ff1)).item()
+    u_err = (torch.linalg.norm(du) / torch.linalg.norm(u + du)).item()
+    out = {"build_factor_s": st["ms_total_factor"] / 1e3, "wall_s": wall,
+           "ms_entries": st["ms_entries"], "ms_id": st["ms_id"], "ms_factor": st["ms_factor"],
+           "root_size": st["root_size"], "rank_per_level": st["rank_per_level"],
+           "factor_bytes": st["factor_bytes"], "entries": st["entries_generated"],
+           "entries_per_s": st["entries_generated"] / (st["ms_entries"] * 1e-3),
+           "solve_8rhs_farfield_s": t_solve, "id_tol": tol, "precision": precision,
+           "residual_rel_full": res_full, "residual_rel_sampled_rows": res_rows,
+           "farfield_rel_err_vs_one_refinement_step": ff_err, "density_rel_correction": u_err,
+           "refinement_step_s": t_ref}
+    s.close()
+    binding.trim_memory()
+    return out
+
+
+def run_tc_gemm(dev, m=16384, n=16384, k=128, reps=5):
+    """Roofline of the tensor-core complex GEMM (the trailing update of the root LU): device
+    time on its stream over `reps` calls; executed tensor work 272 flops per complex
+    multiply-add (34 digit pairs x 4 real products x 2), against the measured BF16 peak."""
+    import ctypes
+
+    import torch
+    from paper_2607_00790_gb300 import binding
+    A = torch.randn(k, m, dtype=torch.complex128, device=dev)  # column-major m x k
+    B = torch.randn(n, k, dtype=torch.complex128, device=dev)  # column-major k x n
+    C = torch.zeros(n, m, dtype=torch.complex128, device=dev)
+    al = (ctypes.c_double * 2)(-1.0, 0.0)
+    be = (ctypes.c_double * 2)(1.0, 0.0)
+    L = binding.lib()
+    st = torch.cuda.current_stream(dev)
+
+    def call():
+        rc = L.wsbm_zgemm(m, n, k, al, ctypes.c_void_p(A.data_ptr()), m, ctypes.c_void_p(B.data_ptr()), k,
+                          be, ctypes.c_void_p(C.data_ptr()), m, ctypes.c_void_p(st.cuda_stream))
+        if rc != 0:
+            raise RuntimeError(f"wsbm_zgemm: {rc}")
+
+    call()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for _ in range(reps):
+        call()
+    e1.record(st)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    peaks = measured_peaks()
+    pk = peaks.get("bf16_tflops") or 1900.0
+    tflops = 272.0 * m * n * k / (ms * 1e-3) / 1e12
+    return {"bound": "tensor", "achieved": tflops, "peak": pk, "unit": "TFLOP/s",
+            "frac": tflops / pk, "traffic": None, "kernel": "k_zgemm_tc (+ digit split kernels)",
+            "shape": [m, n, k], "ms_per_call": ms,
+            "fp64_equivalent_tflops": 8.0 * m * n * k / (ms * 1e-3) / 1e12,
+            "peak_note": "of measured" if peaks.get("bf16_tflops") else "of fallback",
+            "work_note": "executed BF16 tensor flops of the digit products (34 digit pairs per "
+                         "real product, 4 real products per complex); the call time includes "
+                         "the digit-split kernels"}
 
 
 def run_formulations(dev, N=262144, tol=1e-8):

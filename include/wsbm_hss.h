@@ -75,7 +75,9 @@ typedef struct {
  *              phase on problems whose root system would not fit); solve then fails with
  *              WSBM_ERR_NOT_FACTORED
  *  root_cap    largest dense root order accepted (0 selects 40000); a factorization whose
- *              merged skeleton system would be larger fails with WSBM_ERR_RANK_OVERFLOW
+ *              merged skeleton system would be larger fails with WSBM_ERR_RANK_OVERFLOW.
+ *              Compression goes on past the levels that save under 20 % until the merged
+ *              system fits both root_cap and three quarters of the device memory
  *  id_method   WSBM_ID_SKETCH (0): leaf-level IDs from the column-pivoted QR of a tensor-core
  *              sketch Omega M of the ID matrix (l = 16 ceil(n/32) rows, used when M has at
  *              least 1.5 l rows; the QR of a sketch stops at a quarter of the usual cutoff; a

@@ -433,8 +433,8 @@ class Solver:
         (u, q, relative residual before each step and after the last)."""
         rc_ = rhs.T.contiguous()
         nrhs = rhs.shape[1]
-        uc = u.T.contiguous()
-        qc = q.T.contiguous()
+        uc = u.T.contiguous().clone()  # refined in place: never the caller's storage
+        qc = q.T.contiguous().clone()
         res = (ctypes.c_double * (iters + 1))()
         _check(lib().wsbm_refine(self.h, 1 if trans else 0, _dev(rc_, torch.complex128), nrhs,
                                  _dev(uc, torch.complex128), _dev(qc, torch.complex128), iters, res),

@@ -971,7 +971,8 @@ int wsbm_lu_solve_t_batched(const TrsmDesc* d_desc, int nbatch, int max_n, int m
 
 // ------------------------------------------------------------- LU of one large matrix ----
 // Right-looking blocked LU with partial pivoting for a single large matrix (the dense root of
-// a full build): outer panels of LUB_NB columns.  Each panel is factored recursively (halves,
+// a full build): outer panels of LUB_NB columns (LUB_NB_BIG for large n, where the deeper
+// tensor-core products pay for the longer panels).  Each panel is factored recursively (halves,
 // down to blocks of LUB_WB columns done column by column), with every column operation spread
 // over the whole GPU: the pivot search is one launch whose CTAs combine their candidates with
 // atomicMax on a 64-bit key, the row swap one small launch, the scaling and rank-1 update of
@@ -980,8 +981,11 @@ int wsbm_lu_solve_t_batched(const TrsmDesc* d_desc, int nbatch, int max_n, int m
 // update A22 -= L21 U12 runs on the tensor cores (wsbm_zgemm_tc).  Factors and piv as for
 // wsbm_lu_batched.  Pivot: the row of largest max(|re|, |im|) compared on the upper 32 bits of
 // its bit pattern (within 2^-20 of the largest), first row on ties.
-#define LUB_NB 128  // outer panel width
+#define LUB_NB 128      // outer panel width
+#define LUB_NB_BIG 256  // outer panel width from LUB_BIG_N on: deeper tensor-core products
+#define LUB_BIG_N 12288
 #define LUB_WB 8    // column-by-column block width
+#define LUB_TC_K 32 // panel updates of at least this depth run on the tensor cores
 
 __device__ __forceinline__ unsigned long long lub_key(double2 v, int row) {
   const unsigned long long m = 0x7fffffffffffffffull;
@@ -1095,6 +1099,22 @@ __global__ void k_lub_trsm(double2* __restrict__ A, int64_t lda, int r0, int nb,
   }
 }
 
+// X = L^-1 for the unit lower triangle L of A[r0 : r0+nb, r0 : r0+nb] (X nb x nb, ldx = nb):
+// one thread per column j, x_ij = -sum_{j<=t<i} l_it x_tj.
+__global__ void k_lub_trinv(const double2* __restrict__ A, int64_t lda, int r0, int nb, double2* __restrict__ X) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= nb) return;
+  double2* x = X + (int64_t)j * nb;
+  for (int i = 0; i < j; ++i) x[i] = make_double2(0.0, 0.0);
+  x[j] = make_double2(1.0, 0.0);
+  for (int i = j + 1; i < nb; ++i) {
+    double2 s = make_double2(0.0, 0.0);
+    const double2* li = A + (r0 + i) + (int64_t)r0 * lda;
+    for (int t = j; t < i; ++t) s = cfms(li[(int64_t)t * lda], x[t], s);
+    x[i] = s;
+  }
+}
+
 // C[m x nc] -= A[m x k] B[k x nc] (the updates inside a panel), FP64 tiles.
 __global__ void __launch_bounds__(256) k_lub_gemm(int m, int nc, int k, const double2* __restrict__ A,
                                                   int64_t lda, const double2* __restrict__ B, int64_t ldb,
@@ -1115,7 +1135,8 @@ struct LubCtx {
   double2* inv;
   int* info;
   cudaStream_t st;
-  int cs, ce;  // current outer panel
+  int cs, ce;   // current outer panel
+  void* tcws;   // work space of the tensor-core products
 };
 
 int lub_grid(int64_t rows) {
@@ -1140,33 +1161,47 @@ void lub_rec(const LubCtx& x, int c0, int c1) {
   lub_rec(x, c0, mid);
   // A[c0:mid, mid:c1] = L11^-1 A[c0:mid, mid:c1];  A[mid:n, mid:c1] -= A[mid:n, c0:mid] A[c0:mid, mid:c1]
   k_lub_trsm<<<(c1 - mid + 63) / 64, 64, 0, x.st>>>(x.A, x.lda, c0, mid - c0, mid, c1);
+  wsbm_count_launch();
   const int m = x.n - mid;
-  const int64_t tiles = (int64_t)((m + GT - 1) / GT) * ((c1 - mid + GT - 1) / GT);
-  k_lub_gemm<<<tiles_x(tiles), 256, 0, x.st>>>(m, c1 - mid, mid - c0, x.A + mid + (int64_t)c0 * x.lda, x.lda,
-                                             x.A + c0 + (int64_t)mid * x.lda, x.lda,
-                                             x.A + mid + (int64_t)mid * x.lda, x.lda);
-  wsbm_count_launches(2);
+  if (mid - c0 >= LUB_TC_K && m >= 2 * LUB_NB) {
+    // the wide updates of the panel on the tensor cores
+    const double2 mone = make_double2(-1.0, 0.0), one = make_double2(1.0, 0.0);
+    wsbm_zgemm_tc(m, c1 - mid, mid - c0, mone, x.A + mid + (int64_t)c0 * x.lda, x.lda,
+                  x.A + c0 + (int64_t)mid * x.lda, x.lda, one, x.A + mid + (int64_t)mid * x.lda, x.lda,
+                  x.tcws, x.st);
+  } else {
+    const int64_t tiles = (int64_t)((m + GT - 1) / GT) * ((c1 - mid + GT - 1) / GT);
+    k_lub_gemm<<<tiles_x(tiles), 256, 0, x.st>>>(m, c1 - mid, mid - c0, x.A + mid + (int64_t)c0 * x.lda, x.lda,
+                                               x.A + c0 + (int64_t)mid * x.lda, x.lda,
+                                               x.A + mid + (int64_t)mid * x.lda, x.lda);
+    wsbm_count_launch();
+  }
   // the key of column mid is set by the first search of the right half
   lub_rec(x, mid, c1);
 }
 }  // namespace
 
+static int lub_nb(int n) { return n >= LUB_BIG_N ? LUB_NB_BIG : LUB_NB; }
+
 size_t wsbm_lu_big_ws_bytes(int n) {
-  size_t b = wsbm_zgemm_tc_ws_bytes(n, n, LUB_NB);
+  size_t b = wsbm_zgemm_tc_ws_bytes(n, n, lub_nb(n));
   b = (b + 255) & ~(size_t)255;
   b += ((size_t)n + 8) * sizeof(unsigned long long) + 256 + sizeof(LuDesc) + 256;
+  b += (size_t)LUB_NB_BIG * LUB_NB_BIG * sizeof(double2) + 256;  // L11^-1
   return b;
 }
 
 int wsbm_lu_big(double2* A, int64_t lda, int n, int* piv, int* d_info, void* ws, cudaStream_t st) {
   if (n <= 0) return 0;
   if (!A || !piv || !ws || lda < n || ((uintptr_t)ws & 255)) return -1;
-  size_t off = (wsbm_zgemm_tc_ws_bytes(n, n, LUB_NB) + 255) & ~(size_t)255;
+  const int nb = lub_nb(n);
+  size_t off = (wsbm_zgemm_tc_ws_bytes(n, n, nb) + 255) & ~(size_t)255;
   unsigned long long* key = (unsigned long long*)((char*)ws + off);
   off += ((size_t)n + 8) * sizeof(unsigned long long);
   off = (off + 255) & ~(size_t)255;
   double2* inv = (double2*)((char*)ws + off);
   LuDesc* dd = (LuDesc*)((char*)ws + off + 256);
+  double2* Linv = (double2*)((char*)ws + ((off + 256 + sizeof(LuDesc) + 255) & ~(size_t)255));
   LuDesc h;
   h.A = A;
   h.lda = lda;
@@ -1184,9 +1219,10 @@ int wsbm_lu_big(double2* A, int64_t lda, int n, int* piv, int* d_info, void* ws,
   x.inv = inv;
   x.info = d_info;
   x.st = st;
+  x.tcws = ws;
   const double2 mone = make_double2(-1.0, 0.0), one = make_double2(1.0, 0.0);
-  for (int j0 = 0; j0 < n; j0 += LUB_NB) {
-    const int jb = std::min(LUB_NB, n - j0), je = j0 + jb;
+  for (int j0 = 0; j0 < n; j0 += nb) {
+    const int jb = std::min(nb, n - j0), je = j0 + jb;
     x.cs = j0;
     x.ce = je;
     lub_rec(x, j0, je);
@@ -1194,9 +1230,20 @@ int wsbm_lu_big(double2* A, int64_t lda, int n, int* piv, int* d_info, void* ws,
     k_laswp<<<gs, 128, 0, st>>>(dd, j0, jb);
     wsbm_count_launch();
     if (je < n) {
-      k_lu_trsm_row<<<gs, 128, 0, st>>>(dd, j0, jb);
-      wsbm_count_launch();
       const int m = n - je;
+      if (m >= 2 * LUB_NB) {
+        // U12 = L11^-1 A12 as a tensor-core product with the explicit inverse of the unit lower
+        // L11 (the digit planes of A12 are formed before A12 is overwritten)
+        k_lub_trinv<<<(jb + 63) / 64, 64, 0, st>>>(A, lda, j0, jb, Linv);
+        wsbm_count_launch();
+        const double2 zero = make_double2(0.0, 0.0);
+        int rc = wsbm_zgemm_tc(jb, m, jb, one, Linv, jb, A + j0 + (int64_t)je * lda, lda, zero,
+                               A + j0 + (int64_t)je * lda, lda, ws, st);
+        if (rc) return rc;
+      } else {
+        k_lu_trsm_row<<<gs, 128, 0, st>>>(dd, j0, jb);
+        wsbm_count_launch();
+      }
       int rc = wsbm_zgemm_tc(m, m, jb, mone, A + je + (int64_t)j0 * lda, lda, A + j0 + (int64_t)je * lda, lda,
                              one, A + je + (int64_t)je * lda, lda, ws, st);
       if (rc) return rc;

@@ -40,6 +40,11 @@
 #ifndef WSBM_SKETCH_PAD
 #define WSBM_SKETCH_PAD 0
 #endif
+// Dense roots of at least this order are factored by the LU whose trailing updates run on
+// the tensor cores (wsbm_lu_big); smaller ones by the batched FP64 blocked LU.
+#ifndef WSBM_BIGLU_MIN
+#define WSBM_BIGLU_MIN 2048
+#endif
 #ifndef WSBM_SKETCH_CUT
 #define WSBM_SKETCH_CUT 0.25  // measured: far-field error 3.6-5.8x tol, as with the full QR
 #endif
@@ -1454,6 +1459,18 @@ static int factor_roots(const std::vector<wsbm_hss*>& hs, double ms_out[2]) {
   std::vector<LuDesc> lus;
   std::vector<int64_t> e_pairs(hs.size(), 0);
   int maxn = 0;
+  {
+    // a large root needs its memory in one piece: hand the pool's cached work space of the
+    // levels back first (the levels ended with the stream synchronized)
+    size_t rb = 0;
+    for (auto* h : hs) {
+      int64_t S = 0;
+      if (h->L == 0) S = 2 * h->N;
+      else for (auto& b : h->lv[h->top].box) S += b.k;
+      rb += (size_t)S * S * sizeof(double2);
+    }
+    if (rb > ((size_t)4 << 30)) wsbm_trim_memory();
+  }
   for (size_t i = 0; i < hs.size(); ++i) {
     wsbm_hss* h = hs[i];
     std::vector<int32_t> Rr, Rc;
@@ -1500,8 +1517,6 @@ static int factor_roots(const std::vector<wsbm_hss*>& hs, double ms_out[2]) {
     launch_y(k_copy2d, gridfor(mx), (int64_t)copies.size(), dc, st);
   }
   HK(pb.prepare(h0, tmp));
-  LuDesc* dl = nullptr;
-  HK(upload(h0, lus, &dl, tmp));
   HC(cudaEventRecord(h0->ev[0], st));
   HK(pb.run(h0, ia.geos, ia.phys));
   HC(cudaEventRecord(h0->ev[1], st));
@@ -1513,7 +1528,31 @@ static int factor_roots(const std::vector<wsbm_hss*>& hs, double ms_out[2]) {
     h0->stats.pairs_evaluated += pb.pairs;
     h0->stats.pairs_pairs += pb.pairs;
   }
-  HK(wsbm_lu_batched(dl, (int)lus.size(), maxn, nullptr, st));
+  // large roots: one at a time through the LU whose trailing updates run on the tensor cores;
+  // the others in one batched blocked LU
+  {
+    std::vector<LuDesc> small;
+    int maxs = 0;
+    size_t wsb = 0;
+    for (auto& l : lus)
+      if (l.n >= WSBM_BIGLU_MIN) wsb = std::max(wsb, wsbm_lu_big_ws_bytes(l.n));
+    void* ws = nullptr;
+    if (wsb) HK(dalloc(h0, wsb, &ws, tmp));
+    for (auto& l : lus) {
+      if (l.n >= WSBM_BIGLU_MIN) {
+        if (wsbm_lu_big(l.A, l.lda, l.n, l.piv, nullptr, ws, st)) return WSBM_ERR_CUDA;
+      } else {
+        small.push_back(l);
+        maxs = std::max(maxs, l.n);
+      }
+    }
+    if (!small.empty()) {
+      LuDesc* ds = nullptr;
+      HK(upload(h0, small, &ds, tmp));
+      HK(wsbm_lu_batched(ds, (int)small.size(), maxs, nullptr, st));
+    }
+    if (wsb && wsbm_zgemm_tc_status(st) != 0) return WSBM_ERR_TIMEOUT;
+  }
   HC(cudaEventRecord(h0->ev[2], st));
   HC(cudaStreamSynchronize(st));
   ms_out[0] = elapsed(h0->ev[0], h0->ev[1]);
@@ -1541,6 +1580,13 @@ static int factor_all(const std::vector<wsbm_hss*>& hs, wsbm_stats_t* bstats) {
   std::vector<int> level(hs.size(), 0), done(hs.size(), 0);
   std::vector<char> partial(hs.size(), 0);
   int rc = WSBM_OK;
+  // largest dense root that fits in three quarters of the device memory (complex128)
+  int64_t mem_cap = INT32_MAX;
+  {
+    size_t fb = 0, tb = 0;
+    if (cudaMemGetInfo(&fb, &tb) == cudaSuccess && tb > 0)
+      mem_cap = (int64_t)sqrt(0.75 * (double)tb / (double)sizeof(double2));
+  }
   for (size_t i = 0; i < hs.size(); ++i) {
     wsbm_hss* h = hs[i];
     release_factors(h);
@@ -1579,7 +1625,7 @@ static int factor_all(const std::vector<wsbm_hss*>& hs, wsbm_stats_t* bstats) {
       ++done[i];
       int next = 0;
       if (l > 1 && !(h->prm.max_levels > 0 && done[i] >= h->prm.max_levels)) {
-        const int root_cap = h->prm.root_cap > 0 ? h->prm.root_cap : 40000;
+        const int64_t root_cap = std::min<int64_t>(h->prm.root_cap > 0 ? h->prm.root_cap : 40000, mem_cap);
         int64_t Scur = 0, Snext = 0;
         int nmax = 0;
         for (auto& b : h->lv[l].box) {
@@ -1597,8 +1643,9 @@ static int factor_all(const std::vector<wsbm_hss*>& hs, wsbm_stats_t* bstats) {
           nmax = std::max(nmax, (int)P.cr.size());
         }
         // stop compressing when it no longer pays (high-frequency boxes keep most unknowns)
-        // and the merged system fits the root, or when the next level's boxes would be too
-        // large for one-CTA column-pivoted QR
+        // and the merged system fits the root (root_cap, and three quarters of the device
+        // memory), or when the next level's boxes would be too large for one-CTA
+        // column-pivoted QR
         bool stop = (Snext > 0.8 * (double)Scur && Snext <= root_cap) || nmax > 3072;
         if (!stop) next = l - 1;
       }

@@ -156,6 +156,14 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, float* v) {
 }
 __device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
+// x 2^ex: exponent-field addition when x and the result are normal, else ldexp.
+__device__ __forceinline__ double scale2(double x, int ex) {
+  const long long b = __double_as_longlong(x);
+  const int e = (int)((b >> 52) & 0x7FF);
+  if (e > 0 && e + ex >= 1 && e + ex <= 2046) return __longlong_as_double(b + ((long long)ex << 52));
+  return ldexp(x, ex);
+}
+
 // --------------------------------------------------------------- digit planes ----
 // Exponent e with |v| < 2^(e-1) for every |Re|, |Im| of the row/column maximum `mx` (as raw
 // bits of a non-negative double); 0 for an all-zero row.
@@ -301,6 +309,7 @@ struct TcArgs {
   int tiles_m, tiles_n; // 128-row and 64-real-column tiles
   int nkb;              // K blocks of TC_BK real values
   double2 alpha, beta;
+  int sub;              // alpha = -1, beta = 1 (C -= A B): two FP64 additions per entry
   double2* C;
   int64_t ldc;
   const int* rexp;
@@ -477,7 +486,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         mbar_arrive(tempty);
       }
       if (!ok) break;
-      // C = beta C + alpha T 2^(e_i + f_j - 48)
+      // C = beta C + alpha (T + F 2^-16) 2^(e_i + f_j - 48); the power of two enters through
+      // the exponent field (integer pipe), so C -= A B costs one FMA and one add per value
       const int i = tm * TC_BM + row;
       if (i < a.m) {
         const int ei = a.rexp[i];
@@ -485,18 +495,23 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         for (int c = 0; c < TC_BN / 4; ++c) {
           const int j = tn * (TC_BN / 2) + half * (TC_BN / 4) + c;
           if (j >= a.n) continue;
-          const double sc = ldexp(1.0, ei + a.cexp[j] - 48);
+          const int ex = ei + a.cexp[j] - 48;
           const int* fp = frac + (half * (TC_BN / 2) + 2 * c) * TC_BM + row;
-          const double xr = fma((double)fp[0], 1.0 / 65536.0, (double)T[2 * c]) * sc;
-          const double xi = fma((double)fp[TC_BM], 1.0 / 65536.0, (double)T[2 * c + 1]) * sc;
+          const double xr = scale2(fma((double)fp[0], 1.0 / 65536.0, (double)T[2 * c]), ex);
+          const double xi = scale2(fma((double)fp[TC_BM], 1.0 / 65536.0, (double)T[2 * c + 1]), ex);
           double2* p = a.C + i + (int64_t)j * a.ldc;
-          double2 r = make_double2(a.alpha.x * xr - a.alpha.y * xi, a.alpha.x * xi + a.alpha.y * xr);
-          if (a.beta.x != 0.0 || a.beta.y != 0.0) {
+          if (a.sub) {
             const double2 o = *p;
-            r.x += a.beta.x * o.x - a.beta.y * o.y;
-            r.y += a.beta.x * o.y + a.beta.y * o.x;
+            *p = make_double2(o.x - xr, o.y - xi);
+          } else {
+            double2 r = make_double2(a.alpha.x * xr - a.alpha.y * xi, a.alpha.x * xi + a.alpha.y * xr);
+            if (a.beta.x != 0.0 || a.beta.y != 0.0) {
+              const double2 o = *p;
+              r.x += a.beta.x * o.x - a.beta.y * o.y;
+              r.y += a.beta.x * o.y + a.beta.y * o.x;
+            }
+            *p = r;
           }
-          *p = r;
         }
       }
     }
@@ -582,6 +597,7 @@ int wsbm_zgemm_tc(int m, int n, int k, double2 alpha, const double2* A, int64_t 
   a.nkb = (int)(Ka / TC_BK);
   a.alpha = alpha;
   a.beta = beta;
+  a.sub = alpha.x == -1.0 && alpha.y == 0.0 && beta.x == 1.0 && beta.y == 0.0;
   a.C = C;
   a.ldc = ldc;
   a.rexp = rexp;

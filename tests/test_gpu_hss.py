@@ -273,7 +273,9 @@ def test_leaf_level_of_65536_boxes():
     N = 1 << 20
     c = inputs.star(N)
     k0 = float(inputs.k0_for_density(c)) / 4.0  # 60 nodes per wavelength: small box ranks
-    tol = 1e-6
+    # QR cutoff id_tol / (4 sqrt(65536)) = 2.5e-7 relative to each ID matrix's largest column
+    tol = 2.5e-7 * 4 * 256
+    cut = tol / (4 * 256)
     g, keep = binding.make_geom(c)
     p = binding.make_params(k0, 1.5, leaf=16, nproxy=32, id_tol=tol, max_levels=1)
     s = binding.Solver(g, p)
@@ -300,7 +302,7 @@ def test_leaf_level_of_65536_boxes():
             Q, _ = np.linalg.qr(A[pos].T)
             R = A.T - Q @ (Q.conj().T @ A.T)
             rel = np.linalg.norm(R) / np.linalg.norm(A)
-            assert rel < 10 * tol, (box, rows_side, rel)
+            assert rel < 40 * cut, (box, rows_side, rel)
     s.close()
 
 
