@@ -691,24 +691,27 @@ def run_full_2p18(dev, precision=0, tol=1e-8, rows=256):
     Arows = s.entries(ridx, cols)
     r = Arows @ x - rhs[ridx]
     res_rows = (torch.linalg.norm(r) / torch.linalg.norm(rhs[ridx])).item()
-    # one refinement step: r = b - A x (matrix-free), x1 = x + HSS^-1 r
+    # one refinement step for the first plane wave: r = b - A x (matrix-free, O(N^2)),
+    # x1 = x + HSS^-1 r
     t = time.time()
-    rfull = rhs - binding.wsbm_matvec(g, p, x)
-    res_full = (torch.linalg.norm(rfull) / torch.linalg.norm(rhs)).item()
+    b0, x0 = rhs[:, :1].contiguous(), x[:, :1].contiguous()
+    rfull = b0 - binding.wsbm_matvec(g, p, x0)
+    res_full = (torch.linalg.norm(rfull) / torch.linalg.norm(b0)).item()
     du, dq = s.solve(rfull)
-    ff1 = s.farfield(u + du, q + dq, obs)
+    ff1 = s.farfield(u[:, :1] + du, q[:, :1] + dq, obs)
     torch.cuda.synchronize()
     t_ref = time.time() - t
-    ff_err = (torch.linalg.norm(ff - ff1) / torch.linalg.norm(ff1)).item()
-    u_err = (torch.linalg.norm(du) / torch.linalg.norm(u + du)).item()
+    ff_err = (torch.linalg.norm(ff[:, :1] - ff1) / torch.linalg.norm(ff1)).item()
+    u_err = (torch.linalg.norm(du) / torch.linalg.norm(u[:, :1] + du)).item()
     out = {"build_factor_s": st["ms_total_factor"] / 1e3, "wall_s": wall,
            "ms_entries": st["ms_entries"], "ms_id": st["ms_id"], "ms_factor": st["ms_factor"],
            "root_size": st["root_size"], "rank_per_level": st["rank_per_level"],
            "factor_bytes": st["factor_bytes"], "entries": st["entries_generated"],
            "entries_per_s": st["entries_generated"] / (st["ms_entries"] * 1e-3),
            "solve_8rhs_farfield_s": t_solve, "id_tol": tol, "precision": precision,
-           "residual_rel_full": res_full, "residual_rel_sampled_rows": res_rows,
-           "farfield_rel_err_vs_one_refinement_step": ff_err, "density_rel_correction": u_err,
+           "residual_rel_full_angle0": res_full, "residual_rel_sampled_rows": res_rows,
+           "farfield_rel_err_vs_one_refinement_step_angle0": ff_err,
+           "density_rel_correction_angle0": u_err,
            "refinement_step_s": t_ref}
     s.close()
     binding.trim_memory()
@@ -1009,9 +1012,25 @@ def main():
     ap.add_argument("--profile-case", action="store_true",
                     help="one leaf-level build of the star (small case for ncu) per precision mode")
     ap.add_argument("--profile-n", type=int, default=16384, help="nodes of the --profile-case star")
+    ap.add_argument("--profile-tc", action="store_true",
+                    help="two tensor-core GEMM calls, 4096 x 4096 x 128 (small case for ncu)")
+    ap.add_argument("--full-2p18", action="store_true",
+                    help="only the whole build + factor at N = 2^18 (FP64, and WSBM_MIXED_FINE "
+                         "with --mixed-tol)")
+    ap.add_argument("--mixed-tol", type=float, default=0.0)
     args = ap.parse_args()
     if args.profile_case:
         profile_case(args.profile_n)
+        return
+    if args.profile_tc:
+        print(json.dumps(run_tc_gemm("cuda", 4096, 4096, 128, reps=1)), flush=True)
+        return
+    if args.full_2p18:
+        out = {"fp64": run_full_2p18("cuda")}
+        if args.mixed_tol > 0:
+            out["fp64_at_mixed_tol"] = run_full_2p18("cuda", 0, args.mixed_tol)
+            out["mixed_fine"] = run_full_2p18("cuda", 2, args.mixed_tol)
+        print(json.dumps(out), flush=True)
         return
     if args.adjoint:
         print(json.dumps({"adjoint": run_adjoint("cuda", N=args.adjoint_n)}), flush=True)

@@ -8,7 +8,9 @@
 //   z >= 1.5    H_nu = sqrt(2/(pi z)) (P_nu + i Q_nu) e^{i(z - pi/4 - nu pi/2)};
 //               P_nu - 1, Q_nu are degree-10 polynomials in u = 1/z on seven intervals up to
 //               z = 20 (the functions are smooth in 1/z), and degree-6 polynomials in 1/z^2
-//               beyond (P_nu - 1 and z Q_nu);
+//               beyond (P_nu - 1 and z Q_nu), evaluated there in two-float (hi + lo FP32)
+//               arithmetic on the FP32 pipe: they are small corrections, so 48 significant
+//               bits give them an absolute error below 1e-17;
 //   phase       z - pi/4 is reduced by multiples of pi/2 (Cody-Waite with a two-part pi/2 and
 //               fused multiply-adds) and sin/cos of the remainder |w| <= pi/4 come from fitted
 //               polynomials, so no rounding of z - pi/4 enters the phase.
@@ -52,6 +54,7 @@ struct HkTables {
   float ivf[HK_NIV][2];
   float fitf[HK_NIV][4][HKF_DEG + 1];
   float asyf[4][HKF_DEG_T + 1];
+  float asyh[4][HK_DEG_T + 1], asyl[4][HK_DEG_T + 1];  // hk_asy as two-float sums (hi + lo)
 };
 
 template <class T>
@@ -70,6 +73,41 @@ __device__ __forceinline__ void hk_stage_tables(HkTables* t) {
   hk_copy(&t->asyf[0][0], &hkf_asy[0][0], 4 * (HKF_DEG_T + 1));
   for (int k = threadIdx.x; k < HK_NIV * 2; k += blockDim.x)
     (&t->ivf[0][0])[k] = (float)(&hk_iv[0][0])[k];
+  for (int k = threadIdx.x; k < 4 * (HK_DEG_T + 1); k += blockDim.x) {
+    const double c = (&hk_asy[0][0])[k];
+    const float h = __double2float_rn(c);
+    (&t->asyh[0][0])[k] = h;
+    (&t->asyl[0][0])[k] = __double2float_rn(c - (double)h);
+  }
+}
+
+// Two-float (hi + lo, about 48 significant bits) Horner step r <- r s + c on the FP32 pipe:
+// exact product hi part by FMA, Knuth two-sum with the coefficient, renormalisation.
+__device__ __forceinline__ void ff_step(float& rh, float& rl, float sh, float sl, float ch, float cl) {
+  const float ph = rh * sh;
+  float pl = fmaf(rh, sh, -ph);
+  pl = fmaf(rh, sl, pl);
+  pl = fmaf(rl, sh, pl);
+  const float th = ph + ch;
+  const float bb = th - ph;
+  float tl = (ph - (th - bb)) + (ch - bb);
+  tl = tl + (pl + cl);
+  rh = th + tl;
+  rl = tl - (rh - th);
+}
+
+// sum_k c_k s^k of an asymptotic table row: degrees 4.. in FP32 (they carry below 1e-7 of the
+// leading term), degrees 3 to 0 in two-float arithmetic.
+__device__ __forceinline__ void hk_asy_ff(const HkTables& T, int row, float sh, float sl, float* rh,
+                                          float* rl) {
+  float t = T.asyh[row][HK_DEG_T];
+#pragma unroll
+  for (int k = HK_DEG_T - 1; k >= 4; --k) t = fmaf(t, sh, T.asyh[row][k]);
+  float h = t, l = 0.0f;
+#pragma unroll
+  for (int k = 3; k >= 0; --k) ff_step(h, l, sh, sl, T.asyh[row][k], T.asyl[row][k]);
+  *rh = h;
+  *rl = l;
 }
 
 template <int N>
@@ -150,11 +188,19 @@ __device__ __forceinline__ void hk_pq(const HkTables& T, int zhi, double u, doub
     *pm1 = hk_horner<HK_DEG + 1>(T.fit[iv][2], s);
     *Q1 = hk_horner<HK_DEG + 1>(T.fit[iv][3], s);
   } else {
-    double s = (u * u - HK_T_C) * HK_T_IH;
-    *pm0 = hk_horner<HK_DEG_T + 1>(T.asy[0], s);
-    *Q0 = u * hk_horner<HK_DEG_T + 1>(T.asy[1], s);
-    *pm1 = hk_horner<HK_DEG_T + 1>(T.asy[2], s);
-    *Q1 = u * hk_horner<HK_DEG_T + 1>(T.asy[3], s);
+    // z >= 20: P - 1 (|.| < 4e-4) and z Q in two-float arithmetic on the FP32 pipe; the
+    // absolute error of P and Q stays below 1e-17
+    const double s = (u * u - HK_T_C) * HK_T_IH;
+    const float sh = __double2float_rn(s), sl = __double2float_rn(s - (double)sh);
+    float h, l;
+    hk_asy_ff(T, 0, sh, sl, &h, &l);
+    *pm0 = (double)h + (double)l;
+    hk_asy_ff(T, 1, sh, sl, &h, &l);
+    *Q0 = u * ((double)h + (double)l);
+    hk_asy_ff(T, 2, sh, sl, &h, &l);
+    *pm1 = (double)h + (double)l;
+    hk_asy_ff(T, 3, sh, sl, &h, &l);
+    *Q1 = u * ((double)h + (double)l);
   }
 }
 

@@ -151,3 +151,29 @@ def test_proxy_blocks_match_oracle(N, lo, hi, P):
         fine = gpu_proxy(c, ph, side, box, circ, P, precision=2)
         rel = np.linalg.norm(fine - ref) / np.linalg.norm(ref)
         assert rel < 5e-8, (side, rel)
+
+
+def test_proxy_blocks_on_an_upper_level_circle():
+    """Proxy blocks on the circle of a level-3 box of the 2^18 star (32768 nodes, radius ~0.8),
+    where the arguments k r reach ~3e4: 128 of the box's nodes against 1024 proxy points.  The
+    proxy points are placed by sincospi on the GPU and by std::cos/std::sin in the oracle, so
+    their positions can differ by an ulp; the bound adds the phase change that causes,
+    |dz| <= 8 z eps, to the 1e-12 of the entry parity."""
+    N = 262144
+    c = inputs.star(N)
+    ph = oracle.Physics(inputs.k0_for_density(c), n=1.5)
+    lo, hi = 3 * 32768, 4 * 32768
+    circ = oracle.proxy_circle(c, np.arange(lo, hi))
+    nodes = np.arange(lo + 5000, lo + 5128)
+    box = np.concatenate([nodes, nodes + N])
+    R = np.hypot(c["x"][lo:hi] - circ[0], c["y"][lo:hi] - circ[1]).max()
+    zmax = ph.k1 * (circ[2] + R)
+    assert zmax > 1e4
+    bound = TOL + 8 * zmax * 2.0 ** -53
+    for side in (0, 1):
+        ref = (oracle.proxy_row_block(c, ph, box, circ, 1024) if side == 0
+               else oracle.proxy_col_block(c, ph, box, circ, 1024))
+        got = gpu_proxy(c, ph, side, box, circ, 1024)
+        scale = np.maximum(np.abs(ref).max(axis=0, keepdims=True), 1e-300)
+        err = np.abs(got - ref) / scale
+        assert err.max() <= bound, (side, err.max(), bound)
