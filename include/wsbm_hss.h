@@ -333,8 +333,9 @@ void wsbm_batch_destroy(wsbm_batch_t b);
  * matrix of eq. (weakly_bm) (every node pair, O(N^2) work, nothing stored): residuals and
  * iterative refinement of HSS and adjoint solutions.  x, y: device complex128 2N x nrhs in
  * paper order (for trans = 0, x by unknown and y by equation; the reverse for trans = 1).
- * Scratch: 2N x (eight waves of CTAs / ceil(N/128)) complex128 from the library's allocator
- * (wsbm_set_allocator) on `stream`.  Asynchronous.  Errors: INVALID_ARG, OOM, CUDA. */
+ * The Hankel values of each node pair are evaluated once for up to four right-hand sides.
+ * Scratch: 4 x 2N x (eight waves of CTAs / ceil(N/128)) complex128 from the library's
+ * allocator (wsbm_set_allocator) on `stream`.  Asynchronous.  Errors: INVALID_ARG, OOM, CUDA. */
 int wsbm_matvec(const wsbm_geom* g, const wsbm_params* p, int32_t trans, const void* x,
                 int32_t nrhs, void* y, void* stream);
 
@@ -365,9 +366,10 @@ int wsbm_sketch(const void* A, int64_t lda, int32_t m, int32_t n, int32_t l, voi
  * blocked LU factorizations of large boxes and of the dense root (the paper factors with FP64
  * CPU arithmetic; GB300's FP64 pipe runs at 1/64 of its FP32 rate and far below its tensor
  * cores).  Rows of A and columns of B are scaled by powers of two and cut into seven exact
- * 8-bit digits; BF16 tensor-core products of the digits accumulate exactly in FP32 and are
- * recombined in 64-bit integers, so each entry of A B carries an error below about
- * 2^-55 * 2k * max_l |A_il| * max_l |B_lj| (the order of an FP64 product).
+ * 8-bit digits; BF16 tensor-core products of the digits accumulate in FP32 (exactly for the
+ * leading digit diagonals) and are recombined in 64-bit integers with a 2^-64 fraction, so each
+ * entry of A B carries an error below about 2^-53 * 2k * max_l |A_il| * max_l |B_lj| (the
+ * order of an FP64 product).
  *   A  device complex128 m x k (lda >= m); B: k x n (ldb >= k); C: m x n (ldc >= m); all
  *      column-major; alpha, beta: host, 2 doubles (re, im) each
  *   1 <= k <= 32768

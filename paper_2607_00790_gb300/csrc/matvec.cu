@@ -8,14 +8,17 @@
 // Thread = output node i; CTA row blockIdx.y covers the other nodes [j0, j1); per-split
 // partial sums, reduced in a fixed order by k_matvec_reduce.  Vectors in paper order.
 #define MV_THREADS 128
+#define MV_RHS 4  // right-hand sides sharing each pair's Hankel evaluations
 struct MvSlot {
   double x, y, nx, ny, w, kap;
-  double2 u, q;
+  double2 u[MV_RHS], q[MV_RHS];
 };
 
+// nr <= MV_RHS columns c0 .. c0 + nr - 1 of x (column stride 2N); partial sums of column r of
+// split s at part[(s * MV_RHS + r) * 2N + row].
 template <bool TRANS>
 __global__ void __launch_bounds__(MV_THREADS)
-    k_matvec(DevGeom g, Phys ph, const double2* __restrict__ xin, int64_t jspan,
+    k_matvec(DevGeom g, Phys ph, const double2* __restrict__ xin, int nr, int64_t jspan,
              double2* __restrict__ part) {
   __shared__ HkTables T;
   __shared__ MvSlot sj[MV_THREADS];
@@ -34,7 +37,9 @@ __global__ void __launch_bounds__(MV_THREADS)
     wi = g.w[i];
     ki = g.kappa[i];
   }
-  double2 a0 = make_double2(0.0, 0.0), a1 = make_double2(0.0, 0.0);
+  double2 a0[MV_RHS], a1[MV_RHS];
+#pragma unroll
+  for (int r = 0; r < MV_RHS; ++r) a0[r] = a1[r] = make_double2(0.0, 0.0);
   for (int64_t jc = j0; jc < j1; jc += MV_THREADS) {
     __syncthreads();
     {
@@ -47,8 +52,12 @@ __global__ void __launch_bounds__(MV_THREADS)
         s.ny = g.ny[j];
         s.w = g.w[j];
         s.kap = g.kappa[j];
-        s.u = xin[j];
-        s.q = xin[N + j];
+#pragma unroll
+        for (int r = 0; r < MV_RHS; ++r) {
+          const bool on = r < nr;
+          s.u[r] = on ? xin[(int64_t)r * 2 * N + j] : make_double2(0.0, 0.0);
+          s.q[r] = on ? xin[(int64_t)r * 2 * N + N + j] : make_double2(0.0, 0.0);
+        }
       }
     }
     __syncthreads();
@@ -76,29 +85,41 @@ __global__ void __launch_bounds__(MV_THREADS)
         e[0][1] = e[1][0];
         e[1][0] = t;
       }
-      a0.x += e[0][0].x * s.u.x - e[0][0].y * s.u.y + e[0][1].x * s.q.x - e[0][1].y * s.q.y;
-      a0.y += e[0][0].x * s.u.y + e[0][0].y * s.u.x + e[0][1].x * s.q.y + e[0][1].y * s.q.x;
-      a1.x += e[1][0].x * s.u.x - e[1][0].y * s.u.y + e[1][1].x * s.q.x - e[1][1].y * s.q.y;
-      a1.y += e[1][0].x * s.u.y + e[1][0].y * s.u.x + e[1][1].x * s.q.y + e[1][1].y * s.q.x;
+#pragma unroll
+      for (int r = 0; r < MV_RHS; ++r) {
+        if (r >= nr) break;
+        const double2 u = s.u[r], q = s.q[r];
+        a0[r].x += e[0][0].x * u.x - e[0][0].y * u.y + e[0][1].x * q.x - e[0][1].y * q.y;
+        a0[r].y += e[0][0].x * u.y + e[0][0].y * u.x + e[0][1].x * q.y + e[0][1].y * q.x;
+        a1[r].x += e[1][0].x * u.x - e[1][0].y * u.y + e[1][1].x * q.x - e[1][1].y * q.y;
+        a1[r].y += e[1][0].x * u.y + e[1][0].y * u.x + e[1][1].x * q.y + e[1][1].y * q.x;
+      }
     }
   }
   if (valid) {
-    part[(int64_t)blockIdx.y * 2 * N + i] = a0;
-    part[(int64_t)blockIdx.y * 2 * N + N + i] = a1;
+#pragma unroll
+    for (int r = 0; r < MV_RHS; ++r) {
+      if (r >= nr) break;
+      double2* pr = part + ((int64_t)blockIdx.y * MV_RHS + r) * 2 * N;
+      pr[i] = a0[r];
+      pr[N + i] = a1[r];
+    }
   }
 }
 
-__global__ void k_matvec_reduce(int64_t N, int nsplit, const double2* __restrict__ part,
+// y[:, r] = sum over the splits, in split order, for the nr columns of one launch.
+__global__ void k_matvec_reduce(int64_t N, int nsplit, int nr, const double2* __restrict__ part,
                                 double2* __restrict__ y) {
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < 2 * N;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < 2 * N * nr;
        e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = e / (2 * N), row = e % (2 * N);
     double2 s = make_double2(0.0, 0.0);
     for (int t = 0; t < nsplit; ++t) {
-      double2 v = part[(int64_t)t * 2 * N + e];
+      double2 v = part[((int64_t)t * MV_RHS + r) * 2 * N + row];
       s.x += v.x;
       s.y += v.y;
     }
-    y[e] = s;
+    y[r * 2 * N + row] = s;
   }
 }
 
@@ -135,17 +156,18 @@ extern "C" int wsbm_matvec(const wsbm_geom* g, const wsbm_params* p, int32_t tra
   nsplit = (N + jspan - 1) / jspan;
   WsbmScratch scr(st);
   double2* part = nullptr;
-  if ((rc = scr.get((size_t)nsplit * 2 * N * sizeof(double2), (void**)&part))) return rc;
+  if ((rc = scr.get((size_t)nsplit * MV_RHS * 2 * N * sizeof(double2), (void**)&part))) return rc;
   DevGeom dg = wsbm_devgeom(g);
-  for (int c = 0; c < nrhs && rc == WSBM_OK; ++c) {
+  for (int c = 0; c < nrhs && rc == WSBM_OK; c += MV_RHS) {
+    const int nr = nrhs - c < MV_RHS ? nrhs - c : MV_RHS;
     const double2* xc = (const double2*)x + (int64_t)c * 2 * N;
     if (trans)
-      k_matvec<true><<<dim3((unsigned)nti, (unsigned)nsplit), MV_THREADS, 0, st>>>(dg, ph, xc, jspan, part);
+      k_matvec<true><<<dim3((unsigned)nti, (unsigned)nsplit), MV_THREADS, 0, st>>>(dg, ph, xc, nr, jspan, part);
     else
-      k_matvec<false><<<dim3((unsigned)nti, (unsigned)nsplit), MV_THREADS, 0, st>>>(dg, ph, xc, jspan, part);
+      k_matvec<false><<<dim3((unsigned)nti, (unsigned)nsplit), MV_THREADS, 0, st>>>(dg, ph, xc, nr, jspan, part);
     wsbm_count_launch();
-    int64_t blocks = (2 * N + 255) / 256;
-    k_matvec_reduce<<<grid_for(blocks), 256, 0, st>>>(N, (int)nsplit, part,
+    int64_t blocks = (2 * N * nr + 255) / 256;
+    k_matvec_reduce<<<grid_for(blocks), 256, 0, st>>>(N, (int)nsplit, nr, part,
                                                      (double2*)y + (int64_t)c * 2 * N);
     wsbm_count_launch();
     if (cudaGetLastError() != cudaSuccess) rc = WSBM_ERR_CUDA;

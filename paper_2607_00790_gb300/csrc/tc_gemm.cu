@@ -14,10 +14,12 @@
 //     Re A_i1, Im A_i1, ...); column j of C becomes two real columns: 2j = Re C_j with B entries
 //     (Re B_lj, -Im B_lj), 2j+1 = Im C_j with (Im B_lj, Re B_lj).  K_real = 2k.
 //  3. Digit products on the tensor cores.  For every digit diagonal d = t + u <= 7 the FP32
-//     accumulator acc_d (in TMEM) collects sum A_t B_u over a chunk of 128 real K values: every
-//     product is an integer of magnitude <= 2^14 and a chunk adds at most 7 * 128 of them, so
-//     the FP32 sums are exact integers below 2^24.  Pairs with t + u >= 8 are left out: their
-//     weight is below 2^-63 of the leading term.
+//     accumulator acc_d (in TMEM) collects sum A_t B_u over a chunk of 256 real K values.  Every
+//     product is an integer of magnitude <= 2^14, so the sums of diagonals 0..3 (at most 4 * 256
+//     products) are exact integers of magnitude <= 2^24; diagonals 4..7 (weight 2^-48 and below
+//     against 2^-16 for diagonal 0) may round, by less than 2^-53.7 of the chunk's largest
+//     possible leading term.  Pairs with t + u >= 8 are left out: their weight is below 2^-63 of
+//     the leading term.
 //  4. Recombination without FP64 arithmetic.  After each chunk the accumulators are drained
 //     into a fixed-point sum of 2^-64 resolution: a 64-bit integer T of unit 2^-48 (digit
 //     diagonals 0..4 and the high part of 5) and a 16-bit fraction F of unit 2^-64 (the rest of
@@ -50,7 +52,7 @@
 #define TC_S 7                          // digits per operand
 #define TC_ND 8                         // digit diagonals kept (t + u <= 7)
 #define TC_STAGES 2
-#define TC_KC 128                       // real K values per exact accumulation chunk
+#define TC_KC 256                       // real K values per accumulation chunk (drain period)
 #define TC_A_TILE (TC_BM * TC_BK * 2)   // bytes of one A digit plane tile (8 KB)
 #define TC_B_TILE (TC_BN * TC_BK * 2)   // bytes of one B digit plane tile (4 KB)
 #define TC_STAGE_BYTES (TC_S * (TC_A_TILE + TC_B_TILE))
@@ -450,17 +452,20 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         for (int g = 0; g < TC_BN / 16; ++g) {
           // diagonals in pairs, converted as they arrive (fewer live registers)
           float v0[8], v1[8];
-          int p1[8], p2[8], p3[8], f5[8];
+          int p1[8], p3[8], f5[8];
+          long long p2[8];
           tmem_ld8(tq + 0 * TC_BN + g * 8, v0);
           tmem_ld8(tq + 1 * TC_BN + g * 8, v1);
           tmem_ld_wait();
 #pragma unroll
-          for (int c = 0; c < 8; ++c) p1[c] = __float2int_rn(v0[c]) * 256 + __float2int_rn(v1[c]);
+          for (int c = 0; c < 8; ++c) p1[c] = __float2int_rn(v0[c]) * 256 + __float2int_rn(v1[c]);  // < 2^31
           tmem_ld8(tq + 2 * TC_BN + g * 8, v0);
           tmem_ld8(tq + 3 * TC_BN + g * 8, v1);
           tmem_ld_wait();
 #pragma unroll
-          for (int c = 0; c < 8; ++c) p2[c] = __float2int_rn(v0[c]) * 256 + __float2int_rn(v1[c]);
+          for (int c = 0; c < 8; ++c) {
+            p2[c] = ((long long)__float2int_rn(v0[c]) << 8) + __float2int_rn(v1[c]);  // up to 2^32
+          }
           tmem_ld8(tq + 4 * TC_BN + g * 8, v0);
           tmem_ld8(tq + 5 * TC_BN + g * 8, v1);
           tmem_ld_wait();
@@ -479,7 +484,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             int* fp = frac + col * TC_BM + row;
             const int fn = *fp + f5[c] + __float2int_rn(v0[c]) + __float2int_rn(v1[c] * (1.0f / 256.0f));
             *fp = fn & 0xFFFF;
-            T[g * 8 + c] += ((long long)p1[c] << 24) + ((long long)p2[c] << 8) + (long long)p3[c] + (fn >> 16);
+            T[g * 8 + c] += ((long long)p1[c] << 24) + (p2[c] << 8) + (long long)p3[c] + (fn >> 16);
           }
         }
         tc_fence_before();
