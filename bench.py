@@ -319,6 +319,8 @@ def run_ours(args, ws, rank, local):
                     "sketched_id_matrices": s0["sketch_matrices"],
                     "sketch_fallbacks": s0["sketch_fallbacks"], "ms_sketch": s0["ms_sketch"],
                     "ms_cpqr": s0["ms_cpqr"], "ms_lu_fused": s0["ms_lu"]}}
+    if args.step_only:
+        return out
     out["e2e"] = run_e2e(args, curve, cfg, dev, params)
     if ws == 1:
         out["cpu_baseline"] = run_cpu_baseline(curve, cfg, budget_s=12.0)
@@ -1013,6 +1015,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--no-extras", action="store_true")
+    ap.add_argument("--step-only", action="store_true",
+                    help="only the warm-up and timed steps (no e2e, CPU baseline or extras): "
+                         "the launch list of a step for ncu")
     ap.add_argument("--adjoint", action="store_true",
                     help="only the shape-gradient measurement (N = 32768 Fourier curve)")
     ap.add_argument("--adjoint-n", type=int, default=32768)

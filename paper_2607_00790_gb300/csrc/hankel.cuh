@@ -81,6 +81,18 @@ __device__ __forceinline__ void hk_stage_tables(HkTables* t) {
   }
 }
 
+// Exact widening of a normal FP32 value (or zero) to FP64 by integer operations (rebias the
+// exponent, shift the fraction), which keeps the conversion off the FP64 pipe.
+__device__ __forceinline__ double f2d_exact(float f) {
+  const unsigned int b = __float_as_uint(f);
+  const unsigned int e = (b >> 23) & 0xFFu;
+  if (e == 0u) return 0.0;  // zero (the two-float parts here are never subnormal)
+  const unsigned long long d = ((unsigned long long)(b & 0x80000000u) << 32) |
+                               ((unsigned long long)(e + 896u) << 52) |
+                               ((unsigned long long)(b & 0x7FFFFFu) << 29);
+  return __longlong_as_double((long long)d);
+}
+
 // Two-float (hi + lo, about 48 significant bits) Horner step r <- r s + c on the FP32 pipe:
 // exact product hi part by FMA, Knuth two-sum with the coefficient, renormalisation.
 __device__ __forceinline__ void ff_step(float& rh, float& rl, float sh, float sl, float ch, float cl) {
@@ -191,16 +203,16 @@ __device__ __forceinline__ void hk_pq(const HkTables& T, int zhi, double u, doub
     // z >= 20: P - 1 (|.| < 4e-4) and z Q in two-float arithmetic on the FP32 pipe; the
     // absolute error of P and Q stays below 1e-17
     const double s = (u * u - HK_T_C) * HK_T_IH;
-    const float sh = __double2float_rn(s), sl = __double2float_rn(s - (double)sh);
+    const float sh = __double2float_rn(s), sl = __double2float_rn(s - f2d_exact(sh));
     float h, l;
     hk_asy_ff(T, 0, sh, sl, &h, &l);
-    *pm0 = (double)h + (double)l;
+    *pm0 = f2d_exact(h) + f2d_exact(l);
     hk_asy_ff(T, 1, sh, sl, &h, &l);
-    *Q0 = u * ((double)h + (double)l);
+    *Q0 = u * (f2d_exact(h) + f2d_exact(l));
     hk_asy_ff(T, 2, sh, sl, &h, &l);
-    *pm1 = (double)h + (double)l;
+    *pm1 = f2d_exact(h) + f2d_exact(l);
     hk_asy_ff(T, 3, sh, sl, &h, &l);
-    *Q1 = u * ((double)h + (double)l);
+    *Q1 = u * (f2d_exact(h) + f2d_exact(l));
   }
 }
 
