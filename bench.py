@@ -34,9 +34,10 @@ UNIT = "entries/s"
 # for the kernel sources with the recorded hash; when the sources change the traffic figure is
 # withheld until re-measured.
 KERNEL_COUNTS = {
-    "src_sha": "0b66cd3acb2ca2d7",
-    "k_proxy": {"fp64_flops_per_pair": 333.1, "dram_bytes_per_pair": 63.5},
-    "k_pairs": {"fp64_flops_per_pair": 377.3, "dram_bytes_per_pair": 64.4},
+    "src_sha": "33370da20d0ae571",
+    # 16384-node star, leaf level (bench.py --profile-case): 4.16 M / 4.24 M pairs
+    "k_proxy": {"fp64_flops_per_pair": 251.6, "dram_bytes_per_pair": 50.2},
+    "k_pairs": {"fp64_flops_per_pair": 323.9, "dram_bytes_per_pair": 50.6},
     # DRAM traffic of the column-pivoted QR per ID matrix of this workload, keyed by the hash of
     # its dense.cu section and the matrix rows it was measured on
     "k_cpqr": {"src_sha": "845cb05fd193638d", "rows": 128, "dram_bytes_per_matrix": 6.27e7},
