@@ -379,6 +379,23 @@ int wsbm_sketch(const void* A, int64_t lda, int32_t m, int32_t n, int32_t l, voi
 int wsbm_zgemm(int32_t m, int32_t n, int32_t k, const double* alpha, const void* A, int64_t lda,
                const void* B, int64_t ldb, const double* beta, void* C, int64_t ldc, void* stream);
 
+/* Many independent products C_i = beta C_i + alpha A_i B_i in one launch of the same
+ * tensor-core kernel (the batched trailing updates of the box factors): items[i] gives device
+ * pointers and sizes of product i (layout and error bound as for wsbm_zgemm; k_i >= 1, the
+ * shorter products are padded with zeros to the largest k).  count <= 65535; alpha, beta: host,
+ * 2 doubles each, common to all items.  Synchronous.  Errors: as wsbm_zgemm. */
+typedef struct {
+  const void* A;
+  int64_t lda;
+  const void* B;
+  int64_t ldb;
+  void* C;
+  int64_t ldc;
+  int32_t m, n, k, pad;
+} wsbm_gemm_item;
+int wsbm_zgemm_batched(int32_t count, const wsbm_gemm_item* items, const double* alpha,
+                       const double* beta, void* stream);
+
 /* LU factorization with partial pivoting of one dense complex matrix (the dense root of the
  * Martinsson-Rokhlin factor, Sec. III, at the sizes of full builds): right-looking, panels of
  * 128 columns factored on the whole GPU, trailing updates through the tensor-core product of

@@ -107,6 +107,8 @@ def lib():
         L.wsbm_zgemm.argtypes = [i32, i32, i32, ctypes.POINTER(d), vp, i64, vp, i64,
                                  ctypes.POINTER(d), vp, i64, vp]
         L.wsbm_zgemm.restype = ctypes.c_int
+        L.wsbm_zgemm_batched.argtypes = [i32, vp, ctypes.POINTER(d), ctypes.POINTER(d), vp]
+        L.wsbm_zgemm_batched.restype = ctypes.c_int
         L.wsbm_lu_dense.argtypes = [vp, i64, i32, vp, vp]
         L.wsbm_lu_dense.restype = ctypes.c_int
         L.wsbm_refine.restype = ctypes.c_int
@@ -268,6 +270,31 @@ def wsbm_zgemm(A, B, C=None, alpha=1.0, beta=0.0):
     _check(lib().wsbm_zgemm(m, n, k, al, _dev(Af, torch.complex128), m, _dev(Bf, torch.complex128), k,
                             be, _dev(Cf, torch.complex128), m, _stream(A.device)), "wsbm_zgemm")
     return Cf.T
+
+
+class GemmItem(ctypes.Structure):
+    _fields_ = [("A", ctypes.c_void_p), ("lda", ctypes.c_int64), ("B", ctypes.c_void_p),
+                ("ldb", ctypes.c_int64), ("C", ctypes.c_void_p), ("ldc", ctypes.c_int64),
+                ("m", ctypes.c_int32), ("n", ctypes.c_int32), ("k", ctypes.c_int32),
+                ("pad", ctypes.c_int32)]
+
+
+def wsbm_zgemm_batched(As, Bs, Cs, alpha=1.0, beta=0.0):
+    """C_i = beta C_i + alpha A_i B_i for lists of complex128 device tensors stored column-major
+    (pass the transposes' storage: tensors whose .T is contiguous), in one tensor-core launch."""
+    n = len(As)
+    items = (GemmItem * n)()
+    keep = []
+    for i, (A, B, C) in enumerate(zip(As, Bs, Cs)):
+        m, k = A.shape
+        nn = B.shape[1]
+        items[i] = GemmItem(A.data_ptr(), A.stride(1), B.data_ptr(), B.stride(1), C.data_ptr(),
+                            C.stride(1), m, nn, k, 0)
+        keep.append((A, B, C))
+    al = (ctypes.c_double * 2)(complex(alpha).real, complex(alpha).imag)
+    be = (ctypes.c_double * 2)(complex(beta).real, complex(beta).imag)
+    _check(lib().wsbm_zgemm_batched(n, ctypes.cast(items, ctypes.c_void_p), al, be,
+                                    _stream(As[0].device)), "wsbm_zgemm_batched")
 
 
 def wsbm_lu_dense(A):

@@ -342,3 +342,23 @@ extern "C" int wsbm_lu_dense(void* A, int64_t lda, int32_t n, int32_t* piv, void
   rc = wsbm_zgemm_tc_status(st);
   return rc == 0 ? WSBM_OK : (rc == -5 ? WSBM_ERR_TIMEOUT : WSBM_ERR_CUDA);
 }
+
+extern "C" int wsbm_zgemm_batched(int32_t count, const wsbm_gemm_item* items, const double* alpha,
+                                  const double* beta, void* stream) {
+  if (count < 0 || count > 65535 || (count > 0 && !items) || !alpha || !beta) return WSBM_ERR_INVALID_ARG;
+  if (count == 0) return WSBM_OK;
+  static_assert(sizeof(wsbm_gemm_item) == sizeof(TcProduct), "item layout");
+  const TcProduct* p = reinterpret_cast<const TcProduct*>(items);
+  for (int i = 0; i < count; ++i)
+    if (p[i].k < 1 || p[i].k > 32768 || p[i].m < 0 || p[i].n < 0) return WSBM_ERR_INVALID_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  WsbmScratch scr(st);
+  void* ws = nullptr;
+  int rc = scr.get(wsbm_zgemm_tc_batched_ws_bytes(p, count), &ws);
+  if (rc) return rc;
+  rc = wsbm_zgemm_tc_batched(p, count, make_double2(alpha[0], alpha[1]), make_double2(beta[0], beta[1]), ws, st);
+  if (rc == -1) return WSBM_ERR_INVALID_ARG;
+  if (rc) return WSBM_ERR_CUDA;
+  rc = wsbm_zgemm_tc_status(st);
+  return rc == 0 ? WSBM_OK : (rc == -5 ? WSBM_ERR_TIMEOUT : WSBM_ERR_CUDA);
+}

@@ -24,6 +24,21 @@ cudaError_t wsbm_smem_optin(const void* kernel, size_t bytes);
 int wsbm_zgemm_tc(int m, int n, int k, double2 alpha, const double2* A, int64_t lda, const double2* B,
                   int64_t ldb, double2 beta, double2* C, int64_t ldc, void* ws, cudaStream_t st);
 size_t wsbm_zgemm_tc_ws_bytes(int m, int n, int k);
+// Many products in one launch: C_i = beta C_i + alpha A_i B_i (sizes per item; K padded with
+// zeros to the largest k).  ws: 256-byte aligned, wsbm_zgemm_tc_batched_ws_bytes(p, n) bytes.
+// At most 65535 items.  Returns 0, -1 or -3; enqueues only (the item table is copied to ws).
+struct TcProduct {
+  const double2* A;
+  int64_t lda;
+  const double2* B;
+  int64_t ldb;
+  double2* C;
+  int64_t ldc;
+  int m, n, k, pad;
+};
+int wsbm_zgemm_tc_batched(const TcProduct* p, int nitems, double2 alpha, double2 beta, void* ws,
+                          cudaStream_t st);
+size_t wsbm_zgemm_tc_batched_ws_bytes(const TcProduct* p, int nitems);
 // Synchronizes the stream and returns -5 (and clears the flag) if a bounded wait of the GEMM
 // kernel ran out since the last call, else 0 (-3 on a CUDA error).
 int wsbm_zgemm_tc_status(cudaStream_t st);

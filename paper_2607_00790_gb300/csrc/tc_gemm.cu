@@ -43,6 +43,7 @@
 #include <string.h>
 
 #include <mutex>
+#include <vector>
 
 #include "dense.h"
 
@@ -202,33 +203,45 @@ __device__ __forceinline__ void digits7(double v, int e, int* d) {
   d[0] = (int)X;
 }
 
-// Row exponents of A (m x k): one thread per row (coalesced along the column).
-__global__ void k_tc_row_exp(const double2* __restrict__ A, int64_t lda, int m, int k, int* __restrict__ rexp) {
+// One operand of a batched call, as the split kernels see it: source matrix, its sizes, its
+// first row in the plane tensor and the offset of its exponents.
+struct TcSrc {
+  const double2* M;
+  int64_t ld;
+  int rows, k;  // A: m x k (rows = m); B: k x n (rows = n columns of B)
+  int prow;     // first plane row (A: row offset; B': 2 x column offset)
+  int eoff;     // first exponent
+};
+
+// Row exponents of A (m x k): one thread per row (coalesced along the column); item blockIdx.y.
+__global__ void k_tc_row_exp(const TcSrc* __restrict__ src, int* __restrict__ rexp) {
+  const TcSrc q = src[blockIdx.y];
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= m) return;
+  if (i >= q.rows) return;
   uint64_t mx = 0;
-  for (int l = 0; l < k; ++l) {
-    const double2 v = A[i + (int64_t)l * lda];
+  for (int l = 0; l < q.k; ++l) {
+    const double2 v = q.M[i + (int64_t)l * q.ld];
     mx = max(mx, max(abs_bits(v.x), abs_bits(v.y)));
   }
-  rexp[i] = scale_exp(mx);
+  rexp[q.eoff + i] = scale_exp(mx);
 }
 
-// Digit planes of A: PA[t][i][2l + c] (c = 0: Re, 1: Im), rows of Ka BF16 values (zero beyond 2k).
-// Block: 32 rows x 32 complex columns, staged through shared memory so that both the reads
-// (along a column) and the writes (along a row) are contiguous.
-__global__ void __launch_bounds__(256) k_tc_split_a(const double2* __restrict__ A, int64_t lda, int m, int k,
-                                                    const int* __restrict__ rexp, __nv_bfloat16* __restrict__ PA,
-                                                    int64_t Ka) {
+// Digit planes of A: PA[t][row][2l + c] (c = 0: Re, 1: Im), rows of Ka BF16 values (zero
+// beyond 2k).  Block: 32 rows x 32 complex columns of item blockIdx.z, staged through shared
+// memory so that both the reads (along a column) and the writes (along a row) are contiguous.
+__global__ void __launch_bounds__(256) k_tc_split_a(const TcSrc* __restrict__ src, const int* __restrict__ rexp,
+                                                    __nv_bfloat16* __restrict__ PA, int64_t plane, int64_t Ka) {
   __shared__ __nv_bfloat16 s[TC_S][32][64 + 2];
+  const TcSrc q = src[blockIdx.z];
   const int i0 = blockIdx.x * 32, l0 = blockIdx.y * 32;
+  if (i0 >= q.rows) return;
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8
   for (int ll = ty; ll < 32; ll += 8) {
     const int i = i0 + tx, l = l0 + ll;
     int dr[TC_S], di[TC_S];
-    if (i < m && l < k) {
-      const double2 v = A[i + (int64_t)l * lda];
-      const int e = rexp[i];
+    if (i < q.rows && l < q.k) {
+      const double2 v = q.M[i + (int64_t)l * q.ld];
+      const int e = rexp[q.eoff + i];
       digits7(v.x, e, dr);
       digits7(v.y, e, di);
     } else {
@@ -243,25 +256,25 @@ __global__ void __launch_bounds__(256) k_tc_split_a(const double2* __restrict__ 
   }
   __syncthreads();
   // write: for each plane and row, 64 consecutive BF16 values (columns 2 l0 .. 2 l0 + 63)
-  const int64_t plane = (int64_t)m * Ka;
   for (int w = threadIdx.x; w < TC_S * 32 * 32; w += blockDim.x) {
     const int t = w / (32 * 32), r = (w / 32) % 32, c2 = w % 32;  // c2: pair of BF16 values
     const int i = i0 + r, kk = 2 * l0 + 2 * c2;
-    if (i >= m || kk >= Ka) continue;
+    if (i >= q.rows || kk >= Ka) continue;
     __nv_bfloat162 p;
     p.x = s[t][r][2 * c2];
     p.y = s[t][r][2 * c2 + 1];
-    *reinterpret_cast<__nv_bfloat162*>(PA + t * plane + (int64_t)i * Ka + kk) = p;
+    *reinterpret_cast<__nv_bfloat162*>(PA + t * plane + (int64_t)(q.prow + i) * Ka + kk) = p;
   }
 }
 
-// Column exponents of B (k x n): one warp per column.
-__global__ void k_tc_col_exp(const double2* __restrict__ B, int64_t ldb, int k, int n, int* __restrict__ cexp) {
+// Column exponents of B (k x n): one warp per column; item blockIdx.y.
+__global__ void k_tc_col_exp(const TcSrc* __restrict__ src, int* __restrict__ cexp) {
+  const TcSrc q = src[blockIdx.y];
   const int j = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32, lane = threadIdx.x & 31;
-  if (j >= n) return;
+  if (j >= q.rows) return;
   uint64_t mx = 0;
-  for (int l = lane; l < k; l += 32) {
-    const double2 v = B[l + (int64_t)j * ldb];
+  for (int l = lane; l < q.k; l += 32) {
+    const double2 v = q.M[l + (int64_t)j * q.ld];
     mx = max(mx, max(abs_bits(v.x), abs_bits(v.y)));
   }
 #pragma unroll
@@ -269,22 +282,23 @@ __global__ void k_tc_col_exp(const double2* __restrict__ B, int64_t ldb, int k, 
     const unsigned long long other = __shfl_xor_sync(0xFFFFFFFFu, (unsigned long long)mx, o);
     mx = max(mx, (uint64_t)other);
   }
-  if (lane == 0) cexp[j] = scale_exp(mx);
+  if (lane == 0) cexp[q.eoff + j] = scale_exp(mx);
 }
 
 // Digit planes of the real form of B: PB[u][2j][2l] = Re B_lj, PB[u][2j][2l+1] = -Im B_lj,
 // PB[u][2j+1][2l] = Im B_lj, PB[u][2j+1][2l+1] = Re B_lj (digits of; zero beyond 2k).
-// One thread per (l, j): reads along the column, writes along the rows.
-__global__ void __launch_bounds__(256) k_tc_split_b(const double2* __restrict__ B, int64_t ldb, int k, int n,
-                                                    const int* __restrict__ cexp, __nv_bfloat16* __restrict__ PB,
-                                                    int64_t Ka) {
+// One thread per (l, j): reads along the column, writes along the rows.  Column blockIdx.x of
+// item blockIdx.z.
+__global__ void __launch_bounds__(256) k_tc_split_b(const TcSrc* __restrict__ src, const int* __restrict__ cexp,
+                                                    __nv_bfloat16* __restrict__ PB, int64_t plane, int64_t Ka) {
+  const TcSrc q = src[blockIdx.z];
   const int j = blockIdx.x;
-  const int64_t plane = (int64_t)2 * n * Ka;
-  const int e = cexp[j];
+  if (j >= q.rows) return;
+  const int e = cexp[q.eoff + j];
   for (int l = blockIdx.y * blockDim.x + threadIdx.x; 2 * l < Ka; l += gridDim.y * blockDim.x) {
     int dr[TC_S], di[TC_S];
-    if (l < k) {
-      const double2 v = B[l + (int64_t)j * ldb];
+    if (l < q.k) {
+      const double2 v = q.M[l + (int64_t)j * q.ld];
       digits7(v.x, e, dr);
       digits7(v.y, e, di);
     } else {
@@ -298,7 +312,7 @@ __global__ void __launch_bounds__(256) k_tc_split_b(const double2* __restrict__ 
       re.y = __float2bfloat16_rn((float)-di[u]);
       im.x = __float2bfloat16_rn((float)di[u]);
       im.y = __float2bfloat16_rn((float)dr[u]);
-      __nv_bfloat16* row = PB + u * plane + (int64_t)(2 * j) * Ka + 2 * l;
+      __nv_bfloat16* row = PB + u * plane + (int64_t)(q.prow + 2 * j) * Ka + 2 * l;
       *reinterpret_cast<__nv_bfloat162*>(row) = re;
       *reinterpret_cast<__nv_bfloat162*>(row + Ka) = im;
     }
@@ -306,27 +320,48 @@ __global__ void __launch_bounds__(256) k_tc_split_b(const double2* __restrict__ 
 }
 
 // ------------------------------------------------------------------ the GEMM ----
-struct TcArgs {
-  int m, n, k;          // complex sizes
-  int tiles_m, tiles_n; // 128-row and 64-real-column tiles
-  int nkb;              // K blocks of TC_BK real values
-  double2 alpha, beta;
-  int sub;              // alpha = -1, beta = 1 (C -= A B): two FP64 additions per entry
+// One product of a batched call (C_i = beta C_i + alpha A_i B_i), as the GEMM kernel sees it.
+struct TcItem {
   double2* C;
   int64_t ldc;
+  int m, n;              // complex sizes of C_i
+  int arow, brow;        // first plane row of A_i's digits and of B_i's (2 x column offset)
+  int eoff_r, eoff_c;    // first row / column exponent
+  int tiles_m, tiles_n;  // its 128-row and 64-real-column tiles
+  int tile0;             // index of its first tile in the launch
+  int pad;
+};
+
+struct TcArgs {
+  int nitems, ntiles;
+  int nkb;              // K blocks of TC_BK real values (common to all items)
+  double2 alpha, beta;
+  int sub;              // alpha = -1, beta = 1 (C -= A B): two FP64 additions per entry
+  const TcItem* items;
   const int* rexp;
   const int* cexp;
 };
 
-// Tile t -> (tm, tn): groups of 8 row tiles, so that the CTAs running at the same time share
-// their A and B digit planes in L2.
-__device__ __forceinline__ void tile_coords(const TcArgs& a, int t, int& tm, int& tn) {
+// Item of launch tile t (binary search over the items' first tiles).
+__device__ __forceinline__ int find_item(const TcArgs& a, int t) {
+  int lo = 0, hi = a.nitems - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (a.items[mid].tile0 <= t) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+// Tile r of an item -> (tm, tn): groups of 8 row tiles, so that the CTAs running at the same
+// time share their A and B digit planes in L2.
+__device__ __forceinline__ void tile_coords(const TcItem& it, int r, int& tm, int& tn) {
   const int G = 8;
-  const int per_group = G * a.tiles_n;
-  const int g = t / per_group, r = t % per_group;
-  const int gm = min(G, a.tiles_m - g * G);
-  tm = g * G + r % gm;
-  tn = r / gm;
+  const int per_group = G * it.tiles_n;
+  const int g = r / per_group, q = r % per_group;
+  const int gm = min(G, it.tiles_m - g * G);
+  tm = g * G + q % gm;
+  tn = q / gm;
 }
 
 __global__ void __launch_bounds__(TC_THREADS, 1)
@@ -341,7 +376,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                  tempty = tfull + 8;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(gbase + TC_STAGES * TC_STAGE_BYTES + TC_FRAC_BYTES + 128);
   const int warp = threadIdx.x / 32, lane = threadIdx.x & 31;
-  const int ntiles = a.tiles_m * a.tiles_n;
+  const int ntiles = a.ntiles;
   const int nchunk_kb = TC_KC / TC_BK;
 
   if (threadIdx.x == 0) {
@@ -369,8 +404,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       uint32_t it = 0;
       bool ok = true;
       for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+        const TcItem item = a.items[find_item(a, t)];
         int tm, tn;
-        tile_coords(a, t, tm, tn);
+        tile_coords(item, t - item.tile0, tm, tn);
         for (int kb = 0; kb < a.nkb && ok; ++kb, ++it) {
           const uint32_t s = it % TC_STAGES, ph = (it / TC_STAGES) & 1;
           if (!(ok = mbar_wait(empty0 + 8 * s, ph ^ 1))) break;
@@ -379,8 +415,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           const uint32_t sa = base + s * TC_STAGE_BYTES, sb = sa + TC_S * TC_A_TILE;
 #pragma unroll
           for (int p = 0; p < TC_S; ++p) {
-            tma_load_3d(sa + p * TC_A_TILE, &mapA, full, kb * TC_BK, tm * TC_BM, p);
-            tma_load_3d(sb + p * TC_B_TILE, &mapB, full, kb * TC_BK, tn * TC_BN, p);
+            tma_load_3d(sa + p * TC_A_TILE, &mapA, full, kb * TC_BK, item.arow + tm * TC_BM, p);
+            tma_load_3d(sb + p * TC_B_TILE, &mapB, full, kb * TC_BK, item.brow + tn * TC_BN, p);
           }
         }
       }
@@ -437,8 +473,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     uint32_t chunk = 0;
     bool ok = true;
     for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+      const TcItem item = a.items[find_item(a, t)];
       int tm, tn;
-      tile_coords(a, t, tm, tn);
+      tile_coords(item, t - item.tile0, tm, tn);
       long long T[TC_BN / 2];
 #pragma unroll
       for (int c = 0; c < TC_BN / 2; ++c) {
@@ -494,17 +531,17 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       // C = beta C + alpha (T + F 2^-16) 2^(e_i + f_j - 48); the power of two enters through
       // the exponent field (integer pipe), so C -= A B costs one FMA and one add per value
       const int i = tm * TC_BM + row;
-      if (i < a.m) {
-        const int ei = a.rexp[i];
+      if (i < item.m) {
+        const int ei = a.rexp[item.eoff_r + i];
 #pragma unroll
         for (int c = 0; c < TC_BN / 4; ++c) {
           const int j = tn * (TC_BN / 2) + half * (TC_BN / 4) + c;
-          if (j >= a.n) continue;
-          const int ex = ei + a.cexp[j] - 48;
+          if (j >= item.n) continue;
+          const int ex = ei + a.cexp[item.eoff_c + j] - 48;
           const int* fp = frac + (half * (TC_BN / 2) + 2 * c) * TC_BM + row;
           const double xr = scale2(fma((double)fp[0], 1.0 / 65536.0, (double)T[2 * c]), ex);
           const double xi = scale2(fma((double)fp[TC_BM], 1.0 / 65536.0, (double)T[2 * c + 1]), ex);
-          double2* p = a.C + i + (int64_t)j * a.ldc;
+          double2* p = item.C + i + (int64_t)j * item.ldc;
           if (a.sub) {
             const double2 o = *p;
             *p = make_double2(o.x - xr, o.y - xi);
@@ -550,12 +587,44 @@ static EncodeTiledFn encode_fn() {
 
 static int64_t tc_ka(int k) { return ((int64_t)2 * k + TC_BK - 1) / TC_BK * TC_BK; }
 
-size_t wsbm_zgemm_tc_ws_bytes(int m, int n, int k) {
-  const int64_t Ka = tc_ka(k);
-  size_t b = (size_t)TC_S * ((size_t)m + 2 * (size_t)n) * Ka * 2;  // digit planes
+// Work space of a batched call: digit planes (rows of A and B' of all items, padded each to a
+// multiple of 16 rows), exponents, and the three item tables.
+static size_t tc_ws_layout(const TcProduct* p, int nitems, int kmax, int64_t* arows, int64_t* brows,
+                           size_t* off_exp, size_t* off_tab) {
+  int64_t ra = 0, rb = 0, ne = 0;
+  for (int i = 0; i < nitems; ++i) {
+    ra += (p[i].m + 15) / 16 * 16;
+    rb += (2 * (int64_t)p[i].n + 15) / 16 * 16;
+    ne += p[i].m + p[i].n;
+  }
+  const int64_t Ka = tc_ka(kmax);
+  size_t b = (size_t)TC_S * (size_t)(ra + rb) * (size_t)Ka * 2;
   b = (b + 255) & ~(size_t)255;
-  b += ((size_t)m + n) * sizeof(int) + 256;  // exponents
+  *off_exp = b;
+  b += (size_t)ne * sizeof(int);
+  b = (b + 255) & ~(size_t)255;
+  *off_tab = b;
+  b += (size_t)nitems * (sizeof(TcItem) + 2 * sizeof(TcSrc)) + 256;
+  *arows = ra;
+  *brows = rb;
   return b;
+}
+
+size_t wsbm_zgemm_tc_batched_ws_bytes(const TcProduct* p, int nitems) {
+  int kmax = 1;
+  for (int i = 0; i < nitems; ++i) kmax = p[i].k > kmax ? p[i].k : kmax;
+  int64_t ra, rb;
+  size_t oe, ot;
+  return tc_ws_layout(p, nitems, kmax, &ra, &rb, &oe, &ot);
+}
+
+size_t wsbm_zgemm_tc_ws_bytes(int m, int n, int k) {
+  TcProduct p;
+  memset(&p, 0, sizeof(p));
+  p.m = m;
+  p.n = n;
+  p.k = k;
+  return wsbm_zgemm_tc_batched_ws_bytes(&p, 1);
 }
 
 // 3-D map over the digit planes [TC_S][rows][Ka] with boxes of TC_BK x box_rows x 1.
@@ -572,47 +641,107 @@ static int make_map(CUtensorMap* map, void* planes, int64_t rows, int64_t Ka, in
   return r == CUDA_SUCCESS ? 0 : -3;
 }
 
+int wsbm_zgemm_tc_batched(const TcProduct* p, int nitems, double2 alpha, double2 beta, void* ws, cudaStream_t st) {
+  if (nitems <= 0) return 0;
+  if (!p || !ws || ((uintptr_t)ws & 255) != 0) return -1;
+  int kmax = 1, maxm = 0, maxn = 0;
+  for (int i = 0; i < nitems; ++i) {
+    const TcProduct& q = p[i];
+    if (q.m < 0 || q.n < 0 || q.k < 1 || q.k > 32768) return -1;
+    if (q.m > 0 && q.n > 0 && (!q.A || !q.B || !q.C || q.lda < q.m || q.ldb < q.k || q.ldc < q.m)) return -1;
+    kmax = q.k > kmax ? q.k : kmax;
+    maxm = q.m > maxm ? q.m : maxm;
+    maxn = q.n > maxn ? q.n : maxn;
+  }
+  if (nitems > 65535) return -1;
+  int64_t ra, rb;
+  size_t off_exp, off_tab;
+  tc_ws_layout(p, nitems, kmax, &ra, &rb, &off_exp, &off_tab);
+  const int64_t Ka = tc_ka(kmax);
+  __nv_bfloat16* PA = (__nv_bfloat16*)ws;
+  __nv_bfloat16* PB = PA + (size_t)TC_S * ra * Ka;
+  int* exps = (int*)((char*)ws + off_exp);
+  // item tables (host staging, copied in stream order before the launches that read them)
+  std::vector<unsigned char> tab((size_t)nitems * (sizeof(TcItem) + 2 * sizeof(TcSrc)));
+  TcItem* items = (TcItem*)tab.data();
+  TcSrc* sa = (TcSrc*)(tab.data() + (size_t)nitems * sizeof(TcItem));
+  TcSrc* sb = sa + nitems;
+  int64_t arow = 0, brow = 0, eo = 0;
+  int tiles = 0;
+  for (int i = 0; i < nitems; ++i) {
+    const TcProduct& q = p[i];
+    TcItem& it = items[i];
+    it.C = q.C;
+    it.ldc = q.ldc;
+    it.m = q.m;
+    it.n = q.n;
+    it.arow = (int)arow;
+    it.brow = (int)brow;
+    it.eoff_r = (int)eo;
+    it.eoff_c = (int)(eo + q.m);
+    it.tiles_m = (q.m + TC_BM - 1) / TC_BM;
+    it.tiles_n = (2 * q.n + TC_BN - 1) / TC_BN;
+    if (q.m == 0 || q.n == 0) it.tiles_m = it.tiles_n = 0;
+    it.tile0 = tiles;
+    it.pad = 0;
+    tiles += it.tiles_m * it.tiles_n;
+    sa[i] = {q.A, q.lda, q.m, q.k, (int)arow, (int)eo};
+    sb[i] = {q.B, q.ldb, q.n, q.k, (int)brow, (int)(eo + q.m)};
+    arow += (q.m + 15) / 16 * 16;
+    brow += (2 * (int64_t)q.n + 15) / 16 * 16;
+    eo += q.m + q.n;
+  }
+  if (ra >= INT32_MAX || rb >= INT32_MAX) return -1;
+  if (tiles == 0) return 0;
+  unsigned char* dtab = (unsigned char*)ws + off_tab;
+  if (cudaMemcpyAsync(dtab, tab.data(), tab.size(), cudaMemcpyHostToDevice, st) != cudaSuccess) return -3;
+  const TcItem* ditems = (const TcItem*)dtab;
+  const TcSrc* dsa = (const TcSrc*)(dtab + (size_t)nitems * sizeof(TcItem));
+  const TcSrc* dsb = dsa + nitems;
+  // digit planes (the padding rows between items are never read into a stored output)
+  k_tc_row_exp<<<dim3((maxm + 127) / 128, nitems), 128, 0, st>>>(dsa, exps);
+  k_tc_split_a<<<dim3((maxm + 31) / 32, (unsigned)((Ka / 2 + 31) / 32), nitems), 256, 0, st>>>(
+      dsa, exps, PA, (int64_t)ra * Ka, Ka);
+  k_tc_col_exp<<<dim3((maxn + 7) / 8, nitems), 256, 0, st>>>(dsb, exps);
+  k_tc_split_b<<<dim3(maxn, (unsigned)((Ka / 2 + 255) / 256), nitems), 256, 0, st>>>(
+      dsb, exps, PB, (int64_t)rb * Ka, Ka);
+  wsbm_count_launches(4);
+  CUtensorMap ma, mb;
+  if (make_map(&ma, PA, ra, Ka, TC_BM) || make_map(&mb, PB, rb, Ka, TC_BN)) return -3;
+  TcArgs a;
+  a.nitems = nitems;
+  a.ntiles = tiles;
+  a.nkb = (int)(Ka / TC_BK);
+  a.alpha = alpha;
+  a.beta = beta;
+  a.sub = alpha.x == -1.0 && alpha.y == 0.0 && beta.x == 1.0 && beta.y == 0.0;
+  a.items = ditems;
+  a.rexp = exps;
+  a.cexp = exps;
+  if (wsbm_smem_optin((const void*)k_zgemm_tc, TC_SMEM) != cudaSuccess) return -3;
+  const int grid = tiles < wsbm_sm_count() ? tiles : wsbm_sm_count();
+  k_zgemm_tc<<<grid, TC_THREADS, TC_SMEM, st>>>(ma, mb, a);
+  wsbm_count_launch();
+  return cudaGetLastError() == cudaSuccess ? 0 : -3;
+}
+
 int wsbm_zgemm_tc(int m, int n, int k, double2 alpha, const double2* A, int64_t lda, const double2* B,
                   int64_t ldb, double2 beta, double2* C, int64_t ldc, void* ws, cudaStream_t st) {
   if (m < 0 || n < 0 || k < 0) return -1;
   if (m == 0 || n == 0) return 0;
   if (k < 1 || k > 32768) return -1;  // the 64-bit recombination is sized for K_real <= 65536
-  if (!A || !B || !C || !ws || lda < m || ldb < k || ldc < m) return -1;
-  if (((uintptr_t)ws & 255) != 0) return -1;
-  const int64_t Ka = tc_ka(k);
-  __nv_bfloat16* PA = (__nv_bfloat16*)ws;
-  __nv_bfloat16* PB = PA + (size_t)TC_S * m * Ka;
-  size_t off = ((size_t)TC_S * ((size_t)m + 2 * (size_t)n) * Ka * 2 + 255) & ~(size_t)255;
-  int* rexp = (int*)((char*)ws + off);
-  int* cexp = rexp + m;
-  // digit planes (k = 0: all-zero planes, C = beta C)
-  k_tc_row_exp<<<(m + 127) / 128, 128, 0, st>>>(A, lda, m, k, rexp);
-  k_tc_split_a<<<dim3((m + 31) / 32, (unsigned)((Ka / 2 + 31) / 32)), 256, 0, st>>>(A, lda, m, k, rexp, PA, Ka);
-  k_tc_col_exp<<<(n + 7) / 8, 256, 0, st>>>(B, ldb, k, n, cexp);
-  k_tc_split_b<<<dim3(n, (unsigned)((Ka / 2 + 255) / 256)), 256, 0, st>>>(B, ldb, k, n, cexp, PB, Ka);
-  wsbm_count_launches(4);
-  CUtensorMap ma, mb;
-  if (make_map(&ma, PA, m, Ka, TC_BM) || make_map(&mb, PB, 2 * (int64_t)n, Ka, TC_BN)) return -3;
-  TcArgs a;
-  a.m = m;
-  a.n = n;
-  a.k = k;
-  a.tiles_m = (m + TC_BM - 1) / TC_BM;
-  a.tiles_n = (2 * n + TC_BN - 1) / TC_BN;
-  a.nkb = (int)(Ka / TC_BK);
-  a.alpha = alpha;
-  a.beta = beta;
-  a.sub = alpha.x == -1.0 && alpha.y == 0.0 && beta.x == 1.0 && beta.y == 0.0;
-  a.C = C;
-  a.ldc = ldc;
-  a.rexp = rexp;
-  a.cexp = cexp;
-  if (wsbm_smem_optin((const void*)k_zgemm_tc, TC_SMEM) != cudaSuccess) return -3;
-  const int ntiles = a.tiles_m * a.tiles_n;
-  const int grid = ntiles < wsbm_sm_count() ? ntiles : wsbm_sm_count();
-  k_zgemm_tc<<<grid, TC_THREADS, TC_SMEM, st>>>(ma, mb, a);
-  wsbm_count_launch();
-  return cudaGetLastError() == cudaSuccess ? 0 : -3;
+  TcProduct p;
+  p.A = A;
+  p.lda = lda;
+  p.B = B;
+  p.ldb = ldb;
+  p.C = C;
+  p.ldc = ldc;
+  p.m = m;
+  p.n = n;
+  p.k = k;
+  p.pad = 0;
+  return wsbm_zgemm_tc_batched(&p, 1, alpha, beta, ws, st);
 }
 
 // Error flag of the bounded waits: returns it and clears it (synchronizes the stream).

@@ -121,3 +121,44 @@ def test_lu_dense_factors_and_solves(n):
     x = np.linalg.solve(U, np.linalg.solve(L, Pb))
     ref = np.linalg.solve(A, b)
     assert np.linalg.norm(x - ref) <= 1e-11 * np.linalg.norm(ref)
+
+
+def test_zgemm_batched_items_of_different_sizes():
+    """One launch over 37 products of different shapes (empty ones, ragged edges, k from 1 to
+    200 padded to the largest, leading dimensions above the row counts): each C_i against
+    numpy's FP64 product at the same bound."""
+    import torch
+    from paper_2607_00790_gb300 import binding
+    rng = np.random.default_rng(11)
+    As, Bs, Cs, refs, hostA, hostB = [], [], [], [], [], []
+    for i in range(37):
+        m = int(rng.integers(0, 300)) if i % 9 else 0
+        n = int(rng.integers(1, 100)) if i % 11 else 0
+        k = int(rng.integers(1, 200))
+        A = rand_c(rng, (m, k)) * 10.0 ** rng.uniform(-2, 2, size=(m, 1))
+        B = rand_c(rng, (k, n)) * 10.0 ** rng.uniform(-2, 2, size=(1, n))
+        C0 = rand_c(rng, (m, n))
+        lda, ldc = m + 3, m + 5
+        tA = torch.zeros((k, lda), dtype=torch.complex128, device="cuda").T[:m]
+        tA.copy_(torch.as_tensor(A))
+        tB = torch.as_tensor(B, device="cuda").T.contiguous().T
+        tC = torch.zeros((n, ldc), dtype=torch.complex128, device="cuda").T[:m]
+        tC.copy_(torch.as_tensor(C0))
+        As.append(tA)
+        Bs.append(tB)
+        Cs.append(tC)
+        refs.append(C0 - A @ B)
+        hostA.append(A)
+        hostB.append(B)
+    binding.wsbm_zgemm_batched(As, Bs, Cs, alpha=-1.0, beta=1.0)
+    torch.cuda.synchronize()
+    for i in range(37):
+        got = Cs[i].cpu().numpy()
+        if got.size == 0:
+            continue
+        A, B = hostA[i], hostB[i]
+        k = A.shape[1]
+        ra = np.maximum(np.abs(A.real), np.abs(A.imag)).max(axis=1)
+        cb = np.maximum(np.abs(B.real), np.abs(B.imag)).max(axis=0)
+        bound = 4 * EPS * 2 * k * ra[:, None] * cb[None, :] + 8 * EPS * np.abs(refs[i])
+        assert np.all(np.abs(got - refs[i]) <= bound), i
