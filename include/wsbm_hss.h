@@ -130,10 +130,12 @@ typedef struct {
   int64_t sketch_matrices;     /* ID matrices replaced by their sketch                */
   int64_t sketch_fallbacks;    /* sketched sides redone on the full matrix            */
   double ms_sketch;            /* device time of the sketch launches                  */
-  double ms_lu;                /* device time of the fused LU + solve launches (box
-                                  LU with D^-1 L, and Dhat), summed over the levels    */
+  double ms_lu;                /* device time of the box factors' LU + solve launches
+                                  (LU with D^-1 L, and Dhat), summed over the levels   */
   double lu_flops;             /* their algorithmic FP64 flops                        */
   int64_t lu_matrices;         /* matrices they factored                              */
+  int64_t lu_tc_matrices;      /* of these, factored by the batched LU whose products
+                                  run on the tensor cores (the rest: fused FP64 kernel) */
 } wsbm_stats_t;
 
 typedef struct wsbm_hss* wsbm_hss_t;

@@ -58,7 +58,8 @@ class Stats(ctypes.Structure):
                 ("cpqr_matrices", ctypes.c_int64), ("cpqr_flops", ctypes.c_double),
                 ("sketch_matrices", ctypes.c_int64), ("sketch_fallbacks", ctypes.c_int64),
                 ("ms_sketch", ctypes.c_double), ("ms_lu", ctypes.c_double),
-                ("lu_flops", ctypes.c_double), ("lu_matrices", ctypes.c_int64)]
+                ("lu_flops", ctypes.c_double), ("lu_matrices", ctypes.c_int64),
+                ("lu_tc_matrices", ctypes.c_int64)]
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_ if k != "rank_per_level"}

@@ -9,6 +9,8 @@
 #include <math.h>
 
 #include <algorithm>
+#include <cstring>
+#include <vector>
 
 #include "dense.h"
 
@@ -1250,5 +1252,192 @@ int wsbm_lu_big(double2* A, int64_t lda, int n, int* piv, int* d_info, void* ws,
     }
   }
   // (the tensor-core kernel's timeout flag is read by the caller through wsbm_zgemm_tc_status)
+  return cudaGetLastError() == cudaSuccess ? 0 : -3;
+}
+
+// ----------------------------------------------- batched LU + solve on the tensor cores ----
+// The box factors of a level (LU(D) with D^-1 L, and Dhat = M^-1) as a blocked right-looking LU
+// with LUT_NB-column panels over every box of the batch at once: per panel, the panel is
+// factored with partial pivoting on the FP64 pipe (k_lu_panel, one CTA per matrix), its row
+// swaps are applied to the rest of A and to B, U12 = L11^-1 A12 (and L11^-1 B12) and the
+// trailing update A22 -= L21 U12 (B22 likewise) run as batched products on the tensor cores
+// (wsbm_zgemm_tc_batched, two items per box: the A part and the B part), with L11^-1 formed
+// explicitly per box.  The back substitution X = U^-1 B runs by panels from the bottom:
+// X_p = U_pp^-1 X_p and X_{<p} -= U_{<p,p} X_p, again as batched tensor-core products.
+// Same factors (L unit lower, U, piv[j] = the row swapped with row j) and solution as
+// k_lu_solve_fused, to rounding; pivoting by |a|^2 (k_lu_panel).
+#define LUT_NB 64
+
+// Apply the swaps piv[j0 .. je) to the columns of A outside [j0, je) and to every column of B.
+__global__ void k_lut_swap(const LuSolveDesc* __restrict__ d, int j0, int jb) {
+  const LuSolveDesc q = d[blockIdx.y];
+  if (j0 >= q.n) return;
+  const int je = min(j0 + jb, q.n), nc = q.n + q.nrhs;
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < nc; c += gridDim.x * blockDim.x) {
+    if (c >= j0 && c < je) continue;
+    double2* col = c < q.n ? q.A + (int64_t)c * q.lda : q.B + (int64_t)(c - q.n) * q.ldb;
+    for (int j = j0; j < je; ++j) {
+      const int p = q.piv[j];
+      if (p != j) {
+        const double2 t = col[j];
+        col[j] = col[p];
+        col[p] = t;
+      }
+    }
+  }
+}
+
+// X = inverse of the unit lower (upper = 0) or of the upper (upper = 1, non-unit) triangle of
+// the diagonal block A[j0 : j0+jb, j0 : j0+jb] of item blockIdx.y; X: jb x jb (ld jb) at
+// X + blockIdx.y * ldx_item.  One thread per column j: x_ij from the rows before (lower) or
+// after (upper) it.
+__global__ void k_lut_trinv(const LuSolveDesc* __restrict__ d, int j0, int jb, int upper,
+                            double2* __restrict__ Xall, int64_t ldx_item) {
+  const LuSolveDesc q = d[blockIdx.y];
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j0 >= q.n) return;
+  const int b = min(jb, q.n - j0);
+  if (j >= b) return;
+  double2* x = Xall + blockIdx.y * ldx_item + (int64_t)j * b;
+  const double2* T = q.A + j0 + (int64_t)j0 * q.lda;
+  const double2 one = make_double2(1.0, 0.0), zero = make_double2(0.0, 0.0);
+  if (!upper) {
+    for (int i = 0; i < j; ++i) x[i] = zero;
+    x[j] = one;
+    for (int i = j + 1; i < b; ++i) {
+      double2 s = zero;
+      for (int t = j; t < i; ++t) s = cfms(T[i + (int64_t)t * q.lda], x[t], s);
+      x[i] = s;
+    }
+  } else {
+    for (int i = j + 1; i < b; ++i) x[i] = zero;
+    const double2 djj = T[j + (int64_t)j * q.lda];
+    x[j] = (djj.x == 0.0 && djj.y == 0.0) ? zero : cdiv(one, djj);
+    for (int i = j - 1; i >= 0; --i) {
+      double2 s = zero;
+      for (int t = i + 1; t <= j; ++t) s = cfms(T[i + (int64_t)t * q.lda], x[t], s);
+      const double2 dii = T[i + (int64_t)i * q.lda];
+      x[i] = (dii.x == 0.0 && dii.y == 0.0) ? zero : cdiv(s, dii);
+    }
+  }
+}
+
+size_t wsbm_lu_solve_tc_ws_bytes(const LuSolveDesc* h, int nbatch) {
+  // the largest product step: two items per box (A part and B part) of the first panel
+  std::vector<TcProduct> p;
+  p.reserve(2 * (size_t)nbatch);
+  int maxn = 0;
+  for (int i = 0; i < nbatch; ++i) {
+    TcProduct a;
+    memset(&a, 0, sizeof(a));
+    a.m = h[i].n;
+    a.n = h[i].n;
+    a.k = LUT_NB;
+    p.push_back(a);
+    a.n = h[i].nrhs > 0 ? h[i].nrhs : 1;
+    p.push_back(a);
+    maxn = std::max(maxn, h[i].n);
+  }
+  size_t b = wsbm_zgemm_tc_batched_ws_bytes(p.data(), (int)p.size());
+  b = (b + 255) & ~(size_t)255;
+  b += (size_t)nbatch * LUT_NB * LUT_NB * sizeof(double2) + 256;  // diagonal-block inverses
+  return b;
+}
+
+int wsbm_lu_solve_tc_batched(const LuSolveDesc* h, const LuSolveDesc* d, int nbatch, const LuDesc* d_lu,
+                             void* ws, cudaStream_t st) {
+  if (nbatch <= 0) return 0;
+  if (nbatch > 32767 || !h || !d || !d_lu || !ws) return -1;
+  int maxn = 0, maxnc = 0;
+  for (int i = 0; i < nbatch; ++i) {
+    maxn = std::max(maxn, h[i].n);
+    maxnc = std::max(maxnc, h[i].n + h[i].nrhs);
+  }
+  size_t off = wsbm_zgemm_tc_ws_bytes(1, 1, 1);  // recomputed below for the actual products
+  {
+    std::vector<TcProduct> p(2 * (size_t)nbatch);
+    for (int i = 0; i < nbatch; ++i) {
+      memset(&p[2 * i], 0, 2 * sizeof(TcProduct));
+      p[2 * i].m = p[2 * i + 1].m = h[i].n;
+      p[2 * i].n = h[i].n;
+      p[2 * i + 1].n = h[i].nrhs > 0 ? h[i].nrhs : 1;
+      p[2 * i].k = p[2 * i + 1].k = LUT_NB;
+    }
+    off = (wsbm_zgemm_tc_batched_ws_bytes(p.data(), (int)p.size()) + 255) & ~(size_t)255;
+  }
+  double2* X = (double2*)((char*)ws + off);  // LUT_NB x LUT_NB per box
+  const int64_t ldx = (int64_t)LUT_NB * LUT_NB;
+  const double2 one = make_double2(1.0, 0.0), mone = make_double2(-1.0, 0.0), zero = make_double2(0.0, 0.0);
+  std::vector<TcProduct> items;
+  items.reserve(2 * (size_t)nbatch);
+  auto run = [&](double2 alpha, double2 beta) -> int {
+    if (items.empty()) return 0;
+    int rc = wsbm_zgemm_tc_batched(items.data(), (int)items.size(), alpha, beta, ws, st);
+    items.clear();
+    return rc;
+  };
+  auto add = [&](const double2* A, int64_t lda, const double2* B, int64_t ldb, double2* C, int64_t ldc, int m,
+                 int n, int k) {
+    if (m <= 0 || n <= 0 || k <= 0) return;
+    TcProduct t;
+    t.A = A;
+    t.lda = lda;
+    t.B = B;
+    t.ldb = ldb;
+    t.C = C;
+    t.ldc = ldc;
+    t.m = m;
+    t.n = n;
+    t.k = k;
+    t.pad = 0;
+    items.push_back(t);
+  };
+  // ---- factorization
+  for (int j0 = 0; j0 < maxn; j0 += LUT_NB) {
+    k_lu_panel<<<nbatch, 256, 0, st>>>(d_lu, j0, LUT_NB, nullptr);
+    k_lut_swap<<<dim3(tiles_x((maxnc + 127) / 128), nbatch), 128, 0, st>>>(d, j0, LUT_NB);
+    k_lut_trinv<<<dim3(1, nbatch), LUT_NB, 0, st>>>(d, j0, LUT_NB, 0, X, ldx);
+    wsbm_count_launches(3);
+    // U12 = L11^-1 [A12 | B1]  (in place: the digit planes are formed before C is written)
+    for (int i = 0; i < nbatch; ++i) {
+      const LuSolveDesc& q = h[i];
+      if (j0 >= q.n) continue;
+      const int jb = std::min(LUT_NB, q.n - j0), je = j0 + jb;
+      const double2* Li = X + i * ldx;
+      add(Li, jb, q.A + j0 + (int64_t)je * q.lda, q.lda, q.A + j0 + (int64_t)je * q.lda, q.lda, jb, q.n - je, jb);
+      add(Li, jb, q.B + j0, q.ldb, q.B + j0, q.ldb, jb, q.nrhs, jb);
+    }
+    if (int rc = run(one, zero)) return rc;
+    // A22 -= L21 U12, B2 -= L21 U12_B
+    for (int i = 0; i < nbatch; ++i) {
+      const LuSolveDesc& q = h[i];
+      if (j0 >= q.n) continue;
+      const int jb = std::min(LUT_NB, q.n - j0), je = j0 + jb;
+      const double2* L21 = q.A + je + (int64_t)j0 * q.lda;
+      add(L21, q.lda, q.A + j0 + (int64_t)je * q.lda, q.lda, q.A + je + (int64_t)je * q.lda, q.lda, q.n - je,
+          q.n - je, jb);
+      add(L21, q.lda, q.B + j0, q.ldb, q.B + je, q.ldb, q.n - je, q.nrhs, jb);
+    }
+    if (int rc = run(mone, one)) return rc;
+  }
+  // ---- back substitution X = U^-1 (L^-1 P B), panels from the bottom
+  for (int j0 = ((maxn - 1) / LUT_NB) * LUT_NB; j0 >= 0; j0 -= LUT_NB) {
+    k_lut_trinv<<<dim3(1, nbatch), LUT_NB, 0, st>>>(d, j0, LUT_NB, 1, X, ldx);
+    wsbm_count_launch();
+    for (int i = 0; i < nbatch; ++i) {
+      const LuSolveDesc& q = h[i];
+      if (j0 >= q.n) continue;
+      const int jb = std::min(LUT_NB, q.n - j0);
+      add(X + i * ldx, jb, q.B + j0, q.ldb, q.B + j0, q.ldb, jb, q.nrhs, jb);
+    }
+    if (int rc = run(one, zero)) return rc;
+    for (int i = 0; i < nbatch; ++i) {
+      const LuSolveDesc& q = h[i];
+      if (j0 >= q.n || j0 == 0) continue;
+      const int jb = std::min(LUT_NB, q.n - j0);
+      add(q.A + (int64_t)j0 * q.lda, q.lda, q.B + j0, q.ldb, q.B, q.ldb, j0, q.nrhs, jb);
+    }
+    if (int rc = run(mone, one)) return rc;
+  }
   return cudaGetLastError() == cudaSuccess ? 0 : -3;
 }

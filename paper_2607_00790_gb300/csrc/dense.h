@@ -111,6 +111,12 @@ int64_t wsbm_lu_solve_ldr(int n, int nrhs);
 // Returns -1 (nothing launched) when max_n exceeds WSBM_LUS_MAXN.
 int wsbm_lu_solve_fused_batched(const LuSolveDesc* d_desc, int nbatch, int max_n, int max_nc,
                                 cudaStream_t st);
+// The same factorization and solve with the products on the tensor cores (tc_gemm.cu):
+// h: host copy of the descriptors (S unused), d: device copy, d_lu: device LuDesc {A, lda, piv, n}
+// per item.  ws: 256-byte aligned, wsbm_lu_solve_tc_ws_bytes(h, nbatch) bytes.  Enqueues only.
+int wsbm_lu_solve_tc_batched(const LuSolveDesc* h, const LuSolveDesc* d, int nbatch, const LuDesc* d_lu,
+                             void* ws, cudaStream_t st);
+size_t wsbm_lu_solve_tc_ws_bytes(const LuSolveDesc* h, int nbatch);
 
 int wsbm_gemm_batched(const GemmDesc* d_desc, int nbatch, int max_m, int max_n, cudaStream_t st);
 int wsbm_lu_batched(const LuDesc* d_desc, int nbatch, int max_n, int* d_info, cudaStream_t st);

@@ -40,6 +40,11 @@
 #ifndef WSBM_SKETCH_PAD
 #define WSBM_SKETCH_PAD 0
 #endif
+// Boxes of at least this many unknowns (and at most WSBM_LUS_MAXN) are factored by the batched
+// LU whose products run on the tensor cores; smaller ones by the fused FP64 kernel.
+#ifndef WSBM_LU_TC_MIN
+#define WSBM_LU_TC_MIN 128
+#endif
 // Dense roots of at least this order are factored by the LU whose trailing updates run on
 // the tensor cores (wsbm_lu_big); smaller ones by the batched FP64 blocked LU.
 #ifndef WSBM_BIGLU_MIN
@@ -828,7 +833,7 @@ static double lu_solve_flops(double n, double nrhs) {
 
 static int factor_levels(const std::vector<wsbm_hss*>& hs, const std::vector<int>& levels,
                          double ms_out[5], int64_t* cpqr_mats, double* cpqr_flops,
-                         int64_t sketch_out[2], double* sketch_ms, double lu_out[3]) {
+                         int64_t sketch_out[2], double* sketch_ms, double lu_out[4]) {
   wsbm_hss* h0 = hs[0];
   cudaStream_t st = h0->st;
   pin_reset(st);  // the previous level ended with the stream synchronized
@@ -1338,9 +1343,13 @@ static int factor_levels(const std::vector<wsbm_hss*>& hs, const std::vector<int
   HK(upload(h0, idd, &didd, tmp));
   int64_t maxnk = 0;
   for (int r = 0; r < NB; ++r) maxnk = std::max(maxnk, (int64_t)R[r].box().n * R[r].box().k);
-  // LU(D) with Z = D^-1 L, and LU(M) with Dhat = M^-1, in the fused kernel when [D | L] fits it
-  // (one scratch serves both launches), else blocked LU and triangular solves
+  // LU(D) with Z = D^-1 L, and LU(M) with Dhat = M^-1: for boxes of WSBM_LU_TC_MIN unknowns or
+  // more by the batched LU whose products run on the tensor cores, else in the fused kernel when
+  // [D | L] fits it (one scratch serves both launches), else blocked LU and triangular solves
   LuSolveDesc *dfz = nullptr, *dfm = nullptr;
+  std::vector<LuSolveDesc> fz, fm;
+  const bool lu_tc = maxn >= WSBM_LU_TC_MIN && maxn <= WSBM_LUS_MAXN && NB <= 32767;
+  void* wstc = nullptr;
   if (maxn <= WSBM_LUS_MAXN) {
     size_t sz = 0, sm = 0;
     for (int r = 0; r < NB; ++r) {
@@ -1349,8 +1358,9 @@ static int factor_levels(const std::vector<wsbm_hss*>& hs, const std::vector<int
       sm += (size_t)B.k * wsbm_lu_solve_ldr(B.k, B.k);
     }
     double2* Sc = nullptr;
-    HK(dalloc(h0, std::max(sz, sm) * sizeof(double2), (void**)&Sc, tmp));
-    std::vector<LuSolveDesc> fz(NB), fm(NB);
+    if (!lu_tc) HK(dalloc(h0, std::max(sz, sm) * sizeof(double2), (void**)&Sc, tmp));
+    fz.resize(NB);
+    fm.resize(NB);
     size_t oz = 0, om = 0;
     for (int r = 0; r < NB; ++r) {
       const Box& B = R[r].box();
@@ -1361,11 +1371,23 @@ static int factor_levels(const std::vector<wsbm_hss*>& hs, const std::vector<int
     }
     HK(upload(h0, fz, &dfz, tmp));
     HK(upload(h0, fm, &dfm, tmp));
+    if (lu_tc) {
+      size_t wb = std::max(wsbm_lu_solve_tc_ws_bytes(fz.data(), NB), wsbm_lu_solve_tc_ws_bytes(fm.data(), NB));
+      std::vector<TcProduct> gp(gm.size());
+      for (size_t g = 0; g < gm.size(); ++g)
+        gp[g] = {gm[g].A, gm[g].lda, gm[g].B, gm[g].ldb, gm[g].C, gm[g].ldc, gm[g].m, gm[g].n, gm[g].k, 0};
+      if (!gp.empty()) wb = std::max(wb, wsbm_zgemm_tc_batched_ws_bytes(gp.data(), (int)gp.size()));
+      HK(dalloc(h0, wb, &wstc, tmp));
+    }
   }
   launch_y(k_build_L, gridfor(maxnk), NB, dbl, st);
   if (dfz) {
     HC(cudaEventRecord(h0->ev[8], st));
-    HK(wsbm_lu_solve_fused_batched(dfz, NB, maxn, maxn + maxk, st));
+    if (lu_tc) {
+      if (wsbm_lu_solve_tc_batched(fz.data(), dfz, NB, dluD, wstc, st)) return WSBM_ERR_CUDA;
+    } else {
+      HK(wsbm_lu_solve_fused_batched(dfz, NB, maxn, maxn + maxk, st));
+    }
     HC(cudaEventRecord(h0->ev[9], st));
   } else {
     HK(wsbm_lu_batched(dluD, NB, maxn, nullptr, st));
@@ -1373,14 +1395,29 @@ static int factor_levels(const std::vector<wsbm_hss*>& hs, const std::vector<int
   }
   launch_y(k_gather_rows, gridfor(maxnk), NB, dgz, st);
   launch_y(k_copy2d, gridfor((int64_t)maxk * maxk), NB, dpc, st);
-  if (!gm.empty()) HK(wsbm_gemm_batched(dgm, (int)gm.size(), maxk, maxk, st));
+  if (!gm.empty()) {
+    if (lu_tc) {  // M += Tc Zg[k:n] on the tensor cores
+      std::vector<TcProduct> gp(gm.size());
+      for (size_t g = 0; g < gm.size(); ++g)
+        gp[g] = {gm[g].A, gm[g].lda, gm[g].B, gm[g].ldb, gm[g].C, gm[g].ldc, gm[g].m, gm[g].n, gm[g].k, 0};
+      if (wsbm_zgemm_tc_batched(gp.data(), (int)gp.size(), make_double2(1.0, 0.0), make_double2(1.0, 0.0),
+                                wstc, st))
+        return WSBM_ERR_CUDA;
+    } else {
+      HK(wsbm_gemm_batched(dgm, (int)gm.size(), maxk, maxk, st));
+    }
+  }
   if (!tcc.empty()) {
     launch_y(k_copy2d, gridfor(maxnk), (int64_t)tcc.size(), dtcc, st);
   }
   launch_y(k_fill_identity_batched, gridfor((int64_t)maxk * maxk), NB, didd, st);
   if (dfm) {
     HC(cudaEventRecord(h0->ev[10], st));
-    HK(wsbm_lu_solve_fused_batched(dfm, NB, maxk, 2 * maxk, st));
+    if (lu_tc) {
+      if (wsbm_lu_solve_tc_batched(fm.data(), dfm, NB, dluM, wstc, st)) return WSBM_ERR_CUDA;
+    } else {
+      HK(wsbm_lu_solve_fused_batched(dfm, NB, maxk, 2 * maxk, st));
+    }
     HC(cudaEventRecord(h0->ev[11], st));
   } else {
     HK(wsbm_lu_batched(dluM, NB, maxk, nullptr, st));
@@ -1412,6 +1449,7 @@ static int factor_levels(const std::vector<wsbm_hss*>& hs, const std::vector<int
       lu_out[1] += lu_solve_flops(B.n, B.k) + lu_solve_flops(B.k, B.k);
     }
     lu_out[2] += 2.0 * NB;
+    if (lu_tc) lu_out[3] += 2.0 * NB;
   }
   ms_out[0] = elapsed(h0->ev[0], h0->ev[1]);
   ms_out[1] = elapsed(h0->ev[0], h0->ev[4]);
@@ -1575,7 +1613,7 @@ static int factor_all(const std::vector<wsbm_hss*>& hs, wsbm_stats_t* bstats) {
   double ms[5] = {0, 0, 0, 0, 0};  // entries, pair kernel, IDs, factor, CPQR
   int64_t cpqr_mats = 0;
   double cpqr_flops = 0.0, ms_sketch = 0.0;
-  double lu_acc[3] = {0.0, 0.0, 0.0};  // fused LU + solve: device ms, flops, matrices
+  double lu_acc[4] = {0.0, 0.0, 0.0, 0.0};  // box LU + solve: device ms, flops, matrices, on TC
   int64_t sketch_cnt[2] = {0, 0};  // sketched ID matrices, redone on the full matrix
   std::vector<int> level(hs.size(), 0), done(hs.size(), 0);
   std::vector<char> partial(hs.size(), 0);
@@ -1700,6 +1738,7 @@ static int factor_all(const std::vector<wsbm_hss*>& hs, wsbm_stats_t* bstats) {
       h->stats.ms_lu = lu_acc[0];
       h->stats.lu_flops = lu_acc[1];
       h->stats.lu_matrices = (int64_t)lu_acc[2];
+      h->stats.lu_tc_matrices = (int64_t)lu_acc[3];
     }
     size_t bytes = 0;
     for (int l = h->top; l <= h->L && h->L > 0; ++l)
@@ -1738,6 +1777,7 @@ static int factor_all(const std::vector<wsbm_hss*>& hs, wsbm_stats_t* bstats) {
     bstats->ms_lu = lu_acc[0];
     bstats->lu_flops = lu_acc[1];
     bstats->lu_matrices = (int64_t)lu_acc[2];
+    bstats->lu_tc_matrices = (int64_t)lu_acc[3];
   }
   return rc;
 }
