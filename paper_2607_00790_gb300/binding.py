@@ -280,6 +280,16 @@ class GemmItem(ctypes.Structure):
                 ("pad", ctypes.c_int32)]
 
 
+def _ld(t):
+    """Leading dimension of a column-major (stride-1 rows) tensor; a single column's stride is
+    arbitrary in torch, so it counts as the row count."""
+    if t.shape[1] <= 1:
+        return max(int(t.shape[0]), 1)
+    if t.shape[0] > 1 and t.stride(0) != 1:
+        raise ValueError("expected column-major storage (stride 1 along the rows)")
+    return int(t.stride(1))
+
+
 def wsbm_zgemm_batched(As, Bs, Cs, alpha=1.0, beta=0.0):
     """C_i = beta C_i + alpha A_i B_i for lists of complex128 device tensors stored column-major
     (pass the transposes' storage: tensors whose .T is contiguous), in one tensor-core launch."""
@@ -289,8 +299,7 @@ def wsbm_zgemm_batched(As, Bs, Cs, alpha=1.0, beta=0.0):
     for i, (A, B, C) in enumerate(zip(As, Bs, Cs)):
         m, k = A.shape
         nn = B.shape[1]
-        items[i] = GemmItem(A.data_ptr(), A.stride(1), B.data_ptr(), B.stride(1), C.data_ptr(),
-                            C.stride(1), m, nn, k, 0)
+        items[i] = GemmItem(A.data_ptr(), _ld(A), B.data_ptr(), _ld(B), C.data_ptr(), _ld(C), m, nn, k, 0)
         keep.append((A, B, C))
     al = (ctypes.c_double * 2)(complex(alpha).real, complex(alpha).imag)
     be = (ctypes.c_double * 2)(complex(beta).real, complex(beta).imag)

@@ -1255,6 +1255,7 @@ static int factor_levels(const std::vector<wsbm_hss*>& hs, const std::vector<int
   std::vector<TrsmDesc> zl, ml;
   std::vector<GatherDesc> gz;
   std::vector<GemmDesc> gm;
+  std::vector<int> gm_box;  // box of each gm entry
   std::vector<CopyDesc> tcc, pcopy, idd;
   {
     std::vector<size_t> oz(hs.size(), 0), ok(hs.size(), 0), ot(hs.size(), 0), on(hs.size(), 0);
@@ -1309,6 +1310,7 @@ static int factor_levels(const std::vector<wsbm_hss*>& hs, const std::vector<int
         gd.alpha = make_double2(1.0, 0.0);
         gd.beta = make_double2(1.0, 0.0);
         gm.push_back(gd);
+        gm_box.push_back(r);
         tcc.push_back({B.Tc, qc.A + (int64_t)k * qc.lda, k, qc.lda, k, n - k});
       }
       luM.push_back({M, k, pM, k, 0});
@@ -1329,7 +1331,6 @@ static int factor_levels(const std::vector<wsbm_hss*>& hs, const std::vector<int
   BuildLDesc* dbl = nullptr;
   TrsmDesc *dzl = nullptr, *dml = nullptr;
   GatherDesc* dgz = nullptr;
-  GemmDesc* dgm = nullptr;
   CopyDesc *dtcc = nullptr, *dpc = nullptr, *didd = nullptr;
   HK(upload(h0, luD, &dluD, tmp));
   HK(upload(h0, luM, &dluM, tmp));
@@ -1337,57 +1338,93 @@ static int factor_levels(const std::vector<wsbm_hss*>& hs, const std::vector<int
   HK(upload(h0, zl, &dzl, tmp));
   HK(upload(h0, ml, &dml, tmp));
   HK(upload(h0, gz, &dgz, tmp));
-  HK(upload(h0, gm, &dgm, tmp));
   HK(upload(h0, tcc, &dtcc, tmp));
   HK(upload(h0, pcopy, &dpc, tmp));
   HK(upload(h0, idd, &didd, tmp));
   int64_t maxnk = 0;
   for (int r = 0; r < NB; ++r) maxnk = std::max(maxnk, (int64_t)R[r].box().n * R[r].box().k);
-  // LU(D) with Z = D^-1 L, and LU(M) with Dhat = M^-1: for boxes of WSBM_LU_TC_MIN unknowns or
-  // more by the batched LU whose products run on the tensor cores, else in the fused kernel when
-  // [D | L] fits it (one scratch serves both launches), else blocked LU and triangular solves
-  LuSolveDesc *dfz = nullptr, *dfm = nullptr;
-  std::vector<LuSolveDesc> fz, fm;
-  const bool lu_tc = maxn >= WSBM_LU_TC_MIN && maxn <= WSBM_LUS_MAXN && NB <= 32767;
+  // LU(D) with Z = D^-1 L, and LU(M) with Dhat = M^-1 (and M += Tc Zg[k:n] before it), chosen
+  // per box so that a box's factors do not depend on the other boxes of the launch: boxes of
+  // WSBM_LU_TC_MIN unknowns or more by the batched LU whose products run on the tensor cores,
+  // the others in the fused FP64 kernel; when a box exceeds the fused kernel, every box of the
+  // launch by the blocked LU and triangular solves
+  const bool fits = maxn <= WSBM_LUS_MAXN;
+  std::vector<int> itc, ifu;
+  for (int r = 0; r < NB; ++r) (fits && R[r].box().n >= WSBM_LU_TC_MIN ? itc : ifu).push_back(r);
+  if (itc.size() > 32767) {  // beyond one batched launch: the fused kernel for all
+    ifu.insert(ifu.end(), itc.begin(), itc.end());
+    std::sort(ifu.begin(), ifu.end());
+    itc.clear();
+  }
+  std::vector<char> on_tc(NB, 0);
+  for (int r : itc) on_tc[r] = 1;
+  const bool lu_tc = !itc.empty();
+  LuSolveDesc *dfz = nullptr, *dfm = nullptr, *dfz_t = nullptr, *dfm_t = nullptr;
+  LuDesc *dluD_t = nullptr, *dluM_t = nullptr;
+  std::vector<LuSolveDesc> fz_t, fm_t;
+  std::vector<TcProduct> gm_t;
+  std::vector<GemmDesc> gm_f;
+  GemmDesc* dgm_f = nullptr;
+  int maxn_f = 0, maxk_f = 0;
   void* wstc = nullptr;
-  if (maxn <= WSBM_LUS_MAXN) {
+  for (size_t g = 0; g < gm.size(); ++g) {
+    if (on_tc[gm_box[g]])
+      gm_t.push_back({gm[g].A, gm[g].lda, gm[g].B, gm[g].ldb, gm[g].C, gm[g].ldc, gm[g].m, gm[g].n, gm[g].k, 0});
+    else
+      gm_f.push_back(gm[g]);
+  }
+  if (!gm_f.empty()) HK(upload(h0, gm_f, &dgm_f, tmp));
+  if (fits) {
+    // fused kernel: its row-major scratch for the boxes it takes (one scratch serves both launches)
     size_t sz = 0, sm = 0;
-    for (int r = 0; r < NB; ++r) {
+    for (int r : ifu) {
       const Box& B = R[r].box();
       sz += (size_t)B.n * wsbm_lu_solve_ldr(B.n, B.k);
       sm += (size_t)B.k * wsbm_lu_solve_ldr(B.k, B.k);
+      maxn_f = std::max(maxn_f, B.n);
+      maxk_f = std::max(maxk_f, B.k);
     }
-    double2* Sc = nullptr;
-    if (!lu_tc) HK(dalloc(h0, std::max(sz, sm) * sizeof(double2), (void**)&Sc, tmp));
-    fz.resize(NB);
-    fm.resize(NB);
-    size_t oz = 0, om = 0;
-    for (int r = 0; r < NB; ++r) {
-      const Box& B = R[r].box();
-      fz[r] = {B.D, B.n, B.piv, B.Z, B.n, Sc + oz, B.n, B.k};
-      fm[r] = {luM[r].A, B.k, luM[r].piv, B.Dc, B.k, Sc + om, B.k, B.k};
-      oz += (size_t)B.n * wsbm_lu_solve_ldr(B.n, B.k);
-      om += (size_t)B.k * wsbm_lu_solve_ldr(B.k, B.k);
+    if (!ifu.empty()) {
+      double2* Sc = nullptr;
+      HK(dalloc(h0, std::max(sz, sm) * sizeof(double2), (void**)&Sc, tmp));
+      std::vector<LuSolveDesc> fz(ifu.size()), fm(ifu.size());
+      size_t oz = 0, om = 0;
+      for (size_t t = 0; t < ifu.size(); ++t) {
+        const int r = ifu[t];
+        const Box& B = R[r].box();
+        fz[t] = {B.D, B.n, B.piv, B.Z, B.n, Sc + oz, B.n, B.k};
+        fm[t] = {luM[r].A, B.k, luM[r].piv, B.Dc, B.k, Sc + om, B.k, B.k};
+        oz += (size_t)B.n * wsbm_lu_solve_ldr(B.n, B.k);
+        om += (size_t)B.k * wsbm_lu_solve_ldr(B.k, B.k);
+      }
+      HK(upload(h0, fz, &dfz, tmp));
+      HK(upload(h0, fm, &dfm, tmp));
     }
-    HK(upload(h0, fz, &dfz, tmp));
-    HK(upload(h0, fm, &dfm, tmp));
     if (lu_tc) {
-      size_t wb = std::max(wsbm_lu_solve_tc_ws_bytes(fz.data(), NB), wsbm_lu_solve_tc_ws_bytes(fm.data(), NB));
-      std::vector<TcProduct> gp(gm.size());
-      for (size_t g = 0; g < gm.size(); ++g)
-        gp[g] = {gm[g].A, gm[g].lda, gm[g].B, gm[g].ldb, gm[g].C, gm[g].ldc, gm[g].m, gm[g].n, gm[g].k, 0};
-      if (!gp.empty()) wb = std::max(wb, wsbm_zgemm_tc_batched_ws_bytes(gp.data(), (int)gp.size()));
+      std::vector<LuDesc> ld_t, lm_t;
+      for (int r : itc) {
+        const Box& B = R[r].box();
+        fz_t.push_back({B.D, B.n, B.piv, B.Z, B.n, nullptr, B.n, B.k});
+        fm_t.push_back({luM[r].A, B.k, luM[r].piv, B.Dc, B.k, nullptr, B.k, B.k});
+        ld_t.push_back(luD[r]);
+        lm_t.push_back(luM[r]);
+      }
+      HK(upload(h0, fz_t, &dfz_t, tmp));
+      HK(upload(h0, fm_t, &dfm_t, tmp));
+      HK(upload(h0, ld_t, &dluD_t, tmp));
+      HK(upload(h0, lm_t, &dluM_t, tmp));
+      size_t wb = std::max(wsbm_lu_solve_tc_ws_bytes(fz_t.data(), (int)itc.size()),
+                           wsbm_lu_solve_tc_ws_bytes(fm_t.data(), (int)itc.size()));
+      if (!gm_t.empty()) wb = std::max(wb, wsbm_zgemm_tc_batched_ws_bytes(gm_t.data(), (int)gm_t.size()));
       HK(dalloc(h0, wb, &wstc, tmp));
     }
   }
   launch_y(k_build_L, gridfor(maxnk), NB, dbl, st);
-  if (dfz) {
+  if (fits) {
     HC(cudaEventRecord(h0->ev[8], st));
-    if (lu_tc) {
-      if (wsbm_lu_solve_tc_batched(fz.data(), dfz, NB, dluD, wstc, st)) return WSBM_ERR_CUDA;
-    } else {
-      HK(wsbm_lu_solve_fused_batched(dfz, NB, maxn, maxn + maxk, st));
-    }
+    if (dfz) HK(wsbm_lu_solve_fused_batched(dfz, (int)ifu.size(), maxn_f, maxn_f + maxk_f, st));
+    if (lu_tc && wsbm_lu_solve_tc_batched(fz_t.data(), dfz_t, (int)itc.size(), dluD_t, wstc, st))
+      return WSBM_ERR_CUDA;
     HC(cudaEventRecord(h0->ev[9], st));
   } else {
     HK(wsbm_lu_batched(dluD, NB, maxn, nullptr, st));
@@ -1395,29 +1432,20 @@ static int factor_levels(const std::vector<wsbm_hss*>& hs, const std::vector<int
   }
   launch_y(k_gather_rows, gridfor(maxnk), NB, dgz, st);
   launch_y(k_copy2d, gridfor((int64_t)maxk * maxk), NB, dpc, st);
-  if (!gm.empty()) {
-    if (lu_tc) {  // M += Tc Zg[k:n] on the tensor cores
-      std::vector<TcProduct> gp(gm.size());
-      for (size_t g = 0; g < gm.size(); ++g)
-        gp[g] = {gm[g].A, gm[g].lda, gm[g].B, gm[g].ldb, gm[g].C, gm[g].ldc, gm[g].m, gm[g].n, gm[g].k, 0};
-      if (wsbm_zgemm_tc_batched(gp.data(), (int)gp.size(), make_double2(1.0, 0.0), make_double2(1.0, 0.0),
-                                wstc, st))
-        return WSBM_ERR_CUDA;
-    } else {
-      HK(wsbm_gemm_batched(dgm, (int)gm.size(), maxk, maxk, st));
-    }
-  }
+  // M += Tc Zg[k:n]
+  if (!gm_t.empty() && wsbm_zgemm_tc_batched(gm_t.data(), (int)gm_t.size(), make_double2(1.0, 0.0),
+                                             make_double2(1.0, 0.0), wstc, st))
+    return WSBM_ERR_CUDA;
+  if (!gm_f.empty()) HK(wsbm_gemm_batched(dgm_f, (int)gm_f.size(), maxk, maxk, st));
   if (!tcc.empty()) {
     launch_y(k_copy2d, gridfor(maxnk), (int64_t)tcc.size(), dtcc, st);
   }
   launch_y(k_fill_identity_batched, gridfor((int64_t)maxk * maxk), NB, didd, st);
-  if (dfm) {
+  if (fits) {
     HC(cudaEventRecord(h0->ev[10], st));
-    if (lu_tc) {
-      if (wsbm_lu_solve_tc_batched(fm.data(), dfm, NB, dluM, wstc, st)) return WSBM_ERR_CUDA;
-    } else {
-      HK(wsbm_lu_solve_fused_batched(dfm, NB, maxk, 2 * maxk, st));
-    }
+    if (dfm) HK(wsbm_lu_solve_fused_batched(dfm, (int)ifu.size(), maxk_f, 2 * maxk_f, st));
+    if (lu_tc && wsbm_lu_solve_tc_batched(fm_t.data(), dfm_t, (int)itc.size(), dluM_t, wstc, st))
+      return WSBM_ERR_CUDA;
     HC(cudaEventRecord(h0->ev[11], st));
   } else {
     HK(wsbm_lu_batched(dluM, NB, maxk, nullptr, st));
@@ -1442,14 +1470,14 @@ static int factor_levels(const std::vector<wsbm_hss*>& hs, const std::vector<int
   HC(cudaEventRecord(h0->ev[3], st));
   HC(cudaStreamSynchronize(st));
   if (perm_stage) memcpy(hperm.data(), perm_stage, hperm.size() * sizeof(int32_t));
-  if (dfz && dfm) {  // device time, flops and matrices of the two fused LU + solve launches
+  if (fits) {  // device time, flops and matrices of the box factors' LU + solve launches
     lu_out[0] += elapsed(h0->ev[8], h0->ev[9]) + elapsed(h0->ev[10], h0->ev[11]);
     for (int r = 0; r < NB; ++r) {
       const Box& B = R[r].box();
       lu_out[1] += lu_solve_flops(B.n, B.k) + lu_solve_flops(B.k, B.k);
     }
     lu_out[2] += 2.0 * NB;
-    if (lu_tc) lu_out[3] += 2.0 * NB;
+    lu_out[3] += 2.0 * (double)itc.size();
   }
   ms_out[0] = elapsed(h0->ev[0], h0->ev[1]);
   ms_out[1] = elapsed(h0->ev[0], h0->ev[4]);
