@@ -1038,6 +1038,8 @@ def main():
                     help="only the leaf-level builds of the three formulations at N = 2^18")
     ap.add_argument("--batched-solve", action="store_true",
                     help="only the batched-solve measurement (16 scatterers, 256 right-hand sides)")
+    ap.add_argument("--batch-count", type=int, default=16, help="scatterers of --batched-solve")
+    ap.add_argument("--batch-nmax", type=int, default=16384, help="largest N of --batched-solve")
     ap.add_argument("--profile-case", action="store_true",
                     help="one leaf-level build of the star (small case for ncu) per precision mode")
     ap.add_argument("--profile-n", type=int, default=16384, help="nodes of the --profile-case star")
@@ -1071,7 +1073,8 @@ def main():
         print(json.dumps({"adjoint": run_adjoint("cuda", N=args.adjoint_n)}), flush=True)
         return
     if args.batched_solve:
-        print(json.dumps({"batched_solve": run_batched_solve("cuda")}), flush=True)
+        print(json.dumps({"batched_solve": run_batched_solve("cuda", count=args.batch_count,
+                                                            nmax=args.batch_nmax)}), flush=True)
         return
     if args.formulations:
         print(json.dumps({"formulations": run_formulations("cuda")}), flush=True)
