@@ -983,9 +983,15 @@ int wsbm_lu_solve_t_batched(const TrsmDesc* d_desc, int nbatch, int max_n, int m
 // update A22 -= L21 U12 runs on the tensor cores (wsbm_zgemm_tc).  Factors and piv as for
 // wsbm_lu_batched.  Pivot: the row of largest max(|re|, |im|) compared on the upper 32 bits of
 // its bit pattern (within 2^-20 of the largest), first row on ties.
+#ifndef LUB_NB
 #define LUB_NB 128      // outer panel width
+#endif
+#ifndef LUB_NB_BIG
 #define LUB_NB_BIG 256  // outer panel width from LUB_BIG_N on: deeper tensor-core products
+#endif
+#ifndef LUB_BIG_N
 #define LUB_BIG_N 12288
+#endif
 #define LUB_WB 8    // column-by-column block width
 #define LUB_TC_K 32 // panel updates of at least this depth run on the tensor cores
 
