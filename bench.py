@@ -838,10 +838,15 @@ def run_batched_solve(dev, count=16, nmax=16384, nrhs=256, tol=1e-8):
     bt.factor()
     torch.cuda.synchronize()
     t_factor = time.time() - t
+    binding.trim_memory()  # the build's cached work space back to the device
+    bst = bt.stats()
+    free_b, total_b = torch.cuda.mem_get_info(dev)
     ang = torch.tensor(2 * np.pi * np.arange(nrhs) / nrhs, device=dev)
     rhs = [bt.solver(i).rhs_planewave(ang) for i in range(len(man))]
     out = {"scatterers": len(man), "nodes_total": int(sum(m["N"] for m in man)), "nrhs": nrhs,
-           "id_tol": tol, "batch_factor_s": t_factor}
+           "id_tol": tol, "batch_factor_s": t_factor, "factor_bytes": bst["factor_bytes"],
+           "largest_root": bst["root_size"], "device_free_bytes_after_factor": free_b,
+           "rhs_bytes": int(sum(r.numel() * 16 for r in rhs))}
 
     def timed(f, reps=3):
         f()
@@ -854,8 +859,24 @@ def run_batched_solve(dev, count=16, nmax=16384, nrhs=256, tol=1e-8):
             ts.append(time.time() - t0)
         return min(ts)
 
-    out["batched_solve_s"] = timed(lambda: bt.solve(rhs))
-    out["per_curve_solves_s"] = timed(lambda: [bt.solver(i).solve(rhs[i]) for i in range(len(man))])
+    # all right-hand sides in one plan when they fit, else in column chunks (each plan holds its
+    # own copies of the right-hand sides and solutions)
+    chunk = nrhs
+    while True:
+        try:
+            parts = [[r[:, c:c + chunk].contiguous() for r in rhs] for c in range(0, nrhs, chunk)]
+            out["batched_solve_s"] = timed(lambda: [bt.solve(pr) for pr in parts])
+            break
+        except binding.WsbmError as exc:
+            if exc.code != -2 or chunk <= 8:
+                raise
+            parts = None
+            chunk //= 2
+            torch.cuda.empty_cache()
+            binding.trim_memory()
+    out["rhs_per_plan"] = chunk
+    out["per_curve_solves_s"] = timed(lambda: [bt.solver(i).solve(pr[i]) for pr in parts
+                                               for i in range(len(man))])
     out["speedup"] = out["per_curve_solves_s"] / out["batched_solve_s"]
     out["rhs_per_s_batched"] = len(man) * nrhs / out["batched_solve_s"]
     bt.close()
