@@ -230,6 +230,24 @@ def run_ours(args, ws, rank, local):
         return st
 
     p64 = params()
+    # launch shapes before the warm-up: the tensor-core paths timed on synthetic data of this
+    # workload's sizes (leaf boxes of 2 x leaf unknowns, N / leaf of them, 128 right-hand sides
+    # each), the entry-kernel tiles / grids and QR block size on leaf-level builds of it
+    tuning = None
+    if args.set_tuning:
+        # fixed shapes (e.g. the choice of an earlier autotuned run, for a profiler capture)
+        binding.wsbm_tuning_set(**{k: int(v) for k, v in (kv.split("=") for kv in args.set_tuning.split(","))})
+    elif not args.no_autotune:
+        choice, tms = binding.wsbm_autotune(n_box=2 * cfg["leaf"], nbox=cfg["N"] // cfg["leaf"],
+                                            nrhs_box=128, n_root=4096, device=dev)
+        bchoice, bms = binding.wsbm_autotune_build(g, p64, device=dev)
+        cand = [f"{tf}x{128 // tf}@{c}" for tf in (16, 32, 64) for c in (8, 16, 32)]
+        tuning = {"choice": {**choice, **bchoice}, "candidate_ms": {
+            "tc_group_4_8_16": tms[0:3], "box_nb_32_64": tms[3:5], "root_nb_128_256_at_4096": tms[5:7],
+            "cpqr_cb_2_4_8": tms[7:10],
+            "k_pairs_tile@ctas_per_sm": dict(zip(cand, bms[0:9])),
+            "k_proxy_tile@ctas_per_sm": dict(zip(cand, bms[9:18])),
+            "k_cpqr_threads_128_256": bms[18:20]}}
     for _ in range(args.warmup):
         step(p64)
     torch.cuda.synchronize()
@@ -323,6 +341,7 @@ def run_ours(args, ws, rank, local):
            "gpu_launches": launches, "clocks": clk, "roofline": roof_main,
            "roofline_" + ("lu" if roof_other is roof_l else "cpqr") + "_kernel": roof_other,
            "roofline_entry_kernel": roof,
+           "tuning": tuning if tuning is not None else binding.wsbm_tuning(),
            "step": {"entries_per_step": entries / args.steps,
                     "build_factor_s_leaf_level": ms_region / args.steps / 1e3,
                     "ms_entries": ms_kern / args.steps,
@@ -669,6 +688,9 @@ def run_extras(curve, cfg, dev, params):
     return out
 
 
+_FULL_TUNING = {}
+
+
 def run_full_2p18(dev, precision=0, tol=1e-8, rows=256, refine=True, ff_ref=None):
     """The whole HSS build + factor at the bench workload (N = 2^18, 15 nodes per wavelength):
     every level compressed while the one-CTA QR takes its boxes, then the dense root factored by
@@ -683,6 +705,15 @@ def run_full_2p18(dev, precision=0, tol=1e-8, rows=256, refine=True, ff_ref=None
     g, keep = binding.make_geom(curve, device=dev)
     p = binding.make_params(cfg["k0"], cfg["n"], leaf=cfg["leaf"], nproxy=cfg["nproxy"], id_tol=tol,
                             precision=precision, root_cap=200000)
+    # the root of this build is far above 12288 unknowns: the large-class root panel width (and
+    # the other tensor-core shapes) timed once per process, before the build
+    if not _FULL_TUNING:
+        choice, tms = binding.wsbm_autotune(n_box=2 * cfg["leaf"], nbox=N // cfg["leaf"], nrhs_box=128,
+                                            n_root=16384, device=dev)
+        _FULL_TUNING.update(choice=choice, candidate_ms={
+            "tc_group_4_8_16": tms[0:3], "box_nb_32_64": tms[3:5], "root_nb_128_256_at_16384": tms[5:7],
+            "cpqr_cb_2_4_8": tms[7:10]})
+    tuning = dict(_FULL_TUNING)
     binding.trim_memory()
     s = binding.Solver(g, p, device=dev)
     t = time.time()
@@ -710,7 +741,8 @@ def run_full_2p18(dev, precision=0, tol=1e-8, rows=256, refine=True, ff_ref=None
         out = {"build_factor_s": st["ms_total_factor"] / 1e3, "ms_entries": st["ms_entries"],
                "ms_id": st["ms_id"], "ms_factor": st["ms_factor"], "root_size": st["root_size"],
                "rank_per_level": st["rank_per_level"], "id_tol": tol, "precision": precision,
-               "solve_8rhs_farfield_s": t_solve, "residual_rel_sampled_rows": res_rows}
+               "solve_8rhs_farfield_s": t_solve, "residual_rel_sampled_rows": res_rows,
+               "tuning": tuning}
         if ff_ref is not None:
             out["farfield_rel_err_vs_fp64_tol1e-8"] = float(
                 np.linalg.norm(ff.cpu().numpy() - ff_ref) / np.linalg.norm(ff_ref))
@@ -738,7 +770,7 @@ def run_full_2p18(dev, precision=0, tol=1e-8, rows=256, refine=True, ff_ref=None
            "residual_rel_full_angle0": res_full, "residual_rel_sampled_rows": res_rows,
            "farfield_rel_err_vs_one_refinement_step_angle0": ff_err,
            "density_rel_correction_angle0": u_err,
-           "refinement_step_s": t_ref}
+           "refinement_step_s": t_ref, "tuning": tuning}
     s.close()
     binding.trim_memory()
     return out
@@ -1056,6 +1088,11 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--no-extras", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep the default launch shapes instead of timing the candidates")
+    ap.add_argument("--set-tuning", default="",
+                    help="launch shapes to use instead of the autotuners, as key=value,... with the "
+                         "keys of binding.wsbm_tuning() (e.g. pair_tf=32,pair_ctas=16)")
     ap.add_argument("--step-only", action="store_true",
                     help="only the warm-up and timed steps (no e2e, CPU baseline or extras): "
                          "the launch list of a step for ncu")

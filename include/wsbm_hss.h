@@ -408,6 +408,56 @@ int wsbm_zgemm_batched(int32_t count, const wsbm_gemm_item* items, const double*
  * the library's allocator.  Synchronous.  Errors: INVALID_ARG, OOM, CUDA, TIMEOUT. */
 int wsbm_lu_dense(void* A, int64_t lda, int32_t n, int32_t* piv, void* stream);
 
+/* Autotuners of the launch shapes (no counterpart in the paper).  Each times its candidates
+ * with CUDA events on `stream`, keeps the fastest for every later call on the current device
+ * (builds, solves, wsbm_zgemm*, wsbm_lu_dense) for the rest of the process, and leaves the
+ * other shapes as they were.  Every shape gives the same accuracy; the GEMM raster group and
+ * the entry-kernel shapes change no bit of any result (the panel widths and QR block sizes
+ * change the rounding order).
+ *
+ * wsbm_autotune: synthetic complex data of the given sizes, best of three after one warm-up:
+ *   out[0]  rows of 128-row tiles per raster group of the tensor-core GEMM's tile order, of
+ *           {4, 8, 16} (one 8192 x 8192 x 256 product);
+ *   out[1]  panel width of the batched box LU, of {32, 64} (nbox boxes of n_box unknowns with
+ *           nrhs_box right-hand sides each: the leaf level of a build);
+ *   out[2], out[3]  outer panel width of the root LU, of {128, 256}, for roots below and from
+ *           12288 unknowns; only the class of n_root is timed, the other keeps its value;
+ *   out[4]  columns per warp pass of the column-pivoted QR of ID matrices of more than 2048
+ *           rows, of {2, 4, 8} (152 matrices of 2560 x 128).
+ * ms: host, 10 doubles or NULL: the candidates' times in that order.  Work space (two copies of
+ * the boxes, two n_root x n_root matrices, 3 GiB for the product, 1 GiB for the QRs) from the
+ * library's allocator.  Sizes: 64 <= n_box <= 4096, 1 <= nbox <= 32767, 1 <= nrhs_box <= 4096,
+ * at most 8 GiB of boxes, 256 <= n_root <= 32768.  Defaults without a call: 8, 64, 128, 256, 4.
+ * Synchronous.  Errors: INVALID_ARG, OOM, CUDA, TIMEOUT. */
+int wsbm_autotune(int32_t n_box, int32_t nbox, int32_t nrhs_box, int32_t n_root, int32_t* out,
+                  double* ms, void* stream);
+/* wsbm_autotune_build: leaf-level builds (p->max_levels taken as 1) of the given problem, one
+ * per candidate after one warm-up build, timed by the library's per-kernel device times
+ * (wsbm_stats_t ms_pairs, ms_proxy, ms_cpqr):
+ *   out[0], out[1]  tile width (16, 32 or 64 nodes along the contiguous output dimension,
+ *           128 / width along the other) and grid (8, 16 or 32 CTAs per SM) of the node-pair
+ *           entry kernel of eq. (weakly_bm) (the comparison formulations keep 32 and 16);
+ *   out[2], out[3]  the same for the proxy-block kernel;
+ *   out[4]  threads per CTA (128 or 256) of the thread-per-column QR of the ID matrices.
+ * ms: host, 20 doubles or NULL: pair-kernel times of the 9 (width, grid) pairs in row-major
+ * order of {16, 32, 64} x {8, 16, 32}, then the proxy-kernel times in the same order, then the
+ * QR times for 128 and 256 threads.  Defaults without a call: 32, 16, 32, 16, 256.
+ * Synchronous.  Errors: those of wsbm_create / wsbm_factor (the shapes are then unchanged). */
+int wsbm_autotune_build(const wsbm_geom* g, const wsbm_params* p, int32_t* out, double* ms,
+                        void* stream);
+/* The shapes in use on the current device: out[0..4] as wsbm_autotune's, out[5..9] as
+ * wsbm_autotune_build's, out[10] = 1 once wsbm_autotune ran on this device, out[11] = 1 once
+ * wsbm_autotune_build did (or the flags last given to wsbm_tuning_set), out[12] the smallest
+ * dense root order whose solves with 16 or more right-hand sides run as block solves on the
+ * tensor cores (default 1024).  out: 13 int32.  Errors: INVALID_ARG (out NULL). */
+int wsbm_tuning(int32_t* out);
+/* Sets the shapes of the current device without timing (e.g. the result of an earlier
+ * autotune): in[0..12] in the order of wsbm_tuning, each among its documented candidates
+ * (raster group 1..64; box panel width 8..64, a multiple of 8; grids 1..64 CTAs per SM; flags
+ * 0 or 1; root order >= 1).  A solve plan already built keeps the shapes it was built with.
+ * Errors: INVALID_ARG, CUDA (no device). */
+int wsbm_tuning_set(const int32_t* in);
+
 /* ---------------------------------------------------------------- gradients ----
  * Reverse-mode building blocks of shape and refractive-index gradients of a far-field loss
  * (no counterpart in the paper, which does not differentiate its solver).  With the solution x

@@ -112,6 +112,14 @@ def lib():
         L.wsbm_zgemm_batched.restype = ctypes.c_int
         L.wsbm_lu_dense.argtypes = [vp, i64, i32, vp, vp]
         L.wsbm_lu_dense.restype = ctypes.c_int
+        L.wsbm_autotune.argtypes = [i32, i32, i32, i32, vp, vp, vp]
+        L.wsbm_autotune.restype = ctypes.c_int
+        L.wsbm_autotune_build.argtypes = [ctypes.POINTER(Geom), ctypes.POINTER(Params), vp, vp, vp]
+        L.wsbm_autotune_build.restype = ctypes.c_int
+        L.wsbm_tuning.argtypes = [vp]
+        L.wsbm_tuning.restype = ctypes.c_int
+        L.wsbm_tuning_set.argtypes = [vp]
+        L.wsbm_tuning_set.restype = ctypes.c_int
         L.wsbm_refine.restype = ctypes.c_int
         L.wsbm_matvec.argtypes = [G, P, i32, vp, i32, vp, vp]
         L.wsbm_matvec.restype = ctypes.c_int
@@ -316,6 +324,61 @@ def wsbm_lu_dense(A):
     _check(lib().wsbm_lu_dense(_dev(Af, torch.complex128), n, n, _dev(piv, torch.int32),
                                _stream(A.device)), "wsbm_lu_dense")
     return Af.T, piv
+
+
+TUNE_KEYS = ("tc_group", "box_nb", "root_nb_mid", "root_nb_large", "cpqr_cb")
+TUNE_BUILD_KEYS = ("pair_tf", "pair_ctas", "proxy_tf", "proxy_ctas", "cpqr_threads")
+
+
+def wsbm_autotune(n_box=256, nbox=512, nrhs_box=160, n_root=16384, device=None):
+    """Time the candidate shapes of the tensor-core paths and of the warp QR on the current
+    device and keep the fastest (see wsbm_autotune in the C header).  Returns (choices dict,
+    candidate times in ms: raster groups 4/8/16, box panel widths 32/64, root panel widths
+    128/256, QR columns per pass 2/4/8)."""
+    out = (ctypes.c_int32 * 5)()
+    ms = (ctypes.c_double * 10)()
+    _check(lib().wsbm_autotune(n_box, nbox, nrhs_box, n_root, out, ms, _stream(device)), "wsbm_autotune")
+    return dict(zip(TUNE_KEYS, list(out))), list(ms)
+
+
+def wsbm_autotune_build(geom, params, device=None):
+    """Time the entry-kernel tile shapes and grids and the QR block size on leaf-level builds of
+    the given problem (see wsbm_autotune_build in the C header).  Returns (choices dict, times
+    in ms: 9 pair-kernel and 9 proxy-kernel times over (tile width 16/32/64) x (8/16/32 CTAs
+    per SM), then the QR times for 128 / 256 threads)."""
+    out = (ctypes.c_int32 * 5)()
+    ms = (ctypes.c_double * 20)()
+    _check(lib().wsbm_autotune_build(ctypes.byref(geom), ctypes.byref(params), out, ms, _stream(device)),
+           "wsbm_autotune_build")
+    return dict(zip(TUNE_BUILD_KEYS, list(out))), list(ms)
+
+
+def wsbm_tuning():
+    """The launch shapes in use on the current device, with "tuned" / "tuned_build" = True once
+    the respective autotuner ran there, and "solve_tc_min" (the smallest root order whose solves
+    with 16 or more right-hand sides use the tensor cores)."""
+    out = (ctypes.c_int32 * 13)()
+    _check(lib().wsbm_tuning(out), "wsbm_tuning")
+    v = list(out)
+    d = dict(zip(TUNE_KEYS + TUNE_BUILD_KEYS, v[:10]))
+    d["tuned"] = bool(v[10])
+    d["tuned_build"] = bool(v[11])
+    d["solve_tc_min"] = v[12]
+    return d
+
+
+def wsbm_tuning_set(**shapes):
+    """Set launch shapes of the current device without timing; keys as wsbm_tuning() returns
+    them (the ones not given keep their current value)."""
+    cur = wsbm_tuning()
+    for k in shapes:
+        if k not in cur:
+            raise KeyError(k)
+    cur.update(shapes)
+    arr = (ctypes.c_int32 * 13)(*[int(cur[k]) for k in TUNE_KEYS + TUNE_BUILD_KEYS],
+                                int(bool(cur["tuned"])), int(bool(cur["tuned_build"])),
+                                int(cur["solve_tc_min"]))
+    _check(lib().wsbm_tuning_set(arr), "wsbm_tuning_set")
 
 
 def wsbm_sketch(A, l, seed=0):

@@ -543,13 +543,11 @@ __global__ void __launch_bounds__(LUS_T) k_lu_solve_fused(const LuSolveDesc* __r
 // matrix, exact remaining column norms, permutation) lets a later call resume.  On return
 // the R factor sits in rows 0..k-1 (diagonal included; below it, reflector data).
 #ifndef CPQR_CB
-#define CPQR_CB 4  // trailing columns per warp per pass (2*CB partial sums, a power of two <= 16)
+#define CPQR_CB 4  // default trailing columns per warp pass of the warp variant (2, 4 or 8)
 #endif
 #ifndef CPQR_MINB
 #define CPQR_MINB 4  // minimum resident CTAs per SM asked of the register allocator (measured best)
 #endif
-// 5 - log2(2*CPQR_CB): the lane holding reduced value t is t << CPQR_SH
-#define CPQR_SH (CPQR_CB == 1 ? 4 : CPQR_CB == 2 ? 3 : CPQR_CB == 4 ? 2 : CPQR_CB == 8 ? 1 : 0)
 // TPC (thread per column): each thread updates whole trailing columns against the reflector
 // staged in shared memory (no warp reductions; the strided column loads stay in L1, and on
 // GB300 a warp-wide DFMA takes 16 clocks, which hides them).  Used when the reflector fits the
@@ -557,8 +555,11 @@ __global__ void __launch_bounds__(LUS_T) k_lu_solve_fused(const LuSolveDesc* __r
 #ifndef CPQR_TPC_MAXM
 #define CPQR_TPC_MAXM 2048
 #endif
-template <bool TPC>
+// Warp variant: CB trailing columns per warp per pass (2*CB partial sums, a power of two <= 16).
+template <bool TPC, int CB>
 __global__ void __launch_bounds__(256, CPQR_MINB) k_cpqr(const QrDesc* __restrict__ d, int mode) {
+  // 5 - log2(2*CB): the lane holding reduced value t is t << SH
+  constexpr int SH = CB == 1 ? 4 : CB == 2 ? 3 : CB == 4 ? 2 : CB == 8 ? 1 : 0;
   extern __shared__ double2 su[];  // TPC: the reflector u = M[j:m, j]
   const QrDesc q = d[blockIdx.x];
   const int m = q.m, n = q.n;
@@ -706,37 +707,37 @@ __global__ void __launch_bounds__(256, CPQR_MINB) k_cpqr(const QrDesc* __restric
       __syncthreads();
       continue;
     }
-    // apply P to the trailing columns: a warp takes CPQR_CB columns at a time, so each element
-    // of u is loaded once for all of them and the 2*CPQR_CB partial dot products are summed
+    // apply P to the trailing columns: a warp takes CB columns at a time, so each element
+    // of u is loaded once for all of them and the 2*CB partial dot products are summed
     // across the warp by recursive halving (each level hands half of the values to the partner
     // lane; 2*CB - 1 + (5 - log2(2*CB)) adds per lane instead of 10 per column).  The remaining
     // norm is downdated by the new row-j entry and recomputed exactly once cancellation has
     // eaten half its digits (remaining norm below 1e-8 of the last exact one).
     const double2* u = M + (int64_t)j * ld;
-    for (int c0 = j + 1 + warp * CPQR_CB; c0 < n; c0 += nw * CPQR_CB) {
-      const int nc = min(CPQR_CB, n - c0);
-      double acc[2 * CPQR_CB];  // re of the nc columns, then im
+    for (int c0 = j + 1 + warp * CB; c0 < n; c0 += nw * CB) {
+      const int nc = min(CB, n - c0);
+      double acc[2 * CB];  // re of the nc columns, then im
 #pragma unroll
-      for (int v = 0; v < 2 * CPQR_CB; ++v) acc[v] = 0.0;
+      for (int v = 0; v < 2 * CB; ++v) acc[v] = 0.0;
       for (int i = j + lane; i < m; i += 32) {  // w = u^H col, as fused multiply-adds
         const double2 ui = u[i];
 #pragma unroll
-        for (int v = 0; v < CPQR_CB; ++v) {
+        for (int v = 0; v < CB; ++v) {
           if (v < nc) {
             const double2 ci = M[i + (int64_t)(c0 + v) * ld];
             acc[v] = fma(ui.x, ci.x, fma(ui.y, ci.y, acc[v]));
-            acc[CPQR_CB + v] = fma(ui.x, ci.y, fma(-ui.y, ci.x, acc[CPQR_CB + v]));
+            acc[CB + v] = fma(ui.x, ci.y, fma(-ui.y, ci.x, acc[CB + v]));
           }
         }
       }
-      int cur = 2 * CPQR_CB;
+      int cur = 2 * CB;
 #pragma unroll
       for (int o = 16; o >= 1; o >>= 1) {
         if (cur > 1) {
           const int h = cur >> 1;
           const bool up = (lane & o) != 0;
 #pragma unroll
-          for (int v = 0; v < CPQR_CB; ++v) {
+          for (int v = 0; v < CB; ++v) {
             if (v < h) {
               const double send = up ? acc[v] : acc[v + h];
               const double keep = up ? acc[v + h] : acc[v];
@@ -748,17 +749,17 @@ __global__ void __launch_bounds__(256, CPQR_MINB) k_cpqr(const QrDesc* __restric
           acc[0] += __shfl_xor_sync(0xffffffffu, acc[0], o);
         }
       }
-      // value t (re of column t for t < CB, im of column t - CB otherwise) sits in lane t << CPQR_SH
-      double2 w[CPQR_CB];
+      // value t (re of column t for t < CB, im of column t - CB otherwise) sits in lane t << SH
+      double2 w[CB];
 #pragma unroll
-      for (int v = 0; v < CPQR_CB; ++v) {
-        w[v].x = tau * __shfl_sync(0xffffffffu, acc[0], v << CPQR_SH);
-        w[v].y = tau * __shfl_sync(0xffffffffu, acc[0], (CPQR_CB + v) << CPQR_SH);
+      for (int v = 0; v < CB; ++v) {
+        w[v].x = tau * __shfl_sync(0xffffffffu, acc[0], v << SH);
+        w[v].y = tau * __shfl_sync(0xffffffffu, acc[0], (CB + v) << SH);
       }
       for (int i = j + lane; i < m; i += 32) {
         const double2 ui = u[i];
 #pragma unroll
-        for (int v = 0; v < CPQR_CB; ++v) {
+        for (int v = 0; v < CB; ++v) {
           if (v < nc) {
             double2* pc = M + i + (int64_t)(c0 + v) * ld;
             *pc = cfms(ui, w[v], *pc);
@@ -936,10 +937,17 @@ int wsbm_lu_solve_fused_batched(const LuSolveDesc* d_desc, int nbatch, int max_n
 
 int wsbm_cpqr_batched(const QrDesc* d_desc, int nbatch, int mode, int max_m, cudaStream_t st) {
   if (nbatch <= 0) return 0;
-  if (max_m <= CPQR_TPC_MAXM)
-    k_cpqr<true><<<nbatch, 256, (size_t)max_m * sizeof(double2), st>>>(d_desc, mode);
-  else
-    k_cpqr<false><<<nbatch, 256, 0, st>>>(d_desc, mode);
+  const WsbmTune tu = wsbm_tune_current();
+  if (max_m <= CPQR_TPC_MAXM) {
+    const int thr = tu.cpqr_threads == 128 ? 128 : 256;
+    k_cpqr<true, CPQR_CB><<<nbatch, thr, (size_t)max_m * sizeof(double2), st>>>(d_desc, mode);
+  } else if (tu.cpqr_cb == 2) {
+    k_cpqr<false, 2><<<nbatch, 256, 0, st>>>(d_desc, mode);
+  } else if (tu.cpqr_cb == 8) {
+    k_cpqr<false, 8><<<nbatch, 256, 0, st>>>(d_desc, mode);
+  } else {
+    k_cpqr<false, 4><<<nbatch, 256, 0, st>>>(d_desc, mode);
+  }
   wsbm_count_launch();
   return cudaGetLastError() == cudaSuccess ? 0 : -3;
 }
@@ -1189,10 +1197,16 @@ void lub_rec(const LubCtx& x, int c0, int c1) {
 }
 }  // namespace
 
-static int lub_nb(int n) { return n >= LUB_BIG_N ? LUB_NB_BIG : LUB_NB; }
+int wsbm_lu_big_large_n() { return LUB_BIG_N; }
+
+// outer panel width: the tuned one of n's size class (LUB_NB / LUB_NB_BIG by default)
+static int lub_nb(int n) {
+  const WsbmTune t = wsbm_tune_current();
+  return n >= LUB_BIG_N ? t.root_nb_large : t.root_nb_mid;
+}
 
 size_t wsbm_lu_big_ws_bytes(int n) {
-  size_t b = wsbm_zgemm_tc_ws_bytes(n, n, lub_nb(n));
+  size_t b = wsbm_zgemm_tc_ws_bytes(n, n, LUB_NB_BIG);  // either panel width fits
   b = (b + 255) & ~(size_t)255;
   b += ((size_t)n + 8) * sizeof(unsigned long long) + 256 + sizeof(LuDesc) + 256;
   b += (size_t)LUB_NB_BIG * LUB_NB_BIG * sizeof(double2) + 256;  // L11^-1
@@ -1200,10 +1214,14 @@ size_t wsbm_lu_big_ws_bytes(int n) {
 }
 
 int wsbm_lu_big(double2* A, int64_t lda, int n, int* piv, int* d_info, void* ws, cudaStream_t st) {
+  return wsbm_lu_big_nb(A, lda, n, piv, d_info, ws, st, lub_nb(n));
+}
+
+int wsbm_lu_big_nb(double2* A, int64_t lda, int n, int* piv, int* d_info, void* ws, cudaStream_t st, int nb) {
   if (n <= 0) return 0;
   if (!A || !piv || !ws || lda < n || ((uintptr_t)ws & 255)) return -1;
-  const int nb = lub_nb(n);
-  size_t off = (wsbm_zgemm_tc_ws_bytes(n, n, nb) + 255) & ~(size_t)255;
+  if (nb != LUB_NB && nb != LUB_NB_BIG) return -1;
+  size_t off = (wsbm_zgemm_tc_ws_bytes(n, n, LUB_NB_BIG) + 255) & ~(size_t)255;
   unsigned long long* key = (unsigned long long*)((char*)ws + off);
   off += ((size_t)n + 8) * sizeof(unsigned long long);
   off = (off + 255) & ~(size_t)255;
@@ -1328,6 +1346,78 @@ __global__ void k_lut_trinv(const LuSolveDesc* __restrict__ d, int j0, int jb, i
   }
 }
 
+// Inverses of the diagonal blocks of LU factors (unit lower L, upper U), for block triangular
+// solves whose products run on the tensor cores.  Item blockIdx.y with block width nb = q.nb,
+// block p = blockIdx.x (rows and columns p nb .. min(n, (p + 1) nb)), blockIdx.z = 0: L_pp^-1
+// into Linv + p nb^2, 1: U_pp^-1 into Uinv + p nb^2 (column-major, leading dimension nb; the
+// part outside a ragged last block is not written).  Thread j forms column j by substitution.
+// A zero diagonal entry of U leaves a zero row in U_pp^-1.
+__global__ void k_lu_dinv(const DinvDesc* __restrict__ d) {
+  const DinvDesc q = d[blockIdx.y];
+  const int nb = q.nb, p = blockIdx.x, j0 = p * nb;
+  if (j0 >= q.n) return;
+  const int b = min(nb, q.n - j0), j = threadIdx.x;
+  if (j >= b) return;
+  const bool upper = blockIdx.z != 0;
+  double2* x = (upper ? q.Uinv : q.Linv) + (int64_t)p * nb * nb + (int64_t)j * nb;
+  const double2* T = q.A + j0 + (int64_t)j0 * q.lda;
+  const double2 one = make_double2(1.0, 0.0), zero = make_double2(0.0, 0.0);
+  if (!upper) {
+    for (int i = 0; i < j; ++i) x[i] = zero;
+    x[j] = one;
+    for (int i = j + 1; i < b; ++i) {
+      double2 s = zero;
+      for (int t = j; t < i; ++t) s = cfms(T[i + (int64_t)t * q.lda], x[t], s);
+      x[i] = s;
+    }
+  } else {
+    for (int i = j + 1; i < b; ++i) x[i] = zero;
+    const double2 djj = T[j + (int64_t)j * q.lda];
+    x[j] = (djj.x == 0.0 && djj.y == 0.0) ? zero : cdiv(one, djj);
+    for (int i = j - 1; i >= 0; --i) {
+      double2 s = zero;
+      for (int t = i + 1; t <= j; ++t) s = cfms(T[i + (int64_t)t * q.lda], x[t], s);
+      const double2 dii = T[i + (int64_t)i * q.lda];
+      x[i] = (dii.x == 0.0 && dii.y == 0.0) ? zero : cdiv(s, dii);
+    }
+  }
+}
+
+int wsbm_lu_dinv_batched(const DinvDesc* d_desc, int nitems, int max_blocks, int max_nb, cudaStream_t st) {
+  if (nitems <= 0 || max_blocks <= 0) return 0;
+  if (max_nb < 1 || max_nb > 256) return -1;
+  for (int c = 0; c < nitems; c += LAUNCH_MAX_Y) {
+    const int n = std::min(LAUNCH_MAX_Y, nitems - c);
+    k_lu_dinv<<<dim3(max_blocks, n, 2), max_nb, 0, st>>>(d_desc + c);
+    wsbm_count_launch();
+  }
+  return cudaGetLastError() == cudaSuccess ? 0 : -3;
+}
+
+// perm of the row interchanges piv (piv[j]: the row swapped with row j at step j, j = 0..n-1):
+// (P b)[r] = b[perm[r]].  One thread per item (the swaps are sequential).
+__global__ void k_piv_perm(const PermDesc* __restrict__ d, int nitems) {
+  const int it = blockIdx.x * blockDim.x + threadIdx.x;
+  if (it >= nitems) return;
+  const PermDesc q = d[it];
+  for (int r = 0; r < q.n; ++r) q.perm[r] = r;
+  for (int j = 0; j < q.n; ++j) {
+    const int p = q.piv[j];
+    if (p > j && p < q.n) {
+      const int t = q.perm[j];
+      q.perm[j] = q.perm[p];
+      q.perm[p] = t;
+    }
+  }
+}
+
+int wsbm_piv_perm_batched(const PermDesc* d_desc, int nitems, cudaStream_t st) {
+  if (nitems <= 0) return 0;
+  k_piv_perm<<<(nitems + 63) / 64, 64, 0, st>>>(d_desc, nitems);
+  wsbm_count_launch();
+  return cudaGetLastError() == cudaSuccess ? 0 : -3;
+}
+
 size_t wsbm_lu_solve_tc_ws_bytes(const LuSolveDesc* h, int nbatch) {
   // the largest product step: two items per box (A part and B part) of the first panel
   std::vector<TcProduct> p;
@@ -1352,7 +1442,13 @@ size_t wsbm_lu_solve_tc_ws_bytes(const LuSolveDesc* h, int nbatch) {
 
 int wsbm_lu_solve_tc_batched(const LuSolveDesc* h, const LuSolveDesc* d, int nbatch, const LuDesc* d_lu,
                              void* ws, cudaStream_t st) {
+  return wsbm_lu_solve_tc_batched_nb(h, d, nbatch, d_lu, ws, st, wsbm_tune_current().box_nb);
+}
+
+int wsbm_lu_solve_tc_batched_nb(const LuSolveDesc* h, const LuSolveDesc* d, int nbatch, const LuDesc* d_lu,
+                                void* ws, cudaStream_t st, int nb) {
   if (nbatch <= 0) return 0;
+  if (nb < 8 || nb > LUT_NB || nb % 8) return -1;
   if (nbatch > 32767 || !h || !d || !d_lu || !ws) return -1;
   int maxn = 0, maxnc = 0;
   for (int i = 0; i < nbatch; ++i) {
@@ -1399,16 +1495,16 @@ int wsbm_lu_solve_tc_batched(const LuSolveDesc* h, const LuSolveDesc* d, int nba
     items.push_back(t);
   };
   // ---- factorization
-  for (int j0 = 0; j0 < maxn; j0 += LUT_NB) {
-    k_lu_panel<<<nbatch, 256, 0, st>>>(d_lu, j0, LUT_NB, nullptr);
-    k_lut_swap<<<dim3(tiles_x((maxnc + 127) / 128), nbatch), 128, 0, st>>>(d, j0, LUT_NB);
-    k_lut_trinv<<<dim3(1, nbatch), LUT_NB, 0, st>>>(d, j0, LUT_NB, 0, X, ldx);
+  for (int j0 = 0; j0 < maxn; j0 += nb) {
+    k_lu_panel<<<nbatch, 256, 0, st>>>(d_lu, j0, nb, nullptr);
+    k_lut_swap<<<dim3(tiles_x((maxnc + 127) / 128), nbatch), 128, 0, st>>>(d, j0, nb);
+    k_lut_trinv<<<dim3(1, nbatch), nb, 0, st>>>(d, j0, nb, 0, X, ldx);
     wsbm_count_launches(3);
     // U12 = L11^-1 [A12 | B1]  (in place: the digit planes are formed before C is written)
     for (int i = 0; i < nbatch; ++i) {
       const LuSolveDesc& q = h[i];
       if (j0 >= q.n) continue;
-      const int jb = std::min(LUT_NB, q.n - j0), je = j0 + jb;
+      const int jb = std::min(nb, q.n - j0), je = j0 + jb;
       const double2* Li = X + i * ldx;
       add(Li, jb, q.A + j0 + (int64_t)je * q.lda, q.lda, q.A + j0 + (int64_t)je * q.lda, q.lda, jb, q.n - je, jb);
       add(Li, jb, q.B + j0, q.ldb, q.B + j0, q.ldb, jb, q.nrhs, jb);
@@ -1418,7 +1514,7 @@ int wsbm_lu_solve_tc_batched(const LuSolveDesc* h, const LuSolveDesc* d, int nba
     for (int i = 0; i < nbatch; ++i) {
       const LuSolveDesc& q = h[i];
       if (j0 >= q.n) continue;
-      const int jb = std::min(LUT_NB, q.n - j0), je = j0 + jb;
+      const int jb = std::min(nb, q.n - j0), je = j0 + jb;
       const double2* L21 = q.A + je + (int64_t)j0 * q.lda;
       add(L21, q.lda, q.A + j0 + (int64_t)je * q.lda, q.lda, q.A + je + (int64_t)je * q.lda, q.lda, q.n - je,
           q.n - je, jb);
@@ -1427,20 +1523,20 @@ int wsbm_lu_solve_tc_batched(const LuSolveDesc* h, const LuSolveDesc* d, int nba
     if (int rc = run(mone, one)) return rc;
   }
   // ---- back substitution X = U^-1 (L^-1 P B), panels from the bottom
-  for (int j0 = ((maxn - 1) / LUT_NB) * LUT_NB; j0 >= 0; j0 -= LUT_NB) {
-    k_lut_trinv<<<dim3(1, nbatch), LUT_NB, 0, st>>>(d, j0, LUT_NB, 1, X, ldx);
+  for (int j0 = ((maxn - 1) / nb) * nb; j0 >= 0; j0 -= nb) {
+    k_lut_trinv<<<dim3(1, nbatch), nb, 0, st>>>(d, j0, nb, 1, X, ldx);
     wsbm_count_launch();
     for (int i = 0; i < nbatch; ++i) {
       const LuSolveDesc& q = h[i];
       if (j0 >= q.n) continue;
-      const int jb = std::min(LUT_NB, q.n - j0);
+      const int jb = std::min(nb, q.n - j0);
       add(X + i * ldx, jb, q.B + j0, q.ldb, q.B + j0, q.ldb, jb, q.nrhs, jb);
     }
     if (int rc = run(one, zero)) return rc;
     for (int i = 0; i < nbatch; ++i) {
       const LuSolveDesc& q = h[i];
       if (j0 >= q.n || j0 == 0) continue;
-      const int jb = std::min(LUT_NB, q.n - j0);
+      const int jb = std::min(nb, q.n - j0);
       add(q.A + (int64_t)j0 * q.lda, q.lda, q.B + j0, q.ldb, q.B, q.ldb, j0, q.nrhs, jb);
     }
     if (int rc = run(mone, one)) return rc;

@@ -3,6 +3,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 #define WSBM_NB 32  // panel / block width of the blocked LU and triangular solves
 
 // Kernel-launch counter of the library (every launch site calls wsbm_count_launch()).
@@ -16,6 +18,19 @@ int wsbm_sm_count();
 // Opt a kernel in to `bytes` of dynamic shared memory on the current device (remembered per
 // device and kernel, thread safe).  Returns cudaSuccess or the error of the attribute call.
 cudaError_t wsbm_smem_optin(const void* kernel, size_t bytes);
+
+// autotune.cu: launch shapes, per device (defaults until an autotune call or wsbm_tuning_set):
+// rows per raster group of the GEMM's tile order, panel width of the batched box LU (<= 64),
+// outer panel width of the root LU below and from wsbm_lu_big_large_n() unknowns (128 or 256);
+// tile width (16, 32, 64) and CTAs per SM of the node-pair and proxy entry kernels; threads per
+// CTA of the thread-per-column QR (128 or 256) and columns per warp pass of the warp QR (2, 4
+// or 8); the smallest root order whose solves with many right-hand sides use the tensor cores.
+struct WsbmTune {
+  int tc_group, box_nb, root_nb_mid, root_nb_large, tuned;
+  int pair_tf, pair_ctas, proxy_tf, proxy_ctas, cpqr_threads, cpqr_cb, tuned_build;
+  int solve_tc_min;
+};
+WsbmTune wsbm_tune_current();
 
 // tc_gemm.cu: C (m x n) = beta C + alpha A (m x k) B (k x n), complex128 column-major, on the
 // tensor cores from exact 8-bit digit planes (FP64-level accuracy).  ws: 256-byte aligned
@@ -39,6 +54,22 @@ struct TcProduct {
 int wsbm_zgemm_tc_batched(const TcProduct* p, int nitems, double2 alpha, double2 beta, void* ws,
                           cudaStream_t st);
 size_t wsbm_zgemm_tc_batched_ws_bytes(const TcProduct* p, int nitems);
+// The same with an explicit raster group (rows of tiles per group, 1..64).
+int wsbm_zgemm_tc_batched_g(const TcProduct* p, int nitems, double2 alpha, double2 beta, void* ws,
+                            cudaStream_t st, int group);
+// The same split into a host-side plan (item tables and work-space layout, built once) and a
+// launch sequence that reads the item tables from a device copy of `tab` made by the caller:
+// no host memory is read at launch, so the launches can be captured into a CUDA graph.
+// ws: 256-byte aligned, ws_bytes (the item-table region at off_tab is not used by _run).
+struct TcPlan {
+  int nitems = 0, tiles = 0, kmax = 0, maxm = 0, maxn = 0;
+  int64_t ra = 0, rb = 0;
+  size_t off_exp = 0, off_tab = 0, ws_bytes = 0;
+  std::vector<unsigned char> tab;
+};
+int wsbm_zgemm_tc_plan(const TcProduct* p, int nitems, TcPlan* out);
+int wsbm_zgemm_tc_run(const TcPlan& pl, const void* dtab, double2 alpha, double2 beta, void* ws,
+                      cudaStream_t st, int group);
 // Synchronizes the stream and returns -5 (and clears the flag) if a bounded wait of the GEMM
 // kernel ran out since the last call, else 0 (-3 on a CUDA error).
 int wsbm_zgemm_tc_status(cudaStream_t st);
@@ -116,7 +147,30 @@ int wsbm_lu_solve_fused_batched(const LuSolveDesc* d_desc, int nbatch, int max_n
 // per item.  ws: 256-byte aligned, wsbm_lu_solve_tc_ws_bytes(h, nbatch) bytes.  Enqueues only.
 int wsbm_lu_solve_tc_batched(const LuSolveDesc* h, const LuSolveDesc* d, int nbatch, const LuDesc* d_lu,
                              void* ws, cudaStream_t st);
+// The same with an explicit panel width nb (8 <= nb <= 64, a multiple of 8).
+int wsbm_lu_solve_tc_batched_nb(const LuSolveDesc* h, const LuSolveDesc* d, int nbatch, const LuDesc* d_lu,
+                                void* ws, cudaStream_t st, int nb);
 size_t wsbm_lu_solve_tc_ws_bytes(const LuSolveDesc* h, int nbatch);
+
+// Inverses of the nb x nb diagonal blocks (nb <= 256, per item) of LU factors A (n x n, unit
+// lower L and upper U): block p of L into Linv + p nb^2, of U into Uinv + p nb^2 (leading
+// dimension nb).  max_blocks: the largest ceil(n / nb), max_nb the largest nb of the batch.
+// Enqueues only; returns 0, -1 or -3.
+struct DinvDesc {
+  const double2* A;
+  int64_t lda;
+  double2* Linv;
+  double2* Uinv;
+  int32_t n, nb;
+};
+int wsbm_lu_dinv_batched(const DinvDesc* d_desc, int nitems, int max_blocks, int max_nb, cudaStream_t st);
+// The row permutation of LU row interchanges: perm (device int32 n) with (P b)[r] = b[perm[r]].
+struct PermDesc {
+  const int32_t* piv;
+  int32_t* perm;
+  int32_t n, pad;
+};
+int wsbm_piv_perm_batched(const PermDesc* d_desc, int nitems, cudaStream_t st);
 
 int wsbm_gemm_batched(const GemmDesc* d_desc, int nbatch, int max_m, int max_n, cudaStream_t st);
 int wsbm_lu_batched(const LuDesc* d_desc, int nbatch, int max_n, int* d_info, cudaStream_t st);
@@ -125,6 +179,9 @@ int wsbm_lu_batched(const LuDesc* d_desc, int nbatch, int max_n, int* d_info, cu
 // space of wsbm_lu_big_ws_bytes(n) bytes; d_info (device int, may be NULL) receives j + 1 when
 // pivot j is exactly zero.  Enqueues only; returns 0, -1 or -3.
 int wsbm_lu_big(double2* A, int64_t lda, int n, int* piv, int* d_info, void* ws, cudaStream_t st);
+// The same with an explicit outer panel width nb (128 or 256).
+int wsbm_lu_big_nb(double2* A, int64_t lda, int n, int* piv, int* d_info, void* ws, cudaStream_t st, int nb);
+int wsbm_lu_big_large_n();  // n from which the root LU takes the large-class panel width
 size_t wsbm_lu_big_ws_bytes(int n);
 int wsbm_trsm_batched(const TrsmDesc* d_desc, int nbatch, int max_n, int max_nrhs, int lower,
                       cudaStream_t st);

@@ -50,18 +50,22 @@ __device__ __forceinline__ void load_slot(const DevGeom& g, const int32_t* nodes
   s.p1 = pos[2 * t + 1];
 }
 
+// TF slots along the fast (contiguous-output) dimension x TS = WSBM_PAIR_THREADS / TF along the
+// other (TF a power of two, 16..64).
+template <int TF>
 __global__ void __launch_bounds__(WSBM_PAIR_THREADS)
     k_pairs(DevGeom g0, Phys ph0, const PairTask* __restrict__ tasks, int ntasks, int64_t ntiles,
             const DevGeom* __restrict__ geos, const Phys* __restrict__ phys) {
+  constexpr int TS = WSBM_PAIR_THREADS / TF;
   __shared__ HkTables T;
-  __shared__ SlotData sf[WSBM_TILE_F];
-  __shared__ SlotData ss[WSBM_TILE_S];
+  __shared__ SlotData sf[TF];
+  __shared__ SlotData ss[TS];
   __shared__ int s_cnt[WSBM_PAIR_THREADS / 32][3];
   __shared__ int16_t s_list[WSBM_PAIR_THREADS];
   __shared__ int s_ntot;
   hk_stage_tables(&T);
-  const int tx = threadIdx.x & (WSBM_TILE_F - 1);
-  const int ty = threadIdx.x / WSBM_TILE_F;
+  const int tx = threadIdx.x & (TF - 1);
+  const int ty = threadIdx.x / TF;
   const int stride = sizeof(PairTask) / sizeof(int32_t);
   for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     int ti = find_task_by_tile(&tasks[0].tile0, stride, ntasks, tile);
@@ -71,12 +75,12 @@ __global__ void __launch_bounds__(WSBM_PAIR_THREADS)
     const bool fc = tk.fastc != 0;
     const int nf = fc ? tk.nc : tk.nr;
     const int ns = fc ? tk.nr : tk.nc;
-    const int nft = (nf + WSBM_TILE_F - 1) / WSBM_TILE_F;
+    const int nft = (nf + TF - 1) / TF;
     const int64_t lt = tile - tk.tile0;
-    const int f0 = (int)(lt % nft) * WSBM_TILE_F;
-    const int s0 = (int)(lt / nft) * WSBM_TILE_S;
+    const int f0 = (int)(lt % nft) * TF;
+    const int s0 = (int)(lt / nft) * TS;
     __syncthreads();  // previous tile done with the staged slots (and tables staged)
-    if (threadIdx.x < WSBM_TILE_F) {
+    if (threadIdx.x < TF) {
       int f = f0 + threadIdx.x;
       if (f < nf) {
         if (fc)
@@ -84,8 +88,8 @@ __global__ void __launch_bounds__(WSBM_PAIR_THREADS)
         else
           load_slot(g, tk.rnode, tk.rpos, f, sf[threadIdx.x]);
       }
-    } else if (threadIdx.x < WSBM_TILE_F + WSBM_TILE_S) {
-      int k = threadIdx.x - WSBM_TILE_F;
+    } else if (threadIdx.x < TF + TS) {
+      int k = threadIdx.x - TF;
       int s = s0 + k;
       if (s < ns) {
         if (fc)
@@ -145,7 +149,7 @@ __global__ void __launch_bounds__(WSBM_PAIR_THREADS)
     __syncthreads();
     if ((int)threadIdx.x < s_ntot) {
       const int me = s_list[threadIdx.x];
-      const int mx = me & (WSBM_TILE_F - 1), my = me / WSBM_TILE_F;
+      const int mx = me & (TF - 1), my = me / TF;
       const SlotData& R = fc ? ss[my] : sf[mx];
       const SlotData& C = fc ? sf[mx] : ss[my];
       double2 e[2][2];
@@ -362,28 +366,29 @@ __device__ __forceinline__ void proxy_col_mixed(const HkTables& T, const Phys& p
 }
 
 // MODE: WSBM_FP64, WSBM_MIXED or WSBM_MIXED_FINE
-template <int MODE>
+template <int MODE, int TF>
 __global__ void __launch_bounds__(WSBM_PAIR_THREADS)
     k_proxy(DevGeom g0, Phys ph0, const ProxyTask* __restrict__ tasks, int ntasks, int64_t ntiles,
             const DevGeom* __restrict__ geos, const Phys* __restrict__ phys) {
+  constexpr int TS = WSBM_PAIR_THREADS / TF;
   __shared__ HkTables T;
-  __shared__ ProxyPt sp[WSBM_TILE_F];
-  __shared__ SlotData ss[WSBM_TILE_S];
+  __shared__ ProxyPt sp[TF];
+  __shared__ SlotData ss[TS];
   hk_stage_tables(&T);
-  const int tx = threadIdx.x & (WSBM_TILE_F - 1);
-  const int ty = threadIdx.x / WSBM_TILE_F;
+  const int tx = threadIdx.x & (TF - 1);
+  const int ty = threadIdx.x / TF;
   const int stride = sizeof(ProxyTask) / sizeof(int32_t);
   for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     int ti = find_task_by_tile(&tasks[0].tile0, stride, ntasks, tile);
     const ProxyTask tk = tasks[ti];
     const DevGeom g = geos ? geos[tk.inst] : g0;
     const Phys ph = phys ? phys[tk.inst] : ph0;
-    const int nft = (tk.P + WSBM_TILE_F - 1) / WSBM_TILE_F;
+    const int nft = (tk.P + TF - 1) / TF;
     const int64_t lt = tile - tk.tile0;
-    const int m0 = (int)(lt % nft) * WSBM_TILE_F;
-    const int s0 = (int)(lt / nft) * WSBM_TILE_S;
+    const int m0 = (int)(lt % nft) * TF;
+    const int s0 = (int)(lt / nft) * TS;
     __syncthreads();
-    if (threadIdx.x < WSBM_TILE_F) {
+    if (threadIdx.x < TF) {
       int m = m0 + threadIdx.x;
       if (m < tk.P) {
         double sn, cs;
@@ -395,8 +400,8 @@ __global__ void __launch_bounds__(WSBM_PAIR_THREADS)
         sp[threadIdx.x].px = tk.cx + tk.rho * cs;
         sp[threadIdx.x].py = tk.cy + tk.rho * sn;
       }
-    } else if (threadIdx.x < WSBM_TILE_F + WSBM_TILE_S) {
-      int k = threadIdx.x - WSBM_TILE_F;
+    } else if (threadIdx.x < TF + TS) {
+      int k = threadIdx.x - TF;
       if (s0 + k < tk.nn) load_slot(g, tk.node, tk.pos, s0 + k, ss[k]);
     }
     __syncthreads();
@@ -486,40 +491,66 @@ __global__ void k_unknowns_to_slots(const int64_t* __restrict__ idx, int64_t n, 
 }
 
 // ------------------------------------------------------------------- host helpers ----
-static int grid_for(int64_t ntiles) {
-  const int64_t cap = (int64_t)wsbm_sm_count() * 16;
+static int grid_for(int64_t ntiles, int ctas = WSBM_ENTRY_CTAS) {
+  const int64_t cap = (int64_t)wsbm_sm_count() * ctas;
   return (int)(ntiles < cap ? ntiles : cap);
 }
 
-int64_t wsbm_pair_tiles(int32_t nr, int32_t nc, int32_t fastc) {
+static bool tile_ok(int tf, int ctas) { return (tf == 16 || tf == 32 || tf == 64) && ctas >= 1 && ctas <= 64; }
+
+int64_t wsbm_pair_tiles(int32_t nr, int32_t nc, int32_t fastc, int tf) {
   int32_t nf = fastc ? nc : nr, ns = fastc ? nr : nc;
   if (nf <= 0 || ns <= 0) return 0;
-  return (int64_t)((nf + WSBM_TILE_F - 1) / WSBM_TILE_F) * ((ns + WSBM_TILE_S - 1) / WSBM_TILE_S);
+  const int ts = WSBM_PAIR_THREADS / tf;
+  return (int64_t)((nf + tf - 1) / tf) * ((ns + ts - 1) / ts);
 }
 
-int64_t wsbm_proxy_tiles(int32_t nn, int32_t P) {
+int64_t wsbm_proxy_tiles(int32_t nn, int32_t P, int tf) {
   if (nn <= 0 || P <= 0) return 0;
-  return (int64_t)((P + WSBM_TILE_F - 1) / WSBM_TILE_F) * ((nn + WSBM_TILE_S - 1) / WSBM_TILE_S);
+  const int ts = WSBM_PAIR_THREADS / tf;
+  return (int64_t)((P + tf - 1) / tf) * ((nn + ts - 1) / ts);
 }
 
 int wsbm_launch_pairs(const DevGeom& g, const Phys& ph, const PairTask* d_tasks, int ntasks,
-                      int64_t ntiles, cudaStream_t st, const DevGeom* geos, const Phys* phys) {
+                      int64_t ntiles, cudaStream_t st, const DevGeom* geos, const Phys* phys, int tf,
+                      int ctas) {
   if (ntiles <= 0) return WSBM_OK;
-  k_pairs<<<grid_for(ntiles), WSBM_PAIR_THREADS, 0, st>>>(g, ph, d_tasks, ntasks, ntiles, geos, phys);
+  if (!tile_ok(tf, ctas)) return WSBM_ERR_INVALID_ARG;
+  const int gr = grid_for(ntiles, ctas);
+  if (tf == 16)
+    k_pairs<16><<<gr, WSBM_PAIR_THREADS, 0, st>>>(g, ph, d_tasks, ntasks, ntiles, geos, phys);
+  else if (tf == 64)
+    k_pairs<64><<<gr, WSBM_PAIR_THREADS, 0, st>>>(g, ph, d_tasks, ntasks, ntiles, geos, phys);
+  else
+    k_pairs<32><<<gr, WSBM_PAIR_THREADS, 0, st>>>(g, ph, d_tasks, ntasks, ntiles, geos, phys);
   wsbm_count_launch();
   return cudaGetLastError() == cudaSuccess ? WSBM_OK : WSBM_ERR_CUDA;
 }
 
+template <int MODE>
+static void launch_proxy_mode(int tf, int gr, cudaStream_t st, const DevGeom& g, const Phys& ph,
+                              const ProxyTask* d_tasks, int ntasks, int64_t ntiles, const DevGeom* geos,
+                              const Phys* phys) {
+  if (tf == 16)
+    k_proxy<MODE, 16><<<gr, WSBM_PAIR_THREADS, 0, st>>>(g, ph, d_tasks, ntasks, ntiles, geos, phys);
+  else if (tf == 64)
+    k_proxy<MODE, 64><<<gr, WSBM_PAIR_THREADS, 0, st>>>(g, ph, d_tasks, ntasks, ntiles, geos, phys);
+  else
+    k_proxy<MODE, 32><<<gr, WSBM_PAIR_THREADS, 0, st>>>(g, ph, d_tasks, ntasks, ntiles, geos, phys);
+}
+
 int wsbm_launch_proxy(const DevGeom& g, const Phys& ph, const ProxyTask* d_tasks, int ntasks,
                       int64_t ntiles, int mixed, cudaStream_t st, const DevGeom* geos,
-                      const Phys* phys) {
+                      const Phys* phys, int tf, int ctas) {
   if (ntiles <= 0) return WSBM_OK;
+  if (!tile_ok(tf, ctas)) return WSBM_ERR_INVALID_ARG;
+  const int gr = grid_for(ntiles, ctas);
   if (mixed == WSBM_MIXED)
-    k_proxy<WSBM_MIXED><<<grid_for(ntiles), WSBM_PAIR_THREADS, 0, st>>>(g, ph, d_tasks, ntasks, ntiles, geos, phys);
+    launch_proxy_mode<WSBM_MIXED>(tf, gr, st, g, ph, d_tasks, ntasks, ntiles, geos, phys);
   else if (mixed == WSBM_MIXED_FINE)
-    k_proxy<WSBM_MIXED_FINE><<<grid_for(ntiles), WSBM_PAIR_THREADS, 0, st>>>(g, ph, d_tasks, ntasks, ntiles, geos, phys);
+    launch_proxy_mode<WSBM_MIXED_FINE>(tf, gr, st, g, ph, d_tasks, ntasks, ntiles, geos, phys);
   else
-    k_proxy<WSBM_FP64><<<grid_for(ntiles), WSBM_PAIR_THREADS, 0, st>>>(g, ph, d_tasks, ntasks, ntiles, geos, phys);
+    launch_proxy_mode<WSBM_FP64>(tf, gr, st, g, ph, d_tasks, ntasks, ntiles, geos, phys);
   wsbm_count_launch();
   return cudaGetLastError() == cudaSuccess ? WSBM_OK : WSBM_ERR_CUDA;
 }

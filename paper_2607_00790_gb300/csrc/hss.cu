@@ -47,6 +47,16 @@
 #endif
 // Dense roots of at least this order are factored by the LU whose trailing updates run on
 // the tensor cores (wsbm_lu_big); smaller ones by the batched FP64 blocked LU.
+// Solves with at least WSBM_TCSOLVE_RHS right-hand sides run their products on the tensor
+// cores, and their LU solves of box factors of at least WSBM_LU_TC_MIN unknowns and of roots of
+// at least wsbm_tune_current().solve_tc_min unknowns (1024 unless set) as block solves there
+// (WSBM_TCSOLVE_NB rows per block); the other LU solves stay FP64 triangular solves.
+#ifndef WSBM_TCSOLVE_RHS
+#define WSBM_TCSOLVE_RHS 16
+#endif
+#ifndef WSBM_TCSOLVE_NB
+#define WSBM_TCSOLVE_NB 256
+#endif
 #ifndef WSBM_BIGLU_MIN
 #define WSBM_BIGLU_MIN 2048
 #endif
@@ -497,6 +507,7 @@ struct PairBatch {
   };
   std::vector<Ref> refs;
   int64_t tiles = 0, entries = 0, pairs = 0;
+  int tf = WSBM_TILE_F, ctas = WSBM_ENTRY_CTAS;  // tile shape and grid, fixed in prepare()
 
   // entries of the block (rowU x colU) of curve `inst`; `at` is that curve's slot scratch
   int64_t add(int inst, std::vector<int32_t>& at, const std::vector<int32_t>& rowU, int rbase,
@@ -530,21 +541,33 @@ struct PairBatch {
     t.nr = (int32_t)rn.size();
     t.nc = (int32_t)cn.size();
     t.trans = trans;
-    t.tile0 = (int32_t)tiles;
+    t.tile0 = 0;  // counted in prepare() for the launch's tile shape
     t.inst = inst;
-    // the longer slot list runs along the 32-wide fast dimension (fewer idle lanes); for
-    // equal lengths the one that gives contiguous stores
+    // the longer slot list runs along the fast tile dimension (fewer idle lanes); for equal
+    // lengths the one that gives contiguous stores
     t.fastc = t.nc > t.nr ? 1 : (t.nc < t.nr ? 0 : trans);
-    tiles += wsbm_pair_tiles(t.nr, t.nc, t.fastc);
     entries += e;
     pairs += (int64_t)rn.size() * cn.size();
     tasks.push_back(t);
     return e;
   }
 
-  // upload slot data and task list (before any timed region)
+  // tile shape (the tuned one for eq. (weakly_bm), the default for the comparison
+  // formulations) and tile numbering, then upload of slot data and task list (before any
+  // timed region)
   int prepare(wsbm_hss* h, std::vector<void*>& tmp) {
     if (tasks.empty()) return WSBM_OK;
+    if (h->prm.formulation == WSBM_FORM_WSBM) {
+      const WsbmTune tu = wsbm_tune_current();
+      tf = tu.pair_tf;
+      ctas = tu.pair_ctas;
+    }
+    tiles = 0;
+    for (auto& t : tasks) {
+      t.tile0 = (int32_t)tiles;
+      tiles += wsbm_pair_tiles(t.nr, t.nc, t.fastc, tf);
+    }
+    if (tiles > INT32_MAX) return WSBM_ERR_INVALID_ARG;
     int32_t* dints = nullptr;
     HK(upload(h, ints, &dints, tmp));
     for (size_t i = 0; i < tasks.size(); ++i) {
@@ -561,7 +584,7 @@ struct PairBatch {
     if (h->prm.formulation != WSBM_FORM_WSBM)
       return wsbm_launch_pairs_form(h->prm.formulation, h->g, h->ph, dtasks, (int)tasks.size(), tiles,
                                     h->st, geos, phys);
-    return wsbm_launch_pairs(h->g, h->ph, dtasks, (int)tasks.size(), tiles, h->st, geos, phys);
+    return wsbm_launch_pairs(h->g, h->ph, dtasks, (int)tasks.size(), tiles, h->st, geos, phys, tf, ctas);
   }
 };
 
@@ -571,6 +594,7 @@ struct ProxyBatch {
   std::vector<int32_t> ints;
   std::vector<std::pair<int64_t, int64_t>> refs;
   int64_t tiles = 0, entries = 0, pairs = 0;
+  int tf = WSBM_TILE_F, ctas = WSBM_ENTRY_CTAS;  // tile shape and grid, fixed in prepare()
 
   int64_t add(int inst, std::vector<int32_t>& at, const std::vector<int32_t>& U, const Box& b,
               int side, double2* out, int64_t ld) {
@@ -597,9 +621,8 @@ struct ProxyBatch {
     t.side = side;
     t.tr = 0;
     t.off = 0;
-    t.tile0 = (int32_t)tiles;
+    t.tile0 = 0;  // counted in prepare()
     t.inst = inst;
-    tiles += wsbm_proxy_tiles(t.nn, t.P);
     int64_t e = nU * 2 * b.P;
     entries += e;
     pairs += (int64_t)nn.size() * b.P;
@@ -607,8 +630,20 @@ struct ProxyBatch {
     return e;
   }
 
-  int prepare(wsbm_hss* h, std::vector<void*>& tmp) {
+  // forms: row blocks of a comparison formulation (default tile shape)
+  int prepare(wsbm_hss* h, std::vector<void*>& tmp, bool forms = false) {
     if (tasks.empty()) return WSBM_OK;
+    if (!forms) {
+      const WsbmTune tu = wsbm_tune_current();
+      tf = tu.proxy_tf;
+      ctas = tu.proxy_ctas;
+    }
+    tiles = 0;
+    for (auto& t : tasks) {
+      t.tile0 = (int32_t)tiles;
+      tiles += wsbm_proxy_tiles(t.nn, t.P, tf);
+    }
+    if (tiles > INT32_MAX) return WSBM_ERR_INVALID_ARG;
     int32_t* dints = nullptr;
     HK(upload(h, ints, &dints, tmp));
     for (size_t i = 0; i < tasks.size(); ++i) {
@@ -619,7 +654,8 @@ struct ProxyBatch {
   }
   int run(wsbm_hss* h, int mixed, const DevGeom* geos, const Phys* phys) {
     if (tasks.empty()) return WSBM_OK;
-    return wsbm_launch_proxy(h->g, h->ph, dtasks, (int)tasks.size(), tiles, mixed, h->st, geos, phys);
+    return wsbm_launch_proxy(h->g, h->ph, dtasks, (int)tasks.size(), tiles, mixed, h->st, geos, phys, tf,
+                             ctas);
   }
 };
 
@@ -987,7 +1023,7 @@ static int factor_levels(const std::vector<wsbm_hss*>& hs, const std::vector<int
   }
   HK(pb.prepare(h0, tmp));
   for (auto& xb : xbp) HK(xb.prepare(h0, tmp));
-  HK(xbf.prepare(h0, tmp));
+  HK(xbf.prepare(h0, tmp, true));
   // timed: the entry kernels only
   HC(cudaEventRecord(h0->ev[0], st));
   HK(pb.run(h0, ia.geos, ia.phys));
@@ -1921,6 +1957,9 @@ struct SolvePlan {
   cudaGraphExec_t exec = nullptr;
   int64_t launches = 0;
   bool graph_ok = true;
+  void* tcws = nullptr;  // work space of the tensor-core products (shared by their operations)
+  size_t tcws_bytes = 0;
+  bool uses_tc = false;
   ~SolvePlan() {
     if (cs) cudaStreamSynchronize(cs);
     if (exec) cudaGraphExecDestroy(exec);
@@ -2001,6 +2040,180 @@ static int plan_gathers(SolvePlan& P, const std::vector<GatherDesc>& g) {
   });
   return WSBM_OK;
 }
+// One launch sequence of the tensor-core product over `items` (C = beta C + alpha A B each; C
+// may be B itself: B's digit planes are formed before C is written): the item tables are built
+// and uploaded now; the work space is shared by every such operation of the plan and allocated
+// once all are known (plan_tc_finish).
+static int plan_tc(SolvePlan& P, const std::vector<TcProduct>& items, double2 alpha, double2 beta) {
+  for (size_t c0 = 0; c0 < items.size(); c0 += 65535) {
+    const int n = (int)std::min<size_t>(65535, items.size() - c0);
+    auto pl = std::make_shared<TcPlan>();
+    if (wsbm_zgemm_tc_plan(items.data() + c0, n, pl.get())) return WSBM_ERR_INVALID_ARG;
+    if (pl->tiles == 0) continue;
+    unsigned char* dtab = nullptr;
+    HK(plan_upload(P, pl->tab, &dtab));
+    P.tcws_bytes = std::max(P.tcws_bytes, pl->ws_bytes);
+    P.uses_tc = true;
+    const int group = wsbm_tune_current().tc_group;
+    SolvePlan* pp = &P;
+    P.ops.push_back([pl, dtab, alpha, beta, pp, group](cudaStream_t st) {
+      return wsbm_zgemm_tc_run(*pl, dtab, alpha, beta, pp->tcws, st, group) ? WSBM_ERR_CUDA : WSBM_OK;
+    });
+  }
+  return WSBM_OK;
+}
+static int plan_tc_finish(SolvePlan& P) {
+  if (!P.tcws_bytes) return WSBM_OK;
+  HK(wsbm_dev_alloc(P.alloc, P.tcws_bytes, P.st, &P.tcws));
+  P.mem.push_back(P.tcws);
+  return WSBM_OK;
+}
+static TcProduct tc_item(const double2* A, int64_t lda, const double2* B, int64_t ldb, double2* C, int64_t ldc,
+                         int m, int n, int k) {
+  TcProduct t;
+  t.A = A;
+  t.lda = lda;
+  t.B = B;
+  t.ldb = ldb;
+  t.C = C;
+  t.ldc = ldc;
+  t.m = m;
+  t.n = n;
+  t.k = k;
+  t.pad = 0;
+  return t;
+}
+
+// LU solves A x = y with many right-hand sides on the tensor cores, batched over matrices of
+// different orders (box factors D of a tree step, dense roots).  Item: t.T = LU of A (t.n x t.n,
+// leading dimension t.ldt), t.piv its row interchanges, y = t.B (leading dimension t.ldb, the
+// plan's nrhs columns), overwritten by x.  Blocked by nb = min(n, WSBM_TCSOLVE_NB) rows: y is
+// permuted into a working copy W; then, panel by panel, W_p <- L_pp^-1 W_p and
+// W_below -= L_below,p W_p (forward), W_p <- U_pp^-1 W_p and W_above -= U_above,p W_p
+// (backward), with the inverses of the diagonal blocks and the permutation formed once per plan
+// and every product on the tensor cores (one launch sequence per panel step over all items);
+// W is copied back to y.
+static int plan_lu_tc(SolvePlan& P, const std::vector<TrsmDesc>& items) {
+  if (items.empty()) return WSBM_OK;
+  const int nrhs = P.nrhs;
+  const double2 one = make_double2(1.0, 0.0), zero = make_double2(0.0, 0.0), mone = make_double2(-1.0, 0.0);
+  struct R {
+    const double2* LU;
+    int64_t ld;
+    int n, nb, np;
+    double2 *Li, *Ui, *W;
+  };
+  size_t tot_inv = 0, tot_w = 0, tot_perm = 0;
+  for (const TrsmDesc& t : items) {
+    const int nb = std::min(t.n, WSBM_TCSOLVE_NB), np = (t.n + nb - 1) / nb;
+    tot_inv += (size_t)np * nb * nb;
+    tot_w += (size_t)t.n * nrhs;
+    tot_perm += ((size_t)t.n + 63) / 64 * 64;
+  }
+  // one allocation per kind: inverses, working copies, permutations
+  double2 *Li, *Ui, *W;
+  int32_t* perm;
+  HK(plan_alloc(P, tot_inv * sizeof(double2), &Li));
+  HK(plan_alloc(P, tot_inv * sizeof(double2), &Ui));
+  HK(plan_alloc(P, tot_w * sizeof(double2), &W));
+  HK(wsbm_dev_alloc(P.alloc, tot_perm * sizeof(int32_t), P.st, (void**)&perm));
+  P.mem.push_back(perm);
+  std::vector<R> rr;
+  std::vector<DinvDesc> dd;
+  std::vector<PermDesc> pd;
+  std::vector<GatherDesc> g0;
+  std::vector<CopyDesc> cfin;
+  int maxp = 0, maxnb = 0;
+  size_t oi = 0, ow = 0, op = 0;
+  for (const TrsmDesc& t : items) {
+    R r;
+    r.LU = t.T;
+    r.ld = t.ldt;
+    r.n = t.n;
+    r.nb = std::min(t.n, WSBM_TCSOLVE_NB);
+    r.np = (t.n + r.nb - 1) / r.nb;
+    r.Li = Li + oi;
+    r.Ui = Ui + oi;
+    r.W = W + ow;
+    oi += (size_t)r.np * r.nb * r.nb;
+    ow += (size_t)t.n * nrhs;
+    int32_t* pm = perm + op;
+    op += ((size_t)t.n + 63) / 64 * 64;
+    dd.push_back({t.T, t.ldt, r.Li, r.Ui, t.n, r.nb});
+    pd.push_back({t.piv, pm, t.n, 0});
+    g0.push_back({r.W, t.B, pm, t.n, t.ldb, t.n, nrhs});
+    cfin.push_back({t.B, r.W, t.ldb, t.n, t.n, nrhs});
+    maxp = std::max(maxp, r.np);
+    maxnb = std::max(maxnb, r.nb);
+    rr.push_back(r);
+  }
+  // inverses of the diagonal blocks and the permutations: once, now (not recorded operations)
+  {
+    DinvDesc* d = nullptr;
+    PermDesc* q = nullptr;
+    HK(plan_upload(P, dd, &d));
+    HK(plan_upload(P, pd, &q));
+    if (wsbm_lu_dinv_batched(d, (int)dd.size(), maxp, maxnb, P.st)) return WSBM_ERR_CUDA;
+    if (wsbm_piv_perm_batched(q, (int)pd.size(), P.st)) return WSBM_ERR_CUDA;
+  }
+  HK(plan_gathers(P, g0));
+  std::vector<TcProduct> i1, i2;
+  for (int q = 0; q < maxp; ++q) {  // forward: unit lower L
+    i1.clear();
+    i2.clear();
+    for (const R& r : rr) {
+      if (q >= r.np) continue;
+      const int j0 = q * r.nb, jb = std::min(r.nb, r.n - j0), je = j0 + jb;
+      i1.push_back(tc_item(r.Li + (int64_t)q * r.nb * r.nb, r.nb, r.W + j0, r.n, r.W + j0, r.n, jb, nrhs, jb));
+      if (je < r.n)
+        i2.push_back(tc_item(r.LU + je + (int64_t)j0 * r.ld, r.ld, r.W + j0, r.n, r.W + je, r.n, r.n - je, nrhs, jb));
+    }
+    HK(plan_tc(P, i1, one, zero));
+    HK(plan_tc(P, i2, mone, one));
+  }
+  for (int q = 0; q < maxp; ++q) {  // backward: U, from each matrix's last panel
+    i1.clear();
+    i2.clear();
+    for (const R& r : rr) {
+      const int p = r.np - 1 - q;
+      if (p < 0) continue;
+      const int j0 = p * r.nb, jb = std::min(r.nb, r.n - j0);
+      i1.push_back(tc_item(r.Ui + (int64_t)p * r.nb * r.nb, r.nb, r.W + j0, r.n, r.W + j0, r.n, jb, nrhs, jb));
+      if (j0 > 0) i2.push_back(tc_item(r.LU + (int64_t)j0 * r.ld, r.ld, r.W + j0, r.n, r.W, r.n, j0, nrhs, jb));
+    }
+    HK(plan_tc(P, i1, one, zero));
+    HK(plan_tc(P, i2, mone, one));
+  }
+  return plan_copies(P, cfin);
+}
+
+// LU solves of a plan step: with WSBM_TCSOLVE_RHS or more right-hand sides, the matrices of at
+// least min_n unknowns on the tensor cores (plan_lu_tc), the rest as FP64 triangular solves.
+static int plan_lu_solves_auto(SolvePlan& P, const std::vector<TrsmDesc>& t, int min_n) {
+  if (P.nrhs < WSBM_TCSOLVE_RHS) return plan_lu_solves(P, t);
+  std::vector<TrsmDesc> tc, fp;
+  for (const TrsmDesc& x : t) (x.n >= min_n ? tc : fp).push_back(x);
+  HK(plan_lu_solves(P, fp));
+  return plan_lu_tc(P, tc);
+}
+
+// Products of a plan step: on the tensor cores with WSBM_TCSOLVE_RHS or more right-hand sides
+// (when the items share alpha and beta and none is transposed), else the FP64 kernel.
+static int plan_gemms_auto(SolvePlan& P, const std::vector<GemmDesc>& g) {
+  if (g.empty()) return WSBM_OK;
+  bool tc = P.nrhs >= WSBM_TCSOLVE_RHS;
+  for (const GemmDesc& x : g)
+    if (x.ta || x.alpha.x != g[0].alpha.x || x.alpha.y != g[0].alpha.y || x.beta.x != g[0].beta.x ||
+        x.beta.y != g[0].beta.y || x.k > 32768)
+      tc = false;
+  if (!tc) return plan_gemms(P, g);
+  std::vector<TcProduct> it;
+  it.reserve(g.size());
+  for (const GemmDesc& x : g)
+    if (x.m > 0 && x.n > 0 && x.k > 0) it.push_back(tc_item(x.A, x.lda, x.B, x.ldb, x.C, x.ldc, x.m, x.n, x.k));
+  return plan_tc(P, it, g[0].alpha, g[0].beta);
+}
+
 static TrsmDesc lu_desc(const double2* T, int64_t ldt, double2* B, int64_t ldb, const int32_t* piv,
                         int n, int nrhs) {
   TrsmDesc t;
@@ -2129,11 +2342,11 @@ static int plan_build(SolvePlan& P) {
       }
     }
     HK(plan_copies(P, c1));
-    HK(plan_lu_solves(P, sd));
+    HK(plan_lu_solves_auto(P, sd, WSBM_LU_TC_MIN));
     HK(plan_gathers(P, gd));
     HK(plan_copies(P, rc0));
-    HK(plan_gemms(P, g1));
-    HK(plan_gemms(P, g2));
+    HK(plan_gemms_auto(P, g1));
+    HK(plan_gemms_auto(P, g2));
   }
   // ---- roots
   {
@@ -2154,7 +2367,7 @@ static int plan_build(SolvePlan& P) {
       rs.push_back(lu_desc(h->root, h->root_n, Y[i], h->root_n, h->root_piv, h->root_n, nrhs));
     }
     HK(plan_copies(P, c));
-    HK(plan_lu_solves(P, rs));
+    HK(plan_lu_solves_auto(P, rs, wsbm_tune_current().solve_tc_min));
   }
   // ---- down sweep: t = bt - Dhat y (in RT), xh -= Z t; y of a box = its slice of the parent's x
   for (int t = T - 1; t >= 0; --t) {
@@ -2187,8 +2400,8 @@ static int plan_build(SolvePlan& P) {
       }
     }
     HK(plan_copies(P, cb));
-    HK(plan_gemms(P, g1));
-    HK(plan_gemms(P, g2));
+    HK(plan_gemms_auto(P, g1));
+    HK(plan_gemms_auto(P, g2));
   }
   // ---- leaves back to the interleaved vector, then u, q
   {
@@ -2214,6 +2427,7 @@ static int plan_build(SolvePlan& P) {
       return WSBM_OK;
     });
   }
+  HK(plan_tc_finish(P));
   return cudaGetLastError() == cudaSuccess ? WSBM_OK : WSBM_ERR_CUDA;
 }
 
@@ -2301,6 +2515,11 @@ static int solve_set(std::shared_ptr<SolvePlan>& slot, const std::vector<wsbm_hs
     HC(cudaMemcpyAsync(q[i], P.qo[i], bytes, cudaMemcpyDeviceToDevice, st));
   }
   HC(cudaStreamSynchronize(st));
+  if (P.uses_tc) {  // a bounded wait of the tensor-core kernel that ran out
+    const int t = wsbm_zgemm_tc_status(st);
+    if (t == -5) return WSBM_ERR_TIMEOUT;
+    if (t) return WSBM_ERR_CUDA;
+  }
   return WSBM_OK;
 }
 

@@ -337,6 +337,7 @@ struct TcArgs {
   int nkb;              // K blocks of TC_BK real values (common to all items)
   double2 alpha, beta;
   int sub;              // alpha = -1, beta = 1 (C -= A B): two FP64 additions per entry
+  int group;            // row tiles per raster group of the tile order
   const TcItem* items;
   const int* rexp;
   const int* cexp;
@@ -353,10 +354,9 @@ __device__ __forceinline__ int find_item(const TcArgs& a, int t) {
   return lo;
 }
 
-// Tile r of an item -> (tm, tn): groups of 8 row tiles, so that the CTAs running at the same
+// Tile r of an item -> (tm, tn): groups of G row tiles, so that the CTAs running at the same
 // time share their A and B digit planes in L2.
-__device__ __forceinline__ void tile_coords(const TcItem& it, int r, int& tm, int& tn) {
-  const int G = 8;
+__device__ __forceinline__ void tile_coords(const TcItem& it, int r, int G, int& tm, int& tn) {
   const int per_group = G * it.tiles_n;
   const int g = r / per_group, q = r % per_group;
   const int gm = min(G, it.tiles_m - g * G);
@@ -406,7 +406,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
         const TcItem item = a.items[find_item(a, t)];
         int tm, tn;
-        tile_coords(item, t - item.tile0, tm, tn);
+        tile_coords(item, t - item.tile0, a.group, tm, tn);
         for (int kb = 0; kb < a.nkb && ok; ++kb, ++it) {
           const uint32_t s = it % TC_STAGES, ph = (it / TC_STAGES) & 1;
           if (!(ok = mbar_wait(empty0 + 8 * s, ph ^ 1))) break;
@@ -475,7 +475,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
       const TcItem item = a.items[find_item(a, t)];
       int tm, tn;
-      tile_coords(item, t - item.tile0, tm, tn);
+      tile_coords(item, t - item.tile0, a.group, tm, tn);
       long long T[TC_BN / 2];
 #pragma unroll
       for (int c = 0; c < TC_BN / 2; ++c) {
@@ -641,9 +641,14 @@ static int make_map(CUtensorMap* map, void* planes, int64_t rows, int64_t Ka, in
   return r == CUDA_SUCCESS ? 0 : -3;
 }
 
-int wsbm_zgemm_tc_batched(const TcProduct* p, int nitems, double2 alpha, double2 beta, void* ws, cudaStream_t st) {
+int wsbm_zgemm_tc_plan(const TcProduct* p, int nitems, TcPlan* out) {
+  if (!out) return -1;
+  out->nitems = 0;
+  out->tiles = 0;
+  out->ws_bytes = 0;
+  out->tab.clear();
   if (nitems <= 0) return 0;
-  if (!p || !ws || ((uintptr_t)ws & 255) != 0) return -1;
+  if (!p || nitems > 65535) return -1;
   int kmax = 1, maxm = 0, maxn = 0;
   for (int i = 0; i < nitems; ++i) {
     const TcProduct& q = p[i];
@@ -653,21 +658,16 @@ int wsbm_zgemm_tc_batched(const TcProduct* p, int nitems, double2 alpha, double2
     maxm = q.m > maxm ? q.m : maxm;
     maxn = q.n > maxn ? q.n : maxn;
   }
-  if (nitems > 65535) return -1;
   int64_t ra, rb;
   size_t off_exp, off_tab;
-  tc_ws_layout(p, nitems, kmax, &ra, &rb, &off_exp, &off_tab);
-  const int64_t Ka = tc_ka(kmax);
-  __nv_bfloat16* PA = (__nv_bfloat16*)ws;
-  __nv_bfloat16* PB = PA + (size_t)TC_S * ra * Ka;
-  int* exps = (int*)((char*)ws + off_exp);
-  // item tables (host staging, copied in stream order before the launches that read them)
-  std::vector<unsigned char> tab((size_t)nitems * (sizeof(TcItem) + 2 * sizeof(TcSrc)));
-  TcItem* items = (TcItem*)tab.data();
-  TcSrc* sa = (TcSrc*)(tab.data() + (size_t)nitems * sizeof(TcItem));
+  out->ws_bytes = tc_ws_layout(p, nitems, kmax, &ra, &rb, &off_exp, &off_tab);
+  if (ra >= INT32_MAX || rb >= INT32_MAX) return -1;
+  // item tables
+  out->tab.assign((size_t)nitems * (sizeof(TcItem) + 2 * sizeof(TcSrc)), 0);
+  TcItem* items = (TcItem*)out->tab.data();
+  TcSrc* sa = (TcSrc*)(out->tab.data() + (size_t)nitems * sizeof(TcItem));
   TcSrc* sb = sa + nitems;
-  int64_t arow = 0, brow = 0, eo = 0;
-  int tiles = 0;
+  int64_t arow = 0, brow = 0, eo = 0, tiles = 0;
   for (int i = 0; i < nitems; ++i) {
     const TcProduct& q = p[i];
     TcItem& it = items[i];
@@ -682,47 +682,87 @@ int wsbm_zgemm_tc_batched(const TcProduct* p, int nitems, double2 alpha, double2
     it.tiles_m = (q.m + TC_BM - 1) / TC_BM;
     it.tiles_n = (2 * q.n + TC_BN - 1) / TC_BN;
     if (q.m == 0 || q.n == 0) it.tiles_m = it.tiles_n = 0;
-    it.tile0 = tiles;
+    it.tile0 = (int)tiles;
     it.pad = 0;
-    tiles += it.tiles_m * it.tiles_n;
+    tiles += (int64_t)it.tiles_m * it.tiles_n;
     sa[i] = {q.A, q.lda, q.m, q.k, (int)arow, (int)eo};
     sb[i] = {q.B, q.ldb, q.n, q.k, (int)brow, (int)(eo + q.m)};
     arow += (q.m + 15) / 16 * 16;
     brow += (2 * (int64_t)q.n + 15) / 16 * 16;
     eo += q.m + q.n;
   }
-  if (ra >= INT32_MAX || rb >= INT32_MAX) return -1;
-  if (tiles == 0) return 0;
-  unsigned char* dtab = (unsigned char*)ws + off_tab;
-  if (cudaMemcpyAsync(dtab, tab.data(), tab.size(), cudaMemcpyHostToDevice, st) != cudaSuccess) return -3;
+  if (tiles >= INT32_MAX) return -1;
+  out->nitems = nitems;
+  out->tiles = (int)tiles;
+  out->kmax = kmax;
+  out->maxm = maxm;
+  out->maxn = maxn;
+  out->ra = ra;
+  out->rb = rb;
+  out->off_exp = off_exp;
+  out->off_tab = off_tab;
+  return 0;
+}
+
+int wsbm_zgemm_tc_run(const TcPlan& pl, const void* dtab_v, double2 alpha, double2 beta, void* ws,
+                      cudaStream_t st, int group) {
+  if (pl.nitems <= 0 || pl.tiles == 0) return 0;
+  if (group < 1 || group > 64) return -1;
+  if (!dtab_v || !ws || ((uintptr_t)ws & 255) != 0) return -1;
+  const int nitems = pl.nitems;
+  const int64_t Ka = tc_ka(pl.kmax), ra = pl.ra, rb = pl.rb;
+  __nv_bfloat16* PA = (__nv_bfloat16*)ws;
+  __nv_bfloat16* PB = PA + (size_t)TC_S * ra * Ka;
+  int* exps = (int*)((char*)ws + pl.off_exp);
+  const unsigned char* dtab = (const unsigned char*)dtab_v;
   const TcItem* ditems = (const TcItem*)dtab;
   const TcSrc* dsa = (const TcSrc*)(dtab + (size_t)nitems * sizeof(TcItem));
   const TcSrc* dsb = dsa + nitems;
   // digit planes (the padding rows between items are never read into a stored output)
-  k_tc_row_exp<<<dim3((maxm + 127) / 128, nitems), 128, 0, st>>>(dsa, exps);
-  k_tc_split_a<<<dim3((maxm + 31) / 32, (unsigned)((Ka / 2 + 31) / 32), nitems), 256, 0, st>>>(
+  k_tc_row_exp<<<dim3((pl.maxm + 127) / 128, nitems), 128, 0, st>>>(dsa, exps);
+  k_tc_split_a<<<dim3((pl.maxm + 31) / 32, (unsigned)((Ka / 2 + 31) / 32), nitems), 256, 0, st>>>(
       dsa, exps, PA, (int64_t)ra * Ka, Ka);
-  k_tc_col_exp<<<dim3((maxn + 7) / 8, nitems), 256, 0, st>>>(dsb, exps);
-  k_tc_split_b<<<dim3(maxn, (unsigned)((Ka / 2 + 255) / 256), nitems), 256, 0, st>>>(
+  k_tc_col_exp<<<dim3((pl.maxn + 7) / 8, nitems), 256, 0, st>>>(dsb, exps);
+  k_tc_split_b<<<dim3(pl.maxn, (unsigned)((Ka / 2 + 255) / 256), nitems), 256, 0, st>>>(
       dsb, exps, PB, (int64_t)rb * Ka, Ka);
   wsbm_count_launches(4);
   CUtensorMap ma, mb;
   if (make_map(&ma, PA, ra, Ka, TC_BM) || make_map(&mb, PB, rb, Ka, TC_BN)) return -3;
   TcArgs a;
   a.nitems = nitems;
-  a.ntiles = tiles;
+  a.ntiles = pl.tiles;
   a.nkb = (int)(Ka / TC_BK);
   a.alpha = alpha;
   a.beta = beta;
   a.sub = alpha.x == -1.0 && alpha.y == 0.0 && beta.x == 1.0 && beta.y == 0.0;
+  a.group = group;
   a.items = ditems;
   a.rexp = exps;
   a.cexp = exps;
   if (wsbm_smem_optin((const void*)k_zgemm_tc, TC_SMEM) != cudaSuccess) return -3;
-  const int grid = tiles < wsbm_sm_count() ? tiles : wsbm_sm_count();
+  const int grid = pl.tiles < wsbm_sm_count() ? pl.tiles : wsbm_sm_count();
   k_zgemm_tc<<<grid, TC_THREADS, TC_SMEM, st>>>(ma, mb, a);
   wsbm_count_launch();
   return cudaGetLastError() == cudaSuccess ? 0 : -3;
+}
+
+int wsbm_zgemm_tc_batched_g(const TcProduct* p, int nitems, double2 alpha, double2 beta, void* ws,
+                            cudaStream_t st, int group) {
+  if (nitems <= 0) return 0;
+  if (group < 1 || group > 64) return -1;
+  if (!p || !ws || ((uintptr_t)ws & 255) != 0) return -1;
+  TcPlan pl;
+  if (int rc = wsbm_zgemm_tc_plan(p, nitems, &pl)) return rc;
+  if (pl.tiles == 0) return 0;
+  // the item tables sit at the end of the work space, copied in stream order before the
+  // launches that read them
+  unsigned char* dtab = (unsigned char*)ws + pl.off_tab;
+  if (cudaMemcpyAsync(dtab, pl.tab.data(), pl.tab.size(), cudaMemcpyHostToDevice, st) != cudaSuccess) return -3;
+  return wsbm_zgemm_tc_run(pl, dtab, alpha, beta, ws, st, group);
+}
+
+int wsbm_zgemm_tc_batched(const TcProduct* p, int nitems, double2 alpha, double2 beta, void* ws, cudaStream_t st) {
+  return wsbm_zgemm_tc_batched_g(p, nitems, alpha, beta, ws, st, wsbm_tune_current().tc_group);
 }
 
 int wsbm_zgemm_tc(int m, int n, int k, double2 alpha, const double2* A, int64_t lda, const double2* B,

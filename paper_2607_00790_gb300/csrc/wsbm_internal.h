@@ -58,20 +58,25 @@ struct ProxyTask {
   int32_t pad;
 };
 
-// Tiles: TILE_F slots along the fast (contiguous-output) dimension x TILE_S along the other.
+// Tiles: TILE_F slots along the fast (contiguous-output) dimension x TILE_S along the other
+// (the default shape; the entry kernels of eq. (weakly_bm) also take TF = 16 or 64 with
+// TS = 128 / TF, the comparison formulations' kernels this shape only).
 #define WSBM_TILE_F 32
 #define WSBM_TILE_S 4
 #define WSBM_PAIR_THREADS 128
+#define WSBM_ENTRY_CTAS 16  // default grid of the persistent entry kernels, CTAs per SM
 
 // entries.cu
 // Launch the entry kernels.  geos / phys: optional device arrays indexed by the tasks' `inst`
-// (batched launches over several curves); when NULL every task uses g / ph.
+// (batched launches over several curves); when NULL every task uses g / ph.  tf: tile width
+// (16, 32 or 64) that the tasks' tile0 and ntiles were counted with (wsbm_pair_tiles /
+// wsbm_proxy_tiles with the same tf); ctas: grid size in CTAs per SM (1..64).
 int wsbm_launch_pairs(const DevGeom& g, const Phys& ph, const PairTask* d_tasks, int ntasks,
                       int64_t ntiles, cudaStream_t st, const DevGeom* geos = nullptr,
-                      const Phys* phys = nullptr);
+                      const Phys* phys = nullptr, int tf = WSBM_TILE_F, int ctas = WSBM_ENTRY_CTAS);
 int wsbm_launch_proxy(const DevGeom& g, const Phys& ph, const ProxyTask* d_tasks, int ntasks,
                       int64_t ntiles, int mixed, cudaStream_t st, const DevGeom* geos = nullptr,
-                      const Phys* phys = nullptr);
+                      const Phys* phys = nullptr, int tf = WSBM_TILE_F, int ctas = WSBM_ENTRY_CTAS);
 // forms.cu: the same tasks for the comparison formulations (form 1: eq. bm, 2: eq. pmchwt);
 // the proxy launch takes row-side tasks only (the column side is formulation independent).
 int wsbm_launch_pairs_form(int form, const DevGeom& g, const Phys& ph, const PairTask* d_tasks,
@@ -80,8 +85,8 @@ int wsbm_launch_pairs_form(int form, const DevGeom& g, const Phys& ph, const Pai
 int wsbm_launch_proxy_rows_form(int form, const DevGeom& g, const Phys& ph, const ProxyTask* d_tasks,
                                 int ntasks, int64_t ntiles, cudaStream_t st,
                                 const DevGeom* geos = nullptr, const Phys* phys = nullptr);
-int64_t wsbm_pair_tiles(int32_t nr, int32_t nc, int32_t fastc);
-int64_t wsbm_proxy_tiles(int32_t nn, int32_t P);
+int64_t wsbm_pair_tiles(int32_t nr, int32_t nc, int32_t fastc, int tf = WSBM_TILE_F);
+int64_t wsbm_proxy_tiles(int32_t nn, int32_t P, int tf = WSBM_TILE_F);
 int wsbm_launch_hankel(const double* z, int64_t n, double* out, int mixed, cudaStream_t st);
 int wsbm_launch_unknowns_to_slots(const int64_t* idx, int64_t n, int64_t N, int32_t* node,
                                   int32_t* pos, cudaStream_t st);
