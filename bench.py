@@ -236,7 +236,7 @@ def run_ours(args, ws, rank, local):
     tuning = None
     if args.set_tuning:
         # fixed shapes (e.g. the choice of an earlier autotuned run, for a profiler capture)
-        binding.wsbm_tuning_set(**{k: int(v) for k, v in (kv.split("=") for kv in args.set_tuning.split(","))})
+        apply_tuning(args.set_tuning)
     elif not args.no_autotune:
         choice, tms = binding.wsbm_autotune(n_box=2 * cfg["leaf"], nbox=cfg["N"] // cfg["leaf"],
                                             nrhs_box=128, n_root=4096, device=dev)
@@ -247,7 +247,7 @@ def run_ours(args, ws, rank, local):
             "cpqr_cb_2_4_8": tms[7:10],
             "k_pairs_tile@ctas_per_sm": dict(zip(cand, bms[0:9])),
             "k_proxy_tile@ctas_per_sm": dict(zip(cand, bms[9:18])),
-            "k_cpqr_threads_128_256": bms[18:20]}}
+            "id_phase_cpqr_threads_128_256": bms[18:20]}}
     for _ in range(args.warmup):
         step(p64)
     torch.cuda.synchronize()
@@ -1066,6 +1066,12 @@ def run_adjoint(dev, N=32768, fd=("a1", "a8", "a16", "b3", "b12", "n"), tol=1e-8
     return out
 
 
+def apply_tuning(spec):
+    """Launch shapes of the current device from "key=value,..." (keys of binding.wsbm_tuning())."""
+    from paper_2607_00790_gb300 import binding
+    binding.wsbm_tuning_set(**{k: int(v) for k, v in (kv.split("=") for kv in spec.split(","))})
+
+
 def profile_case(N=16384):
     import torch
     from paper_2607_00790_gb300 import binding, inputs
@@ -1115,6 +1121,9 @@ def main():
                          "with --mixed-tol)")
     ap.add_argument("--mixed-tol", type=float, default=0.0)
     args = ap.parse_args()
+    if args.set_tuning and (args.profile_case or args.profile_tc or args.full_2p18 or args.adjoint
+                            or args.batched_solve or args.formulations):
+        apply_tuning(args.set_tuning)  # the single-GPU modes below run on device 0
     if args.profile_case:
         profile_case(args.profile_n)
         return

@@ -433,7 +433,7 @@ int wsbm_autotune(int32_t n_box, int32_t nbox, int32_t nrhs_box, int32_t n_root,
                   double* ms, void* stream);
 /* wsbm_autotune_build: leaf-level builds (p->max_levels taken as 1) of the given problem, one
  * per candidate after one warm-up build, timed by the library's per-kernel device times
- * (wsbm_stats_t ms_pairs, ms_proxy, ms_cpqr):
+ * (wsbm_stats_t ms_pairs, ms_proxy, and ms_id for the QR):
  *   out[0], out[1]  tile width (16, 32 or 64 nodes along the contiguous output dimension,
  *           128 / width along the other) and grid (8, 16 or 32 CTAs per SM) of the node-pair
  *           entry kernel of eq. (weakly_bm) (the comparison formulations keep 32 and 16);
@@ -441,7 +441,7 @@ int wsbm_autotune(int32_t n_box, int32_t nbox, int32_t nrhs_box, int32_t n_root,
  *   out[4]  threads per CTA (128 or 256) of the thread-per-column QR of the ID matrices.
  * ms: host, 20 doubles or NULL: pair-kernel times of the 9 (width, grid) pairs in row-major
  * order of {16, 32, 64} x {8, 16, 32}, then the proxy-kernel times in the same order, then the
- * QR times for 128 and 256 threads.  Defaults without a call: 32, 16, 32, 16, 256.
+ * ID-phase times for 128 and 256 QR threads.  Defaults without a call: 32, 16, 32, 16, 256.
  * Synchronous.  Errors: those of wsbm_create / wsbm_factor (the shapes are then unchanged). */
 int wsbm_autotune_build(const wsbm_geom* g, const wsbm_params* p, int32_t* out, double* ms,
                         void* stream);

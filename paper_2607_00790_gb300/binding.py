@@ -345,7 +345,7 @@ def wsbm_autotune_build(geom, params, device=None):
     """Time the entry-kernel tile shapes and grids and the QR block size on leaf-level builds of
     the given problem (see wsbm_autotune_build in the C header).  Returns (choices dict, times
     in ms: 9 pair-kernel and 9 proxy-kernel times over (tile width 16/32/64) x (8/16/32 CTAs
-    per SM), then the QR times for 128 / 256 threads)."""
+    per SM), then the ID-phase times for 128 / 256 QR threads)."""
     out = (ctypes.c_int32 * 5)()
     ms = (ctypes.c_double * 20)()
     _check(lib().wsbm_autotune_build(ctypes.byref(geom), ctypes.byref(params), out, ms, _stream(device)),

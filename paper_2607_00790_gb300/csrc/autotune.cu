@@ -334,7 +334,7 @@ extern "C" int wsbm_autotune(int32_t n_box, int32_t nbox, int32_t nrhs_box, int3
 }
 
 // Leaf-level builds (max_levels = 1) of the caller's problem with each entry-kernel shape and
-// QR block size; the library's per-kernel device times decide.
+// QR block size; the library's per-kernel device times decide (the ID phase's for the QR).
 extern "C" int wsbm_autotune_build(const wsbm_geom* g, const wsbm_params* p, int32_t* out, double* ms,
                                    void* stream) {
   if (!g || !p) return WSBM_ERR_INVALID_ARG;
@@ -383,9 +383,9 @@ extern "C" int wsbm_autotune_build(const wsbm_geom* g, const wsbm_params* p, int
     c.cpqr_threads = thr[a];
     rc = build(c, &so);
     if (rc) break;
-    tm_qr[a] = so.ms_cpqr;
-    if (so.ms_cpqr < bq) {
-      bq = so.ms_cpqr;
+    tm_qr[a] = so.ms_id;  // every QR launch of the level (sketch IDs, redone sides, completion)
+    if (so.ms_id < bq) {
+      bq = so.ms_id;
       t.cpqr_threads = thr[a];
     }
   }
