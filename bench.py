@@ -820,6 +820,37 @@ def run_tc_gemm(dev, m=16384, n=16384, k=128, reps=5):
                          "the digit-split kernels"}
 
 
+def run_tc_sweep(dev):
+    """The tensor-core complex GEMM at the shapes of the root LU's trailing updates, and the
+    LU of dense complex matrices (wsbm_lu_dense) at 16384 and 32768 unknowns (complex LU:
+    16/3 n^3 real flops)."""
+    import torch
+    from paper_2607_00790_gb300 import binding
+    out = {"gemm": [run_tc_gemm(dev, m, n, k) for m, n, k in
+                    ((4096, 4096, 128), (16384, 16384, 128), (16384, 16384, 256), (8192, 8192, 512),
+                     (32768, 32768, 256))]}
+    torch.cuda.empty_cache()
+    lu = []
+    for n in (16384, 32768):
+        g = torch.Generator(device=dev).manual_seed(n)
+        A = torch.randn(n, n, dtype=torch.complex128, device=dev, generator=g)
+        A.diagonal().add_(4.0 * n ** 0.5)
+        binding.wsbm_lu_dense(A.clone())  # warm-up (work space, opt-ins)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        LU, piv = binding.wsbm_lu_dense(A)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        lu.append({"n": n, "ms": ms, "fp64_equivalent_tflops": 16.0 / 3.0 * n ** 3 / (ms * 1e-3) / 1e12})
+        del A, LU, piv
+        torch.cuda.empty_cache()
+    out["lu_dense"] = lu
+    out["tuning"] = binding.wsbm_tuning()
+    return out
+
+
 def run_formulations(dev, N=262144, tol=1e-8):
     """Leaf-level build (entries, IDs, leaf factors) of the star at N for the three
     formulations of Sec. II: eq. (weakly_bm), eq. (bm) and eq. (pmchwt).  The paper reports the
@@ -908,8 +939,11 @@ def run_batched_solve(dev, count=16, nmax=16384, nrhs=256, tol=1e-8):
             binding.trim_memory()
     out["rhs_per_plan"] = chunk
     # per-curve solves, one curve at a time (each handle caches its own plan: after timing it is
-    # replaced by a one-column plan so that only one large plan exists at a time)
+    # replaced by a one-column plan so that only one large plan exists at a time; the batch's
+    # own plan likewise first)
     one = [torch.zeros((r.shape[0], 1), dtype=r.dtype, device=dev) for r in rhs]
+    bt.solve(one)
+    binding.trim_memory()
     tot = 0.0
     for i in range(len(man)):
         sv = bt.solver(i)
@@ -1094,6 +1128,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--no-extras", action="store_true")
+    ap.add_argument("--tc-sweep", action="store_true",
+                    help="tensor-core GEMM at several shapes and the dense LU at 16384 / 32768 unknowns")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the default launch shapes instead of timing the candidates")
     ap.add_argument("--set-tuning", default="",
@@ -1122,10 +1158,13 @@ def main():
     ap.add_argument("--mixed-tol", type=float, default=0.0)
     args = ap.parse_args()
     if args.set_tuning and (args.profile_case or args.profile_tc or args.full_2p18 or args.adjoint
-                            or args.batched_solve or args.formulations):
+                            or args.batched_solve or args.formulations or args.tc_sweep):
         apply_tuning(args.set_tuning)  # the single-GPU modes below run on device 0
     if args.profile_case:
         profile_case(args.profile_n)
+        return
+    if args.tc_sweep:
+        print(json.dumps({"tc_sweep": run_tc_sweep("cuda")}), flush=True)
         return
     if args.profile_tc:
         print(json.dumps(run_tc_gemm("cuda", 4096, 4096, 128, reps=1)), flush=True)

@@ -134,16 +134,37 @@ __device__ __forceinline__ uint64_t sdesc_sw64(uint32_t addr) {
   d |= (uint64_t)4 << 61;                     // layout: 64-byte swizzle
   return d;
 }
-// Instruction descriptor: BF16 x BF16 -> FP32, both operands K-major, M = 128, N = TC_BN.
-__host__ __device__ constexpr uint32_t tc_idesc() {
-  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TC_BN >> 3) << 17) | ((uint32_t)(TC_BM >> 4) << 24);
+// Instruction descriptor: BF16 x BF16 -> FP32, both operands K-major, M = 128, N = n (a
+// multiple of 16, at most 256).
+__host__ __device__ constexpr uint32_t tc_idesc(int n) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(TC_BM >> 4) << 24);
 }
-__device__ __forceinline__ void tc_mma(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t accum) {
+__device__ __forceinline__ void tc_mma(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t accum) {
   asm volatile(
       "{\n\t.reg .pred p;\n\t"
       "setp.ne.b32 p, %4, 0;\n\t"
       "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
-      "l"(a), "l"(b), "r"(tc_idesc()), "r"(accum));
+      "l"(a), "l"(b), "r"(idesc), "r"(accum));
+}
+
+// The 34 digit pairs (t, u), t + u <= 7, as 11 MMAs: A digit t against the B digits u0 ..
+// u0 + cnt - 1, which sit one after another in shared memory (one tile of 64 * cnt rows) and
+// whose diagonals t + u0 .. t + u0 + cnt - 1 are adjacent accumulators in TMEM (N = 64 cnt).
+// The first two MMAs of a chunk start diagonals 4..7 and 0..3 from zero; every later one adds.
+__device__ __forceinline__ void tc_sched(int e, int& t, int& u0, int& cnt) {
+  switch (e) {
+    case 0: t = 1, u0 = 3, cnt = 4; break;
+    case 1: t = 0, u0 = 0, cnt = 4; break;
+    case 2: t = 0, u0 = 4, cnt = 3; break;
+    case 3: t = 1, u0 = 0, cnt = 3; break;
+    case 4: t = 2, u0 = 0, cnt = 4; break;
+    case 5: t = 2, u0 = 4, cnt = 2; break;
+    case 6: t = 3, u0 = 0, cnt = 4; break;
+    case 7: t = 3, u0 = 4, cnt = 1; break;
+    case 8: t = 4, u0 = 0, cnt = 4; break;
+    case 9: t = 5, u0 = 0, cnt = 3; break;
+    default: t = 6, u0 = 0, cnt = 2; break;
+  }
 }
 __device__ __forceinline__ void tc_commit(uint32_t bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
@@ -444,18 +465,16 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             tc_fence_after();
             const uint32_t sa = base + s * TC_STAGE_BYTES, sb = sa + TC_S * TC_A_TILE;
 #pragma unroll
-            for (int d = 0; d < TC_ND; ++d) {
-              const int t0 = d > TC_S - 1 ? d - (TC_S - 1) : 0;
+            for (int kk = 0; kk < TC_BK / 16; ++kk) {
 #pragma unroll
-              for (int tt = t0; tt <= d && tt < TC_S; ++tt) {
+              for (int e = 0; e < 11; ++e) {
+                int tt, u0, cnt;
+                tc_sched(e, tt, u0, cnt);
                 const uint64_t da = sdesc_sw64(sa + tt * TC_A_TILE);
-                const uint64_t db = sdesc_sw64(sb + (d - tt) * TC_B_TILE);
-#pragma unroll
-                for (int kk = 0; kk < TC_BK / 16; ++kk) {
-                  const uint32_t acc = (kb > kb0 || tt > t0 || kk > 0) ? 1u : 0u;
-                  // K step of 16 BF16 values = 32 bytes = 2 units of the start address
-                  tc_mma(tmem + d * TC_BN, da + 2 * kk, db + 2 * kk, acc);
-                }
+                const uint64_t db = sdesc_sw64(sb + u0 * TC_B_TILE);
+                const uint32_t acc = (kb > kb0 || kk > 0 || e >= 2) ? 1u : 0u;
+                // K step of 16 BF16 values = 32 bytes = 2 units of the start address
+                tc_mma(tmem + (tt + u0) * TC_BN, da + 2 * kk, db + 2 * kk, tc_idesc(cnt * TC_BN), acc);
               }
             }
             tc_commit(empty0 + 8 * s);  // the stage is free once these MMAs have read it
