@@ -356,8 +356,8 @@ int wsbm_field(const wsbm_geom* g, const wsbm_params* p, const void* u, const vo
 /* Randomized row sketch Y = Omega A on the tensor cores: A device complex128 m x n (column-
  * major, lda >= m), Omega the l x m Rademacher matrix with entries +-1 (bit 0 of a counter-based
  * hash of (row, column, seed)), Y device complex128 l x n (ldy >= l).  Products are formed
- * exactly from 8-bit slices of the power-of-two scaled columns of A (BF16 mma with FP32
- * accumulation), so Y carries a relative error of about 2^-41 of its column scale.  The HSS
+ * exactly from seven 8-bit digits of the power-of-two scaled columns of A (tcgen05 BF16 MMAs
+ * with exact FP32 sums), so Y carries a relative error of about 2^-56 of its column scale.  The HSS
  * build uses it for the interpolative decompositions of the leaf level (no counterpart in the
  * paper, which does not say how its IDs are computed).  l: multiple of 16 in [16, 192];
  * m <= 65536.  Synchronous.  Errors: INVALID_ARG, OOM, CUDA. */

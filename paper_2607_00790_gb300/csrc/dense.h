@@ -70,6 +70,12 @@ struct TcPlan {
 int wsbm_zgemm_tc_plan(const TcProduct* p, int nitems, TcPlan* out);
 int wsbm_zgemm_tc_run(const TcPlan& pl, const void* dtab, double2 alpha, double2 beta, void* ws,
                       cudaStream_t st, int group);
+// Randomized row sketches Y_i = Omega[:m_i, :k_i] B_i on the tensor cores (Omega: +-1 from the
+// sketch hash of (row, column, seed), shared by all items; B_i: k_i x n_i complex, C_i = Y_i:
+// m_i x n_i, A ignored).  ws: 256-byte aligned, wsbm_sketch_tc_ws_bytes(p, n) bytes.  At most
+// 65535 items, k_i <= 65536.  Returns 0, -1 or -3; enqueues only.
+size_t wsbm_sketch_tc_ws_bytes(const TcProduct* p, int nitems);
+int wsbm_sketch_tc(const TcProduct* p, int nitems, uint32_t seed, void* ws, cudaStream_t st);
 // Synchronizes the stream and returns -5 (and clears the flag) if a bounded wait of the GEMM
 // kernel ran out since the last call, else 0 (-3 on a CUDA error).
 int wsbm_zgemm_tc_status(cudaStream_t st);

@@ -57,6 +57,9 @@
 #ifndef WSBM_TCSOLVE_NB
 #define WSBM_TCSOLVE_NB 256
 #endif
+#ifndef WSBM_TCSOLVE_WS
+#define WSBM_TCSOLVE_WS ((size_t)4 << 30)  // digit-plane work space of one solve product launch
+#endif
 #ifndef WSBM_BIGLU_MIN
 #define WSBM_BIGLU_MIN 2048
 #endif
@@ -1052,7 +1055,6 @@ static int factor_levels(const std::vector<wsbm_hss*>& hs, const std::vector<int
   bool sketched = false;
   {
     size_t Ytot = 0;
-    int maxl = 0, maxnn = 0;
     for (int r = 0; r < NB; ++r) {
       wsbm_hss* h = R[r].h;
       Box& B = R[r].box();
@@ -1063,8 +1065,6 @@ static int factor_levels(const std::vector<wsbm_hss*>& hs, const std::vector<int
         if (l > 192 || m < (3 * (int64_t)l) / 2 || m > 65536) continue;
         lsk[2 * r + s2] = l;
         Ytot += (size_t)l * B.n;
-        maxl = std::max(maxl, l);
-        maxnn = std::max(maxnn, B.n);
       }
     }
     if (Ytot) {
@@ -1087,10 +1087,12 @@ static int factor_levels(const std::vector<wsbm_hss*>& hs, const std::vector<int
                                 Ysk[2 * r + s2], l, (int32_t)m, B.n, l);
           ++nsk;
         }
-      unsigned char* dsd = nullptr;
-      HK(upload(h0, sd, &dsd, tmp));
+      // digit-plane work space of the tensor-core sketches: at most 4 GiB per launch
+      const size_t cap = (size_t)4 << 30;
+      void* skws = nullptr;
+      HK(dalloc(h0, wsbm_sketch_ws_bytes(sd.data(), nsk, cap), &skws, tmp));
       HC(cudaEventRecord(h0->ev[12], st));
-      HK(wsbm_sketch_batched(dsd, nsk, maxnn, maxl, 0x5eed1234u, st));
+      HK(wsbm_sketch_batched(sd.data(), nsk, 0x5eed1234u, skws, cap, st));
       HC(cudaEventRecord(h0->ev[13], st));
       sketch_out[0] += nsk;
       sketched = true;  // timed after the next synchronization
@@ -2045,10 +2047,15 @@ static int plan_gathers(SolvePlan& P, const std::vector<GatherDesc>& g) {
 // and uploaded now; the work space is shared by every such operation of the plan and allocated
 // once all are known (plan_tc_finish).
 static int plan_tc(SolvePlan& P, const std::vector<TcProduct>& items, double2 alpha, double2 beta) {
-  for (size_t c0 = 0; c0 < items.size(); c0 += 65535) {
-    const int n = (int)std::min<size_t>(65535, items.size() - c0);
+  // launches of at most 65535 items whose digit planes take at most WSBM_TCSOLVE_WS bytes (one
+  // item always forms a launch): the shared work space stays small next to the factors
+  for (size_t c0 = 0; c0 < items.size();) {
+    int n = (int)std::min<size_t>(65535, items.size() - c0);
+    while (n > 1 && wsbm_zgemm_tc_batched_ws_bytes(items.data() + c0, n) > WSBM_TCSOLVE_WS) n = (n + 1) / 2;
     auto pl = std::make_shared<TcPlan>();
-    if (wsbm_zgemm_tc_plan(items.data() + c0, n, pl.get())) return WSBM_ERR_INVALID_ARG;
+    const size_t i0 = c0;
+    c0 += n;
+    if (wsbm_zgemm_tc_plan(items.data() + i0, n, pl.get())) return WSBM_ERR_INVALID_ARG;
     if (pl->tiles == 0) continue;
     unsigned char* dtab = nullptr;
     HK(plan_upload(P, pl->tab, &dtab));

@@ -359,6 +359,7 @@ struct TcArgs {
   double2 alpha, beta;
   int sub;              // alpha = -1, beta = 1 (C -= A B): two FP64 additions per entry
   int group;            // row tiles per raster group of the tile order
+  int a1;               // A is one digit plane of a real matrix (sketches: Omega = +-1)
   const TcItem* items;
   const int* rexp;
   const int* cexp;
@@ -432,11 +433,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           const uint32_t s = it % TC_STAGES, ph = (it / TC_STAGES) & 1;
           if (!(ok = mbar_wait(empty0 + 8 * s, ph ^ 1))) break;
           const uint32_t full = full0 + 8 * s;
-          mbar_expect_tx(full, TC_STAGE_BYTES);
+          mbar_expect_tx(full, a.a1 ? TC_A_TILE + TC_S * TC_B_TILE : TC_STAGE_BYTES);
           const uint32_t sa = base + s * TC_STAGE_BYTES, sb = sa + TC_S * TC_A_TILE;
 #pragma unroll
           for (int p = 0; p < TC_S; ++p) {
-            tma_load_3d(sa + p * TC_A_TILE, &mapA, full, kb * TC_BK, item.arow + tm * TC_BM, p);
+            if (p == 0 || !a.a1) tma_load_3d(sa + p * TC_A_TILE, &mapA, full, kb * TC_BK, item.arow + tm * TC_BM, p);
             tma_load_3d(sb + p * TC_B_TILE, &mapB, full, kb * TC_BK, item.brow + tn * TC_BN, p);
           }
         }
@@ -468,11 +469,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             for (int kk = 0; kk < TC_BK / 16; ++kk) {
 #pragma unroll
               for (int e = 0; e < 11; ++e) {
+                // one-digit A: only A digit 0 (entries 1 and 2: diagonals 0..3 and 4..6, both
+                // started from zero; diagonal 7 stays unused)
+                if (a.a1 && e != 1 && e != 2) continue;
                 int tt, u0, cnt;
                 tc_sched(e, tt, u0, cnt);
                 const uint64_t da = sdesc_sw64(sa + tt * TC_A_TILE);
                 const uint64_t db = sdesc_sw64(sb + u0 * TC_B_TILE);
-                const uint32_t acc = (kb > kb0 || kk > 0 || e >= 2) ? 1u : 0u;
+                const uint32_t acc = (kb > kb0 || kk > 0 || (e >= 2 && !a.a1)) ? 1u : 0u;
                 // K step of 16 BF16 values = 32 bytes = 2 units of the start address
                 tc_mma(tmem + (tt + u0) * TC_BN, da + 2 * kk, db + 2 * kk, tc_idesc(cnt * TC_BN), acc);
               }
@@ -534,6 +538,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           tmem_ld8(tq + 6 * TC_BN + g * 8, v0);
           tmem_ld8(tq + 7 * TC_BN + g * 8, v1);
           tmem_ld_wait();
+          if (a.a1) {
+#pragma unroll
+            for (int c = 0; c < 8; ++c) v1[c] = 0.0f;
+          }
 #pragma unroll
           for (int c = 0; c < 8; ++c) {
             const int col = half * (TC_BN / 2) + g * 8 + c;
@@ -647,10 +655,10 @@ size_t wsbm_zgemm_tc_ws_bytes(int m, int n, int k) {
 }
 
 // 3-D map over the digit planes [TC_S][rows][Ka] with boxes of TC_BK x box_rows x 1.
-static int make_map(CUtensorMap* map, void* planes, int64_t rows, int64_t Ka, int box_rows) {
+static int make_map(CUtensorMap* map, void* planes, int64_t rows, int64_t Ka, int box_rows, int nplanes = TC_S) {
   EncodeTiledFn enc = encode_fn();
   if (!enc) return -3;
-  cuuint64_t dims[3] = {(cuuint64_t)Ka, (cuuint64_t)rows, (cuuint64_t)TC_S};
+  cuuint64_t dims[3] = {(cuuint64_t)Ka, (cuuint64_t)rows, (cuuint64_t)nplanes};
   cuuint64_t strides[2] = {(cuuint64_t)Ka * 2, (cuuint64_t)rows * Ka * 2};
   cuuint32_t box[3] = {TC_BK, (cuuint32_t)box_rows, 1};
   cuuint32_t es[3] = {1, 1, 1};
@@ -755,6 +763,7 @@ int wsbm_zgemm_tc_run(const TcPlan& pl, const void* dtab_v, double2 alpha, doubl
   a.beta = beta;
   a.sub = alpha.x == -1.0 && alpha.y == 0.0 && beta.x == 1.0 && beta.y == 0.0;
   a.group = group;
+  a.a1 = 0;
   a.items = ditems;
   a.rexp = exps;
   a.cexp = exps;
@@ -814,4 +823,172 @@ int wsbm_zgemm_tc_status(cudaStream_t st) {
     return -5;
   }
   return 0;
+}
+
+// ------------------------------------------------ sketches Y = Omega M (Omega = +-1) ----
+// Y_i (l_i x n_i) = Omega[:l_i, :m_i] M_i (m_i x n_i complex) with Omega_rc = -1 when bit 0 of
+// the sketch hash of (r, c, seed) is set, else +1, shared by every item.  Omega is exact in BF16
+// (one digit plane, row scale 2^8: the value +-1 is the digit +-1 of weight 2^-8), so each
+// real-form column of M (Re and Im separately: Omega is real) meets one A digit: 7 digit pairs
+// per product, every FP32 sum exact (|sum| <= 256 * 128 per chunk), and Y carries only the
+// 56-bit rounding of M relative to its column maximum.
+__device__ __forceinline__ uint32_t tc_sk_hash(uint32_t r, uint32_t c, uint32_t seed) {
+  uint32_t h = r * 0x9E3779B1u ^ (c * 0x85EBCA77u + seed);
+  h ^= h >> 16;
+  h *= 0x7FEB352Du;
+  h ^= h >> 15;
+  h *= 0x846CA68Bu;
+  h ^= h >> 16;
+  return h;
+}
+
+// Omega into the A plane (rows x Ka BF16) and the row exponents (8) of its rows.
+__global__ void k_tc_omega(__nv_bfloat16* __restrict__ PA, int rows, int64_t Ka, uint32_t seed,
+                           int* __restrict__ rexp) {
+  const int64_t tot = (int64_t)rows * Ka;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
+    const int r = (int)(e / Ka), c = (int)(e % Ka);
+    PA[e] = __float2bfloat16_rn((tc_sk_hash((uint32_t)r, (uint32_t)c, seed) & 1u) ? -1.0f : 1.0f);
+    if (c == 0) rexp[r] = 8;
+  }
+}
+
+// Digit planes of the real-form columns of M for a real A: PB[u][2j][l] = digit u of Re M_lj,
+// PB[u][2j+1][l] = digit u of Im M_lj (zero beyond k).  Column blockIdx.x of item blockIdx.z.
+__global__ void __launch_bounds__(256) k_tc_split_b_real(const TcSrc* __restrict__ src, const int* __restrict__ cexp,
+                                                         __nv_bfloat16* __restrict__ PB, int64_t plane, int64_t Ka) {
+  const TcSrc q = src[blockIdx.z];
+  const int j = blockIdx.x;
+  if (j >= q.rows) return;
+  const int e = cexp[q.eoff + j];
+  for (int l = blockIdx.y * blockDim.x + threadIdx.x; l < Ka; l += gridDim.y * blockDim.x) {
+    int dr[TC_S], di[TC_S];
+    if (l < q.k) {
+      const double2 v = q.M[l + (int64_t)j * q.ld];
+      digits7(v.x, e, dr);
+      digits7(v.y, e, di);
+    } else {
+#pragma unroll
+      for (int t = 0; t < TC_S; ++t) dr[t] = di[t] = 0;
+    }
+#pragma unroll
+    for (int u = 0; u < TC_S; ++u) {
+      __nv_bfloat16* row = PB + u * plane + (int64_t)(q.prow + 2 * j) * Ka + l;
+      row[0] = __float2bfloat16_rn((float)dr[u]);
+      row[Ka] = __float2bfloat16_rn((float)di[u]);
+    }
+  }
+}
+
+static int64_t tc_ka_real(int k) { return ((int64_t)k + TC_BK - 1) / TC_BK * TC_BK; }
+
+// Work space of one sketch launch over items p[0..n) (p[i].m = l_i rows of Y, k = m_i rows of
+// M, n = n_i columns): Omega plane, B digit planes, exponents, item tables.
+static size_t sk_layout(const TcProduct* p, int n, int64_t* la, int64_t* rb, int64_t* Ka, size_t* off_b,
+                        size_t* off_exp, size_t* off_tab) {
+  int lmax = 0, kmax = 1;
+  int64_t r = 0, ne = 0;
+  for (int i = 0; i < n; ++i) {
+    lmax = std::max(lmax, p[i].m);
+    kmax = std::max(kmax, p[i].k);
+    r += (2 * (int64_t)p[i].n + 15) / 16 * 16;
+    ne += p[i].n;
+  }
+  *la = ((int64_t)lmax + 15) / 16 * 16;
+  *Ka = tc_ka_real(kmax);
+  *rb = r;
+  size_t b = (size_t)(*la) * (*Ka) * 2;
+  b = (b + 255) & ~(size_t)255;
+  *off_b = b;
+  b += (size_t)TC_S * r * (*Ka) * 2;
+  b = (b + 255) & ~(size_t)255;
+  *off_exp = b;
+  b += ((size_t)(*la) + ne) * sizeof(int);
+  b = (b + 255) & ~(size_t)255;
+  *off_tab = b;
+  b += (size_t)n * (sizeof(TcItem) + sizeof(TcSrc)) + 256;
+  return b;
+}
+
+size_t wsbm_sketch_tc_ws_bytes(const TcProduct* p, int nitems) {
+  int64_t la, rb, Ka;
+  size_t ob, oe, ot;
+  return sk_layout(p, nitems, &la, &rb, &Ka, &ob, &oe, &ot);
+}
+
+int wsbm_sketch_tc(const TcProduct* p, int nitems, uint32_t seed, void* ws, cudaStream_t st) {
+  if (nitems <= 0) return 0;
+  if (!p || !ws || ((uintptr_t)ws & 255) != 0 || nitems > 65535) return -1;
+  for (int i = 0; i < nitems; ++i) {
+    const TcProduct& q = p[i];
+    if (q.m < 1 || q.n < 0 || q.k < 1 || q.k > 65536 || !q.B || !q.C || q.ldb < q.k || q.ldc < q.m) return -1;
+  }
+  int64_t la, rb, Ka;
+  size_t off_b, off_exp, off_tab;
+  sk_layout(p, nitems, &la, &rb, &Ka, &off_b, &off_exp, &off_tab);
+  if (rb >= INT32_MAX || la > 65536) return -1;
+  __nv_bfloat16* PA = (__nv_bfloat16*)ws;
+  __nv_bfloat16* PB = (__nv_bfloat16*)((char*)ws + off_b);
+  int* exps = (int*)((char*)ws + off_exp);
+  std::vector<unsigned char> tab((size_t)nitems * (sizeof(TcItem) + sizeof(TcSrc)));
+  TcItem* items = (TcItem*)tab.data();
+  TcSrc* sb = (TcSrc*)(tab.data() + (size_t)nitems * sizeof(TcItem));
+  int64_t brow = 0, eo = la, tiles = 0;
+  int maxn = 0;
+  for (int i = 0; i < nitems; ++i) {
+    const TcProduct& q = p[i];
+    TcItem& it = items[i];
+    it.C = q.C;
+    it.ldc = q.ldc;
+    it.m = q.m;
+    it.n = q.n;
+    it.arow = 0;  // Omega is shared
+    it.brow = (int)brow;
+    it.eoff_r = 0;
+    it.eoff_c = (int)eo;
+    it.tiles_m = (q.m + TC_BM - 1) / TC_BM;
+    it.tiles_n = (2 * q.n + TC_BN - 1) / TC_BN;
+    if (q.n == 0) it.tiles_m = it.tiles_n = 0;
+    it.tile0 = (int)tiles;
+    it.pad = 0;
+    tiles += (int64_t)it.tiles_m * it.tiles_n;
+    sb[i] = {q.B, q.ldb, q.n, q.k, (int)brow, (int)eo};
+    brow += (2 * (int64_t)q.n + 15) / 16 * 16;
+    eo += q.n;
+    maxn = std::max(maxn, q.n);
+  }
+  if (tiles == 0) return 0;
+  if (tiles >= INT32_MAX) return -1;
+  unsigned char* dtab = (unsigned char*)ws + off_tab;
+  if (cudaMemcpyAsync(dtab, tab.data(), tab.size(), cudaMemcpyHostToDevice, st) != cudaSuccess) return -3;
+  const TcItem* ditems = (const TcItem*)dtab;
+  const TcSrc* dsb = (const TcSrc*)(dtab + (size_t)nitems * sizeof(TcItem));
+  {
+    const int64_t tot = la * Ka;
+    const int g = (int)std::min<int64_t>((tot + 255) / 256, (int64_t)wsbm_sm_count() * 8);
+    k_tc_omega<<<g, 256, 0, st>>>(PA, (int)la, Ka, seed, exps);
+  }
+  k_tc_col_exp<<<dim3((maxn + 7) / 8, nitems), 256, 0, st>>>(dsb, exps);
+  k_tc_split_b_real<<<dim3(std::max(maxn, 1), (unsigned)((Ka + 255) / 256), nitems), 256, 0, st>>>(
+      dsb, exps, PB, (int64_t)rb * Ka, Ka);
+  wsbm_count_launches(3);
+  CUtensorMap ma, mb;
+  if (make_map(&ma, PA, la, Ka, TC_BM, 1) || make_map(&mb, PB, rb, Ka, TC_BN)) return -3;
+  TcArgs a;
+  a.nitems = nitems;
+  a.ntiles = (int)tiles;
+  a.nkb = (int)(Ka / TC_BK);
+  a.alpha = make_double2(1.0, 0.0);
+  a.beta = make_double2(0.0, 0.0);
+  a.sub = 0;
+  a.group = wsbm_tune_current().tc_group;
+  a.a1 = 1;
+  a.items = ditems;
+  a.rexp = exps;
+  a.cexp = exps;
+  if (wsbm_smem_optin((const void*)k_zgemm_tc, TC_SMEM) != cudaSuccess) return -3;
+  const int grid = a.ntiles < wsbm_sm_count() ? a.ntiles : wsbm_sm_count();
+  k_zgemm_tc<<<grid, TC_THREADS, TC_SMEM, st>>>(ma, mb, a);
+  wsbm_count_launch();
+  return cudaGetLastError() == cudaSuccess ? 0 : -3;
 }

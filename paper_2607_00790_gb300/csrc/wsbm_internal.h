@@ -91,9 +91,12 @@ int wsbm_launch_hankel(const double* z, int64_t n, double* out, int mixed, cudaS
 int wsbm_launch_unknowns_to_slots(const int64_t* idx, int64_t n, int64_t N, int32_t* node,
                                   int32_t* pos, cudaStream_t st);
 
-// sketch.cu: randomized row sketches Y = Omega M of ID matrices on the tensor cores.
-int wsbm_sketch_batched(const void* d_desc, int ndesc, int max_n, int max_l, uint32_t seed,
-                        cudaStream_t st);
+// sketch.cu: randomized row sketches Y = Omega M of ID matrices on the tensor cores.  h_desc:
+// host array of ndesc descriptors (wsbm_sketch_desc_fill); the matrices go through in launches
+// whose work space stays within `cap` bytes (one matrix always fits: wsbm_sketch_ws_bytes gives
+// the work space the same split needs).  Enqueues only.
+size_t wsbm_sketch_ws_bytes(const void* h_desc, int ndesc, size_t cap);
+int wsbm_sketch_batched(const void* h_desc, int ndesc, uint32_t seed, void* ws, size_t cap, cudaStream_t st);
 size_t wsbm_sketch_desc_size();
 void wsbm_sketch_desc_fill(void* slot, const void* A, int64_t lda, void* Y, int64_t ldy, int32_t m,
                            int32_t n, int32_t l);
