@@ -25,7 +25,8 @@
 //     diagonals 0..4 and the high part of 5) and a 16-bit fraction F of unit 2^-64 (the rest of
 //     5, diagonal 6, and diagonal 7 rounded), whose carries move into T after every chunk
 //     (integer and FP32 pipes only).  At the end of the K loop,
-//     C_ij = beta C_ij + alpha (T + F 2^-16) 2^(e_i + f_j - 48).
+//     C_ij = beta C_ij + alpha (T + F 2^-16) 2^(e_i + f_j - 48),
+//     with (T + F 2^-16) 2^(e_i + f_j - 48) rounded once to a double by integer operations.
 //
 // Error: the rounding of X to 56 bits (relative to the row or column maximum) and the pairs
 // left out keep each entry of A B within about 2^-53 * 2k * max|A_i.| * max|B_.j| of the exact
@@ -186,6 +187,51 @@ __device__ __forceinline__ double scale2(double x, int ex) {
   const int e = (int)((b >> 52) & 0x7FF);
   if (e > 0 && e + ex >= 1 && e + ex <= 2046) return __longlong_as_double(b + ((long long)ex << 52));
   return ldexp(x, ex);
+}
+
+// (T + F 2^-16) 2^ex (F in [0, 2^16)) as the correctly rounded double (to nearest, ties to
+// even), formed with integer operations only: the 80-bit fixed-point value T 2^16 + F is
+// normalized by a leading-zero count, rounded to 53 bits and given its exponent field, so the
+// FP64 pipe (2 operations per clock per SM on this GPU) does not convert the accumulated sums.
+// Returns false (and leaves x) when the result would leave the normal range.
+__device__ __forceinline__ bool fixed_to_double(long long T, int F, int ex, double& x) {
+  uint64_t lo = ((uint64_t)T << 16) | (uint64_t)(uint32_t)F;
+  uint64_t hi = (uint64_t)(T >> 48);  // sign extension of T's top 16 bits
+  const bool neg = T < 0;
+  if (neg) {  // magnitude of the 128-bit two's-complement value
+    lo = ~lo + 1;
+    hi = ~hi + (lo == 0 ? 1 : 0);
+  }
+  if ((hi | lo) == 0) {
+    x = 0.0;
+    return true;
+  }
+  int p;          // bit index of the leading one
+  uint64_t m;     // the 64 bits from the leading one down, left aligned
+  uint64_t below; // the bits below those 64 (nonzero: part of the sticky bit)
+  if (hi) {
+    const int z = __clzll((long long)hi);
+    p = 127 - z;
+    m = z ? (hi << z) | (lo >> (64 - z)) : hi;
+    below = z ? (lo << z) : lo;
+  } else {
+    const int z = __clzll((long long)lo);
+    p = 63 - z;
+    m = lo << z;
+    below = 0;
+  }
+  uint64_t mant = m >> 11;  // 53 significant bits
+  if (((m >> 10) & 1) && ((m & 0x3FF) | below | (mant & 1))) {
+    ++mant;
+    if (mant >> 53) {
+      mant >>= 1;
+      ++p;
+    }
+  }
+  const int E = p - 16 + ex + 1023;
+  if (E <= 0 || E >= 2047) return false;
+  x = __longlong_as_double((long long)(((uint64_t)neg << 63) | ((uint64_t)E << 52) | (mant & 0xFFFFFFFFFFFFFull)));
+  return true;
 }
 
 // --------------------------------------------------------------- digit planes ----
@@ -359,6 +405,7 @@ struct TcArgs {
   double2 alpha, beta;
   int sub;              // alpha = -1, beta = 1 (C -= A B): two FP64 additions per entry
   int group;            // row tiles per raster group of the tile order
+  int assign;           // alpha = 1, beta = 0 (C = A B): no FP64 arithmetic per entry
   int a1;               // A is one digit plane of a real matrix (sketches: Omega = +-1)
   const TcItem* items;
   const int* rexp;
@@ -566,12 +613,17 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           if (j >= item.n) continue;
           const int ex = ei + a.cexp[item.eoff_c + j] - 48;
           const int* fp = frac + (half * (TC_BN / 2) + 2 * c) * TC_BM + row;
-          const double xr = scale2(fma((double)fp[0], 1.0 / 65536.0, (double)T[2 * c]), ex);
-          const double xi = scale2(fma((double)fp[TC_BM], 1.0 / 65536.0, (double)T[2 * c + 1]), ex);
+          double xr, xi;
+          if (!fixed_to_double(T[2 * c], fp[0], ex, xr))
+            xr = scale2(fma((double)fp[0], 1.0 / 65536.0, (double)T[2 * c]), ex);
+          if (!fixed_to_double(T[2 * c + 1], fp[TC_BM], ex, xi))
+            xi = scale2(fma((double)fp[TC_BM], 1.0 / 65536.0, (double)T[2 * c + 1]), ex);
           double2* p = item.C + i + (int64_t)j * item.ldc;
           if (a.sub) {
             const double2 o = *p;
             *p = make_double2(o.x - xr, o.y - xi);
+          } else if (a.assign) {
+            *p = make_double2(xr, xi);
           } else {
             double2 r = make_double2(a.alpha.x * xr - a.alpha.y * xi, a.alpha.x * xi + a.alpha.y * xr);
             if (a.beta.x != 0.0 || a.beta.y != 0.0) {
@@ -762,6 +814,7 @@ int wsbm_zgemm_tc_run(const TcPlan& pl, const void* dtab_v, double2 alpha, doubl
   a.alpha = alpha;
   a.beta = beta;
   a.sub = alpha.x == -1.0 && alpha.y == 0.0 && beta.x == 1.0 && beta.y == 0.0;
+  a.assign = alpha.x == 1.0 && alpha.y == 0.0 && beta.x == 0.0 && beta.y == 0.0;
   a.group = group;
   a.a1 = 0;
   a.items = ditems;
@@ -981,6 +1034,7 @@ int wsbm_sketch_tc(const TcProduct* p, int nitems, uint32_t seed, void* ws, cuda
   a.alpha = make_double2(1.0, 0.0);
   a.beta = make_double2(0.0, 0.0);
   a.sub = 0;
+  a.assign = 1;
   a.group = wsbm_tune_current().tc_group;
   a.a1 = 1;
   a.items = ditems;
