@@ -34,13 +34,16 @@ UNIT = "entries/s"
 # for the kernel sources with the recorded hash; when the sources change the traffic figure is
 # withheld until re-measured.
 KERNEL_COUNTS = {
-    "src_sha": "33370da20d0ae571",
-    # 16384-node star, leaf level (bench.py --profile-case): 4.16 M / 4.24 M pairs
-    "k_proxy": {"fp64_flops_per_pair": 251.6, "dram_bytes_per_pair": 50.2},
-    "k_pairs": {"fp64_flops_per_pair": 323.9, "dram_bytes_per_pair": 50.6},
+    "src_sha": "39971b7a6cb47b86",
+    # 16384-node star, leaf level (bench.py --profile-case), tiles of 16 x 8 node pairs (the
+    # autotuned shape; the proxy kernel's per-pair count includes its proxy-point set-up, which
+    # depends on the tile width): 4.16 M / 4.24 M pairs
+    "k_proxy": {"tf": 16, "fp64_flops_per_pair": 244.5, "dram_bytes_per_pair": 50.1},
+    "k_pairs": {"tf": 16, "fp64_flops_per_pair": 323.9, "dram_bytes_per_pair": 50.8},
     # DRAM traffic of the column-pivoted QR per ID matrix of this workload, keyed by the hash of
-    # its dense.cu section and the matrix rows it was measured on
-    "k_cpqr": {"src_sha": "845cb05fd193638d", "rows": 128, "dram_bytes_per_matrix": 6.27e7},
+    # its dense.cu section and the matrix rows it was measured on (1024 sketches of 128 rows,
+    # 65536-node star)
+    "k_cpqr": {"src_sha": "efa00c1011a862ff", "rows": 128, "dram_bytes_per_matrix": 6.30e7},
     # DRAM traffic of the two fused LU + solve launches of a leaf level (box LU with D^-1 L of
     # 256 unknowns, and Dhat), per factored matrix: 25.71 GB over the 1024 matrices of the
     # 512 leaf boxes of the same star at N = 65536 (boxes of the same size and ranks)
@@ -321,7 +324,8 @@ def run_ours(args, ws, rank, local):
     pairs = s0["pairs_proxy"] if dom == "k_proxy" else s0["pairs_pairs"]
     ms_dom = s0["ms_proxy"] if dom == "k_proxy" else s0["ms_pairs"]
     kc = KERNEL_COUNTS[dom]
-    fresh = KERNEL_COUNTS["src_sha"] == kernel_src_sha()
+    tf_now = binding.wsbm_tuning()["pair_tf" if dom == "k_pairs" else "proxy_tf"]
+    fresh = KERNEL_COUNTS["src_sha"] == kernel_src_sha() and kc["tf"] == tf_now
     fl = kc["fp64_flops_per_pair"] if fresh else None
     achieved = (pairs * fl / (ms_dom * 1e-3) / 1e12) if fl else None
     roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
