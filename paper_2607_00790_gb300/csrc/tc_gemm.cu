@@ -25,8 +25,7 @@
 //     diagonals 0..4 and the high part of 5) and a 16-bit fraction F of unit 2^-64 (the rest of
 //     5, diagonal 6, and diagonal 7 rounded), whose carries move into T after every chunk
 //     (integer and FP32 pipes only).  At the end of the K loop,
-//     C_ij = beta C_ij + alpha (T + F 2^-16) 2^(e_i + f_j - 48),
-//     with (T + F 2^-16) 2^(e_i + f_j - 48) rounded once to a double by integer operations.
+//     C_ij = beta C_ij + alpha (T + F 2^-16) 2^(e_i + f_j - 48).
 //
 // Error: the rounding of X to 56 bits (relative to the row or column maximum) and the pairs
 // left out keep each entry of A B within about 2^-53 * 2k * max|A_i.| * max|B_.j| of the exact
@@ -613,10 +612,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           if (j >= item.n) continue;
           const int ex = ei + a.cexp[item.eoff_c + j] - 48;
           const int* fp = frac + (half * (TC_BN / 2) + 2 * c) * TC_BM + row;
+          // the sketch's tiles (one A digit) are short next to their epilogue: there the sums
+          // become doubles by integer operations (off the FP64 pipe); the full products keep two
+          // conversions and one FMA on the FP64 pipe, which their longer MMA phase hides
           double xr, xi;
-          if (!fixed_to_double(T[2 * c], fp[0], ex, xr))
+          if (!a.a1 || !fixed_to_double(T[2 * c], fp[0], ex, xr))
             xr = scale2(fma((double)fp[0], 1.0 / 65536.0, (double)T[2 * c]), ex);
-          if (!fixed_to_double(T[2 * c + 1], fp[TC_BM], ex, xi))
+          if (!a.a1 || !fixed_to_double(T[2 * c + 1], fp[TC_BM], ex, xi))
             xi = scale2(fma((double)fp[TC_BM], 1.0 / 65536.0, (double)T[2 * c + 1]), ex);
           double2* p = item.C + i + (int64_t)j * item.ldc;
           if (a.sub) {
