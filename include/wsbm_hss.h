@@ -448,7 +448,7 @@ int wsbm_autotune_build(const wsbm_geom* g, const wsbm_params* p, int32_t* out, 
 /* The shapes in use on the current device: out[0..4] as wsbm_autotune's, out[5..9] as
  * wsbm_autotune_build's, out[10] = 1 once wsbm_autotune ran on this device, out[11] = 1 once
  * wsbm_autotune_build did (or the flags last given to wsbm_tuning_set), out[12] the smallest
- * dense root order whose solves with 16 or more right-hand sides run as block solves on the
+ * dense root order whose solves with 4 or more right-hand sides run as block solves on the
  * tensor cores (default 1024).  out: 13 int32.  Errors: INVALID_ARG (out NULL). */
 int wsbm_tuning(int32_t* out);
 /* Sets the shapes of the current device without timing (e.g. the result of an earlier

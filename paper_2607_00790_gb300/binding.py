@@ -356,7 +356,7 @@ def wsbm_autotune_build(geom, params, device=None):
 def wsbm_tuning():
     """The launch shapes in use on the current device, with "tuned" / "tuned_build" = True once
     the respective autotuner ran there, and "solve_tc_min" (the smallest root order whose solves
-    with 16 or more right-hand sides use the tensor cores)."""
+    with 4 or more right-hand sides use the tensor cores)."""
     out = (ctypes.c_int32 * 13)()
     _check(lib().wsbm_tuning(out), "wsbm_tuning")
     v = list(out)

@@ -48,9 +48,15 @@
 // Dense roots of at least this order are factored by the LU whose trailing updates run on
 // the tensor cores (wsbm_lu_big); smaller ones by the batched FP64 blocked LU.
 // Solves with at least WSBM_TCSOLVE_RHS right-hand sides run their products on the tensor
-// cores, and their LU solves of box factors of at least WSBM_LU_TC_MIN unknowns and of roots of
-// at least wsbm_tune_current().solve_tc_min unknowns (1024 unless set) as block solves there
-// (WSBM_TCSOLVE_NB rows per block); the other LU solves stay FP64 triangular solves.
+// cores, and their LU solves of box factors of at least WSBM_LU_TC_MIN unknowns as block solves
+// there (WSBM_TCSOLVE_NB rows per block); the LU solves of dense roots of at least
+// wsbm_tune_current().solve_tc_min unknowns (1024 unless set) take the block solve from
+// WSBM_TCSOLVE_RHS_ROOT right-hand sides on (a large root is read once per solve either way,
+// and its FP64 triangular solve is bound by the FP64 pipe already at a few right-hand sides).
+// The other LU solves stay FP64 triangular solves.
+#ifndef WSBM_TCSOLVE_RHS_ROOT
+#define WSBM_TCSOLVE_RHS_ROOT 4
+#endif
 #ifndef WSBM_TCSOLVE_RHS
 #define WSBM_TCSOLVE_RHS 16
 #endif
@@ -2194,10 +2200,10 @@ static int plan_lu_tc(SolvePlan& P, const std::vector<TrsmDesc>& items) {
   return plan_copies(P, cfin);
 }
 
-// LU solves of a plan step: with WSBM_TCSOLVE_RHS or more right-hand sides, the matrices of at
-// least min_n unknowns on the tensor cores (plan_lu_tc), the rest as FP64 triangular solves.
-static int plan_lu_solves_auto(SolvePlan& P, const std::vector<TrsmDesc>& t, int min_n) {
-  if (P.nrhs < WSBM_TCSOLVE_RHS) return plan_lu_solves(P, t);
+// LU solves of a plan step: with min_rhs or more right-hand sides, the matrices of at least
+// min_n unknowns on the tensor cores (plan_lu_tc), the rest as FP64 triangular solves.
+static int plan_lu_solves_auto(SolvePlan& P, const std::vector<TrsmDesc>& t, int min_n, int min_rhs) {
+  if (P.nrhs < min_rhs) return plan_lu_solves(P, t);
   std::vector<TrsmDesc> tc, fp;
   for (const TrsmDesc& x : t) (x.n >= min_n ? tc : fp).push_back(x);
   HK(plan_lu_solves(P, fp));
@@ -2349,7 +2355,7 @@ static int plan_build(SolvePlan& P) {
       }
     }
     HK(plan_copies(P, c1));
-    HK(plan_lu_solves_auto(P, sd, WSBM_LU_TC_MIN));
+    HK(plan_lu_solves_auto(P, sd, WSBM_LU_TC_MIN, WSBM_TCSOLVE_RHS));
     HK(plan_gathers(P, gd));
     HK(plan_copies(P, rc0));
     HK(plan_gemms_auto(P, g1));
@@ -2374,7 +2380,7 @@ static int plan_build(SolvePlan& P) {
       rs.push_back(lu_desc(h->root, h->root_n, Y[i], h->root_n, h->root_piv, h->root_n, nrhs));
     }
     HK(plan_copies(P, c));
-    HK(plan_lu_solves_auto(P, rs, wsbm_tune_current().solve_tc_min));
+    HK(plan_lu_solves_auto(P, rs, wsbm_tune_current().solve_tc_min, WSBM_TCSOLVE_RHS_ROOT));
   }
   // ---- down sweep: t = bt - Dhat y (in RT), xh -= Z t; y of a box = its slice of the parent's x
   for (int t = T - 1; t >= 0; --t) {
