@@ -1132,6 +1132,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--no-extras", action="store_true")
+    ap.add_argument("--profile-tc-shape", default="4096,4096,128",
+                    help="m,n,k of the --profile-tc product")
     ap.add_argument("--tc-sweep", action="store_true",
                     help="tensor-core GEMM at several shapes and the dense LU at 16384 / 32768 unknowns")
     ap.add_argument("--no-autotune", action="store_true",
@@ -1171,7 +1173,8 @@ def main():
         print(json.dumps({"tc_sweep": run_tc_sweep("cuda")}), flush=True)
         return
     if args.profile_tc:
-        print(json.dumps(run_tc_gemm("cuda", 4096, 4096, 128, reps=1)), flush=True)
+        m, n, k = (int(v) for v in args.profile_tc_shape.split(","))
+        print(json.dumps(run_tc_gemm("cuda", m, n, k, reps=1)), flush=True)
         return
     if args.full_2p18:
         if args.mixed_tol > 0:
