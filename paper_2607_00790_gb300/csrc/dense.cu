@@ -1317,41 +1317,33 @@ __global__ void k_lut_swap(const LuSolveDesc* __restrict__ d, int j0, int jb) {
 // after (upper) it.
 __global__ void k_lut_trinv(const LuSolveDesc* __restrict__ d, int j0, int jb, int upper,
                             double2* __restrict__ Xall, int64_t ldx_item) {
-  // the inverse is formed in shared memory, element (r, c) at xs[r * (LUT_NB + 1) + c]: thread
-  // j owns column j, so a warp's accesses to one row are consecutive
-  extern __shared__ double2 xs[];
   const LuSolveDesc q = d[blockIdx.y];
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j0 >= q.n) return;
   const int b = min(jb, q.n - j0);
-  const int ld = LUT_NB + 1;
+  if (j >= b) return;
+  double2* x = Xall + blockIdx.y * ldx_item + (int64_t)j * b;
   const double2* T = q.A + j0 + (int64_t)j0 * q.lda;
   const double2 one = make_double2(1.0, 0.0), zero = make_double2(0.0, 0.0);
-  if (j < b) {
-    if (!upper) {
-      for (int i = 0; i < j; ++i) xs[i * ld + j] = zero;
-      xs[j * ld + j] = one;
-      for (int i = j + 1; i < b; ++i) {
-        double2 s = zero;
-        for (int t = j; t < i; ++t) s = cfms(T[i + (int64_t)t * q.lda], xs[t * ld + j], s);
-        xs[i * ld + j] = s;
-      }
-    } else {
-      for (int i = j + 1; i < b; ++i) xs[i * ld + j] = zero;
-      const double2 djj = T[j + (int64_t)j * q.lda];
-      xs[j * ld + j] = (djj.x == 0.0 && djj.y == 0.0) ? zero : cdiv(one, djj);
-      for (int i = j - 1; i >= 0; --i) {
-        double2 s = zero;
-        for (int t = i + 1; t <= j; ++t) s = cfms(T[i + (int64_t)t * q.lda], xs[t * ld + j], s);
-        const double2 dii = T[i + (int64_t)i * q.lda];
-        xs[i * ld + j] = (dii.x == 0.0 && dii.y == 0.0) ? zero : cdiv(s, dii);
-      }
+  if (!upper) {
+    for (int i = 0; i < j; ++i) x[i] = zero;
+    x[j] = one;
+    for (int i = j + 1; i < b; ++i) {
+      double2 s = zero;
+      for (int t = j; t < i; ++t) s = cfms(T[i + (int64_t)t * q.lda], x[t], s);
+      x[i] = s;
+    }
+  } else {
+    for (int i = j + 1; i < b; ++i) x[i] = zero;
+    const double2 djj = T[j + (int64_t)j * q.lda];
+    x[j] = (djj.x == 0.0 && djj.y == 0.0) ? zero : cdiv(one, djj);
+    for (int i = j - 1; i >= 0; --i) {
+      double2 s = zero;
+      for (int t = i + 1; t <= j; ++t) s = cfms(T[i + (int64_t)t * q.lda], x[t], s);
+      const double2 dii = T[i + (int64_t)i * q.lda];
+      x[i] = (dii.x == 0.0 && dii.y == 0.0) ? zero : cdiv(s, dii);
     }
   }
-  __syncthreads();
-  // column-major store, b x b with leading dimension b: consecutive threads, consecutive rows
-  double2* x = Xall + blockIdx.y * ldx_item;
-  for (int e = threadIdx.x; e < b * b; e += blockDim.x) x[e] = xs[(e % b) * ld + e / b];
 }
 
 // Inverses of the diagonal blocks of LU factors (unit lower L, upper U), for block triangular
@@ -1476,8 +1468,6 @@ int wsbm_lu_solve_tc_batched_nb(const LuSolveDesc* h, const LuSolveDesc* d, int 
     off = (wsbm_zgemm_tc_batched_ws_bytes(p.data(), (int)p.size()) + 255) & ~(size_t)255;
   }
   double2* X = (double2*)((char*)ws + off);  // LUT_NB x LUT_NB per box
-  const size_t trinv_smem = (size_t)LUT_NB * (LUT_NB + 1) * sizeof(double2);
-  if (wsbm_smem_optin((const void*)k_lut_trinv, trinv_smem) != cudaSuccess) return -3;
   const int64_t ldx = (int64_t)LUT_NB * LUT_NB;
   const double2 one = make_double2(1.0, 0.0), mone = make_double2(-1.0, 0.0), zero = make_double2(0.0, 0.0);
   std::vector<TcProduct> items;
@@ -1508,7 +1498,7 @@ int wsbm_lu_solve_tc_batched_nb(const LuSolveDesc* h, const LuSolveDesc* d, int 
   for (int j0 = 0; j0 < maxn; j0 += nb) {
     k_lu_panel<<<nbatch, 256, 0, st>>>(d_lu, j0, nb, nullptr);
     k_lut_swap<<<dim3(tiles_x((maxnc + 127) / 128), nbatch), 128, 0, st>>>(d, j0, nb);
-    k_lut_trinv<<<dim3(1, nbatch), nb, trinv_smem, st>>>(d, j0, nb, 0, X, ldx);
+    k_lut_trinv<<<dim3(1, nbatch), nb, 0, st>>>(d, j0, nb, 0, X, ldx);
     wsbm_count_launches(3);
     // U12 = L11^-1 [A12 | B1]  (in place: the digit planes are formed before C is written)
     for (int i = 0; i < nbatch; ++i) {
@@ -1534,7 +1524,7 @@ int wsbm_lu_solve_tc_batched_nb(const LuSolveDesc* h, const LuSolveDesc* d, int 
   }
   // ---- back substitution X = U^-1 (L^-1 P B), panels from the bottom
   for (int j0 = ((maxn - 1) / nb) * nb; j0 >= 0; j0 -= nb) {
-    k_lut_trinv<<<dim3(1, nbatch), nb, trinv_smem, st>>>(d, j0, nb, 1, X, ldx);
+    k_lut_trinv<<<dim3(1, nbatch), nb, 0, st>>>(d, j0, nb, 1, X, ldx);
     wsbm_count_launch();
     for (int i = 0; i < nbatch; ++i) {
       const LuSolveDesc& q = h[i];
