@@ -246,8 +246,8 @@ def run_ours(args, ws, rank, local):
         bchoice, bms = binding.wsbm_autotune_build(g, p64, device=dev)
         cand = [f"{tf}x{128 // tf}@{c}" for tf in (16, 32, 64) for c in (8, 16, 32)]
         tuning = {"choice": {**choice, **bchoice}, "candidate_ms": {
-            "tc_group_4_8_16": tms[0:3], "box_nb_32_64": tms[3:5], "root_nb_128_256_at_4096": tms[5:7],
-            "cpqr_cb_2_4_8": tms[7:10],
+            "tc_group_4_8_16_one_pass": tms[0:3], "tc_group_4_8_16_two_passes": tms[3:6],
+            "box_nb_32_64": tms[6:8], "root_nb_128_256_at_4096": tms[8:10], "cpqr_cb_2_4_8": tms[10:13],
             "k_pairs_tile@ctas_per_sm": dict(zip(cand, bms[0:9])),
             "k_proxy_tile@ctas_per_sm": dict(zip(cand, bms[9:18])),
             "id_phase_cpqr_threads_128_256": bms[18:20]}}
@@ -709,14 +709,15 @@ def run_full_2p18(dev, precision=0, tol=1e-8, rows=256, refine=True, ff_ref=None
     g, keep = binding.make_geom(curve, device=dev)
     p = binding.make_params(cfg["k0"], cfg["n"], leaf=cfg["leaf"], nproxy=cfg["nproxy"], id_tol=tol,
                             precision=precision, root_cap=200000)
-    # the root of this build is far above 12288 unknowns: the large-class root panel width (and
-    # the other tensor-core shapes) timed once per process, before the build
+    # the tensor-core shapes timed once per process, before the build; the root panel width is
+    # timed on a 4096-unknown matrix (its class below 12288 unknowns), so the large class keeps
+    # its width (256): a timing at 16384 unknowns does not carry over to a root of ~1e5
     if not _FULL_TUNING:
         choice, tms = binding.wsbm_autotune(n_box=2 * cfg["leaf"], nbox=N // cfg["leaf"], nrhs_box=128,
-                                            n_root=16384, device=dev)
+                                            n_root=4096, device=dev)
         _FULL_TUNING.update(choice=choice, candidate_ms={
-            "tc_group_4_8_16": tms[0:3], "box_nb_32_64": tms[3:5], "root_nb_128_256_at_16384": tms[5:7],
-            "cpqr_cb_2_4_8": tms[7:10]})
+            "tc_group_4_8_16_one_pass": tms[0:3], "tc_group_4_8_16_two_passes": tms[3:6],
+            "box_nb_32_64": tms[6:8], "root_nb_128_256_at_4096": tms[8:10], "cpqr_cb_2_4_8": tms[10:13]})
     tuning = dict(_FULL_TUNING)
     binding.trim_memory()
     s = binding.Solver(g, p, device=dev)
