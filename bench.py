@@ -246,8 +246,8 @@ def run_ours(args, ws, rank, local):
         bchoice, bms = binding.wsbm_autotune_build(g, p64, device=dev)
         cand = [f"{tf}x{128 // tf}@{c}" for tf in (16, 32, 64) for c in (8, 16, 32)]
         tuning = {"choice": {**choice, **bchoice}, "candidate_ms": {
-            "tc_group_4_8_16_one_pass": tms[0:3], "tc_group_4_8_16_two_passes": tms[3:6],
-            "box_nb_32_64": tms[6:8], "root_nb_128_256_at_4096": tms[8:10], "cpqr_cb_2_4_8": tms[10:13],
+            "tc_group_4_8_16": tms[0:3], "box_nb_32_64": tms[3:5], "root_nb_128_256_at_4096": tms[5:7],
+            "cpqr_cb_2_4_8": tms[7:10],
             "k_pairs_tile@ctas_per_sm": dict(zip(cand, bms[0:9])),
             "k_proxy_tile@ctas_per_sm": dict(zip(cand, bms[9:18])),
             "id_phase_cpqr_threads_128_256": bms[18:20]}}
@@ -716,8 +716,8 @@ def run_full_2p18(dev, precision=0, tol=1e-8, rows=256, refine=True, ff_ref=None
         choice, tms = binding.wsbm_autotune(n_box=2 * cfg["leaf"], nbox=N // cfg["leaf"], nrhs_box=128,
                                             n_root=4096, device=dev)
         _FULL_TUNING.update(choice=choice, candidate_ms={
-            "tc_group_4_8_16_one_pass": tms[0:3], "tc_group_4_8_16_two_passes": tms[3:6],
-            "box_nb_32_64": tms[6:8], "root_nb_128_256_at_4096": tms[8:10], "cpqr_cb_2_4_8": tms[10:13]})
+            "tc_group_4_8_16": tms[0:3], "box_nb_32_64": tms[3:5], "root_nb_128_256_at_4096": tms[5:7],
+            "cpqr_cb_2_4_8": tms[7:10]})
     tuning = dict(_FULL_TUNING)
     binding.trim_memory()
     s = binding.Solver(g, p, device=dev)

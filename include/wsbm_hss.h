@@ -417,20 +417,17 @@ int wsbm_lu_dense(void* A, int64_t lda, int32_t n, int32_t* piv, void* stream);
  *
  * wsbm_autotune: synthetic complex data of the given sizes, best of three after one warm-up:
  *   out[0]  rows of 128-row tiles per raster group of the tensor-core GEMM's tile order, of
- *           {4, 8, 16}, and out[5] its passes per accumulation chunk, of {1 (0), 2 (1): the high
- *           digit diagonals, then the low ones, each half of the accumulators drained while the
- *           other pass runs} (one 8192 x 8192 x 256 product per pair);
+ *           {4, 8, 16} (one 8192 x 8192 x 256 product);
  *   out[1]  panel width of the batched box LU, of {32, 64} (nbox boxes of n_box unknowns with
  *           nrhs_box right-hand sides each: the leaf level of a build);
  *   out[2], out[3]  outer panel width of the root LU, of {128, 256}, for roots below and from
  *           12288 unknowns; only the class of n_root is timed, the other keeps its value;
  *   out[4]  columns per warp pass of the column-pivoted QR of ID matrices of more than 2048
  *           rows, of {2, 4, 8} (152 matrices of 2560 x 128).
- * ms: host, 13 doubles or NULL: the GEMM times for groups 4, 8, 16 with one pass, then with two
- * passes, then the other candidates in the order above.  out: 6 int32.  Work space (two copies of
+ * ms: host, 10 doubles or NULL: the candidates' times in that order.  Work space (two copies of
  * the boxes, two n_root x n_root matrices, 3 GiB for the product, 1 GiB for the QRs) from the
  * library's allocator.  Sizes: 64 <= n_box <= 4096, 1 <= nbox <= 32767, 1 <= nrhs_box <= 4096,
- * at most 8 GiB of boxes, 256 <= n_root <= 32768.  Defaults without a call: 8, 64, 128, 256, 4, 0.
+ * at most 8 GiB of boxes, 256 <= n_root <= 32768.  Defaults without a call: 8, 64, 128, 256, 4.
  * Synchronous.  Errors: INVALID_ARG, OOM, CUDA, TIMEOUT. */
 int wsbm_autotune(int32_t n_box, int32_t nbox, int32_t nrhs_box, int32_t n_root, int32_t* out,
                   double* ms, void* stream);
@@ -452,13 +449,12 @@ int wsbm_autotune_build(const wsbm_geom* g, const wsbm_params* p, int32_t* out, 
  * wsbm_autotune_build's, out[10] = 1 once wsbm_autotune ran on this device, out[11] = 1 once
  * wsbm_autotune_build did (or the flags last given to wsbm_tuning_set), out[12] the smallest
  * dense root order whose solves with 4 or more right-hand sides run as block solves on the
- * tensor cores (default 1024), out[13] the GEMM's pass split (out[5] of wsbm_autotune).
- * out: 14 int32.  Errors: INVALID_ARG (out NULL). */
+ * tensor cores (default 1024).  out: 13 int32.  Errors: INVALID_ARG (out NULL). */
 int wsbm_tuning(int32_t* out);
 /* Sets the shapes of the current device without timing (e.g. the result of an earlier
- * autotune): in[0..13] in the order of wsbm_tuning, each among its documented candidates
+ * autotune): in[0..12] in the order of wsbm_tuning, each among its documented candidates
  * (raster group 1..64; box panel width 8..64, a multiple of 8; grids 1..64 CTAs per SM; flags
- * and the pass split 0 or 1; root order >= 1).  A solve plan already built keeps the shapes it was built with.
+ * 0 or 1; root order >= 1).  A solve plan already built keeps the shapes it was built with.
  * Errors: INVALID_ARG, CUDA (no device). */
 int wsbm_tuning_set(const int32_t* in);
 

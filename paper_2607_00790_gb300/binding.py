@@ -334,14 +334,11 @@ def wsbm_autotune(n_box=256, nbox=512, nrhs_box=160, n_root=16384, device=None):
     """Time the candidate shapes of the tensor-core paths and of the warp QR on the current
     device and keep the fastest (see wsbm_autotune in the C header).  Returns (choices dict,
     candidate times in ms: raster groups 4/8/16, box panel widths 32/64, root panel widths
-    128/256, QR columns per pass 2/4/8; the raster groups are timed with one and with two
-    passes per accumulation chunk, choice "tc_split")."""
-    out = (ctypes.c_int32 * 6)()
-    ms = (ctypes.c_double * 13)()
+    128/256, QR columns per pass 2/4/8)."""
+    out = (ctypes.c_int32 * 5)()
+    ms = (ctypes.c_double * 10)()
     _check(lib().wsbm_autotune(n_box, nbox, nrhs_box, n_root, out, ms, _stream(device)), "wsbm_autotune")
-    d = dict(zip(TUNE_KEYS, list(out)[:5]))
-    d["tc_split"] = out[5]
-    return d, list(ms)
+    return dict(zip(TUNE_KEYS, list(out))), list(ms)
 
 
 def wsbm_autotune_build(geom, params, device=None):
@@ -360,14 +357,13 @@ def wsbm_tuning():
     """The launch shapes in use on the current device, with "tuned" / "tuned_build" = True once
     the respective autotuner ran there, and "solve_tc_min" (the smallest root order whose solves
     with 4 or more right-hand sides use the tensor cores)."""
-    out = (ctypes.c_int32 * 14)()
+    out = (ctypes.c_int32 * 13)()
     _check(lib().wsbm_tuning(out), "wsbm_tuning")
     v = list(out)
     d = dict(zip(TUNE_KEYS + TUNE_BUILD_KEYS, v[:10]))
     d["tuned"] = bool(v[10])
     d["tuned_build"] = bool(v[11])
     d["solve_tc_min"] = v[12]
-    d["tc_split"] = v[13]
     return d
 
 
@@ -379,9 +375,9 @@ def wsbm_tuning_set(**shapes):
         if k not in cur:
             raise KeyError(k)
     cur.update(shapes)
-    arr = (ctypes.c_int32 * 14)(*[int(cur[k]) for k in TUNE_KEYS + TUNE_BUILD_KEYS],
+    arr = (ctypes.c_int32 * 13)(*[int(cur[k]) for k in TUNE_KEYS + TUNE_BUILD_KEYS],
                                 int(bool(cur["tuned"])), int(bool(cur["tuned_build"])),
-                                int(cur["solve_tc_min"]), int(cur["tc_split"]))
+                                int(cur["solve_tc_min"]))
     _check(lib().wsbm_tuning_set(arr), "wsbm_tuning_set")
 
 

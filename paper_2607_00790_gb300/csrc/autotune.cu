@@ -3,8 +3,6 @@
 // wsbm_autotune (synthetic data of the caller's sizes):
 //   tc_group      rows of 128-row tiles per raster group of the GEMM's tile order (how much of
 //                 A and B the CTAs running at the same time share in L2): 4, 8 or 16;
-//   tc_split      one pass per accumulation chunk, or two (high then low digit diagonals, each
-//                 half of TMEM drained while the other pass runs): 0 or 1;
 //   box_nb        panel width of the batched box LU (FP64 panel vs tensor-core product work):
 //                 32 or 64;
 //   root_nb_*     outer panel width of the root LU below / from wsbm_lu_big_large_n() unknowns:
@@ -45,7 +43,6 @@ static WsbmTune tune_default() {
   t.cpqr_cb = 4;
   t.tuned_build = 0;
   t.solve_tc_min = 1024;
-  t.tc_split = 0;
   return t;
 }
 
@@ -124,7 +121,7 @@ extern "C" int wsbm_autotune(int32_t n_box, int32_t nbox, int32_t nrhs_box, int3
   const WsbmTune t0 = wsbm_tune_current();
   WsbmTune t = t0;
   Timer tm;
-  double times[13] = {0};
+  double times[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
   auto best_of = [&](auto&& f, double* out_ms) -> int {
     int rc = f();  // warm-up
     if (rc) return rc;
@@ -167,24 +164,20 @@ extern "C" int wsbm_autotune(int32_t n_box, int32_t nbox, int32_t nrhs_box, int3
     p.pad = 0;
     const int cand[3] = {4, 8, 16};
     double bestv = 1e30;
-    for (int sp = 0; sp < 2; ++sp)
-      for (int c = 0; c < 3; ++c) {
-        double* tv = &times[3 * sp + c];
-        rc = best_of(
-            [&] {
-              return wsbm_zgemm_tc_batched_g(&p, 1, make_double2(-1.0, 0.0), make_double2(1.0, 0.0), ws, st,
-                                             cand[c], sp)
-                         ? WSBM_ERR_CUDA
-                         : WSBM_OK;
-            },
-            tv);
-        if (rc) return rc;
-        if (*tv < bestv) {
-          bestv = *tv;
-          t.tc_group = cand[c];
-          t.tc_split = sp;
-        }
+    for (int c = 0; c < 3; ++c) {
+      rc = best_of(
+          [&] {
+            return wsbm_zgemm_tc_batched_g(&p, 1, make_double2(-1.0, 0.0), make_double2(1.0, 0.0), ws, st, cand[c])
+                       ? WSBM_ERR_CUDA
+                       : WSBM_OK;
+          },
+          &times[c]);
+      if (rc) return rc;
+      if (times[c] < bestv) {
+        bestv = times[c];
+        t.tc_group = cand[c];
       }
+    }
   }
   // 2. box LU panel width: nbox boxes of n_box unknowns with nrhs_box right-hand sides
   {
@@ -224,10 +217,10 @@ extern "C" int wsbm_autotune(int32_t n_box, int32_t nbox, int32_t nrhs_box, int3
               return WSBM_ERR_CUDA;
             return wsbm_lu_solve_tc_batched_nb(h.data(), dh, nbox, dl, ws, st, cand[c]) ? WSBM_ERR_CUDA : WSBM_OK;
           },
-          &times[6 + c]);
+          &times[3 + c]);
       if (rc) return rc;
-      if (times[6 + c] < bestv) {
-        bestv = times[6 + c];
+      if (times[3 + c] < bestv) {
+        bestv = times[3 + c];
         t.box_nb = cand[c];
       }
     }
@@ -252,10 +245,10 @@ extern "C" int wsbm_autotune(int32_t n_box, int32_t nbox, int32_t nrhs_box, int3
               return WSBM_ERR_CUDA;
             return wsbm_lu_big_nb(A, n, (int)n, piv, nullptr, ws, st, cand[c]) ? WSBM_ERR_CUDA : WSBM_OK;
           },
-          &times[8 + c]);
+          &times[5 + c]);
       if (rc) return rc;
-      if (times[8 + c] < bestv) {
-        bestv = times[8 + c];
+      if (times[5 + c] < bestv) {
+        bestv = times[5 + c];
         pick = cand[c];
       }
     }
@@ -314,13 +307,13 @@ extern "C" int wsbm_autotune(int32_t n_box, int32_t nbox, int32_t nrhs_box, int3
               return WSBM_ERR_CUDA;
             return wsbm_cpqr_batched(dq, nb, 1, m, st) ? WSBM_ERR_CUDA : WSBM_OK;
           },
-          &times[10 + c]);
+          &times[7 + c]);
       if (rc) {
         tune_store(t0);
         return rc;
       }
-      if (times[10 + c] < bestv) {
-        bestv = times[10 + c];
+      if (times[7 + c] < bestv) {
+        bestv = times[7 + c];
         pick = cand[c];
       }
     }
@@ -334,10 +327,9 @@ extern "C" int wsbm_autotune(int32_t n_box, int32_t nbox, int32_t nrhs_box, int3
     out[2] = t.root_nb_mid;
     out[3] = t.root_nb_large;
     out[4] = t.cpqr_cb;
-    out[5] = t.tc_split;
   }
   if (ms)
-    for (int i = 0; i < 13; ++i) ms[i] = times[i];
+    for (int i = 0; i < 10; ++i) ms[i] = times[i];
   return WSBM_OK;
 }
 
@@ -424,9 +416,9 @@ extern "C" int wsbm_autotune_build(const wsbm_geom* g, const wsbm_params* p, int
 extern "C" int wsbm_tuning(int32_t* out) {
   if (!out) return WSBM_ERR_INVALID_ARG;
   const WsbmTune t = wsbm_tune_current();
-  const int32_t v[14] = {t.tc_group, t.box_nb,     t.root_nb_mid, t.root_nb_large, t.cpqr_cb,
+  const int32_t v[13] = {t.tc_group, t.box_nb,     t.root_nb_mid, t.root_nb_large, t.cpqr_cb,
                          t.pair_tf,  t.pair_ctas,  t.proxy_tf,    t.proxy_ctas,    t.cpqr_threads,
-                         t.tuned,    t.tuned_build, t.solve_tc_min, t.tc_split};
+                         t.tuned,    t.tuned_build, t.solve_tc_min};
   memcpy(out, v, sizeof(v));
   return WSBM_OK;
 }
@@ -438,7 +430,7 @@ extern "C" int wsbm_tuning_set(const int32_t* in) {
   if (in[0] < 1 || in[0] > 64 || in[1] < 8 || in[1] > 64 || in[1] % 8 || (in[2] != 128 && in[2] != 256) ||
       (in[3] != 128 && in[3] != 256) || (in[4] != 2 && in[4] != 4 && in[4] != 8) || !tf_ok(in[5]) ||
       !ctas_ok(in[6]) || !tf_ok(in[7]) || !ctas_ok(in[8]) || (in[9] != 128 && in[9] != 256) ||
-      (in[10] != 0 && in[10] != 1) || (in[11] != 0 && in[11] != 1) || in[12] < 1 || (in[13] != 0 && in[13] != 1))
+      (in[10] != 0 && in[10] != 1) || (in[11] != 0 && in[11] != 1) || in[12] < 1)
     return WSBM_ERR_INVALID_ARG;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return WSBM_ERR_CUDA;
@@ -457,7 +449,6 @@ extern "C" int wsbm_tuning_set(const int32_t* in) {
   t.tuned = in[10];
   t.tuned_build = in[11];
   t.solve_tc_min = in[12];
-  t.tc_split = in[13];
   tune_store(t);
   return WSBM_OK;
 }

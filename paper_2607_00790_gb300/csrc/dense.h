@@ -29,7 +29,6 @@ struct WsbmTune {
   int tc_group, box_nb, root_nb_mid, root_nb_large, tuned;
   int pair_tf, pair_ctas, proxy_tf, proxy_ctas, cpqr_threads, cpqr_cb, tuned_build;
   int solve_tc_min;
-  int tc_split;  // 1: two passes per accumulation chunk of the GEMM (drains overlapped)
 };
 WsbmTune wsbm_tune_current();
 
@@ -55,9 +54,9 @@ struct TcProduct {
 int wsbm_zgemm_tc_batched(const TcProduct* p, int nitems, double2 alpha, double2 beta, void* ws,
                           cudaStream_t st);
 size_t wsbm_zgemm_tc_batched_ws_bytes(const TcProduct* p, int nitems);
-// The same with an explicit raster group (rows of tiles per group, 1..64) and pass split (0, 1).
+// The same with an explicit raster group (rows of tiles per group, 1..64).
 int wsbm_zgemm_tc_batched_g(const TcProduct* p, int nitems, double2 alpha, double2 beta, void* ws,
-                            cudaStream_t st, int group, int split);
+                            cudaStream_t st, int group);
 // The same split into a host-side plan (item tables and work-space layout, built once) and a
 // launch sequence that reads the item tables from a device copy of `tab` made by the caller:
 // no host memory is read at launch, so the launches can be captured into a CUDA graph.
@@ -70,7 +69,7 @@ struct TcPlan {
 };
 int wsbm_zgemm_tc_plan(const TcProduct* p, int nitems, TcPlan* out);
 int wsbm_zgemm_tc_run(const TcPlan& pl, const void* dtab, double2 alpha, double2 beta, void* ws,
-                      cudaStream_t st, int group, int split);
+                      cudaStream_t st, int group);
 // Randomized row sketches Y_i = Omega[:m_i, :k_i] B_i on the tensor cores (Omega: +-1 from the
 // sketch hash of (row, column, seed), shared by all items; B_i: k_i x n_i complex, C_i = Y_i:
 // m_i x n_i, A ignored).  ws: 256-byte aligned, wsbm_sketch_tc_ws_bytes(p, n) bytes.  At most

@@ -2067,11 +2067,10 @@ static int plan_tc(SolvePlan& P, const std::vector<TcProduct>& items, double2 al
     HK(plan_upload(P, pl->tab, &dtab));
     P.tcws_bytes = std::max(P.tcws_bytes, pl->ws_bytes);
     P.uses_tc = true;
-    const WsbmTune tu = wsbm_tune_current();
-    const int group = tu.tc_group, split = tu.tc_split;
+    const int group = wsbm_tune_current().tc_group;
     SolvePlan* pp = &P;
-    P.ops.push_back([pl, dtab, alpha, beta, pp, group, split](cudaStream_t st) {
-      return wsbm_zgemm_tc_run(*pl, dtab, alpha, beta, pp->tcws, st, group, split) ? WSBM_ERR_CUDA : WSBM_OK;
+    P.ops.push_back([pl, dtab, alpha, beta, pp, group](cudaStream_t st) {
+      return wsbm_zgemm_tc_run(*pl, dtab, alpha, beta, pp->tcws, st, group) ? WSBM_ERR_CUDA : WSBM_OK;
     });
   }
   return WSBM_OK;

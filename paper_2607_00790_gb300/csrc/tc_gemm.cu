@@ -167,31 +167,6 @@ __device__ __forceinline__ void tc_sched(int e, int& t, int& u0, int& cnt) {
   }
 }
 
-// The same 34 pairs for the two-pass chunk (TcArgs.split): a pass over the chunk's K blocks
-// that writes only diagonals 4..7 (7 MMAs, 24 pairs, every A and B digit), then a pass that
-// writes only diagonals 0..3 (4 MMAs, 10 pairs, A and B digits 0..3).  Each half of TMEM is then
-// drained while the other pass runs.  The first MMA of each pass starts its diagonals from zero.
-__device__ __forceinline__ void tc_sched_hi(int e, int& t, int& u0, int& cnt) {
-  switch (e) {
-    case 0: t = 1, u0 = 3, cnt = 4; break;  // diagonals 4..7
-    case 1: t = 0, u0 = 4, cnt = 3; break;
-    case 2: t = 2, u0 = 2, cnt = 4; break;
-    case 3: t = 3, u0 = 1, cnt = 4; break;
-    case 4: t = 4, u0 = 0, cnt = 4; break;
-    case 5: t = 5, u0 = 0, cnt = 3; break;
-    default: t = 6, u0 = 0, cnt = 2; break;
-  }
-}
-__device__ __forceinline__ void tc_sched_lo(int e, int& t, int& u0, int& cnt) {
-  switch (e) {
-    case 0: t = 0, u0 = 0, cnt = 4; break;  // diagonals 0..3
-    case 1: t = 1, u0 = 0, cnt = 3; break;
-    case 2: t = 2, u0 = 0, cnt = 2; break;
-    default: t = 3, u0 = 0, cnt = 1; break;
-  }
-}
-#define TC_LO_PLANES 4                                      // digits read by the low pass
-#define TC_LO_STAGE_BYTES (TC_LO_PLANES * (TC_A_TILE + TC_B_TILE))
 __device__ __forceinline__ void tc_commit(uint32_t bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
                : "memory");
@@ -430,9 +405,6 @@ struct TcArgs {
   double2 alpha, beta;
   int sub;              // alpha = -1, beta = 1 (C -= A B): two FP64 additions per entry
   int group;            // row tiles per raster group of the tile order
-  int assign;           // alpha = 1, beta = 0 (C = A B): no FP64 arithmetic per entry
-  int split;            // two passes per chunk (high, then low diagonals), drains overlapped
-  int a1;               // A is one digit plane of a real matrix (sketches: Omega = +-1)
   const TcItem* items;
   const int* rexp;
   const int* cexp;
@@ -459,6 +431,8 @@ __device__ __forceinline__ void tile_coords(const TcItem& it, int r, int G, int&
   tn = q / gm;
 }
 
+// A1: A is one digit plane of a real matrix (the sketches: Omega = +-1, row scale 2^8).
+template <bool A1>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     k_zgemm_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, const TcArgs a) {
   extern __shared__ unsigned char smem_raw[];
@@ -467,16 +441,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   unsigned char* gbase = smem_raw + (base - raw);
   int* frac = reinterpret_cast<int*>(gbase + TC_STAGES * TC_STAGE_BYTES);  // F[col][row]
   const uint32_t bars = base + TC_STAGES * TC_STAGE_BYTES + TC_FRAC_BYTES;  // full[S], empty[S], tfull, tempty
-  // tfull / tempty: the chunk's accumulators (split: diagonals 4..7); tfull2 / tempty2: split
-  // chunks' diagonals 0..3
   const uint32_t full0 = bars, empty0 = bars + 8 * TC_STAGES, tfull = bars + 16 * TC_STAGES,
-                 tempty = tfull + 8, tfull2 = tfull + 16, tempty2 = tfull + 24;
+                 tempty = tfull + 8;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(gbase + TC_STAGES * TC_STAGE_BYTES + TC_FRAC_BYTES + 128);
   const int warp = threadIdx.x / 32, lane = threadIdx.x & 31;
   const int ntiles = a.ntiles;
   const int nchunk_kb = TC_KC / TC_BK;
-  const bool split = a.split && !a.a1;
-  const int npass = split ? 2 : 1;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < TC_STAGES; ++s) {
@@ -485,8 +455,6 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     }
     mbar_init(tfull, 1);
     mbar_init(tempty, TC_EPI);
-    mbar_init(tfull2, 1);
-    mbar_init(tempty2, TC_EPI);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 1) {
@@ -508,23 +476,18 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         const TcItem item = a.items[find_item(a, t)];
         int tm, tn;
         tile_coords(item, t - item.tile0, a.group, tm, tn);
-        for (int kb0 = 0; kb0 < a.nkb && ok; kb0 += nchunk_kb)
-          for (int pass = 0; pass < npass && ok; ++pass)
-            for (int kb = kb0; kb < min(a.nkb, kb0 + nchunk_kb) && ok; ++kb, ++it) {
-              const uint32_t s = it % TC_STAGES, ph = (it / TC_STAGES) & 1;
-              if (!(ok = mbar_wait(empty0 + 8 * s, ph ^ 1))) break;
-              const uint32_t full = full0 + 8 * s;
-              const bool lo = pass == 1;  // the low pass reads digits 0..3 only
-              mbar_expect_tx(full, a.a1 ? TC_A_TILE + TC_S * TC_B_TILE : (lo ? TC_LO_STAGE_BYTES : TC_STAGE_BYTES));
-              const uint32_t sa = base + s * TC_STAGE_BYTES, sb = sa + TC_S * TC_A_TILE;
+        for (int kb = 0; kb < a.nkb && ok; ++kb, ++it) {
+          const uint32_t s = it % TC_STAGES, ph = (it / TC_STAGES) & 1;
+          if (!(ok = mbar_wait(empty0 + 8 * s, ph ^ 1))) break;
+          const uint32_t full = full0 + 8 * s;
+          mbar_expect_tx(full, A1 ? TC_A_TILE + TC_S * TC_B_TILE : TC_STAGE_BYTES);
+          const uint32_t sa = base + s * TC_STAGE_BYTES, sb = sa + TC_S * TC_A_TILE;
 #pragma unroll
-              for (int p = 0; p < TC_S; ++p) {
-                if (lo && p >= TC_LO_PLANES) continue;
-                if (p == 0 || !a.a1)
-                  tma_load_3d(sa + p * TC_A_TILE, &mapA, full, kb * TC_BK, item.arow + tm * TC_BM, p);
-                tma_load_3d(sb + p * TC_B_TILE, &mapB, full, kb * TC_BK, item.brow + tn * TC_BN, p);
-              }
-            }
+          for (int p = 0; p < TC_S; ++p) {
+            if (p == 0 || !A1) tma_load_3d(sa + p * TC_A_TILE, &mapA, full, kb * TC_BK, item.arow + tm * TC_BM, p);
+            tma_load_3d(sb + p * TC_B_TILE, &mapB, full, kb * TC_BK, item.brow + tn * TC_BN, p);
+          }
+        }
       }
       // every load issued must have landed before the CTA can leave: wait (bounded) for the
       // last fill of each stage (no later phase of that barrier exists)
@@ -541,64 +504,33 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       bool ok = true;
       for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
         for (int kb0 = 0; kb0 < a.nkb && ok; kb0 += nchunk_kb, ++chunk) {
+          if (!(ok = mbar_wait(tempty, (chunk & 1) ^ 1))) break;
+          tc_fence_after();
           const int kb1 = min(a.nkb, kb0 + nchunk_kb);
-          for (int pass = 0; pass < npass && ok; ++pass) {
-            if (!(ok = mbar_wait(pass ? tempty2 : tempty, (chunk & 1) ^ 1))) break;
+          for (int kb = kb0; kb < kb1; ++kb, ++it) {
+            const uint32_t s = it % TC_STAGES, ph = (it / TC_STAGES) & 1;
+            if (!(ok = mbar_wait(full0 + 8 * s, ph))) break;
             tc_fence_after();
-            for (int kb = kb0; kb < kb1; ++kb, ++it) {
-              const uint32_t s = it % TC_STAGES, ph = (it / TC_STAGES) & 1;
-              if (!(ok = mbar_wait(full0 + 8 * s, ph))) break;
-              tc_fence_after();
-              const uint32_t sa = base + s * TC_STAGE_BYTES, sb = sa + TC_S * TC_A_TILE;
-              if (!split) {
+            const uint32_t sa = base + s * TC_STAGE_BYTES, sb = sa + TC_S * TC_A_TILE;
 #pragma unroll
-                for (int kk = 0; kk < TC_BK / 16; ++kk) {
+            for (int kk = 0; kk < TC_BK / 16; ++kk) {
 #pragma unroll
-                  for (int e = 0; e < 11; ++e) {
-                    // one-digit A: only A digit 0 (entries 1 and 2: diagonals 0..3 and 4..6,
-                    // both started from zero; diagonal 7 stays unused)
-                    if (a.a1 && e != 1 && e != 2) continue;
-                    int tt, u0, cnt;
-                    tc_sched(e, tt, u0, cnt);
-                    const uint64_t da = sdesc_sw64(sa + tt * TC_A_TILE);
-                    const uint64_t db = sdesc_sw64(sb + u0 * TC_B_TILE);
-                    const uint32_t acc = (kb > kb0 || kk > 0 || (e >= 2 && !a.a1)) ? 1u : 0u;
-                    // K step of 16 BF16 values = 32 bytes = 2 units of the start address
-                    tc_mma(tmem + (tt + u0) * TC_BN, da + 2 * kk, db + 2 * kk, tc_idesc(cnt * TC_BN), acc);
-                  }
-                }
-              } else if (pass == 0) {
-#pragma unroll
-                for (int kk = 0; kk < TC_BK / 16; ++kk) {
-#pragma unroll
-                  for (int e = 0; e < 7; ++e) {
-                    int tt, u0, cnt;
-                    tc_sched_hi(e, tt, u0, cnt);
-                    const uint64_t da = sdesc_sw64(sa + tt * TC_A_TILE);
-                    const uint64_t db = sdesc_sw64(sb + u0 * TC_B_TILE);
-                    const uint32_t acc = (kb > kb0 || kk > 0 || e > 0) ? 1u : 0u;
-                    tc_mma(tmem + (tt + u0) * TC_BN, da + 2 * kk, db + 2 * kk, tc_idesc(cnt * TC_BN), acc);
-                  }
-                }
-              } else {
-#pragma unroll
-                for (int kk = 0; kk < TC_BK / 16; ++kk) {
-#pragma unroll
-                  for (int e = 0; e < 4; ++e) {
-                    int tt, u0, cnt;
-                    tc_sched_lo(e, tt, u0, cnt);
-                    const uint64_t da = sdesc_sw64(sa + tt * TC_A_TILE);
-                    const uint64_t db = sdesc_sw64(sb + u0 * TC_B_TILE);
-                    const uint32_t acc = (kb > kb0 || kk > 0 || e > 0) ? 1u : 0u;
-                    tc_mma(tmem + (tt + u0) * TC_BN, da + 2 * kk, db + 2 * kk, tc_idesc(cnt * TC_BN), acc);
-                  }
-                }
+              for (int e = 0; e < 11; ++e) {
+                // one-digit A: only A digit 0 (entries 1 and 2: diagonals 0..3 and 4..6, both
+                // started from zero; diagonal 7 stays unused)
+                if (A1 && e != 1 && e != 2) continue;
+                int tt, u0, cnt;
+                tc_sched(e, tt, u0, cnt);
+                const uint64_t da = sdesc_sw64(sa + tt * TC_A_TILE);
+                const uint64_t db = sdesc_sw64(sb + u0 * TC_B_TILE);
+                const uint32_t acc = (kb > kb0 || kk > 0 || (e >= 2 && !A1)) ? 1u : 0u;
+                // K step of 16 BF16 values = 32 bytes = 2 units of the start address
+                tc_mma(tmem + (tt + u0) * TC_BN, da + 2 * kk, db + 2 * kk, tc_idesc(cnt * TC_BN), acc);
               }
-              tc_commit(empty0 + 8 * s);  // the stage is free once these MMAs have read it
             }
-            // the pass's accumulators are complete
-            if (ok) tc_commit(pass ? tfull2 : tfull);
+            tc_commit(empty0 + 8 * s);  // the stage is free once these MMAs have read it
           }
+          if (ok) tc_commit(tfull);  // the chunk's accumulators are complete
         }
       }
     }
@@ -620,12 +552,27 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         T[c] = 0;
         frac[(half * (TC_BN / 2) + c) * TC_BM + row] = 0;
       }
-      // high diagonals 4..7: the unit-2^-48 part into T, the 2^-64 fraction into F
-      auto drain_hi = [&]() {
+      for (int kb0 = 0; kb0 < a.nkb; kb0 += nchunk_kb, ++chunk) {
+        if (!(ok = mbar_wait(tfull, chunk & 1))) break;
+        tc_fence_after();
 #pragma unroll
         for (int g = 0; g < TC_BN / 16; ++g) {
+          // diagonals in pairs, converted as they arrive (fewer live registers)
           float v0[8], v1[8];
-          int p3[8], f5[8];
+          int p1[8], p3[8], f5[8];
+          long long p2[8];
+          tmem_ld8(tq + 0 * TC_BN + g * 8, v0);
+          tmem_ld8(tq + 1 * TC_BN + g * 8, v1);
+          tmem_ld_wait();
+#pragma unroll
+          for (int c = 0; c < 8; ++c) p1[c] = __float2int_rn(v0[c]) * 256 + __float2int_rn(v1[c]);  // < 2^31
+          tmem_ld8(tq + 2 * TC_BN + g * 8, v0);
+          tmem_ld8(tq + 3 * TC_BN + g * 8, v1);
+          tmem_ld_wait();
+#pragma unroll
+          for (int c = 0; c < 8; ++c) {
+            p2[c] = ((long long)__float2int_rn(v0[c]) << 8) + __float2int_rn(v1[c]);  // up to 2^32
+          }
           tmem_ld8(tq + 4 * TC_BN + g * 8, v0);
           tmem_ld8(tq + 5 * TC_BN + g * 8, v1);
           tmem_ld_wait();
@@ -638,7 +585,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           tmem_ld8(tq + 6 * TC_BN + g * 8, v0);
           tmem_ld8(tq + 7 * TC_BN + g * 8, v1);
           tmem_ld_wait();
-          if (a.a1) {
+          if (A1) {
 #pragma unroll
             for (int c = 0; c < 8; ++c) v1[c] = 0.0f;
           }
@@ -648,49 +595,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             int* fp = frac + col * TC_BM + row;
             const int fn = *fp + f5[c] + __float2int_rn(v0[c]) + __float2int_rn(v1[c] * (1.0f / 256.0f));
             *fp = fn & 0xFFFF;
-            T[g * 8 + c] += (long long)p3[c] + (fn >> 16);
+            T[g * 8 + c] += ((long long)p1[c] << 24) + (p2[c] << 8) + (long long)p3[c] + (fn >> 16);
           }
         }
-      };
-      // low diagonals 0..3 (exact integer sums): into T
-      auto drain_lo = [&]() {
-#pragma unroll
-        for (int g = 0; g < TC_BN / 16; ++g) {
-          float v0[8], v1[8];
-          int p1[8];
-          tmem_ld8(tq + 0 * TC_BN + g * 8, v0);
-          tmem_ld8(tq + 1 * TC_BN + g * 8, v1);
-          tmem_ld_wait();
-#pragma unroll
-          for (int c = 0; c < 8; ++c) p1[c] = __float2int_rn(v0[c]) * 256 + __float2int_rn(v1[c]);  // < 2^31
-          tmem_ld8(tq + 2 * TC_BN + g * 8, v0);
-          tmem_ld8(tq + 3 * TC_BN + g * 8, v1);
-          tmem_ld_wait();
-#pragma unroll
-          for (int c = 0; c < 8; ++c) {
-            const long long p2 = ((long long)__float2int_rn(v0[c]) << 8) + __float2int_rn(v1[c]);  // up to 2^32
-            T[g * 8 + c] += ((long long)p1[c] << 24) + (p2 << 8);
-          }
-        }
-      };
-      for (int kb0 = 0; kb0 < a.nkb; kb0 += nchunk_kb, ++chunk) {
-        if (!(ok = mbar_wait(tfull, chunk & 1))) break;
-        tc_fence_after();
-        drain_hi();
-        if (split) {
-          // the high half is free for the next chunk's first pass while the low pass runs
-          tc_fence_before();
-          mbar_arrive(tempty);
-          if (!(ok = mbar_wait(tfull2, chunk & 1))) break;
-          tc_fence_after();
-          drain_lo();
-          tc_fence_before();
-          mbar_arrive(tempty2);
-        } else {
-          drain_lo();
-          tc_fence_before();
-          mbar_arrive(tempty);
-        }
+        tc_fence_before();
+        mbar_arrive(tempty);
       }
       if (!ok) break;
       // C = beta C + alpha (T + F 2^-16) 2^(e_i + f_j - 48); the power of two enters through
@@ -704,20 +613,23 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           if (j >= item.n) continue;
           const int ex = ei + a.cexp[item.eoff_c + j] - 48;
           const int* fp = frac + (half * (TC_BN / 2) + 2 * c) * TC_BM + row;
-          // the sketch's tiles (one A digit) are short next to their epilogue: there the sums
-          // become doubles by integer operations (off the FP64 pipe); the full products keep two
-          // conversions and one FMA on the FP64 pipe, which their longer MMA phase hides
-          double xr, xi;
-          if (!a.a1 || !fixed_to_double(T[2 * c], fp[0], ex, xr))
-            xr = scale2(fma((double)fp[0], 1.0 / 65536.0, (double)T[2 * c]), ex);
-          if (!a.a1 || !fixed_to_double(T[2 * c + 1], fp[TC_BM], ex, xi))
-            xi = scale2(fma((double)fp[TC_BM], 1.0 / 65536.0, (double)T[2 * c + 1]), ex);
           double2* p = item.C + i + (int64_t)j * item.ldc;
+          if (A1) {
+            // the sketch's tiles (one A digit) are short next to their epilogue: the sums become
+            // doubles by integer operations (off the FP64 pipe) and are stored (C = A B)
+            double xr, xi;
+            if (!fixed_to_double(T[2 * c], fp[0], ex, xr))
+              xr = scale2(fma((double)fp[0], 1.0 / 65536.0, (double)T[2 * c]), ex);
+            if (!fixed_to_double(T[2 * c + 1], fp[TC_BM], ex, xi))
+              xi = scale2(fma((double)fp[TC_BM], 1.0 / 65536.0, (double)T[2 * c + 1]), ex);
+            *p = make_double2(xr, xi);
+            continue;
+          }
+          const double xr = scale2(fma((double)fp[0], 1.0 / 65536.0, (double)T[2 * c]), ex);
+          const double xi = scale2(fma((double)fp[TC_BM], 1.0 / 65536.0, (double)T[2 * c + 1]), ex);
           if (a.sub) {
             const double2 o = *p;
             *p = make_double2(o.x - xr, o.y - xi);
-          } else if (a.assign) {
-            *p = make_double2(xr, xi);
           } else {
             double2 r = make_double2(a.alpha.x * xr - a.alpha.y * xi, a.alpha.x * xi + a.alpha.y * xr);
             if (a.beta.x != 0.0 || a.beta.y != 0.0) {
@@ -878,9 +790,9 @@ int wsbm_zgemm_tc_plan(const TcProduct* p, int nitems, TcPlan* out) {
 }
 
 int wsbm_zgemm_tc_run(const TcPlan& pl, const void* dtab_v, double2 alpha, double2 beta, void* ws,
-                      cudaStream_t st, int group, int split) {
+                      cudaStream_t st, int group) {
   if (pl.nitems <= 0 || pl.tiles == 0) return 0;
-  if (group < 1 || group > 64 || (split != 0 && split != 1)) return -1;
+  if (group < 1 || group > 64) return -1;
   if (!dtab_v || !ws || ((uintptr_t)ws & 255) != 0) return -1;
   const int nitems = pl.nitems;
   const int64_t Ka = tc_ka(pl.kmax), ra = pl.ra, rb = pl.rb;
@@ -908,22 +820,19 @@ int wsbm_zgemm_tc_run(const TcPlan& pl, const void* dtab_v, double2 alpha, doubl
   a.alpha = alpha;
   a.beta = beta;
   a.sub = alpha.x == -1.0 && alpha.y == 0.0 && beta.x == 1.0 && beta.y == 0.0;
-  a.assign = alpha.x == 1.0 && alpha.y == 0.0 && beta.x == 0.0 && beta.y == 0.0;
-  a.split = split;
   a.group = group;
-  a.a1 = 0;
   a.items = ditems;
   a.rexp = exps;
   a.cexp = exps;
-  if (wsbm_smem_optin((const void*)k_zgemm_tc, TC_SMEM) != cudaSuccess) return -3;
+  if (wsbm_smem_optin((const void*)k_zgemm_tc<false>, TC_SMEM) != cudaSuccess) return -3;
   const int grid = pl.tiles < wsbm_sm_count() ? pl.tiles : wsbm_sm_count();
-  k_zgemm_tc<<<grid, TC_THREADS, TC_SMEM, st>>>(ma, mb, a);
+  k_zgemm_tc<false><<<grid, TC_THREADS, TC_SMEM, st>>>(ma, mb, a);
   wsbm_count_launch();
   return cudaGetLastError() == cudaSuccess ? 0 : -3;
 }
 
 int wsbm_zgemm_tc_batched_g(const TcProduct* p, int nitems, double2 alpha, double2 beta, void* ws,
-                            cudaStream_t st, int group, int split) {
+                            cudaStream_t st, int group) {
   if (nitems <= 0) return 0;
   if (group < 1 || group > 64) return -1;
   if (!p || !ws || ((uintptr_t)ws & 255) != 0) return -1;
@@ -934,12 +843,11 @@ int wsbm_zgemm_tc_batched_g(const TcProduct* p, int nitems, double2 alpha, doubl
   // launches that read them
   unsigned char* dtab = (unsigned char*)ws + pl.off_tab;
   if (cudaMemcpyAsync(dtab, pl.tab.data(), pl.tab.size(), cudaMemcpyHostToDevice, st) != cudaSuccess) return -3;
-  return wsbm_zgemm_tc_run(pl, dtab, alpha, beta, ws, st, group, split);
+  return wsbm_zgemm_tc_run(pl, dtab, alpha, beta, ws, st, group);
 }
 
 int wsbm_zgemm_tc_batched(const TcProduct* p, int nitems, double2 alpha, double2 beta, void* ws, cudaStream_t st) {
-  const WsbmTune t = wsbm_tune_current();
-  return wsbm_zgemm_tc_batched_g(p, nitems, alpha, beta, ws, st, t.tc_group, t.tc_split);
+  return wsbm_zgemm_tc_batched_g(p, nitems, alpha, beta, ws, st, wsbm_tune_current().tc_group);
 }
 
 int wsbm_zgemm_tc(int m, int n, int k, double2 alpha, const double2* A, int64_t lda, const double2* B,
@@ -1130,16 +1038,13 @@ int wsbm_sketch_tc(const TcProduct* p, int nitems, uint32_t seed, void* ws, cuda
   a.alpha = make_double2(1.0, 0.0);
   a.beta = make_double2(0.0, 0.0);
   a.sub = 0;
-  a.assign = 1;
-  a.split = 0;
   a.group = wsbm_tune_current().tc_group;
-  a.a1 = 1;
   a.items = ditems;
   a.rexp = exps;
   a.cexp = exps;
-  if (wsbm_smem_optin((const void*)k_zgemm_tc, TC_SMEM) != cudaSuccess) return -3;
+  if (wsbm_smem_optin((const void*)k_zgemm_tc<true>, TC_SMEM) != cudaSuccess) return -3;
   const int grid = a.ntiles < wsbm_sm_count() ? a.ntiles : wsbm_sm_count();
-  k_zgemm_tc<<<grid, TC_THREADS, TC_SMEM, st>>>(ma, mb, a);
+  k_zgemm_tc<true><<<grid, TC_THREADS, TC_SMEM, st>>>(ma, mb, a);
   wsbm_count_launch();
   return cudaGetLastError() == cudaSuccess ? 0 : -3;
 }

@@ -26,15 +26,14 @@ def test_autotune_picks_candidates_and_keeps_them(restore_tuning):
     assert choice["root_nb_mid"] in (128, 256)
     assert choice["root_nb_large"] == restore_tuning["root_nb_large"]  # class not timed: kept
     assert choice["cpqr_cb"] in (2, 4, 8)
-    assert choice["tc_split"] in (0, 1)
-    assert len(ms) == 13 and all(t > 0 for t in ms)
+    assert len(ms) == 10 and all(t > 0 for t in ms)
     # the fastest candidate of each group is the one kept
-    assert ms[3 * choice["tc_split"] + [4, 8, 16].index(choice["tc_group"])] == min(ms[0:6])
-    assert ms[6 + [32, 64].index(choice["box_nb"])] == min(ms[6:8])
-    assert ms[8 + [128, 256].index(choice["root_nb_mid"])] == min(ms[8:10])
-    assert ms[10 + [2, 4, 8].index(choice["cpqr_cb"])] == min(ms[10:13])
+    assert ms[[4, 8, 16].index(choice["tc_group"])] == min(ms[0:3])
+    assert ms[3 + [32, 64].index(choice["box_nb"])] == min(ms[3:5])
+    assert ms[5 + [128, 256].index(choice["root_nb_mid"])] == min(ms[5:7])
+    assert ms[7 + [2, 4, 8].index(choice["cpqr_cb"])] == min(ms[7:10])
     now = binding.wsbm_tuning()
-    assert now["tuned"] and all(now[k] == choice[k] for k in binding.TUNE_KEYS + ("tc_split",))
+    assert now["tuned"] and all(now[k] == choice[k] for k in binding.TUNE_KEYS)
     # the build shapes are untouched
     assert all(now[k] == restore_tuning[k] for k in binding.TUNE_BUILD_KEYS)
 
@@ -43,8 +42,7 @@ def test_tuning_rejects_bad_shapes_and_sizes(restore_tuning):
     from paper_2607_00790_gb300 import binding
     for bad in [dict(tc_group=0), dict(box_nb=12), dict(box_nb=72), dict(root_nb_mid=192),
                 dict(root_nb_large=512), dict(cpqr_cb=3), dict(pair_tf=8), dict(proxy_tf=128),
-                dict(pair_ctas=0), dict(proxy_ctas=65), dict(cpqr_threads=64), dict(solve_tc_min=0),
-                dict(tc_split=2)]:
+                dict(pair_ctas=0), dict(proxy_ctas=65), dict(cpqr_threads=64), dict(solve_tc_min=0)]:
         with pytest.raises(binding.WsbmError):
             binding.wsbm_tuning_set(**bad)
     assert binding.wsbm_tuning() == restore_tuning
@@ -54,10 +52,7 @@ def test_tuning_rejects_bad_shapes_and_sizes(restore_tuning):
         binding.wsbm_autotune(n_box=128, nbox=4, nrhs_box=4, n_root=65536)
 
 
-def test_raster_group_and_pass_split_change_no_bit(restore_tuning):
-    """Every raster group, with one or two passes per chunk (k = 300: two chunks and a ragged
-    third), gives the same product bit for bit: the digit sums are exact integers or are
-    accumulated in the same order per diagonal, and the fixed-point drain adds integers."""
+def test_raster_group_changes_no_bit(restore_tuning):
     import torch
     from paper_2607_00790_gb300 import binding
     rng = np.random.default_rng(21)
@@ -65,8 +60,8 @@ def test_raster_group_and_pass_split_change_no_bit(restore_tuning):
     A = torch.as_tensor(rng.normal(size=(m, k)) + 1j * rng.normal(size=(m, k)), device="cuda")
     B = torch.as_tensor(rng.normal(size=(k, n)) + 1j * rng.normal(size=(k, n)), device="cuda")
     outs = []
-    for g, sp in ((1, 0), (4, 0), (8, 0), (16, 0), (64, 0), (8, 1), (16, 1), (1, 1)):
-        binding.wsbm_tuning_set(tc_group=g, tc_split=sp)
+    for g in (1, 4, 8, 16, 64):
+        binding.wsbm_tuning_set(tc_group=g)
         outs.append(np.ascontiguousarray(binding.wsbm_zgemm(A, B).cpu().numpy()))
     for o in outs[1:]:
         assert o.tobytes() == outs[0].tobytes()
