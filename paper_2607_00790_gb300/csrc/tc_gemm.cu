@@ -32,7 +32,7 @@
 // product, the bound of an FP64 product.
 //
 // Kernel: one CTA per SM, persistent over 128 x 64 (real) output tiles.  Warp 0 issues the TMA
-// loads of the 14 digit planes of a 32-wide K block (a 2-stage ring in shared memory, 64-byte
+// loads of the 14 digit planes of a 16-wide K block (a 4-stage ring in shared memory, 32-byte
 // swizzled rows), warp 1 allocates TMEM (8 accumulators x 64 columns) and issues the MMAs
 // (one thread), warps 2-9 drain the accumulators (two threads per TMEM lane = output row, each
 // with 32 of the 64 columns) and write C.  Every wait on a barrier is bounded in time; a wait that runs out sets an error
@@ -49,13 +49,15 @@
 
 #define TC_BM 128                       // output rows per tile (= TMEM lanes)
 #define TC_BN 64                        // real output columns per tile (32 complex)
-#define TC_BK 32                        // real K values per pipeline stage (64-byte rows)
+#ifndef TC_BK
+#define TC_BK 16                        // real K values per pipeline stage (32-byte rows)
+#endif
 #define TC_S 7                          // digits per operand
 #define TC_ND 8                         // digit diagonals kept (t + u <= 7)
-#define TC_STAGES 2
+#define TC_STAGES (64 / TC_BK)          // 4 stages of 16 K values (2 of 32): about 168 KB in flight
 #define TC_KC 256                       // real K values per accumulation chunk (drain period)
-#define TC_A_TILE (TC_BM * TC_BK * 2)   // bytes of one A digit plane tile (8 KB)
-#define TC_B_TILE (TC_BN * TC_BK * 2)   // bytes of one B digit plane tile (4 KB)
+#define TC_A_TILE (TC_BM * TC_BK * 2)   // bytes of one A digit plane tile (4 KB)
+#define TC_B_TILE (TC_BN * TC_BK * 2)   // bytes of one B digit plane tile (2 KB)
 #define TC_STAGE_BYTES (TC_S * (TC_A_TILE + TC_B_TILE))
 #define TC_FRAC_BYTES (TC_BN * TC_BM * 4)  // fraction words F of a tile (int32, column-major)
 #define TC_SMEM (TC_STAGES * TC_STAGE_BYTES + TC_FRAC_BYTES + 256 + 1024)
@@ -66,6 +68,7 @@
 
 static_assert(TC_STAGE_BYTES % 1024 == 0, "stage alignment");
 static_assert(TC_KC % TC_BK == 0, "chunk of whole stages");
+static_assert(TC_BK == 16 || TC_BK == 32, "rows of 32 bytes (32-byte swizzle) or 64 (64-byte swizzle)");
 
 static __device__ int g_tc_error;  // set when a bounded wait ran out
 
@@ -123,15 +126,16 @@ __device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
-// Shared-memory operand descriptor: K-major tile of 64-byte rows with the 64-byte swizzle
-// (atoms of 8 rows x 64 bytes, 512 bytes apart), descriptor version 1.
-__device__ __forceinline__ uint64_t sdesc_sw64(uint32_t addr) {
+// Shared-memory operand descriptor: K-major tile of TC_BK * 2-byte rows swizzled over the row
+// width (atoms of 8 rows, 8 * 2 TC_BK bytes apart), descriptor version 1; swizzle code 6 for
+// 32-byte rows, 4 for 64-byte rows.
+__device__ __forceinline__ uint64_t sdesc_sw(uint32_t addr) {
   uint64_t d = 0;
-  d |= (uint64_t)((addr >> 4) & 0x3FFF);      // start address
-  d |= (uint64_t)1 << 16;                     // leading byte offset (unused for this layout)
-  d |= (uint64_t)(512 >> 4) << 32;            // stride byte offset: 8-row groups
-  d |= (uint64_t)1 << 46;                     // version
-  d |= (uint64_t)4 << 61;                     // layout: 64-byte swizzle
+  d |= (uint64_t)((addr >> 4) & 0x3FFF);               // start address
+  d |= (uint64_t)1 << 16;                              // leading byte offset (unused for this layout)
+  d |= (uint64_t)((8 * 2 * TC_BK) >> 4) << 32;         // stride byte offset: 8-row groups
+  d |= (uint64_t)1 << 46;                              // version
+  d |= (uint64_t)(TC_BK == 16 ? 6 : 4) << 61;          // layout: 32- or 64-byte swizzle
   return d;
 }
 // Instruction descriptor: BF16 x BF16 -> FP32, both operands K-major, M = 128, N = n (a
@@ -521,8 +525,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 if (A1 && e != 1 && e != 2) continue;
                 int tt, u0, cnt;
                 tc_sched(e, tt, u0, cnt);
-                const uint64_t da = sdesc_sw64(sa + tt * TC_A_TILE);
-                const uint64_t db = sdesc_sw64(sb + u0 * TC_B_TILE);
+                const uint64_t da = sdesc_sw(sa + tt * TC_A_TILE);
+                const uint64_t db = sdesc_sw(sb + u0 * TC_B_TILE);
                 const uint32_t acc = (kb > kb0 || kk > 0 || (e >= 2 && !A1)) ? 1u : 0u;
                 // K step of 16 BF16 values = 32 bytes = 2 units of the start address
                 tc_mma(tmem + (tt + u0) * TC_BN, da + 2 * kk, db + 2 * kk, tc_idesc(cnt * TC_BN), acc);
@@ -721,7 +725,8 @@ static int make_map(CUtensorMap* map, void* planes, int64_t rows, int64_t Ka, in
   cuuint32_t box[3] = {TC_BK, (cuuint32_t)box_rows, 1};
   cuuint32_t es[3] = {1, 1, 1};
   CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, planes, dims, strides, box, es,
-                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, TC_BK == 16 ? CU_TENSOR_MAP_SWIZZLE_32B : CU_TENSOR_MAP_SWIZZLE_64B,
+                   CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS ? 0 : -3;
 }
