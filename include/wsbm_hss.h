@@ -413,7 +413,8 @@ int wsbm_lu_dense(void* A, int64_t lda, int32_t n, int32_t* piv, void* stream);
  * (builds, solves, wsbm_zgemm*, wsbm_lu_dense) for the rest of the process, and leaves the
  * other shapes as they were.  Every shape gives the same accuracy; the GEMM raster group and
  * the entry-kernel shapes change no bit of any result (the panel widths and QR block sizes
- * change the rounding order).
+ * change the rounding order).  While an autotuner runs it switches the device's shapes between
+ * candidates: other calls on the same device must not run at the same time.
  *
  * wsbm_autotune: synthetic complex data of the given sizes, best of three after one warm-up:
  *   out[0]  rows of 128-row tiles per raster group of the tensor-core GEMM's tile order, of
