@@ -1115,49 +1115,20 @@ __global__ void k_lub_trsm(double2* __restrict__ A, int64_t lda, int r0, int nb,
   }
 }
 
-// Row i of the inverse X of a b x b triangular block T (leading dimension ldt): unit lower
-// (upper = false) or upper (upper = true); X column-major with leading dimension ldx.  One thread
-// per row, all threads of a warp on the same column c at a time, so that the reads of T are
-// broadcasts and the reads and writes of X are consecutive across the warp:
-//   lower: X(i, c) = -sum_{t = c+1..i} X(i, t) T(t, c),            c = i-1 .. 0, X(i, i) = 1
-//   upper: X(i, c) = -sum_{t = i..c-1} X(i, t) T(t, c) / T(c, c),   c = i+1 .. b-1, X(i, i) = 1 / T(i, i)
-// (a zero diagonal entry of U gives zeros).  Every thread of the block must call it (the loops
-// over c are uniform); rows i >= b do nothing.
-__device__ __forceinline__ void tri_inv_row(const double2* __restrict__ T, int64_t ldt, int b, bool upper,
-                                            double2* __restrict__ X, int64_t ldx, int i) {
-  const double2 one = make_double2(1.0, 0.0), zero = make_double2(0.0, 0.0);
-  const bool act = i < b;
-  if (!upper) {
-    if (act)
-      for (int c = i; c < b; ++c) X[i + (int64_t)c * ldx] = c == i ? one : zero;
-    for (int c = b - 2; c >= 0; --c) {
-      if (act && i > c) {
-        double2 s = zero;
-        for (int t = c + 1; t <= i; ++t) s = cfms(X[i + (int64_t)t * ldx], T[t + (int64_t)c * ldt], s);
-        X[i + (int64_t)c * ldx] = s;
-      }
-    }
-  } else {
-    if (act) {
-      for (int c = 0; c < i; ++c) X[i + (int64_t)c * ldx] = zero;
-      const double2 dii = T[i + (int64_t)i * ldt];
-      X[i + (int64_t)i * ldx] = (dii.x == 0.0 && dii.y == 0.0) ? zero : cdiv(one, dii);
-    }
-    for (int c = 1; c < b; ++c) {
-      if (act && i < c) {
-        double2 s = zero;
-        for (int t = c - 1; t >= i; --t) s = cfms(X[i + (int64_t)t * ldx], T[t + (int64_t)c * ldt], s);
-        const double2 dcc = T[c + (int64_t)c * ldt];
-        X[i + (int64_t)c * ldx] = (dcc.x == 0.0 && dcc.y == 0.0) ? zero : cdiv(s, dcc);
-      }
-    }
-  }
-}
-
-// X = L^-1 for the unit lower triangle L of A[r0 : r0+nb, r0 : r0+nb] (X nb x nb, ldx = nb),
-// one thread per row.
+// X = L^-1 for the unit lower triangle L of A[r0 : r0+nb, r0 : r0+nb] (X nb x nb, ldx = nb):
+// one thread per column j, x_ij = -sum_{j<=t<i} l_it x_tj.
 __global__ void k_lub_trinv(const double2* __restrict__ A, int64_t lda, int r0, int nb, double2* __restrict__ X) {
-  tri_inv_row(A + r0 + (int64_t)r0 * lda, lda, nb, false, X, nb, blockIdx.x * blockDim.x + threadIdx.x);
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= nb) return;
+  double2* x = X + (int64_t)j * nb;
+  for (int i = 0; i < j; ++i) x[i] = make_double2(0.0, 0.0);
+  x[j] = make_double2(1.0, 0.0);
+  for (int i = j + 1; i < nb; ++i) {
+    double2 s = make_double2(0.0, 0.0);
+    const double2* li = A + (r0 + i) + (int64_t)r0 * lda;
+    for (int t = j; t < i; ++t) s = cfms(li[(int64_t)t * lda], x[t], s);
+    x[i] = s;
+  }
 }
 
 // C[m x nc] -= A[m x k] B[k x nc] (the updates inside a panel), FP64 tiles.
@@ -1342,29 +1313,74 @@ __global__ void k_lut_swap(const LuSolveDesc* __restrict__ d, int j0, int jb) {
 
 // X = inverse of the unit lower (upper = 0) or of the upper (upper = 1, non-unit) triangle of
 // the diagonal block A[j0 : j0+jb, j0 : j0+jb] of item blockIdx.y; X: jb x jb (ld jb) at
-// X + blockIdx.y * ldx_item.  One thread per row (tri_inv_row).
+// X + blockIdx.y * ldx_item.  One thread per column j: x_ij from the rows before (lower) or
+// after (upper) it.
 __global__ void k_lut_trinv(const LuSolveDesc* __restrict__ d, int j0, int jb, int upper,
                             double2* __restrict__ Xall, int64_t ldx_item) {
   const LuSolveDesc q = d[blockIdx.y];
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j0 >= q.n) return;
   const int b = min(jb, q.n - j0);
-  tri_inv_row(q.A + j0 + (int64_t)j0 * q.lda, q.lda, b, upper != 0, Xall + blockIdx.y * ldx_item, b,
-              blockIdx.x * blockDim.x + threadIdx.x);
+  if (j >= b) return;
+  double2* x = Xall + blockIdx.y * ldx_item + (int64_t)j * b;
+  const double2* T = q.A + j0 + (int64_t)j0 * q.lda;
+  const double2 one = make_double2(1.0, 0.0), zero = make_double2(0.0, 0.0);
+  if (!upper) {
+    for (int i = 0; i < j; ++i) x[i] = zero;
+    x[j] = one;
+    for (int i = j + 1; i < b; ++i) {
+      double2 s = zero;
+      for (int t = j; t < i; ++t) s = cfms(T[i + (int64_t)t * q.lda], x[t], s);
+      x[i] = s;
+    }
+  } else {
+    for (int i = j + 1; i < b; ++i) x[i] = zero;
+    const double2 djj = T[j + (int64_t)j * q.lda];
+    x[j] = (djj.x == 0.0 && djj.y == 0.0) ? zero : cdiv(one, djj);
+    for (int i = j - 1; i >= 0; --i) {
+      double2 s = zero;
+      for (int t = i + 1; t <= j; ++t) s = cfms(T[i + (int64_t)t * q.lda], x[t], s);
+      const double2 dii = T[i + (int64_t)i * q.lda];
+      x[i] = (dii.x == 0.0 && dii.y == 0.0) ? zero : cdiv(s, dii);
+    }
+  }
 }
 
 // Inverses of the diagonal blocks of LU factors (unit lower L, upper U), for block triangular
 // solves whose products run on the tensor cores.  Item blockIdx.y with block width nb = q.nb,
 // block p = blockIdx.x (rows and columns p nb .. min(n, (p + 1) nb)), blockIdx.z = 0: L_pp^-1
 // into Linv + p nb^2, 1: U_pp^-1 into Uinv + p nb^2 (column-major, leading dimension nb; the
-// part outside a ragged last block is not written), one thread per row (tri_inv_row).  A zero
-// diagonal entry of U leaves zeros in U_pp^-1.
+// part outside a ragged last block is not written).  Thread j forms column j by substitution.
+// A zero diagonal entry of U leaves a zero row in U_pp^-1.
 __global__ void k_lu_dinv(const DinvDesc* __restrict__ d) {
   const DinvDesc q = d[blockIdx.y];
   const int nb = q.nb, p = blockIdx.x, j0 = p * nb;
   if (j0 >= q.n) return;
+  const int b = min(nb, q.n - j0), j = threadIdx.x;
+  if (j >= b) return;
   const bool upper = blockIdx.z != 0;
-  tri_inv_row(q.A + j0 + (int64_t)j0 * q.lda, q.lda, min(nb, q.n - j0), upper,
-              (upper ? q.Uinv : q.Linv) + (int64_t)p * nb * nb, nb, threadIdx.x);
+  double2* x = (upper ? q.Uinv : q.Linv) + (int64_t)p * nb * nb + (int64_t)j * nb;
+  const double2* T = q.A + j0 + (int64_t)j0 * q.lda;
+  const double2 one = make_double2(1.0, 0.0), zero = make_double2(0.0, 0.0);
+  if (!upper) {
+    for (int i = 0; i < j; ++i) x[i] = zero;
+    x[j] = one;
+    for (int i = j + 1; i < b; ++i) {
+      double2 s = zero;
+      for (int t = j; t < i; ++t) s = cfms(T[i + (int64_t)t * q.lda], x[t], s);
+      x[i] = s;
+    }
+  } else {
+    for (int i = j + 1; i < b; ++i) x[i] = zero;
+    const double2 djj = T[j + (int64_t)j * q.lda];
+    x[j] = (djj.x == 0.0 && djj.y == 0.0) ? zero : cdiv(one, djj);
+    for (int i = j - 1; i >= 0; --i) {
+      double2 s = zero;
+      for (int t = i + 1; t <= j; ++t) s = cfms(T[i + (int64_t)t * q.lda], x[t], s);
+      const double2 dii = T[i + (int64_t)i * q.lda];
+      x[i] = (dii.x == 0.0 && dii.y == 0.0) ? zero : cdiv(s, dii);
+    }
+  }
 }
 
 int wsbm_lu_dinv_batched(const DinvDesc* d_desc, int nitems, int max_blocks, int max_nb, cudaStream_t st) {
