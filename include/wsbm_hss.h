@@ -426,8 +426,8 @@ int wsbm_lu_dense(void* A, int64_t lda, int32_t n, int32_t* piv, void* stream);
  *   out[4]  columns per warp pass of the column-pivoted QR of ID matrices of more than 2048
  *           rows, of {2, 4, 8} (152 matrices of 2560 x 128).
  * ms: host, 10 doubles or NULL: the candidates' times in that order.  Work space (two copies of
- * the boxes, two n_root x n_root matrices, about 1.2 GiB for the product and 1.5 GiB for the QRs) from the
- * library's allocator.  Sizes: 64 <= n_box <= 4096, 1 <= nbox <= 32767, 1 <= nrhs_box <= 4096,
+ * the boxes, two n_root x n_root matrices, about 1.2 GiB for the product and 1.5 GiB for the
+ * QRs) from the library's allocator.  Sizes: 64 <= n_box <= 4096, 1 <= nbox <= 32767, 1 <= nrhs_box <= 4096,
  * at most 8 GiB of boxes, 256 <= n_root <= 32768.  Defaults without a call: 8, 64, 128, 256, 4.
  * Synchronous.  Errors: INVALID_ARG, OOM, CUDA, TIMEOUT. */
 int wsbm_autotune(int32_t n_box, int32_t nbox, int32_t nrhs_box, int32_t n_root, int32_t* out,
