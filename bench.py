@@ -57,7 +57,7 @@ FP64_DFMA_MEASURED = (1.013, 2000.0)
 
 
 def measured_peaks():
-    """The measured peaks of this GPU pool (HBM copy, cuBLAS BF16), when present."""
+    """Measured peaks of this GPU model (HBM copy, cuBLAS BF16) from MEASURED_PEAKS.json, when present."""
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
             return json.load(fh)
